@@ -1,0 +1,66 @@
+"""Planted mistakes in the CPU oracle must fail the pins (no GPU).
+
+Each case edits a copy of oracle/mh_oracle.c (a dropped term, a wrong
+operand, an off-by-one, a wrong bound), compiles it to a temporary library
+and checks that the exact-enumeration, marginal or weight-law pin rejects it.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.oracle_pins import enumeration_pvalue, marginal_zmax, weight_pvalue
+from tests.test_oracle import UBCM_CASES, UECM_X, UECM_Y
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "mh_oracle.c")
+
+# (name, original text, replacement, which pin should catch it)
+MUTATIONS = [
+    ("skip_missing_plus_one", "int64_t j = pos + 1 + (int64_t)floor(t);", "int64_t j = pos + (int64_t)floor(t);",
+     "ubcm"),
+    ("accept_without_dividing_by_q", "if (V < p / q) {", "if (V < p) {", "ubcm"),
+    ("first_candidate_without_skip", "double t = (q >= 1.0) ? 0.0 : log(U) / log1p(-q);",
+     "double t = (q >= 1.0 || d == 1) ? 0.0 : log(U) / log1p(-q);", "ubcm"),
+    ("sort_ascending", "if (a->key > b->key) return -1;\n    if (a->key < b->key) return 1;",
+     "if (a->key > b->key) return 1;\n    if (a->key < b->key) return -1;", "ubcm"),
+    ("ubcm_q_not_updated_to_p", "q = uecm ? prob_hat(g, i, j, c) : p;", "q = uecm ? prob_hat(g, i, j, c) : q * 0.5;",
+     "ubcm"),
+    ("uecm_q_from_p_not_phat", "q = uecm ? prob_hat(g, i, j, c) : p;", "q = p;", "uecm"),
+    ("uecm_bound_from_head_y_only", "return g->ys[i] * g->ymax[a];", "return g->ys[i] * g->ys[a];", "uecm"),
+    ("uecm_r_dropped_from_p", "return A / ((1.0 - r) + A);", "return A / (1.0 + A);", "uecm"),
+    ("weight_log_of_one_minus_r", "double tw = log(Uw) / log(r);", "double tw = log(Uw) / log1p(-r);", "weight"),
+    ("weight_missing_plus_one", "wt = 1 + (int32_t)floor(tw);", "wt = (int32_t)floor(tw);", "weight"),
+]
+
+
+def _compile(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation {name}: text not found"
+    mutated = src.replace(old, new)
+    c_path = tmp_path / f"{name}.c"
+    so_path = tmp_path / f"{name}.so"
+    c_path.write_text(mutated)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so_path),
+                    str(c_path), "-lm"], check=True)
+    return oracle.load(str(so_path))
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, pin):
+    lib = _compile(tmp_path, name, old, new)
+    if pin == "ubcm":
+        pvals = [enumeration_pvalue(oracle.UBCM, x, samples=20000, lib=lib, seg_target=T)
+                 for x in UBCM_CASES for T in (2, 1 << 30)]
+        assert min(pvals) < 1e-8
+    elif pin == "uecm":
+        p = min(enumeration_pvalue(oracle.UECM, UECM_X, UECM_Y, samples=40000, lib=lib, seg_target=T)
+                for T in (2, 1 << 30))
+        rng = np.random.default_rng(3)
+        x = np.exp(rng.normal(-0.5, 1.2, 12))
+        y = rng.uniform(0.1, 0.9, 12)
+        z = marginal_zmax(oracle.UECM, x, y, lib=lib)
+        assert p < 1e-8 or z > 8.0
+    else:
+        assert weight_pvalue(UECM_X, UECM_Y, lib=lib) < 1e-8
