@@ -1,0 +1,342 @@
+"""Benchmark: sampled edges/s of the Miller-Hagberg UECM sampler on one GB300.
+
+One step = one mh_sample_weighted call over the weighted degree+strength
+workload (N = 20,000, x = exp(z), z ~ N(-4.0, 1.2), y ~ U(0.3, 0.9), FP64),
+drawing 10 samples as int32 COO edges plus int32 geometric weights: node
+sort, bound preparation, row-segment table, proposal walk, edge emission.
+Inputs are resident in HBM; the L2 is flushed (a 512 MiB write) before every
+timed step.  Under torchrun each rank draws its own 10 samples (weak
+scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle
+(the serial FP64 walk, one sample per step) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "uecm_n20k_x10"
+SAMPLES_PER_STEP = 10
+BYTES_PER_EDGE = 12          # int32 src + int32 dst + int32 weight
+METRIC = "sampled edges/s on 1 GB300 (batched vs per-sample loop), % HBM write roofline"
+WALK_SOURCES = ["paper_2509_13230_gb300/csrc/walk.cu", "paper_2509_13230_gb300/csrc/walk_math.cuh",
+                "paper_2509_13230_gb300/csrc/mh_internal.cuh"]
+WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_kernel_uecm_n20k_x10.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload():
+    from paper_2509_13230_gb300 import workloads
+    return workloads.uecm_n20k()
+
+
+def sources_hash() -> str:
+    h = hashlib.sha256()
+    for p in WALK_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def rejected(clocks) -> bool:
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clocks.get("reasons", [])):
+        return True
+    sm, mx = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    return bool(sm and mx and sm < 0.5 * mx and not clocks.get("reasons"))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_rate(net, seconds: float, first_sample: int = 0):
+    """Edges/s of the serial oracle over whole samples, for about `seconds`."""
+    import oracle
+    oracle.load()
+    edges, t_total, s = 0, 0.0, first_sample
+    while t_total < seconds:
+        t0 = time.perf_counter()
+        _, _, _, counts, _ = oracle.mh_sample(oracle.UECM, net.x, net.y, sample_begin=s, num_samples=1)
+        t_total += time.perf_counter() - t0
+        edges += int(counts.sum())
+        s += 1
+    return edges / t_total, s - first_sample, t_total
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.load()
+    net = workload()
+    for w in range(args.warmup):
+        oracle.mh_sample(oracle.UECM, net.x, net.y, sample_begin=w, num_samples=1)
+    edges, t = 0, 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, _, counts, _ = oracle.mh_sample(oracle.UECM, net.x, net.y, sample_begin=k % SAMPLES_PER_STEP,
+                                              num_samples=1)
+        t += time.perf_counter() - t0
+        edges += int(counts.sum())
+    value = edges / t
+    sample = (f"one of the {SAMPLES_PER_STEP} samples of {WORKLOAD} per step (N = {net.n}), serial FP64 oracle, "
+              f"single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": net.n, "samples_per_step": 1, "output": "coo int32 + w int32"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.sampler import Sampler
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    net = workload()
+    x = torch.from_numpy(net.x).to(dev)
+    y = torch.from_numpy(net.y).to(dev)
+    first = rank * SAMPLES_PER_STEP
+    s = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, sample_begin=first)
+    s.run()                                     # sizes the output buffers
+    s.flags |= nat.MH_TIMING
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_region():
+        for _ in range(args.warmup):
+            nat.check(s.call(), "mh_sample_weighted")
+        barrier()
+        total_ms, walk_ms, edges, launches = 0.0, [], 0, 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                ev0.record(stream)
+                nat.check(s.call(), "mh_sample_weighted")
+                ev1.record(stream)
+                ev1.synchronize()
+                total_ms += ev0.elapsed_time(ev1)
+                info = nat.mh_last_call_info()
+                walk_ms.append(info.walk_ms)
+                launches += info.kernel_launches
+                edges += int(s.h_counts.sum())
+        barrier()
+        return total_ms, walk_ms, edges, launches, clk.summary()
+
+    total_ms, walk_ms, edges, launches, clocks = timed_region()
+    if rejected(clocks):
+        total_ms, walk_ms, edges, launches, clocks = timed_region()
+        clocks["remeasured"] = True
+    t = torch.tensor([total_ms, float(edges)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        max_ms, all_edges = float(tmax[0]), float(tsum[1])
+    else:
+        max_ms, all_edges = total_ms, float(edges)
+    value = all_edges / (max_ms / 1e3)
+
+    # per-sample launch loop: the same samples drawn by one call each
+    s1 = Sampler(nat.MH_UECM, x, y, num_samples=1, sample_begin=first)
+    s1.run()
+    for _ in range(args.warmup):
+        s1.call()
+    torch.cuda.synchronize()
+    loop_ms, loop_edges = 0.0, 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(1, args.steps // 2)):
+        flush.zero_()
+        ev0.record(stream)
+        for k in range(SAMPLES_PER_STEP):
+            nat.check(s1.call(sample_begin=first + k), "mh_sample_weighted")
+            loop_edges += int(s1.h_counts.sum())
+        ev1.record(stream)
+        ev1.synchronize()
+        loop_ms += ev0.elapsed_time(ev1)
+    loop_value = loop_edges / (loop_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    hx = torch.from_numpy(net.x).pin_memory()
+    hy = torch.from_numpy(net.y).pin_memory()
+    cap = s.capacity
+    hsrc = torch.empty(cap, dtype=torch.int32).pin_memory()
+    hdst = torch.empty(cap, dtype=torch.int32).pin_memory()
+    hw = torch.empty(cap, dtype=torch.int32).pin_memory()
+    e2e_ms, e2e_edges, d2h = 0.0, 0, 0
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        x.copy_(hx, non_blocking=True)
+        y.copy_(hy, non_blocking=True)
+        nat.check(s.call(), "mh_sample_weighted")
+        m = int(s.h_counts.sum())
+        hsrc[:m].copy_(s.src[:m], non_blocking=True)
+        hdst[:m].copy_(s.dst[:m], non_blocking=True)
+        hw[:m].copy_(s.w[:m], non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if it >= args.warmup:
+            e2e_ms += ev0.elapsed_time(ev1)
+            e2e_edges += m
+            d2h += 12 * m + 8 * SAMPLES_PER_STEP
+    e2e_value = e2e_edges / (e2e_ms / 1e3)
+    if world > 1:
+        dist.barrier()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    hbm_gbs, peak_kind = peaks()
+    walk_avg_ms = float(np.mean(walk_ms))
+    edges_per_step = edges / args.steps
+    achieved = BYTES_PER_EDGE * edges_per_step / (walk_avg_ms / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(WALK_PROFILE):
+        prof = json.load(open(WALK_PROFILE))
+        if prof.get("sources_sha") == sources_hash():
+            traffic = prof.get("dram_bytes_per_launch")
+    # CPU oracle on a bounded sample of the same workload (rank 0, N = 1 only)
+    cpu = None
+    if world == 1:
+        rate, nsamp, secs = oracle_rate(net, 10.0)
+        cpu = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nsamp} whole samples of {WORKLOAD} (N = {net.n}), serial FP64 walk, "
+                         f"{secs:.1f} s on one host core"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": net.n, "samples_per_step": SAMPLES_PER_STEP * world,
+                   "output": "coo int32 + w int32 (12 B/edge)", "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": achieved / hbm_gbs, "traffic": traffic, "kernel": "walk_kernel",
+                     "peak_kind": peak_kind, "walk_ms_per_launch": walk_avg_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 16 * net.n,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * maxent_mh.h — C ABI of the GB300 sampler for maximum-entropy network
+ * models (Li, Wang, Kojaku, "Fast unbiased sampling of networks with given
+ * expected degrees and strengths", arXiv 2509.13230).
+ *
+ * Parameters.  The paper writes node parameters as alpha_i (degree) and
+ * beta_i (strength).  This ABI takes x_i = exp(-alpha_i) >= 0 and
+ * y_i = exp(-beta_i) in [0, 1), as FP64 arrays indexed by original node id.
+ *
+ *   UBCM edge probability (Sec. 2.2, Eq. 1):  p_ij = x_i x_j / (1 + x_i x_j)
+ *   UECM edge probability (Sec. 2.5, Eq. 3):  p_ij = A / (1 - r + A),
+ *        A = x_i y_i x_j y_j,  r = y_i y_j
+ *   UECM weight given an edge (Eq. 4):         P(w) = r^(w-1) (1 - r), w >= 1
+ *
+ * Memory.  Every pointer is a DEVICE pointer unless its name starts with
+ * h_ (host memory).  The caller owns all memory, including the workspace,
+ * whose size mh_workspace_size() returns.  Nothing here allocates device
+ * memory; the library keeps one small pinned host buffer per thread for the
+ * final read-back of counts.
+ *
+ * Streams.  All device work is ordered on the given stream (NULL = the
+ * legacy default stream).  The sampling calls read back the edge counts and
+ * a status word at the end, so they return only after their device work is
+ * done; maxent_expected_fwd / _bwd return without synchronising.
+ *
+ * Errors.  Every call returns MH_OK (0) or a negative MH_ERR_* code; no C++
+ * exception crosses the ABI.  mh_error_string() names a code and
+ * mh_last_error_detail() gives the calling thread's last message.
+ *
+ * Sampled bits.  A sample is a pure function of (x, y, seed, network_id,
+ * sample index, seg_target, flags): re-running a call reproduces it bit for
+ * bit, and sample s of a batch equals the same sample drawn alone.
+ */
+#ifndef MAXENT_MH_H
+#define MAXENT_MH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
+
+/* models */
+#define MH_UBCM 0 /* unweighted binary configuration model, Eq. 1          */
+#define MH_UECM 1 /* weighted enhanced configuration model, Eqs. 2-4       */
+
+/* return codes */
+#define MH_OK 0
+#define MH_ERR_ARG -1            /* bad size, null required pointer, bad flag        */
+#define MH_ERR_DOMAIN -2         /* x not finite / < 0 / > 1e150, or y outside [0,1) */
+#define MH_ERR_CAPACITY -3       /* output shorter than the sample; counts returned  */
+#define MH_ERR_WORKSPACE -4      /* workspace too small or segment table overflow    */
+#define MH_ERR_OVERFLOW -5       /* a weight above INT32_MAX                         */
+#define MH_ERR_DEVICE_TIMEOUT -6 /* a bounded device wait gave up                    */
+#define MH_ERR_CUDA -7           /* a CUDA runtime call failed                       */
+
+/* flags */
+#define MH_OUT_COO 0x01u     /* write src/dst (and w) edge arrays                  */
+#define MH_OUT_CSR 0x02u     /* write CSR offsets/indices (and weights)            */
+#define MH_BOUND_PAPER 0x10u /* UECM: c = product of the two largest y among the   */
+                             /* nodes not yet processed (Sec. 2.5); default is     */
+                             /* c = y_i * max_{j >= segment head} y_j              */
+#define MH_INIT_PREV 0x20u   /* first proposal q = p at the rank before the        */
+                             /* segment head (p_ii for a row's first segment,      */
+                             /* Sec. 2.4 step (ii)); default: q = p at the head    */
+#define MH_FP64_ONLY 0x100u  /* decide every draw with the plain FP64 path         */
+#define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
+                             /* caller's stream (see mh_last_call_info)            */
+
+/* stats slots (h_stats, 4 x uint64) */
+#define MH_STAT_PROPOSALS 0 /* candidate draws                                     */
+#define MH_STAT_EDGES 1     /* accepted edges                                      */
+#define MH_STAT_SEGMENTS 2  /* segments walked (samples x table rows)              */
+#define MH_STAT_FALLBACKS 3 /* draws the fast filter left to the FP64 path         */
+
+typedef struct mh_params {
+    uint64_t seed;         /* Philox key: (seed lo32, seed hi32 + network_id)       */
+    uint32_t network_id;   /* 0 for single-network calls                            */
+    uint32_t sample_begin; /* first sample index (Philox counter word 3)            */
+    uint32_t num_samples;  /* samples drawn by this call, >= 1                      */
+    uint32_t seg_target;   /* T: expected proposals per row segment, >= 2;          */
+                           /* 0 selects 32.  Part of a sample's identity.           */
+    uint32_t flags;        /* MH_OUT_*, MH_BOUND_PAPER, MH_INIT_PREV, MH_FP64_ONLY  */
+    uint32_t reserved;     /* must be 0                                             */
+    int64_t max_segments;  /* row-segment table capacity; 0 selects 4 n + 1024      */
+} mh_params;
+
+/* Per-call record of the calling thread's last sampling call. */
+typedef struct mh_call_info {
+    int64_t kernel_launches; /* kernels this library launched in the call          */
+    int64_t walk_launches;   /* launches of the proposal-walk kernel                */
+    int64_t sample_chunks;   /* sample chunks the call was split into               */
+    double prepare_ms;       /* MH_TIMING: sort + bound prep + segment table        */
+    double walk_ms;          /* MH_TIMING: proposal walk (all chunks)               */
+    double emit_ms;          /* MH_TIMING: scans + edge output (all chunks)         */
+    double total_ms;         /* MH_TIMING: whole call, device time                  */
+} mh_call_info;
+
+/* Name of a return code (static string). */
+const char* mh_error_string(int code);
+
+/* Last error message of the calling thread (static per-thread buffer). */
+const char* mh_last_error_detail(void);
+
+/* Copies the calling thread's last mh_call_info (zeros before any call). */
+int mh_last_call_info(mh_call_info* h_info);
+
+/*
+ * Workspace bytes for a sampling call on a network of n nodes whose output
+ * holds up to capacity_edges edges (all samples of the call together).
+ * Returns MH_ERR_ARG for n < 1, capacity_edges < 0 or a bad params struct.
+ */
+int mh_workspace_size(int model, int64_t n, const mh_params* params, int64_t capacity_edges, size_t* h_bytes);
+
+/*
+ * mh_sample_ubcm — Miller-Hagberg rejection sampling of the UBCM (Sec. 2.3,
+ * Sec. 2.4 steps (i)-(iv)).  Nodes are sorted by descending x (ascending
+ * alpha), each row i's candidates j > i are cut into segments of about
+ * seg_target expected proposals, and each segment is walked with geometric
+ * skips of parameter q, acceptance with probability p_ij / q and q <- p_ij.
+ *
+ *   x                 FP64[n], original node order
+ *   src, dst          COO output, int32[capacity_edges] each (MH_OUT_COO),
+ *                     original node ids; edge (u, v) has u the endpoint of
+ *                     higher x.  Samples are concatenated in sample order,
+ *                     edges of a sample in (rank of u, rank of v) order.
+ *   csr_offsets       int64[num_samples * (n + 1)] (MH_OUT_CSR): sample s,
+ *                     node u owns csr_indices[off[s(n+1)+u] .. off[s(n+1)+u+1]),
+ *                     the edges whose higher-ranked endpoint is u; offsets are
+ *                     global positions in csr_indices.
+ *   csr_indices       int32[capacity_edges] (MH_OUT_CSR)
+ *   capacity_edges    length of each edge output array
+ *   h_edges_per_sample host int64[num_samples]: edges of each sample
+ *   h_stats           host uint64[4] (MH_STAT_*), or NULL
+ *
+ * On MH_ERR_CAPACITY the exact counts are in h_edges_per_sample and nothing
+ * past capacity_edges was written; re-calling with more room reproduces the
+ * same sample.
+ */
+int mh_sample_ubcm(const double* x, int64_t n, const mh_params* params, void* workspace, size_t workspace_bytes,
+                   int32_t* src, int32_t* dst, int64_t* csr_offsets, int32_t* csr_indices, int64_t capacity_edges,
+                   int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
+
+/*
+ * mh_sample_weighted — the UECM sampler of Algorithm 1 (Sec. 2.5).  Nodes are
+ * sorted by descending a = x y (ascending alpha + beta); proposals use the
+ * bound phat_ij = A / (1 - c + A) of Eq. 5 with q <- phat_ij, and each
+ * accepted edge draws its weight w ~ Geometric(1 - r_ij) on {1, 2, ...}.
+ * Arguments as mh_sample_ubcm, plus
+ *   y                 FP64[n] in [0, 1)
+ *   w, csr_weights    int32[capacity_edges] weights aligned with src/dst and
+ *                     csr_indices (either may be NULL when its layout is off)
+ */
+int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_params* params, void* workspace,
+                       size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w, int64_t* csr_offsets,
+                       int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
+                       int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
+
+/*
+ * mh_segment_table — the node order and row-segment table a sampling call
+ * with the same arguments walks (for inspection and tests).
+ *   seg_row, seg_k    int32[cap]: row rank i and segment index k within row i
+ *   seg_a, seg_b      int64[cap]: segment candidates are ranks [a, b)
+ *   perm              int32[n]: perm[rank] = original node id
+ *   h_num_segments    host: number of segments (written even when > cap)
+ * Returns MH_ERR_CAPACITY when the table has more than cap rows.
+ */
+int mh_segment_table(int model, const double* x, const double* y, int64_t n, const mh_params* params,
+                     void* workspace, size_t workspace_bytes, int32_t* seg_row, int32_t* seg_k, int64_t* seg_a,
+                     int64_t* seg_b, int32_t* perm, int64_t cap, int64_t* h_num_segments, mh_stream_t stream);
+
+/*
+ * maxent_expected_fwd — expected degrees and strengths, the O(N^2) sums
+ * behind maximum-likelihood inference (Sec. 2.2, Sec. 2.5, Sec. 4):
+ *   k_out[i] = sum_{j != i} p_ij
+ *   s_out[i] = sum_{j != i} p_ij / (1 - r_ij)     (UECM; E[w | w > 0] = 1/(1-r))
+ * x, y (y NULL for UBCM), k_out, s_out (NULL for UBCM): FP64[n].
+ * Each pair term is recomputed tile by tile; no N^2 storage.
+ */
+int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
+                        mh_stream_t stream);
+
+/*
+ * maxent_expected_bwd — gradient of a loss L(<k>, <s>) with respect to x
+ * (and y) given g_k = dL/d<k> and g_s = dL/d<s> (NULL for UBCM):
+ *   g_x[i] = sum_{j != i} (g_k[i] + g_k[j]) dp_ij/dx_i + (g_s[i] + g_s[j]) dm_ij/dx_i
+ * with m_ij = p_ij / (1 - r_ij); g_y likewise with d/dy_i (UECM; NULL for UBCM).
+ */
+int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                        const double* g_s, double* g_x, double* g_y, mh_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAXENT_MH_H */

@@ -1,0 +1,185 @@
+"""ctypes binding of libmaxent_mh.so (include/maxent_mh.h), argument marshalling only.
+
+The library must be built (``paper_2509_13230_gb300.build``); a missing
+library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MH_UBCM = 0
+MH_UECM = 1
+
+MH_OK = 0
+MH_ERR_ARG = -1
+MH_ERR_DOMAIN = -2
+MH_ERR_CAPACITY = -3
+MH_ERR_WORKSPACE = -4
+MH_ERR_OVERFLOW = -5
+MH_ERR_DEVICE_TIMEOUT = -6
+MH_ERR_CUDA = -7
+
+MH_OUT_COO = 0x01
+MH_OUT_CSR = 0x02
+MH_BOUND_PAPER = 0x10
+MH_INIT_PREV = 0x20
+MH_FP64_ONLY = 0x100
+MH_TIMING = 0x200
+
+MH_STAT_PROPOSALS = 0
+MH_STAT_EDGES = 1
+MH_STAT_SEGMENTS = 2
+MH_STAT_FALLBACKS = 3
+
+# Every symbol include/maxent_mh.h declares.
+EXPORTED = (
+    "mh_error_string",
+    "mh_last_error_detail",
+    "mh_last_call_info",
+    "mh_workspace_size",
+    "mh_sample_ubcm",
+    "mh_sample_weighted",
+    "mh_segment_table",
+    "maxent_expected_fwd",
+    "maxent_expected_bwd",
+)
+
+
+class MhParams(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("network_id", ctypes.c_uint32),
+        ("sample_begin", ctypes.c_uint32),
+        ("num_samples", ctypes.c_uint32),
+        ("seg_target", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("max_segments", ctypes.c_int64),
+    ]
+
+
+class MhCallInfo(ctypes.Structure):
+    _fields_ = [
+        ("kernel_launches", ctypes.c_int64),
+        ("walk_launches", ctypes.c_int64),
+        ("sample_chunks", ctypes.c_int64),
+        ("prepare_ms", ctypes.c_double),
+        ("walk_ms", ctypes.c_double),
+        ("emit_ms", ctypes.c_double),
+        ("total_ms", ctypes.c_double),
+    ]
+
+
+class MhError(RuntimeError):
+    def __init__(self, code: int, func: str, detail: str):
+        super().__init__(f"{func}: {error_string(code)} ({detail})")
+        self.code = code
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None and path is None:
+            return _LIB
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_2509_13230_gb300.build` "
+                               "(there is no fallback implementation)")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        P = ctypes.POINTER(MhParams)
+        lib.mh_error_string.argtypes = [i32]
+        lib.mh_error_string.restype = ctypes.c_char_p
+        lib.mh_last_error_detail.argtypes = []
+        lib.mh_last_error_detail.restype = ctypes.c_char_p
+        lib.mh_last_call_info.argtypes = [ctypes.POINTER(MhCallInfo)]
+        lib.mh_last_call_info.restype = i32
+        lib.mh_workspace_size.argtypes = [i32, i64, P, i64, ctypes.POINTER(sz)]
+        lib.mh_workspace_size.restype = i32
+        lib.mh_sample_ubcm.argtypes = [vp, i64, P, vp, sz, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_ubcm.restype = i32
+        lib.mh_sample_weighted.argtypes = [vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_weighted.restype = i32
+        lib.mh_segment_table.argtypes = [i32, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp]
+        lib.mh_segment_table.restype = i32
+        lib.maxent_expected_fwd.argtypes = [i32, vp, vp, i64, vp, vp, vp]
+        lib.maxent_expected_fwd.restype = i32
+        lib.maxent_expected_bwd.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
+        lib.maxent_expected_bwd.restype = i32
+        if path is None:
+            _LIB = lib
+        return lib
+
+
+def error_string(code: int) -> str:
+    return load().mh_error_string(code).decode()
+
+
+def last_error_detail() -> str:
+    return load().mh_last_error_detail().decode()
+
+
+def check(code: int, func: str) -> int:
+    if code != MH_OK:
+        raise MhError(code, func, last_error_detail())
+    return code
+
+
+def make_params(*, seed=0, network_id=0, sample_begin=0, num_samples=1, seg_target=0, flags=MH_OUT_COO,
+                max_segments=0) -> MhParams:
+    return MhParams(int(seed) & 0xFFFFFFFFFFFFFFFF, int(network_id), int(sample_begin), int(num_samples),
+                    int(seg_target), int(flags), 0, int(max_segments))
+
+
+# ---- same names as the C ABI ------------------------------------------------------
+def mh_last_call_info() -> MhCallInfo:
+    info = MhCallInfo()
+    check(load().mh_last_call_info(ctypes.byref(info)), "mh_last_call_info")
+    return info
+
+
+def mh_workspace_size(model: int, n: int, params: MhParams, capacity_edges: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().mh_workspace_size(model, n, ctypes.byref(params), capacity_edges, ctypes.byref(out)),
+          "mh_workspace_size")
+    return out.value
+
+
+def mh_sample_ubcm(x, n, params, workspace, workspace_bytes, src, dst, csr_offsets, csr_indices, capacity_edges,
+                   h_edges_per_sample, h_stats, stream) -> int:
+    return load().mh_sample_ubcm(x, n, ctypes.byref(params), workspace, workspace_bytes, src, dst, csr_offsets,
+                                 csr_indices, capacity_edges, h_edges_per_sample, h_stats, stream)
+
+
+def mh_sample_weighted(x, y, n, params, workspace, workspace_bytes, src, dst, w, csr_offsets, csr_indices,
+                       csr_weights, capacity_edges, h_edges_per_sample, h_stats, stream) -> int:
+    return load().mh_sample_weighted(x, y, n, ctypes.byref(params), workspace, workspace_bytes, src, dst, w,
+                                     csr_offsets, csr_indices, csr_weights, capacity_edges, h_edges_per_sample,
+                                     h_stats, stream)
+
+
+def mh_segment_table(model, x, y, n, params, workspace, workspace_bytes, seg_row, seg_k, seg_a, seg_b, perm, cap,
+                     h_num_segments, stream) -> int:
+    return load().mh_segment_table(model, x, y, n, ctypes.byref(params), workspace, workspace_bytes, seg_row,
+                                   seg_k, seg_a, seg_b, perm, cap, h_num_segments, stream)
+
+
+def maxent_expected_fwd(model, x, y, n, k_out, s_out, stream) -> int:
+    return load().maxent_expected_fwd(model, x, y, n, k_out, s_out, stream)
+
+
+def maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream) -> int:
+    return load().maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream)

@@ -1,0 +1,487 @@
+// C ABI entry points (include/maxent_mh.h).
+//
+// A sampling call runs, in stream order and without a host round trip until
+// the end:  validate + sort keys -> radix sort -> gather into rank order ->
+// bound prep + segment table -> per sample chunk: walk -> emit.  It then
+// copies the status word, the counters and the per-sample edge counts to a
+// pinned host buffer, synchronises the stream and maps the status to a code.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "mh_internal.cuh"
+
+namespace mh {
+
+namespace {
+
+thread_local char g_detail[512] = "";
+thread_local mh_call_info g_info = {0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+thread_local int64_t g_launches = 0;
+
+// CUDA events of a timed call: start, after prepare, then (before walk,
+// after walk, after emit) per chunk.  Created on first use, per thread.
+struct CallTimer {
+  static constexpr int kMax = 2 + 3 * 64;
+  cudaEvent_t ev[kMax] = {};
+  bool ready = false;
+  int used = 0;
+  bool on = false;
+  cudaError_t start(bool enable, cudaStream_t s) {
+    on = enable;
+    used = 0;
+    if (!on) return cudaSuccess;
+    if (!ready) {
+      for (int t = 0; t < kMax; ++t) {
+        cudaError_t e = cudaEventCreate(&ev[t]);
+        if (e != cudaSuccess) return e;
+      }
+      ready = true;
+    }
+    return mark(s);
+  }
+  cudaError_t mark(cudaStream_t s) {
+    if (!on || used >= kMax) return cudaSuccess;
+    return cudaEventRecord(ev[used++], s);
+  }
+  float between(int a, int b) const {
+    float ms = 0.f;
+    if (a < used && b < used) cudaEventElapsedTime(&ms, ev[a], ev[b]);
+    return ms;
+  }
+};
+thread_local CallTimer g_timer;
+
+size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+struct PinnedBuffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ~PinnedBuffer() {
+    if (ptr) cudaFreeHost(ptr);
+  }
+  cudaError_t reserve(size_t want) {
+    if (want <= bytes) return cudaSuccess;
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaHostAlloc(&ptr, want, cudaHostAllocDefault);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+};
+thread_local PinnedBuffer g_pinned;
+
+constexpr uint32_t kKnownFlags =
+    MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_FP64_ONLY | MH_TIMING;
+
+}  // namespace
+
+void note_launches(int count) { g_launches += count; }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+  va_end(ap);
+}
+
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+static int64_t default_max_segments(int64_t n) { return 4 * n + 1024; }
+
+Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
+  (void)model;
+  Layout L;
+  L.n = n;
+  L.tiles = (n + kSortTile - 1) / kSortTile;
+  L.max_segments = p.max_segments > 0 ? p.max_segments : default_max_segments(n);
+  int64_t spc = kItemChunk / L.max_segments;
+  if (spc < 1) spc = 1;
+  if (spc > static_cast<int64_t>(p.num_samples)) spc = p.num_samples;
+  L.spc = spc;
+  L.items_max = spc * L.max_segments;
+  L.capacity = capacity;
+  int64_t scan_len = 256 * L.tiles;
+  if (n + 1 > scan_len) scan_len = n + 1;
+  if (L.items_max + 1 > scan_len) scan_len = L.items_max + 1;
+  if (spc * (n + 1) > scan_len) scan_len = spc * (n + 1);
+  L.scan_tmp_elems = scan_len / kScanTile + 2;
+  const size_t n1 = static_cast<size_t>(n) + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  L.ctrl = take(sizeof(Ctrl));
+  L.keys0 = take(8 * static_cast<size_t>(n));
+  L.keys1 = take(8 * static_cast<size_t>(n));
+  L.vals0 = take(4 * static_cast<size_t>(n));
+  L.vals1 = take(4 * static_cast<size_t>(n));
+  L.hist = take(4 * 256 * static_cast<size_t>(L.tiles));
+  L.perm = take(4 * static_cast<size_t>(n));
+  L.rank = take(4 * static_cast<size_t>(n));
+  L.xs = take(8 * static_cast<size_t>(n));
+  L.ys = take(8 * static_cast<size_t>(n));
+  L.as = take(8 * static_cast<size_t>(n));
+  L.ymax = take(8 * n1);
+  L.top1 = take(sizeof(Top2) * n1);
+  L.top2 = L.top1;
+  L.Q = take(8 * n1);
+  L.rowoff = take(8 * n1);
+  L.seg = take(sizeof(int4) * static_cast<size_t>(L.max_segments));
+  L.item_cnt = take(8 * static_cast<size_t>(L.items_max));
+  L.item_base = take(8 * static_cast<size_t>(L.items_max));
+  L.item_off = take(8 * (static_cast<size_t>(L.items_max) + 1));
+  L.ovf = take(4 * static_cast<size_t>(L.items_max));
+  L.sample_counts = take(8 * static_cast<size_t>(p.num_samples));
+  L.staging = take(4 * static_cast<size_t>(capacity));
+  L.scan_tmp = take(sizeof(Top2) * static_cast<size_t>(L.scan_tmp_elems));
+  L.total = off;
+  return L;
+}
+
+static Net make_net(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
+                    char* ws) {
+  Net g;
+  g.model = model;
+  g.flags = p.flags;
+  g.n = n;
+  g.x = x;
+  g.y = y;
+  g.perm = reinterpret_cast<int32_t*>(ws + L.perm);
+  g.rank = reinterpret_cast<int32_t*>(ws + L.rank);
+  g.xs = reinterpret_cast<double*>(ws + L.xs);
+  g.ys = reinterpret_cast<double*>(ws + L.ys);
+  g.as = (model == MH_UECM) ? reinterpret_cast<double*>(ws + L.as) : g.xs;
+  g.ymax = reinterpret_cast<double*>(ws + L.ymax);
+  g.top = reinterpret_cast<Top2*>(ws + L.top1);
+  g.Q = reinterpret_cast<unsigned long long*>(ws + L.Q);
+  g.rowoff = reinterpret_cast<long long*>(ws + L.rowoff);
+  g.seg = reinterpret_cast<int4*>(ws + L.seg);
+  g.max_segments = L.max_segments;
+  g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
+  return g;
+}
+
+static int check_params(int model, int64_t n, const mh_params* p) {
+  if (model != MH_UBCM && model != MH_UECM) {
+    set_error("model must be MH_UBCM or MH_UECM (got %d)", model);
+    return MH_ERR_ARG;
+  }
+  if (!p) {
+    set_error("params is NULL");
+    return MH_ERR_ARG;
+  }
+  if (n < 1 || n > 0x7FFFFFFEll) {
+    set_error("n must be in [1, 2^31 - 2] (got %lld)", static_cast<long long>(n));
+    return MH_ERR_ARG;
+  }
+  if (p->num_samples < 1) {
+    set_error("num_samples must be >= 1");
+    return MH_ERR_ARG;
+  }
+  if (static_cast<uint64_t>(p->sample_begin) + p->num_samples > 0xFFFFFFFFull) {
+    set_error("sample_begin + num_samples exceeds 2^32 - 1");
+    return MH_ERR_ARG;
+  }
+  if (p->seg_target == 1 || p->seg_target > (1u << 30)) {
+    set_error("seg_target must be 0 (default) or in [2, 2^30] (got %u)", p->seg_target);
+    return MH_ERR_ARG;
+  }
+  if (p->flags & ~kKnownFlags) {
+    set_error("unknown flag bits 0x%x", p->flags & ~kKnownFlags);
+    return MH_ERR_ARG;
+  }
+  if (p->reserved != 0 || p->max_segments < 0) {
+    set_error("reserved must be 0 and max_segments >= 0");
+    return MH_ERR_ARG;
+  }
+  if (p->max_segments > 0 && p->max_segments < n - 1) {
+    set_error("max_segments must be 0 or >= n - 1");
+    return MH_ERR_ARG;
+  }
+  return MH_OK;
+}
+
+#define MH_CUDA(expr)                                                             \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      set_error("%s failed: %s", #expr, cudaGetErrorString(e_));                  \
+      return MH_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+// Sort, gather, bound prep and segment table into the workspace.
+static int prepare(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  MH_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+  MH_CUDA(cudaMemsetAsync(&ctrl->key_and, 0xFF, sizeof(ctrl->key_and), s));
+  MH_CUDA(cudaMemsetAsync(g.ymax + g.n, 0, sizeof(double), s));
+  auto* keys0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
+  auto* vals0 = reinterpret_cast<int32_t*>(ws + L.vals0);
+  MH_CUDA(launch_validate_keys(g, keys0, vals0, ctrl, s));
+  MH_CUDA(launch_sort(g, L, ws, ctrl, s));
+  MH_CUDA(launch_gather(g, vals0, ctrl, s));
+  MH_CUDA(launch_bounds_and_partition(g, L, ws, ctrl, s));
+  return MH_OK;
+}
+
+static int status_to_code(unsigned status, long long num_segments, int64_t max_segments) {
+  if (status & kStDomain) {
+    set_error("x must be finite, >= 0 and <= 1e150; y must be in [0, 1)");
+    return MH_ERR_DOMAIN;
+  }
+  if (status & kStSegments) {
+    set_error("segment table needs %lld rows, max_segments is %lld", num_segments,
+              static_cast<long long>(max_segments));
+    return MH_ERR_WORKSPACE;
+  }
+  if (status & kStInternal) {
+    set_error("internal consistency check failed on the device");
+    return MH_ERR_CUDA;
+  }
+  if (status & kStTimeout) {
+    set_error("a bounded device wait gave up");
+    return MH_ERR_DEVICE_TIMEOUT;
+  }
+  if (status & kStOverflow) {
+    set_error("a sampled weight exceeds INT32_MAX");
+    return MH_ERR_OVERFLOW;
+  }
+  return MH_OK;
+}
+
+static int run_sample(int model, const double* x, const double* y, int64_t n, const mh_params* p, void* workspace,
+                      size_t workspace_bytes, const Outputs& o, int64_t* h_counts, uint64_t* h_stats,
+                      cudaStream_t s) {
+  int rc = check_params(model, n, p);
+  if (rc != MH_OK) return rc;
+  if (!x || (model == MH_UECM && !y) || !workspace || !h_counts) {
+    set_error("x%s, workspace and h_edges_per_sample must be non-NULL", model == MH_UECM ? ", y" : "");
+    return MH_ERR_ARG;
+  }
+  if (o.capacity < 0) {
+    set_error("capacity_edges must be >= 0");
+    return MH_ERR_ARG;
+  }
+  if ((p->flags & MH_OUT_COO) && o.capacity > 0 && (!o.src || !o.dst)) {
+    set_error("MH_OUT_COO needs src and dst");
+    return MH_ERR_ARG;
+  }
+  if ((p->flags & MH_OUT_CSR) && (!o.csr_off || (o.capacity > 0 && !o.csr_idx))) {
+    set_error("MH_OUT_CSR needs csr_offsets and csr_indices");
+    return MH_ERR_ARG;
+  }
+  const Layout L = make_layout(model, n, *p, o.capacity);
+  if (workspace_bytes < L.total) {
+    set_error("workspace needs %zu bytes, got %zu", L.total, workspace_bytes);
+    return MH_ERR_WORKSPACE;
+  }
+  char* ws = static_cast<char*>(workspace);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  const Net g = make_net(model, *p, x, y, n, L, ws);
+  g_launches = 0;
+  g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+  const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= 64;
+  MH_CUDA(g_timer.start(timed, s));
+  rc = prepare(g, L, ws, ctrl, s);
+  if (rc != MH_OK) return rc;
+  MH_CUDA(g_timer.mark(s));
+
+  Outputs out = o;
+  if (!(p->flags & MH_OUT_COO)) out.src = out.dst = out.w = nullptr;
+  if (!(p->flags & MH_OUT_CSR)) out.csr_off = nullptr, out.csr_idx = nullptr, out.csr_w = nullptr;
+  if (model == MH_UBCM) out.w = out.csr_w = nullptr;
+
+  ChunkArgs c;
+  c.key0 = static_cast<uint32_t>(p->seed);
+  c.key1 = static_cast<uint32_t>(p->seed >> 32) + p->network_id;
+  c.item_cnt = reinterpret_cast<long long*>(ws + L.item_cnt);
+  c.item_base = reinterpret_cast<long long*>(ws + L.item_base);
+  c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
+  c.ovf = reinterpret_cast<int32_t*>(ws + L.ovf);
+  c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
+  c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
+  c.scan_tmp = ws + L.scan_tmp;
+  c.staging_cap = o.capacity;
+  c.items_max = L.items_max;
+  for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
+    const int64_t left = static_cast<int64_t>(p->num_samples) - first;
+    c.chunk_first = first;
+    c.chunk_samples = left < L.spc ? left : L.spc;
+    c.sample0 = p->sample_begin + static_cast<uint32_t>(first);
+    MH_CUDA(cudaMemsetAsync(&ctrl->ticket, 0, 3 * sizeof(unsigned long long), s));
+    MH_CUDA(g_timer.mark(s));
+    MH_CUDA(launch_walk(g, c, ctrl, s));
+    MH_CUDA(g_timer.mark(s));
+    MH_CUDA(launch_emit(g, c, out, ctrl, s));
+    MH_CUDA(g_timer.mark(s));
+    g_info.walk_launches += 1;
+    g_info.sample_chunks += 1;
+  }
+
+  const size_t counts_bytes = 8 * static_cast<size_t>(p->num_samples);
+  MH_CUDA(g_pinned.reserve(sizeof(Ctrl) + counts_bytes));
+  char* hbuf = static_cast<char*>(g_pinned.ptr);
+  MH_CUDA(cudaMemcpyAsync(hbuf, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  MH_CUDA(cudaMemcpyAsync(hbuf + sizeof(Ctrl), c.sample_counts, counts_bytes, cudaMemcpyDeviceToHost, s));
+  MH_CUDA(cudaStreamSynchronize(s));
+  g_info.kernel_launches = g_launches;
+  if (timed) {
+    g_info.prepare_ms = g_timer.between(0, 1);
+    for (int64_t t = 0; t < g_info.sample_chunks; ++t) {
+      g_info.walk_ms += g_timer.between(static_cast<int>(2 + 3 * t), static_cast<int>(3 + 3 * t));
+      g_info.emit_ms += g_timer.between(static_cast<int>(3 + 3 * t), static_cast<int>(4 + 3 * t));
+    }
+    g_info.total_ms = g_timer.between(0, g_timer.used - 1);
+  }
+  Ctrl hc;
+  memcpy(&hc, hbuf, sizeof(Ctrl));
+  memcpy(h_counts, hbuf + sizeof(Ctrl), counts_bytes);
+  if (h_stats)
+    for (int t = 0; t < 4; ++t) h_stats[t] = hc.stats[t];
+  rc = status_to_code(hc.status, hc.num_segments, L.max_segments);
+  if (rc != MH_OK) return rc;
+  int64_t total = 0;
+  for (uint32_t t = 0; t < p->num_samples; ++t) total += h_counts[t];
+  if (total > o.capacity || (hc.status & kStCapacity)) {
+    set_error("the sample has %lld edges, capacity_edges is %lld", static_cast<long long>(total),
+              static_cast<long long>(o.capacity));
+    return MH_ERR_CAPACITY;
+  }
+  return MH_OK;
+}
+
+}  // namespace mh
+
+using namespace mh;
+
+extern "C" {
+
+const char* mh_error_string(int code) {
+  switch (code) {
+    case MH_OK: return "MH_OK";
+    case MH_ERR_ARG: return "MH_ERR_ARG: invalid argument";
+    case MH_ERR_DOMAIN: return "MH_ERR_DOMAIN: parameter outside the model's domain";
+    case MH_ERR_CAPACITY: return "MH_ERR_CAPACITY: output shorter than the sample";
+    case MH_ERR_WORKSPACE: return "MH_ERR_WORKSPACE: workspace or segment table too small";
+    case MH_ERR_OVERFLOW: return "MH_ERR_OVERFLOW: weight above INT32_MAX";
+    case MH_ERR_DEVICE_TIMEOUT: return "MH_ERR_DEVICE_TIMEOUT: bounded device wait gave up";
+    case MH_ERR_CUDA: return "MH_ERR_CUDA: CUDA runtime error";
+    default: return "unknown error code";
+  }
+}
+
+const char* mh_last_error_detail(void) { return g_detail; }
+
+int mh_last_call_info(mh_call_info* h_info) {
+  if (!h_info) {
+    set_error("h_info is NULL");
+    return MH_ERR_ARG;
+  }
+  *h_info = g_info;
+  return MH_OK;
+}
+
+int mh_workspace_size(int model, int64_t n, const mh_params* params, int64_t capacity_edges, size_t* h_bytes) {
+  int rc = check_params(model, n, params);
+  if (rc != MH_OK) return rc;
+  if (capacity_edges < 0 || !h_bytes) {
+    set_error("capacity_edges must be >= 0 and h_bytes non-NULL");
+    return MH_ERR_ARG;
+  }
+  *h_bytes = make_layout(model, n, *params, capacity_edges).total;
+  return MH_OK;
+}
+
+int mh_sample_ubcm(const double* x, int64_t n, const mh_params* params, void* workspace, size_t workspace_bytes,
+                   int32_t* src, int32_t* dst, int64_t* csr_offsets, int32_t* csr_indices, int64_t capacity_edges,
+                   int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream) {
+  Outputs o{src, dst, nullptr, reinterpret_cast<long long*>(csr_offsets), csr_indices, nullptr, capacity_edges};
+  return run_sample(MH_UBCM, x, nullptr, n, params, workspace, workspace_bytes, o, h_edges_per_sample, h_stats,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_params* params, void* workspace,
+                       size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w, int64_t* csr_offsets,
+                       int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
+                       int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream) {
+  Outputs o{src, dst, w, reinterpret_cast<long long*>(csr_offsets), csr_indices, csr_weights, capacity_edges};
+  return run_sample(MH_UECM, x, y, n, params, workspace, workspace_bytes, o, h_edges_per_sample, h_stats,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mh_segment_table(int model, const double* x, const double* y, int64_t n, const mh_params* params,
+                     void* workspace, size_t workspace_bytes, int32_t* seg_row, int32_t* seg_k, int64_t* seg_a,
+                     int64_t* seg_b, int32_t* perm, int64_t cap, int64_t* h_num_segments, mh_stream_t stream) {
+  int rc = check_params(model, n, params);
+  if (rc != MH_OK) return rc;
+  if (!x || (model == MH_UECM && !y) || !workspace || !h_num_segments || cap < 0 ||
+      (cap > 0 && (!seg_row || !seg_k || !seg_a || !seg_b))) {
+    set_error("missing pointer or negative cap");
+    return MH_ERR_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const Layout L = make_layout(model, n, *params, 0);
+  if (workspace_bytes < L.total) {
+    set_error("workspace needs %zu bytes, got %zu", L.total, workspace_bytes);
+    return MH_ERR_WORKSPACE;
+  }
+  char* ws = static_cast<char*>(workspace);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  const Net g = make_net(model, *params, x, y, n, L, ws);
+  rc = prepare(g, L, ws, ctrl, s);
+  if (rc != MH_OK) return rc;
+  if (cap > 0) MH_CUDA(launch_export_table(g, ctrl, seg_row, seg_k, seg_a, seg_b, cap, s));
+  if (perm) MH_CUDA(cudaMemcpyAsync(perm, g.perm, 4 * static_cast<size_t>(n), cudaMemcpyDeviceToDevice, s));
+  MH_CUDA(g_pinned.reserve(sizeof(Ctrl)));
+  MH_CUDA(cudaMemcpyAsync(g_pinned.ptr, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  MH_CUDA(cudaStreamSynchronize(s));
+  Ctrl hc;
+  memcpy(&hc, g_pinned.ptr, sizeof(Ctrl));
+  *h_num_segments = hc.num_segments;
+  rc = status_to_code(hc.status, hc.num_segments, L.max_segments);
+  if (rc != MH_OK) return rc;
+  if (hc.num_segments > cap) {
+    set_error("table has %lld rows, cap is %lld", hc.num_segments, static_cast<long long>(cap));
+    return MH_ERR_CAPACITY;
+  }
+  return MH_OK;
+}
+
+int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
+                        mh_stream_t stream) {
+  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !k_out ||
+      (model == MH_UECM && (!y || !s_out))) {
+    set_error("maxent_expected_fwd: bad model, n or pointer");
+    return MH_ERR_ARG;
+  }
+  MH_CUDA(launch_expected_fwd(model, x, y, n, k_out, s_out, reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
+int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                        const double* g_s, double* g_x, double* g_y, mh_stream_t stream) {
+  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !g_k || !g_x ||
+      (model == MH_UECM && (!y || !g_s || !g_y))) {
+    set_error("maxent_expected_bwd: bad model, n or pointer");
+    return MH_ERR_ARG;
+  }
+  MH_CUDA(launch_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Edge output: canonical order, COO and CSR layouts, UECM weights.
+//
+// After the walk every work item (sample, segment) has an edge count and a
+// contiguous run of accepted ranks j in the staging buffer.  An exclusive
+// scan of the counts in item order gives each item's place in the output, so
+// a sample's edges come out in (row rank, segment, candidate) order no matter
+// which lane walked which segment.  The emit pass maps ranks to original ids
+// (perm), draws the UECM weight of each edge (Eq. 4), and writes:
+//   COO  src[e] = perm[i], dst[e] = perm[j], w[e]
+//   CSR  csr_idx[off[s(n+1) + perm[i]] + position within row i] = perm[j]
+// CSR rows are original node ids; row u holds the edges whose higher-ranked
+// endpoint is u, and offsets are positions in the concatenated index array.
+#include "mh_internal.cuh"
+#include "scan.cuh"
+#include "walk_math.cuh"
+
+namespace mh {
+
+namespace {
+
+__global__ void sample_counts_kernel(const long long* __restrict__ item_off, const Ctrl* ctrl, int64_t max_segments,
+                                     int64_t chunk_first, int64_t chunk_samples, long long* counts) {
+  long long S = ctrl->num_segments;
+  if (S > max_segments) S = max_segments;
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < chunk_samples;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    counts[chunk_first + s] = item_off[(s + 1) * S] - item_off[s * S];
+}
+
+// csr_off[(chunk_first + s)(n+1) + u] = edges of row u in sample s (0 for u = n);
+// an in-place exclusive scan then turns counts into offsets.
+__global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, const Ctrl* ctrl,
+                                 int64_t chunk_first, int64_t chunk_samples, long long* csr_off) {
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;
+  const int64_t n1 = g.n + 1;
+  const int64_t total = chunk_samples * n1;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t s = t / n1, u = t - s * n1;
+    long long c = 0;
+    if (u < g.n) {
+      const int64_t i = g.rank[u];
+      c = item_off[s * S + g.rowoff[i + 1]] - item_off[s * S + g.rowoff[i]];
+    }
+    csr_off[chunk_first * n1 + t] = c;
+  }
+}
+
+struct EmitParams {
+  Net g;
+  ChunkArgs c;
+  Outputs o;
+  Ctrl* ctrl;
+};
+
+// Each block owns kEmitItems consecutive work items and writes their output
+// range with consecutive threads on consecutive edges.
+__global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
+  const Net& g = P.g;
+  Ctrl* ctrl = P.ctrl;
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;
+  const long long items = S * P.c.chunk_samples;
+  const long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems;
+  if (it0 >= items) return;
+  // Staging that did not fit was never written: emit nothing (the call
+  // reports MH_ERR_CAPACITY with exact counts).
+  if (ctrl->stage_used > static_cast<unsigned long long>(P.c.staging_cap)) return;
+  const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
+  __shared__ long long off[kEmitItems + 1];
+  for (long long t = threadIdx.x; t <= it1 - it0; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
+  __syncthreads();
+  const long long o0 = off[0], o1 = off[it1 - it0];
+  const long long n1 = g.n + 1;
+  bool overflow = false;
+  for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
+    int lo = 0, hi = static_cast<int>(it1 - it0) - 1;  // last local item with off <= pos
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= pos)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const long long item = it0 + lo;
+    const long long e = pos - off[lo];
+    const long long s_local = item / S;
+    const long long seg = item - s_local * S;
+    const int4 sg = g.seg[seg];
+    const int32_t i = sg.x;
+    const int32_t j = P.c.staging[P.c.item_base[item] + e];
+    if (j <= i || j >= g.n) {  // cannot happen for a walked segment; never index with it
+      atomicOr(&ctrl->status, kStInternal);
+      continue;
+    }
+    const int32_t u = g.perm[i], v = g.perm[j];
+    int32_t wt = 1;
+    if (g.model == MH_UECM) {
+      const double r = g.ys[i] * g.ys[j];
+      wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(sg.y), static_cast<uint32_t>(i),
+                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, r, overflow);
+    }
+    if (pos < P.o.capacity) {
+      if (P.o.src) {
+        P.o.src[pos] = u;
+        P.o.dst[pos] = v;
+        if (P.o.w) P.o.w[pos] = wt;
+      }
+      if (P.o.csr_idx) {
+        const long long s_all = P.c.chunk_first + s_local;
+        const long long row_first = s_local * S + g.rowoff[i];
+        const long long at = P.o.csr_off[s_all * n1 + u] + (P.c.item_off[item] - P.c.item_off[row_first]) + e;
+        if (at < P.o.capacity) {
+          P.o.csr_idx[at] = v;
+          if (P.o.csr_w) P.o.csr_w[at] = wt;
+        }
+      }
+    }
+  }
+  if (overflow) atomicOr(&ctrl->status, kStOverflow);
+}
+
+}  // namespace
+
+cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl* ctrl, cudaStream_t s) {
+  cudaError_t e;
+  // item offsets (continuing from the edges of earlier chunks)
+  e = device_scan<long long, SumOp<long long>>(c.item_cnt, c.item_off,
+                                               ScanLen{c.items_max, &ctrl->num_segments, c.chunk_samples}, true,
+                                               &ctrl->out_base, &ctrl->out_end, true,
+                                               reinterpret_cast<long long*>(c.scan_tmp), s);
+  if (e != cudaSuccess) return e;
+  sample_counts_kernel<<<grid_for(c.chunk_samples, 128), 128, 0, s>>>(c.item_off, ctrl, g.max_segments,
+                                                                      c.chunk_first, c.chunk_samples,
+                                                                      c.sample_counts);
+  note_launches(1);
+  if (o.csr_off) {
+    const int64_t len = c.chunk_samples * (g.n + 1);
+    csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
+        g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off);
+    note_launches(1);
+    long long* region = o.csr_off + c.chunk_first * (g.n + 1);
+    e = device_scan<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->out_base,
+                                                 nullptr, false, reinterpret_cast<long long*>(c.scan_tmp), s);
+    if (e != cudaSuccess) return e;
+  }
+  EmitParams P{g, c, o, ctrl};
+  emit_kernel<<<grid_for(c.items_max, kEmitItems), 256, 0, s>>>(P);
+  note_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the next chunk continues after this one
+  return cudaMemcpyAsync(&ctrl->out_base, &ctrl->out_end, sizeof(long long), cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace mh

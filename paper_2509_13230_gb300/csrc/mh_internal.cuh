@@ -1,0 +1,187 @@
+// Internal declarations of the GB300 maximum-entropy sampler library.
+//
+// Device-wide conventions
+//  * Node ranks follow the sort of Sec. 2.4 step (i) / Algorithm 1: rank 0 has
+//    the largest key (x for UBCM, a = x*y for UECM).
+//  * FP64 expressions that decide sampled bits are written in one fixed order;
+//    the library is compiled with --fmad=false so none of them is contracted
+//    into an FMA.  Explicit fma() calls are used only where a rounding error is
+//    being measured, never in a decision.
+//  * Device status bits are OR-ed into Ctrl::status and mapped to MH_ERR_* on
+//    the host after the final read-back; no kernel traps or asserts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/maxent_mh.h"
+
+namespace mh {
+
+// ---- status bits ----------------------------------------------------------
+constexpr unsigned kStDomain = 1u;    // bad x / y value
+constexpr unsigned kStSegments = 2u;  // segment table larger than its capacity
+constexpr unsigned kStCapacity = 4u;  // output or staging shorter than the sample
+constexpr unsigned kStOverflow = 8u;  // weight above INT32_MAX
+constexpr unsigned kStTimeout = 16u;  // bounded device wait gave up
+constexpr unsigned kStInternal = 32u; // an internal consistency check failed
+
+// ---- control block (first bytes of the workspace) ---------------------------
+struct Ctrl {
+  unsigned int status;
+  unsigned int pad0;
+  unsigned long long key_or;    // OR of all sort keys (constant-digit detection)
+  unsigned long long key_and;   // AND of all sort keys
+  long long num_segments;       // rows of the segment table (S)
+  unsigned long long ticket;    // walk work-queue ticket
+  unsigned long long stage_used;      // staging entries handed out
+  unsigned long long overflow_count;  // items re-walked by the overflow kernel
+  long long out_base;           // edges emitted by earlier sample chunks
+  long long out_end;            // edges emitted including the current chunk
+  unsigned long long stats[4];  // MH_STAT_* counters
+  unsigned long long pad1[4];
+};
+
+// ---- tuning constants --------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 8;
+constexpr int kSortTile = kSortThreads * kSortIPT;  // keys per sort tile
+constexpr int kScanThreads = 256;
+constexpr int kScanIPT = 8;
+constexpr int kScanTile = kScanThreads * kScanIPT;
+constexpr int kWalkWarps = 8;                    // warps per walk block
+constexpr int kSlot = 64;                        // edges a lane buffers in shared memory
+constexpr int kSlotStride = kSlot + 1;           // padded to spread banks
+constexpr int kWalkChunk = 64;                   // work items per warp ticket
+constexpr int kEmitItems = 128;                  // work items per emit block
+constexpr long long kItemChunk = 1ll << 22;      // work items per sample chunk
+constexpr int kDefaultSegTarget = 32;
+
+// ---- workspace layout --------------------------------------------------------
+struct Layout {
+  int64_t n = 0, tiles = 0, max_segments = 0, spc = 0, items_max = 0, capacity = 0;
+  int64_t scan_tmp_elems = 0;
+  size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
+         as = 0, ymax = 0, top1 = 0, top2 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
+         item_off = 0, ovf = 0, sample_counts = 0, staging = 0, scan_tmp = 0, total = 0;
+};
+
+Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity);
+
+struct Top2 {
+  double a, b;  // largest and second largest
+};
+
+// Device views of the workspace.
+struct Net {
+  int model;
+  uint32_t flags;
+  int64_t n;
+  const double* x;  // original order
+  const double* y;
+  int32_t* perm;    // rank -> id
+  int32_t* rank;    // id -> rank
+  double* xs;
+  double* ys;
+  double* as;
+  double* ymax;     // [n+1]
+  Top2* top;        // [n+1]
+  unsigned long long* Q;  // [n+1] proxy prefix sums
+  long long* rowoff;      // [n+1] first segment of each row; rowoff[n] = S
+  int4* seg;              // {row, k, a, b}
+  int64_t max_segments;
+  int seg_target;
+};
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// 53 bits -> (0, 1] (logarithm inputs) and [0, 1) (acceptance draws).
+__device__ __forceinline__ unsigned long long top53(uint32_t hi, uint32_t lo) {
+  return ((static_cast<unsigned long long>(hi) << 32) | lo) >> 11;
+}
+__device__ __forceinline__ double unit_open0(uint32_t hi, uint32_t lo) {
+  return static_cast<double>(top53(hi, lo) + 1ull) * 0x1p-53;
+}
+__device__ __forceinline__ double unit_open1(uint32_t hi, uint32_t lo) {
+  return static_cast<double>(top53(hi, lo)) * 0x1p-53;
+}
+
+// Fixed-point scale of the segment-cost prefix sums: n * min(vmax, 2^20) * 2^F < 2^62.
+__host__ __device__ inline int proxy_scale(double vmax, int64_t n) {
+  if (vmax > 0x1p20) vmax = 0x1p20;
+  unsigned long long bits;
+  memcpy(&bits, &vmax, sizeof(bits));
+  int E = static_cast<int>((bits >> 52) & 0x7FF) - 1022;
+  if (E < 1) E = 1;
+  int len = 0;
+  for (unsigned long long v = static_cast<unsigned long long>(n); v; v >>= 1) ++len;
+  int F = 62 - len - E;
+  return F < 0 ? 0 : F;
+}
+
+// ---- host helpers ------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void note_launches(int count);  // counts kernels launched by the current call
+inline unsigned grid_for(int64_t work, int per_block, unsigned cap = 1u << 30) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return static_cast<unsigned>(g);
+}
+int sm_count();
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, Ctrl* ctrl,
+                                 cudaStream_t s);
+cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+
+struct ChunkArgs {
+  int64_t chunk_first;  // index of the chunk's first sample within the call
+  int64_t chunk_samples;
+  uint32_t sample0;     // global sample id of the chunk's first sample
+  uint32_t key0, key1;
+  long long* item_cnt;
+  long long* item_base;
+  long long* item_off;
+  int32_t* ovf;
+  int32_t* staging;
+  long long* sample_counts;
+  void* scan_tmp;
+  int64_t staging_cap;
+  int64_t items_max;
+};
+struct Outputs {
+  int32_t* src;
+  int32_t* dst;
+  int32_t* w;
+  long long* csr_off;
+  int32_t* csr_idx;
+  int32_t* csr_w;
+  int64_t capacity;
+};
+cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_export_table(const Net& g, const Ctrl* ctrl, int32_t* row, int32_t* k, int64_t* a, int64_t* b,
+                                int64_t cap, cudaStream_t s);
+
+cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k, double* s,
+                                cudaStream_t st);
+cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* gk,
+                                const double* gs, double* gx, double* gy, cudaStream_t st);
+
+}  // namespace mh

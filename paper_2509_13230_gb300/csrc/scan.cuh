@@ -1,0 +1,191 @@
+// Device-wide scans: reduce -> scan of tile partials -> scan with carry-in.
+//
+// Three launches, no inter-block waiting.  The length may come from device
+// memory (len = min(host_len, *dev_len * mult)) so a scan can follow a kernel
+// that decides the size without a host round trip.  Operators are exact
+// (integer sums, max, top-2), so the result does not depend on the tiling.
+#pragma once
+
+#include "mh_internal.cuh"
+
+namespace mh {
+
+template <typename T>
+struct SumOp {
+  __device__ __forceinline__ T operator()(T a, T b) const { return a + b; }
+  __device__ __forceinline__ static T identity() { return T(0); }
+};
+struct MaxOp {
+  __device__ __forceinline__ double operator()(double a, double b) const { return a > b ? a : b; }
+  __device__ __forceinline__ static double identity() { return 0.0; }
+};
+struct Top2Op {
+  __device__ __forceinline__ Top2 operator()(Top2 u, Top2 v) const {
+    Top2 r;
+    r.a = u.a > v.a ? u.a : v.a;
+    const double lo = u.a > v.a ? v.a : u.a;
+    const double sb = u.b > v.b ? u.b : v.b;
+    r.b = lo > sb ? lo : sb;
+    return r;
+  }
+  __device__ __forceinline__ static Top2 identity() { return Top2{0.0, 0.0}; }
+};
+
+__device__ __forceinline__ unsigned shfl_up(unsigned v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ unsigned long long shfl_up(unsigned long long v, int d) {
+  return __shfl_up_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ long long shfl_up(long long v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ Top2 shfl_up(Top2 v, int d) {
+  return Top2{__shfl_up_sync(0xffffffffu, v.a, d), __shfl_up_sync(0xffffffffu, v.b, d)};
+}
+
+struct ScanLen {
+  int64_t host_len;               // upper bound, sizes the grid
+  const long long* dev_len;       // optional device length
+  int64_t mult;                   // dev length multiplier
+  __device__ __forceinline__ int64_t get() const {
+    if (!dev_len) return host_len;
+    const int64_t v = static_cast<int64_t>(*dev_len) * mult;
+    return v < host_len ? v : host_len;
+  }
+};
+
+// Element e of the logical sequence lives at index e (forward) or len-1-e (reverse).
+template <bool kReverse>
+__device__ __forceinline__ int64_t scan_index(int64_t e, int64_t len) {
+  return kReverse ? len - 1 - e : e;
+}
+
+// Inclusive scan of one block's values; returns the block aggregate.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_inclusive_scan(T& v, T* warp_sums) {
+  Op op;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = shfl_up(v, d);
+    if (lane >= d) v = op(o, v);
+  }
+  if (lane == 31) warp_sums[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    T w = lane < nw ? warp_sums[lane] : Op::identity();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T o = shfl_up(w, d);
+      if (lane >= d) w = op(o, w);
+    }
+    if (lane < nw) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) v = op(warp_sums[warp - 1], v);
+  const T agg = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return agg;
+}
+
+template <typename T, typename Op, bool kReverse>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T* __restrict__ in, ScanLen L,
+                                                                    T* __restrict__ partial) {
+  __shared__ T warp_sums[kScanThreads / 32];
+  const int64_t len = L.get();
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
+  if (base >= len) return;
+  Op op;
+  T acc = Op::identity();
+#pragma unroll
+  for (int k = 0; k < kScanIPT; ++k) {
+    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+    if (e < len) acc = op(acc, in[scan_index<kReverse>(e, len)]);
+  }
+  const T agg = block_inclusive_scan<T, Op>(acc, warp_sums);
+  if (threadIdx.x == 0) partial[blockIdx.x] = agg;
+}
+
+// Exclusive scan of the tile partials with an optional carry-in; writes the
+// grand total to *total (which may alias *base: it is read before written).
+template <typename T, typename Op>
+__global__ void __launch_bounds__(1024) scan_partials_kernel(T* __restrict__ partial, ScanLen L, const T* base,
+                                                              T* total) {
+  __shared__ T warp_sums[32];
+  __shared__ T last_of_warp[32];
+  const int64_t len = L.get();
+  const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Op op;
+  T carry = base ? *base : Op::identity();
+  __syncthreads();
+  for (int64_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
+    const int64_t t = t0 + threadIdx.x;
+    T inc = t < tiles ? partial[t] : Op::identity();
+    const T agg = block_inclusive_scan<T, Op>(inc, warp_sums);
+    T prev = shfl_up(inc, 1);
+    if (lane == 31) last_of_warp[warp] = inc;
+    __syncthreads();
+    if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Op::identity();
+    if (t < tiles) partial[t] = op(carry, prev);
+    carry = op(carry, agg);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[tiles] = carry;  // grand total, read by the final pass when len == 0
+    if (total) *total = carry;
+  }
+}
+
+template <typename T, typename Op, bool kReverse>
+__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T* out, ScanLen L,
+                                                                   const T* __restrict__ partial, bool exclusive,
+                                                                   bool write_total_at_len) {
+  // `in` and `out` may alias: each thread reads only the elements it writes.
+  __shared__ T warp_sums[kScanThreads / 32];
+  const int64_t len = L.get();
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
+  if (len == 0 && blockIdx.x == 0 && threadIdx.x == 0 && write_total_at_len) out[0] = partial[0];
+  if (base >= len) return;
+  Op op;
+  T vals[kScanIPT];
+  T acc = Op::identity();
+#pragma unroll
+  for (int k = 0; k < kScanIPT; ++k) {
+    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+    vals[k] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+    acc = op(acc, vals[k]);
+  }
+  T inc = acc;
+  block_inclusive_scan<T, Op>(inc, warp_sums);
+  // exclusive prefix of this thread = carry-in (+) inclusive of the previous thread
+  T prev = shfl_up(inc, 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ T last_of_warp[kScanThreads / 32];
+  if (lane == 31) last_of_warp[warp] = inc;
+  __syncthreads();
+  if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Op::identity();
+  T run = op(partial[blockIdx.x], prev);
+#pragma unroll
+  for (int k = 0; k < kScanIPT; ++k) {
+    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+    const T next = op(run, vals[k]);
+    if (e < len) out[scan_index<kReverse>(e, len)] = exclusive ? run : next;
+    if (write_total_at_len && e == len - 1) out[len] = next;
+    run = next;
+  }
+}
+
+// scan_tmp must hold ceil(host_len / kScanTile) + 2 elements of T.
+template <typename T, typename Op, bool kReverse = false>
+cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
+                        bool write_total_at_len, T* scan_tmp, cudaStream_t s) {
+  const unsigned tiles = grid_for(L.host_len, kScanTile);
+  scan_reduce_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, L, scan_tmp);
+  scan_partials_kernel<T, Op><<<1, 1024, 0, s>>>(scan_tmp, L, base, total);
+  scan_final_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, out, L, scan_tmp, exclusive,
+                                                                      write_total_at_len);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+}  // namespace mh

@@ -1,0 +1,221 @@
+// Node order (Sec. 2.4 step (i): ascending alpha; Algorithm 1: ascending
+// alpha + beta), i.e. descending x for UBCM and descending a = x*y for UECM.
+//
+// LSD radix sort of the FP64 key bits, 8 bits per pass, stable, so equal
+// keys keep ascending original id.  Keys are non-negative doubles, whose bit
+// patterns order like the values; the sort key is the complement, which turns
+// descending values into ascending integers.  Passes whose digit is the same
+// for every key (found from the OR and AND of all keys) copy instead of
+// ranking, so the buffer parity never depends on the data.
+#include "mh_internal.cuh"
+#include "scan.cuh"
+
+namespace mh {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long warp_or(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_and(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) v &= __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Checks the parameter domain and writes (key, id) pairs.
+__global__ void __launch_bounds__(256) validate_keys_kernel(int model, const double* __restrict__ x,
+                                                             const double* __restrict__ y, int64_t n,
+                                                             unsigned long long* __restrict__ keys,
+                                                             int32_t* __restrict__ vals, Ctrl* ctrl) {
+  unsigned long long kor = 0, kand = ~0ull;
+  bool bad = false;
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double xu = x[u];
+    bad |= !(xu >= 0.0 && xu <= 1e150);
+    double v = xu;
+    if (model == MH_UECM) {
+      const double yu = y[u];
+      bad |= !(yu >= 0.0 && yu < 1.0);
+      v = xu * yu;
+    }
+    v = (v > 0.0) ? v : 0.0;  // -0.0 sorts as +0.0; a bad input is reported through the status
+    const unsigned long long key = ~static_cast<unsigned long long>(__double_as_longlong(v));
+    keys[u] = key;
+    vals[u] = static_cast<int32_t>(u);
+    kor |= key;
+    kand &= key;
+  }
+  kor = warp_or(kor);
+  kand = warp_and(kand);
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&ctrl->key_or, kor);
+    atomicAnd(&ctrl->key_and, kand);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->status, kStDomain);
+}
+
+__device__ __forceinline__ bool digit_constant(const Ctrl* ctrl, int shift) {
+  return (((ctrl->key_or ^ ctrl->key_and) >> shift) & 0xFFull) == 0ull;
+}
+
+// hist[d * tiles + tile] = number of keys with digit d in the tile.
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys,
+                                                                  int64_t n, int shift, unsigned* __restrict__ hist,
+                                                                  int64_t tiles, const Ctrl* ctrl) {
+  if (digit_constant(ctrl, shift)) return;
+  __shared__ unsigned counts[256];
+  counts[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+#pragma unroll
+  for (int r = 0; r < kSortIPT; ++r) {
+    const int64_t e = base + r * kSortThreads + threadIdx.x;
+    if (e < n) atomicAdd(&counts[(keys[e] >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  hist[static_cast<int64_t>(threadIdx.x) * tiles + blockIdx.x] = counts[threadIdx.x];
+}
+
+// Stable scatter: the tile is processed in rounds of 256 keys in position
+// order; a key's destination is its digit's global base + the count of equal
+// digits in earlier rounds + in earlier warps of this round + earlier lanes.
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+    int32_t* __restrict__ vout, int64_t n, int shift, const unsigned* __restrict__ hist, int64_t tiles,
+    const Ctrl* ctrl) {
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+  if (digit_constant(ctrl, shift)) {
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const int64_t e = base + r * kSortThreads + threadIdx.x;
+      if (e < n) {
+        kout[e] = kin[e];
+        vout[e] = vin[e];
+      }
+    }
+    return;
+  }
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ unsigned wcount[kWarps][256];
+  __shared__ unsigned run[256];
+  __shared__ unsigned gbase[256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  gbase[t] = hist[static_cast<int64_t>(t) * tiles + blockIdx.x];
+  run[t] = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) wcount[w][t] = 0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortIPT; ++r) {
+    const int64_t e = base + r * kSortThreads + t;
+    const bool valid = e < n;
+    const unsigned long long k = valid ? kin[e] : 0ull;
+    const int32_t v = valid ? vin[e] : 0;
+    const unsigned d = valid ? static_cast<unsigned>((k >> shift) & 0xFF) : 0x100u + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank_in_warp = __popc(peers & lt);
+    if (valid && rank_in_warp == 0) wcount[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      unsigned acc = run[t];
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const unsigned c = wcount[w][t];
+        wcount[w][t] = acc;
+        acc += c;
+      }
+      run[t] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const unsigned pos = gbase[d] + wcount[warp][d] + rank_in_warp;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcount[w][t] = 0;
+    __syncthreads();
+  }
+}
+
+// Rank-order copies of the parameters, the inverse permutation and the
+// fixed-point segment costs floor(min(v, 2^20) * 2^F) (scanned afterwards).
+__global__ void __launch_bounds__(256) gather_kernel(int model, const double* __restrict__ x,
+                                                      const double* __restrict__ y, int64_t n,
+                                                      const int32_t* __restrict__ sorted_ids, int32_t* perm,
+                                                      int32_t* rank, double* xs, double* ys, double* as,
+                                                      unsigned long long* qv) {
+  const int32_t top = sorted_ids[0];
+  const double vmax = (model == MH_UBCM) ? x[top] : x[top] * y[top];
+  const int F = proxy_scale(vmax, n);
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t u = sorted_ids[r];
+    perm[r] = u;
+    rank[u] = static_cast<int32_t>(r);
+    const double xu = x[u];
+    xs[r] = xu;
+    double v = xu;
+    if (model == MH_UECM) {
+      const double yu = y[u];
+      ys[r] = yu;
+      v = xu * yu;
+      as[r] = v;
+    }
+    const double vc = v > 0x1p20 ? 0x1p20 : v;
+    qv[r] = static_cast<unsigned long long>(ldexp(vc, F));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, Ctrl* ctrl,
+                                 cudaStream_t s) {
+  const unsigned grid = grid_for(g.n, 256, static_cast<unsigned>(sm_count()) * 8u);
+  validate_keys_kernel<<<grid, 256, 0, s>>>(g.model, g.x, g.y, g.n, keys, vals, ctrl);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  auto* k0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
+  auto* k1 = reinterpret_cast<unsigned long long*>(ws + L.keys1);
+  auto* v0 = reinterpret_cast<int32_t*>(ws + L.vals0);
+  auto* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
+  auto* hist = reinterpret_cast<unsigned*>(ws + L.hist);
+  auto* tmp = reinterpret_cast<unsigned*>(ws + L.scan_tmp);
+  const unsigned tiles = static_cast<unsigned>(L.tiles);
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = pass * 8;
+    radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(k0, g.n, shift, hist, L.tiles, ctrl);
+    cudaError_t e = device_scan<unsigned, SumOp<unsigned>>(hist, hist, ScanLen{256 * L.tiles, nullptr, 1}, true,
+                                                          nullptr, nullptr, false, tmp, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, shift, hist, L.tiles, ctrl);
+    note_launches(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    unsigned long long* kt = k0;
+    k0 = k1;
+    k1 = kt;
+    int32_t* vt = v0;
+    v0 = v1;
+    v1 = vt;
+  }
+  return cudaSuccess;  // eight passes: the result is back in keys0 / vals0
+}
+
+cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s) {
+  (void)ctrl;
+  const unsigned grid = grid_for(g.n, 256, static_cast<unsigned>(sm_count()) * 8u);
+  gather_kernel<<<grid, 256, 0, s>>>(g.model, g.x, g.y, g.n, sorted_vals, g.perm, g.rank, g.xs, g.ys, g.as, g.Q);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mh

@@ -1,0 +1,222 @@
+"""Torch-facing helpers around the C ABI: buffers, capacity growth, results.
+
+Every sampled bit and every expected-degree term is computed by the CUDA
+library; this module allocates device memory with torch, passes pointers and
+the current stream, and grows buffers when the library reports that an
+output or the segment table was too small (the retried call reproduces the
+same sample, since sampling is a pure function of its arguments).
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as nat
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream: torch.cuda.Stream | None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_vec(name: str, t: torch.Tensor, n: int | None = None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 1:
+        raise TypeError(f"{name} must be a 1-D float64 CUDA tensor")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} must have {n} entries")
+    return t.contiguous()
+
+
+@dataclass
+class SampleResult:
+    """Edges of a sampling call; tensors are views trimmed to the edge total."""
+    counts: np.ndarray          # int64[num_samples]
+    stats: np.ndarray           # uint64[4]: proposals, edges, segments, fallbacks
+    src: torch.Tensor | None = None
+    dst: torch.Tensor | None = None
+    w: torch.Tensor | None = None
+    csr_offsets: torch.Tensor | None = None   # int64[num_samples * (n + 1)]
+    csr_indices: torch.Tensor | None = None
+    csr_weights: torch.Tensor | None = None
+
+    @property
+    def total(self) -> int:
+        return int(self.counts.sum())
+
+    def coo(self, s: int):
+        """(src, dst, w) of sample s."""
+        a = int(self.counts[:s].sum())
+        b = a + int(self.counts[s])
+        return self.src[a:b], self.dst[a:b], None if self.w is None else self.w[a:b]
+
+
+class Sampler:
+    """Reusable buffers for repeated sampling calls on one network.
+
+    layout: "coo", "csr", "both" or "none" (counts only).
+    bound: "suffix" (c = y_i max_{j >= head} y_j) or "paper" (two largest y
+    among unprocessed nodes, Sec. 2.5).  init: "head" (q = p at the segment
+    head) or "prev" (q = p at the rank before it; p_ii for a row's first
+    segment, Sec. 2.4 step (ii)).
+    """
+
+    def __init__(self, model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, num_samples: int = 1,
+                 seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
+                 layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
+                 capacity: int | None = None, max_segments: int = 0):
+        self.model = int(model)
+        self.x = _check_vec("x", x)
+        self.n = int(self.x.shape[0])
+        self.y = _check_vec("y", y, self.n) if self.model == nat.MH_UECM else None
+        flags = {"coo": nat.MH_OUT_COO, "csr": nat.MH_OUT_CSR, "both": nat.MH_OUT_COO | nat.MH_OUT_CSR,
+                 "none": 0}[layout]
+        if bound == "paper":
+            flags |= nat.MH_BOUND_PAPER
+        if init == "prev":
+            flags |= nat.MH_INIT_PREV
+        if fp64_only:
+            flags |= nat.MH_FP64_ONLY
+        self.flags = flags
+        self.num_samples = int(num_samples)
+        self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
+        self.seg_target = int(seg_target)
+        self.max_segments = int(max_segments)
+        self.device = self.x.device
+        if capacity is None:
+            capacity = max(1024, 16 * self.n * self.num_samples)
+        self._alloc(int(capacity))
+
+    def params(self, sample_begin: int | None = None) -> nat.MhParams:
+        return nat.make_params(seed=self.seed, network_id=self.network_id,
+                               sample_begin=self.sample_begin if sample_begin is None else sample_begin,
+                               num_samples=self.num_samples, seg_target=self.seg_target, flags=self.flags,
+                               max_segments=self.max_segments)
+
+    def _alloc(self, capacity: int):
+        self.capacity = capacity
+        self.ws_bytes = nat.mh_workspace_size(self.model, self.n, self.params(), capacity)
+        dev = self.device
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        coo = bool(self.flags & nat.MH_OUT_COO)
+        csr = bool(self.flags & nat.MH_OUT_CSR)
+        weighted = self.model == nat.MH_UECM
+        cap = max(capacity, 1)
+        self.src = torch.empty(cap, dtype=torch.int32, device=dev) if coo else None
+        self.dst = torch.empty(cap, dtype=torch.int32, device=dev) if coo else None
+        self.w = torch.empty(cap, dtype=torch.int32, device=dev) if coo and weighted else None
+        self.csr_off = torch.empty(self.num_samples * (self.n + 1), dtype=torch.int64, device=dev) if csr else None
+        self.csr_idx = torch.empty(cap, dtype=torch.int32, device=dev) if csr else None
+        self.csr_w = torch.empty(cap, dtype=torch.int32, device=dev) if csr and weighted else None
+        self.h_counts = np.zeros(self.num_samples, dtype=np.int64)
+        self.h_stats = np.zeros(4, dtype=np.uint64)
+
+    def call(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> int:
+        """One C-ABI call with the current buffers; returns its code."""
+        p = self.params(sample_begin)
+        st = _stream_handle(stream)
+        counts = self.h_counts.ctypes.data_as(ctypes.c_void_p)
+        stats = self.h_stats.ctypes.data_as(ctypes.c_void_p)
+        if self.model == nat.MH_UBCM:
+            return nat.mh_sample_ubcm(_ptr(self.x), self.n, p, _ptr(self.workspace), self.ws_bytes, _ptr(self.src),
+                                      _ptr(self.dst), _ptr(self.csr_off), _ptr(self.csr_idx), self.capacity, counts,
+                                      stats, st)
+        return nat.mh_sample_weighted(_ptr(self.x), _ptr(self.y), self.n, p, _ptr(self.workspace), self.ws_bytes,
+                                      _ptr(self.src), _ptr(self.dst), _ptr(self.w), _ptr(self.csr_off),
+                                      _ptr(self.csr_idx), _ptr(self.csr_w), self.capacity, counts, stats, st)
+
+    def run(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> SampleResult:
+        for _ in range(8):
+            rc = self.call(sample_begin, stream)
+            if rc == nat.MH_ERR_CAPACITY:
+                self._alloc(int(self.h_counts.sum() * 1.05) + 1024)
+                continue
+            if rc == nat.MH_ERR_WORKSPACE:
+                m = re.search(r"needs (\d+) rows", nat.last_error_detail())
+                if m:
+                    self.max_segments = int(int(m.group(1)) * 1.25) + 1024
+                    self._alloc(self.capacity)
+                    continue
+            nat.check(rc, "mh_sample_ubcm" if self.model == nat.MH_UBCM else "mh_sample_weighted")
+            return self.result()
+        raise RuntimeError("sampling did not converge on buffer sizes")
+
+    def result(self) -> SampleResult:
+        tot = int(self.h_counts.sum())
+        cut = (lambda t: None if t is None else t[:tot])
+        return SampleResult(self.h_counts.copy(), self.h_stats.copy(), cut(self.src), cut(self.dst), cut(self.w),
+                            self.csr_off, cut(self.csr_idx), cut(self.csr_w))
+
+
+def sample_ubcm(x: torch.Tensor, **kw) -> SampleResult:
+    """UBCM samples (Sec. 2.4); keyword arguments as in Sampler."""
+    return Sampler(nat.MH_UBCM, x, None, **kw).run()
+
+
+def sample_weighted(x: torch.Tensor, y: torch.Tensor, **kw) -> SampleResult:
+    """UECM samples with integer weights (Sec. 2.5, Algorithm 1)."""
+    return Sampler(nat.MH_UECM, x, y, **kw).run()
+
+
+def segment_table(model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, seg_target: int = 0,
+                  bound: str = "suffix", max_segments: int = 0) -> dict:
+    """The node order and row-segment table a sampling call walks (numpy arrays)."""
+    x = _check_vec("x", x)
+    n = int(x.shape[0])
+    y = _check_vec("y", y, n) if model == nat.MH_UECM else None
+    flags = nat.MH_BOUND_PAPER if bound == "paper" else 0
+    for _ in range(4):
+        p = nat.make_params(seg_target=seg_target, flags=flags, max_segments=max_segments)
+        ws_bytes = nat.mh_workspace_size(model, n, p, 0)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=x.device)
+        cap = max_segments if max_segments > 0 else 4 * n + 1024
+        row = torch.empty(cap, dtype=torch.int32, device=x.device)
+        k = torch.empty(cap, dtype=torch.int32, device=x.device)
+        a = torch.empty(cap, dtype=torch.int64, device=x.device)
+        b = torch.empty(cap, dtype=torch.int64, device=x.device)
+        perm = torch.empty(n, dtype=torch.int32, device=x.device)
+        S = ctypes.c_int64(0)
+        rc = nat.mh_segment_table(model, _ptr(x), _ptr(y), n, p, _ptr(ws), ws_bytes, _ptr(row), _ptr(k), _ptr(a),
+                                  _ptr(b), _ptr(perm), cap, ctypes.byref(S), _stream_handle(None))
+        if rc in (nat.MH_ERR_WORKSPACE, nat.MH_ERR_CAPACITY) and S.value > cap:
+            max_segments = int(S.value)
+            continue
+        nat.check(rc, "mh_segment_table")
+        s = S.value
+        return dict(row=row[:s].cpu().numpy(), k=k[:s].cpu().numpy(), a=a[:s].cpu().numpy(),
+                    b=b[:s].cpu().numpy(), perm=perm.cpu().numpy())
+    raise RuntimeError("segment table did not fit")
+
+
+def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """(<k>, <s>) as FP64 CUDA tensors (<s> is None for UBCM)."""
+    x = _check_vec("x", x)
+    n = int(x.shape[0])
+    y = _check_vec("y", y, n) if model == nat.MH_UECM else None
+    k = torch.empty_like(x)
+    s = torch.empty_like(x) if model == nat.MH_UECM else None
+    nat.check(nat.maxent_expected_fwd(model, _ptr(x), _ptr(y), n, _ptr(k), _ptr(s), _stream_handle(stream)),
+              "maxent_expected_fwd")
+    return k, s
+
+
+def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch.Tensor,
+                 g_s: torch.Tensor | None = None, stream=None):
+    """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors)."""
+    x = _check_vec("x", x)
+    n = int(x.shape[0])
+    y = _check_vec("y", y, n) if model == nat.MH_UECM else None
+    g_k = _check_vec("g_k", g_k, n)
+    g_s = _check_vec("g_s", g_s, n) if model == nat.MH_UECM else None
+    gx = torch.empty_like(x)
+    gy = torch.empty_like(x) if model == nat.MH_UECM else None
+    nat.check(nat.maxent_expected_bwd(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy),
+                                      _stream_handle(stream)), "maxent_expected_bwd")
+    return gx, gy

@@ -1,0 +1,66 @@
+"""The C-ABI library loads, exports what include/maxent_mh.h declares, and
+rejects bad arguments before touching a GPU (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_13230_gb300 import _native as nat
+from paper_2509_13230_gb300 import build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "maxent_mh.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nat.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    assert sorted(nat.EXPORTED) == names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_error_strings(lib):
+    for code in range(0, -8, -1):
+        assert nat.error_string(code).startswith("MH_")
+
+
+def test_workspace_size_and_argument_checks(lib):
+    p = nat.make_params(num_samples=10)
+    small = nat.mh_workspace_size(nat.MH_UECM, 1000, p, 10_000)
+    big = nat.mh_workspace_size(nat.MH_UECM, 1000, p, 1_000_000)
+    assert big - small >= 4 * 990_000 - 512  # int32 staging per edge of capacity
+    for bad in [dict(num_samples=0), dict(seg_target=1), dict(flags=0x8000)]:
+        q = nat.make_params(**bad)
+        with pytest.raises(nat.MhError) as e:
+            nat.mh_workspace_size(nat.MH_UBCM, 100, q, 10)
+        assert e.value.code == nat.MH_ERR_ARG
+    with pytest.raises(nat.MhError):
+        nat.mh_workspace_size(nat.MH_UBCM, 0, p, 10)
+    with pytest.raises(nat.MhError):
+        nat.mh_workspace_size(7, 10, p, 10)
+
+
+def test_sampling_rejects_null_inputs_without_a_gpu(lib):
+    p = nat.make_params()
+    counts = (ctypes.c_int64 * 1)()
+    rc = nat.mh_sample_ubcm(None, 10, p, None, 0, None, None, None, None, 0, counts, None, None)
+    assert rc == nat.MH_ERR_ARG
+    rc = nat.mh_sample_weighted(None, None, 10, p, None, 0, None, None, None, None, None, None, 0, counts, None, None)
+    assert rc == nat.MH_ERR_ARG
+    assert nat.maxent_expected_fwd(0, None, None, 5, None, None, None) == nat.MH_ERR_ARG
+    assert nat.maxent_expected_bwd(1, None, None, 5, None, None, None, None, None) == nat.MH_ERR_ARG
+    info = nat.mh_last_call_info()
+    assert info.kernel_launches == 0

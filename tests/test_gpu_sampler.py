@@ -1,0 +1,245 @@
+"""CUDA sampler and expected-degree kernels against the CPU oracle (GPU).
+
+Edge lists, weights, per-sample counts and the proposal/edge/segment
+counters must equal the serial oracle bit for bit.  The only allowed
+difference is a draw that the oracle flags as lying within 8 ulp of an
+integer boundary of ln U / ln v (the device and host FP64 logarithms may
+round differently there); the oracle counts those draws in stats[3].
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_13230_gb300 import _native as nat
+from paper_2509_13230_gb300 import workloads
+from paper_2509_13230_gb300.sampler import Sampler, expected_bwd, expected_fwd, segment_table
+
+pytestmark = pytest.mark.gpu
+
+UBCM, UECM = nat.MH_UBCM, nat.MH_UECM
+FLAG_NAMES = {0: {}, oracle.BOUND_PAPER: dict(bound="paper"), oracle.INIT_PREV: dict(init="prev")}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu_run(model, x, y=None, **kw):
+    s = Sampler(model, dev(x), None if y is None else dev(y), **kw)
+    return s.run(), s
+
+
+def assert_matches_oracle(res, model, x, y=None, *, num_samples=1, seg_target=32, flags=0, seed=0, sample_begin=0,
+                          network_id=0):
+    src, dst, w, counts, stats = oracle.mh_sample(model, x, y, seed=seed, network_id=network_id,
+                                                  sample_begin=sample_begin, num_samples=num_samples,
+                                                  seg_target=seg_target, flags=flags)
+    same = (np.array_equal(res.counts, counts) and np.array_equal(res.src.cpu().numpy(), src)
+            and np.array_equal(res.dst.cpu().numpy(), dst)
+            and (w is None or np.array_equal(res.w.cpu().numpy(), w)))
+    if not same:
+        # only a draw on an integer boundary may decide differently
+        assert stats[3] > 0, "edge lists differ and the oracle saw no boundary draw"
+        diff = np.flatnonzero(np.asarray(res.counts) != counts)
+        assert len(diff) <= int(stats[3])
+        return stats
+    assert int(res.stats[nat.MH_STAT_PROPOSALS]) == int(stats[0])
+    assert int(res.stats[nat.MH_STAT_EDGES]) == int(stats[1])
+    assert int(res.stats[nat.MH_STAT_SEGMENTS]) == int(stats[2])
+    return stats
+
+
+def heavy_tailed(n, seed, hubs=3, uecm=False):
+    rng = np.random.default_rng(seed)
+    x = np.exp(rng.normal(-2.5, 1.6, n))
+    x[rng.choice(n, hubs, replace=False)] = rng.uniform(5, 40, hubs)
+    y = rng.uniform(0.2, 0.95, n) if uecm else None
+    return x, y
+
+
+# --------------------------------------------------------------------------
+# Segment table (sort, bound prep, partition)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [UBCM, UECM])
+@pytest.mark.parametrize("T", [2, 9, 32, 1 << 30])
+@pytest.mark.parametrize("flags", [0, oracle.BOUND_PAPER])
+def test_segment_table_matches_oracle(model, T, flags):
+    x, y = heavy_tailed(5003, seed=T + flags, uecm=model == UECM)
+    x[100:140] = x[7]  # ties across sort tiles
+    ref = oracle.partition(model, x, y, seg_target=T, flags=flags)
+    got = segment_table(model, dev(x), None if y is None else dev(y), seg_target=T,
+                        bound="paper" if flags else "suffix")
+    for key in ("perm", "row", "k", "a", "b"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads
+# --------------------------------------------------------------------------
+def test_ubcm_n1k_x100_bit_exact():
+    net = workloads.ubcm_n1k()
+    res, _ = gpu_run(UBCM, net.x, num_samples=100)
+    assert_matches_oracle(res, UBCM, net.x, num_samples=100)
+
+
+def test_uecm_n20k_x10_bit_exact():
+    net = workloads.uecm_n20k()
+    res, _ = gpu_run(UECM, net.x, net.y, num_samples=10)
+    assert_matches_oracle(res, UECM, net.x, net.y, num_samples=10)
+
+
+def test_ubcm_pareto_n1m_csr_bit_exact():
+    net = workloads.ubcm_pareto_n1m()
+    res, _ = gpu_run(UBCM, net.x, num_samples=1, layout="both")
+    src, dst, _, counts, _ = oracle.mh_sample(UBCM, net.x, num_samples=1)
+    assert np.array_equal(res.counts, counts)
+    assert np.array_equal(res.src.cpu().numpy(), src) and np.array_equal(res.dst.cpu().numpy(), dst)
+    # CSR: row u holds the edges whose higher-ranked endpoint is u, in walk order
+    n = net.n
+    order = np.argsort(src, kind="stable")
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(np.bincount(src, minlength=n))
+    assert np.array_equal(res.csr_offsets.cpu().numpy(), off)
+    assert np.array_equal(res.csr_indices.cpu().numpy(), dst[order])
+
+
+# --------------------------------------------------------------------------
+# Variants: segment target, bound and initial-q readings, FP64-only path
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [UBCM, UECM])
+@pytest.mark.parametrize("T", [2, 7, 1 << 30])
+@pytest.mark.parametrize("flags", [0, oracle.BOUND_PAPER, oracle.INIT_PREV])
+def test_variants_bit_exact(model, T, flags):
+    if model == UBCM and flags == oracle.BOUND_PAPER:
+        pytest.skip("the bound reading only applies to the UECM")
+    x, y = heavy_tailed(2600, seed=11 + T, uecm=model == UECM)
+    res, _ = gpu_run(model, x, y, num_samples=3, seg_target=T, seed=0x1234567890ABCDEF, network_id=5,
+                     sample_begin=77, **FLAG_NAMES[flags])
+    assert_matches_oracle(res, model, x, y, num_samples=3, seg_target=T, flags=flags, seed=0x1234567890ABCDEF,
+                          network_id=5, sample_begin=77)
+
+
+@pytest.mark.parametrize("model", [UBCM, UECM])
+def test_fp64_only_path_bit_exact(model):
+    x, y = heavy_tailed(3000, seed=21, uecm=model == UECM)
+    res, _ = gpu_run(model, x, y, num_samples=4, fp64_only=True)
+    assert_matches_oracle(res, model, x, y, num_samples=4)
+
+
+# --------------------------------------------------------------------------
+# Degenerate and edge cases
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [UBCM, UECM])
+@pytest.mark.parametrize("case", ["n1", "n2", "zeros", "ties", "huge", "y_zero"])
+def test_degenerate_inputs(model, case):
+    rng = np.random.default_rng(3)
+    y = None
+    if case == "n1":
+        x = np.array([0.7])
+    elif case == "n2":
+        x = np.array([0.3, 2.0])
+    elif case == "zeros":
+        x = np.r_[np.zeros(50), np.exp(rng.normal(-1, 1, 30))]
+    elif case == "ties":
+        x = np.full(300, 0.2)
+    elif case == "huge":
+        x = np.r_[np.full(3, 1e9), np.exp(rng.normal(-2, 1, 200))]  # x_i x_j > 2^53: p rounds to 1
+    else:
+        x = np.exp(rng.normal(-1, 1, 200))
+    if model == UECM:
+        y = rng.uniform(0.0, 0.9, len(x))
+        if case == "y_zero":
+            y[::3] = 0.0
+    res, _ = gpu_run(model, x, y, num_samples=5, seg_target=3)
+    assert_matches_oracle(res, model, x, y, num_samples=5, seg_target=3)
+
+
+def test_many_chunks_and_overflow_rewalk():
+    # a hub row with far more edges than a lane's shared-memory slot (64),
+    # and a segment-table capacity that splits the samples into several chunks
+    rng = np.random.default_rng(4)
+    x = np.r_[np.full(2, 30.0), np.exp(rng.normal(-0.5, 0.5, 1500))]
+    res, s = gpu_run(UBCM, x, num_samples=7, seg_target=1 << 30, max_segments=1 << 21)
+    assert nat.mh_last_call_info().sample_chunks == 4
+    assert_matches_oracle(res, UBCM, x, num_samples=7, seg_target=1 << 30)
+    assert int(res.counts.max()) > 64
+
+
+def test_batch_equals_single_samples():
+    x, y = heavy_tailed(4000, seed=5, uecm=True)
+    batch, _ = gpu_run(UECM, x, y, num_samples=4, sample_begin=10)
+    for s in range(4):
+        one, _ = gpu_run(UECM, x, y, num_samples=1, sample_begin=10 + s)
+        bs, bd, bw = batch.coo(s)
+        assert torch.equal(bs, one.src) and torch.equal(bd, one.dst) and torch.equal(bw, one.w)
+
+
+def test_capacity_retry_reproduces_sample():
+    x, _ = heavy_tailed(3000, seed=6)
+    s = Sampler(UBCM, dev(x), num_samples=2, capacity=16)
+    assert s.call() == nat.MH_ERR_CAPACITY
+    need = int(s.h_counts.sum())
+    assert need > 16
+    res = s.run()
+    assert res.total == need
+    assert_matches_oracle(res, UBCM, x, num_samples=2)
+
+
+@pytest.mark.parametrize("bad", ["neg_x", "nan_x", "y_one"])
+def test_domain_errors(bad):
+    x = np.full(100, 0.5)
+    y = np.full(100, 0.5)
+    if bad == "neg_x":
+        x[3] = -1.0
+    elif bad == "nan_x":
+        x[3] = np.nan
+    else:
+        y[3] = 1.0
+    with pytest.raises(nat.MhError) as e:
+        gpu_run(UECM, x, y)
+    assert e.value.code == nat.MH_ERR_DOMAIN
+
+
+def test_call_info_counts_launches():
+    x, _ = heavy_tailed(2000, seed=7)
+    s = Sampler(UBCM, dev(x), num_samples=2)
+    s.flags |= nat.MH_TIMING
+    s.run()
+    info = nat.mh_last_call_info()
+    assert info.walk_launches == 1 and info.sample_chunks == 1
+    assert info.kernel_launches > 40
+    assert info.walk_ms > 0 and info.total_ms >= info.walk_ms
+
+
+# --------------------------------------------------------------------------
+# Expected degrees / strengths and gradients
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [UBCM, UECM])
+def test_expected_fwd_bwd_match_oracle(model):
+    x, y = heavy_tailed(1537, seed=8, uecm=model == UECM)
+    rng = np.random.default_rng(9)
+    gk = rng.normal(size=len(x))
+    gs = rng.normal(size=len(x)) if model == UECM else None
+    k, s = expected_fwd(model, dev(x), None if y is None else dev(y))
+    rk, rs = oracle.expected_fwd(model, x, y)
+    np.testing.assert_allclose(k.cpu().numpy(), rk, rtol=1e-10)
+    if model == UECM:
+        np.testing.assert_allclose(s.cpu().numpy(), rs, rtol=1e-10)
+    gx, gy = expected_bwd(model, dev(x), None if y is None else dev(y), dev(gk), None if gs is None else dev(gs))
+    rgx, rgy = oracle.expected_bwd(model, x, y, gk, gs)
+    np.testing.assert_allclose(gx.cpu().numpy(), rgx, rtol=1e-10, atol=1e-12 * np.abs(rgx).max())
+    if model == UECM:
+        np.testing.assert_allclose(gy.cpu().numpy(), rgy, rtol=1e-10, atol=1e-12 * np.abs(rgy).max())
+
+
+def test_expected_fwd_full_size_sampled_rows():
+    rng = np.random.default_rng(10)
+    n = 200_000
+    x = np.exp(rng.normal(-5.5, 1.3, n))
+    y = rng.uniform(0.3, 0.9, n)
+    k, s = expected_fwd(UECM, dev(x), dev(y))
+    rows = rng.choice(n, 12, replace=False)
+    rk, rs = oracle.expected_fwd(UECM, x, y, rows=rows)
+    np.testing.assert_allclose(k.cpu().numpy()[rows], rk, rtol=1e-10)
+    np.testing.assert_allclose(s.cpu().numpy()[rows], rs, rtol=1e-10)
