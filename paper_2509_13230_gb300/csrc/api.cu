@@ -145,10 +145,14 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.item_cnt = take(8 * static_cast<size_t>(L.items_max));
   L.item_base = take(8 * static_cast<size_t>(L.items_max));
   L.item_off = take(8 * (static_cast<size_t>(L.items_max) + 1));
-  L.ovf = take(4 * static_cast<size_t>(L.items_max));
   L.sample_counts = take(8 * static_cast<size_t>(p.num_samples));
   L.staging = take(4 * static_cast<size_t>(capacity));
   L.scan_tmp = take(sizeof(Top2) * static_cast<size_t>(L.scan_tmp_elems));
+  L.xdf = take(8 * static_cast<size_t>(n));
+  L.adf = take(8 * static_cast<size_t>(n));
+  L.ydf = take(8 * static_cast<size_t>(n));
+  L.lny = take(8 * static_cast<size_t>(n));
+  L.lntab = take(16 * 512);
   L.total = off;
   return L;
 }
@@ -171,6 +175,11 @@ static Net make_net(int model, const mh_params& p, const double* x, const double
   g.Q = reinterpret_cast<unsigned long long*>(ws + L.Q);
   g.rowoff = reinterpret_cast<long long*>(ws + L.rowoff);
   g.seg = reinterpret_cast<int4*>(ws + L.seg);
+  g.xdf = reinterpret_cast<float2*>(ws + L.xdf);
+  g.adf = (model == MH_UECM) ? reinterpret_cast<float2*>(ws + L.adf) : g.xdf;
+  g.ydf = reinterpret_cast<float2*>(ws + L.ydf);
+  g.lny = reinterpret_cast<float2*>(ws + L.lny);
+  g.lntab = reinterpret_cast<LnEntry*>(ws + L.lntab);
   g.max_segments = L.max_segments;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
   return g;
@@ -312,7 +321,6 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   c.item_cnt = reinterpret_cast<long long*>(ws + L.item_cnt);
   c.item_base = reinterpret_cast<long long*>(ws + L.item_base);
   c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
-  c.ovf = reinterpret_cast<int32_t*>(ws + L.ovf);
   c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
   c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
   c.scan_tmp = ws + L.scan_tmp;

@@ -59,6 +59,13 @@ struct EmitParams {
 __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   const Net& g = P.g;
   Ctrl* ctrl = P.ctrl;
+  __shared__ LnEntry tab[kLnTable];
+  if (g.model == MH_UECM) {
+    ln_table_to_shared(tab, g.lntab);
+    __syncthreads();
+  }
+  const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
+  unsigned long long fallbacks = 0;
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   const long long items = S * P.c.chunk_samples;
@@ -97,9 +104,10 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     const int32_t u = g.perm[i], v = g.perm[j];
     int32_t wt = 1;
     if (g.model == MH_UECM) {
-      const double r = g.ys[i] * g.ys[j];
+      const float2 li = g.lny[i], lj = g.lny[j];
       wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(sg.y), static_cast<uint32_t>(i),
-                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, r, overflow);
+                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, g.ys[i], g.ys[j],
+                       df2{li.x, li.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
     }
     if (pos < P.o.capacity) {
       if (P.o.src) {
@@ -119,6 +127,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     }
   }
   if (overflow) atomicOr(&ctrl->status, kStOverflow);
+  (void)fallbacks;
 }
 
 }  // namespace

@@ -63,7 +63,8 @@ struct Layout {
   int64_t scan_tmp_elems = 0;
   size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
          as = 0, ymax = 0, top1 = 0, top2 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
-         item_off = 0, ovf = 0, sample_counts = 0, staging = 0, scan_tmp = 0, total = 0;
+         item_off = 0, sample_counts = 0, staging = 0, scan_tmp = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
+         lntab = 0, total = 0;
 };
 
 Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity);
@@ -71,6 +72,7 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity);
 struct Top2 {
   double a, b;  // largest and second largest
 };
+struct LnEntry;  // logarithm table entry (walk_math.cuh)
 
 // Device views of the workspace.
 struct Net {
@@ -89,6 +91,11 @@ struct Net {
   unsigned long long* Q;  // [n+1] proxy prefix sums
   long long* rowoff;      // [n+1] first segment of each row; rowoff[n] = S
   int4* seg;              // {row, k, a, b}
+  float2* xdf;            // x_s as double-float (hi, lo)
+  float2* adf;            // a_s = x_s y_s as double-float (UECM)
+  float2* ydf;            // y_s as double-float (UECM)
+  float2* lny;            // ln y_s as double-float (UECM weights)
+  LnEntry* lntab;         // logarithm table (kLnTable entries)
   int64_t max_segments;
   int seg_target;
 };
@@ -158,7 +165,6 @@ struct ChunkArgs {
   long long* item_cnt;
   long long* item_base;
   long long* item_off;
-  int32_t* ovf;
   int32_t* staging;
   long long* sample_counts;
   void* scan_tmp;

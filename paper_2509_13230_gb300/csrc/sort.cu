@@ -9,6 +9,7 @@
 // ranking, so the buffer parity never depends on the data.
 #include "mh_internal.cuh"
 #include "scan.cuh"
+#include "walk_math.cuh"
 
 namespace mh {
 
@@ -143,32 +144,41 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
   }
 }
 
-// Rank-order copies of the parameters, the inverse permutation and the
-// fixed-point segment costs floor(min(v, 2^20) * 2^F) (scanned afterwards).
-__global__ void __launch_bounds__(256) gather_kernel(int model, const double* __restrict__ x,
-                                                      const double* __restrict__ y, int64_t n,
-                                                      const int32_t* __restrict__ sorted_ids, int32_t* perm,
-                                                      int32_t* rank, double* xs, double* ys, double* as,
-                                                      unsigned long long* qv) {
+__device__ __forceinline__ float2 split2(double v) {
+  const df2 d = df_from_double(v);
+  return make_float2(d.hi, d.lo);
+}
+
+// Rank-order copies of the parameters (FP64 and double-float), ln y for the
+// weights, the inverse permutation, the fixed-point segment costs
+// floor(min(v, 2^20) * 2^F) (scanned afterwards) and, in block 0, the
+// logarithm table.
+__global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __restrict__ sorted_ids) {
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < kLnTable; k += blockDim.x) ln_table_entry(g.lntab, k);
   const int32_t top = sorted_ids[0];
-  const double vmax = (model == MH_UBCM) ? x[top] : x[top] * y[top];
-  const int F = proxy_scale(vmax, n);
-  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+  const double vmax = (g.model == MH_UBCM) ? g.x[top] : g.x[top] * g.y[top];
+  const int F = proxy_scale(vmax, g.n);
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < g.n;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int32_t u = sorted_ids[r];
-    perm[r] = u;
-    rank[u] = static_cast<int32_t>(r);
-    const double xu = x[u];
-    xs[r] = xu;
+    g.perm[r] = u;
+    g.rank[u] = static_cast<int32_t>(r);
+    const double xu = g.x[u];
+    g.xs[r] = xu;
+    g.xdf[r] = split2(xu);
     double v = xu;
-    if (model == MH_UECM) {
-      const double yu = y[u];
-      ys[r] = yu;
+    if (g.model == MH_UECM) {
+      const double yu = g.y[u];
+      g.ys[r] = yu;
       v = xu * yu;
-      as[r] = v;
+      g.as[r] = v;
+      g.adf[r] = split2(v);
+      g.ydf[r] = split2(yu);
+      g.lny[r] = split2(log(yu));
     }
     const double vc = v > 0x1p20 ? 0x1p20 : v;
-    qv[r] = static_cast<unsigned long long>(ldexp(vc, F));
+    g.Q[r] = static_cast<unsigned long long>(ldexp(vc, F));
   }
 }
 
@@ -213,7 +223,7 @@ cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cud
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s) {
   (void)ctrl;
   const unsigned grid = grid_for(g.n, 256, static_cast<unsigned>(sm_count()) * 8u);
-  gather_kernel<<<grid, 256, 0, s>>>(g.model, g.x, g.y, g.n, sorted_vals, g.perm, g.rank, g.xs, g.ys, g.as, g.Q);
+  gather_kernel<<<grid, 256, 0, s>>>(g, sorted_vals);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -10,17 +10,21 @@
 // Random words: Philox4x32-10 of counter {d, k, i, s} (draw d of segment k of
 // row i in sample s); U from words (1,0), V from words (3,2).
 //
-// Decision arithmetic (walk_math.cuh).  The skip needs floor(t) exactly and
-// the acceptance test compares V with p/q; both use FP64 values computed in
-// one fixed order, so they match the serial definition bit for bit except for
-// draws within a few ulp of an integer boundary of t.
+// Decision arithmetic (walk_math.cuh): each draw is decided in double-float
+// arithmetic with an error bound and falls back to the canonical FP64
+// expressions only when it lies within that bound of a decision boundary
+// (or outside the fast path's range).  The acceptance test compares V with
+// the FP64 quotient p/q whenever the FP32 estimate is inconclusive, so the
+// decisions reproduce the FP64 definition bit for bit.
 //
-// Scheduling.  Warps take chunks of work items from a global ticket; an idle
-// lane takes the chunk's next item, so lanes stay busy when segment lengths
-// differ.  A lane buffers accepted ranks j in its shared-memory slot; when
-// its segment ends, the warp reserves staging space with one atomic and
-// copies the slot out with coalesced stores.  A segment with more than kSlot
-// edges is re-walked by a second kernel that writes straight to staging.
+// Scheduling.  Persistent warps take chunks of work items from a global
+// ticket; an idle lane takes the chunk's next item, so lanes stay busy when
+// segment lengths differ.  A lane buffers accepted ranks j in its
+// shared-memory slot; when its segment ends, the warp reserves staging space
+// with one atomic and copies the slot out with coalesced stores.  A segment
+// with more than kSlot edges is walked a second time by the same lane (the
+// walk is a pure function of the counter), now writing straight into a
+// staging range of exactly the counted size.
 #include "mh_internal.cuh"
 #include "walk_math.cuh"
 
@@ -42,82 +46,149 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // One segment's walk state.
 struct SegWalker {
-  int32_t i, k, b, pos;
-  uint32_t sample, d, cnt;
-  double q;       // current proposal probability (FP64 value of p or phat)
-  double xi;      // x_i (UBCM) or a_i = x_i y_i (UECM)
-  double yi;      // y_i (UECM)
-  double c;       // UECM bound constant exp(-beta_min)
-  bool uecm;
+  int32_t i, k, a, b, pos, qj;  // qj: the rank whose p (or phat) is the current q
+  uint32_t sample, d;
+  bool uecm, fast;              // fast: q lies inside the double-float path's range
+  double xi;                    // canonical x_i (UBCM) or a_i (UECM)
+  double yi, c;                 // UECM: y_i and the bound constant exp(-beta_min)
+  df2 xi_df, yi_df, inv1mc;     // double-float copies; inv1mc = 1 / (1 - c)
+  float omc_f;                  // 1 - c in FP32
+  df2 lam;                      // -ln(1 - q)
+  float q_f;                    // q in FP32
 
-  __device__ __forceinline__ void init(const Net& g, long long item, long long S, uint32_t sample0) {
+  __device__ __forceinline__ double q64(const Net& g) const {
+    return uecm ? prob_hat(xi, g.as[qj], c) : prob_ubcm(xi, g.xs[qj]);
+  }
+
+  // q <- p (UBCM) or phat (UECM) of candidate j, given its double-float
+  // product z = x_i x_j or A = a_i a_j.
+  __device__ __forceinline__ void set_q(int32_t j, df2 prod, const LnEntry* tab) {
+    qj = j;
+    if (!uecm) {
+      fast = prod.hi > 0x1p-100f && prod.hi < 0x1p40f;
+      if (fast) {
+        lam = log1p_df(prod, tab);
+        q_f = __fdividef(prod.hi, 1.0f + prod.hi);
+      }
+    } else {
+      const df2 gq = df_mul(prod, inv1mc);
+      fast = gq.hi > 0x1p-100f && gq.hi < 0x1p40f && omc_f >= 0x1p-20f;
+      if (fast) {
+        lam = log1p_df(gq, tab);
+        q_f = __fdividef(prod.hi, omc_f + prod.hi);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void init(const Net& g, long long item, long long S, uint32_t sample0,
+                                       const LnEntry* tab) {
     const long long s_local = item / S;
     const long long seg = item - s_local * S;
     const int4 e = g.seg[seg];
     i = e.x;
     k = e.y;
-    const int32_t a = e.z;
+    a = e.z;
     b = e.w;
     pos = a - 1;
     sample = sample0 + static_cast<uint32_t>(s_local);
     d = 0;
-    cnt = 0;
     uecm = (g.model == MH_UECM);
     const int32_t head = (g.flags & MH_INIT_PREV) ? a - 1 : a;
     if (!uecm) {
       xi = g.xs[i];
-      q = prob_ubcm(xi, g.xs[head]);
+      xi_df = to_df(g.xdf[i]);
+      set_q(head, df_mul(xi_df, to_df(g.xdf[head])), tab);
     } else {
       xi = g.as[i];
       yi = g.ys[i];
+      xi_df = to_df(g.adf[i]);
+      yi_df = to_df(g.ydf[i]);
       c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : yi * g.ymax[a];
-      q = prob_hat(xi, g.as[head], c);
+      const double omc = 1.0 - c;
+      inv1mc = df_from_double(1.0 / omc);
+      omc_f = static_cast<float>(omc);
+      set_q(head, df_mul(xi_df, to_df(g.adf[head])), tab);
     }
   }
 
   // One candidate.  Returns false when the segment has ended; otherwise sets
   // `accepted` and `j`.
   __device__ __forceinline__ bool step(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
-                                       unsigned long long& fallbacks, bool& accepted, int32_t& j) {
+                                       const LnEntry* tab, unsigned long long& fallbacks, bool& accepted,
+                                       int32_t& j) {
     accepted = false;
-    if (!(q > 0.0)) return false;
+    const bool fast_q = fast && !fp64_only;
+    double qc = 0.0;  // canonical q, computed only when a decision needs it
+    bool have_qc = false;
+    if (!fast_q) {
+      qc = q64(g);
+      have_qc = true;
+      if (!(qc > 0.0)) return false;
+    }
     const uint4 r = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0,
                                   key1);
     d += 1;
-    const int64_t room = static_cast<int64_t>(b) - pos - 1;  // candidates left in the segment
-    int64_t skip;  // floor(t), or >= room when the segment ends
-    if (q >= 1.0) {
-      skip = 0;
-    } else {
-      skip = skip_floor(r.y, r.x, q, room, fp64_only, fallbacks);
+    const unsigned long long NU = top53(r.y, r.x) + 1ull;  // U = NU 2^-53
+    const unsigned long long mV = top53(r.w, r.z);        // V = mV 2^-53
+    const int64_t room = static_cast<int64_t>(b) - pos - 1;
+    int64_t skip = 0;
+    bool decided = false;
+    if (fast_q) {
+      const df2 t = df_div(neg_ln_u53(NU, tab), lam);
+      decided = floor_decided(t, room, skip) != 0;
+    }
+    if (!decided) {
+      if (fast_q) fallbacks += 1;
+      if (!have_qc) {
+        qc = q64(g);
+        have_qc = true;
+      }
+      skip = skip_fp64(NU, qc, room);
     }
     if (skip >= room) return false;
     j = pos + 1 + static_cast<int32_t>(skip);
-    const double V = unit_open1(r.w, r.z);
-    double p, qn;
+
+    // acceptance and the next q
+    df2 prod;
+    int verdict = -1;
     if (!uecm) {
-      p = prob_ubcm(xi, g.xs[j]);
-      qn = p;
+      prod = df_mul(xi_df, to_df(g.xdf[j]));
+      if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f)
+        verdict = accept_decided(mV, __fdividef(prod.hi, 1.0f + prod.hi), q_f);
     } else {
-      const double aj = g.as[j];
-      p = prob_uecm(xi, aj, yi * g.ys[j]);
-      qn = prob_hat(xi, aj, c);
+      prod = df_mul(xi_df, to_df(g.adf[j]));
+      const df2 yj = to_df(g.ydf[j]);
+      const float omr = fmaf(-yi_df.hi, yj.hi, 1.0f) - fmaf(yi_df.hi, yj.lo, yi_df.lo * yj.hi);
+      if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f && omr > 0x1p-20f)
+        verdict = accept_decided(mV, __fdividef(prod.hi, omr + prod.hi), q_f);
     }
-    accepted = V < p / q;
-    q = qn;
+    if (verdict < 0) {
+      if (fast_q) fallbacks += 1;
+      if (!have_qc) qc = q64(g);
+      const double p = uecm ? prob_uecm(xi, g.as[j], yi * g.ys[j]) : prob_ubcm(xi, g.xs[j]);
+      verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
+    }
+    accepted = verdict != 0;
+    set_q(j, prod, tab);
     pos = j;
     return true;
   }
 };
 
 __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
-  extern __shared__ int32_t slots[];
+  extern __shared__ unsigned char smem_raw[];
+  LnEntry* tab = reinterpret_cast<LnEntry*>(smem_raw);
+  int32_t* slots = reinterpret_cast<int32_t*>(smem_raw + sizeof(LnEntry) * kLnTable);
+  ln_table_to_shared(tab, P.g.lntab);
+  __syncthreads();
+
   const Net& g = P.g;
   Ctrl* ctrl = P.ctrl;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   int32_t* my_slot = slots + (warp * 32 + lane) * kSlotStride;
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
+  const unsigned long long cap = static_cast<unsigned long long>(P.c.staging_cap);
 
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
@@ -126,6 +197,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
 
   SegWalker wk;
   bool active = false;
+  bool rewalk = false;           // second pass of an overflowing segment
+  unsigned cnt = 0;              // edges of the current pass
+  unsigned long long rbase = 0;  // staging base of a second pass
   long long item = 0;
   unsigned long long next = 0, end = 0;  // warp-uniform chunk cursor
   bool work_left = total > 0;
@@ -150,8 +224,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
         const unsigned rank = __popc(idle & lt);
         if (!active && rank < avail) {
           item = static_cast<long long>(next + rank);
-          wk.init(g, item, S, P.c.sample0);
+          wk.init(g, item, S, P.c.sample0, tab);
           active = true;
+          rewalk = false;
+          cnt = 0;
           n_segs += 1;
         }
         const unsigned take = __popc(idle);
@@ -165,23 +241,39 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
     if (active) {
       bool acc;
       int32_t j;
-      if (wk.step(g, P.c.key0, P.c.key1, fp64_only, n_fallback, acc, j)) {
+      if (wk.step(g, P.c.key0, P.c.key1, fp64_only, tab, n_fallback, acc, j)) {
         if (acc) {
-          if (wk.cnt < kSlot) my_slot[wk.cnt] = j;
-          wk.cnt += 1;
+          if (!rewalk) {
+            if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
+          } else if (rbase + cnt < cap) {
+            P.c.staging[rbase + cnt] = j;
+          }
+          cnt += 1;
         }
+      } else if (rewalk) {
+        active = false;  // second pass done; count and base were recorded
       } else {
-        n_draws += wk.d;  // every Philox draw of the segment, the ending one included
-        ended = true;
+        n_draws += wk.d;
+        n_edges += cnt;
+        if (cnt <= static_cast<unsigned>(kSlot)) {
+          ended = true;
+        } else {
+          // too many edges for the slot: reserve exactly cnt entries and walk again
+          rbase = atomicAdd(&ctrl->stage_used, static_cast<unsigned long long>(cnt));
+          if (rbase + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
+          P.c.item_cnt[item] = cnt;
+          P.c.item_base[item] = static_cast<long long>(rbase);
+          wk.init(g, item, S, P.c.sample0, tab);
+          rewalk = true;
+          cnt = 0;
+        }
       }
     }
 
     const unsigned ended_mask = __ballot_sync(0xffffffffu, ended);
     if (ended_mask) {
-      const bool direct = ended && wk.cnt <= kSlot;
-      unsigned long long need = direct ? wk.cnt : 0;
-      // warp-exclusive prefix of the staging need
-      unsigned long long incl = need;
+      const unsigned long long need = ended ? cnt : 0;
+      unsigned long long incl = need;  // warp-inclusive prefix of the staging need
 #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
         const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, dd);
@@ -193,27 +285,18 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
       base0 = __shfl_sync(0xffffffffu, base0, 0);
       const unsigned long long my_base = base0 + incl - need;
       if (ended) {
-        n_edges += wk.cnt;
-        P.c.item_cnt[item] = wk.cnt;
-        if (direct) {
-          P.c.item_base[item] = static_cast<long long>(my_base);
-          if (my_base + wk.cnt > static_cast<unsigned long long>(P.c.staging_cap))
-            atomicOr(&ctrl->status, kStCapacity);
-        } else {
-          P.c.item_base[item] = -1;
-          const unsigned long long slot_idx = atomicAdd(&ctrl->overflow_count, 1ull);
-          P.c.ovf[slot_idx] = static_cast<int32_t>(item);
-        }
+        P.c.item_cnt[item] = cnt;
+        P.c.item_base[item] = static_cast<long long>(my_base);
+        if (my_base + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
       }
       __syncwarp();
       unsigned m = ended_mask;
       while (m) {
         const int l = __ffs(m) - 1;
         m &= m - 1;
-        const unsigned cnt_l = __shfl_sync(0xffffffffu, wk.cnt, l);
+        const unsigned cnt_l = __shfl_sync(0xffffffffu, cnt, l);
         const unsigned long long base_l = __shfl_sync(0xffffffffu, my_base, l);
-        if (cnt_l <= static_cast<unsigned>(kSlot) &&
-            base_l + cnt_l <= static_cast<unsigned long long>(P.c.staging_cap)) {
+        if (base_l + cnt_l <= cap) {
           const int32_t* src_slot = slots + (warp * 32 + l) * kSlotStride;
           for (unsigned e = lane; e < cnt_l; e += 32) P.c.staging[base_l + e] = src_slot[e];
         }
@@ -223,7 +306,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
     }
   }
 
-  // statistics
 #pragma unroll
   for (int dd = 16; dd; dd >>= 1) {
     n_draws += __shfl_xor_sync(0xffffffffu, n_draws, dd);
@@ -239,60 +321,31 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
   }
 }
 
-// Segments with more edges than a shared-memory slot: walk again and write
-// the ranks straight into staging.
-__global__ void __launch_bounds__(128) overflow_kernel(WalkParams P) {
-  const Net& g = P.g;
-  Ctrl* ctrl = P.ctrl;
-  long long S = ctrl->num_segments;
-  if (S > g.max_segments) S = g.max_segments;
-  const unsigned long long count = ctrl->overflow_count;
-  const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
-  for (unsigned long long t = blockIdx.x * static_cast<unsigned long long>(blockDim.x) + threadIdx.x; t < count;
-       t += static_cast<unsigned long long>(gridDim.x) * blockDim.x) {
-    const long long item = P.c.ovf[t];
-    const long long cnt = P.c.item_cnt[item];
-    const unsigned long long base = atomicAdd(&ctrl->stage_used, static_cast<unsigned long long>(cnt));
-    P.c.item_base[item] = static_cast<long long>(base);
-    const bool fits = base + cnt <= static_cast<unsigned long long>(P.c.staging_cap);
-    if (!fits) atomicOr(&ctrl->status, kStCapacity);
-    SegWalker wk;
-    wk.init(g, item, S, P.c.sample0);
-    unsigned long long fb = 0;
-    long long e = 0;
-    bool acc;
-    int32_t j;
-    while (wk.step(g, P.c.key0, P.c.key1, fp64_only, fb, acc, j)) {
-      if (acc) {
-        if (fits && e < cnt) P.c.staging[base + e] = j;
-        ++e;
-      }
-    }
-  }
-}
-
 }  // namespace
+
+size_t walk_smem_bytes() {
+  return sizeof(LnEntry) * kLnTable + static_cast<size_t>(kWalkWarps) * 32 * kSlotStride * sizeof(int32_t);
+}
 
 cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
   WalkParams P{g, c, ctrl};
   const int threads = kWalkWarps * 32;
-  const size_t smem = static_cast<size_t>(threads) * kSlotStride * sizeof(int32_t);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  const size_t smem = walk_smem_bytes();
+  static int per_sm_cache[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+  if (per_sm == 0) {
+    e = cudaFuncSetAttribute(walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    configured = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel, threads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   walk_kernel<<<static_cast<unsigned>(sm_count() * per_sm), threads, smem, s>>>(P);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  overflow_kernel<<<static_cast<unsigned>(sm_count()), 128, 0, s>>>(P);
-  note_launches(2);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -1,20 +1,40 @@
 // Decision arithmetic of the walk and of the weight draw.
 //
-// Edge probabilities in the canonical FP64 order (no FMA contraction; the
-// library is built with --fmad=false):
+// Canonical values (the definition every decision must reproduce): FP64
+// expressions in one fixed order, no FMA contraction (--fmad=false):
 //   UBCM  (Eq. 1): z = x_i x_j,          p = z / (1 + z)
 //   UECM  (Eq. 3): A = a_i a_j,          p = A / ((1 - r) + A),  r = y_i y_j
 //   bound (Eq. 5):                       phat = A / ((1 - c) + A)
-// with a = x y.  The geometric skip and the weight need floor(ln U / ln v)
-// for v = 1 - q and v = r; skip_floor / weight_floor return it exactly up to
-// draws within a few ulp of an integer, where the FP64 library logarithm of
-// the device and of the host may round differently.
+//   skip  (Fig. 2): L = 1 + floor(log(U) / log1p(-q))
+//   accept:        V < p / q
+//   weight (Eq. 4): w = 1 + floor(log(U_w) / log(r))
+// with a = x y and the FP64 library log / log1p.
+//
+// Fast path.  A draw is first decided in double-float arithmetic: values
+// are unevaluated sums hi + lo of two FP32 numbers (about 48 significant
+// bits), built from error-free transformations (Dekker 1971; Joldes, Muller,
+// Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", 2017).  Logarithms use Tang's table-driven method
+// ("Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 1990): f = c_k (1 + r) with c_k from a
+// 512-entry table, ln f = ln c_k + log1p(r), |r| < 2^-9, log1p by its
+// alternating series.  With these
+//   t = E / lambda,  E = -ln U,  lambda = -ln(1 - q) = log1p(z)  (UBCM)
+//                                              = log1p(A / (1 - c))  (UECM)
+// is known to a relative error far below 2^-36; the skip is decided when t
+// lies more than t 2^-36 + 2^-40 from every integer, the acceptance when
+// V lies more than p/q 2^-18 from p/q (estimated in FP32).  Anything else,
+// and any input outside the fast path's range, takes the canonical FP64
+// path above, so decisions equal the canonical ones except where the device
+// and host FP64 logarithms themselves round differently (draws within a few
+// ulp of an integer boundary).
 #pragma once
 
 #include "mh_internal.cuh"
 
 namespace mh {
 
+// ---- canonical FP64 values ----------------------------------------------------
 __device__ __forceinline__ double prob_ubcm(double xi, double xj) {
   const double z = xi * xj;
   return z / (1.0 + z);
@@ -28,34 +48,248 @@ __device__ __forceinline__ double prob_hat(double ai, double aj, double c) {
   return A / ((1.0 - c) + A);
 }
 
-// floor(t), t = ln U / ln(1 - q) with U from 53 random bits, 0 < q < 1.
-// Returns `room` (or more) when t >= room, i.e. the candidate falls past the
-// segment end.
-__device__ __forceinline__ int64_t skip_floor(uint32_t hi, uint32_t lo, double q, int64_t room, bool fp64_only,
-                                              unsigned long long& fallbacks) {
-  (void)fp64_only;
-  (void)fallbacks;
-  const double U = unit_open0(hi, lo);
+// ---- double-float primitives ---------------------------------------------------
+struct df2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return df2{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df2 fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = a + b;
+  return df2{s, b - (s - a)};
+}
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+  const df2 s = two_sum(a.hi, b.hi);
+  const df2 t = two_sum(a.lo, b.lo);
+  const df2 v = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(v.hi, t.lo + v.lo);
+}
+__device__ __forceinline__ df2 df_add_f(df2 a, float b) {
+  const df2 s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, a.lo + s.lo);
+}
+__device__ __forceinline__ df2 df_div(df2 a, df2 b) {
+  const float th = __fdividef(a.hi, b.hi);
+  const df2 r = df_mul_f(b, th);
+  const float dh = a.hi - r.hi;  // exact: th is within a few ulp of a.hi / b.hi
+  const float dl = a.lo - r.lo;
+  const float tl = __fdividef(dh + dl, b.hi);
+  return fast_two_sum(th, tl);
+}
+__device__ __forceinline__ df2 to_df(float2 v) { return df2{v.x, v.y}; }
+
+// FP64 value -> nearest double-float (setup only; uses the FP64 pipe).
+__device__ __forceinline__ df2 df_from_double(double v) {
+  const float h = __double2float_rn(v);
+  return df2{h, __double2float_rn(v - static_cast<double>(h))};
+}
+
+// ---- logarithm table (Tang 1990) ------------------------------------------------
+// Entry k: c_k = the FP32 value f with the 14 low fraction bits cleared, for
+// f in [0.75, 1.5): k < 256 covers c in [1, 1.5) (step 2^-9), k >= 256 covers
+// c in [0.75, 1) (step 2^-10).  inv = 1 / c_k and ln = ln c_k as double-floats.
+constexpr int kLnTable = 512;
+struct LnEntry {
+  float inv_hi, inv_lo, ln_hi, ln_lo;
+};
+
+__device__ __forceinline__ float ln_table_c(int k) {
+  return k < 256 ? 1.0f + static_cast<float>(k) * 0x1p-9f : 0.5f * (1.0f + static_cast<float>(k) * 0x1p-9f);
+}
+
+// Fills `tab` (kLnTable entries); one thread per entry.
+__device__ __forceinline__ void ln_table_entry(LnEntry* tab, int k) {
+  const double c = static_cast<double>(ln_table_c(k));
+  const df2 inv = df_from_double(1.0 / c);
+  const df2 ln = df_from_double(log(c));
+  tab[k] = LnEntry{inv.hi, inv.lo, ln.hi, ln.lo};
+}
+
+// Copies the workspace table into shared memory (whole block, then sync).
+__device__ __forceinline__ void ln_table_to_shared(LnEntry* sh, const LnEntry* global) {
+  for (int t = threadIdx.x; t < kLnTable; t += blockDim.x) sh[t] = global[t];
+}
+
+constexpr float kLn2Hi = 0.693147182464599609375f;    // ln 2 rounded to FP32
+constexpr float kLn2Lo = -1.904654323148236017e-09f;  // ln 2 - kLn2Hi
+
+// ln f for a double-float f in [0.75, 1.5) (|ln f| >= 2^-10 when f < 1,
+// see neg_ln_u53).  Relative error below 2^-44 away from f = 1.
+__device__ __forceinline__ df2 ln_mid(df2 f, const LnEntry* tab) {
+  const unsigned bits = __float_as_uint(f.hi);
+  const int k = static_cast<int>((bits >> 14) & 511u);
+  const float c = __uint_as_float(bits & ~0x3FFFu);  // f.hi with 14 low bits cleared
+  const LnEntry e = tab[k];
+  const df2 d = two_sum(f.hi - c, f.lo);             // f.hi - c is exact
+  const df2 r = df_mul(d, df2{e.inv_hi, e.inv_lo});  // f = c (1 + r), |r| < 2^-9
+  // log1p(r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 (truncation < |r|^6/6 < 2^-56)
+  const float rh = r.hi;
+  const float r2h = rh * rh;
+  const float r2l = fmaf(rh, rh, -r2h) + 2.0f * rh * r.lo;
+  const float tail = rh * r2h * fmaf(rh, fmaf(rh, 0.2f, -0.25f), 0.333333343f);
+  const df2 half_r2 = df2{-0.5f * r2h, -0.5f * r2l};
+  df2 s = df_add(r, half_r2);
+  s = df_add_f(s, tail);
+  return df_add(df2{e.ln_hi, e.ln_lo}, s);
+}
+
+// Splits a double-float v >= 2^-100 into 2^e * f with f in [0.75, 1.5).
+__device__ __forceinline__ df2 split_mid(df2 v, int& e) {
+  int ex = static_cast<int>((__float_as_uint(v.hi) >> 23) & 0xFF) - 127;
+  if (__uint_as_float((__float_as_uint(v.hi) & 0x007FFFFFu) | 0x3F800000u) >= 1.5f) ex += 1;
+  e = ex;
+  const float sc = __uint_as_float(static_cast<unsigned>(127 - ex) << 23);  // 2^-ex, exact
+  return df2{v.hi * sc, v.lo * sc};
+}
+
+// log1p(v) for a double-float v >= 0 (v.hi >= 2^-100).
+__device__ __forceinline__ df2 log1p_df(df2 v, const LnEntry* tab) {
+  if (v.hi < 0x1p-9f) {
+    // v - v^2/2 + v^3/3 - v^4/4 + v^5/5 (truncation < v^6/6)
+    const float vh = v.hi;
+    const float v2h = vh * vh;
+    const float v2l = fmaf(vh, vh, -v2h) + 2.0f * vh * v.lo;
+    const float tail = vh * v2h * fmaf(vh, fmaf(vh, 0.2f, -0.25f), 0.333333343f);
+    df2 s = df_add(v, df2{-0.5f * v2h, -0.5f * v2l});
+    return df_add_f(s, tail);
+  }
+  int e;
+  const df2 f = split_mid(df_add_f(v, 1.0f), e);
+  const df2 lf = ln_mid(f, tab);
+  if (e == 0) return lf;
+  const float ef = static_cast<float>(e);
+  const df2 eln2 = df_mul_f(df2{kLn2Hi, kLn2Lo}, ef);
+  return df_add(eln2, lf);
+}
+
+// E = -ln U for U = N 2^-53, N = 1 .. 2^53 (exact integer input).
+__device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* tab) {
+  const unsigned long long W = (1ull << 53) - N;  // (1 - U) 2^53, exact
+  if (W < (1ull << 44)) {
+    // -ln(1 - w) = w + w^2/2 + w^3/3 + w^4/4 + w^5/5 (truncation < w^6/6), w < 2^-9
+    const float wh0 = static_cast<float>(W);
+    const float wl0 = static_cast<float>(static_cast<long long>(W) - static_cast<long long>(wh0));
+    const df2 w = fast_two_sum(wh0 * 0x1p-53f, wl0 * 0x1p-53f);
+    const float wh = w.hi;
+    const float w2h = wh * wh;
+    const float w2l = fmaf(wh, wh, -w2h) + 2.0f * wh * w.lo;
+    const float tail = wh * w2h * fmaf(wh, fmaf(wh, 0.2f, 0.25f), 0.333333343f);
+    df2 s = df_add(w, df2{0.5f * w2h, 0.5f * w2l});
+    return df_add_f(s, tail);
+  }
+  // N = 2^(e) f, f in [0.75, 1.5); E = (53 - e) ln 2 - ln f
+  const int lz = __clzll(static_cast<long long>(N));
+  const unsigned long long Nn = N << lz;                      // leading one at bit 63
+  const float h = static_cast<float>(Nn >> 40) * 0x1p-23f;    // top 24 bits, in [1, 2)
+  const float l = static_cast<float>(Nn & ((1ull << 40) - 1)) * 0x1p-63f;
+  int e = 63 - lz;
+  df2 f = fast_two_sum(h, l);
+  if (f.hi >= 1.5f) {
+    f = df2{f.hi * 0.5f, f.lo * 0.5f};
+    e += 1;
+  }
+  const df2 lf = ln_mid(f, tab);
+  const int m = 53 - e;
+  if (m == 0) return df2{-lf.hi, -lf.lo};
+  const df2 mln2 = df_mul_f(df2{kLn2Hi, kLn2Lo}, static_cast<float>(m));
+  return df_add(mln2, df2{-lf.hi, -lf.lo});
+}
+
+// Exact decision of floor(t) for a double-float t >= 0 against `room`:
+// returns 1 and sets `fl` when decided, 0 when t is within the error margin
+// of an integer.  fl >= room means the candidate is past the segment end.
+__device__ __forceinline__ int floor_decided(df2 t, int64_t room, int64_t& fl) {
+  if (t.hi > static_cast<float>(room) * 1.0001f + 2.0f) {  // far past the end
+    fl = room;
+    return 1;
+  }
+  const float margin = fmaf(t.hi, 0x1p-36f, 0x1p-40f);
+  const float fh = floorf(t.hi);
+  float f0, f1;
+  int64_t F;
+  if (fh == t.hi) {
+    const float fl_lo = floorf(t.lo);
+    F = static_cast<int64_t>(fh) + static_cast<int64_t>(fl_lo);
+    f0 = t.lo - fl_lo;
+    f1 = 1.0f - f0;
+  } else {
+    F = static_cast<int64_t>(fh);
+    const float d = t.hi - fh;  // exact
+    f0 = d + t.lo;
+    f1 = (1.0f - d) - t.lo;
+  }
+  if (!(f0 > margin) || !(f1 > margin)) return 0;
+  fl = F;
+  return 1;
+}
+
+// Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.
+static __device__ __noinline__ int64_t skip_fp64(unsigned long long N, double q, int64_t room) {
+  if (q >= 1.0) return 0;
+  const double U = static_cast<double>(N) * 0x1p-53;
   const double t = log(U) / log1p(-q);
   if (t >= static_cast<double>(room)) return room;
   return static_cast<int64_t>(floor(t));
 }
 
-// UECM weight of edge e of segment k, row i, sample s (Eq. 4):
-// w = 1 + floor(ln U_w / ln r), U_w from Philox {2^31 | e/2, k, i, s},
-// words (1,0) for even e and (3,2) for odd e.  Sets `overflow` and returns
-// INT32_MAX above INT32_MAX - 1.
-__device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t i, uint32_t sample, uint32_t key0,
-                                               uint32_t key1, double r, bool& overflow) {
+// Acceptance filter: 1 = accept, 0 = reject, -1 = undecided (use FP64).
+// p_f / q_f approximates p/q to a relative error well below 2^-18.
+__device__ __forceinline__ int accept_decided(unsigned long long mV, float p_f, float q_f) {
+  const float R = __fdividef(p_f, q_f);
+  const float vlo = static_cast<float>(mV >> 29) * 0x1p-24f;          // V in [vlo, vlo + 2^-24)
+  const float vhi = vlo + 0x1p-24f;
+  if (vhi <= R * (1.0f - 0x1p-18f)) return 1;
+  if (vlo >= R * (1.0f + 0x1p-18f)) return 0;
+  return -1;
+}
+
+// ---- UECM weight (Eq. 4) ---------------------------------------------------------
+// w = 1 + floor(ln U_w / ln r) for edge e of segment k, row i, sample s; U_w
+// from Philox {2^31 | e/2, k, i, s}, words (1,0) for even e and (3,2) for odd
+// e.  lny_i + lny_j approximates ln r in double-float (per-node ln y); the
+// FP64 path computes log(U_w) / log(fl(y_i y_j)).
+static __device__ __noinline__ int32_t weight_fp64(unsigned long long N, double r, bool& overflow) {
   if (!(r > 0.0)) return 1;
-  const uint4 w = philox4x32_10(make_uint4(0x80000000u | (e >> 1), k, i, sample), key0, key1);
-  const double Uw = (e & 1u) ? unit_open0(w.w, w.z) : unit_open0(w.y, w.x);
-  const double tw = log(Uw) / log(r);
+  const double tw = log(static_cast<double>(N) * 0x1p-53) / log(r);
   if (tw >= 2147483646.0) {
     overflow = true;
     return 2147483647;
   }
   return 1 + static_cast<int32_t>(floor(tw));
+}
+
+__device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t i, uint32_t sample, uint32_t key0,
+                                               uint32_t key1, double yi, double yj, df2 lnyi, df2 lnyj,
+                                               const LnEntry* tab, bool fp64_only, bool& overflow,
+                                               unsigned long long& fallbacks) {
+  const uint4 w = philox4x32_10(make_uint4(0x80000000u | (e >> 1), k, i, sample), key0, key1);
+  const unsigned long long N = (e & 1u) ? top53(w.w, w.z) + 1ull : top53(w.y, w.x) + 1ull;
+  const df2 nlr = df_add(lnyi, lnyj);  // ln r (negative)
+  if (!fp64_only && nlr.hi < -0x1p-12f && nlr.hi > -0x1p+100f) {
+    const df2 E = neg_ln_u53(N, tab);
+    const df2 t = df_div(E, df2{-nlr.hi, -nlr.lo});
+    int64_t fl;
+    if (t.hi < 2.0e9f && floor_decided(t, 0x7FFFFFFFll, fl)) return 1 + static_cast<int32_t>(fl);
+  }
+  fallbacks += 1;
+  return weight_fp64(N, yi * yj, overflow);
 }
 
 }  // namespace mh
