@@ -146,13 +146,19 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.item_base = take(8 * static_cast<size_t>(L.items_max));
   L.item_off = take(8 * (static_cast<size_t>(L.items_max) + 1));
   L.sample_counts = take(8 * static_cast<size_t>(p.num_samples));
-  L.staging = take(4 * static_cast<size_t>(capacity));
+  // Warps reserve staging in chunks of kStageChunk entries; a chunk switch
+  // leaves fewer than kSlot entries behind and a warp's last chunk may be
+  // partly unused, so staging holds capacity + capacity / 16 + the chunks.
+  L.staging_entries = capacity + capacity / 16 + static_cast<int64_t>(kMaxWalkWarps) * (kStageChunk + kSlot);
+  L.staging = take(4 * static_cast<size_t>(L.staging_entries));
   L.scan_tmp = take(sizeof(Top2) * static_cast<size_t>(L.scan_tmp_elems));
   L.xdf = take(8 * static_cast<size_t>(n));
   L.adf = take(8 * static_cast<size_t>(n));
   L.ydf = take(8 * static_cast<size_t>(n));
   L.lny = take(8 * static_cast<size_t>(n));
   L.lntab = take(16 * 512);
+  L.seg_c = take(8 * static_cast<size_t>(L.max_segments));
+  L.seg_cf = take(16 * static_cast<size_t>(L.max_segments));
   L.total = off;
   return L;
 }
@@ -175,6 +181,8 @@ static Net make_net(int model, const mh_params& p, const double* x, const double
   g.Q = reinterpret_cast<unsigned long long*>(ws + L.Q);
   g.rowoff = reinterpret_cast<long long*>(ws + L.rowoff);
   g.seg = reinterpret_cast<int4*>(ws + L.seg);
+  g.seg_c = reinterpret_cast<double*>(ws + L.seg_c);
+  g.seg_cf = reinterpret_cast<float4*>(ws + L.seg_cf);
   g.xdf = reinterpret_cast<float2*>(ws + L.xdf);
   g.adf = (model == MH_UECM) ? reinterpret_cast<float2*>(ws + L.adf) : g.xdf;
   g.ydf = reinterpret_cast<float2*>(ws + L.ydf);
@@ -324,7 +332,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
   c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
   c.scan_tmp = ws + L.scan_tmp;
-  c.staging_cap = o.capacity;
+  c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
   for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
     const int64_t left = static_cast<int64_t>(p->num_samples) - first;

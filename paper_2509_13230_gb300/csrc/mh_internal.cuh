@@ -50,9 +50,10 @@ constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;
 constexpr int kWalkWarps = 8;                    // warps per walk block
-constexpr int kSlot = 64;                        // edges a lane buffers in shared memory
+constexpr int kSlot = 48;                        // edges a lane buffers in shared memory
 constexpr int kSlotStride = kSlot + 1;           // padded to spread banks
-constexpr int kWalkChunk = 64;                   // work items per warp ticket
+constexpr int kMaxWalkWarps = 8192;              // cap on resident walk warps (staging slack)
+constexpr int kStageChunk = 1024;                // staging entries a warp reserves at a time
 constexpr int kEmitItems = 128;                  // work items per emit block
 constexpr long long kItemChunk = 1ll << 22;      // work items per sample chunk
 constexpr int kDefaultSegTarget = 32;
@@ -64,7 +65,8 @@ struct Layout {
   size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
          as = 0, ymax = 0, top1 = 0, top2 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
          item_off = 0, sample_counts = 0, staging = 0, scan_tmp = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
-         lntab = 0, total = 0;
+         lntab = 0, seg_c = 0, seg_cf = 0, total = 0;
+  int64_t staging_entries = 0;
 };
 
 Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity);
@@ -91,6 +93,8 @@ struct Net {
   unsigned long long* Q;  // [n+1] proxy prefix sums
   long long* rowoff;      // [n+1] first segment of each row; rowoff[n] = S
   int4* seg;              // {row, k, a, b}
+  double* seg_c;          // UECM: bound constant c of each segment
+  float4* seg_cf;         // UECM: (1/(1-c) hi, lo, 1-c, 0) of each segment
   float2* xdf;            // x_s as double-float (hi, lo)
   float2* adf;            // a_s = x_s y_s as double-float (UECM)
   float2* ydf;            // y_s as double-float (UECM)

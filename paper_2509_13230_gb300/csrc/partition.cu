@@ -17,6 +17,7 @@
 // reproducible and strictly increasing for T >= 2.
 #include "mh_internal.cuh"
 #include "scan.cuh"
+#include "walk_math.cuh"
 
 namespace mh {
 
@@ -136,6 +137,14 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
     const int64_t a = (k == 0) ? i + 1 : cut(k);
     const int64_t b = (k + 1 == nseg) ? g.n : cut(k + 1);
     g.seg[s] = make_int4(static_cast<int>(i), static_cast<int>(k), static_cast<int>(a), static_cast<int>(b));
+    if (g.model == MH_UECM) {
+      // exp(-beta_min) of this segment and the walk's FP32 / double-float forms
+      const double c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : g.ys[i] * g.ymax[a];
+      const double omc = 1.0 - c;
+      const df2 inv = df_from_double(1.0 / omc);
+      g.seg_c[s] = c;
+      g.seg_cf[s] = make_float4(inv.hi, inv.lo, static_cast<float>(omc), 0.0f);
+    }
   }
 }
 

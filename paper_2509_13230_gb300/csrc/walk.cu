@@ -44,27 +44,126 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// One segment's walk state.
+// One segment's walk state.  A lane's iteration is either the head of a new
+// segment (q <- p at the head, no draw consumed) or one candidate; both run
+// the same expensive code (Philox and -ln U of the next draw, the product
+// x_i x_j, log1p for the next q), so a warp whose lanes start segments at
+// different times stays converged.  The draw of the next iteration is
+// computed one iteration ahead: it does not depend on the decisions taken in
+// this one, so the two dependency chains overlap.
 struct SegWalker {
   int32_t i, k, a, b, pos, qj;  // qj: the rank whose p (or phat) is the current q
-  uint32_t sample, d;
-  bool uecm, fast;              // fast: q lies inside the double-float path's range
+  uint32_t sample, d;           // d: index of the next draw
+  bool fresh;                   // the head of the segment is still to be set up
+  bool fast;                    // q lies inside the double-float path's range
   double xi;                    // canonical x_i (UBCM) or a_i (UECM)
   double yi, c;                 // UECM: y_i and the bound constant exp(-beta_min)
   df2 xi_df, yi_df, inv1mc;     // double-float copies; inv1mc = 1 / (1 - c)
   float omc_f;                  // 1 - c in FP32
   df2 lam;                      // -ln(1 - q)
   float q_f;                    // q in FP32
+  uint4 rnd;                    // Philox words of draw d
+  df2 E;                        // -ln U of draw d
 
-  __device__ __forceinline__ double q64(const Net& g) const {
+  __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
     return uecm ? prob_hat(xi, g.as[qj], c) : prob_ubcm(xi, g.xs[qj]);
   }
 
-  // q <- p (UBCM) or phat (UECM) of candidate j, given its double-float
-  // product z = x_i x_j or A = a_i a_j.
-  __device__ __forceinline__ void set_q(int32_t j, df2 prod, const LnEntry* tab) {
-    qj = j;
+  // Loads the segment of `item`; its head is set up by the next advance().
+  __device__ __forceinline__ void begin(const Net& g, long long item, long long S, uint32_t sample0, bool uecm) {
+    const long long s_local = item / S;
+    const long long seg = item - s_local * S;
+    const int4 e = g.seg[seg];
+    i = e.x;
+    k = e.y;
+    a = e.z;
+    b = e.w;
+    pos = a - 1;
+    sample = sample0 + static_cast<uint32_t>(s_local);
+    d = 0;
+    fresh = true;
     if (!uecm) {
+      xi = g.xs[i];
+      xi_df = to_df(g.xdf[i]);
+    } else {
+      xi = g.as[i];
+      yi = g.ys[i];
+      xi_df = to_df(g.adf[i]);
+      yi_df = to_df(g.ydf[i]);
+      c = g.seg_c[seg];
+      const float4 cf = g.seg_cf[seg];
+      inv1mc = df2{cf.x, cf.y};
+      omc_f = cf.z;
+    }
+  }
+
+  // One iteration.  Returns false when the segment has ended; sets
+  // `accepted` / `j` when a candidate was evaluated (never on a head step).
+  template <bool kUecm>
+  __device__ __forceinline__ bool advance(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
+                                          bool init_prev, const LnEntry* tab, unsigned long long& fallbacks,
+                                          bool& accepted, int32_t& j) {
+    accepted = false;
+    const bool head = fresh;
+    const bool fast_q = !head && fast && !fp64_only;
+    double qc = 0.0;  // canonical q, computed only when a decision needs it
+    bool have_qc = false;
+    if (!head && !fast_q) {
+      qc = q64(g, kUecm);
+      have_qc = true;
+      if (!(qc > 0.0)) return false;
+    }
+    const uint4 r = rnd;
+    df2 t = df2{0.0f, 0.0f};
+    if (fast_q) t = df_div(E, lam);
+    if (!head) d += 1;
+    // Philox words and -ln U of the next draw (draw 0 on a head step)
+    rnd = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0, key1);
+    E = neg_ln_u53(top53(rnd.y, rnd.x) + 1ull, tab);
+    if (head) {
+      fresh = false;
+      j = init_prev ? a - 1 : a;
+    } else {
+      const int room = b - pos - 1;
+      unsigned skip = 0;
+      const bool decided = fast_q && floor_decided(t, room, skip);
+      if (!decided) {
+        if (fast_q) fallbacks += 1;
+        if (!have_qc) {
+          qc = q64(g, kUecm);
+          have_qc = true;
+        }
+        skip = skip_fp64(top53(r.y, r.x) + 1ull, qc, room);
+      }
+      if (skip >= static_cast<unsigned>(room)) return false;
+      j = pos + 1 + static_cast<int32_t>(skip);
+    }
+    // product x_i x_j (a_i a_j) for the acceptance test and the next q
+    const df2 prod = df_mul(xi_df, to_df(kUecm ? g.adf[j] : g.xdf[j]));
+    if (!head) {
+      const unsigned long long mV = top53(r.w, r.z);  // V = mV 2^-53
+      int verdict = -1;
+      if (!kUecm) {
+        if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f)
+          verdict = accept_decided(mV, __fdividef(prod.hi, 1.0f + prod.hi), q_f);
+      } else {
+        const df2 yj = to_df(g.ydf[j]);
+        const float omr = fmaf(-yi_df.hi, yj.hi, 1.0f) - fmaf(yi_df.hi, yj.lo, yi_df.lo * yj.hi);
+        if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f && omr > 0x1p-20f)
+          verdict = accept_decided(mV, __fdividef(prod.hi, omr + prod.hi), q_f);
+      }
+      if (verdict < 0) {
+        if (fast_q) fallbacks += 1;
+        if (!have_qc) qc = q64(g, kUecm);
+        const double p = kUecm ? prob_uecm(xi, g.as[j], yi * g.ys[j]) : prob_ubcm(xi, g.xs[j]);
+        verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
+      }
+      accepted = verdict != 0;
+      pos = j;
+    }
+    // q <- p (UBCM) or phat (UECM) of j
+    qj = j;
+    if (!kUecm) {
       fast = prod.hi > 0x1p-100f && prod.hi < 0x1p40f;
       if (fast) {
         lam = log1p_df(prod, tab);
@@ -78,104 +177,12 @@ struct SegWalker {
         q_f = __fdividef(prod.hi, omc_f + prod.hi);
       }
     }
-  }
-
-  __device__ __forceinline__ void init(const Net& g, long long item, long long S, uint32_t sample0,
-                                       const LnEntry* tab) {
-    const long long s_local = item / S;
-    const long long seg = item - s_local * S;
-    const int4 e = g.seg[seg];
-    i = e.x;
-    k = e.y;
-    a = e.z;
-    b = e.w;
-    pos = a - 1;
-    sample = sample0 + static_cast<uint32_t>(s_local);
-    d = 0;
-    uecm = (g.model == MH_UECM);
-    const int32_t head = (g.flags & MH_INIT_PREV) ? a - 1 : a;
-    if (!uecm) {
-      xi = g.xs[i];
-      xi_df = to_df(g.xdf[i]);
-      set_q(head, df_mul(xi_df, to_df(g.xdf[head])), tab);
-    } else {
-      xi = g.as[i];
-      yi = g.ys[i];
-      xi_df = to_df(g.adf[i]);
-      yi_df = to_df(g.ydf[i]);
-      c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : yi * g.ymax[a];
-      const double omc = 1.0 - c;
-      inv1mc = df_from_double(1.0 / omc);
-      omc_f = static_cast<float>(omc);
-      set_q(head, df_mul(xi_df, to_df(g.adf[head])), tab);
-    }
-  }
-
-  // One candidate.  Returns false when the segment has ended; otherwise sets
-  // `accepted` and `j`.
-  __device__ __forceinline__ bool step(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
-                                       const LnEntry* tab, unsigned long long& fallbacks, bool& accepted,
-                                       int32_t& j) {
-    accepted = false;
-    const bool fast_q = fast && !fp64_only;
-    double qc = 0.0;  // canonical q, computed only when a decision needs it
-    bool have_qc = false;
-    if (!fast_q) {
-      qc = q64(g);
-      have_qc = true;
-      if (!(qc > 0.0)) return false;
-    }
-    const uint4 r = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0,
-                                  key1);
-    d += 1;
-    const unsigned long long NU = top53(r.y, r.x) + 1ull;  // U = NU 2^-53
-    const unsigned long long mV = top53(r.w, r.z);        // V = mV 2^-53
-    const int64_t room = static_cast<int64_t>(b) - pos - 1;
-    int64_t skip = 0;
-    bool decided = false;
-    if (fast_q) {
-      const df2 t = df_div(neg_ln_u53(NU, tab), lam);
-      decided = floor_decided(t, room, skip) != 0;
-    }
-    if (!decided) {
-      if (fast_q) fallbacks += 1;
-      if (!have_qc) {
-        qc = q64(g);
-        have_qc = true;
-      }
-      skip = skip_fp64(NU, qc, room);
-    }
-    if (skip >= room) return false;
-    j = pos + 1 + static_cast<int32_t>(skip);
-
-    // acceptance and the next q
-    df2 prod;
-    int verdict = -1;
-    if (!uecm) {
-      prod = df_mul(xi_df, to_df(g.xdf[j]));
-      if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f)
-        verdict = accept_decided(mV, __fdividef(prod.hi, 1.0f + prod.hi), q_f);
-    } else {
-      prod = df_mul(xi_df, to_df(g.adf[j]));
-      const df2 yj = to_df(g.ydf[j]);
-      const float omr = fmaf(-yi_df.hi, yj.hi, 1.0f) - fmaf(yi_df.hi, yj.lo, yi_df.lo * yj.hi);
-      if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f && omr > 0x1p-20f)
-        verdict = accept_decided(mV, __fdividef(prod.hi, omr + prod.hi), q_f);
-    }
-    if (verdict < 0) {
-      if (fast_q) fallbacks += 1;
-      if (!have_qc) qc = q64(g);
-      const double p = uecm ? prob_uecm(xi, g.as[j], yi * g.ys[j]) : prob_ubcm(xi, g.xs[j]);
-      verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
-    }
-    accepted = verdict != 0;
-    set_q(j, prod, tab);
-    pos = j;
     return true;
   }
 };
 
-__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
+template <bool kUecm>
+__global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) {
   extern __shared__ unsigned char smem_raw[];
   LnEntry* tab = reinterpret_cast<LnEntry*>(smem_raw);
   int32_t* slots = reinterpret_cast<int32_t*>(smem_raw + sizeof(LnEntry) * kLnTable);
@@ -188,11 +195,17 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
   const int warp = threadIdx.x >> 5;
   int32_t* my_slot = slots + (warp * 32 + lane) * kSlotStride;
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
+  const bool init_prev = (g.flags & MH_INIT_PREV) != 0;
   const unsigned long long cap = static_cast<unsigned long long>(P.c.staging_cap);
+  const uint32_t key0 = P.c.key0, key1 = P.c.key1;
 
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   const unsigned long long total = static_cast<unsigned long long>(S) * P.c.chunk_samples;
+  // work items per ticket: about 1/8 of an even share, within [32, 1024]
+  const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * kWalkWarps;
+  unsigned long long chunk = total / (warps * 8ull);
+  chunk = chunk < 32ull ? 32ull : (chunk > 1024ull ? 1024ull : chunk);
   const unsigned lt = lanemask_lt();
 
   SegWalker wk;
@@ -201,7 +214,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
   unsigned cnt = 0;              // edges of the current pass
   unsigned long long rbase = 0;  // staging base of a second pass
   long long item = 0;
-  unsigned long long next = 0, end = 0;  // warp-uniform chunk cursor
+  unsigned long long next = 0, end = 0;     // warp-uniform work cursor
+  unsigned long long wbase = 0, wleft = 0;  // warp-uniform staging chunk
   bool work_left = total > 0;
   unsigned long long n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0;
 
@@ -211,20 +225,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
       while (idle && work_left) {
         if (next >= end) {
           unsigned long long t0 = 0;
-          if (lane == 0) t0 = atomicAdd(&ctrl->ticket, static_cast<unsigned long long>(kWalkChunk));
+          if (lane == 0) t0 = atomicAdd(&ctrl->ticket, chunk);
           t0 = __shfl_sync(0xffffffffu, t0, 0);
           if (t0 >= total) {
             work_left = false;
             break;
           }
           next = t0;
-          end = t0 + kWalkChunk < total ? t0 + kWalkChunk : total;
+          end = t0 + chunk < total ? t0 + chunk : total;
         }
         const unsigned long long avail = end - next;
         const unsigned rank = __popc(idle & lt);
         if (!active && rank < avail) {
           item = static_cast<long long>(next + rank);
-          wk.init(g, item, S, P.c.sample0, tab);
+          wk.begin(g, item, S, P.c.sample0, kUecm);
           active = true;
           rewalk = false;
           cnt = 0;
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
     if (active) {
       bool acc;
       int32_t j;
-      if (wk.step(g, P.c.key0, P.c.key1, fp64_only, tab, n_fallback, acc, j)) {
+      if (wk.advance<kUecm>(g, key0, key1, fp64_only, init_prev, tab, n_fallback, acc, j)) {
         if (acc) {
           if (!rewalk) {
             if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
           if (rbase + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
           P.c.item_cnt[item] = cnt;
           P.c.item_base[item] = static_cast<long long>(rbase);
-          wk.init(g, item, S, P.c.sample0, tab);
+          wk.begin(g, item, S, P.c.sample0, kUecm);
           rewalk = true;
           cnt = 0;
         }
@@ -272,18 +286,37 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkParams P) {
 
     const unsigned ended_mask = __ballot_sync(0xffffffffu, ended);
     if (ended_mask) {
+      // Place the ended lanes' runs in the warp's staging chunk, in lane
+      // order; lanes that do not fit go to a fresh chunk (a run never spans
+      // two chunks, so each segment stays contiguous).
       const unsigned long long need = ended ? cnt : 0;
-      unsigned long long incl = need;  // warp-inclusive prefix of the staging need
+      unsigned long long incl = need;
 #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
         const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, dd);
         if (lane >= dd) incl += o;
       }
-      const unsigned long long warp_need = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned long long base0 = 0;
-      if (lane == 0 && warp_need) base0 = atomicAdd(&ctrl->stage_used, warp_need);
-      base0 = __shfl_sync(0xffffffffu, base0, 0);
-      const unsigned long long my_base = base0 + incl - need;
+      const unsigned long long excl = incl - need;
+      const bool fits = incl <= wleft;
+      const unsigned spill_mask = __ballot_sync(0xffffffffu, ended && !fits);
+      unsigned long long my_base = wbase + excl;
+      if (spill_mask) {
+        const int first = __ffs(spill_mask) - 1;  // lanes from `first` on move to the new chunk
+        const unsigned long long moved_excl = __shfl_sync(0xffffffffu, excl, first);
+        const unsigned long long warp_need = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned long long rest = warp_need - moved_excl;
+        const unsigned long long want = rest > static_cast<unsigned long long>(kStageChunk) ? rest : kStageChunk;
+        unsigned long long nb = 0;
+        if (lane == 0) nb = atomicAdd(&ctrl->stage_used, want);
+        nb = __shfl_sync(0xffffffffu, nb, 0);
+        if (lane >= first) my_base = nb + (excl - moved_excl);
+        wbase = nb + rest;
+        wleft = want - rest;
+      } else {
+        const unsigned long long warp_need = __shfl_sync(0xffffffffu, incl, 31);
+        wbase += warp_need;
+        wleft -= warp_need;
+      }
       if (ended) {
         P.c.item_cnt[item] = cnt;
         P.c.item_base[item] = static_cast<long long>(my_base);
@@ -331,20 +364,24 @@ cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream
   WalkParams P{g, c, ctrl};
   const int threads = kWalkWarps * 32;
   const size_t smem = walk_smem_bytes();
-  static int per_sm_cache[64] = {0};
+  const bool uecm = g.model == MH_UECM;
+  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
+  static int per_sm_cache[64][2] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+  int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev][uecm] : 0;
   if (per_sm == 0) {
-    e = cudaFuncSetAttribute(walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    if (dev >= 0 && dev < 64) per_sm_cache[dev][uecm] = per_sm;
   }
-  walk_kernel<<<static_cast<unsigned>(sm_count() * per_sm), threads, smem, s>>>(P);
+  int blocks = sm_count() * per_sm;
+  if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
+  kernel<<<static_cast<unsigned>(blocks), threads, smem, s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -179,14 +179,18 @@ __device__ __forceinline__ df2 log1p_df(df2 v, const LnEntry* tab) {
   return df_add(eln2, lf);
 }
 
+// Exact u32 -> f32 conversion for values below 2^24 (a 32-bit convert; the
+// 64-bit integer converts run on the FP64 unit).
+__device__ __forceinline__ float u32f(unsigned v) { return __uint2float_rn(v); }
+
 // E = -ln U for U = N 2^-53, N = 1 .. 2^53 (exact integer input).
 __device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* tab) {
   const unsigned long long W = (1ull << 53) - N;  // (1 - U) 2^53, exact
   if (W < (1ull << 44)) {
     // -ln(1 - w) = w + w^2/2 + w^3/3 + w^4/4 + w^5/5 (truncation < w^6/6), w < 2^-9
-    const float wh0 = static_cast<float>(W);
-    const float wl0 = static_cast<float>(static_cast<long long>(W) - static_cast<long long>(wh0));
-    const df2 w = fast_two_sum(wh0 * 0x1p-53f, wl0 * 0x1p-53f);
+    const float wh0 = u32f(static_cast<unsigned>(W >> 20)) * 0x1p-33f;          // exact (24 bits)
+    const float wl0 = u32f(static_cast<unsigned>(W & 0xFFFFFu)) * 0x1p-53f;    // exact (20 bits)
+    const df2 w = fast_two_sum(wh0, wl0);
     const float wh = w.hi;
     const float w2h = wh * wh;
     const float w2l = fmaf(wh, wh, -w2h) + 2.0f * wh * w.lo;
@@ -194,11 +198,13 @@ __device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* t
     df2 s = df_add(w, df2{0.5f * w2h, 0.5f * w2l});
     return df_add_f(s, tail);
   }
-  // N = 2^(e) f, f in [0.75, 1.5); E = (53 - e) ln 2 - ln f
+  // N = 2^e f, f in [0.75, 1.5); E = (53 - e) ln 2 - ln f
   const int lz = __clzll(static_cast<long long>(N));
-  const unsigned long long Nn = N << lz;                      // leading one at bit 63
-  const float h = static_cast<float>(Nn >> 40) * 0x1p-23f;    // top 24 bits, in [1, 2)
-  const float l = static_cast<float>(Nn & ((1ull << 40) - 1)) * 0x1p-63f;
+  const unsigned long long Nn = N << lz;  // leading one at bit 63
+  const unsigned top = static_cast<unsigned>(Nn >> 40);                 // 24 bits
+  const unsigned mid = static_cast<unsigned>(Nn >> 16) & 0xFFFFFFu;     // next 24 bits
+  const float h = u32f(top) * 0x1p-23f;                                  // in [1, 2), exact
+  const float l = u32f(mid) * 0x1p-47f;                                  // exact; bits below 2^-47 dropped
   int e = 63 - lz;
   df2 f = fast_two_sum(h, l);
   if (f.hi >= 1.5f) {
@@ -212,25 +218,26 @@ __device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* t
   return df_add(mln2, df2{-lf.hi, -lf.lo});
 }
 
-// Exact decision of floor(t) for a double-float t >= 0 against `room`:
-// returns 1 and sets `fl` when decided, 0 when t is within the error margin
-// of an integer.  fl >= room means the candidate is past the segment end.
-__device__ __forceinline__ int floor_decided(df2 t, int64_t room, int64_t& fl) {
-  if (t.hi > static_cast<float>(room) * 1.0001f + 2.0f) {  // far past the end
-    fl = room;
+// Exact decision of floor(t) for a double-float t >= 0 against `room`
+// (0 <= room < 2^31): returns 1 and sets `fl` when decided, 0 when t lies
+// within the error margin of an integer.  fl >= room: past the segment end.
+__device__ __forceinline__ int floor_decided(df2 t, int room, unsigned& fl) {
+  const float froom = static_cast<float>(room);
+  if (t.hi > fmaf(froom, 0x1p-20f, froom) + 2.0f) {  // far past the end
+    fl = static_cast<unsigned>(room);
     return 1;
   }
   const float margin = fmaf(t.hi, 0x1p-36f, 0x1p-40f);
   const float fh = floorf(t.hi);
   float f0, f1;
-  int64_t F;
+  unsigned F;
   if (fh == t.hi) {
     const float fl_lo = floorf(t.lo);
-    F = static_cast<int64_t>(fh) + static_cast<int64_t>(fl_lo);
+    F = __float2uint_rz(fh) + static_cast<unsigned>(__float2int_rz(fl_lo));
     f0 = t.lo - fl_lo;
     f1 = 1.0f - f0;
   } else {
-    F = static_cast<int64_t>(fh);
+    F = __float2uint_rz(fh);
     const float d = t.hi - fh;  // exact
     f0 = d + t.lo;
     f1 = (1.0f - d) - t.lo;
@@ -241,12 +248,12 @@ __device__ __forceinline__ int floor_decided(df2 t, int64_t room, int64_t& fl) {
 }
 
 // Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.
-static __device__ __noinline__ int64_t skip_fp64(unsigned long long N, double q, int64_t room) {
+static __device__ __noinline__ unsigned skip_fp64(unsigned long long N, double q, int room) {
   if (q >= 1.0) return 0;
   const double U = static_cast<double>(N) * 0x1p-53;
   const double t = log(U) / log1p(-q);
-  if (t >= static_cast<double>(room)) return room;
-  return static_cast<int64_t>(floor(t));
+  if (t >= static_cast<double>(room)) return static_cast<unsigned>(room);
+  return static_cast<unsigned>(floor(t));
 }
 
 // Acceptance filter: 1 = accept, 0 = reject, -1 = undecided (use FP64).
@@ -285,8 +292,8 @@ __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t 
   if (!fp64_only && nlr.hi < -0x1p-12f && nlr.hi > -0x1p+100f) {
     const df2 E = neg_ln_u53(N, tab);
     const df2 t = df_div(E, df2{-nlr.hi, -nlr.lo});
-    int64_t fl;
-    if (t.hi < 2.0e9f && floor_decided(t, 0x7FFFFFFFll, fl)) return 1 + static_cast<int32_t>(fl);
+    unsigned fl;
+    if (t.hi < 2.0e9f && floor_decided(t, 0x7FFFFFFF, fl)) return 1 + static_cast<int32_t>(fl);
   }
   fallbacks += 1;
   return weight_fp64(N, yi * yj, overflow);
