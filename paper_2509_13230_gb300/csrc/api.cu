@@ -28,10 +28,7 @@ struct CallTimer {
   bool ready = false;
   int used = 0;
   bool on = false;
-  cudaError_t start(bool enable, cudaStream_t s) {
-    on = enable;
-    used = 0;
-    if (!on) return cudaSuccess;
+  cudaError_t create() {  // outside any capture
     if (!ready) {
       for (int t = 0; t < kMax; ++t) {
         cudaError_t e = cudaEventCreate(&ev[t]);
@@ -39,10 +36,23 @@ struct CallTimer {
       }
       ready = true;
     }
+    return cudaSuccess;
+  }
+  cudaError_t start(bool enable, cudaStream_t s) {
+    on = enable;
+    used = 0;
+    if (!on) return cudaSuccess;
+    cudaError_t e = create();
+    if (e != cudaSuccess) return e;
     return mark(s);
   }
   cudaError_t mark(cudaStream_t s) {
     if (!on || used >= kMax) return cudaSuccess;
+    // inside a capture the record must become a graph node of its own
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &st);
+    if (e != cudaSuccess) return e;
+    if (st == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev[used++], s, cudaEventRecordExternal);
     return cudaEventRecord(ev[used++], s);
   }
   float between(int a, int b) const {
@@ -230,6 +240,10 @@ static int check_params(int model, int64_t n, const mh_params* p) {
     set_error("max_segments must be 0 or >= n - 1");
     return MH_ERR_ARG;
   }
+  if (p->max_segments >= (1ll << 31) || (p->max_segments == 0 && default_max_segments(n) >= (1ll << 31))) {
+    set_error("the segment table would exceed 2^31 rows");
+    return MH_ERR_ARG;
+  }
   return MH_OK;
 }
 
@@ -281,6 +295,102 @@ static int status_to_code(unsigned status, long long num_segments, int64_t max_s
   return MH_OK;
 }
 
+// Everything a sampling call enqueues: prepare, then walk + emit per sample
+// chunk, then the read-back of the control block and the per-sample counts
+// into the pinned buffer `hbuf`.
+static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_params* p, const Outputs& o,
+                          bool timed, char* hbuf, cudaStream_t s) {
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  MH_CUDA(g_timer.start(timed, s));
+  int rc = prepare(g, L, ws, ctrl, s);
+  if (rc != MH_OK) return rc;
+  MH_CUDA(g_timer.mark(s));
+
+  Outputs out = o;
+  if (!(p->flags & MH_OUT_COO)) out.src = out.dst = out.w = nullptr;
+  if (!(p->flags & MH_OUT_CSR)) out.csr_off = nullptr, out.csr_idx = nullptr, out.csr_w = nullptr;
+  if (g.model == MH_UBCM) out.w = out.csr_w = nullptr;
+
+  ChunkArgs c;
+  c.key0 = static_cast<uint32_t>(p->seed);
+  c.key1 = static_cast<uint32_t>(p->seed >> 32) + p->network_id;
+  c.item_cnt = reinterpret_cast<long long*>(ws + L.item_cnt);
+  c.item_base = reinterpret_cast<long long*>(ws + L.item_base);
+  c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
+  c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
+  c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
+  c.scan_tmp = ws + L.scan_tmp;
+  c.staging_cap = L.staging_entries;
+  c.items_max = L.items_max;
+  for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
+    const int64_t left = static_cast<int64_t>(p->num_samples) - first;
+    c.chunk_first = first;
+    c.chunk_samples = left < L.spc ? left : L.spc;
+    c.sample0 = p->sample_begin + static_cast<uint32_t>(first);
+    MH_CUDA(cudaMemsetAsync(&ctrl->ticket, 0, 3 * sizeof(unsigned long long), s));
+    MH_CUDA(g_timer.mark(s));
+    MH_CUDA(launch_walk(g, c, ctrl, s));
+    MH_CUDA(g_timer.mark(s));
+    MH_CUDA(launch_emit(g, c, out, ctrl, s));
+    MH_CUDA(g_timer.mark(s));
+  }
+  const size_t counts_bytes = 8 * static_cast<size_t>(p->num_samples);
+  MH_CUDA(cudaMemcpyAsync(hbuf, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  MH_CUDA(cudaMemcpyAsync(hbuf + sizeof(Ctrl), c.sample_counts, counts_bytes, cudaMemcpyDeviceToHost, s));
+  return MH_OK;
+}
+
+// ---- graph cache --------------------------------------------------------------
+// A call's kernel sequence depends only on its arguments, so it is captured
+// once into a CUDA graph (on a library-owned stream: the legacy default
+// stream cannot be captured) and replayed on the caller's stream.
+struct CallKey {
+  int model, device;
+  int64_t n, capacity;
+  const void *x, *y, *ws, *src, *dst, *w, *csr_off, *csr_idx, *csr_w, *hbuf;
+  size_t ws_bytes;
+  mh_params params;
+};
+struct CachedGraph {
+  CallKey key;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0, chunks = 0, timer_marks = 0;
+  uint64_t last_use = 0;
+};
+constexpr int kGraphCache = 8;
+struct GraphCache {
+  CachedGraph entries[kGraphCache];
+  uint64_t clock = 0;
+  cudaStream_t capture_stream[64] = {};
+  ~GraphCache() { clear(); }
+  void clear() {
+    for (auto& e : entries)
+      if (e.exec) {
+        cudaGraphExecDestroy(e.exec);
+        e.exec = nullptr;
+      }
+  }
+  CachedGraph* find(const CallKey& k) {
+    for (auto& e : entries)
+      if (e.exec && memcmp(&e.key, &k, sizeof(CallKey)) == 0) {
+        e.last_use = ++clock;
+        return &e;
+      }
+    return nullptr;
+  }
+  CachedGraph* slot() {
+    CachedGraph* v = &entries[0];
+    for (auto& e : entries) {
+      if (!e.exec) return &e;
+      if (e.last_use < v->last_use) v = &e;
+    }
+    cudaGraphExecDestroy(v->exec);
+    v->exec = nullptr;
+    return v;
+  }
+};
+thread_local GraphCache g_graphs;
+
 static int run_sample(int model, const double* x, const double* y, int64_t n, const mh_params* p, void* workspace,
                       size_t workspace_bytes, const Outputs& o, int64_t* h_counts, uint64_t* h_stats,
                       cudaStream_t s) {
@@ -307,55 +417,90 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     set_error("workspace needs %zu bytes, got %zu", L.total, workspace_bytes);
     return MH_ERR_WORKSPACE;
   }
-  char* ws = static_cast<char*>(workspace);
-  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
-  const Net g = make_net(model, *p, x, y, n, L, ws);
-  g_launches = 0;
-  g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
-  const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= 64;
-  MH_CUDA(g_timer.start(timed, s));
-  rc = prepare(g, L, ws, ctrl, s);
-  if (rc != MH_OK) return rc;
-  MH_CUDA(g_timer.mark(s));
-
-  Outputs out = o;
-  if (!(p->flags & MH_OUT_COO)) out.src = out.dst = out.w = nullptr;
-  if (!(p->flags & MH_OUT_CSR)) out.csr_off = nullptr, out.csr_idx = nullptr, out.csr_w = nullptr;
-  if (model == MH_UBCM) out.w = out.csr_w = nullptr;
-
-  ChunkArgs c;
-  c.key0 = static_cast<uint32_t>(p->seed);
-  c.key1 = static_cast<uint32_t>(p->seed >> 32) + p->network_id;
-  c.item_cnt = reinterpret_cast<long long*>(ws + L.item_cnt);
-  c.item_base = reinterpret_cast<long long*>(ws + L.item_base);
-  c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
-  c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
-  c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
-  c.scan_tmp = ws + L.scan_tmp;
-  c.staging_cap = L.staging_entries;
-  c.items_max = L.items_max;
-  for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
-    const int64_t left = static_cast<int64_t>(p->num_samples) - first;
-    c.chunk_first = first;
-    c.chunk_samples = left < L.spc ? left : L.spc;
-    c.sample0 = p->sample_begin + static_cast<uint32_t>(first);
-    MH_CUDA(cudaMemsetAsync(&ctrl->ticket, 0, 3 * sizeof(unsigned long long), s));
-    MH_CUDA(g_timer.mark(s));
-    MH_CUDA(launch_walk(g, c, ctrl, s));
-    MH_CUDA(g_timer.mark(s));
-    MH_CUDA(launch_emit(g, c, out, ctrl, s));
-    MH_CUDA(g_timer.mark(s));
-    g_info.walk_launches += 1;
-    g_info.sample_chunks += 1;
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  MH_CUDA(cudaStreamIsCapturing(s, &cap_status));
+  if (cap_status != cudaStreamCaptureStatusNone) {
+    set_error("sampling calls read results back and cannot be captured into a caller's graph");
+    return MH_ERR_ARG;
   }
-
+  char* ws = static_cast<char*>(workspace);
+  const Net g = make_net(model, *p, x, y, n, L, ws);
+  const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= 64;
   const size_t counts_bytes = 8 * static_cast<size_t>(p->num_samples);
-  MH_CUDA(g_pinned.reserve(sizeof(Ctrl) + counts_bytes));
+  if (g_pinned.bytes < sizeof(Ctrl) + counts_bytes) {
+    g_graphs.clear();  // cached graphs copy into the old buffer
+    MH_CUDA(g_pinned.reserve(sizeof(Ctrl) + counts_bytes));
+  }
   char* hbuf = static_cast<char*>(g_pinned.ptr);
-  MH_CUDA(cudaMemcpyAsync(hbuf, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-  MH_CUDA(cudaMemcpyAsync(hbuf + sizeof(Ctrl), c.sample_counts, counts_bytes, cudaMemcpyDeviceToHost, s));
+  MH_CUDA(prepare_kernel_attributes(model));
+  if (timed) MH_CUDA(g_timer.create());
+
+  int dev = 0;
+  MH_CUDA(cudaGetDevice(&dev));
+  CallKey key;
+  memset(&key, 0, sizeof(key));
+  key.model = model;
+  key.device = dev;
+  key.n = n;
+  key.capacity = o.capacity;
+  key.x = x;
+  key.y = y;
+  key.ws = workspace;
+  key.src = o.src;
+  key.dst = o.dst;
+  key.w = o.w;
+  key.csr_off = o.csr_off;
+  key.csr_idx = o.csr_idx;
+  key.csr_w = o.csr_w;
+  key.hbuf = hbuf;
+  key.ws_bytes = workspace_bytes;
+  key.params = *p;
+
+  g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+  CachedGraph* cg = g_graphs.find(key);
+  if (!cg && dev >= 0 && dev < 64) {
+    cudaStream_t& cs = g_graphs.capture_stream[dev];
+    if (!cs) MH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    g_launches = 0;
+    cudaGraph_t graph = nullptr;
+    MH_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, cs);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (rc != MH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec == cudaSuccess && graph) {
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei == cudaSuccess) {
+        cg = g_graphs.slot();
+        cg->key = key;
+        cg->exec = exec;
+        cg->launches = g_launches;
+        cg->chunks = (p->num_samples + L.spc - 1) / L.spc;
+        cg->timer_marks = g_timer.used;
+        cg->last_use = ++g_graphs.clock;
+      }
+    }
+    cudaGetLastError();  // a failed capture falls back to direct launches below
+  }
+  if (cg) {
+    MH_CUDA(cudaGraphLaunch(cg->exec, s));
+    g_timer.on = timed;
+    g_timer.used = static_cast<int>(cg->timer_marks);
+    g_info.kernel_launches = cg->launches;
+    g_info.sample_chunks = cg->chunks;
+  } else {
+    g_launches = 0;
+    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, s);
+    if (rc != MH_OK) return rc;
+    g_info.kernel_launches = g_launches;
+    g_info.sample_chunks = (p->num_samples + L.spc - 1) / L.spc;
+  }
+  g_info.walk_launches = g_info.sample_chunks;
   MH_CUDA(cudaStreamSynchronize(s));
-  g_info.kernel_launches = g_launches;
   if (timed) {
     g_info.prepare_ms = g_timer.between(0, 1);
     for (int64_t t = 0; t < g_info.sample_chunks; ++t) {

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     }
     const long long item = it0 + lo;
     const long long e = pos - off[lo];
-    const long long s_local = item / S;
+    const long long s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);  // items < 2^31
     const long long seg = item - s_local * S;
     const int4 sg = g.seg[seg];
     const int32_t i = sg.x;

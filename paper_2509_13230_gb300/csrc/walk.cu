@@ -71,8 +71,9 @@ struct SegWalker {
 
   // Loads the segment of `item`; its head is set up by the next advance().
   __device__ __forceinline__ void begin(const Net& g, long long item, long long S, uint32_t sample0, bool uecm) {
-    const long long s_local = item / S;
-    const long long seg = item - s_local * S;
+    // item < 2^31 (the workspace layout bounds the items of a chunk)
+    const unsigned s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);
+    const unsigned seg = static_cast<unsigned>(item) - s_local * static_cast<unsigned>(S);
     const int4 e = g.seg[seg];
     i = e.x;
     k = e.y;
@@ -360,28 +361,40 @@ size_t walk_smem_bytes() {
   return sizeof(LnEntry) * kLnTable + static_cast<size_t>(kWalkWarps) * 32 * kSlotStride * sizeof(int32_t);
 }
 
-cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
-  WalkParams P{g, c, ctrl};
-  const int threads = kWalkWarps * 32;
-  const size_t smem = walk_smem_bytes();
-  const bool uecm = g.model == MH_UECM;
-  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
-  static int per_sm_cache[64][2] = {};
+// Shared-memory opt-in and occupancy of the walk kernel, per device (done
+// before a call is captured into a graph).
+static int g_per_sm[64][2] = {};
+
+cudaError_t prepare_kernel_attributes(int model) {
+  const bool uecm = model == MH_UECM;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev][uecm] : 0;
-  if (per_sm == 0) {
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (dev >= 0 && dev < 64) per_sm_cache[dev][uecm] = per_sm;
-  }
-  int blocks = sm_count() * per_sm;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (g_per_sm[dev][uecm]) return cudaSuccess;
+  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
+  const size_t smem = walk_smem_bytes();
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  g_per_sm[dev][uecm] = per_sm < 1 ? 1 : per_sm;
+  return cudaSuccess;
+}
+
+cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
+  WalkParams P{g, c, ctrl};
+  const bool uecm = g.model == MH_UECM;
+  cudaError_t e = prepare_kernel_attributes(g.model);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
+  int blocks = sm_count() * g_per_sm[dev][uecm];
   if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
-  kernel<<<static_cast<unsigned>(blocks), threads, smem, s>>>(P);
+  kernel<<<static_cast<unsigned>(blocks), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

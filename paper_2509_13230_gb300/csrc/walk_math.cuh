@@ -81,6 +81,14 @@ __device__ __forceinline__ df2 df_add(df2 a, df2 b) {
   const df2 v = fast_two_sum(s.hi, s.lo + t.hi);
   return fast_two_sum(v.hi, t.lo + v.lo);
 }
+// Sum without the second error-free transformation on the low parts
+// (Joldes et al.'s "sloppy" addition).  Used only where the operands cannot
+// cancel by more than a small factor (same signs, or a bounded ratio),
+// where its error stays a few units of 2^-48 of the result.
+__device__ __forceinline__ df2 df_add_sloppy(df2 a, df2 b) {
+  const df2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
 __device__ __forceinline__ df2 df_add_f(df2 a, float b) {
   const df2 s = two_sum(a.hi, b);
   return fast_two_sum(s.hi, a.lo + s.lo);
@@ -145,9 +153,9 @@ __device__ __forceinline__ df2 ln_mid(df2 f, const LnEntry* tab) {
   const float r2l = fmaf(rh, rh, -r2h) + 2.0f * rh * r.lo;
   const float tail = rh * r2h * fmaf(rh, fmaf(rh, 0.2f, -0.25f), 0.333333343f);
   const df2 half_r2 = df2{-0.5f * r2h, -0.5f * r2l};
-  df2 s = df_add(r, half_r2);
+  df2 s = df_add_sloppy(r, half_r2);           // |r^2/2| < 2^-10 |r|
   s = df_add_f(s, tail);
-  return df_add(df2{e.ln_hi, e.ln_lo}, s);
+  return df_add_sloppy(df2{e.ln_hi, e.ln_lo}, s);  // cancels at most about 2x (see neg_ln_u53)
 }
 
 // Splits a double-float v >= 2^-100 into 2^e * f with f in [0.75, 1.5).
@@ -167,7 +175,7 @@ __device__ __forceinline__ df2 log1p_df(df2 v, const LnEntry* tab) {
     const float v2h = vh * vh;
     const float v2l = fmaf(vh, vh, -v2h) + 2.0f * vh * v.lo;
     const float tail = vh * v2h * fmaf(vh, fmaf(vh, 0.2f, -0.25f), 0.333333343f);
-    df2 s = df_add(v, df2{-0.5f * v2h, -0.5f * v2l});
+    df2 s = df_add_sloppy(v, df2{-0.5f * v2h, -0.5f * v2l});
     return df_add_f(s, tail);
   }
   int e;
@@ -176,7 +184,7 @@ __device__ __forceinline__ df2 log1p_df(df2 v, const LnEntry* tab) {
   if (e == 0) return lf;
   const float ef = static_cast<float>(e);
   const df2 eln2 = df_mul_f(df2{kLn2Hi, kLn2Lo}, ef);
-  return df_add(eln2, lf);
+  return df_add_sloppy(eln2, lf);  // e >= 1: |ln f| < 0.41 < e ln 2
 }
 
 // Exact u32 -> f32 conversion for values below 2^24 (a 32-bit convert; the
@@ -195,7 +203,7 @@ __device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* t
     const float w2h = wh * wh;
     const float w2l = fmaf(wh, wh, -w2h) + 2.0f * wh * w.lo;
     const float tail = wh * w2h * fmaf(wh, fmaf(wh, 0.2f, 0.25f), 0.333333343f);
-    df2 s = df_add(w, df2{0.5f * w2h, 0.5f * w2l});
+    df2 s = df_add_sloppy(w, df2{0.5f * w2h, 0.5f * w2l});
     return df_add_f(s, tail);
   }
   // N = 2^e f, f in [0.75, 1.5); E = (53 - e) ln 2 - ln f
@@ -215,7 +223,7 @@ __device__ __forceinline__ df2 neg_ln_u53(unsigned long long N, const LnEntry* t
   const int m = 53 - e;
   if (m == 0) return df2{-lf.hi, -lf.lo};
   const df2 mln2 = df_mul_f(df2{kLn2Hi, kLn2Lo}, static_cast<float>(m));
-  return df_add(mln2, df2{-lf.hi, -lf.lo});
+  return df_add_sloppy(mln2, df2{-lf.hi, -lf.lo});  // m >= 1, ln f < 0.41: cancels at most 2.4x
 }
 
 // Exact decision of floor(t) for a double-float t >= 0 against `room`
