@@ -46,24 +46,30 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // One segment's walk state.  A lane's iteration is either the head of a new
 // segment (q <- p at the head, no draw consumed) or one candidate; both run
-// the same expensive code (Philox and -ln U of the next draw, the product
-// x_i x_j, log1p for the next q), so a warp whose lanes start segments at
-// different times stays converged.  The draw of the next iteration is
-// computed one iteration ahead: it does not depend on the decisions taken in
-// this one, so the two dependency chains overlap.
+// the same code for the next draw (Philox, -ln U), the product x_i x_j and
+// the next q, so a warp whose lanes start segments at different times stays
+// converged.  The next draw is computed one iteration ahead: it does not
+// depend on this iteration's decisions, so the dependency chains overlap.
+//
+// Decisions go through three levels: FP32 estimates (walk_math.cuh) decide
+// almost every draw; draws within the FP32 margin of a boundary recompute t
+// in double-float from the kept product; draws within that margin, or with q
+// outside the fast range, use the canonical FP64 expressions.
 struct SegWalker {
   int32_t i, k, a, b, pos, qj;  // qj: the rank whose p (or phat) is the current q
   uint32_t sample, d;           // d: index of the next draw
   bool fresh;                   // the head of the segment is still to be set up
-  bool fast;                    // q lies inside the double-float path's range
+  bool fast;                    // q lies inside the fast levels' range
+  bool e_ok;                    // Ef is valid
   double xi;                    // canonical x_i (UBCM) or a_i (UECM)
   double yi, c;                 // UECM: y_i and the bound constant exp(-beta_min)
   df2 xi_df, yi_df, inv1mc;     // double-float copies; inv1mc = 1 / (1 - c)
   float omc_f;                  // 1 - c in FP32
-  df2 lam;                      // -ln(1 - q)
+  df2 zq;                       // -ln(1 - q) = log1p(zq): zq = x_i x_j (UBCM) or A / (1 - c) (UECM)
+  float lam_f;                  // log1p(zq) in FP32
   float q_f;                    // q in FP32
   uint4 rnd;                    // Philox words of draw d
-  df2 E;                        // -ln U of draw d
+  float Ef;                     // -ln U of draw d in FP32
 
   __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
     return uecm ? prob_hat(xi, g.as[qj], c) : prob_ubcm(xi, g.xs[qj]);
@@ -80,7 +86,7 @@ struct SegWalker {
     a = e.z;
     b = e.w;
     pos = a - 1;
-    sample = sample0 + static_cast<uint32_t>(s_local);
+    sample = sample0 + s_local;
     d = 0;
     fresh = true;
     if (!uecm) {
@@ -115,20 +121,24 @@ struct SegWalker {
       if (!(qc > 0.0)) return false;
     }
     const uint4 r = rnd;
-    df2 t = df2{0.0f, 0.0f};
-    if (fast_q) t = df_div(E, lam);
+    const float t1 = __fdividef(Ef, lam_f);
+    const bool e1 = e_ok;
     if (!head) d += 1;
     // Philox words and -ln U of the next draw (draw 0 on a head step)
     rnd = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0, key1);
-    E = neg_ln_u53(top53(rnd.y, rnd.x) + 1ull, tab);
+    Ef = neg_ln_u53_f(top53(rnd.y, rnd.x) + 1ull, tab, e_ok);
     if (head) {
       fresh = false;
       j = init_prev ? a - 1 : a;
     } else {
       const int room = b - pos - 1;
       unsigned skip = 0;
-      const bool decided = fast_q && floor_decided(t, room, skip);
-      if (!decided) {
+      bool decided = fast_q && e1 && floor_decided_f(t1, room, skip);
+      if (!decided && fast_q) {  // double-float level
+        const df2 t = df_div(neg_ln_u53(top53(r.y, r.x) + 1ull, tab), log1p_df(zq, tab));
+        decided = floor_decided(t, room, skip) != 0;
+      }
+      if (!decided) {  // canonical FP64
         if (fast_q) fallbacks += 1;
         if (!have_qc) {
           qc = q64(g, kUecm);
@@ -165,19 +175,15 @@ struct SegWalker {
     // q <- p (UBCM) or phat (UECM) of j
     qj = j;
     if (!kUecm) {
+      zq = prod;
       fast = prod.hi > 0x1p-100f && prod.hi < 0x1p40f;
-      if (fast) {
-        lam = log1p_df(prod, tab);
-        q_f = __fdividef(prod.hi, 1.0f + prod.hi);
-      }
+      q_f = __fdividef(prod.hi, 1.0f + prod.hi);
     } else {
-      const df2 gq = df_mul(prod, inv1mc);
-      fast = gq.hi > 0x1p-100f && gq.hi < 0x1p40f && omc_f >= 0x1p-20f;
-      if (fast) {
-        lam = log1p_df(gq, tab);
-        q_f = __fdividef(prod.hi, omc_f + prod.hi);
-      }
+      zq = df_mul(prod, inv1mc);
+      fast = zq.hi > 0x1p-100f && zq.hi < 0x1p40f && omc_f >= 0x1p-20f;
+      q_f = __fdividef(prod.hi, omc_f + prod.hi);
     }
+    lam_f = fast ? log1p_f(zq, tab) : 1.0f;
     return true;
   }
 };

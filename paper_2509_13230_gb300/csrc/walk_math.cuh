@@ -255,6 +255,84 @@ __device__ __forceinline__ int floor_decided(df2 t, int room, unsigned& fl) {
   return 1;
 }
 
+// ---- FP32 first level ------------------------------------------------------------
+// The same table, used in FP32: ln f = ln c_k + log1p(r) with r rounded once
+// and a cubic in r.  These estimates have a relative error of a few 2^-24;
+// a decision is taken from them only when it is 2^-18 t away from a boundary.
+
+// float(v) for v < 2^23, exact, without a convert instruction.
+__device__ __forceinline__ float small_u2f(unsigned v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
+
+__device__ __forceinline__ float log1p_poly_f(float r) {  // r - r^2/2 + r^3/3, |r| < 2^-9
+  return r * fmaf(r, fmaf(r, 0.333333343f, -0.5f), 1.0f);
+}
+
+// ln f for f in [0.75, 1.5).
+__device__ __forceinline__ float ln_mid_f(float f, const LnEntry* tab) {
+  const unsigned bits = __float_as_uint(f);
+  const int k = static_cast<int>((bits >> 14) & 511u);
+  const float c = __uint_as_float(bits & ~0x3FFFu);
+  const LnEntry e = tab[k];
+  return e.ln_hi + log1p_poly_f((f - c) * e.inv_hi);
+}
+
+// -ln U for U = N 2^-53.  Sets ok = false for U < 2^-8 (about 2^-8 of the
+// draws), which the double-float level then handles.
+__device__ __forceinline__ float neg_ln_u53_f(unsigned long long N, const LnEntry* tab, bool& ok) {
+  const unsigned long long W = (1ull << 53) - N;
+  ok = true;
+  if (W < (1ull << 44)) {  // U > 1 - 2^-9: -ln(1 - w) = w + w^2/2 + w^3/3 + ...
+    const float w = small_u2f(static_cast<unsigned>(W >> 22)) * 0x1p-31f +
+                    small_u2f(static_cast<unsigned>(W & 0x3FFFFFu)) * 0x1p-53f;
+    return w * fmaf(w, fmaf(w, 0.333333343f, 0.5f), 1.0f);
+  }
+  const unsigned nh = static_cast<unsigned>(N >> 21);  // top 32 bits of the 53-bit N
+  const int lz = __clz(nh);
+  if (lz > 8) {
+    ok = false;
+    return 0.0f;
+  }
+  const unsigned top = nh << lz;                // leading one at bit 31: f = top 2^-31 in [1, 2)
+  const int k = static_cast<int>((top >> 22) & 511u);
+  const bool half = top >= 0xC0000000u;         // f >= 1.5: use f / 2 and one more power of two
+  const float d = small_u2f(top & 0x3FFFFFu) * (half ? 0x1p-32f : 0x1p-31f);  // f - c_k, exact
+  const LnEntry e = tab[k];
+  const float lnf = e.ln_hi + log1p_poly_f(d * e.inv_hi);
+  const float m = static_cast<float>(1 + lz - static_cast<int>(half));  // U = 2^-m f
+  return fmaf(m, kLn2Lo, fmaf(m, kLn2Hi, -lnf));
+}
+
+// log1p(v) for v.hi in [2^-100, 2^40).
+__device__ __forceinline__ float log1p_f(df2 v, const LnEntry* tab) {
+  if (v.hi < 0x1p-9f) return log1p_poly_f(v.hi) + v.lo;
+  const df2 D = two_sum(1.0f, v.hi);            // 1 + v.hi exactly
+  const float corr = __fdividef(D.lo + v.lo, D.hi);
+  int ex = static_cast<int>((__float_as_uint(D.hi) >> 23) & 0xFF) - 127;
+  float f = __uint_as_float((__float_as_uint(D.hi) & 0x007FFFFFu) | 0x3F800000u);
+  if (f >= 1.5f) {
+    f *= 0.5f;
+    ex += 1;
+  }
+  const float fe = static_cast<float>(ex);
+  return fmaf(fe, kLn2Lo, fmaf(fe, kLn2Hi, ln_mid_f(f, tab))) + corr;
+}
+
+// floor(t) from the FP32 estimate t ~ E / lambda: 1 and `fl` when decided.
+__device__ __forceinline__ int floor_decided_f(float t, int room, unsigned& fl) {
+  const float froom = static_cast<float>(room);
+  if (t > fmaf(froom, 0x1p-16f, froom) + 1.0f) {  // past the end of the segment
+    fl = static_cast<unsigned>(room);
+    return 1;
+  }
+  if (!(t < 0x1p23f)) return 0;
+  const float margin = fmaf(t, 0x1p-18f, 0x1p-22f);
+  const float fh = floorf(t);
+  const float fr = t - fh;  // exact
+  if (!(fr > margin) || !(1.0f - fr > margin)) return 0;
+  fl = static_cast<unsigned>(fh);
+  return 1;
+}
+
 // Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.
 static __device__ __noinline__ unsigned skip_fp64(unsigned long long N, double q, int room) {
   if (q >= 1.0) return 0;
