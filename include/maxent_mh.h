@@ -160,6 +160,31 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
 
 /*
+ * mh_sample_ubcm_noalloc — mh_sample_ubcm without a caller-supplied
+ * workspace.  The paper has no counterpart: this is an interface for callers
+ * that cannot allocate device memory while they sample, such as code that
+ * runs inside another framework's memory budget (a cudaMalloc / cudaFree
+ * here would bypass its caching allocator or synchronise the device),
+ * runtimes that allow allocation only at start-up, and plug-ins whose host
+ * forbids it.  It allocates nothing: its scratch is a fixed 64 MiB device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits, and results are read back into a static host buffer.
+ *
+ * Arguments as mh_sample_ubcm (no workspace).  Limits: the call's
+ * mh_workspace_size must fit in the 64 MiB (about n <= 50,000 with a few
+ * million edges; otherwise MH_ERR_WORKSPACE, use mh_sample_ubcm),
+ * num_samples <= 1024, no MH_TIMING.  The first call on a device looks up
+ * the scratch's device address; make it before any stream capture, and do
+ * not call it inside a capture.  Calls share the scratch: the library
+ * serialises them with a process-wide lock and each returns after its
+ * device work, so calls through this function never overlap on a GPU.
+ * Output is bit-identical to mh_sample_ubcm with the same arguments.
+ */
+int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_params* params, int32_t* src, int32_t* dst,
+                           int64_t* csr_offsets, int32_t* csr_indices, int64_t capacity_edges,
+                           int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
+
+/*
  * mh_segment_table — the node order and row-segment table a sampling call
  * with the same arguments walks (for inspection and tests).
  *   seg_row, seg_k    int32[cap]: row rank i and segment index k within row i

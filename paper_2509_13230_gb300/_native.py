@@ -43,6 +43,7 @@ EXPORTED = (
     "mh_workspace_size",
     "mh_sample_ubcm",
     "mh_sample_weighted",
+    "mh_sample_ubcm_noalloc",
     "mh_segment_table",
     "maxent_expected_fwd",
     "maxent_expected_bwd",
@@ -113,6 +114,8 @@ def load(path: str | None = None):
         lib.mh_sample_ubcm.restype = i32
         lib.mh_sample_weighted.argtypes = [vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
         lib.mh_sample_weighted.restype = i32
+        lib.mh_sample_ubcm_noalloc.argtypes = [vp, i64, P, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_ubcm_noalloc.restype = i32
         lib.mh_segment_table.argtypes = [i32, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp]
         lib.mh_segment_table.restype = i32
         lib.maxent_expected_fwd.argtypes = [i32, vp, vp, i64, vp, vp, vp]
@@ -169,6 +172,12 @@ def mh_sample_weighted(x, y, n, params, workspace, workspace_bytes, src, dst, w,
     return load().mh_sample_weighted(x, y, n, ctypes.byref(params), workspace, workspace_bytes, src, dst, w,
                                      csr_offsets, csr_indices, csr_weights, capacity_edges, h_edges_per_sample,
                                      h_stats, stream)
+
+
+def mh_sample_ubcm_noalloc(x, n, params, src, dst, csr_offsets, csr_indices, capacity_edges, h_edges_per_sample,
+                           h_stats, stream) -> int:
+    return load().mh_sample_ubcm_noalloc(x, n, ctypes.byref(params), src, dst, csr_offsets, csr_indices,
+                                         capacity_edges, h_edges_per_sample, h_stats, stream)
 
 
 def mh_segment_table(model, x, y, n, params, workspace, workspace_bytes, seg_row, seg_k, seg_a, seg_b, perm, cap,

@@ -646,3 +646,19 @@ int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, 
 }
 
 }  // extern "C"
+
+// ---- forwarders for the fixed-scratch entry point (noalloc.cu) -------------------
+namespace mh {
+int check_sample_params(int model, int64_t n, const mh_params* p) { return check_params(model, n, p); }
+Net net_view(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
+             char* ws) {
+  return make_net(model, p, x, y, n, L, ws);
+}
+int enqueue_sample_direct(const Net& g, const Layout& L, char* ws, const mh_params* p, const Outputs& o, char* hbuf,
+                          cudaStream_t s) {
+  return enqueue_sample(g, L, ws, p, o, false, hbuf, s);
+}
+int status_code(unsigned status, long long num_segments, int64_t max_segments) {
+  return status_to_code(status, num_segments, max_segments);
+}
+}  // namespace mh

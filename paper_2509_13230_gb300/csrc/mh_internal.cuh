@@ -191,6 +191,14 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
 cudaError_t launch_export_table(const Net& g, const Ctrl* ctrl, int32_t* row, int32_t* k, int64_t* a, int64_t* b,
                                 int64_t cap, cudaStream_t s);
 
+// Existing sampling steps, reachable from the fixed-scratch entry point.
+int check_sample_params(int model, int64_t n, const mh_params* p);
+Net net_view(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
+             char* ws);
+int enqueue_sample_direct(const Net& g, const Layout& L, char* ws, const mh_params* p, const Outputs& o, char* hbuf,
+                          cudaStream_t s);
+int status_code(unsigned status, long long num_segments, int64_t max_segments);
+
 cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k, double* s,
                                 cudaStream_t st);
 cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* gk,
