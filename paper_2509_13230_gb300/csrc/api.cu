@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "mh_internal.cuh"
+#include "scan.cuh"
 
 namespace mh {
 
@@ -127,7 +128,6 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   if (n + 1 > scan_len) scan_len = n + 1;
   if (L.items_max + 1 > scan_len) scan_len = L.items_max + 1;
   if (spc * (n + 1) > scan_len) scan_len = spc * (n + 1);
-  L.scan_tmp_elems = scan_len / kScanTile + 2;
   const size_t n1 = static_cast<size_t>(n) + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -146,9 +146,7 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.xs = take(8 * static_cast<size_t>(n));
   L.ys = take(8 * static_cast<size_t>(n));
   L.as = take(8 * static_cast<size_t>(n));
-  L.ymax = take(8 * n1);
   L.top1 = take(sizeof(Top2) * n1);
-  L.top2 = L.top1;
   L.Q = take(8 * n1);
   L.rowoff = take(8 * n1);
   L.seg = take(sizeof(int4) * static_cast<size_t>(L.max_segments));
@@ -161,7 +159,6 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   // partly unused, so staging holds capacity + capacity / 16 + the chunks.
   L.staging_entries = capacity + capacity / 16 + static_cast<int64_t>(kMaxWalkWarps) * (kStageChunk + kSlot);
   L.staging = take(4 * static_cast<size_t>(L.staging_entries));
-  L.scan_tmp = take(sizeof(Top2) * static_cast<size_t>(L.scan_tmp_elems));
   L.xdf = take(8 * static_cast<size_t>(n));
   L.adf = take(8 * static_cast<size_t>(n));
   L.ydf = take(8 * static_cast<size_t>(n));
@@ -169,6 +166,17 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.lntab = take(16 * 512);
   L.seg_c = take(8 * static_cast<size_t>(L.max_segments));
   L.seg_cf = take(16 * static_cast<size_t>(L.max_segments));
+  // states of the single-pass scans and of the one-sweep sort, cleared by one
+  // memset per call (the kernels leave them cleared)
+  L.scan_tiles = scan_len / kScanTile + 2;
+  L.zero_begin = off;
+  L.ghist = take(4 * 8 * 256);
+  L.sort_counters = take(16);
+  L.sort_state = take(8 * 256 * static_cast<size_t>(L.tiles > 0 ? L.tiles : 1));
+  L.scan_counters = take(16);
+  L.scan_flags = take(4 * static_cast<size_t>(L.scan_tiles));
+  L.zero_end = off;
+  L.scan_values = take(2 * sizeof(Top2) * static_cast<size_t>(L.scan_tiles));
   L.total = off;
   return L;
 }
@@ -186,7 +194,6 @@ static Net make_net(int model, const mh_params& p, const double* x, const double
   g.xs = reinterpret_cast<double*>(ws + L.xs);
   g.ys = reinterpret_cast<double*>(ws + L.ys);
   g.as = (model == MH_UECM) ? reinterpret_cast<double*>(ws + L.as) : g.xs;
-  g.ymax = reinterpret_cast<double*>(ws + L.ymax);
   g.top = reinterpret_cast<Top2*>(ws + L.top1);
   g.Q = reinterpret_cast<unsigned long long*>(ws + L.Q);
   g.rowoff = reinterpret_cast<long long*>(ws + L.rowoff);
@@ -260,10 +267,10 @@ static int check_params(int model, int64_t n, const mh_params* p) {
 static int prepare(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
   MH_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
   MH_CUDA(cudaMemsetAsync(&ctrl->key_and, 0xFF, sizeof(ctrl->key_and), s));
-  MH_CUDA(cudaMemsetAsync(g.ymax + g.n, 0, sizeof(double), s));
+  MH_CUDA(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));
   auto* keys0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
   auto* vals0 = reinterpret_cast<int32_t*>(ws + L.vals0);
-  MH_CUDA(launch_validate_keys(g, keys0, vals0, ctrl, s));
+  MH_CUDA(launch_validate_keys(g, keys0, vals0, reinterpret_cast<unsigned*>(ws + L.ghist), ctrl, s));
   MH_CUDA(launch_sort(g, L, ws, ctrl, s));
   MH_CUDA(launch_gather(g, vals0, ctrl, s));
   MH_CUDA(launch_bounds_and_partition(g, L, ws, ctrl, s));
@@ -319,7 +326,9 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
   c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
   c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
   c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
-  c.scan_tmp = ws + L.scan_tmp;
+  const ScanState scan_state{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
+                             reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
+  c.scan_state = const_cast<ScanState*>(&scan_state);
   c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
   for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {

@@ -18,15 +18,6 @@ namespace mh {
 
 namespace {
 
-__global__ void sample_counts_kernel(const long long* __restrict__ item_off, const Ctrl* ctrl, int64_t max_segments,
-                                     int64_t chunk_first, int64_t chunk_samples, long long* counts) {
-  long long S = ctrl->num_segments;
-  if (S > max_segments) S = max_segments;
-  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < chunk_samples;
-       s += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    counts[chunk_first + s] = item_off[(s + 1) * S] - item_off[s * S];
-}
-
 // csr_off[(chunk_first + s)(n+1) + u] = edges of row u in sample s (0 for u = n);
 // an in-place exclusive scan then turns counts into offsets.
 __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, const Ctrl* ctrl,
@@ -69,6 +60,12 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   const long long items = S * P.c.chunk_samples;
+  if (blockIdx.x == 0) {
+    // per-sample edge counts of this chunk; the next chunk continues after it
+    for (int64_t s = threadIdx.x; s < P.c.chunk_samples; s += blockDim.x)
+      P.c.sample_counts[P.c.chunk_first + s] = P.c.item_off[(s + 1) * S] - P.c.item_off[s * S];
+    if (threadIdx.x == 0) ctrl->out_base = ctrl->out_end;
+  }
   const long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems;
   if (it0 >= items) return;
   // Staging that did not fit was never written: emit nothing (the call
@@ -92,6 +89,10 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     }
     const long long item = it0 + lo;
     const long long e = pos - off[lo];
+    if (e >= P.c.item_cnt[item]) {  // offsets inconsistent with the counts: never read past a run
+      atomicOr(&ctrl->status, kStInternal);
+      continue;
+    }
     const long long s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);  // items < 2^31
     const long long seg = item - s_local * S;
     const int4 sg = g.seg[seg];
@@ -133,34 +134,27 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
 }  // namespace
 
 cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl* ctrl, cudaStream_t s) {
+  const ScanState& st = *static_cast<const ScanState*>(c.scan_state);
   cudaError_t e;
   // item offsets (continuing from the edges of earlier chunks)
-  e = device_scan<long long, SumOp<long long>>(c.item_cnt, c.item_off,
-                                               ScanLen{c.items_max, &ctrl->num_segments, c.chunk_samples}, true,
-                                               &ctrl->out_base, &ctrl->out_end, true,
-                                               reinterpret_cast<long long*>(c.scan_tmp), s);
+  e = scan_any<long long, SumOp<long long>>(c.item_cnt, c.item_off,
+                                                  ScanLen{c.items_max, &ctrl->num_segments, c.chunk_samples}, true,
+                                                  &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;
-  sample_counts_kernel<<<grid_for(c.chunk_samples, 128), 128, 0, s>>>(c.item_off, ctrl, g.max_segments,
-                                                                      c.chunk_first, c.chunk_samples,
-                                                                      c.sample_counts);
-  note_launches(1);
   if (o.csr_off) {
     const int64_t len = c.chunk_samples * (g.n + 1);
     csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
         g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off);
     note_launches(1);
     long long* region = o.csr_off + c.chunk_first * (g.n + 1);
-    e = device_scan<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->out_base,
-                                                 nullptr, false, reinterpret_cast<long long*>(c.scan_tmp), s);
+    e = scan_any<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->out_base,
+                                                    nullptr, false, st, s);
     if (e != cudaSuccess) return e;
   }
   EmitParams P{g, c, o, ctrl};
   emit_kernel<<<grid_for(c.items_max, kEmitItems), 256, 0, s>>>(P);
   note_launches(1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // the next chunk continues after this one
-  return cudaMemcpyAsync(&ctrl->out_base, &ctrl->out_end, sizeof(long long), cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
 }
 
 }  // namespace mh

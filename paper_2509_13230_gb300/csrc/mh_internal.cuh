@@ -61,11 +61,12 @@ constexpr int kDefaultSegTarget = 32;
 // ---- workspace layout --------------------------------------------------------
 struct Layout {
   int64_t n = 0, tiles = 0, max_segments = 0, spc = 0, items_max = 0, capacity = 0;
-  int64_t scan_tmp_elems = 0;
   size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
-         as = 0, ymax = 0, top1 = 0, top2 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
-         item_off = 0, sample_counts = 0, staging = 0, scan_tmp = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
-         lntab = 0, seg_c = 0, seg_cf = 0, total = 0;
+         as = 0, top1 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
+         item_off = 0, sample_counts = 0, staging = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
+         lntab = 0, seg_c = 0, seg_cf = 0, ghist = 0, sort_state = 0, sort_counters = 0, scan_flags = 0,
+         scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, total = 0;
+  int64_t scan_tiles = 0;
   int64_t staging_entries = 0;
 };
 
@@ -88,8 +89,7 @@ struct Net {
   double* xs;
   double* ys;
   double* as;
-  double* ymax;     // [n+1]
-  Top2* top;        // [n+1]
+  Top2* top;        // [n+1]: two largest y among ranks >= i (top[i].a = suffix max)
   unsigned long long* Q;  // [n+1] proxy prefix sums
   long long* rowoff;      // [n+1] first segment of each row; rowoff[n] = S
   int4* seg;              // {row, k, a, b}
@@ -156,7 +156,7 @@ inline unsigned grid_for(int64_t work, int per_block, unsigned cap = 1u << 30) {
 int sm_count();
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, Ctrl* ctrl,
+cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, unsigned* ghist, Ctrl* ctrl,
                                  cudaStream_t s);
 cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s);
@@ -172,7 +172,7 @@ struct ChunkArgs {
   long long* item_off;
   int32_t* staging;
   long long* sample_counts;
-  void* scan_tmp;
+  void* scan_state;  // ScanState of the single-pass scans
   int64_t staging_cap;
   int64_t items_max;
 };

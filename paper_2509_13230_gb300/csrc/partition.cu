@@ -25,7 +25,7 @@ namespace {
 
 __device__ __forceinline__ double row_c(const Net& g, int64_t i) {
   if (g.flags & MH_BOUND_PAPER) return g.top[i].a * g.top[i].b;
-  return g.ys[i] * g.ymax[i + 1];
+  return g.ys[i] * g.top[i + 1].a;
 }
 
 __device__ __forceinline__ double row_weight(const Net& g, int64_t i) {
@@ -139,19 +139,13 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
     g.seg[s] = make_int4(static_cast<int>(i), static_cast<int>(k), static_cast<int>(a), static_cast<int>(b));
     if (g.model == MH_UECM) {
       // exp(-beta_min) of this segment and the walk's FP32 / double-float forms
-      const double c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : g.ys[i] * g.ymax[a];
+      const double c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : g.ys[i] * g.top[a].a;
       const double omc = 1.0 - c;
       const df2 inv = df_from_double(1.0 / omc);
       g.seg_c[s] = c;
       g.seg_cf[s] = make_float4(inv.hi, inv.lo, static_cast<float>(omc), 0.0f);
     }
   }
-}
-
-__global__ void init_top_kernel(const double* __restrict__ ys, Top2* top, int64_t n) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i <= n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    top[i] = Top2{i < n ? ys[i] : 0.0, 0.0};
 }
 
 __global__ void export_table_kernel(const int4* __restrict__ seg, const Ctrl* ctrl, int64_t max_segments,
@@ -172,32 +166,26 @@ __global__ void export_table_kernel(const int4* __restrict__ seg, const Ctrl* ct
 }  // namespace
 
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
-  const unsigned blocks = grid_for(g.n + 1, 256, static_cast<unsigned>(sm_count()) * 8u);
+  const ScanState st{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
+                     reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
   cudaError_t e;
   // Q = exclusive prefix of the fixed-point costs, Q[n] = total.
-  e = device_scan<unsigned long long, SumOp<unsigned long long>>(
-      g.Q, g.Q, ScanLen{g.n, nullptr, 1}, true, nullptr, nullptr, true,
-      reinterpret_cast<unsigned long long*>(ws + L.scan_tmp), s);
+  e = scan_any<unsigned long long, SumOp<unsigned long long>>(g.Q, g.Q, ScanLen{g.n, nullptr, 1}, true,
+                                                                    nullptr, nullptr, true, st, s);
   if (e != cudaSuccess) return e;
   if (g.model == MH_UECM) {
-    // ymax[a] = max_{j >= a} y_j (ymax[n] = 0 by the workspace clear)
-    e = device_scan<double, MaxOp, true>(g.ys, g.ymax, ScanLen{g.n, nullptr, 1}, false, nullptr, nullptr, false,
-                                         reinterpret_cast<double*>(ws + L.scan_tmp), s);
-    if (e != cudaSuccess) return e;
-    // top[i] = two largest y among ranks >= i
-    init_top_kernel<<<blocks, 256, 0, s>>>(g.ys, g.top, g.n);
-    note_launches(1);
-    e = device_scan<Top2, Top2Op, true>(g.top, g.top, ScanLen{g.n, nullptr, 1}, false, nullptr, nullptr, false,
-                                        reinterpret_cast<Top2*>(ws + L.scan_tmp), s);
+    // top[i] = two largest y among ranks >= i; top[i].a is the suffix maximum
+    e = scan_any<Top2, Top2Op, true>(g.top, g.top, ScanLen{g.n, nullptr, 1}, false, nullptr, nullptr, false,
+                                           st, s);
     if (e != cudaSuccess) return e;
   }
+  const unsigned blocks = grid_for(g.n + 1, 256, static_cast<unsigned>(sm_count()) * 8u);
   row_count_kernel<<<blocks, 256, 0, s>>>(g);
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = device_scan<long long, SumOp<long long>>(g.rowoff, g.rowoff, ScanLen{g.n, nullptr, 1}, true, nullptr,
-                                               &ctrl->num_segments, true,
-                                               reinterpret_cast<long long*>(ws + L.scan_tmp), s);
+  e = scan_any<long long, SumOp<long long>>(g.rowoff, g.rowoff, ScanLen{g.n, nullptr, 1}, true, nullptr,
+                                                  &ctrl->num_segments, true, st, s);
   if (e != cudaSuccess) return e;
   const unsigned fill_blocks = grid_for(g.max_segments, 256, static_cast<unsigned>(sm_count()) * 16u);
   seg_fill_kernel<<<fill_blocks, 256, 0, s>>>(g, ctrl);

@@ -1,9 +1,9 @@
-// Device-wide scans: reduce -> scan of tile partials -> scan with carry-in.
+// Device-wide scans in one launch (chained tiles with decoupled look-back).
 //
-// Three launches, no inter-block waiting.  The length may come from device
-// memory (len = min(host_len, *dev_len * mult)) so a scan can follow a kernel
-// that decides the size without a host round trip.  Operators are exact
-// (integer sums, max, top-2), so the result does not depend on the tiling.
+// The length may come from device memory (len = min(host_len, *dev_len *
+// mult)) so a scan can follow a kernel that decides the size without a host
+// round trip.  Operators are exact (integer sums, max, top-2), so the result
+// does not depend on the tiling or on the order tiles finish in.
 #pragma once
 
 #include "mh_internal.cuh"
@@ -175,6 +175,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T
   }
 }
 
+// Multi-kernel form (reduce, scan of partials, scan with carry-in) for long
+// inputs, where a single-pass look-back would walk back over many tiles.
 // scan_tmp must hold ceil(host_len / kScanTile) + 2 elements of T.
 template <typename T, typename Op, bool kReverse = false>
 cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
@@ -186,6 +188,180 @@ cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T*
                                                                       write_total_at_len);
   note_launches(3);
   return cudaGetLastError();
+}
+
+
+// ---- single-pass scan (chained tiles, decoupled look-back) ---------------------
+// Tiles are claimed in ticket order, so a tile only ever waits on tiles that
+// are already running.  Each tile publishes its aggregate, then walks back
+// over its predecessors until it meets an inclusive prefix, and publishes
+// its own.  Every wait is bounded: after kSpinLimit polls the tile records
+// kStTimeout in the status word and publishes anyway, so no block waits
+// forever (the call then reports MH_ERR_DEVICE_TIMEOUT).  The last block to
+// finish clears the tile states and tickets for the next scan.
+constexpr unsigned kSpinLimit = 1u << 22;
+constexpr int kLookBack = 16;  // predecessor tiles read per look-back step
+
+struct ScanState {
+  unsigned* flags;     // per tile: 0 empty, 1 aggregate published, 2 inclusive prefix published
+  void* values;        // 2 x tiles values of the scanned type: aggregates, then inclusive prefixes
+  unsigned* counters;  // [0] tile ticket, [1] finished blocks
+  Ctrl* ctrl;          // status word for timeouts
+  int64_t max_tiles;   // capacity of `values` (per half)
+};
+
+__device__ __forceinline__ unsigned poll_flag(const unsigned* f) {
+  return *reinterpret_cast<const volatile unsigned*>(f);
+}
+
+// Loads through L2 (a value another block published after a fence).
+__device__ __forceinline__ unsigned load_cg(const unsigned* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long load_cg(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ long long load_cg(const long long* p) { return __ldcg(p); }
+__device__ __forceinline__ double load_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ Top2 load_cg(const Top2* p) {
+  const double* d = reinterpret_cast<const double*>(p);
+  return Top2{__ldcg(d), __ldcg(d + 1)};
+}
+
+template <typename T, typename Op, bool kReverse>
+__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in, T* out, ScanLen L, bool exclusive,
+                                                                     const T* base, T* total,
+                                                                     bool write_total_at_len, ScanState st) {
+  __shared__ T warp_sums[kScanThreads / 32];
+  __shared__ T last_of_warp[kScanThreads / 32];
+  __shared__ unsigned s_tile;
+  __shared__ T s_prefix;
+  __shared__ bool s_last;
+  Op op;
+  // Aggregates and inclusive prefixes live in separate arrays: each entry is
+  // written once, before its flag, so a reader never sees one replaced by
+  // the other.
+  T* agg_v = static_cast<T*>(st.values);
+  T* inc_v = agg_v + st.max_tiles;
+  const int64_t len = L.get();
+  const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&st.counters[0], 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (tile < tiles) {
+    const int64_t b0 = tile * kScanTile;
+    T vals[kScanIPT];
+    T acc = Op::identity();
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k) {
+      const int64_t e = b0 + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+      vals[k] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+      acc = op(acc, vals[k]);
+    }
+    T inc = acc;
+    const T agg = block_inclusive_scan<T, Op>(inc, warp_sums);
+    if (threadIdx.x == 0) {
+      T prefix = Op::identity();
+      if (tile == 0) {
+        if (base) prefix = *base;
+      } else {
+        agg_v[tile] = agg;
+        __threadfence();
+        atomicExch(&st.flags[tile], 1u);
+        // walk back kLookBack tiles per step (independent loads in flight)
+        int64_t t = tile - 1;
+        bool done = false;
+        while (!done) {
+          unsigned f[kLookBack];
+#pragma unroll
+          for (int q = 0; q < kLookBack; ++q) f[q] = (t - q >= 0) ? poll_flag(&st.flags[t - q]) : 2u;
+#pragma unroll
+          for (int q = 0; q < kLookBack; ++q) {
+            if (done) break;
+            const int64_t tq = t - q;
+            if (tq < 0) {
+              done = true;
+              break;
+            }
+            for (unsigned it = 0; f[q] == 0u; ++it) {
+              if (it >= kSpinLimit) {
+                atomicOr(&st.ctrl->status, kStTimeout);
+                f[q] = 2u;  // give up: publish below so successors finish
+                break;
+              }
+              __nanosleep(32);
+              f[q] = poll_flag(&st.flags[tq]);
+            }
+            __threadfence();
+            prefix = op(load_cg(f[q] == 2u ? &inc_v[tq] : &agg_v[tq]), prefix);
+            if (f[q] == 2u) done = true;
+          }
+          t -= kLookBack;
+        }
+      }
+      inc_v[tile] = op(prefix, agg);
+      __threadfence();
+      atomicExch(&st.flags[tile], 2u);
+      s_prefix = prefix;
+    }
+    T prev = shfl_up(inc, 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 31) last_of_warp[warp] = inc;
+    __syncthreads();
+    if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Op::identity();
+    T run = op(s_prefix, prev);
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k) {
+      const int64_t e = b0 + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+      const T next = op(run, vals[k]);
+      if (e < len) out[scan_index<kReverse>(e, len)] = exclusive ? run : next;
+      if (e == len - 1) {
+        if (write_total_at_len) out[len] = next;
+        if (total) *total = next;
+      }
+      run = next;
+    }
+  } else if (tile == 0 && threadIdx.x == 0) {  // empty input
+    const T v = base ? *base : Op::identity();
+    if (write_total_at_len) out[0] = v;
+    if (total) *total = v;
+  }
+  // the last block to finish resets the tile states
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&st.counters[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) st.flags[t] = 0u;
+    if (threadIdx.x == 0) {
+      st.counters[0] = 0u;
+      st.counters[1] = 0u;
+    }
+  }
+}
+
+// One launch; `st` must hold ceil(host_len / kScanTile) flags and values and
+// start cleared (it is left cleared).
+template <typename T, typename Op, bool kReverse = false>
+cudaError_t device_scan_1p(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
+                           bool write_total_at_len, const ScanState& st, cudaStream_t s) {
+  const unsigned tiles = grid_for(L.host_len, kScanTile);
+  scan_onepass_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, out, L, exclusive, base, total,
+                                                                       write_total_at_len, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Single pass for short inputs (launch count dominates), three kernels for
+// long ones (when every tile starts at once, look-backs would walk back over
+// many tiles).  `st.values` doubles as the three-kernel form's partials.
+constexpr int64_t kOnePassMaxTiles = 32;
+
+template <typename T, typename Op, bool kReverse = false>
+cudaError_t scan_any(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total, bool write_total_at_len,
+                     const ScanState& st, cudaStream_t s) {
+  if ((L.host_len + kScanTile - 1) / kScanTile <= kOnePassMaxTiles)
+    return device_scan_1p<T, Op, kReverse>(in, out, L, exclusive, base, total, write_total_at_len, st, s);
+  return device_scan<T, Op, kReverse>(in, out, L, exclusive, base, total, write_total_at_len,
+                                      static_cast<T*>(st.values), s);
 }
 
 }  // namespace mh

@@ -26,11 +26,16 @@ __device__ __forceinline__ unsigned long long warp_and(unsigned long long v) {
   return v;
 }
 
-// Checks the parameter domain and writes (key, id) pairs.
+// Checks the parameter domain, writes (key, id) pairs and accumulates the
+// histograms of all eight 8-bit digits (one read of the keys for all passes).
 __global__ void __launch_bounds__(256) validate_keys_kernel(int model, const double* __restrict__ x,
                                                              const double* __restrict__ y, int64_t n,
                                                              unsigned long long* __restrict__ keys,
-                                                             int32_t* __restrict__ vals, Ctrl* ctrl) {
+                                                             int32_t* __restrict__ vals, unsigned* ghist,
+                                                             Ctrl* ctrl) {
+  __shared__ unsigned hist[8 * 256];
+  for (int t = threadIdx.x; t < 8 * 256; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
   unsigned long long kor = 0, kand = ~0ull;
   bool bad = false;
   for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
@@ -49,6 +54,8 @@ __global__ void __launch_bounds__(256) validate_keys_kernel(int model, const dou
     vals[u] = static_cast<int32_t>(u);
     kor |= key;
     kand &= key;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) atomicAdd(&hist[p * 256 + static_cast<int>((key >> (8 * p)) & 0xFF)], 1u);
   }
   kor = warp_or(kor);
   kand = warp_and(kand);
@@ -57,6 +64,9 @@ __global__ void __launch_bounds__(256) validate_keys_kernel(int model, const dou
     atomicAnd(&ctrl->key_and, kand);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->status, kStDomain);
+  __syncthreads();
+  for (int t = threadIdx.x; t < 8 * 256; t += blockDim.x)
+    if (hist[t]) atomicAdd(&ghist[t], hist[t]);
 }
 
 __device__ __forceinline__ bool digit_constant(const Ctrl* ctrl, int shift) {
@@ -149,13 +159,180 @@ __device__ __forceinline__ float2 split2(double v) {
   return make_float2(d.hi, d.lo);
 }
 
+constexpr int kSortLookBack = 8;  // predecessor tiles read per look-back step
+
+struct SortState {
+  unsigned long long* words;  // per (tile, digit): count << 2 | flag (1 aggregate, 2 inclusive)
+  unsigned* counters;         // [0] tile ticket, [1] finished blocks
+};
+
+// One LSD pass (one-sweep): a tile claimed by ticket ranks its keys stably
+// (rounds of 256 keys in position order: earlier rounds, earlier warps,
+// earlier lanes), finds each digit's count in earlier tiles by decoupled
+// look-back, and scatters to digit base + earlier-tile count + local rank.
+// Passes whose digit is the same for every key copy instead.
+__global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
+    const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+    int32_t* __restrict__ vout, int64_t n, int pass, const unsigned* __restrict__ ghist, SortState st, Ctrl* ctrl) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ unsigned s_tile;
+  __shared__ bool s_last;
+  __shared__ unsigned wcount[kWarps][256];
+  __shared__ unsigned run[256];
+  __shared__ unsigned long long dbase[256];  // global start of each digit + earlier tiles
+  const int shift = 8 * pass;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  if (t == 0) s_tile = atomicAdd(&st.counters[0], 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * kSortTile;
+  if (digit_constant(ctrl, shift)) {
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const int64_t e = base + r * kSortThreads + t;
+      if (e < n) {
+        kout[e] = kin[e];
+        vout[e] = vin[e];
+      }
+    }
+  } else {
+    // exclusive prefix of the digit histogram (thread t owns digit t)
+    {
+      unsigned v = ghist[pass * 256 + t];
+      unsigned inc = v;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, inc, dd);
+        if (lane >= dd) inc += o;
+      }
+      if (lane == 31) wcount[0][warp] = inc;
+      __syncthreads();
+      unsigned wp = 0;
+      for (int w = 0; w < warp; ++w) wp += wcount[0][w];
+      dbase[t] = static_cast<unsigned long long>(wp + inc - v);
+      run[t] = 0;
+      __syncthreads();
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) wcount[w][t] = 0;
+      __syncthreads();
+    }
+    // stable local ranks
+    unsigned long long k[kSortIPT];
+    int32_t v[kSortIPT];
+    unsigned dig[kSortIPT], lr[kSortIPT];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const int64_t e = base + r * kSortThreads + t;
+      const bool valid = e < n;
+      k[r] = valid ? kin[e] : 0ull;
+      v[r] = valid ? vin[e] : 0;
+      const unsigned d = valid ? static_cast<unsigned>((k[r] >> shift) & 0xFF) : 0x100u + lane;
+      dig[r] = d;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned rank_in_warp = __popc(peers & lt);
+      if (valid && rank_in_warp == 0) wcount[warp][d] = __popc(peers);
+      __syncthreads();
+      {
+        unsigned acc = run[t];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          const unsigned c = wcount[w][t];
+          wcount[w][t] = acc;
+          acc += c;
+        }
+        run[t] = acc;
+      }
+      __syncthreads();
+      lr[r] = valid ? wcount[warp][d] + rank_in_warp : 0u;
+      __syncthreads();
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) wcount[w][t] = 0;
+      __syncthreads();
+    }
+    // decoupled look-back per digit: counts of digit t in earlier tiles
+    {
+      const unsigned long long cnt = run[t];
+      unsigned long long* my = &st.words[tile * 256 + t];
+      unsigned long long prefix = 0;
+      if (tile == 0) {
+        atomicExch(my, (cnt << 2) | 2ull);
+      } else {
+        atomicExch(my, (cnt << 2) | 1ull);
+        int64_t p = tile - 1;
+        bool done = false;
+        while (!done) {  // kSortLookBack predecessor tiles per step
+          unsigned long long w[kSortLookBack];
+#pragma unroll
+          for (int q = 0; q < kSortLookBack; ++q)
+            w[q] = (p - q >= 0) ? *reinterpret_cast<const volatile unsigned long long*>(&st.words[(p - q) * 256 + t])
+                                : 2ull;
+#pragma unroll
+          for (int q = 0; q < kSortLookBack; ++q) {
+            if (done) break;
+            if (p - q < 0) {
+              done = true;
+              break;
+            }
+            for (unsigned it = 0; (w[q] & 3ull) == 0ull; ++it) {
+              if (it >= kSpinLimit) {
+                atomicOr(&ctrl->status, kStTimeout);
+                w[q] = 2ull;  // give up; the call reports MH_ERR_DEVICE_TIMEOUT
+                break;
+              }
+              __nanosleep(32);
+              w[q] = *reinterpret_cast<const volatile unsigned long long*>(&st.words[(p - q) * 256 + t]);
+            }
+            prefix += w[q] >> 2;
+            if ((w[q] & 3ull) == 2ull) done = true;
+          }
+          p -= kSortLookBack;
+        }
+        atomicExch(my, ((prefix + cnt) << 2) | 2ull);
+      }
+      dbase[t] += prefix;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const int64_t e = base + r * kSortThreads + t;
+      if (e < n) {
+        const unsigned long long pos = dbase[dig[r]] + lr[r];
+        if (pos < static_cast<unsigned long long>(n)) {
+          kout[pos] = k[r];
+          vout[pos] = v[r];
+        } else {
+          atomicOr(&ctrl->status, kStInternal);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    s_last = atomicAdd(&st.counters[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int64_t w = t; w < tiles * 256; w += blockDim.x) st.words[w] = 0ull;
+    if (t == 0) {
+      st.counters[0] = 0u;
+      st.counters[1] = 0u;
+    }
+  }
+}
+
+
 // Rank-order copies of the parameters (FP64 and double-float), ln y for the
 // weights, the inverse permutation, the fixed-point segment costs
 // floor(min(v, 2^20) * 2^F) (scanned afterwards) and, in block 0, the
 // logarithm table.
 __global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __restrict__ sorted_ids) {
-  if (blockIdx.x == 0)
+  if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < kLnTable; k += blockDim.x) ln_table_entry(g.lntab, k);
+    if (threadIdx.x == 0 && g.model == MH_UECM) g.top[g.n] = Top2{0.0, 0.0};
+  }
   const int32_t top = sorted_ids[0];
   const double vmax = (g.model == MH_UBCM) ? g.x[top] : g.x[top] * g.y[top];
   const int F = proxy_scale(vmax, g.n);
@@ -176,6 +353,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __res
       g.adf[r] = split2(v);
       g.ydf[r] = split2(yu);
       g.lny[r] = split2(log(yu));
+      g.top[r] = Top2{yu, 0.0};  // scanned in reverse into suffix top-2
     }
     const double vc = v > 0x1p20 ? 0x1p20 : v;
     g.Q[r] = static_cast<unsigned long long>(ldexp(vc, F));
@@ -184,31 +362,48 @@ __global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __res
 
 }  // namespace
 
-cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, Ctrl* ctrl,
+cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, unsigned* ghist, Ctrl* ctrl,
                                  cudaStream_t s) {
-  const unsigned grid = grid_for(g.n, 256, static_cast<unsigned>(sm_count()) * 8u);
-  validate_keys_kernel<<<grid, 256, 0, s>>>(g.model, g.x, g.y, g.n, keys, vals, ctrl);
+  const unsigned grid = grid_for(g.n, 256, static_cast<unsigned>(sm_count()) * 4u);
+  validate_keys_kernel<<<grid, 256, 0, s>>>(g.model, g.x, g.y, g.n, keys, vals, ghist, ctrl);
   note_launches(1);
   return cudaGetLastError();
 }
+
+// Small inputs: eight one-sweep passes (one launch each).  Large inputs:
+// per pass a tile histogram, a scan of the (digit, tile) counts and a stable
+// scatter, which keeps every launch bandwidth-bound.
+constexpr int64_t kOneSweepMaxTiles = 32;
 
 cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
   auto* k0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
   auto* k1 = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   auto* v0 = reinterpret_cast<int32_t*>(ws + L.vals0);
   auto* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
+  const unsigned* ghist = reinterpret_cast<const unsigned*>(ws + L.ghist);
+  SortState st{reinterpret_cast<unsigned long long*>(ws + L.sort_state),
+               reinterpret_cast<unsigned*>(ws + L.sort_counters)};
+  const ScanState sst{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
+                      reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
   auto* hist = reinterpret_cast<unsigned*>(ws + L.hist);
-  auto* tmp = reinterpret_cast<unsigned*>(ws + L.scan_tmp);
   const unsigned tiles = static_cast<unsigned>(L.tiles);
   for (int pass = 0; pass < 8; ++pass) {
-    const int shift = pass * 8;
-    radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(k0, g.n, shift, hist, L.tiles, ctrl);
-    cudaError_t e = device_scan<unsigned, SumOp<unsigned>>(hist, hist, ScanLen{256 * L.tiles, nullptr, 1}, true,
-                                                          nullptr, nullptr, false, tmp, s);
-    if (e != cudaSuccess) return e;
-    radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, shift, hist, L.tiles, ctrl);
-    note_launches(2);
-    e = cudaGetLastError();
+    cudaError_t e;
+    if (L.tiles <= kOneSweepMaxTiles) {
+      onesweep_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, pass, ghist, st, ctrl);
+      note_launches(1);
+      e = cudaGetLastError();
+    } else {
+      const int shift = pass * 8;
+      radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(k0, g.n, shift, hist, L.tiles, ctrl);
+      note_launches(1);
+      e = scan_any<unsigned, SumOp<unsigned>>(hist, hist, ScanLen{256 * L.tiles, nullptr, 1}, true, nullptr, nullptr,
+                                              false, sst, s);
+      if (e != cudaSuccess) return e;
+      radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, shift, hist, L.tiles, ctrl);
+      note_launches(1);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     unsigned long long* kt = k0;
     k0 = k1;
