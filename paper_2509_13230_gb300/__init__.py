@@ -8,10 +8,12 @@ parameter inference, as hand-written sm_103a CUDA kernels behind a C ABI
 """
 from ._native import (MH_BOUND_PAPER, MH_FP64_ONLY, MH_INIT_PREV, MH_OUT_COO, MH_OUT_CSR, MH_UBCM, MH_UECM,
                       MhError)
+from .expected import ExpectedDegrees, FitResult, expected_degrees, fit
 from .sampler import (SampleResult, Sampler, expected_bwd, expected_fwd, sample_ubcm, sample_weighted,
                       segment_table)
 
 __all__ = [
     "MH_UBCM", "MH_UECM", "MH_OUT_COO", "MH_OUT_CSR", "MH_BOUND_PAPER", "MH_INIT_PREV", "MH_FP64_ONLY", "MhError",
     "Sampler", "SampleResult", "sample_ubcm", "sample_weighted", "segment_table", "expected_fwd", "expected_bwd",
+    "ExpectedDegrees", "expected_degrees", "fit", "FitResult",
 ]

@@ -1,0 +1,82 @@
+"""Expected degrees / strengths, their autograd Function and fitting (GPU).
+
+Targets are produced by the CPU oracle from known parameters; fitted
+parameters are checked by the oracle again, so no expected value comes from
+the CUDA path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_13230_gb300 import _native as nat
+from paper_2509_13230_gb300.expected import ExpectedDegrees, fit
+from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_out_of_range_operands_take_the_fp64_terms(model):
+    rng = np.random.default_rng(12)
+    n = 700
+    x = np.exp(rng.normal(-1.0, 1.5, n))
+    x[:3] = [1e30, 1e-30, 0.0]  # outside the double-float range, and an isolated node
+    y = rng.uniform(0.1, 0.95, n) if model == nat.MH_UECM else None
+    k, s = expected_fwd(model, dev(x), None if y is None else dev(y))
+    rk, rs = oracle.expected_fwd(model, x, y)
+    np.testing.assert_allclose(k.cpu().numpy(), rk, rtol=1e-10, atol=1e-300)
+    if y is not None:
+        np.testing.assert_allclose(s.cpu().numpy(), rs, rtol=1e-10, atol=1e-300)
+    gk = rng.normal(size=n)
+    gs = rng.normal(size=n) if y is not None else None
+    keep = np.arange(3, n)  # the oracle's closed forms divide by x_i
+    gx, gy = expected_bwd(model, dev(x), None if y is None else dev(y), dev(gk), None if gs is None else dev(gs))
+    rgx, rgy = oracle.expected_bwd(model, x, y, gk, gs, rows=keep)
+    np.testing.assert_allclose(gx.cpu().numpy()[keep], rgx, rtol=1e-10, atol=1e-12 * np.abs(rgx).max())
+    if y is not None:
+        np.testing.assert_allclose(gy.cpu().numpy()[keep], rgy, rtol=1e-10, atol=1e-12 * np.abs(rgy).max())
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_autograd_function_gradcheck(model):
+    # The forward is accurate to about 2^-45 relative (double-float terms), so
+    # the finite-difference step is 1e-5: truncation and rounding noise both
+    # stay near 1e-7, below the tolerance.
+    rng = np.random.default_rng(13)
+    n = 24
+    x = dev(np.exp(rng.normal(-0.5, 1.0, n))).requires_grad_(True)
+    if model == nat.MH_UBCM:
+        assert torch.autograd.gradcheck(lambda a: ExpectedDegrees.apply(a, None), (x,), eps=1e-5, atol=1e-5,
+                                        rtol=1e-4)
+    else:
+        y = dev(rng.uniform(0.2, 0.9, n)).requires_grad_(True)
+        assert torch.autograd.gradcheck(lambda a, b: ExpectedDegrees.apply(a, b), (x, y), eps=1e-5, atol=1e-5,
+                                        rtol=1e-4)
+
+
+def test_fit_ubcm_to_1e8():
+    rng = np.random.default_rng(14)
+    n = 600
+    x_true = np.exp(rng.normal(-2.5, 1.2, n))
+    k_t, _ = oracle.expected_fwd(oracle.UBCM, x_true)
+    res = fit(dev(k_t), tol=1e-8, adam_steps=100, newton_steps=300)
+    assert res.residual <= 1e-8
+    k_fit, _ = oracle.expected_fwd(oracle.UBCM, res.x.cpu().numpy())
+    assert np.max(np.abs(k_fit - k_t) / k_t) <= 2e-8
+
+
+def test_fit_uecm_to_1e8():
+    rng = np.random.default_rng(15)
+    n = 500
+    x_true = np.exp(rng.normal(-1.5, 1.0, n))
+    y_true = rng.uniform(0.3, 0.9, n)
+    k_t, s_t = oracle.expected_fwd(oracle.UECM, x_true, y_true)
+    res = fit(dev(k_t), dev(s_t), tol=1e-8, adam_steps=100, newton_steps=400)
+    assert res.residual <= 1e-8, res.history[-5:]
+    k_fit, s_fit = oracle.expected_fwd(oracle.UECM, res.x.cpu().numpy(), res.y.cpu().numpy())
+    assert np.max(np.abs(k_fit - k_t) / k_t) <= 2e-8
+    assert np.max(np.abs(s_fit - s_t) / s_t) <= 2e-8
