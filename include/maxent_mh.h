@@ -160,6 +160,89 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
 
 /*
+ * Batched ensembles: many networks of uneven size, UBCM and UECM mixed, each
+ * sampled num_samples times.  The paper samples one network at a time
+ * (Sec. 2.4, Algorithm 1); batching only schedules those same samples, so
+ * sample s of network t is bit-identical to mh_sample_ubcm / _weighted on
+ * that network alone with network_id = nets[t].network_id and
+ * sample_begin = params->sample_begin + s.
+ *
+ * Work is split into (network, sample) PAIRS, numbered network-major:
+ * pair p is network t = p / num_samples, sample params->sample_begin +
+ * p % num_samples.  One mh_sample_batched call draws a contiguous range of
+ * pairs (a wave) with one persistent walk launch per model over all of the
+ * wave's (network, sample, row segment) work items, then writes the wave's
+ * edges in pair order.  The caller sizes waves so their work items fit
+ * max_wave_items and their edges fit capacity_edges; the segment counts
+ * from mh_batch_prepare give the items of a pair exactly.
+ */
+typedef struct mh_network_desc {
+    int32_t model;       /* MH_UBCM or MH_UECM                                    */
+    uint32_t network_id; /* Philox key word 1 = hi32(seed) + network_id          */
+    int64_t n;           /* nodes, >= 1                                           */
+    const double* x;     /* FP64[n], >= 0                                         */
+    const double* y;     /* FP64[n] in [0, 1) for MH_UECM; NULL for MH_UBCM      */
+} mh_network_desc;
+
+/*
+ * Workspace bytes for a batch: the prepared networks (about 100 bytes per
+ * node plus 40 bytes per segment-table row) and the larger of the sort
+ * scratch and a wave's buffers (24 bytes per work item, staging for
+ * capacity_edges edges).
+ *   h_nets           host array of n_nets descriptors (1 <= n_nets <= 65536,
+ *                    sum of n < 2^31 - 2^20)
+ *   params           seed, sample_begin, num_samples (per network),
+ *                    seg_target, flags, max_segments (per network; 0 selects
+ *                    4 n + 1024); network_id and reserved must be 0
+ *   max_wave_items   work items one wave may hold, in [1, 2^30]; 0 selects 2^26
+ *   capacity_edges   edges one wave may write
+ */
+int mh_batch_workspace_size(const mh_network_desc* h_nets, int32_t n_nets, const mh_params* params,
+                            int64_t max_wave_items, int64_t capacity_edges, size_t* h_bytes);
+
+/*
+ * mh_batch_prepare — sort, bound prep and segment table of every network
+ * (Sec. 2.4 step (i), Algorithm 1's ordering and bound, row segments), kept
+ * in the workspace for any number of mh_sample_batched calls.  Networks are
+ * prepared on several internal streams joined back to `stream`.
+ *   h_num_segments   host int64[n_nets]: segment-table rows of each network;
+ *                    a pair of network t is h_num_segments[t] work items
+ * Errors: MH_ERR_DOMAIN (a bad x or y; the detail names the network),
+ * MH_ERR_WORKSPACE (workspace too small, or a segment table above
+ * max_segments: h_num_segments holds the needed rows).
+ */
+int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_params* params, void* workspace,
+                     size_t workspace_bytes, int64_t* h_num_segments, mh_stream_t stream);
+
+/*
+ * mh_sample_batched — one wave: pairs [pair_begin, pair_begin + pair_count).
+ * The workspace must hold mh_batch_prepare's result for the same h_nets and
+ * params (same n, model, x and y pointers, seg_target, MH_BOUND_PAPER and
+ * max_segments; the seed, sample_begin, network ids and the other flags may
+ * differ).  A workspace prepared for other networks gives MH_ERR_ARG.
+ *   src, dst, w      COO (MH_OUT_COO), int32[capacity_edges]; the wave's
+ *                    edges in pair order, each pair's edges in the order of
+ *                    the single-network call; ids are node ids within the
+ *                    pair's network; w only when the wave has UECM networks
+ *   csr_offsets      int64 (MH_OUT_CSR): for each pair of the wave in order,
+ *                    n_t + 1 offsets into csr_indices (as mh_sample_ubcm's
+ *                    per-sample offsets); sum over the wave's pairs of n_t + 1
+ *                    entries
+ *   csr_indices, csr_weights  int32[capacity_edges]
+ *   h_edges_per_pair host int64[pair_count]: edges of each pair
+ *   h_stats          host uint64[4] (MH_STAT_*) of the wave, or NULL
+ * pair_count must be >= 1 and at most 2^20.  MH_ERR_WORKSPACE when the
+ * wave has more than max_wave_items work items or the workspace is too
+ * small; MH_ERR_CAPACITY as for the single-network calls (exact counts are
+ * returned and a larger capacity_edges reproduces the wave).
+ */
+int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_params* params,
+                      int64_t max_wave_items, void* workspace, size_t workspace_bytes, int64_t pair_begin,
+                      int64_t pair_count, int32_t* src, int32_t* dst, int32_t* w, int64_t* csr_offsets,
+                      int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
+                      int64_t* h_edges_per_pair, uint64_t* h_stats, mh_stream_t stream);
+
+/*
  * mh_sample_ubcm_noalloc — mh_sample_ubcm without a caller-supplied
  * workspace.  The paper has no counterpart: this is an interface for callers
  * that cannot allocate device memory while they sample, such as code that

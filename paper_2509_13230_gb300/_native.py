@@ -47,6 +47,9 @@ EXPORTED = (
     "mh_segment_table",
     "maxent_expected_fwd",
     "maxent_expected_bwd",
+    "mh_batch_workspace_size",
+    "mh_batch_prepare",
+    "mh_sample_batched",
 )
 
 
@@ -61,6 +64,24 @@ class MhParams(ctypes.Structure):
         ("reserved", ctypes.c_uint32),
         ("max_segments", ctypes.c_int64),
     ]
+
+
+class MhNetworkDesc(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int32),
+        ("network_id", ctypes.c_uint32),
+        ("n", ctypes.c_int64),
+        ("x", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+    ]
+
+
+def network_descs(entries) -> ctypes.Array:
+    """Host array of mh_network_desc from (model, network_id, n, x_ptr, y_ptr) tuples."""
+    arr = (MhNetworkDesc * len(entries))()
+    for t, (model, network_id, n, x, y) in enumerate(entries):
+        arr[t] = MhNetworkDesc(int(model), int(network_id), int(n), x, y)
+    return arr
 
 
 class MhCallInfo(ctypes.Structure):
@@ -122,6 +143,13 @@ def load(path: str | None = None):
         lib.maxent_expected_fwd.restype = i32
         lib.maxent_expected_bwd.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_bwd.restype = i32
+        D = ctypes.POINTER(MhNetworkDesc)
+        lib.mh_batch_workspace_size.argtypes = [D, i32, P, i64, i64, ctypes.POINTER(sz)]
+        lib.mh_batch_workspace_size.restype = i32
+        lib.mh_batch_prepare.argtypes = [D, i32, P, vp, sz, vp, vp]
+        lib.mh_batch_prepare.restype = i32
+        lib.mh_sample_batched.argtypes = [D, i32, P, i64, vp, sz, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_batched.restype = i32
         if path is None:
             _LIB = lib
         return lib
@@ -192,3 +220,23 @@ def maxent_expected_fwd(model, x, y, n, k_out, s_out, stream) -> int:
 
 def maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream) -> int:
     return load().maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream)
+
+
+def mh_batch_workspace_size(h_nets, n_nets, params, max_wave_items, capacity_edges) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().mh_batch_workspace_size(h_nets, n_nets, ctypes.byref(params), max_wave_items, capacity_edges,
+                                         ctypes.byref(out)), "mh_batch_workspace_size")
+    return out.value
+
+
+def mh_batch_prepare(h_nets, n_nets, params, workspace, workspace_bytes, h_num_segments, stream) -> int:
+    return load().mh_batch_prepare(h_nets, n_nets, ctypes.byref(params), workspace, workspace_bytes, h_num_segments,
+                                   stream)
+
+
+def mh_sample_batched(h_nets, n_nets, params, max_wave_items, workspace, workspace_bytes, pair_begin, pair_count,
+                      src, dst, w, csr_offsets, csr_indices, csr_weights, capacity_edges, h_edges_per_pair, h_stats,
+                      stream) -> int:
+    return load().mh_sample_batched(h_nets, n_nets, ctypes.byref(params), max_wave_items, workspace,
+                                    workspace_bytes, pair_begin, pair_count, src, dst, w, csr_offsets, csr_indices,
+                                    csr_weights, capacity_edges, h_edges_per_pair, h_stats, stream)

@@ -350,9 +350,9 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
 }
 
 // ---- graph cache --------------------------------------------------------------
-// A call's kernel sequence depends only on its arguments, so it is captured
-// once into a CUDA graph (on a library-owned stream: the legacy default
-// stream cannot be captured) and replayed on the caller's stream.
+// A call's kernel sequence depends only on its arguments, so a repeated call
+// is captured into a CUDA graph (on a library-owned stream: the legacy
+// default stream cannot be captured) and replayed on the caller's stream.
 struct CallKey {
   int model, device;
   int64_t n, capacity;
@@ -367,10 +367,29 @@ struct CachedGraph {
   uint64_t last_use = 0;
 };
 constexpr int kGraphCache = 8;
+constexpr int kSeenKeys = 16;
 struct GraphCache {
   CachedGraph entries[kGraphCache];
   uint64_t clock = 0;
   cudaStream_t capture_stream[64] = {};
+  unsigned long long seen[kSeenKeys] = {};
+  int seen_next = 0;
+  // A call is captured the second time its key is seen; one-off calls
+  // launch directly, which costs less than a capture.
+  bool seen_before(const CallKey& k) {
+    unsigned long long h = 0xcbf29ce484222325ull;
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&k);
+    for (size_t i = 0; i < sizeof(CallKey); ++i) {
+      h ^= b[i];
+      h *= 0x100000001b3ull;
+    }
+    h |= 1ull;
+    for (auto v : seen)
+      if (v == h) return true;
+    seen[seen_next] = h;
+    seen_next = (seen_next + 1) % kSeenKeys;
+    return false;
+  }
   ~GraphCache() { clear(); }
   void clear() {
     for (auto& e : entries)
@@ -467,7 +486,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
 
   g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
   CachedGraph* cg = g_graphs.find(key);
-  if (!cg && dev >= 0 && dev < 64) {
+  if (!cg && dev >= 0 && dev < 64 && g_graphs.seen_before(key)) {
     cudaStream_t& cs = g_graphs.capture_stream[dev];
     if (!cs) MH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     g_launches = 0;
@@ -670,4 +689,14 @@ int enqueue_sample_direct(const Net& g, const Layout& L, char* ws, const mh_para
 int status_code(unsigned status, long long num_segments, int64_t max_segments) {
   return status_to_code(status, num_segments, max_segments);
 }
+int prepare_network(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  return prepare(g, L, ws, ctrl, s);
+}
+int64_t default_segments(int64_t n) { return default_max_segments(n); }
+int64_t take_launch_count() {
+  const int64_t v = g_launches;
+  g_launches = 0;
+  return v;
+}
+void record_call_info(const mh_call_info& info) { g_info = info; }
 }  // namespace mh

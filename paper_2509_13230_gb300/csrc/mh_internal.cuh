@@ -25,6 +25,8 @@ constexpr unsigned kStCapacity = 4u;  // output or staging shorter than the samp
 constexpr unsigned kStOverflow = 8u;  // weight above INT32_MAX
 constexpr unsigned kStTimeout = 16u;  // bounded device wait gave up
 constexpr unsigned kStInternal = 32u; // an internal consistency check failed
+constexpr unsigned kStNotPrepared = 64u;  // batch workspace prepared for other networks
+constexpr unsigned kStWaveItems = 128u;   // a wave holds more work items than its buffers
 
 // ---- control block (first bytes of the workspace) ---------------------------
 struct Ctrl {
@@ -39,7 +41,9 @@ struct Ctrl {
   long long out_base;           // edges emitted by earlier sample chunks
   long long out_end;            // edges emitted including the current chunk
   unsigned long long stats[4];  // MH_STAT_* counters
-  unsigned long long pad1[4];
+  unsigned long long ticket2;   // batched waves: work-queue ticket of the UECM walk
+  long long wave_items;         // batched waves: work items of the wave
+  long long model_items[2];     // batched waves: work items of the UBCM / UECM queues
 };
 
 // ---- tuning constants --------------------------------------------------------
@@ -186,6 +190,45 @@ struct Outputs {
   int64_t capacity;
 };
 cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s);
+
+// ---- batched ensembles (batch.cu) ------------------------------------------------
+// Static data of one network of a batch.  Its per-node arrays are slices of
+// concatenated arrays: ranks of network t occupy [node_base, node_base + n)
+// of xs, as, ys, xdf, adf, ydf, lny, perm (local ids) and rank (local ranks);
+// its (n+1)-long arrays (top, Q, rowoff) start at node1_base and its segment
+// table rows (local coordinates) at seg_base.
+struct BatchNet {
+  long long node_base;
+  long long node1_base;
+  long long seg_base;
+  long long max_segments;
+  int n;
+  int model;
+};
+// One network's share of a wave: host part first, then what the plan kernel
+// derives from the prepared segment counts.
+struct WaveNet {
+  long long pair_base;   // index of the network's first pair within the wave
+  long long csr_base;    // first CSR offset entry of that pair
+  uint32_t sample_lo;    // sample id of that pair
+  uint32_t sample_cnt;   // pairs of this network in the wave (0: none)
+  uint32_t key1;         // Philox key word 1
+  uint32_t pad;
+  long long S;           // segment-table rows (device)
+  long long item_begin;  // first work item of the network in the wave (device)
+};
+// What a batched walk launch reads besides the concatenated arrays.
+struct BatchQueue {
+  const BatchNet* nets;
+  const WaveNet* wave;
+  const int32_t* order;   // networks of the launch's model, ascending
+  const long long* mb;    // [n_order + 1]: first queue position of each
+  int n_order;
+  unsigned long long* ticket;
+  const long long* total;  // queue length
+};
+cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQueue& q, Ctrl* ctrl, int model,
+                                cudaStream_t s);
 cudaError_t prepare_kernel_attributes(int model);  // before any capture
 cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_export_table(const Net& g, const Ctrl* ctrl, int32_t* row, int32_t* k, int64_t* a, int64_t* b,

@@ -36,6 +36,7 @@ struct WalkParams {
   Net g;
   ChunkArgs c;
   Ctrl* ctrl;
+  BatchQueue q;  // batched waves only
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -75,33 +76,43 @@ struct SegWalker {
     return uecm ? prob_hat(xi, g.as[qj], c) : prob_ubcm(xi, g.xs[qj]);
   }
 
-  // Loads the segment of `item`; its head is set up by the next advance().
-  __device__ __forceinline__ void begin(const Net& g, long long item, long long S, uint32_t sample0, bool uecm) {
-    // item < 2^31 (the workspace layout bounds the items of a chunk)
-    const unsigned s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);
-    const unsigned seg = static_cast<unsigned>(item) - s_local * static_cast<unsigned>(S);
+  // Loads row segment `seg` of sample `smp`; its head is set up by the next
+  // advance().  Segment rows hold ranks local to their network; nb is the
+  // network's first slot in the node arrays (0 for a single network), so a,
+  // b, pos and j index the node arrays while i stays the local rank that the
+  // Philox counter uses.
+  __device__ __forceinline__ void begin_seg(const Net& g, unsigned seg, uint32_t smp, int nb, bool uecm) {
     const int4 e = g.seg[seg];
     i = e.x;
     k = e.y;
-    a = e.z;
-    b = e.w;
+    a = nb + e.z;
+    b = nb + e.w;
     pos = a - 1;
-    sample = sample0 + s_local;
+    sample = smp;
     d = 0;
     fresh = true;
+    const int gi = nb + e.x;
     if (!uecm) {
-      xi = g.xs[i];
-      xi_df = to_df(g.xdf[i]);
+      xi = g.xs[gi];
+      xi_df = to_df(g.xdf[gi]);
     } else {
-      xi = g.as[i];
-      yi = g.ys[i];
-      xi_df = to_df(g.adf[i]);
-      yi_df = to_df(g.ydf[i]);
+      xi = g.as[gi];
+      yi = g.ys[gi];
+      xi_df = to_df(g.adf[gi]);
+      yi_df = to_df(g.ydf[gi]);
       c = g.seg_c[seg];
       const float4 cf = g.seg_cf[seg];
       inv1mc = df2{cf.x, cf.y};
       omc_f = cf.z;
     }
+  }
+
+  // Single network: work item = (sample within the chunk, segment).
+  __device__ __forceinline__ void begin(const Net& g, long long item, long long S, uint32_t sample0, bool uecm) {
+    // item < 2^31 (the workspace layout bounds the items of a chunk)
+    const unsigned s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);
+    const unsigned seg = static_cast<unsigned>(item) - s_local * static_cast<unsigned>(S);
+    begin_seg(g, seg, sample0 + s_local, 0, uecm);
   }
 
   // One iteration.  Returns false when the segment has ended; sets
@@ -188,7 +199,43 @@ struct SegWalker {
   }
 };
 
+// Batched waves: position `qpos` of a model's queue lies in network
+// order[p], where p is the last queue entry with mb[p] <= qpos.  Entries of
+// networks without work have mb[p] == mb[p + 1] and are passed over.
+__device__ __forceinline__ int queue_entry(const BatchQueue& q, unsigned long long qpos) {
+  int lo = 0, hi = q.n_order - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (static_cast<unsigned long long>(q.mb[mid]) <= qpos)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Sets up the work item at queue position qpos, starting the network search
+// at entry p (a position at or before qpos's entry).  Returns the global
+// work item (its slot in item_cnt / item_base) and the network's key word.
 template <bool kUecm>
+__device__ __forceinline__ long long begin_queued(const Net& g, const BatchQueue& q, unsigned long long qpos, int p,
+                                                  SegWalker& wk, uint32_t& key1) {
+  while (p + 1 < q.n_order && static_cast<unsigned long long>(q.mb[p + 1]) <= qpos) ++p;
+  const int t = q.order[p];
+  const WaveNet& w = q.wave[t];
+  // a wave holds fewer than 2^31 work items and a network fewer than 2^31 rows
+  const unsigned local = static_cast<unsigned>(qpos - static_cast<unsigned long long>(q.mb[p]));
+  const unsigned S = static_cast<unsigned>(w.S);
+  const unsigned s_local = local / S;
+  const unsigned seg = local - s_local * S;
+  const BatchNet& bn = q.nets[t];
+  key1 = w.key1;
+  wk.begin_seg(g, static_cast<unsigned>(bn.seg_base) + seg, w.sample_lo + s_local, static_cast<int>(bn.node_base),
+               kUecm);
+  return w.item_begin + local;
+}
+
+template <bool kUecm, bool kBatch>
 __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) {
   extern __shared__ unsigned char smem_raw[];
   LnEntry* tab = reinterpret_cast<LnEntry*>(smem_raw);
@@ -208,7 +255,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
 
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
-  const unsigned long long total = static_cast<unsigned long long>(S) * P.c.chunk_samples;
+  const unsigned long long total = kBatch ? static_cast<unsigned long long>(*P.q.total)
+                                          : static_cast<unsigned long long>(S) * P.c.chunk_samples;
+  unsigned long long* const ticket = kBatch ? P.q.ticket : &ctrl->ticket;
   // work items per ticket: about 1/8 of an even share, within [32, 1024]
   const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * kWalkWarps;
   unsigned long long chunk = total / (warps * 8ull);
@@ -221,6 +270,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   unsigned cnt = 0;              // edges of the current pass
   unsigned long long rbase = 0;  // staging base of a second pass
   long long item = 0;
+  unsigned qpos = 0;        // batched: the lane's queue position (< 2^31)
+  uint32_t lane_key1 = key1;
+  int qcur = 0;             // batched: queue entry at or before the chunk's first position
   unsigned long long next = 0, end = 0;     // warp-uniform work cursor
   unsigned long long wbase = 0, wleft = 0;  // warp-uniform staging chunk
   bool work_left = total > 0;
@@ -232,20 +284,26 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
       while (idle && work_left) {
         if (next >= end) {
           unsigned long long t0 = 0;
-          if (lane == 0) t0 = atomicAdd(&ctrl->ticket, chunk);
+          if (lane == 0) t0 = atomicAdd(ticket, chunk);
           t0 = __shfl_sync(0xffffffffu, t0, 0);
           if (t0 >= total) {
             work_left = false;
             break;
           }
+          if (kBatch) qcur = queue_entry(P.q, t0);  // the same on every lane
           next = t0;
           end = t0 + chunk < total ? t0 + chunk : total;
         }
         const unsigned long long avail = end - next;
         const unsigned rank = __popc(idle & lt);
         if (!active && rank < avail) {
-          item = static_cast<long long>(next + rank);
-          wk.begin(g, item, S, P.c.sample0, kUecm);
+          if (kBatch) {
+            qpos = static_cast<unsigned>(next + rank);
+            item = begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1);
+          } else {
+            item = static_cast<long long>(next + rank);
+            wk.begin(g, item, S, P.c.sample0, kUecm);
+          }
           active = true;
           rewalk = false;
           cnt = 0;
@@ -262,7 +320,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
     if (active) {
       bool acc;
       int32_t j;
-      if (wk.advance<kUecm>(g, key0, key1, fp64_only, init_prev, tab, n_fallback, acc, j)) {
+      if (wk.advance<kUecm>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback, acc, j)) {
         if (acc) {
           if (!rewalk) {
             if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
@@ -284,7 +342,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
           if (rbase + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
           P.c.item_cnt[item] = cnt;
           P.c.item_base[item] = static_cast<long long>(rbase);
-          wk.begin(g, item, S, P.c.sample0, kUecm);
+          if (kBatch)
+            begin_queued<kUecm>(g, P.q, qpos, queue_entry(P.q, qpos), wk, lane_key1);
+          else
+            wk.begin(g, item, S, P.c.sample0, kUecm);
           rewalk = true;
           cnt = 0;
         }
@@ -367,40 +428,70 @@ size_t walk_smem_bytes() {
   return sizeof(LnEntry) * kLnTable + static_cast<size_t>(kWalkWarps) * 32 * kSlotStride * sizeof(int32_t);
 }
 
-// Shared-memory opt-in and occupancy of the walk kernel, per device (done
+// Shared-memory opt-in and occupancy of the walk kernels, per device (done
 // before a call is captured into a graph).
-static int g_per_sm[64][2] = {};
+static int g_per_sm[64][2][2] = {};
 
-cudaError_t prepare_kernel_attributes(int model) {
-  const bool uecm = model == MH_UECM;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (g_per_sm[dev][uecm]) return cudaSuccess;
-  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
+template <bool kUecm, bool kBatch>
+static cudaError_t walk_attributes(int dev) {
+  if (g_per_sm[dev][kUecm][kBatch]) return cudaSuccess;
+  auto kernel = walk_kernel<kUecm, kBatch>;
   const size_t smem = walk_smem_bytes();
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkWarps * 32, smem);
   if (e != cudaSuccess) return e;
-  g_per_sm[dev][uecm] = per_sm < 1 ? 1 : per_sm;
+  g_per_sm[dev][kUecm][kBatch] = per_sm < 1 ? 1 : per_sm;
   return cudaSuccess;
 }
 
+cudaError_t prepare_kernel_attributes(int model) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (model == MH_UECM) {
+    e = walk_attributes<true, false>(dev);
+    return e != cudaSuccess ? e : walk_attributes<true, true>(dev);
+  }
+  e = walk_attributes<false, false>(dev);
+  return e != cudaSuccess ? e : walk_attributes<false, true>(dev);
+}
+
+static unsigned walk_blocks(int dev, bool uecm, bool batch) {
+  int blocks = sm_count() * g_per_sm[dev][uecm][batch];
+  if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
+  return static_cast<unsigned>(blocks < 1 ? 1 : blocks);
+}
+
 cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
-  WalkParams P{g, c, ctrl};
+  WalkParams P{g, c, ctrl, BatchQueue{}};
   const bool uecm = g.model == MH_UECM;
   cudaError_t e = prepare_kernel_attributes(g.model);
   if (e != cudaSuccess) return e;
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  auto kernel = uecm ? walk_kernel<true> : walk_kernel<false>;
-  int blocks = sm_count() * g_per_sm[dev][uecm];
-  if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
-  kernel<<<static_cast<unsigned>(blocks), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  auto kernel = uecm ? walk_kernel<true, false> : walk_kernel<false, false>;
+  kernel<<<walk_blocks(dev, uecm, false), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// One persistent launch over the queue of one model's networks in a wave;
+// g holds the concatenated arrays of all networks.
+cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQueue& q, Ctrl* ctrl, int model,
+                                cudaStream_t s) {
+  WalkParams P{g, c, ctrl, q};
+  const bool uecm = model == MH_UECM;
+  cudaError_t e = prepare_kernel_attributes(model);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  auto kernel = uecm ? walk_kernel<true, true> : walk_kernel<false, true>;
+  kernel<<<walk_blocks(dev, uecm, true), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

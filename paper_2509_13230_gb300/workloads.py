@@ -21,6 +21,12 @@ import numpy as np
 # oracle/calibrate_scale.py (bisection on the oracle's exact expected degrees).
 PARETO_SCALE_N1M = 6.285e-4
 
+# The same calibration over sizes N = 10^(3 + k/4), k = 0..12 (written by
+# oracle/calibrate_ensemble_scale.py); sizes in between interpolate log c
+# linearly in log N.
+PARETO_SCALE_GRID_N = (1000, 1778, 3162, 5623, 10000, 17783, 31623, 56234, 100000, 177828, 316228, 562341, 1000000)
+PARETO_SCALE_GRID = (0.03231, 0.021, 0.01528, 0.01048, 0.007334, 0.005434, 0.004009, 0.002909, 0.002062, 0.001531, 0.001151, 0.0008664, 0.0006285)
+
 
 @dataclass(frozen=True)
 class Network:
@@ -56,6 +62,22 @@ def pareto_ubcm(n: int, scale: float, x_max: float = 50.0, tail: float = 1.1, se
     return Network(0, np.minimum(scale * u ** (-1.0 / tail), x_max), None)
 
 
+def pareto_scale(n: int) -> float:
+    """Scale c giving the capped Pareto fitness a mean expected degree of
+    about 20 at size n (clamped to the calibrated range [10^3, 10^6])."""
+    if n in PARETO_SCALE_GRID_N:
+        return PARETO_SCALE_GRID[PARETO_SCALE_GRID_N.index(n)]
+    return float(np.exp(np.interp(np.log(n), np.log(PARETO_SCALE_GRID_N), np.log(PARETO_SCALE_GRID))))
+
+
+def pareto_uecm(n: int, scale: float, y_lo: float = 0.3, y_hi: float = 0.9, x_max: float = 50.0, tail: float = 1.1,
+                seed: int = 3) -> Network:
+    """The Pareto fitness of pareto_ubcm with y ~ Uniform(y_lo, y_hi)."""
+    x = pareto_ubcm(n, scale, x_max=x_max, tail=tail, seed=seed).x
+    y = np.random.default_rng(seed + 7919).uniform(y_lo, y_hi, n)
+    return Network(1, x, y)
+
+
 # --------------------------------------------------------------------------
 # The five named workloads.
 # --------------------------------------------------------------------------
@@ -76,17 +98,25 @@ def ubcm_pareto_n1m(n: int = 1_000_000) -> Network:
     return pareto_ubcm(n, PARETO_SCALE_N1M, seed=3)
 
 
-def ensemble_128(num_networks: int = 128, n_lo: int = 1_000, n_hi: int = 1_000_000, seed: int = 4):
+def ensemble_128(num_networks: int = 128, n_lo: int = 1_000, n_hi: int = 1_000_000, seed: int = 4,
+                 fitness: str = "pareto"):
     """Batched ensemble: sizes log-uniform in [n_lo, n_hi], first half UBCM and
-    second half UECM, z ~ N(-4.0, 1.2), y ~ U(0.3, 0.9); 64 samples each."""
+    second half UECM (y ~ U(0.3, 0.9)); 64 samples each.  fitness "pareto":
+    the capped Pareto law of the N = 10^6 workload with its scale c(N)
+    calibrated per size (mean expected degree about 20 for the UBCM half);
+    "lognormal": z ~ N(-4.0, 1.2) as in the N = 20,000 workload."""
     rng = np.random.default_rng(seed)
     sizes = np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), num_networks))).astype(np.int64)
     nets = []
     for t, n in enumerate(sizes):
-        if t < num_networks // 2:
-            nets.append(lognormal_ubcm(int(n), -4.0, 1.2, seed=10_000 + t))
-        else:
+        uecm = t >= num_networks // 2
+        if fitness == "pareto":
+            c = pareto_scale(int(n))
+            nets.append(pareto_uecm(int(n), c, seed=10_000 + t) if uecm else pareto_ubcm(int(n), c, seed=10_000 + t))
+        elif uecm:
             nets.append(lognormal_uecm(int(n), -4.0, 1.2, 0.3, 0.9, seed=10_000 + t))
+        else:
+            nets.append(lognormal_ubcm(int(n), -4.0, 1.2, seed=10_000 + t))
     return nets
 
 

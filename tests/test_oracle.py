@@ -276,3 +276,17 @@ def test_pareto_scale_matches_calibration():
     g = json.load(open(os.path.join(GOLDEN, "pareto_scale.json")))
     assert workloads.PARETO_SCALE_N1M == g["scale"]
     assert abs(g["mean_degree"] - 20.0) < 0.05
+
+
+def test_pareto_scale_grid_matches_calibration():
+    from paper_2509_13230_gb300 import workloads
+    g = json.load(open(os.path.join(GOLDEN, "pareto_scale_grid.json")))
+    assert list(workloads.PARETO_SCALE_GRID_N) == g["n"]
+    assert list(workloads.PARETO_SCALE_GRID) == g["scale"]
+    assert max(abs(k - 20.0) for k in g["mean_degree"]) < 0.05
+    assert workloads.pareto_scale(1_000_000) == workloads.PARETO_SCALE_N1M
+    # between grid points: a fresh oracle sample at an off-grid size lands near 20
+    n = 7000
+    net = workloads.pareto_ubcm(n, workloads.pareto_scale(n), seed=3)
+    _, _, _, counts, _ = oracle.mh_sample(oracle.UBCM, net.x, seed=0, num_samples=1, seg_target=1 << 30)
+    assert abs(2.0 * counts[0] / n - 20.0) < 1.5
