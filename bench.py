@@ -12,6 +12,11 @@ scaling, no collective on the data path).
 
 Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle
 (the serial FP64 walk, one sample per step) on the host cores instead.
+
+At N = 1 the line also carries "ensemble": the 128-network batched ensemble
+(N log-uniform in [10^3, 10^6], half UBCM and half UECM, 64 samples each,
+CSR output) drawn by mh_batch_prepare + mh_sample_batched waves, beside a
+loop of one single-network call per (network, sample) on the same networks.
 """
 from __future__ import annotations
 
@@ -166,6 +171,100 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------------------
+# Batched ensemble leg: 128 networks (N log-uniform in [10^3, 10^6], half
+# UBCM, half UECM, capped Pareto fitness), 64 samples each, CSR output.
+# ---------------------------------------------------------------------------
+ENSEMBLE_SAMPLES = 64
+
+
+def ensemble_leg(args, dev, flush):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.ensemble import Ensemble
+    from paper_2509_13230_gb300.sampler import Sampler
+
+    nets_np = workloads.ensemble_128()
+    keep = max(1, min(args.ensemble_networks, len(nets_np)))
+    nets_np = [nets_np[t] for t in np.linspace(0, len(nets_np) - 1, keep).round().astype(int)]
+    nets = [(nw.model, torch.from_numpy(nw.x).to(dev), None if nw.y is None else torch.from_numpy(nw.y).to(dev), t)
+            for t, nw in enumerate(nets_np)]
+    n = np.array([nw.n for nw in nets_np], dtype=np.int64)
+    uecm = np.array([nw.model == nat.MH_UECM for nw in nets_np])
+    samples = args.ensemble_samples
+    ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=1 << 28, timing=True)
+    stream = torch.cuda.current_stream()
+    walk = {"ms": 0.0, "emit_ms": 0.0, "prepare_ms": 0.0}
+
+    def on_wave(res):
+        info = nat.mh_last_call_info()
+        walk["ms"] += info.walk_ms
+        walk["emit_ms"] += info.emit_ms
+
+    def one_pass():
+        ens.prepare()                # sort + segment tables are part of a step
+        walk["prepare_ms"] += nat.mh_last_call_info().prepare_ms
+        return ens.sample(on_wave=on_wave)
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 3))
+    total_ms, edges, out_bytes, waves = 0.0, 0, 0, 0
+    for k in walk:
+        walk[k] = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        counts, _ = one_pass()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        edges += int(counts.sum())
+        per_net = counts.reshape(len(nets), samples).sum(axis=1)
+        out_bytes += int((4 * per_net + 4 * per_net * uecm + 8 * (n + 1) * samples).sum())
+        waves += ens.waves_run
+    value = edges / (total_ms / 1e3)
+
+    # per-sample loop: one mh_sample_* call per (network, sample), same networks
+    loop_ms, loop_edges = 0.0, 0
+    loop_samples = args.ensemble_loop_samples
+    for (m, x, y, nid) in (nets if loop_samples > 0 else []):
+        s1 = Sampler(m, x, y, num_samples=1, network_id=nid, layout="csr")
+        s1.run()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(loop_samples):
+            nat.check(s1.call(sample_begin=k), "mh_sample")
+            loop_edges += int(s1.h_counts.sum())
+        ev1.record(stream)
+        ev1.synchronize()
+        loop_ms += ev0.elapsed_time(ev1)
+        del s1
+    loop_value = loop_edges / (loop_ms / 1e3) if loop_ms > 0 else None
+    hbm_gbs, peak_kind = peaks()
+    walk_ms = walk["ms"] / steps
+    return {
+        "workload": f"ensemble_{len(nets)}_x{samples}", "networks": len(nets), "nodes": int(n.sum()),
+        "samples_per_network": samples, "value": value, "unit": "edges/s", "ms_per_step": total_ms / steps,
+        "edges_per_step": edges // steps, "waves_per_step": waves / steps,
+        "output": "CSR int64 offsets + int32 indices (+ int32 weights for the UECM half)",
+        "write_gbs_of_step": out_bytes / steps / (total_ms / steps / 1e3) / 1e9,
+        "walk_ms_per_step": walk_ms,
+        "prepare_ms_per_step": walk["prepare_ms"] / steps,
+        "scan_emit_ms_per_step": walk["emit_ms"] / steps,
+        "write_gbs_of_walk": out_bytes / steps / (walk_ms / 1e3) / 1e9 if walk_ms > 0 else None,
+        "hbm_peak": hbm_gbs, "peak_kind": peak_kind,
+        "per_sample_loop": None if loop_value is None else {
+            "value": loop_value, "unit": "edges/s", "calls": len(nets) * loop_samples,
+            "samples_per_network": loop_samples, "batched_over_loop": value / loop_value},
+        "step": "mh_batch_prepare of all 128 networks + every (network, sample) pair in waves",
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -275,6 +374,9 @@ def run_ours(args, rank, world, local_rank):
             e2e_edges += m
             d2h += 12 * m + 8 * SAMPLES_PER_STEP
     e2e_value = e2e_edges / (e2e_ms / 1e3)
+    ensemble = None
+    if world == 1 and not args.no_ensemble:
+        ensemble = ensemble_leg(args, dev, flush)
     if world > 1:
         dist.barrier()
 
@@ -313,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
         "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
+        "ensemble": ensemble,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -326,6 +429,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
+    ap.add_argument("--leg", choices=["all", "ensemble"], default="all",
+                    help="ensemble: run only the batched ensemble leg and print its object")
+    ap.add_argument("--ensemble-networks", type=int, default=128,
+                    help="networks of the ensemble leg (evenly spaced subset of the 128)")
+    ap.add_argument("--ensemble-samples", type=int, default=ENSEMBLE_SAMPLES, help="samples per network")
+    ap.add_argument("--ensemble-loop-samples", type=int, default=4,
+                    help="samples per network of the ensemble's per-sample loop (0 skips the loop)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -334,6 +445,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+    elif args.leg == "ensemble":
+        import torch
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"ensemble": ensemble_leg(args, dev, flush)}), flush=True)
     else:
         run_ours(args, rank, world, local_rank)
 

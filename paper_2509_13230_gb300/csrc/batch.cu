@@ -456,9 +456,11 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
     const int t = last_at_or_below(V.n_nets, o, [&](int k) { return V.wave[k].csr_base; });
     const WaveNet& w = V.wave[t];
     const BatchNet& bn = V.nets[t];
-    const long long n1 = bn.n + 1;
-    const long long s = (o - w.csr_base) / n1;
-    const long long u = o - w.csr_base - s * n1;
+    // a wave holds fewer than 2^31 CSR offsets
+    const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
+    const unsigned rel = static_cast<unsigned>(o - w.csr_base);
+    const long long s = rel / n1;
+    const long long u = rel - static_cast<unsigned>(s) * n1;
     long long c = 0;
     if (u < bn.n) {
       const long long i = rank[bn.node_base + u];
@@ -482,34 +484,101 @@ struct BatchEmitParams {
   bool any_uecm;
 };
 
-// Blocks take kEmitItems consecutive work items at a time; consecutive
-// threads write consecutive edges of them.
+// What every edge of a work item shares, set up once per item.
+struct EmitItem {
+  long long base;    // staging position of the item's first rank
+  long long row_at;  // CSR: index position of the item's first edge
+  int cnt;           // edges of the item
+  int i;             // row rank within the network
+  int u;             // original id of row i's node
+  int k;             // segment index within the row
+  uint32_t sample;
+  uint32_t key1;
+  int nb;            // the network's first slot in the node arrays
+  int n;
+  int uecm;
+  float2 lnyi;
+  double yi;
+};
+constexpr int kBatchEmitItems = 256;
+
+// Blocks take kBatchEmitItems consecutive work items at a time: one thread
+// per item sets up its EmitItem, then consecutive threads write consecutive
+// edges of the items.
 __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
   const BatchView& V = P.V;
   const Net& g = P.g;
   Ctrl* wc = V.wc;
   __shared__ LnEntry tab[kLnTable];
-  __shared__ long long off[kEmitItems + 1];
-  __shared__ int item_net[kEmitItems];
-  if (P.any_uecm) {
-    ln_table_to_shared(tab, g.lntab);
-    __syncthreads();
-  }
+  __shared__ long long off[kBatchEmitItems + 1];
+  __shared__ EmitItem info[kBatchEmitItems];
+  __shared__ int net_lo, net_hi;
+  if (P.any_uecm) ln_table_to_shared(tab, g.lntab);
+  __syncthreads();
   const long long items = wc->wave_items;
   if (wc->stage_used > static_cast<unsigned long long>(P.staging_cap)) return;  // staging overflowed
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
+  const bool csr = P.o.csr_idx != nullptr;
   unsigned long long fallbacks = 0;
   bool overflow = false, bad = false;
-  for (long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems; it0 < items;
-       it0 += static_cast<long long>(gridDim.x) * kEmitItems) {
-    const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
-    for (long long t = threadIdx.x; t <= it1 - it0; t += blockDim.x) off[t] = P.item_off[it0 + t];
-    for (long long t = threadIdx.x; t < it1 - it0; t += blockDim.x)
-      item_net[t] = last_at_or_below(V.n_nets, it0 + t, [&](int k) { return V.wave[k].item_begin; });
+  for (long long it0 = static_cast<long long>(blockIdx.x) * kBatchEmitItems; it0 < items;
+       it0 += static_cast<long long>(gridDim.x) * kBatchEmitItems) {
+    const long long it1 = it0 + kBatchEmitItems < items ? it0 + kBatchEmitItems : items;
+    const int nit = static_cast<int>(it1 - it0);
+    for (int t = threadIdx.x; t <= nit; t += blockDim.x) off[t] = P.item_off[it0 + t];
+    // networks of the first and last item bound every item's network
+    if (threadIdx.x == 0) net_lo = last_at_or_below(V.n_nets, it0, [&](int q) { return V.wave[q].item_begin; });
+    if (threadIdx.x == 32)
+      net_hi = last_at_or_below(V.n_nets, it1 - 1, [&](int q) { return V.wave[q].item_begin; });
     __syncthreads();
-    const long long o0 = off[0], o1 = off[it1 - it0];
+    if (threadIdx.x < nit) {
+      const long long item = it0 + threadIdx.x;
+      int t = net_lo, hi = net_hi;
+      while (t < hi) {
+        const int mid = (t + hi + 1) >> 1;
+        if (V.wave[mid].item_begin <= item)
+          t = mid;
+        else
+          hi = mid - 1;
+      }
+      const WaveNet& w = V.wave[t];
+      const BatchNet& bn = V.nets[t];
+      // a wave holds fewer than 2^31 items and a network fewer than 2^31 rows
+      const unsigned local = static_cast<unsigned>(item - w.item_begin);
+      const unsigned S = static_cast<unsigned>(w.S);
+      const unsigned s_local = local / S;
+      const unsigned seg_local = local - s_local * S;
+      const int4 sg = g.seg[bn.seg_base + seg_local];
+      const long long gi = bn.node_base + sg.x;
+      EmitItem it;
+      it.base = P.item_base[item];
+      it.cnt = static_cast<int>(P.item_cnt[item]);
+      it.i = sg.x;
+      it.u = g.perm[gi];
+      it.k = sg.y;
+      it.sample = w.sample_lo + s_local;
+      it.key1 = w.key1;
+      it.nb = static_cast<int>(bn.node_base);
+      it.n = bn.n;
+      it.uecm = bn.model == MH_UECM;
+      it.row_at = 0;
+      if (csr) {
+        const long long row_first = w.item_begin + static_cast<long long>(s_local) * S + g.rowoff[bn.node1_base + sg.x];
+        it.row_at = P.o.csr_off[w.csr_base + static_cast<long long>(s_local) * (bn.n + 1) + it.u] +
+                    (P.item_off[item] - P.item_off[row_first]);
+      }
+      it.yi = 0.0;
+      it.lnyi = make_float2(0.f, 0.f);
+      if (it.uecm) {
+        it.yi = g.ys[gi];
+        it.lnyi = g.lny[gi];
+      }
+      info[threadIdx.x] = it;
+    }
+    __syncthreads();
+    const long long o0 = off[0], o1 = off[nit];
     for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
-      int lo = 0, hi = static_cast<int>(it1 - it0) - 1;  // last local item with off <= pos
+      int lo = 0, hi = nit - 1;  // last local item with off <= pos
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (off[mid] <= pos)
@@ -517,49 +586,36 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
         else
           hi = mid - 1;
       }
-      const long long item = it0 + lo;
-      const long long e = pos - off[lo];
-      if (e >= P.item_cnt[item]) {
+      const EmitItem& it = info[lo];
+      const int e = static_cast<int>(pos - off[lo]);
+      if (e >= it.cnt) {
         bad = true;
         continue;
       }
-      const int t = item_net[lo];
-      const WaveNet& w = V.wave[t];
-      const BatchNet& bn = V.nets[t];
-      const long long local = item - w.item_begin;
-      const long long s_local = local / w.S;
-      const long long seg_local = local - s_local * w.S;
-      const int4 sg = g.seg[bn.seg_base + seg_local];
-      const int32_t i = sg.x;
-      const long long gi = bn.node_base + i;
-      const long long gj = P.staging[P.item_base[item] + e];
-      const long long j = gj - bn.node_base;
-      if (j <= i || j >= bn.n) {  // cannot happen for a walked segment; never index with it
+      const int gj = P.staging[it.base + e];
+      const int j = gj - it.nb;
+      if (j <= it.i || j >= it.n) {  // cannot happen for a walked segment; never index with it
         bad = true;
         continue;
       }
-      const int32_t u = g.perm[gi], v = g.perm[gj];
+      const int32_t v = g.perm[gj];
       int32_t wt = 1;
-      if (bn.model == MH_UECM) {
-        const float2 li = g.lny[gi], lj = g.lny[gj];
-        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(sg.y), static_cast<uint32_t>(i),
-                         w.sample_lo + static_cast<uint32_t>(s_local), P.key0, w.key1, g.ys[gi], g.ys[gj],
-                         df2{li.x, li.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
+      if (it.uecm) {
+        const float2 lj = g.lny[gj];
+        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
+                         it.sample, P.key0, it.key1, it.yi, g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
+                         tab, fp64_only, overflow, fallbacks);
       }
-      if (pos < P.o.capacity) {
-        if (P.o.src) {
-          P.o.src[pos] = u;
-          P.o.dst[pos] = v;
-          if (P.o.w) P.o.w[pos] = wt;
-        }
-        if (P.o.csr_idx) {
-          const long long row_first = w.item_begin + s_local * w.S + g.rowoff[bn.node1_base + i];
-          const long long at =
-              P.o.csr_off[w.csr_base + s_local * (bn.n + 1) + u] + (P.item_off[item] - P.item_off[row_first]) + e;
-          if (at < P.o.capacity) {
-            P.o.csr_idx[at] = v;
-            if (P.o.csr_w) P.o.csr_w[at] = wt;
-          }
+      if (pos < P.o.capacity && P.o.src) {
+        P.o.src[pos] = it.u;
+        P.o.dst[pos] = v;
+        if (P.o.w) P.o.w[pos] = wt;
+      }
+      if (csr) {
+        const long long at = it.row_at + e;
+        if (at < P.o.capacity) {
+          P.o.csr_idx[at] = v;
+          if (P.o.csr_w) P.o.csr_w[at] = wt;
         }
       }
     }
@@ -1154,7 +1210,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     }
     BatchEmitParams P{V, gall, c.item_cnt, c.item_base, c.item_off, c.staging, c.staging_cap, out, c.key0,
                       B.n_model[1] > 0};
-    batch_emit_kernel<<<grid_for(items_max, kEmitItems, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(P);
+    batch_emit_kernel<<<grid_for(items_max, kBatchEmitItems, static_cast<unsigned>(sm_count()) * 6u), 256, 0, q>>>(P);
     note_launches(1);
     MHB_CUDA(cudaGetLastError());
     MHB_CUDA(cudaMemcpyAsync(hback, wc, sizeof(Ctrl), cudaMemcpyDeviceToHost, q));

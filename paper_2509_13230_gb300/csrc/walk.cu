@@ -62,9 +62,9 @@ struct SegWalker {
   bool fresh;                   // the head of the segment is still to be set up
   bool fast;                    // q lies inside the fast levels' range
   bool e_ok;                    // Ef is valid
-  double xi;                    // canonical x_i (UBCM) or a_i (UECM)
-  double yi, c;                 // UECM: y_i and the bound constant exp(-beta_min)
-  df2 xi_df, yi_df, inv1mc;     // double-float copies; inv1mc = 1 / (1 - c)
+  int32_t gi;                   // slot of row i in the node arrays
+  uint32_t seg;                 // segment-table row (UECM: its bound constant c)
+  df2 xi_df, yi_df, inv1mc;     // double-float x_i (a_i), y_i and 1 / (1 - c)
   float omc_f;                  // 1 - c in FP32
   df2 zq;                       // -ln(1 - q) = log1p(zq): zq = x_i x_j (UBCM) or A / (1 - c) (UECM)
   float lam_f;                  // log1p(zq) in FP32
@@ -72,8 +72,9 @@ struct SegWalker {
   uint4 rnd;                    // Philox words of draw d
   float Ef;                     // -ln U of draw d in FP32
 
+  // Canonical FP64 values are read back on the (rare) FP64 paths.
   __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
-    return uecm ? prob_hat(xi, g.as[qj], c) : prob_ubcm(xi, g.xs[qj]);
+    return uecm ? prob_hat(g.as[gi], g.as[qj], g.seg_c[seg]) : prob_ubcm(g.xs[gi], g.xs[qj]);
   }
 
   // Loads row segment `seg` of sample `smp`; its head is set up by the next
@@ -81,8 +82,9 @@ struct SegWalker {
   // network's first slot in the node arrays (0 for a single network), so a,
   // b, pos and j index the node arrays while i stays the local rank that the
   // Philox counter uses.
-  __device__ __forceinline__ void begin_seg(const Net& g, unsigned seg, uint32_t smp, int nb, bool uecm) {
-    const int4 e = g.seg[seg];
+  __device__ __forceinline__ void begin_seg(const Net& g, unsigned sg, uint32_t smp, int nb, bool uecm) {
+    const int4 e = g.seg[sg];
+    seg = sg;
     i = e.x;
     k = e.y;
     a = nb + e.z;
@@ -91,17 +93,13 @@ struct SegWalker {
     sample = smp;
     d = 0;
     fresh = true;
-    const int gi = nb + e.x;
+    gi = nb + e.x;
     if (!uecm) {
-      xi = g.xs[gi];
       xi_df = to_df(g.xdf[gi]);
     } else {
-      xi = g.as[gi];
-      yi = g.ys[gi];
       xi_df = to_df(g.adf[gi]);
       yi_df = to_df(g.ydf[gi]);
-      c = g.seg_c[seg];
-      const float4 cf = g.seg_cf[seg];
+      const float4 cf = g.seg_cf[sg];
       inv1mc = df2{cf.x, cf.y};
       omc_f = cf.z;
     }
@@ -177,7 +175,7 @@ struct SegWalker {
       if (verdict < 0) {
         if (fast_q) fallbacks += 1;
         if (!have_qc) qc = q64(g, kUecm);
-        const double p = kUecm ? prob_uecm(xi, g.as[j], yi * g.ys[j]) : prob_ubcm(xi, g.xs[j]);
+        const double p = kUecm ? prob_uecm(g.as[gi], g.as[j], g.ys[gi] * g.ys[j]) : prob_ubcm(g.xs[gi], g.xs[j]);
         verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
       }
       accepted = verdict != 0;
@@ -357,21 +355,21 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
       // Place the ended lanes' runs in the warp's staging chunk, in lane
       // order; lanes that do not fit go to a fresh chunk (a run never spans
       // two chunks, so each segment stays contiguous).
-      const unsigned long long need = ended ? cnt : 0;
-      unsigned long long incl = need;
+      const unsigned need = ended ? cnt : 0u;  // an ended run holds at most kSlot ranks
+      unsigned incl = need;
 #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, dd);
+        const unsigned o = __shfl_up_sync(0xffffffffu, incl, dd);
         if (lane >= dd) incl += o;
       }
-      const unsigned long long excl = incl - need;
+      const unsigned excl = incl - need;
+      const unsigned warp_need = __shfl_sync(0xffffffffu, incl, 31);
       const bool fits = incl <= wleft;
       const unsigned spill_mask = __ballot_sync(0xffffffffu, ended && !fits);
       unsigned long long my_base = wbase + excl;
       if (spill_mask) {
         const int first = __ffs(spill_mask) - 1;  // lanes from `first` on move to the new chunk
-        const unsigned long long moved_excl = __shfl_sync(0xffffffffu, excl, first);
-        const unsigned long long warp_need = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned moved_excl = __shfl_sync(0xffffffffu, excl, first);
         const unsigned long long rest = warp_need - moved_excl;
         const unsigned long long want = rest > static_cast<unsigned long long>(kStageChunk) ? rest : kStageChunk;
         unsigned long long nb = 0;
@@ -381,7 +379,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
         wbase = nb + rest;
         wleft = want - rest;
       } else {
-        const unsigned long long warp_need = __shfl_sync(0xffffffffu, incl, 31);
         wbase += warp_need;
         wleft -= warp_need;
       }
@@ -391,15 +388,22 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
         if (my_base + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
       }
       __syncwarp();
-      unsigned m = ended_mask;
-      while (m) {
-        const int l = __ffs(m) - 1;
-        m &= m - 1;
-        const unsigned cnt_l = __shfl_sync(0xffffffffu, cnt, l);
+      // Copy all ended runs in one pass: element idx of the concatenated
+      // runs belongs to the last lane whose exclusive prefix is <= idx.
+      const int32_t* wslots = slots + warp * 32 * kSlotStride;
+      for (unsigned r0 = 0; r0 < warp_need; r0 += 32) {
+        const unsigned idx = r0 + lane;
+        int l = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const unsigned v = __shfl_sync(0xffffffffu, excl, l + step);
+          if (v <= idx) l += step;
+        }
+        const unsigned ex_l = __shfl_sync(0xffffffffu, excl, l);
         const unsigned long long base_l = __shfl_sync(0xffffffffu, my_base, l);
-        if (base_l + cnt_l <= cap) {
-          const int32_t* src_slot = slots + (warp * 32 + l) * kSlotStride;
-          for (unsigned e = lane; e < cnt_l; e += 32) P.c.staging[base_l + e] = src_slot[e];
+        if (idx < warp_need) {
+          const unsigned e = idx - ex_l;
+          if (base_l + e < cap) P.c.staging[base_l + e] = wslots[l * kSlotStride + e];
         }
       }
       __syncwarp();

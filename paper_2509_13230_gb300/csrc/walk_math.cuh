@@ -376,6 +376,20 @@ __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t 
   const unsigned long long N = (e & 1u) ? top53(w.w, w.z) + 1ull : top53(w.y, w.x) + 1ull;
   const df2 nlr = df_add(lnyi, lnyj);  // ln r (negative)
   if (!fp64_only && nlr.hi < -0x1p-12f && nlr.hi > -0x1p+100f) {
+    // FP32 level: t = E / -ln r with E from the FP32 logarithm of U; the
+    // divisor is the double-float ln r rounded once, more accurate than the
+    // walk's FP32 log1p, so the walk's FP32 margin covers this quotient.
+    bool ok;
+    const float Ef = neg_ln_u53_f(N, tab, ok);
+    if (ok) {
+      const float t = __fdividef(Ef, -nlr.hi);
+      if (t < 0x1p22f) {
+        const float margin = fmaf(t, 0x1p-18f, 0x1p-22f);
+        const float fh = floorf(t);
+        const float fr = t - fh;  // exact
+        if (fr > margin && 1.0f - fr > margin) return 1 + static_cast<int32_t>(fh);
+      }
+    }
     const df2 E = neg_ln_u53(N, tab);
     const df2 t = df_div(E, df2{-nlr.hi, -nlr.lo});
     unsigned fl;
