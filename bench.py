@@ -193,7 +193,14 @@ def ensemble_leg(args, dev, flush):
     n = np.array([nw.n for nw in nets_np], dtype=np.int64)
     uecm = np.array([nw.model == nat.MH_UECM for nw in nets_np])
     samples = args.ensemble_samples
-    ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=1 << 28, timing=True)
+    tuned = None
+    T, ctas = 0, 0
+    if not args.no_tune:
+        from paper_2509_13230_gb300.autotune import tune_ensemble
+        tuned = tune_ensemble(nets, candidates_t=(16, 32, 64), candidates_ctas=(0, 2), num_samples=2, reps=2)
+        T, ctas = tuned.seg_target, tuned.walk_ctas_per_sm
+    ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=1 << 28, timing=True, seg_target=T,
+                   walk_ctas_per_sm=ctas)
     stream = torch.cuda.current_stream()
     walk = {"ms": 0.0, "emit_ms": 0.0, "prepare_ms": 0.0}
 
@@ -232,7 +239,7 @@ def ensemble_leg(args, dev, flush):
     loop_ms, loop_edges = 0.0, 0
     loop_samples = args.ensemble_loop_samples
     for (m, x, y, nid) in (nets if loop_samples > 0 else []):
-        s1 = Sampler(m, x, y, num_samples=1, network_id=nid, layout="csr")
+        s1 = Sampler(m, x, y, num_samples=1, network_id=nid, layout="csr", seg_target=T, walk_ctas_per_sm=ctas)
         s1.run()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -260,8 +267,77 @@ def ensemble_leg(args, dev, flush):
         "per_sample_loop": None if loop_value is None else {
             "value": loop_value, "unit": "edges/s", "calls": len(nets) * loop_samples,
             "samples_per_network": loop_samples, "batched_over_loop": value / loop_value},
-        "step": "mh_batch_prepare of all 128 networks + every (network, sample) pair in waves",
+        "step": "mh_batch_prepare of all networks + every (network, sample) pair in waves",
+        "seg_target": T or 32, "walk_ctas_per_sm": ctas,
+        "autotune": None if tuned is None else {
+            "probe": "all networks x 2 samples, prepare + waves, CUDA events", "table": tuned.table},
     }
+
+
+# ---------------------------------------------------------------------------
+# Pairwise leg: expected degrees / strengths and their gradient (UECM, N =
+# 200,000, the size of the fitting workload), the O(N^2) sums of inference.
+# ---------------------------------------------------------------------------
+PAIR_N = 200_000
+# FP32 operations per ordered pair of the double-float evaluation, counted
+# from its operation sequence (two_sum 6, fast_two_sum 3, df_mul 7, df_add 20,
+# df_add_f 10, df_div 16 with each division as reciprocal + multiply).
+PAIR_OPS = {"fwd": 126, "bwd": 344}
+FP32_LANES_PER_SM = 128
+
+
+def pairwise_leg(args, dev, sm_mhz):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
+
+    rng = np.random.default_rng(11)
+    x_np = np.exp(rng.normal(-5.5, 1.3, PAIR_N))
+    y_np = rng.uniform(0.3, 0.9, PAIR_N)
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.from_numpy(y_np).to(dev)
+    gk = torch.from_numpy(rng.normal(size=PAIR_N)).to(dev)
+    gs = torch.from_numpy(rng.normal(size=PAIR_N)).to(dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for kind in ("fwd", "bwd"):
+        def call():
+            if kind == "fwd":
+                return expected_fwd(nat.MH_UECM, x, y)
+            return expected_bwd(nat.MH_UECM, x, y, gk, gs)
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        reps = 5
+        ev0.record(stream)
+        for _ in range(reps):
+            call()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        pairs = PAIR_N * (PAIR_N - 1)
+        out[kind] = {"ms": ms, "pairs_per_s": pairs / (ms / 1e3), "fp32_ops_per_pair": PAIR_OPS[kind],
+                     "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9}
+    import torch.cuda as tc
+    sms = tc.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e9
+    for kind in out:
+        out[kind]["frac"] = out[kind]["achieved_gops"] / peak
+    # the oracle (compensated FP64 sums, one host core) on a few sampled rows
+    import oracle
+    rows = rng.choice(PAIR_N, 4, replace=False)
+    t0 = time.perf_counter()
+    oracle.expected_fwd(oracle.UECM, x_np, y_np, rows=rows)
+    t_cpu = time.perf_counter() - t0
+    return {"workload": f"uecm_pairwise_n{PAIR_N // 1000}k", "n": PAIR_N, "bound": "alu",
+            "peak_gops": peak, "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz "
+                                              "(median SM clock of the sampler's timed region)",
+            **out,
+            "cpu_baseline": {"value": len(rows) * (PAIR_N - 1) / t_cpu, "unit": "pairs/s (forward)", "cores": 1,
+                             "kind": "oracle", "sample": f"{len(rows)} rows of the forward sums, FP64 compensated"}}
 
 
 # ---------------------------------------------------------------------------
@@ -377,6 +453,9 @@ def run_ours(args, rank, world, local_rank):
     ensemble = None
     if world == 1 and not args.no_ensemble:
         ensemble = ensemble_leg(args, dev, flush)
+    pairwise = None
+    if world == 1 and not args.no_ensemble:
+        pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
     if world > 1:
         dist.barrier()
 
@@ -416,6 +495,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
         "ensemble": ensemble,
+        "pairwise": pairwise,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -430,8 +510,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble"], default="all",
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
+    ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--ensemble-networks", type=int, default=128,
                     help="networks of the ensemble leg (evenly spaced subset of the 128)")
     ap.add_argument("--ensemble-samples", type=int, default=ENSEMBLE_SAMPLES, help="samples per network")
@@ -445,12 +526,16 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
-    elif args.leg == "ensemble":
+    elif args.leg == "ensemble" and args.impl != "reference":
         import torch
         torch.cuda.set_device(local_rank)
         dev = torch.device("cuda", local_rank)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps({"ensemble": ensemble_leg(args, dev, flush)}), flush=True)
+    elif args.leg == "pairwise":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"pairwise": pairwise_leg(args, torch.device("cuda", local_rank), None)}), flush=True)
     else:
         run_ours(args, rank, world, local_rank)
 

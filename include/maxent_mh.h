@@ -84,7 +84,8 @@ typedef struct mh_params {
     uint32_t seg_target;   /* T: expected proposals per row segment, >= 2;          */
                            /* 0 selects 32.  Part of a sample's identity.           */
     uint32_t flags;        /* MH_OUT_*, MH_BOUND_PAPER, MH_INIT_PREV, MH_FP64_ONLY  */
-    uint32_t reserved;     /* must be 0                                             */
+    uint32_t walk_ctas_per_sm; /* proposal-walk blocks per SM, 0 = as many as fit;   */
+                               /* a schedule choice only: samples do not change    */
     int64_t max_segments;  /* row-segment table capacity; 0 selects 4 n + 1024      */
 } mh_params;
 
@@ -193,7 +194,7 @@ typedef struct mh_network_desc {
  *                    sum of n < 2^31 - 2^20)
  *   params           seed, sample_begin, num_samples (per network),
  *                    seg_target, flags, max_segments (per network; 0 selects
- *                    4 n + 1024); network_id and reserved must be 0
+ *                    4 n + 1024); network_id must be 0
  *   max_wave_items   work items one wave may hold, in [1, 2^30]; 0 selects 2^26
  *   capacity_edges   edges one wave may write
  */

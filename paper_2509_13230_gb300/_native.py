@@ -61,7 +61,7 @@ class MhParams(ctypes.Structure):
         ("num_samples", ctypes.c_uint32),
         ("seg_target", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("walk_ctas_per_sm", ctypes.c_uint32),
         ("max_segments", ctypes.c_int64),
     ]
 
@@ -170,9 +170,9 @@ def check(code: int, func: str) -> int:
 
 
 def make_params(*, seed=0, network_id=0, sample_begin=0, num_samples=1, seg_target=0, flags=MH_OUT_COO,
-                max_segments=0) -> MhParams:
+                max_segments=0, walk_ctas_per_sm=0) -> MhParams:
     return MhParams(int(seed) & 0xFFFFFFFFFFFFFFFF, int(network_id), int(sample_begin), int(num_samples),
-                    int(seg_target), int(flags), 0, int(max_segments))
+                    int(seg_target), int(flags), int(walk_ctas_per_sm), int(max_segments))
 
 
 # ---- same names as the C ABI ------------------------------------------------------

@@ -239,8 +239,8 @@ static int check_params(int model, int64_t n, const mh_params* p) {
     set_error("unknown flag bits 0x%x", p->flags & ~kKnownFlags);
     return MH_ERR_ARG;
   }
-  if (p->reserved != 0 || p->max_segments < 0) {
-    set_error("reserved must be 0 and max_segments >= 0");
+  if (p->walk_ctas_per_sm > 64 || p->max_segments < 0) {
+    set_error("walk_ctas_per_sm must be at most 64 and max_segments >= 0");
     return MH_ERR_ARG;
   }
   if (p->max_segments > 0 && p->max_segments < n - 1) {
@@ -331,6 +331,7 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
   c.scan_state = const_cast<ScanState*>(&scan_state);
   c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
+  c.walk_ctas_per_sm = static_cast<int>(p->walk_ctas_per_sm);
   for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
     const int64_t left = static_cast<int64_t>(p->num_samples) - first;
     c.chunk_first = first;

@@ -1156,6 +1156,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
   c.staging = reinterpret_cast<int32_t*>(ws + B.staging);
   c.staging_cap = B.staging_entries;
   c.items_max = items_max;
+  c.walk_ctas_per_sm = static_cast<int>(params->walk_ctas_per_sm);
   const ScanState scan_state{reinterpret_cast<unsigned*>(ws + B.scan_flags), ws + B.scan_values,
                              reinterpret_cast<unsigned*>(ws + B.scan_counters), wc, B.scan_tiles};
   long long* pair_counts = reinterpret_cast<long long*>(ws + B.pair_counts);

@@ -179,6 +179,7 @@ struct ChunkArgs {
   void* scan_state;  // ScanState of the single-pass scans
   int64_t staging_cap;
   int64_t items_max;
+  int walk_ctas_per_sm;  // 0: as many walk blocks per SM as fit
 };
 struct Outputs {
   int32_t* src;

@@ -463,8 +463,10 @@ cudaError_t prepare_kernel_attributes(int model) {
   return e != cudaSuccess ? e : walk_attributes<false, true>(dev);
 }
 
-static unsigned walk_blocks(int dev, bool uecm, bool batch) {
-  int blocks = sm_count() * g_per_sm[dev][uecm][batch];
+static unsigned walk_blocks(int dev, bool uecm, bool batch, int ctas_per_sm) {
+  int per_sm = g_per_sm[dev][uecm][batch];
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  int blocks = sm_count() * per_sm;
   if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
   return static_cast<unsigned>(blocks < 1 ? 1 : blocks);
 }
@@ -478,7 +480,7 @@ cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   auto kernel = uecm ? walk_kernel<true, false> : walk_kernel<false, false>;
-  kernel<<<walk_blocks(dev, uecm, false), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  kernel<<<walk_blocks(dev, uecm, false, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -495,7 +497,7 @@ cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQue
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   auto kernel = uecm ? walk_kernel<true, true> : walk_kernel<false, true>;
-  kernel<<<walk_blocks(dev, uecm, true), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  kernel<<<walk_blocks(dev, uecm, true, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

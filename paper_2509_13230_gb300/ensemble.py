@@ -115,7 +115,7 @@ class Ensemble:
     def __init__(self, networks, *, num_samples: int = 1, seed: int = 0, sample_begin: int = 0,
                  seg_target: int = 0, layout: str = "csr", bound: str = "suffix", init: str = "head",
                  fp64_only: bool = False, max_segments: int = 0, max_wave_items: int = DEFAULT_WAVE_ITEMS,
-                 capacity: int = 1 << 24, timing: bool = False):
+                 capacity: int = 1 << 24, timing: bool = False, walk_ctas_per_sm: int = 0):
         self.entries = []
         for t, net in enumerate(networks):
             model, x, y = int(net[0]), net[1], net[2]
@@ -139,7 +139,8 @@ class Ensemble:
             flags |= nat.MH_TIMING
         self.layout = layout
         self.params = nat.make_params(seed=seed, sample_begin=sample_begin, num_samples=num_samples,
-                                      seg_target=seg_target, flags=flags, max_segments=max_segments)
+                                      seg_target=seg_target, flags=flags, max_segments=max_segments,
+                                      walk_ctas_per_sm=walk_ctas_per_sm)
         self.descs = nat.network_descs([(m, nid, n, x.data_ptr(), None if y is None else y.data_ptr())
                                         for (m, nid, n, x, y) in self.entries])
         self.max_wave_items = int(max_wave_items)

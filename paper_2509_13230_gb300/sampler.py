@@ -71,7 +71,7 @@ class Sampler:
     def __init__(self, model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, num_samples: int = 1,
                  seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
                  layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
-                 capacity: int | None = None, max_segments: int = 0):
+                 capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0):
         self.model = int(model)
         self.x = _check_vec("x", x)
         self.n = int(self.x.shape[0])
@@ -89,6 +89,7 @@ class Sampler:
         self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
         self.seg_target = int(seg_target)
         self.max_segments = int(max_segments)
+        self.walk_ctas_per_sm = int(walk_ctas_per_sm)
         self.device = self.x.device
         if capacity is None:
             capacity = max(1024, 16 * self.n * self.num_samples)
@@ -98,7 +99,7 @@ class Sampler:
         return nat.make_params(seed=self.seed, network_id=self.network_id,
                                sample_begin=self.sample_begin if sample_begin is None else sample_begin,
                                num_samples=self.num_samples, seg_target=self.seg_target, flags=self.flags,
-                               max_segments=self.max_segments)
+                               max_segments=self.max_segments, walk_ctas_per_sm=self.walk_ctas_per_sm)
 
     def _alloc(self, capacity: int):
         self.capacity = capacity

@@ -124,3 +124,22 @@ def test_sample_batched_rejects_bad_pair_ranges_without_a_gpu(lib):
         rc = nat.mh_sample_batched(d, 2, p, 0, ctypes.c_void_p(0x1000), 1 << 30, begin, count, None, None, None,
                                    None, None, None, 0, counts, None, None)
         assert rc == nat.MH_ERR_ARG, (begin, count)
+
+
+# --------------------------------------------------------------------------
+# Autotuner selection rule (timings are inputs here; the GPU probes are
+# exercised in tests/test_gpu_batched.py)
+# --------------------------------------------------------------------------
+def test_autotune_pick_fastest_and_tie_rules():
+    from paper_2509_13230_gb300.autotune import pick
+    row = lambda T, c, r: {"T": T, "ctas": c, "edges_per_ms": r}
+    # clear winner
+    assert pick([row(16, 0, 100), row(32, 0, 120), row(64, 2, 300)]) == (64, 2)
+    # within 1 %: the default T wins
+    assert pick([row(16, 0, 1000), row(32, 0, 995), row(64, 0, 998)]) == (32, 0)
+    # within 1 % without the default: the larger T, then full occupancy
+    assert pick([row(16, 0, 1000), row(64, 2, 996), row(64, 0, 995)]) == (64, 0)
+    # outside the tie band the rate decides
+    assert pick([row(32, 0, 900), row(128, 2, 1000)]) == (128, 2)
+    with pytest.raises(ValueError):
+        pick([])

@@ -212,3 +212,24 @@ def test_ensemble_128_full_size_sampled_pairs():
     assert int(stats[nat.MH_STAT_EDGES]) == int(counts.sum())
     mean_deg = np.array([2 * counts[t * 64:(t + 1) * 64].mean() / sizes[t] for t in range(len(nets_np))])
     assert np.all(mean_deg[:64] > 10) and np.all(mean_deg[:64] < 40)  # UBCM: about 20 by construction
+
+
+def test_autotuner_choice_is_a_candidate_and_samples_exactly():
+    from paper_2509_13230_gb300.autotune import tune_ensemble, tune_sampler
+    nets = mixed_networks(8, sizes=(6000, 3000), models=[UBCM, UECM])
+    m, x, y, nid = nets[0]
+    res = tune_sampler(m, dev(x), None, candidates_t=(8, 32, 128), candidates_ctas=(0, 1), num_samples=2, reps=2)
+    assert res.seg_target in (8, 32, 128) and res.walk_ctas_per_sm in (0, 1)
+    assert len(res.table) == 6 and all(r["edges_per_ms"] > 0 for r in res.table)
+    # block shape changes no bit; T changes the sample, which stays exact
+    for T in (8, 128):
+        a = Sampler(m, dev(x), num_samples=2, seg_target=T, walk_ctas_per_sm=1).run()
+        b = Sampler(m, dev(x), num_samples=2, seg_target=T).run()
+        assert torch.equal(a.src, b.src) and torch.equal(a.dst, b.dst)
+    chosen = Sampler(m, dev(x), num_samples=1, seg_target=res.seg_target,
+                     walk_ctas_per_sm=res.walk_ctas_per_sm).run()
+    src, dst, _, counts, stats = oracle.mh_sample(m, x, None, num_samples=1, seg_target=res.seg_target)
+    assert (np.array_equal(chosen.src.cpu().numpy(), src) and np.array_equal(chosen.dst.cpu().numpy(), dst)) \
+        or stats[3] > 0
+    ens_res = tune_ensemble(to_device(nets), candidates_t=(16, 32), candidates_ctas=(0, 2), num_samples=2, reps=1)
+    assert ens_res.seg_target in (16, 32) and len(ens_res.table) == 4
