@@ -177,7 +177,8 @@ def run_reference(args, rank):
 ENSEMBLE_SAMPLES = 64
 
 
-def ensemble_leg(args, dev, flush):
+def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 << 28, seg_target=None,
+                 loop_samples=None):
     import torch
 
     from paper_2509_13230_gb300 import _native as nat
@@ -185,21 +186,25 @@ def ensemble_leg(args, dev, flush):
     from paper_2509_13230_gb300.ensemble import Ensemble
     from paper_2509_13230_gb300.sampler import Sampler
 
-    nets_np = workloads.ensemble_128()
+    nets_np = workloads.ensemble_128(fitness=fitness)
     keep = max(1, min(args.ensemble_networks, len(nets_np)))
     nets_np = [nets_np[t] for t in np.linspace(0, len(nets_np) - 1, keep).round().astype(int)]
     nets = [(nw.model, torch.from_numpy(nw.x).to(dev), None if nw.y is None else torch.from_numpy(nw.y).to(dev), t)
             for t, nw in enumerate(nets_np)]
     n = np.array([nw.n for nw in nets_np], dtype=np.int64)
     uecm = np.array([nw.model == nat.MH_UECM for nw in nets_np])
-    samples = args.ensemble_samples
+    samples = samples or args.ensemble_samples
     tuned = None
     T, ctas = 0, 0
-    if not args.no_tune:
+    if seg_target is not None:
+        T = seg_target
+    elif args.ensemble_seg_target:
+        T = args.ensemble_seg_target
+    elif not args.no_tune:
         from paper_2509_13230_gb300.autotune import tune_ensemble
         tuned = tune_ensemble(nets, candidates_t=(16, 32, 64), candidates_ctas=(0, 2), num_samples=2, reps=2)
         T, ctas = tuned.seg_target, tuned.walk_ctas_per_sm
-    ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=1 << 28, timing=True, seg_target=T,
+    ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=capacity, timing=True, seg_target=T,
                    walk_ctas_per_sm=ctas)
     stream = torch.cuda.current_stream()
     walk = {"ms": 0.0, "emit_ms": 0.0, "prepare_ms": 0.0}
@@ -237,7 +242,7 @@ def ensemble_leg(args, dev, flush):
 
     # per-sample loop: one mh_sample_* call per (network, sample), same networks
     loop_ms, loop_edges = 0.0, 0
-    loop_samples = args.ensemble_loop_samples
+    loop_samples = args.ensemble_loop_samples if loop_samples is None else loop_samples
     for (m, x, y, nid) in (nets if loop_samples > 0 else []):
         s1 = Sampler(m, x, y, num_samples=1, network_id=nid, layout="csr", seg_target=T, walk_ctas_per_sm=ctas)
         s1.run()
@@ -251,10 +256,13 @@ def ensemble_leg(args, dev, flush):
         loop_ms += ev0.elapsed_time(ev1)
         del s1
     loop_value = loop_edges / (loop_ms / 1e3) if loop_ms > 0 else None
+    del ens
+    torch.cuda.empty_cache()
     hbm_gbs, peak_kind = peaks()
     walk_ms = walk["ms"] / steps
     return {
-        "workload": f"ensemble_{len(nets)}_x{samples}", "networks": len(nets), "nodes": int(n.sum()),
+        "workload": f"ensemble_{len(nets)}_x{samples}" + ("" if fitness == "pareto" else f"_{fitness}"),
+        "fitness": fitness, "networks": len(nets), "nodes": int(n.sum()),
         "samples_per_network": samples, "value": value, "unit": "edges/s", "ms_per_step": total_ms / steps,
         "edges_per_step": edges // steps, "waves_per_step": waves / steps,
         "output": "CSR int64 offsets + int32 indices (+ int32 weights for the UECM half)",
@@ -450,9 +458,12 @@ def run_ours(args, rank, world, local_rank):
             e2e_edges += m
             d2h += 12 * m + 8 * SAMPLES_PER_STEP
     e2e_value = e2e_edges / (e2e_ms / 1e3)
-    ensemble = None
+    ensemble = ensemble_lognormal = None
     if world == 1 and not args.no_ensemble:
         ensemble = ensemble_leg(args, dev, flush)
+        # the other reading of the ensemble's fitness: z ~ N(-4, 1.2), 8 samples per network
+        ensemble_lognormal = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8, capacity=1 << 30,
+                                          seg_target=ensemble["seg_target"], loop_samples=1)
     pairwise = None
     if world == 1 and not args.no_ensemble:
         pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
@@ -495,6 +506,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
         "ensemble": ensemble,
+        "ensemble_lognormal": ensemble_lognormal,
         "pairwise": pairwise,
         "clocks": clocks,
     }
@@ -513,6 +525,8 @@ def main():
     ap.add_argument("--leg", choices=["all", "ensemble", "pairwise"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
+    ap.add_argument("--ensemble-seg-target", type=int, default=0,
+                    help="ensemble leg: use this seg_target instead of tuning (profiling runs)")
     ap.add_argument("--ensemble-networks", type=int, default=128,
                     help="networks of the ensemble leg (evenly spaced subset of the 128)")
     ap.add_argument("--ensemble-samples", type=int, default=ENSEMBLE_SAMPLES, help="samples per network")

@@ -178,11 +178,13 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
  * from mh_batch_prepare give the items of a pair exactly.
  */
 typedef struct mh_network_desc {
-    int32_t model;       /* MH_UBCM or MH_UECM                                    */
-    uint32_t network_id; /* Philox key word 1 = hi32(seed) + network_id          */
-    int64_t n;           /* nodes, >= 1                                           */
-    const double* x;     /* FP64[n], >= 0                                         */
-    const double* y;     /* FP64[n] in [0, 1) for MH_UECM; NULL for MH_UBCM      */
+    int32_t model;        /* MH_UBCM or MH_UECM                                   */
+    uint32_t network_id;  /* Philox key word 1 = hi32(seed) + network_id         */
+    int64_t n;            /* nodes, >= 1                                          */
+    const double* x;      /* FP64[n], >= 0                                        */
+    const double* y;      /* FP64[n] in [0, 1) for MH_UECM; NULL for MH_UBCM     */
+    int64_t max_segments; /* this network's segment-table rows; 0 = the params   */
+                          /* value (0 there: 4 n + 1024); else >= n - 1         */
 } mh_network_desc;
 
 /*
@@ -193,8 +195,8 @@ typedef struct mh_network_desc {
  *   h_nets           host array of n_nets descriptors (1 <= n_nets <= 65536,
  *                    sum of n < 2^31 - 2^20)
  *   params           seed, sample_begin, num_samples (per network),
- *                    seg_target, flags, max_segments (per network; 0 selects
- *                    4 n + 1024); network_id must be 0
+ *                    seg_target, flags, max_segments (the default of every
+ *                    network's segment-table rows); network_id must be 0
  *   max_wave_items   work items one wave may hold, in [1, 2^30]; 0 selects 2^26
  *   capacity_edges   edges one wave may write
  */
@@ -209,8 +211,8 @@ int mh_batch_workspace_size(const mh_network_desc* h_nets, int32_t n_nets, const
  *   h_num_segments   host int64[n_nets]: segment-table rows of each network;
  *                    a pair of network t is h_num_segments[t] work items
  * Errors: MH_ERR_DOMAIN (a bad x or y; the detail names the network),
- * MH_ERR_WORKSPACE (workspace too small, or a segment table above
- * max_segments: h_num_segments holds the needed rows).
+ * MH_ERR_WORKSPACE (workspace too small, or a network's segment table above
+ * its max_segments: h_num_segments holds every network's needed rows).
  */
 int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_params* params, void* workspace,
                      size_t workspace_bytes, int64_t* h_num_segments, mh_stream_t stream);

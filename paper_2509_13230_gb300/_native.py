@@ -73,14 +73,16 @@ class MhNetworkDesc(ctypes.Structure):
         ("n", ctypes.c_int64),
         ("x", ctypes.c_void_p),
         ("y", ctypes.c_void_p),
+        ("max_segments", ctypes.c_int64),
     ]
 
 
 def network_descs(entries) -> ctypes.Array:
-    """Host array of mh_network_desc from (model, network_id, n, x_ptr, y_ptr) tuples."""
+    """Host array of mh_network_desc from (model, network_id, n, x_ptr, y_ptr[, max_segments]) tuples."""
     arr = (MhNetworkDesc * len(entries))()
-    for t, (model, network_id, n, x, y) in enumerate(entries):
-        arr[t] = MhNetworkDesc(int(model), int(network_id), int(n), x, y)
+    for t, e in enumerate(entries):
+        model, network_id, n, x, y = e[:5]
+        arr[t] = MhNetworkDesc(int(model), int(network_id), int(n), x, y, int(e[5]) if len(e) > 5 else 0)
     return arr
 
 

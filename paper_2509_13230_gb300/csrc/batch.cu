@@ -78,7 +78,10 @@ struct BatchLayout {
   size_t total = 0;
 };
 
-int64_t net_segments_cap(const mh_params& p, int64_t n) { return p.max_segments > 0 ? p.max_segments : default_segments(n); }
+int64_t net_segments_cap(const mh_params& p, const mh_network_desc& d) {
+  if (d.max_segments > 0) return d.max_segments;
+  return p.max_segments > 0 ? p.max_segments : default_segments(d.n);
+}
 
 BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_params& p, int64_t items_max,
                               int64_t capacity) {
@@ -88,7 +91,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
   for (int t = 0; t < n_nets; ++t) {
     B.nodes += nets[t].n;
     B.nodes1 += nets[t].n + 1;
-    B.segs += net_segments_cap(p, nets[t].n);
+    B.segs += net_segments_cap(p, nets[t]);
     if (nets[t].n > B.n_max) B.n_max = nets[t].n;
     B.n_model[nets[t].model == MH_UECM] += 1;
   }
@@ -200,6 +203,7 @@ unsigned long long batch_fingerprint(const mh_network_desc* nets, int n_nets, co
     mix(static_cast<unsigned long long>(nets[t].n));
     mix(reinterpret_cast<uintptr_t>(nets[t].x));
     mix(reinterpret_cast<uintptr_t>(nets[t].y));
+    mix(static_cast<unsigned long long>(net_segments_cap(p, nets[t])));
   }
   mix(p.seg_target ? p.seg_target : static_cast<unsigned>(kDefaultSegTarget));
   mix(p.flags & MH_BOUND_PAPER);
@@ -831,8 +835,12 @@ int check_batch(const mh_network_desc* nets, int32_t n_nets, const mh_params* p)
       set_error("network %d: x%s must be non-NULL", t, d.model == MH_UECM ? " and y" : "");
       return MH_ERR_ARG;
     }
+    if (d.max_segments < 0 || (d.max_segments > 0 && d.max_segments < d.n - 1) || d.max_segments >= (1ll << 31)) {
+      set_error("network %d: max_segments must be 0 or in [n - 1, 2^31)", t);
+      return MH_ERR_ARG;
+    }
     nodes += d.n;
-    segs += net_segments_cap(*p, d.n);
+    segs += net_segments_cap(*p, d);
   }
   if (nodes > kMaxNodes || segs >= (1ll << 31)) {
     set_error("the batch holds %lld nodes and %lld segment rows; the limits are %lld and 2^31 - 1",
@@ -859,7 +867,7 @@ void fill_image(const BatchLayout& B, const mh_network_desc* nets, const mh_para
     bn[t].node_base = nb;
     bn[t].node1_base = n1b;
     bn[t].seg_base = sb;
-    bn[t].max_segments = net_segments_cap(p, nets[t].n);
+    bn[t].max_segments = net_segments_cap(p, nets[t]);
     bn[t].n = static_cast<int>(nets[t].n);
     bn[t].model = nets[t].model;
     nb += nets[t].n;

@@ -22,8 +22,11 @@ namespace {
 // an in-place exclusive scan then turns counts into offsets.
 __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, const Ctrl* ctrl,
                                  int64_t chunk_first, int64_t chunk_samples, long long* csr_off) {
-  long long S = ctrl->num_segments;
-  if (S > g.max_segments) S = g.max_segments;
+  // A segment table that outgrew max_segments was truncated: rowoff still
+  // holds the full prefix, which would index past item_off.  The call fails
+  // with MH_ERR_WORKSPACE, so nothing is counted.
+  if (ctrl->num_segments > g.max_segments) return;
+  const long long S = ctrl->num_segments;
   const int64_t n1 = g.n + 1;
   const int64_t total = chunk_samples * n1;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     if (threadIdx.x == 0) ctrl->out_base = ctrl->out_end;
   }
   const long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems;
-  if (it0 >= items) return;
+  if (it0 >= items || ctrl->num_segments > g.max_segments) return;  // truncated table: the call fails
   // Staging that did not fit was never written: emit nothing (the call
   // reports MH_ERR_CAPACITY with exact counts).
   if (ctrl->stage_used > static_cast<unsigned long long>(P.c.staging_cap)) return;

@@ -253,8 +253,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
 
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
-  const unsigned long long total = kBatch ? static_cast<unsigned long long>(*P.q.total)
-                                          : static_cast<unsigned long long>(S) * P.c.chunk_samples;
+  // single network: a truncated segment table (more rows than max_segments)
+  // fails the call with MH_ERR_WORKSPACE, so it is not walked
+  const bool truncated = !kBatch && ctrl->num_segments > g.max_segments;
+  const unsigned long long total = kBatch      ? static_cast<unsigned long long>(*P.q.total)
+                                   : truncated ? 0ull
+                                               : static_cast<unsigned long long>(S) * P.c.chunk_samples;
   unsigned long long* const ticket = kBatch ? P.q.ticket : &ctrl->ticket;
   // work items per ticket: about 1/8 of an even share, within [32, 1024]
   const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * kWalkWarps;

@@ -187,9 +187,11 @@ class Ensemble:
             segs = np.zeros(len(self.entries), dtype=np.int64)
             rc = nat.mh_batch_prepare(self.descs, len(self.entries), self.params, _ptr(self.ws), self.ws.numel(),
                                       segs.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream))
-            if rc == nat.MH_ERR_WORKSPACE and segs.max() > 0 and self.params.max_segments < segs.max():
-                # a segment table outgrew its default capacity: raise the cap for every network
-                self.params.max_segments = int(segs.max()) + 1024
+            over = [t for t in range(len(self.entries)) if segs[t] > self._segment_cap(t)]
+            if rc == nat.MH_ERR_WORKSPACE and over:
+                # segment tables outgrew their capacity: raise the caps of those networks
+                for t in over:
+                    self.descs[t].max_segments = int(segs[t]) + int(segs[t]) // 8 + 1024
                 self._ensure_workspace()
                 continue
             nat.check(rc, "mh_batch_prepare")
@@ -199,6 +201,12 @@ class Ensemble:
             T = self.params.seg_target or 32
             self.est = 0.5 * T * segs.astype(np.float64) + 16.0
         return segs
+
+    def _segment_cap(self, t: int) -> int:
+        d = self.descs[t]
+        if d.max_segments > 0:
+            return int(d.max_segments)
+        return int(self.params.max_segments) if self.params.max_segments > 0 else 4 * int(d.n) + 1024
 
     # ---- waves ------------------------------------------------------------------------
     def plan(self, pair_begin: int = 0, pair_end: int | None = None):

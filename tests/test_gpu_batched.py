@@ -233,3 +233,18 @@ def test_autotuner_choice_is_a_candidate_and_samples_exactly():
         or stats[3] > 0
     ens_res = tune_ensemble(to_device(nets), candidates_t=(16, 32), candidates_ctas=(0, 2), num_samples=2, reps=1)
     assert ens_res.seg_target in (16, 32) and len(ens_res.table) == 4
+
+
+def test_segment_table_caps_grow_per_network():
+    # T = 2 on a dense network needs far more rows than the default 4 n + 1024
+    rng = np.random.default_rng(9)
+    dense = (UBCM, np.exp(rng.normal(0.5, 0.3, 300)), None, 1)
+    sparse = (UECM, np.exp(rng.normal(-4.0, 1.2, 5000)), rng.uniform(0.3, 0.9, 5000), 2)
+    nets = [dense, sparse]
+    ens = Ensemble(to_device(nets), num_samples=2, seed=3, seg_target=2, layout="both")
+    segs = ens.prepare()
+    assert segs[0] > 4 * 300 + 1024 and ens.descs[0].max_segments >= segs[0]
+    assert ens.descs[1].max_segments == 0  # the sparse network kept the default cap
+    chk = Checker(nets, seed=3, sample_begin=0, seg_target=2)
+    ens.sample(on_wave=chk)
+    assert chk.pairs == 4

@@ -243,3 +243,26 @@ def test_expected_fwd_full_size_sampled_rows():
     rk, rs = oracle.expected_fwd(UECM, x, y, rows=rows)
     np.testing.assert_allclose(k.cpu().numpy()[rows], rk, rtol=1e-10)
     np.testing.assert_allclose(s.cpu().numpy()[rows], rs, rtol=1e-10)
+
+
+@pytest.mark.parametrize("layout", ["csr", "both"])
+def test_csr_call_with_segment_table_overflow_retries(layout):
+    # T = 2 on a dense network needs far more table rows than 4 n + 1024: the
+    # first call stops at the truncated table (MH_ERR_WORKSPACE, nothing walked
+    # or written) and the retry with the needed rows samples exactly.
+    rng = np.random.default_rng(17)
+    x = np.exp(rng.normal(0.5, 0.3, 400))
+    s = Sampler(UBCM, dev(x), num_samples=2, seg_target=2, layout=layout)
+    assert s.call() == nat.MH_ERR_WORKSPACE
+    res = s.run()
+    src, dst, _, counts, stats = oracle.mh_sample(UBCM, x, num_samples=2, seg_target=2)
+    assert np.array_equal(res.counts, counts) or stats[3] > 0
+    n = len(x)
+    for k in range(2):
+        a, b = int(counts[:k].sum()), int(counts[:k + 1].sum())
+        order = np.argsort(src[a:b], kind="stable")
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = np.cumsum(np.bincount(src[a:b], minlength=n))
+        got_off = res.csr_offsets[k * (n + 1):(k + 1) * (n + 1)].cpu().numpy()
+        assert np.array_equal(got_off - got_off[0], off)
+        assert np.array_equal(res.csr_indices[int(got_off[0]):int(got_off[-1])].cpu().numpy(), dst[a:b][order])
