@@ -349,6 +349,61 @@ def pairwise_leg(args, dev, sm_mhz):
 
 
 # ---------------------------------------------------------------------------
+# Fit-then-sample leg: degree and strength targets for N = 200,000 (discrete
+# power law 2.5 on [2, 2000], s = k U(1, 5)), x and y fitted to a 1e-8
+# relative residual, then 1,000 weighted networks drawn in batched waves.
+# ---------------------------------------------------------------------------
+FIT_N = 200_000
+FIT_SAMPLES = 1000
+
+
+def fit_leg(args, dev):
+    import torch
+
+    import oracle
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.ensemble import Ensemble
+    from paper_2509_13230_gb300.expected import fit
+
+    k_np, s_np = workloads.degree_strength_targets(n=FIT_N)
+    k_t = torch.from_numpy(k_np).to(dev)
+    s_t = torch.from_numpy(s_np).to(dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    res = fit(k_t, s_t, tol=1e-8)
+    ev1.record(stream)
+    ev1.synchronize()
+    fit_ms = ev0.elapsed_time(ev1)
+    # the oracle's compensated FP64 sums at the fitted parameters, on sampled rows
+    rng = np.random.default_rng(12)
+    rows = rng.choice(FIT_N, 6, replace=False)
+    x_np, y_np = res.x.cpu().numpy(), res.y.cpu().numpy()
+    kk, ss = oracle.expected_fwd(oracle.UECM, x_np, y_np, rows=rows)
+    oracle_resid = float(max(np.max(np.abs(kk - k_np[rows]) / k_np[rows]),
+                             np.max(np.abs(ss - s_np[rows]) / s_np[rows])))
+    ens = Ensemble([(nat.MH_UECM, res.x, res.y, 0)], num_samples=FIT_SAMPLES, layout="coo", capacity=1 << 27)
+    ens.sample()                                 # warm-up: buffers, estimates
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ens.prepare()
+    counts, _ = ens.sample()
+    ev1.record(stream)
+    ev1.synchronize()
+    sample_ms = ev0.elapsed_time(ev1)
+    edges = int(counts.sum())
+    return {"workload": f"fit_uecm_n{FIT_N // 1000}k_then_x{FIT_SAMPLES}", "n": FIT_N,
+            "fit_ms": fit_ms, "residual": res.residual, "residual_oracle_sampled_rows": oracle_resid,
+            "adam_steps": res.adam_steps, "newton_steps": res.newton_steps,
+            "sample_ms": sample_ms, "samples": FIT_SAMPLES, "edges": edges,
+            "edges_per_s": edges / (sample_ms / 1e3), "mean_degree": 2.0 * edges / FIT_SAMPLES / FIT_N,
+            "target_mean_degree": float(k_np.mean()),
+            "output": "COO int32 + w int32, 1,000 samples in batched waves"}
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -464,9 +519,10 @@ def run_ours(args, rank, world, local_rank):
         # the other reading of the ensemble's fitness: z ~ N(-4, 1.2), 8 samples per network
         ensemble_lognormal = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8, capacity=1 << 30,
                                           seg_target=ensemble["seg_target"], loop_samples=1)
-    pairwise = None
+    pairwise = fitted = None
     if world == 1 and not args.no_ensemble:
         pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
+        fitted = fit_leg(args, dev)
     if world > 1:
         dist.barrier()
 
@@ -508,6 +564,7 @@ def run_ours(args, rank, world, local_rank):
         "ensemble": ensemble,
         "ensemble_lognormal": ensemble_lognormal,
         "pairwise": pairwise,
+        "fit_then_sample": fitted,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -522,7 +579,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise"], default="all",
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--ensemble-seg-target", type=int, default=0,
@@ -546,6 +603,10 @@ def main():
         dev = torch.device("cuda", local_rank)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps({"ensemble": ensemble_leg(args, dev, flush)}), flush=True)
+    elif args.leg == "fit":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"fit_then_sample": fit_leg(args, torch.device("cuda", local_rank))}), flush=True)
     elif args.leg == "pairwise":
         import torch
         torch.cuda.set_device(local_rank)

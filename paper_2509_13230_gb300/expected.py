@@ -9,10 +9,14 @@ stored (the maximum-likelihood conditions of Sec. 2.2 and Sec. 2.5).
 ``fit`` finds x (and y) whose expected degrees (and strengths) match target
 sequences, the inference step that precedes sampling (Sec. 3 uses a
 quasi-Newton solver for it): Adam on log-parameters through the autograd
-Function, then Newton steps on the per-node 1x1 (UBCM) or 2x2 (UECM)
-diagonal blocks of the Jacobian until the largest relative residual is at
-most ``tol``.  The diagonal blocks come from the backward kernel itself: with
-dL/d<k> = 1 and dL/d<s> = 0 it returns 2 d<k_i>/dx_i and 2 d<k_i>/dy_i.
+Function, then inexact Newton steps until the largest relative residual is
+at most ``tol``.  In log-parameters (theta = log x, phi = log y) the
+Jacobian of (<k>, <s>) is symmetric: <k_i> and <s_i> are the derivatives of
+the model's log-partition function, and pair by pair
+d<k_i>/dtheta_j = p_ij (1 - p_ij), d<k_i>/dphi_j = d<s_j>/dtheta_i = A / D^2.
+So J v equals the backward kernel's vector-Jacobian product times x (and y),
+and each Newton step solves J d = -(residual) by conjugate gradients
+preconditioned with the per-node 1x1 / 2x2 diagonal blocks.
 """
 from __future__ import annotations
 
@@ -70,14 +74,87 @@ def _residual(model, x, y, k_t, s_t):
     rk = (k - k_t) / k_t
     rs = None if s is None else (s - s_t) / s_t
     worst = float(rk.abs().max()) if rs is None else max(float(rk.abs().max()), float(rs.abs().max()))
-    return k, s, rk, rs, worst
+    merit = float((rk * rk).sum()) + (0.0 if rs is None else float((rs * rs).sum()))
+    return k, s, rk, rs, worst, merit
+
+
+def _diagonal_blocks(model, x, y, n):
+    """Per-node d<k_i>/dtheta_i (UBCM) or the 2x2 block of d(<k_i>, <s_i>) /
+    d(theta_i, phi_i) (UECM).  The backward kernel with all-ones dL/d<k>
+    returns 2 d<k_i>/dx_i (each pair term enters both endpoints' sums), so
+    half of it times x_i is the diagonal entry."""
+    ones = torch.ones(n, dtype=torch.float64, device=x.device)
+    if model == nat.MH_UBCM:
+        gx, _ = expected_bwd(model, x, None, ones)
+        return (0.5 * gx * x,)
+    zeros = torch.zeros_like(ones)
+    gx_k, gy_k = expected_bwd(model, x, y, ones, zeros)
+    gx_s, gy_s = expected_bwd(model, x, y, zeros, ones)
+    return 0.5 * gx_k * x, 0.5 * gy_k * y, 0.5 * gx_s * x, 0.5 * gy_s * y
+
+
+def _jvp(model, x, y, v):
+    """J v in log-parameters (J symmetric: the vector-Jacobian product)."""
+    if model == nat.MH_UBCM:
+        gx, _ = expected_bwd(model, x, None, v[0].contiguous())
+        return (gx * x,)
+    gx, gy = expected_bwd(model, x, y, v[0].contiguous(), v[1].contiguous())
+    return gx * x, gy * y
+
+
+def _precond(blocks, r):
+    """Solves each node's diagonal block against r."""
+    if len(blocks) == 1:
+        return (r[0] / blocks[0],)
+    a11, a12, a21, a22 = blocks
+    det = a11 * a22 - a12 * a21
+    return (r[0] * a22 - a12 * r[1]) / det, (a11 * r[1] - a21 * r[0]) / det
+
+
+def _dot(u, v):
+    return float(sum((a * b).sum() for a, b in zip(u, v)))
+
+
+def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int):
+    """Preconditioned conjugate gradients on J d = b, started from the
+    block-diagonal solution."""
+    d = _precond(blocks, b)
+    Jd = _jvp(model, x, y, d)
+    r = tuple(bi - ji for bi, ji in zip(b, Jd))
+    bnorm = math.sqrt(_dot(b, b))
+    z = _precond(blocks, r)
+    p = z
+    rz = _dot(r, z)
+    for _ in range(maxiter):
+        if math.sqrt(_dot(r, r)) <= rtol * bnorm:
+            break
+        Ap = _jvp(model, x, y, p)
+        pAp = _dot(p, Ap)
+        if not pAp > 0.0:
+            break
+        alpha = rz / pAp
+        d = tuple(di + alpha * pi for di, pi in zip(d, p))
+        r = tuple(ri - alpha * ai for ri, ai in zip(r, Ap))
+        z = _precond(blocks, r)
+        rz_new = _dot(r, z)
+        p = tuple(zi + (rz_new / rz) * pi for zi, pi in zip(z, p))
+        rz = rz_new
+    return d
 
 
 def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None, y0=None, tol: float = 1e-8,
-        adam_steps: int = 200, lr: float = 0.05, newton_steps: int = 200, verbose: bool = False) -> FitResult:
+        adam_steps: int = 10, lr: float = 0.05, newton_steps: int = 100, cg_iters: int = 12,
+        cg_rtol: float = 0.05, max_step: float = 2.0, verbose: bool = False) -> FitResult:
     """Fit x (UBCM) or x, y (UECM) so that the expected degrees (and strengths)
     equal the targets.  Targets are float64 CUDA tensors with k_i > 0 (and
-    s_i > k_i, since every weight is at least 1)."""
+    s_i > k_i, since every weight is at least 1).
+
+    Adam stage: adam_steps steps on the mean squared relative residual (a
+    warm start; the Newton stage converges from the sparse-limit start too).
+    Newton stage: each step solves J d = -(<k> - k, <s> - s) by up to
+    cg_iters preconditioned conjugate-gradient iterations (relative residual
+    cg_rtol), scales d to at most max_step per log-parameter, and backtracks
+    on the sum of squared relative residuals."""
     model = nat.MH_UECM if s_target is not None else nat.MH_UBCM
     k_t = k_target.to(torch.float64).contiguous()
     s_t = None if s_target is None else s_target.to(torch.float64).contiguous()
@@ -115,56 +192,41 @@ def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None
             if verbose:
                 print("adam", steps, float(loss.detach()))
 
-    # --- Newton on the diagonal blocks ---
+    # --- inexact Newton (preconditioned CG), line search on the squared residuals ---
     theta = theta.detach()
-    phi = None if phi is None else phi.detach()
-    ones = torch.ones(n, dtype=torch.float64, device=k_t.device)
-    zeros = torch.zeros_like(ones)
+    phi = None if phi is None else torch.clamp(phi.detach(), max=-1e-9)
     x = torch.exp(theta)
     y = None if phi is None else torch.exp(phi)
-    _, _, rk, rs, worst = _residual(model, x, y, k_t, s_t)
+    k, s, rk, rs, worst, merit = _residual(model, x, y, k_t, s_t)
     it = 0
     for it in range(1, newton_steps + 1):
         if worst <= tol:
             it -= 1
             break
-        if model == nat.MH_UBCM:
-            gx, _ = expected_bwd(model, x, None, ones)
-            dk_dtheta = 0.5 * gx * x
-            step = -(rk * k_t) / dk_dtheta
-            step = torch.clamp(step, -1.0, 1.0)
-            t = 1.0
-            while True:
-                x_new = torch.exp(theta + t * step)
-                _, _, rk_new, _, worst_new = _residual(model, x_new, None, k_t, None)
-                if worst_new < worst or t < 1e-3:
-                    break
-                t *= 0.5
-            theta = theta + t * step
-            x, rk, worst = x_new, rk_new, worst_new
-        else:
-            gx_k, gy_k = expected_bwd(model, x, y, ones, zeros)
-            gx_s, gy_s = expected_bwd(model, x, y, zeros, ones)
-            a11, a12 = 0.5 * gx_k * x, 0.5 * gy_k * y   # d<k>/dtheta, d<k>/dphi
-            a21, a22 = 0.5 * gx_s * x, 0.5 * gy_s * y   # d<s>/dtheta, d<s>/dphi
-            b1, b2 = -rk * k_t, -rs * s_t
-            det = a11 * a22 - a12 * a21
-            d_theta = (b1 * a22 - a12 * b2) / det
-            d_phi = (a11 * b2 - a21 * b1) / det
-            d_theta = torch.clamp(d_theta, -1.0, 1.0)
-            d_phi = torch.clamp(d_phi, -1.0, 1.0)
-            t = 1.0
-            while True:
-                th_new = theta + t * d_theta
-                ph_new = torch.clamp(phi + t * d_phi, max=-1e-9)
-                x_new, y_new = torch.exp(th_new), torch.exp(ph_new)
-                _, _, rk_new, rs_new, worst_new = _residual(model, x_new, y_new, k_t, s_t)
-                if worst_new < worst or t < 1e-3:
-                    break
-                t *= 0.5
-            theta, phi = th_new, ph_new
-            x, y, rk, rs, worst = x_new, y_new, rk_new, rs_new, worst_new
-        history.append(("newton", it, worst))
+        blocks = _diagonal_blocks(model, x, y, n)
+        b = (k_t - k,) if model == nat.MH_UBCM else (k_t - k, s_t - s)
+        d = _newton_direction(model, x, y, blocks, b, rtol=cg_rtol, maxiter=cg_iters)
+        biggest = max(float(di.abs().max()) for di in d)
+        if biggest > max_step:
+            d = tuple(di * (max_step / biggest) for di in d)
+        t = 1.0
+        accepted = False
+        while t >= 1.0 / 256:
+            th_new = theta + t * d[0]
+            ph_new = None if phi is None else torch.clamp(phi + t * d[1], max=-1e-9)
+            x_new = torch.exp(th_new)
+            y_new = None if ph_new is None else torch.exp(ph_new)
+            k_new, s_new, rk_new, rs_new, worst_new, merit_new = _residual(model, x_new, y_new, k_t, s_t)
+            if merit_new < (1.0 - 1e-4 * t) * merit:
+                accepted = True
+                break
+            t *= 0.5
+        if not accepted:
+            history.append(("newton-stalled", it, worst))
+            break
+        theta, phi, x, y = th_new, ph_new, x_new, y_new
+        k, s, rk, rs, worst, merit = k_new, s_new, rk_new, rs_new, worst_new, merit_new
+        history.append(("newton", it, worst, t))
         if verbose:
-            print("newton", it, worst)
+            print("newton", it, worst, merit, t)
     return FitResult(x=x, y=y, residual=worst, adam_steps=steps, newton_steps=it, history=history)

@@ -80,3 +80,59 @@ def test_fit_uecm_to_1e8():
     k_fit, s_fit = oracle.expected_fwd(oracle.UECM, res.x.cpu().numpy(), res.y.cpu().numpy())
     assert np.max(np.abs(k_fit - k_t) / k_t) <= 2e-8
     assert np.max(np.abs(s_fit - s_t) / s_t) <= 2e-8
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_jacobian_vector_product_is_the_symmetric_vjp(model):
+    # fit() uses J v = (backward kernel with upstream v) * (x, y) in
+    # log-parameters; check it against central differences of the oracle's
+    # sums along a random direction.
+    from paper_2509_13230_gb300.expected import _jvp
+    rng = np.random.default_rng(16)
+    n = 300
+    theta = rng.normal(-1.5, 1.0, n)
+    phi = np.log(rng.uniform(0.2, 0.9, n)) if model == nat.MH_UECM else None
+    v = [rng.normal(size=n)] + ([rng.normal(size=n)] if model == nat.MH_UECM else [])
+    x, y = np.exp(theta), None if phi is None else np.exp(phi)
+    got = _jvp(model, dev(x), None if y is None else dev(y), tuple(dev(a) for a in v))
+    eps = 1e-6
+
+    def sums(sign):
+        xs = np.exp(theta + sign * eps * v[0])
+        ys = None if phi is None else np.exp(phi + sign * eps * v[1])
+        return oracle.expected_fwd(model, xs, ys)
+
+    (kp, sp), (km, sm) = sums(1), sums(-1)
+    fd = [(kp - km) / (2 * eps)] + ([(sp - sm) / (2 * eps)] if model == nat.MH_UECM else [])
+    for g, f in zip(got, fd):
+        np.testing.assert_allclose(g.cpu().numpy(), f, rtol=1e-6, atol=1e-8 * np.abs(f).max())
+
+
+def test_fit_then_sample_full_size():
+    """The fit-then-sample workload at full size: N = 200,000 power-law degree
+    targets with strengths s = k U(1, 5), fitted to 1e-8 (checked by the
+    oracle's sums on sampled rows), then samples drawn in batched waves and
+    checked against the oracle's samples of the fitted network."""
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.ensemble import Ensemble
+    k_np, s_np = workloads.degree_strength_targets(n=200_000)
+    res = fit(dev(k_np), dev(s_np), tol=1e-8)
+    assert res.residual <= 1e-8, res.history[-4:]
+    x, y = res.x.cpu().numpy(), res.y.cpu().numpy()
+    rows = np.random.default_rng(18).choice(len(x), 8, replace=False)
+    kk, ss = oracle.expected_fwd(oracle.UECM, x, y, rows=rows)
+    assert np.max(np.abs(kk - k_np[rows]) / k_np[rows]) <= 2e-8
+    assert np.max(np.abs(ss - s_np[rows]) / s_np[rows]) <= 2e-8
+    ens = Ensemble([(nat.MH_UECM, res.x, res.y, 0)], num_samples=40, layout="coo", capacity=1 << 25)
+    got = {}
+
+    def keep(w):
+        for k in range(w.pair_count):
+            if int(w.samples[k]) in (0, 39):
+                got[int(w.samples[k])] = [a.cpu().numpy() for a in w.coo(k)]
+
+    counts, _ = ens.sample(on_wave=keep)
+    assert abs(2 * counts.mean() / len(x) - k_np.mean()) < 0.05 * k_np.mean()
+    for smp, (gs, gd, gw) in got.items():
+        src, dst, w, _, stats = oracle.mh_sample(oracle.UECM, x, y, sample_begin=smp, num_samples=1)
+        assert (np.array_equal(gs, src) and np.array_equal(gd, dst) and np.array_equal(gw, w)) or stats[3] > 0
