@@ -404,6 +404,30 @@ def fit_leg(args, dev):
 
 
 # ---------------------------------------------------------------------------
+# Replicas: rank r draws samples [r S, (r + 1) S) of the same network (the
+# counters are keyed by sample, so the union is the single-GPU ensemble);
+# the job's time is the slowest rank's and its edges are all ranks' edges.
+# ---------------------------------------------------------------------------
+def rank_samples(rank: int, per_rank: int = SAMPLES_PER_STEP):
+    """(first sample index, sample count) of a rank."""
+    return rank * per_rank, per_rank
+
+
+def reduce_over_ranks(total_ms: float, edges: float, world: int, device):
+    """(max over ranks of the timed milliseconds, sum over ranks of the edges)."""
+    if world <= 1:
+        return total_ms, float(edges)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, float(edges)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -426,7 +450,7 @@ def run_ours(args, rank, world, local_rank):
     net = workload()
     x = torch.from_numpy(net.x).to(dev)
     y = torch.from_numpy(net.y).to(dev)
-    first = rank * SAMPLES_PER_STEP
+    first, _ = rank_samples(rank)
     s = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, sample_begin=first)
     s.run()                                     # sizes the output buffers
     s.flags |= nat.MH_TIMING
@@ -458,15 +482,7 @@ def run_ours(args, rank, world, local_rank):
     if rejected(clocks):
         total_ms, walk_ms, edges, launches, clocks = timed_region()
         clocks["remeasured"] = True
-    t = torch.tensor([total_ms, float(edges)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        max_ms, all_edges = float(tmax[0]), float(tsum[1])
-    else:
-        max_ms, all_edges = total_ms, float(edges)
+    max_ms, all_edges = reduce_over_ranks(total_ms, edges, world, dev)
     value = all_edges / (max_ms / 1e3)
 
     # per-sample launch loop: the same samples drawn by one call each
