@@ -259,6 +259,21 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 <<
     del ens
     torch.cuda.empty_cache()
     hbm_gbs, peak_kind = peaks()
+    # the oracle on a bounded sample of the same ensemble: whole samples of
+    # the networks in size order, up to about 8 s of one host core
+    import oracle
+    oracle.load()
+    cpu_edges, cpu_s, cpu_pairs = 0, 0.0, 0
+    for t in np.argsort(n):
+        if cpu_s > 8.0:
+            break
+        nw = nets_np[t]
+        t0 = time.perf_counter()
+        _, _, _, c, _ = oracle.mh_sample(nw.model, nw.x, nw.y, network_id=nets[t][3], num_samples=1,
+                                         seg_target=T or 32)
+        cpu_s += time.perf_counter() - t0
+        cpu_edges += int(c.sum())
+        cpu_pairs += 1
     walk_ms = walk["ms"] / steps
     return {
         "workload": f"ensemble_{len(nets)}_x{samples}" + ("" if fitness == "pareto" else f"_{fitness}"),
@@ -272,6 +287,15 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 <<
         "scan_emit_ms_per_step": walk["emit_ms"] / steps,
         "write_gbs_of_walk": out_bytes / steps / (walk_ms / 1e3) / 1e9 if walk_ms > 0 else None,
         "hbm_peak": hbm_gbs, "peak_kind": peak_kind,
+        "roofline": {"bound": "hbm", "kernel": "walk_kernel (batched, both models)",
+                     "achieved": out_bytes / steps / (walk_ms / 1e3) / 1e9 if walk_ms > 0 else None,
+                     "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": (out_bytes / steps / (walk_ms / 1e3) / 1e9) / hbm_gbs if walk_ms > 0 else None,
+                     "traffic": None, "basis": "CSR output bytes (4 B index, 4 B UECM weight, 8 B per offset) / "
+                                               "walk time of the step (both walks' fork-join interval per wave)"},
+        "cpu_baseline": {"value": cpu_edges / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one sample of each of the {cpu_pairs} smallest networks of the ensemble, "
+                                   f"serial FP64 walk, {cpu_s:.1f} s on one host core"},
         "per_sample_loop": None if loop_value is None else {
             "value": loop_value, "unit": "edges/s", "calls": len(nets) * loop_samples,
             "samples_per_network": loop_samples, "batched_over_loop": value / loop_value},
@@ -451,7 +475,16 @@ def run_ours(args, rank, world, local_rank):
     x = torch.from_numpy(net.x).to(dev)
     y = torch.from_numpy(net.y).to(dev)
     first, _ = rank_samples(rank)
-    s = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, sample_begin=first)
+    # segment length and walk block shape from the autotuner (probe: the same
+    # 10-sample call, device time); every rank tunes the same workload alike
+    T, ctas, tuned = 0, 0, None
+    if not args.no_tune:
+        from paper_2509_13230_gb300.autotune import tune_sampler
+        tuned = tune_sampler(nat.MH_UECM, x, y, candidates_t=(8, 16, 32), candidates_ctas=(0,),
+                             num_samples=SAMPLES_PER_STEP, reps=5)
+        T, ctas = tuned.seg_target, tuned.walk_ctas_per_sm
+    s = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, sample_begin=first, seg_target=T,
+                walk_ctas_per_sm=ctas)
     s.run()                                     # sizes the output buffers
     s.flags |= nat.MH_TIMING
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -462,6 +495,7 @@ def run_ours(args, rank, world, local_rank):
             nat.check(s.call(), "mh_sample_weighted")
         barrier()
         total_ms, walk_ms, edges, launches = 0.0, [], 0, 0
+        phases.clear()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
             for _ in range(args.steps):
@@ -473,11 +507,13 @@ def run_ours(args, rank, world, local_rank):
                 total_ms += ev0.elapsed_time(ev1)
                 info = nat.mh_last_call_info()
                 walk_ms.append(info.walk_ms)
+                phases.append((info.prepare_ms, info.walk_ms, info.emit_ms, info.total_ms))
                 launches += info.kernel_launches
                 edges += int(s.h_counts.sum())
         barrier()
         return total_ms, walk_ms, edges, launches, clk.summary()
 
+    phases = []
     total_ms, walk_ms, edges, launches, clocks = timed_region()
     if rejected(clocks):
         total_ms, walk_ms, edges, launches, clocks = timed_region()
@@ -486,7 +522,7 @@ def run_ours(args, rank, world, local_rank):
     value = all_edges / (max_ms / 1e3)
 
     # per-sample launch loop: the same samples drawn by one call each
-    s1 = Sampler(nat.MH_UECM, x, y, num_samples=1, sample_begin=first)
+    s1 = Sampler(nat.MH_UECM, x, y, num_samples=1, sample_begin=first, seg_target=T, walk_ctas_per_sm=ctas)
     s1.run()
     for _ in range(args.warmup):
         s1.call()
@@ -553,7 +589,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if os.path.exists(WALK_PROFILE):
         prof = json.load(open(WALK_PROFILE))
-        if prof.get("sources_sha") == sources_hash():
+        if prof.get("sources_sha") == sources_hash() and prof.get("seg_target", 32) == (T or 32):
             traffic = prof.get("dram_bytes_per_launch")
     # CPU oracle on a bounded sample of the same workload (rank 0, N = 1 only)
     cpu = None
@@ -567,6 +603,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": net.n, "samples_per_step": SAMPLES_PER_STEP * world,
+                   "seg_target": T or 32, "walk_ctas_per_sm": ctas,
+                   "autotune": None if tuned is None else tuned.table,
                    "output": "coo int32 + w int32 (12 B/edge)", "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
@@ -576,6 +614,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 16 * net.n,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
+        "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit", "call"),
+                                       (float(v) for v in np.mean(np.array(phases), axis=0)))),
         "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
         "ensemble": ensemble,
         "ensemble_lognormal": ensemble_lognormal,
