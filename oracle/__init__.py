@@ -13,6 +13,10 @@ Everything here is plain and slow on purpose:
   FP64 with correctly rounded summation (``math.fsum``).
 * ``graph_probabilities`` enumerates every simple graph of a tiny network
   and multiplies the independent pair probabilities (Eq. 1 / Eq. 3).
+* ``bip_*`` are the same for bipartite and directed networks (Sec. 2.6): the
+  rows are the + set, the candidates the - set; a directed network uses the
+  out-parameters as the + set and the in-parameters as the - set, without
+  the pairs (i, i).
 
 Notation: x_i = exp(-alpha_i), y_i = exp(-beta_i) (the paper's alpha, beta).
 """
@@ -64,6 +68,13 @@ def _declare(lib):
     lib.orc_mh_sample.restype = i64
     lib.orc_bf_sample.argtypes = [i32, vp, vp, i64, u64, u32, vp, vp, vp, i64, vp]
     lib.orc_bf_sample.restype = i64
+    lib.orc_bip_partition.argtypes = [i32, vp, vp, i64, vp, vp, i64, i64, vp, vp, vp, vp, i64, vp, vp]
+    lib.orc_bip_partition.restype = i64
+    lib.orc_bip_sample.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, u64, u32, u32, u32, i64, vp, vp, vp, i64,
+                                   vp, vp]
+    lib.orc_bip_sample.restype = i64
+    lib.orc_bip_bf_sample.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, u64, u32, vp, vp, vp, i64, vp]
+    lib.orc_bip_bf_sample.restype = i64
     return lib
 
 
@@ -298,3 +309,98 @@ def graph_codes(src, dst, counts, n):
         codes[s] = code
         pos += int(c)
     return codes
+
+
+# --------------------------------------------------------------------------
+# Bipartite and directed networks (Sec. 2.6)
+# --------------------------------------------------------------------------
+def bip_partition(model, xp, yp, xm, ym, seg_target=32, lib=None):
+    """Row-segment table of a bipartite network: (+ rank, k, a, b) with a, b
+    in - ranks, plus both node orders."""
+    lib = lib or load()
+    xp, xm = _f64(xp), _f64(xm)
+    yp = _f64(yp) if model == UECM else None
+    ym = _f64(ym) if model == UECM else None
+    np_, nm = len(xp), len(xm)
+    cap = max(4 * np_ + 1024, 16)
+    while True:
+        row = np.zeros(cap, np.int32)
+        k = np.zeros(cap, np.int32)
+        a = np.zeros(cap, np.int64)
+        b = np.zeros(cap, np.int64)
+        pp = np.zeros(max(np_, 1), np.int32)
+        pm = np.zeros(max(nm, 1), np.int32)
+        total = lib.orc_bip_partition(model, _ptr(xp), _ptr(yp), np_, _ptr(xm), _ptr(ym), nm, int(seg_target),
+                                      _ptr(row), _ptr(k), _ptr(a), _ptr(b), cap, _ptr(pp), _ptr(pm))
+        if total <= cap:
+            return dict(row=row[:total], k=k[:total], a=a[:total], b=b[:total], perm_plus=pp[:np_],
+                        perm_minus=pm[:nm])
+        cap = int(total)
+
+
+def bip_sample(model, xp, yp, xm, ym, *, directed=False, seed=0, network_id=0, sample_begin=0, num_samples=1,
+               seg_target=32, lib=None):
+    """Serial walk of a bipartite (or directed) network.  Returns (src, dst, w
+    or None, counts, stats) with src a + id and dst a - id (out / in ids when
+    directed); stats as in mh_sample."""
+    lib = lib or load()
+    xp, xm = _f64(xp), _f64(xm)
+    yp = _f64(yp) if model == UECM else None
+    ym = _f64(ym) if model == UECM else None
+    cap = 1024
+    while True:
+        src = np.zeros(cap, np.int32)
+        dst = np.zeros(cap, np.int32)
+        w = np.zeros(cap, np.int32) if model == UECM else None
+        counts = np.zeros(max(num_samples, 1), np.int64)
+        st = np.zeros(4, np.uint64)
+        total = lib.orc_bip_sample(model, _ptr(xp), _ptr(yp), len(xp), _ptr(xm), _ptr(ym), len(xm), int(directed),
+                                   int(seed), int(network_id), int(sample_begin), int(num_samples), int(seg_target),
+                                   _ptr(src), _ptr(dst), _ptr(w), cap, _ptr(counts), _ptr(st))
+        if total < 0:
+            raise ValueError("weight above INT32_MAX, or a directed network with unequal sets")
+        if total <= cap:
+            return src[:total], dst[:total], None if w is None else w[:total], counts[:num_samples], st
+        cap = int(total)
+
+
+def bip_bf_sample(model, xp, yp, xm, ym, *, directed=False, seed=0, sample=0, lib=None):
+    """Brute-force sample of a bipartite (or directed) network: (src, dst, w or None, evaluations)."""
+    lib = lib or load()
+    xp, xm = _f64(xp), _f64(xm)
+    yp = _f64(yp) if model == UECM else None
+    ym = _f64(ym) if model == UECM else None
+    cap = len(xp) * len(xm) + 1
+    src = np.zeros(cap, np.int32)
+    dst = np.zeros(cap, np.int32)
+    w = np.zeros(cap, np.int32) if model == UECM else None
+    ev = ctypes.c_uint64(0)
+    total = lib.orc_bip_bf_sample(model, _ptr(xp), _ptr(yp), len(xp), _ptr(xm), _ptr(ym), len(xm), int(directed),
+                                  int(seed), int(sample), _ptr(src), _ptr(dst), _ptr(w), cap, ctypes.byref(ev))
+    return src[:total], dst[:total], None if w is None else w[:total], int(ev.value)
+
+
+def bip_pair_list(n_plus, n_minus, directed=False):
+    return [(u, v) for u in range(n_plus) for v in range(n_minus) if not (directed and u == v)]
+
+
+def bip_graph_probabilities(model, alpha_p, alpha_m, beta_p=None, beta_m=None, directed=False):
+    """Probability of every graph on the pairs of bip_pair_list (independent
+    pairs, Eq. 1 / Eq. 3 with one endpoint in each set), in the paper's
+    alpha/beta notation.  Graph g has bit t set when pair t is an edge."""
+    pairs = bip_pair_list(len(alpha_p), len(alpha_m), directed)
+    probs = []
+    for (u, v) in pairs:
+        if model == UBCM:
+            e = math.exp(-alpha_p[u] - alpha_m[v])
+            probs.append(e / (1.0 + e))
+        else:
+            num = math.exp(-alpha_p[u] - alpha_m[v] - beta_p[u] - beta_m[v])
+            probs.append(num / (1.0 - math.exp(-beta_p[u] - beta_m[v]) + num))
+    out = np.zeros(1 << len(pairs))
+    for g, bits in enumerate(itertools.product((0, 1), repeat=len(pairs))):
+        pr = 1.0
+        for t, b in enumerate(reversed(bits)):
+            pr *= probs[t] if b else (1.0 - probs[t])
+        out[g] = pr
+    return out, np.array(probs)

@@ -22,6 +22,9 @@
  *   orc_partition       row-segment table (restart of the proposal bound)
  *   orc_mh_sample       serial Miller-Hagberg walk, Sec. 2.3-2.5, Algorithm 1
  *   orc_bf_sample       brute-force Bernoulli sampler, Sec. 2.2 / Sec. 3
+ *   orc_bip_partition   row-segment table of a bipartite network, Sec. 2.6
+ *   orc_bip_sample      serial walk of bipartite and directed networks, Sec. 2.6
+ *   orc_bip_bf_sample   brute-force sampler of bipartite and directed networks
  */
 #include <math.h>
 #include <stdint.h>
@@ -544,6 +547,324 @@ int64_t orc_bf_sample(int model, const double* x, const double* y, int64_t n, ui
             }
             evals += 1;
             uint32_t ctr[4] = {(uint32_t)u, (uint32_t)v, 0xB0F0B0F0u, sample};
+            uint32_t rnd[4];
+            orc_philox4x32_10(ctr, key, rnd);
+            double V = unit_open1(rnd[1], rnd[0]);
+            if (V < p) {
+                int32_t wt = 1;
+                if (model == ORC_UECM && r > 0.0) {
+                    double Uw = unit_open0(rnd[3], rnd[2]);
+                    double tw = log(Uw) / log(r);
+                    wt = (tw >= 2147483646.0) ? 2147483647 : 1 + (int32_t)floor(tw);
+                }
+                if (count < cap) {
+                    src[count] = (int32_t)u;
+                    dst[count] = (int32_t)v;
+                    if (w) w[count] = wt;
+                }
+                count += 1;
+            }
+        }
+    }
+    if (evaluations) *evaluations = evals;
+    return count;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bipartite and directed networks (Sec. 2.6).  The rows are the nodes of    */
+/* the + set, each walked over all nodes of the - set; each set is sorted by */
+/* its own key (descending x, or a = x*y for the UECM form), so p_ij is      */
+/* non-increasing along a row and the same geometric skipping applies:       */
+/*   UBCM form  p_ij = x+_i x-_j / (1 + x+_i x-_j)                           */
+/*   UECM form  p_ij = A / (1 - r + A),  A = a+_i a-_j,  r = y+_i y-_j        */
+/*   bound c of a segment [a, b) of row i: y+_i max_{j >= a} y-_j (>= r_ij)  */
+/* A directed network is the bipartite one with the out-parameters of every  */
+/* node as the + set and its in-parameters as the - set (the same ids), and  */
+/* without the pairs (i, i): the walk of row i skips the - rank e_i of node  */
+/* i.  Candidates are then counted in "virtual" positions that leave e_i     */
+/* out: virtual v is - rank v for v < e_i and v + 1 from e_i on; p stays     */
+/* non-increasing along virtual positions.  The segment table is the        */
+/* bipartite one in - ranks (a segment that holds only e_i has no candidate).*/
+/* Random words as in the one-set walk, with i the + rank of the row.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    net_t R;         /* + set (rows)                                        */
+    net_t C;         /* - set (candidates)                                  */
+    int32_t* rank_c; /* - id -> - rank                                      */
+    int directed;
+} bip_t;
+
+static void bip_build(bip_t* B, int model, const double* xp, const double* yp, int64_t np, const double* xm,
+                      const double* ym, int64_t nm, int directed)
+{
+    net_build(&B->R, model, xp, yp, np, 0u);
+    net_build(&B->C, model, xm, ym, nm, 0u);
+    B->directed = directed;
+    B->rank_c = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nm > 0 ? nm : 1));
+    for (int64_t j = 0; j < nm; ++j) B->rank_c[B->C.perm[j]] = (int32_t)j;
+}
+
+static void bip_free(bip_t* B)
+{
+    net_free(&B->R);
+    net_free(&B->C);
+    free(B->rank_c);
+}
+
+static double bip_prob(const bip_t* B, int64_t i, int64_t j)
+{
+    if (B->R.model == ORC_UBCM) {
+        double z = B->R.xs[i] * B->C.xs[j];
+        return z / (1.0 + z);
+    }
+    double A = B->R.as[i] * B->C.as[j];
+    double r = B->R.ys[i] * B->C.ys[j];
+    return A / ((1.0 - r) + A);
+}
+
+static double bip_prob_hat(const bip_t* B, int64_t i, int64_t j, double c)
+{
+    double A = B->R.as[i] * B->C.as[j];
+    return A / ((1.0 - c) + A);
+}
+
+static double bip_bound_c(const bip_t* B, int64_t i, int64_t a)
+{
+    return B->R.ys[i] * B->C.ymax[a];
+}
+
+/* Cost weight of row i over the whole - set (bound at a = 0). */
+static double bip_row_weight(const bip_t* B, int64_t i)
+{
+    if (B->R.model == ORC_UBCM) return B->R.xs[i];
+    return B->R.as[i] / (1.0 - bip_bound_c(B, i, 0));
+}
+
+/* First - rank j with w v_j < 1, else m. */
+static int64_t bip_unit_cut(const bip_t* B, double w)
+{
+    const double* v = (B->C.model == ORC_UBCM) ? B->C.xs : B->C.as;
+    int64_t lo = 0, hi = B->C.n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (w * v[mid] < 1.0)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+/* Cumulative cost of - ranks [0, b), as row_cost with the row starting at 0. */
+static uint64_t bip_row_cost(const proxy_t* P, int64_t J, uint64_t qw, int64_t b)
+{
+    int64_t units = (b < J ? b : J);
+    uint64_t c = (uint64_t)units << P->F;
+    if (b > J) {
+        unsigned __int128 prod = (unsigned __int128)qw * (unsigned __int128)(P->Q[b] - P->Q[J]);
+        c += (uint64_t)(prod >> 40);
+    }
+    return c;
+}
+
+/* Segments of row i over - ranks [0, m), as row_segments. */
+static int64_t bip_row_segments(const bip_t* B, const proxy_t* P, int64_t i, int64_t T, int64_t* seg_a,
+                                int64_t* seg_b, int64_t cap)
+{
+    int64_t m = B->C.n;
+    if (m < 1) return 0;
+    double w = bip_row_weight(B, i);
+    int64_t J = bip_unit_cut(B, w);
+    uint64_t qw = weight_fixed(w);
+    uint64_t total = bip_row_cost(P, J, qw, m);
+    uint64_t nseg = (total >> P->F) / (uint64_t)T;
+    if (nseg < 1) nseg = 1;
+    uint64_t Tc = total / nseg;
+    int64_t prev = 0;
+    for (uint64_t k = 0; k < nseg; ++k) {
+        int64_t b = m;
+        if (k + 1 < nseg) {
+            uint64_t target = Tc * (k + 1);
+            int64_t lo = 1, hi = m; /* first b with cost >= target */
+            while (lo < hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (bip_row_cost(P, J, qw, mid) >= target)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            b = lo;
+        }
+        if ((int64_t)k < cap) {
+            seg_a[k] = prev;
+            seg_b[k] = b;
+        }
+        prev = b;
+    }
+    return (int64_t)nseg;
+}
+
+/* Whole bipartite table in (+ rank, k) order; segment bounds are - ranks. */
+int64_t orc_bip_partition(int model, const double* xp, const double* yp, int64_t np, const double* xm,
+                          const double* ym, int64_t nm, int64_t T, int32_t* seg_row, int32_t* seg_k,
+                          int64_t* seg_a, int64_t* seg_b, int64_t cap, int32_t* perm_plus, int32_t* perm_minus)
+{
+    bip_t B;
+    proxy_t P;
+    bip_build(&B, model, xp, yp, np, xm, ym, nm, 0);
+    proxy_build(&P, &B.C);
+    if (perm_plus) memcpy(perm_plus, B.R.perm, sizeof(int32_t) * (size_t)np);
+    if (perm_minus) memcpy(perm_minus, B.C.perm, sizeof(int32_t) * (size_t)nm);
+    int64_t total = 0;
+    int64_t* ta = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    for (int64_t i = 0; i < np; ++i) {
+        int64_t ns = bip_row_segments(&B, &P, i, T, ta, tb, nm);
+        for (int64_t k = 0; k < ns; ++k, ++total) {
+            if (total < cap) {
+                seg_row[total] = (int32_t)i;
+                seg_k[total] = (int32_t)k;
+                seg_a[total] = ta[k];
+                seg_b[total] = tb[k];
+            }
+        }
+    }
+    free(ta);
+    free(tb);
+    free(P.Q);
+    bip_free(&B);
+    return total;
+}
+
+/* - rank of virtual position v of a row whose excluded - rank is ex (-1: none). */
+static int64_t bip_actual(int64_t v, int64_t ex)
+{
+    return (ex >= 0 && v >= ex) ? v + 1 : v;
+}
+
+static void bip_walk_segment(const bip_t* B, const uint32_t key[2], uint32_t sample, int64_t i, int32_t k,
+                             int64_t a, int64_t b, int64_t ex, sink_t* out)
+{
+    const int uecm = (B->R.model == ORC_UECM);
+    const int64_t va = (ex >= 0 && a > ex) ? a - 1 : a;
+    const int64_t vb = (ex >= 0 && b > ex) ? b - 1 : b;
+    out->stats[ORC_ST_SEGMENTS] += 1;
+    if (va >= vb) return; /* the segment holds only the excluded candidate */
+    const double c = uecm ? bip_bound_c(B, i, a) : 0.0;
+    int64_t head = bip_actual(va, ex);
+    double q = uecm ? bip_prob_hat(B, i, head, c) : bip_prob(B, i, head);
+    int64_t pos = va - 1;
+    uint32_t d = 0, e = 0;
+    for (;;) {
+        if (!(q > 0.0)) break;
+        uint32_t ctr[4] = {d, (uint32_t)k, (uint32_t)i, sample};
+        uint32_t rnd[4];
+        orc_philox4x32_10(ctr, key, rnd);
+        d += 1;
+        out->stats[ORC_ST_DRAWS] += 1;
+        double U = unit_open0(rnd[1], rnd[0]);
+        double V = unit_open1(rnd[3], rnd[2]);
+        double R = (double)(vb - pos - 1);
+        double t = (q >= 1.0) ? 0.0 : log(U) / log1p(-q);
+        if (near_integer(t)) out->stats[ORC_ST_BOUNDARY] += 1;
+        if (t >= R) break;
+        int64_t jv = pos + 1 + (int64_t)floor(t);
+        int64_t j = bip_actual(jv, ex);
+        double p = bip_prob(B, i, j);
+        if (V < p / q) {
+            int32_t wt = 1;
+            if (uecm) {
+                uint32_t wctr[4] = {0x80000000u | (e >> 1), (uint32_t)k, (uint32_t)i, sample};
+                uint32_t wr[4];
+                orc_philox4x32_10(wctr, key, wr);
+                double Uw = (e & 1u) ? unit_open0(wr[3], wr[2]) : unit_open0(wr[1], wr[0]);
+                double r = B->R.ys[i] * B->C.ys[j];
+                if (r > 0.0) {
+                    double tw = log(Uw) / log(r);
+                    if (near_integer(tw)) out->stats[ORC_ST_BOUNDARY] += 1;
+                    if (tw >= 2147483646.0) {
+                        wt = 2147483647;
+                        out->weight_overflow = 1;
+                    } else {
+                        wt = 1 + (int32_t)floor(tw);
+                    }
+                }
+            }
+            if (out->count < out->cap) {
+                out->src[out->count] = B->R.perm[i];
+                out->dst[out->count] = B->C.perm[j];
+                if (out->w) out->w[out->count] = wt;
+            }
+            out->count += 1;
+            out->stats[ORC_ST_EDGES] += 1;
+            e += 1;
+        }
+        q = uecm ? bip_prob_hat(B, i, j, c) : p;
+        pos = jv;
+    }
+}
+
+/* Samples of a bipartite (directed = 0) or directed (directed = 1, np == nm)
+ * network.  Edges (+ id, - id) of all samples concatenated in sample order,
+ * each sample in (+ rank, segment, candidate) order.  Returns the total
+ * edge count, or -1 on a weight above INT32_MAX or np != nm when directed. */
+int64_t orc_bip_sample(int model, const double* xp, const double* yp, int64_t np, const double* xm,
+                       const double* ym, int64_t nm, int directed, uint64_t seed, uint32_t network_id,
+                       uint32_t sample_begin, uint32_t num_samples, int64_t T, int32_t* src, int32_t* dst,
+                       int32_t* w, int64_t cap, int64_t* counts, uint64_t* stats)
+{
+    if (directed && np != nm) return -1;
+    bip_t B;
+    proxy_t P;
+    bip_build(&B, model, xp, yp, np, xm, ym, nm, directed);
+    proxy_build(&P, &B.C);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) + network_id};
+    uint64_t local_stats[4] = {0, 0, 0, 0};
+    sink_t out = {src, dst, w, cap, 0, stats ? stats : local_stats, 0};
+    int64_t* ta = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    for (uint32_t s = 0; s < num_samples; ++s) {
+        int64_t before = out.count;
+        for (int64_t i = 0; i < np; ++i) {
+            int64_t ex = directed ? (int64_t)B.rank_c[B.R.perm[i]] : -1;
+            int64_t ns = bip_row_segments(&B, &P, i, T, ta, tb, nm);
+            for (int64_t kk = 0; kk < ns; ++kk)
+                bip_walk_segment(&B, key, sample_begin + s, i, (int32_t)kk, ta[kk], tb[kk], ex, &out);
+        }
+        if (counts) counts[s] = out.count - before;
+    }
+    free(ta);
+    free(tb);
+    free(P.Q);
+    bip_free(&B);
+    return out.weight_overflow ? -1 : out.count;
+}
+
+/* Brute force for bipartite / directed networks: every pair (u, v), u a +
+ * id and v a - id (u != v when directed), is an independent Bernoulli(p_uv)
+ * with a UECM weight as in orc_bf_sample; Philox(ctr = {u, v, 0xB1B1B1B1,
+ * s}).  Edges in (u, v) order. */
+int64_t orc_bip_bf_sample(int model, const double* xp, const double* yp, int64_t np, const double* xm,
+                          const double* ym, int64_t nm, int directed, uint64_t seed, uint32_t sample,
+                          int32_t* src, int32_t* dst, int32_t* w, int64_t cap, uint64_t* evaluations)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t count = 0;
+    uint64_t evals = 0;
+    for (int64_t u = 0; u < np; ++u) {
+        for (int64_t v = 0; v < nm; ++v) {
+            if (directed && u == v) continue;
+            double p, r = 0.0;
+            if (model == ORC_UBCM) {
+                double z = xp[u] * xm[v];
+                p = z / (1.0 + z);
+            } else {
+                double A = (xp[u] * yp[u]) * (xm[v] * ym[v]);
+                r = yp[u] * ym[v];
+                p = A / ((1.0 - r) + A);
+            }
+            evals += 1;
+            uint32_t ctr[4] = {(uint32_t)u, (uint32_t)v, 0xB1B1B1B1u, sample};
             uint32_t rnd[4];
             orc_philox4x32_10(ctr, key, rnd);
             double V = unit_open1(rnd[1], rnd[0]);

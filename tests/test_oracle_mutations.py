@@ -64,3 +64,55 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new, pin):
         assert p < 1e-8 or z > 8.0
     else:
         assert weight_pvalue(UECM_X, UECM_Y, lib=lib) < 1e-8
+
+
+# Planted mistakes in the bipartite / directed walk (Sec. 2.6).
+BIP_MUTATIONS = [
+    ("directed_self_pair_not_excluded",
+     "int64_t ex = directed ? (int64_t)B.rank_c[B.R.perm[i]] : -1;", "int64_t ex = -1;", "directed"),
+    ("virtual_position_off_by_one", "return (ex >= 0 && v >= ex) ? v + 1 : v;",
+     "return (ex >= 0 && v > ex) ? v + 1 : v;", "directed"),
+    ("bipartite_bound_from_head_y_only", "return B->R.ys[i] * B->C.ymax[a];", "return B->R.ys[i] * B->C.ys[a];",
+     "bipartite_uecm"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", BIP_MUTATIONS, ids=[m[0] for m in BIP_MUTATIONS])
+def test_planted_bipartite_mistake_is_caught(tmp_path, name, old, new, pin):
+    from tests.test_oracle_bipartite import DIR_XI, DIR_XO, DIR_YI, DIR_YO, bip_code_counts, bip_enumeration_pvalue
+    lib = _compile(tmp_path, name, old, new)
+    if pin == "directed":
+        caught = False
+        for model in (oracle.UBCM, oracle.UECM):
+            yo, yi = (DIR_YO, DIR_YI) if model == oracle.UECM else (None, None)
+            for T in (2, 1 << 30):
+                src, dst, _, counts, _ = oracle.bip_sample(model, DIR_XO, yo, DIR_XI, yi, directed=True,
+                                                           num_samples=20000, seg_target=T, lib=lib)
+                hist = bip_code_counts(src, dst, counts, 3, 3, True)
+                if hist[-1] > 0:
+                    caught = True
+                    continue
+                if bip_enumeration_pvalue(model, DIR_XO, DIR_XI, yo, yi, directed=True, samples=20000,
+                                          seg_target=T, lib=lib) < 1e-8:
+                    caught = True
+        assert caught
+    else:
+        # the - set in sorted order has y rising while a = x y falls, so in a
+        # whole-row segment (T = 2^30) the head's y understates r_ij for every
+        # later candidate and those pairs are proposed too rarely
+        from tests.oracle_pins import alpha_of
+        ym = np.array([0.1, 0.3, 0.5, 0.7, 0.9])
+        xm = np.array([1.0, 0.8, 0.6, 0.4, 0.2]) / ym
+        yp = np.array([0.95, 0.6])
+        xp = np.array([1.0, 0.5]) / yp
+        S = 20000
+        src, dst, _, counts, _ = oracle.bip_sample(oracle.UECM, xp, yp, xm, ym, num_samples=S,
+                                                   seg_target=1 << 30, lib=lib)
+        ap, am, bp, bm = alpha_of(xp), alpha_of(xm), alpha_of(yp), alpha_of(ym)
+        zmax = 0.0
+        for (u, v) in oracle.bip_pair_list(2, 5):
+            num = np.exp(-ap[u] - am[v] - bp[u] - bm[v])
+            p = num / (1.0 - np.exp(-bp[u] - bm[v]) + num)
+            f = ((src == u) & (dst == v)).sum() / S
+            zmax = max(zmax, abs(f - p) / np.sqrt(p * (1 - p) / S))
+        assert zmax > 6.0
