@@ -66,6 +66,7 @@ typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
 #define MH_INIT_PREV 0x20u   /* first proposal q = p at the rank before the        */
                              /* segment head (p_ii for a row's first segment,      */
                              /* Sec. 2.4 step (ii)); default: q = p at the head    */
+#define MH_DIRECTED 0x40u    /* mh_sample_bipartite: a directed network (Sec. 2.6) */
 #define MH_FP64_ONLY 0x100u  /* decide every draw with the plain FP64 path         */
 #define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
                              /* caller's stream (see mh_last_call_info)            */
@@ -159,6 +160,41 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
                        size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w, int64_t* csr_offsets,
                        int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
+
+/*
+ * Bipartite and directed networks (Sec. 2.6).  The + set's nodes are the
+ * rows, each walked over every node of the - set; each set is sorted by its
+ * own key (descending x, or a = x y for MH_UECM), so
+ *   UBCM form  p_ij = x+_i x-_j / (1 + x+_i x-_j)
+ *   UECM form  p_ij = A / (1 - r + A),  A = x+_i y+_i x-_j y-_j,  r = y+_i y-_j
+ * with the proposal bound c = y+_i max_{j >= segment head} y-_j.  With
+ * MH_DIRECTED the + set holds every node's out-parameters and the - set
+ * its in-parameters (n_plus == n_minus, the same ids): edge (u, v) is u -> v
+ * and the pairs (i, i) are never proposed.
+ *
+ * Workspace bytes for mh_sample_bipartite (as mh_workspace_size).
+ */
+int mh_bipartite_workspace_size(int model, int64_t n_plus, int64_t n_minus, const mh_params* params,
+                                int64_t capacity_edges, size_t* h_bytes);
+
+/*
+ * mh_sample_bipartite — samples of a bipartite (or, with MH_DIRECTED, a
+ * directed) network.  Arguments as mh_sample_weighted with
+ *   x_plus, y_plus      FP64[n_plus]  (y only for MH_UECM, else NULL)
+ *   x_minus, y_minus    FP64[n_minus]
+ *   src, dst            + id and - id of each edge (out and in node when
+ *                       directed); a sample's edges in (+ rank, - rank) order
+ *   w, csr_weights      MH_UECM weights (else NULL)
+ *   csr_offsets         int64[num_samples * (n_plus + 1)]: rows are + ids
+ * MH_BOUND_PAPER and MH_INIT_PREV do not apply (MH_ERR_ARG); MH_DIRECTED
+ * needs n_plus == n_minus.  max_segments (0: 4 n_plus + 1024) must be at
+ * least n_plus.  Errors as mh_sample_weighted.
+ */
+int mh_sample_bipartite(int model, const double* x_plus, const double* y_plus, int64_t n_plus,
+                        const double* x_minus, const double* y_minus, int64_t n_minus, const mh_params* params,
+                        void* workspace, size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w,
+                        int64_t* csr_offsets, int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
+                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
 
 /*
  * Batched ensembles: many networks of uneven size, UBCM and UECM mixed, each

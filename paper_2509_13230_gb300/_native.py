@@ -27,6 +27,7 @@ MH_OUT_COO = 0x01
 MH_OUT_CSR = 0x02
 MH_BOUND_PAPER = 0x10
 MH_INIT_PREV = 0x20
+MH_DIRECTED = 0x40
 MH_FP64_ONLY = 0x100
 MH_TIMING = 0x200
 
@@ -50,6 +51,8 @@ EXPORTED = (
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
+    "mh_bipartite_workspace_size",
+    "mh_sample_bipartite",
 )
 
 
@@ -145,6 +148,11 @@ def load(path: str | None = None):
         lib.maxent_expected_fwd.restype = i32
         lib.maxent_expected_bwd.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_bwd.restype = i32
+        lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
+        lib.mh_bipartite_workspace_size.restype = i32
+        lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
+                                            vp, vp, vp]
+        lib.mh_sample_bipartite.restype = i32
         D = ctypes.POINTER(MhNetworkDesc)
         lib.mh_batch_workspace_size.argtypes = [D, i32, P, i64, i64, ctypes.POINTER(sz)]
         lib.mh_batch_workspace_size.restype = i32
@@ -242,3 +250,18 @@ def mh_sample_batched(h_nets, n_nets, params, max_wave_items, workspace, workspa
     return load().mh_sample_batched(h_nets, n_nets, ctypes.byref(params), max_wave_items, workspace,
                                     workspace_bytes, pair_begin, pair_count, src, dst, w, csr_offsets, csr_indices,
                                     csr_weights, capacity_edges, h_edges_per_pair, h_stats, stream)
+
+
+def mh_bipartite_workspace_size(model, n_plus, n_minus, params, capacity_edges) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().mh_bipartite_workspace_size(model, n_plus, n_minus, ctypes.byref(params), capacity_edges,
+                                             ctypes.byref(out)), "mh_bipartite_workspace_size")
+    return out.value
+
+
+def mh_sample_bipartite(model, x_plus, y_plus, n_plus, x_minus, y_minus, n_minus, params, workspace, workspace_bytes,
+                        src, dst, w, csr_offsets, csr_indices, csr_weights, capacity_edges, h_edges_per_sample,
+                        h_stats, stream) -> int:
+    return load().mh_sample_bipartite(model, x_plus, y_plus, n_plus, x_minus, y_minus, n_minus, ctypes.byref(params),
+                                      workspace, workspace_bytes, src, dst, w, csr_offsets, csr_indices, csr_weights,
+                                      capacity_edges, h_edges_per_sample, h_stats, stream)

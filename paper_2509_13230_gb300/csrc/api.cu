@@ -85,7 +85,7 @@ struct PinnedBuffer {
 thread_local PinnedBuffer g_pinned;
 
 constexpr uint32_t kKnownFlags =
-    MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_FP64_ONLY | MH_TIMING;
+    MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_DIRECTED | MH_FP64_ONLY | MH_TIMING;
 
 }  // namespace
 
@@ -112,12 +112,17 @@ int sm_count() {
 
 static int64_t default_max_segments(int64_t n) { return 4 * n + 1024; }
 
-Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
+// Rows and candidates: one node set (rows = n, bip = false) or a bipartite
+// network (rows = the + set, candidates = the - set).
+static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, const mh_params& p, int64_t capacity) {
   (void)model;
   Layout L;
   L.n = n;
-  L.tiles = (n + kSortTile - 1) / kSortTile;
-  L.max_segments = p.max_segments > 0 ? p.max_segments : default_max_segments(n);
+  L.rows = rows;
+  L.bip = bip;
+  const int64_t nmax = rows > n ? rows : n;
+  L.tiles = (nmax + kSortTile - 1) / kSortTile;
+  L.max_segments = p.max_segments > 0 ? p.max_segments : default_max_segments(rows);
   int64_t spc = kItemChunk / L.max_segments;
   if (spc < 1) spc = 1;
   if (spc > static_cast<int64_t>(p.num_samples)) spc = p.num_samples;
@@ -126,9 +131,10 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.capacity = capacity;
   int64_t scan_len = 256 * L.tiles;
   if (n + 1 > scan_len) scan_len = n + 1;
+  if (rows + 1 > scan_len) scan_len = rows + 1;
   if (L.items_max + 1 > scan_len) scan_len = L.items_max + 1;
-  if (spc * (n + 1) > scan_len) scan_len = spc * (n + 1);
-  const size_t n1 = static_cast<size_t>(n) + 1;
+  if (spc * (rows + 1) > scan_len) scan_len = spc * (rows + 1);
+  const size_t n1 = static_cast<size_t>(n) + 1, r1 = static_cast<size_t>(rows) + 1, nm = static_cast<size_t>(nmax);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -136,10 +142,10 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
     return at;
   };
   L.ctrl = take(sizeof(Ctrl));
-  L.keys0 = take(8 * static_cast<size_t>(n));
-  L.keys1 = take(8 * static_cast<size_t>(n));
-  L.vals0 = take(4 * static_cast<size_t>(n));
-  L.vals1 = take(4 * static_cast<size_t>(n));
+  L.keys0 = take(8 * nm);
+  L.keys1 = take(8 * nm);
+  L.vals0 = take(4 * nm);
+  L.vals1 = take(4 * nm);
   L.hist = take(4 * 256 * static_cast<size_t>(L.tiles));
   L.perm = take(4 * static_cast<size_t>(n));
   L.rank = take(4 * static_cast<size_t>(n));
@@ -148,7 +154,7 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.as = take(8 * static_cast<size_t>(n));
   L.top1 = take(sizeof(Top2) * n1);
   L.Q = take(8 * n1);
-  L.rowoff = take(8 * n1);
+  L.rowoff = take(8 * r1);
   L.seg = take(sizeof(int4) * static_cast<size_t>(L.max_segments));
   L.item_cnt = take(8 * static_cast<size_t>(L.items_max));
   L.item_base = take(8 * static_cast<size_t>(L.items_max));
@@ -166,8 +172,23 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.lntab = take(16 * 512);
   L.seg_c = take(8 * static_cast<size_t>(L.max_segments));
   L.seg_cf = take(16 * static_cast<size_t>(L.max_segments));
+  if (bip) {
+    const size_t r = static_cast<size_t>(rows);
+    L.perm_r = take(4 * r);
+    L.rank_r = take(4 * r);
+    L.xs_r = take(8 * r);
+    L.ys_r = take(8 * r);
+    L.as_r = take(8 * r);
+    L.xdf_r = take(8 * r);
+    L.adf_r = take(8 * r);
+    L.ydf_r = take(8 * r);
+    L.lny_r = take(8 * r);
+    L.Q_r = take(8 * r1);
+    L.top_r = take(sizeof(Top2) * r1);
+    L.excl = take(4 * r);
+  }
   // states of the single-pass scans and of the one-sweep sort, cleared by one
-  // memset per call (the kernels leave them cleared)
+  // memset per sort (the kernels leave them cleared)
   L.scan_tiles = scan_len / kScanTile + 2;
   L.zero_begin = off;
   L.ghist = take(4 * 8 * 256);
@@ -179,6 +200,14 @@ Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
   L.scan_values = take(2 * sizeof(Top2) * static_cast<size_t>(L.scan_tiles));
   L.total = off;
   return L;
+}
+
+Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity) {
+  return make_layout_impl(model, n, n, false, p, capacity);
+}
+
+Layout make_layout_bip(int model, int64_t n_plus, int64_t n_minus, const mh_params& p, int64_t capacity) {
+  return make_layout_impl(model, n_plus, n_minus, true, p, capacity);
 }
 
 static Net make_net(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
@@ -207,10 +236,59 @@ static Net make_net(int model, const mh_params& p, const double* x, const double
   g.lntab = reinterpret_cast<LnEntry*>(ws + L.lntab);
   g.max_segments = L.max_segments;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
+  g.rows = L.rows;
+  g.bip = L.bip;
+  g.excl = nullptr;
+  if (!L.bip) {
+    g.x_r = g.x;
+    g.y_r = g.y;
+    g.perm_r = g.perm;
+    g.rank_r = g.rank;
+    g.xs_r = g.xs;
+    g.ys_r = g.ys;
+    g.as_r = g.as;
+    g.xdf_r = g.xdf;
+    g.adf_r = g.adf;
+    g.ydf_r = g.ydf;
+    g.lny_r = g.lny;
+  } else {
+    g.perm_r = reinterpret_cast<int32_t*>(ws + L.perm_r);
+    g.rank_r = reinterpret_cast<int32_t*>(ws + L.rank_r);
+    g.xs_r = reinterpret_cast<double*>(ws + L.xs_r);
+    g.ys_r = reinterpret_cast<double*>(ws + L.ys_r);
+    g.as_r = (model == MH_UECM) ? reinterpret_cast<double*>(ws + L.as_r) : g.xs_r;
+    g.xdf_r = reinterpret_cast<float2*>(ws + L.xdf_r);
+    g.adf_r = (model == MH_UECM) ? reinterpret_cast<float2*>(ws + L.adf_r) : g.xdf_r;
+    g.ydf_r = reinterpret_cast<float2*>(ws + L.ydf_r);
+    g.lny_r = reinterpret_cast<float2*>(ws + L.lny_r);
+    if (p.flags & MH_DIRECTED) g.excl = reinterpret_cast<int32_t*>(ws + L.excl);
+  }
   return g;
 }
 
-static int check_params(int model, int64_t n, const mh_params* p) {
+// The rows of a bipartite network as a one-set view, for their sort and gather.
+static Net row_view(const Net& g, const Layout& L, char* ws) {
+  Net r = g;
+  r.n = g.rows;
+  r.x = g.x_r;
+  r.y = g.y_r;
+  r.perm = g.perm_r;
+  r.rank = g.rank_r;
+  r.xs = g.xs_r;
+  r.ys = g.ys_r;
+  r.as = g.as_r;
+  r.xdf = g.xdf_r;
+  r.adf = g.adf_r;
+  r.ydf = g.ydf_r;
+  r.lny = g.lny_r;
+  r.Q = reinterpret_cast<unsigned long long*>(ws + L.Q_r);
+  r.top = reinterpret_cast<Top2*>(ws + L.top_r);
+  r.bip = false;
+  r.rows = g.rows;
+  return r;
+}
+
+static int check_params_impl(int model, int64_t rows, int64_t n, bool bip, const mh_params* p) {
   if (model != MH_UBCM && model != MH_UECM) {
     set_error("model must be MH_UBCM or MH_UECM (got %d)", model);
     return MH_ERR_ARG;
@@ -219,8 +297,9 @@ static int check_params(int model, int64_t n, const mh_params* p) {
     set_error("params is NULL");
     return MH_ERR_ARG;
   }
-  if (n < 1 || n > 0x7FFFFFFEll) {
-    set_error("n must be in [1, 2^31 - 2] (got %lld)", static_cast<long long>(n));
+  if (n < 1 || n > 0x7FFFFFFEll || rows < 1 || rows > 0x7FFFFFFEll) {
+    set_error("node counts must be in [1, 2^31 - 2] (got %lld and %lld)", static_cast<long long>(rows),
+              static_cast<long long>(n));
     return MH_ERR_ARG;
   }
   if (p->num_samples < 1) {
@@ -239,20 +318,36 @@ static int check_params(int model, int64_t n, const mh_params* p) {
     set_error("unknown flag bits 0x%x", p->flags & ~kKnownFlags);
     return MH_ERR_ARG;
   }
+  if (!bip && (p->flags & MH_DIRECTED)) {
+    set_error("MH_DIRECTED applies to mh_sample_bipartite only");
+    return MH_ERR_ARG;
+  }
+  if (bip && (p->flags & (MH_BOUND_PAPER | MH_INIT_PREV))) {
+    set_error("MH_BOUND_PAPER and MH_INIT_PREV do not apply to bipartite networks");
+    return MH_ERR_ARG;
+  }
+  if (bip && (p->flags & MH_DIRECTED) && rows != n) {
+    set_error("a directed network needs n_plus == n_minus (got %lld and %lld)", static_cast<long long>(rows),
+              static_cast<long long>(n));
+    return MH_ERR_ARG;
+  }
   if (p->walk_ctas_per_sm > 64 || p->max_segments < 0) {
     set_error("walk_ctas_per_sm must be at most 64 and max_segments >= 0");
     return MH_ERR_ARG;
   }
-  if (p->max_segments > 0 && p->max_segments < n - 1) {
-    set_error("max_segments must be 0 or >= n - 1");
+  const int64_t least = bip ? rows : n - 1;  // every row with candidates has a segment
+  if (p->max_segments > 0 && p->max_segments < least) {
+    set_error("max_segments must be 0 or >= %lld", static_cast<long long>(least));
     return MH_ERR_ARG;
   }
-  if (p->max_segments >= (1ll << 31) || (p->max_segments == 0 && default_max_segments(n) >= (1ll << 31))) {
+  if (p->max_segments >= (1ll << 31) || (p->max_segments == 0 && default_max_segments(rows) >= (1ll << 31))) {
     set_error("the segment table would exceed 2^31 rows");
     return MH_ERR_ARG;
   }
   return MH_OK;
 }
+
+static int check_params(int model, int64_t n, const mh_params* p) { return check_params_impl(model, n, n, false, p); }
 
 #define MH_CUDA(expr)                                                             \
   do {                                                                            \
@@ -264,15 +359,30 @@ static int check_params(int model, int64_t n, const mh_params* p) {
   } while (0)
 
 // Sort, gather, bound prep and segment table into the workspace.
-static int prepare(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
-  MH_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+// Validation, sort and gather of one node set (g.n nodes).
+static int sort_set(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  MH_CUDA(cudaMemsetAsync(&ctrl->key_or, 0, sizeof(ctrl->key_or), s));
   MH_CUDA(cudaMemsetAsync(&ctrl->key_and, 0xFF, sizeof(ctrl->key_and), s));
   MH_CUDA(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));
+  Layout Ls = L;  // the sort's tiles follow this set's size
+  Ls.tiles = (g.n + kSortTile - 1) / kSortTile;
   auto* keys0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
   auto* vals0 = reinterpret_cast<int32_t*>(ws + L.vals0);
   MH_CUDA(launch_validate_keys(g, keys0, vals0, reinterpret_cast<unsigned*>(ws + L.ghist), ctrl, s));
-  MH_CUDA(launch_sort(g, L, ws, ctrl, s));
+  MH_CUDA(launch_sort(g, Ls, ws, ctrl, s));
   MH_CUDA(launch_gather(g, vals0, ctrl, s));
+  return MH_OK;
+}
+
+static int prepare(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  MH_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+  int rc = sort_set(g, L, ws, ctrl, s);  // the candidates (the - set when bipartite)
+  if (rc != MH_OK) return rc;
+  if (g.bip) {
+    rc = sort_set(row_view(g, L, ws), L, ws, ctrl, s);  // the rows (the + set)
+    if (rc != MH_OK) return rc;
+    if (g.excl) MH_CUDA(launch_exclusions(g, s));
+  }
   MH_CUDA(launch_bounds_and_partition(g, L, ws, ctrl, s));
   return MH_OK;
 }
@@ -356,8 +466,8 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
 // default stream cannot be captured) and replayed on the caller's stream.
 struct CallKey {
   int model, device;
-  int64_t n, capacity;
-  const void *x, *y, *ws, *src, *dst, *w, *csr_off, *csr_idx, *csr_w, *hbuf;
+  int64_t n, capacity, rows;
+  const void *x, *y, *xr, *yr, *ws, *src, *dst, *w, *csr_off, *csr_idx, *csr_w, *hbuf;
   size_t ws_bytes;
   mh_params params;
 };
@@ -420,12 +530,16 @@ struct GraphCache {
 };
 thread_local GraphCache g_graphs;
 
+// One sampling call: a single node set (xr == NULL) or a bipartite network
+// whose rows are (xr, yr, rows) and candidates (x, y, n).
 static int run_sample(int model, const double* x, const double* y, int64_t n, const mh_params* p, void* workspace,
                       size_t workspace_bytes, const Outputs& o, int64_t* h_counts, uint64_t* h_stats,
-                      cudaStream_t s) {
-  int rc = check_params(model, n, p);
+                      cudaStream_t s, const double* xr = nullptr, const double* yr = nullptr, int64_t rows = 0) {
+  const bool bip = xr != nullptr;
+  if (!bip) rows = n;
+  int rc = check_params_impl(model, rows, n, bip, p);
   if (rc != MH_OK) return rc;
-  if (!x || (model == MH_UECM && !y) || !workspace || !h_counts) {
+  if (!x || (model == MH_UECM && (!y || (bip && !yr))) || !workspace || !h_counts) {
     set_error("x%s, workspace and h_edges_per_sample must be non-NULL", model == MH_UECM ? ", y" : "");
     return MH_ERR_ARG;
   }
@@ -441,7 +555,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     set_error("MH_OUT_CSR needs csr_offsets and csr_indices");
     return MH_ERR_ARG;
   }
-  const Layout L = make_layout(model, n, *p, o.capacity);
+  const Layout L = bip ? make_layout_bip(model, rows, n, *p, o.capacity) : make_layout(model, n, *p, o.capacity);
   if (workspace_bytes < L.total) {
     set_error("workspace needs %zu bytes, got %zu", L.total, workspace_bytes);
     return MH_ERR_WORKSPACE;
@@ -453,7 +567,11 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     return MH_ERR_ARG;
   }
   char* ws = static_cast<char*>(workspace);
-  const Net g = make_net(model, *p, x, y, n, L, ws);
+  Net g = make_net(model, *p, x, y, n, L, ws);
+  if (bip) {
+    g.x_r = xr;
+    g.y_r = yr;
+  }
   const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= 64;
   const size_t counts_bytes = 8 * static_cast<size_t>(p->num_samples);
   if (g_pinned.bytes < sizeof(Ctrl) + counts_bytes) {
@@ -474,6 +592,9 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   key.capacity = o.capacity;
   key.x = x;
   key.y = y;
+  key.xr = xr;
+  key.yr = yr;
+  key.rows = rows;
   key.ws = workspace;
   key.src = o.src;
   key.dst = o.dst;
@@ -612,6 +733,32 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
   Outputs o{src, dst, w, reinterpret_cast<long long*>(csr_offsets), csr_indices, csr_weights, capacity_edges};
   return run_sample(MH_UECM, x, y, n, params, workspace, workspace_bytes, o, h_edges_per_sample, h_stats,
                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mh_bipartite_workspace_size(int model, int64_t n_plus, int64_t n_minus, const mh_params* params,
+                                int64_t capacity_edges, size_t* h_bytes) {
+  int rc = check_params_impl(model, n_plus, n_minus, true, params);
+  if (rc != MH_OK) return rc;
+  if (capacity_edges < 0 || !h_bytes) {
+    set_error("capacity_edges must be >= 0 and h_bytes non-NULL");
+    return MH_ERR_ARG;
+  }
+  *h_bytes = make_layout_bip(model, n_plus, n_minus, *params, capacity_edges).total;
+  return MH_OK;
+}
+
+int mh_sample_bipartite(int model, const double* x_plus, const double* y_plus, int64_t n_plus,
+                        const double* x_minus, const double* y_minus, int64_t n_minus, const mh_params* params,
+                        void* workspace, size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w,
+                        int64_t* csr_offsets, int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
+                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream) {
+  if (!x_plus) {
+    set_error("x_plus must be non-NULL");
+    return MH_ERR_ARG;
+  }
+  Outputs o{src, dst, w, reinterpret_cast<long long*>(csr_offsets), csr_indices, csr_weights, capacity_edges};
+  return run_sample(model, x_minus, y_minus, n_minus, params, workspace, workspace_bytes, o, h_edges_per_sample,
+                    h_stats, reinterpret_cast<cudaStream_t>(stream), x_plus, y_plus, n_plus);
 }
 
 int mh_segment_table(int model, const double* x, const double* y, int64_t n, const mh_params* params,

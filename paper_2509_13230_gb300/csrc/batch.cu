@@ -253,6 +253,25 @@ Layout net_layout(const BatchLayout& B, const BatchNet& bn, int lane) {
   return L;
 }
 
+// Rows of a one-set network: the same nodes and arrays as the candidates.
+Net one_set_rows(Net g) {
+  g.rows = g.n;
+  g.bip = false;
+  g.excl = nullptr;
+  g.x_r = g.x;
+  g.y_r = g.y;
+  g.perm_r = g.perm;
+  g.rank_r = g.rank;
+  g.xs_r = g.xs;
+  g.ys_r = g.ys;
+  g.as_r = g.as;
+  g.xdf_r = g.xdf;
+  g.adf_r = g.adf;
+  g.ydf_r = g.ydf;
+  g.lny_r = g.lny;
+  return g;
+}
+
 Net make_batch_net(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
                    char* ws) {
   Net g;
@@ -280,7 +299,7 @@ Net make_batch_net(int model, const mh_params& p, const double* x, const double*
   g.lntab = reinterpret_cast<LnEntry*>(ws + L.lntab);
   g.max_segments = L.max_segments;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
-  return g;
+  return one_set_rows(g);
 }
 
 // ---- device side -------------------------------------------------------------------
@@ -902,7 +921,7 @@ Net concatenated_net(const BatchLayout& B, const mh_params& p, char* ws) {
   g.lntab = reinterpret_cast<LnEntry*>(ws + B.lntab);
   g.max_segments = B.segs;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
-  return g;
+  return one_set_rows(g);
 }
 
 // UBCM networks keep their x products in xs / xdf; the UBCM walk reads as /
@@ -914,7 +933,7 @@ Net model_view(const Net& g, int model) {
     v.as = g.xs;
     v.adf = g.xdf;
   }
-  return v;
+  return one_set_rows(v);
 }
 
 }  // namespace

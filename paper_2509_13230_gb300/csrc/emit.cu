@@ -9,7 +9,8 @@
 //   COO  src[e] = perm[i], dst[e] = perm[j], w[e]
 //   CSR  csr_idx[off[s(n+1) + perm[i]] + position within row i] = perm[j]
 // CSR rows are original node ids; row u holds the edges whose higher-ranked
-// endpoint is u, and offsets are positions in the concatenated index array.
+// endpoint is u (bipartite: whose + endpoint is u), and offsets are
+// positions in the concatenated index array.
 #include "mh_internal.cuh"
 #include "scan.cuh"
 #include "walk_math.cuh"
@@ -18,8 +19,8 @@ namespace mh {
 
 namespace {
 
-// csr_off[(chunk_first + s)(n+1) + u] = edges of row u in sample s (0 for u = n);
-// an in-place exclusive scan then turns counts into offsets.
+// csr_off[(chunk_first + s)(rows+1) + u] = edges of row u in sample s (0 for
+// u = rows); an in-place exclusive scan then turns counts into offsets.
 __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, const Ctrl* ctrl,
                                  int64_t chunk_first, int64_t chunk_samples, long long* csr_off) {
   // A segment table that outgrew max_segments was truncated: rowoff still
@@ -27,14 +28,14 @@ __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, 
   // with MH_ERR_WORKSPACE, so nothing is counted.
   if (ctrl->num_segments > g.max_segments) return;
   const long long S = ctrl->num_segments;
-  const int64_t n1 = g.n + 1;
+  const int64_t n1 = g.rows + 1;
   const int64_t total = chunk_samples * n1;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t s = t / n1, u = t - s * n1;
     long long c = 0;
-    if (u < g.n) {
-      const int64_t i = g.rank[u];
+    if (u < g.rows) {
+      const int64_t i = g.rank_r[u];
       c = item_off[s * S + g.rowoff[i + 1]] - item_off[s * S + g.rowoff[i]];
     }
     csr_off[chunk_first * n1 + t] = c;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   for (long long t = threadIdx.x; t <= it1 - it0; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
   __syncthreads();
   const long long o0 = off[0], o1 = off[it1 - it0];
-  const long long n1 = g.n + 1;
+  const long long n1 = g.rows + 1;
   bool overflow = false;
   for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
     int lo = 0, hi = static_cast<int>(it1 - it0) - 1;  // last local item with off <= pos
@@ -101,16 +102,17 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     const int4 sg = g.seg[seg];
     const int32_t i = sg.x;
     const int32_t j = P.c.staging[P.c.item_base[item] + e];
-    if (j <= i || j >= g.n) {  // cannot happen for a walked segment; never index with it
+    if (j < row_start(g, i) || j >= g.n || (g.excl && j == g.excl[i])) {
+      // cannot happen for a walked segment; never index with it
       atomicOr(&ctrl->status, kStInternal);
       continue;
     }
-    const int32_t u = g.perm[i], v = g.perm[j];
+    const int32_t u = g.perm_r[i], v = g.perm[j];
     int32_t wt = 1;
     if (g.model == MH_UECM) {
-      const float2 li = g.lny[i], lj = g.lny[j];
+      const float2 li = g.lny_r[i], lj = g.lny[j];
       wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(sg.y), static_cast<uint32_t>(i),
-                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, g.ys[i], g.ys[j],
+                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, g.ys_r[i], g.ys[j],
                        df2{li.x, li.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
     }
     if (pos < P.o.capacity) {
@@ -145,11 +147,11 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
                                                   &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;
   if (o.csr_off) {
-    const int64_t len = c.chunk_samples * (g.n + 1);
+    const int64_t len = c.chunk_samples * (g.rows + 1);
     csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
         g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off);
     note_launches(1);
-    long long* region = o.csr_off + c.chunk_first * (g.n + 1);
+    long long* region = o.csr_off + c.chunk_first * (g.rows + 1);
     e = scan_any<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->out_base,
                                                     nullptr, false, st, s);
     if (e != cudaSuccess) return e;

@@ -64,7 +64,12 @@ constexpr int kDefaultSegTarget = 32;
 
 // ---- workspace layout --------------------------------------------------------
 struct Layout {
-  int64_t n = 0, tiles = 0, max_segments = 0, spc = 0, items_max = 0, capacity = 0;
+  int64_t n = 0, rows = 0, tiles = 0, max_segments = 0, spc = 0, items_max = 0, capacity = 0;
+  bool bip = false;
+  // bipartite rows (the + set): arrays of the sorted rows, scratch for the
+  // row set's own cost prefix and bounds (unused), the directed exclusions
+  size_t perm_r = 0, rank_r = 0, xs_r = 0, ys_r = 0, as_r = 0, xdf_r = 0, adf_r = 0, ydf_r = 0, lny_r = 0,
+         Q_r = 0, top_r = 0, excl = 0;
   size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
          as = 0, top1 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
          item_off = 0, sample_counts = 0, staging = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
@@ -75,6 +80,8 @@ struct Layout {
 };
 
 Layout make_layout(int model, int64_t n, const mh_params& p, int64_t capacity);
+// Bipartite: rows = the + set (n_plus), candidates = the - set (n_minus).
+Layout make_layout_bip(int model, int64_t n_plus, int64_t n_minus, const mh_params& p, int64_t capacity);
 
 struct Top2 {
   double a, b;  // largest and second largest
@@ -106,7 +113,27 @@ struct Net {
   LnEntry* lntab;         // logarithm table (kLnTable entries)
   int64_t max_segments;
   int seg_target;
+  // Rows.  One node set: the same nodes and arrays as the candidates, row i
+  // walking candidates [i+1, n).  Bipartite (Sec. 2.6): the + set, in its own
+  // rank order, each row walking all candidates [0, n) of the - set.
+  int64_t rows;
+  bool bip;
+  const double* x_r;      // row parameters in original order
+  const double* y_r;
+  int32_t* excl;          // directed: the candidate rank row i skips (its own in-copy), else NULL
+  int32_t* perm_r;        // row rank -> row id
+  int32_t* rank_r;        // row id -> row rank
+  double* xs_r;
+  double* ys_r;
+  double* as_r;
+  float2* xdf_r;
+  float2* adf_r;
+  float2* ydf_r;
+  float2* lny_r;
 };
+
+// First candidate of row i.
+__host__ __device__ inline int64_t row_start(const Net& g, int64_t i) { return g.bip ? 0 : i + 1; }
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -165,6 +192,7 @@ cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t
 cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_exclusions(const Net& g, cudaStream_t s);  // directed: excl[i] = rank of row i's own node
 
 struct ChunkArgs {
   int64_t chunk_first;  // index of the chunk's first sample within the call

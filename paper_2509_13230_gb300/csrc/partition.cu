@@ -7,7 +7,8 @@
 // the segment starting at rank a, which also bounds every r_ij ahead.  Both
 // need suffix maxima of y in rank order (exact, order-free operators).
 //
-// Segments: row i's candidates [i+1, n) are cut into pieces [a, b) of about
+// Segments: row i's candidates [i+1, n) (bipartite: all candidates [0, n) of
+// the other set, Sec. 2.6) are cut into pieces [a, b) of about
 // T expected proposals.  A walk restarted at every piece head with q = p at
 // the head is exact because q only has to bound p on the candidates it
 // proposes, and p is non-increasing along the sorted order (Sec. 2.3).  The
@@ -23,14 +24,15 @@ namespace mh {
 
 namespace {
 
+// Bound of row i over all its candidates (from row_start on).
 __device__ __forceinline__ double row_c(const Net& g, int64_t i) {
   if (g.flags & MH_BOUND_PAPER) return g.top[i].a * g.top[i].b;
-  return g.ys[i] * g.top[i + 1].a;
+  return g.ys_r[i] * g.top[row_start(g, i)].a;
 }
 
 __device__ __forceinline__ double row_weight(const Net& g, int64_t i) {
-  if (g.model == MH_UBCM) return g.xs[i];
-  return g.as[i] / (1.0 - row_c(g, i));
+  if (g.model == MH_UBCM) return g.xs_r[i];
+  return g.as_r[i] / (1.0 - row_c(g, i));
 }
 
 __device__ __forceinline__ unsigned long long weight_fixed(double w) {
@@ -39,10 +41,10 @@ __device__ __forceinline__ unsigned long long weight_fixed(double w) {
   return static_cast<unsigned long long>(wq);
 }
 
-// First j in [i+1, n) with w v_j < 1, else n.
+// First candidate j of row i with w v_j < 1, else n.
 __device__ __forceinline__ int64_t unit_cut(const Net& g, int64_t i, double w) {
   const double* v = (g.model == MH_UBCM) ? g.xs : g.as;
-  int64_t lo = i + 1, hi = g.n;
+  int64_t lo = row_start(g, i), hi = g.n;
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo) / 2;
     if (w * v[mid] < 1.0)
@@ -54,11 +56,11 @@ __device__ __forceinline__ int64_t unit_cut(const Net& g, int64_t i, double w) {
 }
 
 struct RowCost {
-  int64_t i, J;
+  int64_t start, J;  // first candidate of the row, unit cut
   unsigned long long qw;
   int F;
   __device__ __forceinline__ unsigned long long operator()(const unsigned long long* Q, int64_t b) const {
-    const int64_t units = (b < J ? b : J) - (i + 1);
+    const int64_t units = (b < J ? b : J) - start;
     unsigned long long c = static_cast<unsigned long long>(units) << F;
     if (b > J) {
       const unsigned long long dq = Q[b] - Q[J];
@@ -77,7 +79,7 @@ __device__ __forceinline__ int proxy_F(const Net& g) {
 __device__ __forceinline__ RowCost make_row_cost(const Net& g, int64_t i, int F) {
   const double w = row_weight(g, i);
   RowCost rc;
-  rc.i = i;
+  rc.start = row_start(g, i);
   rc.J = unit_cut(g, i, w);
   rc.qw = weight_fixed(w);
   rc.F = F;
@@ -86,10 +88,10 @@ __device__ __forceinline__ RowCost make_row_cost(const Net& g, int64_t i, int F)
 
 __global__ void __launch_bounds__(256) row_count_kernel(Net g) {
   const int F = proxy_F(g);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < g.n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < g.rows;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     long long nseg = 0;
-    if (i + 1 < g.n) {
+    if (row_start(g, i) < g.n) {
       const RowCost rc = make_row_cost(g, i, F);
       const unsigned long long total = rc(g.Q, g.n);
       unsigned long long ns = (total >> F) / static_cast<unsigned long long>(g.seg_target);
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
   const int F = proxy_F(g);
   for (long long s = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; s < lim;
        s += static_cast<long long>(gridDim.x) * blockDim.x) {
-    int64_t lo = 0, hi = g.n - 1;  // last row with rowoff[row] <= s
+    int64_t lo = 0, hi = g.rows - 1;  // last row with rowoff[row] <= s
     while (lo < hi) {
       const int64_t mid = lo + (hi - lo + 1) / 2;
       if (g.rowoff[mid] <= s)
@@ -122,9 +124,9 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
     const RowCost rc = make_row_cost(g, i, F);
     const unsigned long long total = rc(g.Q, g.n);
     const unsigned long long Tc = total / static_cast<unsigned long long>(nseg);
-    auto cut = [&](long long kk) -> int64_t {  // first b in [i+2, n] with cost(b) >= kk * Tc
+    auto cut = [&](long long kk) -> int64_t {  // first b in [start+1, n] with cost(b) >= kk * Tc
       const unsigned long long target = Tc * static_cast<unsigned long long>(kk);
-      int64_t a = i + 2, b = g.n;
+      int64_t a = rc.start + 1, b = g.n;
       while (a < b) {
         const int64_t mid = a + (b - a) / 2;
         if (rc(g.Q, mid) >= target)
@@ -134,12 +136,12 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
       }
       return a;
     };
-    const int64_t a = (k == 0) ? i + 1 : cut(k);
+    const int64_t a = (k == 0) ? rc.start : cut(k);
     const int64_t b = (k + 1 == nseg) ? g.n : cut(k + 1);
     g.seg[s] = make_int4(static_cast<int>(i), static_cast<int>(k), static_cast<int>(a), static_cast<int>(b));
     if (g.model == MH_UECM) {
       // exp(-beta_min) of this segment and the walk's FP32 / double-float forms
-      const double c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : g.ys[i] * g.top[a].a;
+      const double c = (g.flags & MH_BOUND_PAPER) ? g.top[i].a * g.top[i].b : g.ys_r[i] * g.top[a].a;
       const double omc = 1.0 - c;
       const df2 inv = df_from_double(1.0 / omc);
       g.seg_c[s] = c;
@@ -179,16 +181,32 @@ cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws,
                                            st, s);
     if (e != cudaSuccess) return e;
   }
-  const unsigned blocks = grid_for(g.n + 1, 256, static_cast<unsigned>(sm_count()) * 8u);
+  const unsigned blocks = grid_for(g.rows + 1, 256, static_cast<unsigned>(sm_count()) * 8u);
   row_count_kernel<<<blocks, 256, 0, s>>>(g);
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = scan_any<long long, SumOp<long long>>(g.rowoff, g.rowoff, ScanLen{g.n, nullptr, 1}, true, nullptr,
+  e = scan_any<long long, SumOp<long long>>(g.rowoff, g.rowoff, ScanLen{g.rows, nullptr, 1}, true, nullptr,
                                                   &ctrl->num_segments, true, st, s);
   if (e != cudaSuccess) return e;
   const unsigned fill_blocks = grid_for(g.max_segments, 256, static_cast<unsigned>(sm_count()) * 16u);
   seg_fill_kernel<<<fill_blocks, 256, 0, s>>>(g, ctrl);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
+// Directed networks (Sec. 2.6): row i (the out-copy of node perm_r[i]) never
+// proposes its own in-copy, the candidate of rank rank[perm_r[i]].
+__global__ void exclusions_kernel(Net g) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < g.rows;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    g.excl[i] = g.rank[g.perm_r[i]];
+}
+}  // namespace
+
+cudaError_t launch_exclusions(const Net& g, cudaStream_t s) {
+  exclusions_kernel<<<grid_for(g.rows, 256, static_cast<unsigned>(sm_count()) * 4u), 256, 0, s>>>(g);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -62,7 +62,8 @@ struct SegWalker {
   bool fresh;                   // the head of the segment is still to be set up
   bool fast;                    // q lies inside the fast levels' range
   bool e_ok;                    // Ef is valid
-  int32_t gi;                   // slot of row i in the node arrays
+  int32_t gi;                   // slot of row i in the row arrays
+  int32_t ex;                   // directed: the candidate row i skips (its own in-copy)
   uint32_t seg;                 // segment-table row (UECM: its bound constant c)
   df2 xi_df, yi_df, inv1mc;     // double-float x_i (a_i), y_i and 1 / (1 - c)
   float omc_f;                  // 1 - c in FP32
@@ -74,14 +75,17 @@ struct SegWalker {
 
   // Canonical FP64 values are read back on the (rare) FP64 paths.
   __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
-    return uecm ? prob_hat(g.as[gi], g.as[qj], g.seg_c[seg]) : prob_ubcm(g.xs[gi], g.xs[qj]);
+    return uecm ? prob_hat(g.as_r[gi], g.as[qj], g.seg_c[seg]) : prob_ubcm(g.xs_r[gi], g.xs[qj]);
   }
 
   // Loads row segment `seg` of sample `smp`; its head is set up by the next
   // advance().  Segment rows hold ranks local to their network; nb is the
   // network's first slot in the node arrays (0 for a single network), so a,
   // b, pos and j index the node arrays while i stays the local rank that the
-  // Philox counter uses.
+  // Philox counter uses.  Directed networks (kExcl): a, b, pos and the
+  // walk's positions are virtual, counting the candidates without the
+  // excluded one ex; candidate v is rank v below ex and v + 1 from ex on.
+  template <bool kExcl = false>
   __device__ __forceinline__ void begin_seg(const Net& g, unsigned sg, uint32_t smp, int nb, bool uecm) {
     const int4 e = g.seg[sg];
     seg = sg;
@@ -89,16 +93,21 @@ struct SegWalker {
     k = e.y;
     a = nb + e.z;
     b = nb + e.w;
+    if (kExcl) {
+      ex = g.excl[e.x];
+      a -= a > ex;
+      b -= b > ex;
+    }
     pos = a - 1;
     sample = smp;
     d = 0;
     fresh = true;
     gi = nb + e.x;
     if (!uecm) {
-      xi_df = to_df(g.xdf[gi]);
+      xi_df = to_df(g.xdf_r[gi]);
     } else {
-      xi_df = to_df(g.adf[gi]);
-      yi_df = to_df(g.ydf[gi]);
+      xi_df = to_df(g.adf_r[gi]);
+      yi_df = to_df(g.ydf_r[gi]);
       const float4 cf = g.seg_cf[sg];
       inv1mc = df2{cf.x, cf.y};
       omc_f = cf.z;
@@ -106,21 +115,23 @@ struct SegWalker {
   }
 
   // Single network: work item = (sample within the chunk, segment).
+  template <bool kExcl = false>
   __device__ __forceinline__ void begin(const Net& g, long long item, long long S, uint32_t sample0, bool uecm) {
     // item < 2^31 (the workspace layout bounds the items of a chunk)
     const unsigned s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);
     const unsigned seg = static_cast<unsigned>(item) - s_local * static_cast<unsigned>(S);
-    begin_seg(g, seg, sample0 + s_local, 0, uecm);
+    begin_seg<kExcl>(g, seg, sample0 + s_local, 0, uecm);
   }
 
   // One iteration.  Returns false when the segment has ended; sets
   // `accepted` / `j` when a candidate was evaluated (never on a head step).
-  template <bool kUecm>
+  template <bool kUecm, bool kExcl = false>
   __device__ __forceinline__ bool advance(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
                                           bool init_prev, const LnEntry* tab, unsigned long long& fallbacks,
                                           bool& accepted, int32_t& j) {
     accepted = false;
     const bool head = fresh;
+    if (kExcl && head && a >= b) return false;  // the segment held only the excluded candidate
     const bool fast_q = !head && fast && !fp64_only;
     double qc = 0.0;  // canonical q, computed only when a decision needs it
     bool have_qc = false;
@@ -136,9 +147,10 @@ struct SegWalker {
     // Philox words and -ln U of the next draw (draw 0 on a head step)
     rnd = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0, key1);
     Ef = neg_ln_u53_f(top53(rnd.y, rnd.x) + 1ull, tab, e_ok);
+    int32_t jv;  // position of the candidate (virtual when kExcl)
     if (head) {
       fresh = false;
-      j = init_prev ? a - 1 : a;
+      jv = init_prev ? a - 1 : a;
     } else {
       const int room = b - pos - 1;
       unsigned skip = 0;
@@ -156,8 +168,9 @@ struct SegWalker {
         skip = skip_fp64(top53(r.y, r.x) + 1ull, qc, room);
       }
       if (skip >= static_cast<unsigned>(room)) return false;
-      j = pos + 1 + static_cast<int32_t>(skip);
+      jv = pos + 1 + static_cast<int32_t>(skip);
     }
+    j = kExcl ? jv + (jv >= ex) : jv;  // the candidate's rank
     // product x_i x_j (a_i a_j) for the acceptance test and the next q
     const df2 prod = df_mul(xi_df, to_df(kUecm ? g.adf[j] : g.xdf[j]));
     if (!head) {
@@ -175,11 +188,12 @@ struct SegWalker {
       if (verdict < 0) {
         if (fast_q) fallbacks += 1;
         if (!have_qc) qc = q64(g, kUecm);
-        const double p = kUecm ? prob_uecm(g.as[gi], g.as[j], g.ys[gi] * g.ys[j]) : prob_ubcm(g.xs[gi], g.xs[j]);
+        const double p =
+            kUecm ? prob_uecm(g.as_r[gi], g.as[j], g.ys_r[gi] * g.ys[j]) : prob_ubcm(g.xs_r[gi], g.xs[j]);
         verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
       }
       accepted = verdict != 0;
-      pos = j;
+      pos = jv;
     }
     // q <- p (UBCM) or phat (UECM) of j
     qj = j;
@@ -233,8 +247,11 @@ __device__ __forceinline__ long long begin_queued(const Net& g, const BatchQueue
   return w.item_begin + local;
 }
 
-template <bool kUecm, bool kBatch>
+// kMode: 0 one network, 1 batched waves, 2 one directed network.
+template <bool kUecm, int kMode>
 __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) {
+  constexpr bool kBatch = kMode == 1;
+  constexpr bool kExcl = kMode == 2;
   extern __shared__ unsigned char smem_raw[];
   LnEntry* tab = reinterpret_cast<LnEntry*>(smem_raw);
   int32_t* slots = reinterpret_cast<int32_t*>(smem_raw + sizeof(LnEntry) * kLnTable);
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
             item = begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1);
           } else {
             item = static_cast<long long>(next + rank);
-            wk.begin(g, item, S, P.c.sample0, kUecm);
+            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
           }
           active = true;
           rewalk = false;
@@ -322,7 +339,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
     if (active) {
       bool acc;
       int32_t j;
-      if (wk.advance<kUecm>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback, acc, j)) {
+      if (wk.advance<kUecm, kExcl>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback, acc,
+                                   j)) {
         if (acc) {
           if (!rewalk) {
             if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
@@ -347,7 +365,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
           if (kBatch)
             begin_queued<kUecm>(g, P.q, qpos, queue_entry(P.q, qpos), wk, lane_key1);
           else
-            wk.begin(g, item, S, P.c.sample0, kUecm);
+            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
           rewalk = true;
           cnt = 0;
         }
@@ -438,19 +456,19 @@ size_t walk_smem_bytes() {
 
 // Shared-memory opt-in and occupancy of the walk kernels, per device (done
 // before a call is captured into a graph).
-static int g_per_sm[64][2][2] = {};
+static int g_per_sm[64][2][3] = {};
 
-template <bool kUecm, bool kBatch>
+template <bool kUecm, int kMode>
 static cudaError_t walk_attributes(int dev) {
-  if (g_per_sm[dev][kUecm][kBatch]) return cudaSuccess;
-  auto kernel = walk_kernel<kUecm, kBatch>;
+  if (g_per_sm[dev][kUecm][kMode]) return cudaSuccess;
+  auto kernel = walk_kernel<kUecm, kMode>;
   const size_t smem = walk_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkWarps * 32, smem);
   if (e != cudaSuccess) return e;
-  g_per_sm[dev][kUecm][kBatch] = per_sm < 1 ? 1 : per_sm;
+  g_per_sm[dev][kUecm][kMode] = per_sm < 1 ? 1 : per_sm;
   return cudaSuccess;
 }
 
@@ -460,15 +478,17 @@ cudaError_t prepare_kernel_attributes(int model) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (model == MH_UECM) {
-    e = walk_attributes<true, false>(dev);
-    return e != cudaSuccess ? e : walk_attributes<true, true>(dev);
+    if ((e = walk_attributes<true, 0>(dev)) != cudaSuccess) return e;
+    if ((e = walk_attributes<true, 1>(dev)) != cudaSuccess) return e;
+    return walk_attributes<true, 2>(dev);
   }
-  e = walk_attributes<false, false>(dev);
-  return e != cudaSuccess ? e : walk_attributes<false, true>(dev);
+  if ((e = walk_attributes<false, 0>(dev)) != cudaSuccess) return e;
+  if ((e = walk_attributes<false, 1>(dev)) != cudaSuccess) return e;
+  return walk_attributes<false, 2>(dev);
 }
 
-static unsigned walk_blocks(int dev, bool uecm, bool batch, int ctas_per_sm) {
-  int per_sm = g_per_sm[dev][uecm][batch];
+static unsigned walk_blocks(int dev, bool uecm, int mode, int ctas_per_sm) {
+  int per_sm = g_per_sm[dev][uecm][mode];
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   int blocks = sm_count() * per_sm;
   if (blocks * kWalkWarps > kMaxWalkWarps) blocks = kMaxWalkWarps / kWalkWarps;
@@ -478,13 +498,15 @@ static unsigned walk_blocks(int dev, bool uecm, bool batch, int ctas_per_sm) {
 cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
   WalkParams P{g, c, ctrl, BatchQueue{}};
   const bool uecm = g.model == MH_UECM;
+  const int mode = g.excl ? 2 : 0;
   cudaError_t e = prepare_kernel_attributes(g.model);
   if (e != cudaSuccess) return e;
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  auto kernel = uecm ? walk_kernel<true, false> : walk_kernel<false, false>;
-  kernel<<<walk_blocks(dev, uecm, false, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  auto kernel = uecm ? (mode ? walk_kernel<true, 2> : walk_kernel<true, 0>)
+                     : (mode ? walk_kernel<false, 2> : walk_kernel<false, 0>);
+  kernel<<<walk_blocks(dev, uecm, mode, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -500,8 +522,8 @@ cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQue
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  auto kernel = uecm ? walk_kernel<true, true> : walk_kernel<false, true>;
-  kernel<<<walk_blocks(dev, uecm, true, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
+  auto kernel = uecm ? walk_kernel<true, 1> : walk_kernel<false, 1>;
+  kernel<<<walk_blocks(dev, uecm, 1, c.walk_ctas_per_sm), kWalkWarps * 32, walk_smem_bytes(), s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

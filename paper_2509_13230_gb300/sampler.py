@@ -71,7 +71,8 @@ class Sampler:
     def __init__(self, model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, num_samples: int = 1,
                  seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
                  layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
-                 capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0):
+                 capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0,
+                 extra_flags: int = 0):
         self.model = int(model)
         self.x = _check_vec("x", x)
         self.n = int(self.x.shape[0])
@@ -84,7 +85,7 @@ class Sampler:
             flags |= nat.MH_INIT_PREV
         if fp64_only:
             flags |= nat.MH_FP64_ONLY
-        self.flags = flags
+        self.flags = flags | int(extra_flags)
         self.num_samples = int(num_samples)
         self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
         self.seg_target = int(seg_target)
@@ -101,9 +102,12 @@ class Sampler:
                                num_samples=self.num_samples, seg_target=self.seg_target, flags=self.flags,
                                max_segments=self.max_segments, walk_ctas_per_sm=self.walk_ctas_per_sm)
 
+    def _workspace_bytes(self, capacity: int) -> int:
+        return nat.mh_workspace_size(self.model, self.n, self.params(), capacity)
+
     def _alloc(self, capacity: int):
         self.capacity = capacity
-        self.ws_bytes = nat.mh_workspace_size(self.model, self.n, self.params(), capacity)
+        self.ws_bytes = self._workspace_bytes(capacity)
         dev = self.device
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         coo = bool(self.flags & nat.MH_OUT_COO)
@@ -154,6 +158,42 @@ class Sampler:
         cut = (lambda t: None if t is None else t[:tot])
         return SampleResult(self.h_counts.copy(), self.h_stats.copy(), cut(self.src), cut(self.dst), cut(self.w),
                             self.csr_off, cut(self.csr_idx), cut(self.csr_w))
+
+
+class BipartiteSampler(Sampler):
+    """Reusable buffers for sampling a bipartite network (Sec. 2.6): rows are
+    the + set (x_plus, y_plus), candidates the - set (x_minus, y_minus).  With
+    directed=True both sets are the same nodes (out- and in-parameters) and
+    the pairs (i, i) are excluded.  CSR rows are + ids.  Other arguments as
+    Sampler (bound and init readings do not apply)."""
+
+    def __init__(self, model: int, x_plus: torch.Tensor, y_plus: torch.Tensor | None, x_minus: torch.Tensor,
+                 y_minus: torch.Tensor | None, *, directed: bool = False, **kw):
+        self.x_minus = _check_vec("x_minus", x_minus)
+        self.n_minus = int(self.x_minus.shape[0])
+        self.y_minus = _check_vec("y_minus", y_minus, self.n_minus) if int(model) == nat.MH_UECM else None
+        self.directed = bool(directed)
+        # self.n is the + set's size: CSR offsets take n_plus + 1 per sample
+        super().__init__(model, x_plus, y_plus, extra_flags=nat.MH_DIRECTED if self.directed else 0, **kw)
+
+    def _workspace_bytes(self, capacity: int) -> int:
+        return nat.mh_bipartite_workspace_size(self.model, self.n, self.n_minus, self.params(), capacity)
+
+    def call(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> int:
+        p = self.params(sample_begin)
+        counts = self.h_counts.ctypes.data_as(ctypes.c_void_p)
+        stats = self.h_stats.ctypes.data_as(ctypes.c_void_p)
+        return nat.mh_sample_bipartite(self.model, _ptr(self.x), _ptr(self.y), self.n, _ptr(self.x_minus),
+                                       _ptr(self.y_minus), self.n_minus, p, _ptr(self.workspace), self.ws_bytes,
+                                       _ptr(self.src), _ptr(self.dst), _ptr(self.w), _ptr(self.csr_off),
+                                       _ptr(self.csr_idx), _ptr(self.csr_w), self.capacity, counts, stats,
+                                       _stream_handle(stream))
+
+
+def sample_bipartite(model: int, x_plus: torch.Tensor, y_plus, x_minus: torch.Tensor, y_minus, *,
+                     directed: bool = False, **kw) -> SampleResult:
+    """Samples of a bipartite or directed network (Sec. 2.6)."""
+    return BipartiteSampler(model, x_plus, y_plus, x_minus, y_minus, directed=directed, **kw).run()
 
 
 def sample_ubcm(x: torch.Tensor, **kw) -> SampleResult:

@@ -64,3 +64,21 @@ def test_sampling_rejects_null_inputs_without_a_gpu(lib):
     assert nat.maxent_expected_bwd(1, None, None, 5, None, None, None, None, None) == nat.MH_ERR_ARG
     info = nat.mh_last_call_info()
     assert info.kernel_launches == 0
+
+
+def test_bipartite_workspace_and_argument_checks(lib):
+    p = nat.make_params(num_samples=3)
+    a = nat.mh_bipartite_workspace_size(nat.MH_UECM, 1000, 3000, p, 10_000)
+    b = nat.mh_bipartite_workspace_size(nat.MH_UECM, 1000, 30_000, p, 10_000)
+    assert b - a >= 27_000 * 48  # the - set's sorted copies grow with n_minus
+    for flags, n_plus, n_minus in [(nat.MH_BOUND_PAPER, 10, 10), (nat.MH_INIT_PREV, 10, 10),
+                                   (nat.MH_DIRECTED, 10, 11)]:
+        q = nat.make_params(flags=nat.MH_OUT_COO | flags)
+        with pytest.raises(nat.MhError) as e:
+            nat.mh_bipartite_workspace_size(nat.MH_UBCM, n_plus, n_minus, q, 10)
+        assert e.value.code == nat.MH_ERR_ARG
+    # MH_DIRECTED belongs to the bipartite call only
+    with pytest.raises(nat.MhError):
+        nat.mh_workspace_size(nat.MH_UBCM, 10, nat.make_params(flags=nat.MH_DIRECTED), 10)
+    # a directed network of equal sets is fine
+    assert nat.mh_bipartite_workspace_size(nat.MH_UBCM, 10, 10, nat.make_params(flags=nat.MH_DIRECTED), 10) > 0
