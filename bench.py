@@ -428,6 +428,80 @@ def fit_leg(args, dev):
 
 
 # ---------------------------------------------------------------------------
+# Bipartite / directed leg (Sec. 2.6): a directed weighted network of 20,000
+# nodes (10 samples per call, COO + weights) and a 200,000 x 20,000 bipartite
+# unweighted network (2 samples per call, COO).
+# ---------------------------------------------------------------------------
+def bipartite_leg(args, dev, flush):
+    import torch
+
+    import oracle
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.autotune import pick
+    from paper_2509_13230_gb300.sampler import BipartiteSampler
+
+    hbm_gbs, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+    xo, yo, xi, yi = workloads.directed_uecm_n20k()
+    xp, xm = workloads.bipartite_ubcm_pareto()
+    cases = [("directed_uecm_n20k_x10", nat.MH_UECM, (xo, yo, xi, yi), True, 10, 12),
+             ("bipartite_ubcm_200k_20k_x2", nat.MH_UBCM, (xp, None, xm, None), False, 2, 8)]
+    for name, model, arrays, directed, samples, bytes_per_edge in cases:
+        t_arrays = [None if a is None else torch.from_numpy(a).to(dev) for a in arrays]
+        # segment length from the autotuner's rule on a short probe
+        table = []
+        for T in (8, 16, 32):
+            s = BipartiteSampler(model, *t_arrays, directed=directed, num_samples=samples, seg_target=T)
+            s.run()
+            s.flags |= nat.MH_TIMING
+            ms, edges = 0.0, 0
+            for _ in range(4):
+                nat.check(s.call(), "mh_sample_bipartite")
+                ms += nat.mh_last_call_info().total_ms
+                edges += int(s.h_counts.sum())
+            table.append({"T": T, "ctas": 0, "ms": ms / 4, "edges": edges // 4, "edges_per_ms": edges / ms})
+        T, _ = pick(table)
+        s = BipartiteSampler(model, *t_arrays, directed=directed, num_samples=samples, seg_target=T)
+        s.run()
+        s.flags |= nat.MH_TIMING
+        for _ in range(args.warmup):
+            nat.check(s.call(), "mh_sample_bipartite")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total_ms, edges = 0.0, 0
+        phase = np.zeros(3)
+        steps = max(args.steps, 5)
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            nat.check(s.call(), "mh_sample_bipartite")
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            info = nat.mh_last_call_info()
+            phase += (info.prepare_ms, info.walk_ms, info.emit_ms)
+            edges += int(s.h_counts.sum())
+        walk_ms = phase[1]
+        achieved = bytes_per_edge * edges / (walk_ms / 1e3) / 1e9
+        t0 = time.perf_counter()
+        _, _, _, c, _ = oracle.bip_sample(model, *arrays, directed=directed, num_samples=1, seg_target=T)
+        cpu_s = time.perf_counter() - t0
+        out[name] = {"value": edges / (total_ms / 1e3), "unit": "edges/s", "ms_per_step": total_ms / steps,
+                     "samples_per_step": samples, "edges_per_step": edges // steps, "seg_target": T,
+                     "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit"), (phase / steps).tolist())),
+                     "autotune": table,
+                     "roofline": {"bound": "hbm", "kernel": "walk_kernel", "achieved": achieved, "peak": hbm_gbs,
+                                  "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+                                  "peak_kind": peak_kind, "walk_ms_per_step": walk_ms / steps,
+                                  "bytes_per_edge": bytes_per_edge},
+                     "cpu_baseline": {"value": int(c.sum()) / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"one sample of the same network, serial FP64 walk, {cpu_s:.2f} s"}}
+        del s
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Replicas: rank r draws samples [r S, (r + 1) S) of the same network (the
 # counters are keyed by sample, so the union is the single-GPU ensemble);
 # the job's time is the slowest rank's and its edges are all ranks' edges.
@@ -571,10 +645,11 @@ def run_ours(args, rank, world, local_rank):
         # the other reading of the ensemble's fitness: z ~ N(-4, 1.2), 8 samples per network
         ensemble_lognormal = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8, capacity=1 << 30,
                                           seg_target=ensemble["seg_target"], loop_samples=1)
-    pairwise = fitted = None
+    pairwise = fitted = bipartite = None
     if world == 1 and not args.no_ensemble:
         pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
         fitted = fit_leg(args, dev)
+        bipartite = bipartite_leg(args, dev, flush)
     if world > 1:
         dist.barrier()
 
@@ -621,6 +696,7 @@ def run_ours(args, rank, world, local_rank):
         "ensemble_lognormal": ensemble_lognormal,
         "pairwise": pairwise,
         "fit_then_sample": fitted,
+        "bipartite": bipartite,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -635,7 +711,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit"], default="all",
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--ensemble-seg-target", type=int, default=0,
@@ -663,6 +739,12 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"fit_then_sample": fit_leg(args, torch.device("cuda", local_rank))}), flush=True)
+    elif args.leg == "bipartite":
+        import torch
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"bipartite": bipartite_leg(args, dev, flush)}), flush=True)
     elif args.leg == "pairwise":
         import torch
         torch.cuda.set_device(local_rank)

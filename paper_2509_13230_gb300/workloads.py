@@ -133,6 +133,27 @@ def degree_strength_targets(n: int = 200_000, exponent: float = 2.5, k_min: int 
     return k, k * wbar
 
 
+def directed_uecm_n20k(n: int = 20_000, seed: int = 6):
+    """Directed weighted network (Sec. 2.6): out- and in-parameters of N =
+    20,000 nodes, x = exp(z), z ~ N(-4.0, 1.2), y ~ U(0.3, 0.9) on both sides.
+    Returns (x_out, y_out, x_in, y_in)."""
+    rng = np.random.default_rng(seed)
+    return (np.exp(rng.normal(-4.0, 1.2, n)), rng.uniform(0.3, 0.9, n), np.exp(rng.normal(-4.0, 1.2, n)),
+            rng.uniform(0.3, 0.9, n))
+
+
+def bipartite_ubcm_pareto(n_plus: int = 200_000, n_minus: int = 20_000, seed: int = 7):
+    """Bipartite unweighted network (Sec. 2.6), e.g. users x items: capped
+    Pareto fitness on both sides, scales chosen so that a + node has about 10
+    expected edges.  Returns (x_plus, x_minus)."""
+    rng = np.random.default_rng(seed)
+    up = np.where((u := rng.uniform(0.0, 1.0, n_plus)) > 0.0, u, np.finfo(np.float64).tiny)
+    um = np.where((u := rng.uniform(0.0, 1.0, n_minus)) > 0.0, u, np.finfo(np.float64).tiny)
+    xp = np.minimum(2e-3 * up ** (-1.0 / 1.1), 50.0)
+    xm = np.minimum(0.0125 * um ** (-1.0 / 1.1), 50.0)
+    return xp, xm
+
+
 WORKLOADS = {
     "ubcm_n1k_x100": dict(make=ubcm_n1k, samples=100, output="coo"),
     "uecm_n20k_x10": dict(make=uecm_n20k, samples=10, output="coo"),
