@@ -146,6 +146,7 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.keys1 = take(8 * nm);
   L.vals0 = take(4 * nm);
   L.vals1 = take(4 * nm);
+  L.tsuf = take(sizeof(Top2) * nm);
   L.hist = take(4 * 256 * static_cast<size_t>(L.tiles));
   L.perm = take(4 * static_cast<size_t>(n));
   L.rank = take(4 * static_cast<size_t>(n));
@@ -361,6 +362,10 @@ static int check_params(int model, int64_t n, const mh_params* p) { return check
 // Sort, gather, bound prep and segment table into the workspace.
 // Validation, sort and gather of one node set (g.n nodes).
 static int sort_set(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  if (merge_sorted(g.n)) {
+    MH_CUDA(launch_sort_merge(g, L, ws, ctrl, s));
+    return MH_OK;
+  }
   MH_CUDA(cudaMemsetAsync(&ctrl->key_or, 0, sizeof(ctrl->key_or), s));
   MH_CUDA(cudaMemsetAsync(&ctrl->key_and, 0xFF, sizeof(ctrl->key_and), s));
   MH_CUDA(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));

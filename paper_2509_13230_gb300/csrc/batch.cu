@@ -148,6 +148,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
     L.keys1 = ltake(8 * nm);
     L.vals0 = ltake(4 * nm);
     L.vals1 = ltake(4 * nm);
+    L.tsuf = ltake(sizeof(Top2) * nm);
     L.hist = ltake(4 * 256 * tiles);
     L.zero_begin = lo;
     L.ghist = ltake(4 * 8 * 256);
@@ -220,6 +221,7 @@ Layout net_layout(const BatchLayout& B, const BatchNet& bn, int lane) {
   L.keys1 += lane_at;
   L.vals0 += lane_at;
   L.vals1 += lane_at;
+  L.tsuf += lane_at;
   L.hist += lane_at;
   L.zero_begin += lane_at;
   L.ghist += lane_at;

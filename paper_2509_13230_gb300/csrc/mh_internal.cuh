@@ -50,6 +50,9 @@ struct Ctrl {
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;  // keys per sort tile
+constexpr int kMergeMaxTiles = 32;                  // tile sorts + merge up to this many tiles
+// Node sets sorted by tile sorts + merge, which also leave the suffix top-2 of y.
+__host__ __device__ inline bool merge_sorted(int64_t n) { return (n + kSortTile - 1) / kSortTile <= kMergeMaxTiles; }
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;
@@ -74,7 +77,7 @@ struct Layout {
          as = 0, top1 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
          item_off = 0, sample_counts = 0, staging = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
          lntab = 0, seg_c = 0, seg_cf = 0, ghist = 0, sort_state = 0, sort_counters = 0, scan_flags = 0,
-         scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, total = 0;
+         scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, tsuf = 0, total = 0;
   int64_t scan_tiles = 0;
   int64_t staging_entries = 0;
 };
@@ -191,6 +194,9 @@ cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t
                                  cudaStream_t s);
 cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s);
+// Sets of at most kMergeMaxTiles tiles: validation, tile sorts, then merge by
+// rank and gather (two launches); also clears the single-pass scan states.
+cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_exclusions(const Net& g, cudaStream_t s);  // directed: excl[i] = rank of row i's own node
 

@@ -175,8 +175,9 @@ cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws,
   e = scan_any<unsigned long long, SumOp<unsigned long long>>(g.Q, g.Q, ScanLen{g.n, nullptr, 1}, true,
                                                                     nullptr, nullptr, true, st, s);
   if (e != cudaSuccess) return e;
-  if (g.model == MH_UECM) {
+  if (g.model == MH_UECM && !merge_sorted(g.n)) {
     // top[i] = two largest y among ranks >= i; top[i].a is the suffix maximum
+    // (the tile sorts + merge of small node sets leave it already)
     e = scan_any<Top2, Top2Op, true>(g.top, g.top, ScanLen{g.n, nullptr, 1}, false, nullptr, nullptr, false,
                                            st, s);
     if (e != cudaSuccess) return e;

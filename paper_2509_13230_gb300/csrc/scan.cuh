@@ -200,7 +200,6 @@ cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T*
 // forever (the call then reports MH_ERR_DEVICE_TIMEOUT).  The last block to
 // finish clears the tile states and tickets for the next scan.
 constexpr unsigned kSpinLimit = 1u << 22;
-constexpr int kLookBack = 16;  // predecessor tiles read per look-back step
 
 struct ScanState {
   unsigned* flags;     // per tile: 0 empty, 1 aggregate published, 2 inclusive prefix published
@@ -222,6 +221,55 @@ __device__ __forceinline__ double load_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ Top2 load_cg(const Top2* p) {
   const double* d = reinterpret_cast<const double*>(p);
   return Top2{__ldcg(d), __ldcg(d + 1)};
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor(unsigned long long v, int d) {
+  return __shfl_xor_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ long long shfl_xor(long long v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ unsigned shfl_xor(unsigned v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_xor(double v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ Top2 shfl_xor(Top2 v, int d) {
+  return Top2{__shfl_xor_sync(0xffffffffu, v.a, d), __shfl_xor_sync(0xffffffffu, v.b, d)};
+}
+
+// Exclusive prefix of tile `tile` from its predecessors' published values,
+// by one full warp: lane q reads tile - 1 - q - 32 w in step w, so 32 flags
+// and values are in flight at once.  The lanes up to the nearest inclusive
+// prefix are combined in lane order's reverse, which is exact because every
+// operator here is commutative (integer sums, max, top-2).  Waits on a flag
+// are bounded: after kSpinLimit polls the lane records kStTimeout and stops
+// waiting (the call then reports MH_ERR_DEVICE_TIMEOUT).
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_look_back(int64_t tile, const unsigned* flags, const T* agg_v, const T* inc_v,
+                                            Ctrl* ctrl) {
+  Op op;
+  const int lane = threadIdx.x & 31;
+  T prefix = Op::identity();
+  for (int64_t top = tile - 1;; top -= 32) {
+    const int64_t tq = top - lane;
+    unsigned f = tq >= 0 ? poll_flag(&flags[tq]) : 2u;  // before tile 0: an empty inclusive prefix
+    for (unsigned it = 0; __any_sync(0xffffffffu, f == 0u); ++it) {
+      if (f == 0u) {
+        if (it >= kSpinLimit) {
+          atomicOr(&ctrl->status, kStTimeout);
+          f = 2u;  // give up: publish below so successors finish
+        } else {
+          __nanosleep(32);
+          f = poll_flag(&flags[tq]);
+        }
+      }
+    }
+    const unsigned inc = __ballot_sync(0xffffffffu, f == 2u);
+    const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest lane holding an inclusive prefix
+    __threadfence();
+    T v = Op::identity();
+    if (lane <= stop && tq >= 0) v = load_cg(f == 2u ? &inc_v[tq] : &agg_v[tq]);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v = op(v, shfl_xor(v, d));
+    prefix = op(v, prefix);
+    if (inc) return prefix;
+  }
 }
 
 template <typename T, typename Op, bool kReverse>
@@ -256,49 +304,25 @@ __global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in,
     }
     T inc = acc;
     const T agg = block_inclusive_scan<T, Op>(inc, warp_sums);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       T prefix = Op::identity();
       if (tile == 0) {
         if (base) prefix = *base;
       } else {
-        agg_v[tile] = agg;
-        __threadfence();
-        atomicExch(&st.flags[tile], 1u);
-        // walk back kLookBack tiles per step (independent loads in flight)
-        int64_t t = tile - 1;
-        bool done = false;
-        while (!done) {
-          unsigned f[kLookBack];
-#pragma unroll
-          for (int q = 0; q < kLookBack; ++q) f[q] = (t - q >= 0) ? poll_flag(&st.flags[t - q]) : 2u;
-#pragma unroll
-          for (int q = 0; q < kLookBack; ++q) {
-            if (done) break;
-            const int64_t tq = t - q;
-            if (tq < 0) {
-              done = true;
-              break;
-            }
-            for (unsigned it = 0; f[q] == 0u; ++it) {
-              if (it >= kSpinLimit) {
-                atomicOr(&st.ctrl->status, kStTimeout);
-                f[q] = 2u;  // give up: publish below so successors finish
-                break;
-              }
-              __nanosleep(32);
-              f[q] = poll_flag(&st.flags[tq]);
-            }
-            __threadfence();
-            prefix = op(load_cg(f[q] == 2u ? &inc_v[tq] : &agg_v[tq]), prefix);
-            if (f[q] == 2u) done = true;
-          }
-          t -= kLookBack;
+        if (threadIdx.x == 0) {
+          agg_v[tile] = agg;
+          __threadfence();
+          atomicExch(&st.flags[tile], 1u);
         }
+        __syncwarp();
+        prefix = warp_look_back<T, Op>(tile, st.flags, agg_v, inc_v, st.ctrl);
       }
-      inc_v[tile] = op(prefix, agg);
-      __threadfence();
-      atomicExch(&st.flags[tile], 2u);
-      s_prefix = prefix;
+      if (threadIdx.x == 0) {
+        inc_v[tile] = op(prefix, agg);
+        __threadfence();
+        atomicExch(&st.flags[tile], 2u);
+        s_prefix = prefix;
+      }
     }
     T prev = shfl_up(inc, 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

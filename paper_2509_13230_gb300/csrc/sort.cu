@@ -325,39 +325,280 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
 
 
 // Rank-order copies of the parameters (FP64 and double-float), ln y for the
-// weights, the inverse permutation, the fixed-point segment costs
-// floor(min(v, 2^20) * 2^F) (scanned afterwards) and, in block 0, the
-// logarithm table.
-__global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __restrict__ sorted_ids) {
-  if (blockIdx.x == 0) {
-    for (int k = threadIdx.x; k < kLnTable; k += blockDim.x) ln_table_entry(g.lntab, k);
-    if (threadIdx.x == 0 && g.model == MH_UECM) g.top[g.n] = Top2{0.0, 0.0};
+// weights, the inverse permutation and the fixed-point segment cost
+// floor(min(v, 2^20) * 2^F) (scanned afterwards) of the node u at rank r.
+__device__ __forceinline__ void gather_rank(const Net& g, int64_t r, int32_t u, int F) {
+  g.perm[r] = u;
+  g.rank[u] = static_cast<int32_t>(r);
+  const double xu = g.x[u];
+  g.xs[r] = xu;
+  g.xdf[r] = split2(xu);
+  double v = xu;
+  if (g.model == MH_UECM) {
+    const double yu = g.y[u];
+    g.ys[r] = yu;
+    v = xu * yu;
+    g.as[r] = v;
+    g.adf[r] = split2(v);
+    g.ydf[r] = split2(yu);
+    g.lny[r] = split2(log(yu));
+    g.top[r] = Top2{yu, 0.0};  // scanned in reverse into suffix top-2
   }
-  const int32_t top = sorted_ids[0];
+  const double vc = v > 0x1p20 ? 0x1p20 : v;
+  g.Q[r] = static_cast<unsigned long long>(ldexp(vc, F));
+}
+
+// Block 0's share of a gather: the logarithm table and the sentinel top[n].
+__device__ __forceinline__ void gather_tables(const Net& g) {
+  for (int k = threadIdx.x; k < kLnTable; k += blockDim.x) ln_table_entry(g.lntab, k);
+  if (threadIdx.x == 0 && g.model == MH_UECM) g.top[g.n] = Top2{0.0, 0.0};
+}
+
+__device__ __forceinline__ int top_scale(const Net& g, int32_t top) {
   const double vmax = (g.model == MH_UBCM) ? g.x[top] : g.x[top] * g.y[top];
-  const int F = proxy_scale(vmax, g.n);
+  return proxy_scale(vmax, g.n);
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(Net g, const int32_t* __restrict__ sorted_ids) {
+  if (blockIdx.x == 0) gather_tables(g);
+  const int F = top_scale(g, sorted_ids[0]);
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < g.n;
-       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int32_t u = sorted_ids[r];
-    g.perm[r] = u;
-    g.rank[u] = static_cast<int32_t>(r);
-    const double xu = g.x[u];
-    g.xs[r] = xu;
-    g.xdf[r] = split2(xu);
-    double v = xu;
-    if (g.model == MH_UECM) {
-      const double yu = g.y[u];
-      g.ys[r] = yu;
-      v = xu * yu;
-      g.as[r] = v;
-      g.adf[r] = split2(v);
-      g.ydf[r] = split2(yu);
-      g.lny[r] = split2(log(yu));
-      g.top[r] = Top2{yu, 0.0};  // scanned in reverse into suffix top-2
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    gather_rank(g, r, sorted_ids[r], F);
+}
+
+// ---- small node sets: tile sorts + merge by rank ---------------------------------
+// Up to kMergeMaxTiles tiles of kSortTile keys.  Each block validates and
+// sorts one tile in shared memory by (key, id), a total order since ids are
+// distinct: every warp sorts 64 entries with a bitonic network over
+// shuffles, then five merge levels double the sorted runs, each entry moving
+// to its own position in its run plus the number of smaller entries in the
+// partner run (a binary search).  For UECM the block also writes, for every
+// position of the sorted tile, the two largest y at that position or later.
+// The merge kernel then finds every node's rank as its position in its own
+// tile plus, for every other tile, the number of smaller entries there (a
+// search over every 32nd entry kept in shared memory, then five steps in the
+// tile); the two largest y among ranks >= r combine the tiles' suffixes at
+// those positions.  The order is the radix sort's: descending value, ties by
+// ascending id.
+constexpr int kMergeThreads = 256;
+constexpr int kMergeGroup = 8;                             // threads per node in the merge
+constexpr int kMergeStride = 32;                           // tile entries per shared sample
+constexpr int kMergeSamples = kSortTile / kMergeStride;    // samples per tile
+constexpr int kTileThreads = kSortTile / 2;
+
+__device__ __forceinline__ bool key_less(unsigned long long ka, int32_t ia, unsigned long long kb, int32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Entries of 64-long warp runs: lane holds indices lane and lane + 32.
+__device__ __forceinline__ void warp_bitonic64(unsigned long long& k0, int32_t& i0, unsigned long long& k1,
+                                               int32_t& i1) {
+  const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+  for (unsigned k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // partner in the same lane; k == 64, ascending
+        if (key_less(k1, i1, k0, i0)) {
+          const unsigned long long tk = k0;
+          const int32_t ti = i0;
+          k0 = k1;
+          i0 = i1;
+          k1 = tk;
+          i1 = ti;
+        }
+      } else {
+        const unsigned long long pk0 = __shfl_xor_sync(0xffffffffu, k0, j);
+        const int32_t pi0 = __shfl_xor_sync(0xffffffffu, i0, j);
+        const unsigned long long pk1 = __shfl_xor_sync(0xffffffffu, k1, j);
+        const int32_t pi1 = __shfl_xor_sync(0xffffffffu, i1, j);
+        const bool lower = (lane & j) == 0;
+        // index lane: ascending iff bit k of lane is clear; index lane + 32: bit k of lane + 32
+        const bool asc0 = (lane & k) == 0, asc1 = ((lane + 32) & k) == 0;
+        const bool pl0 = key_less(pk0, pi0, k0, i0), pl1 = key_less(pk1, pi1, k1, i1);
+        if ((asc0 == lower) == pl0) {  // keep the smaller when asc0 == lower
+          k0 = pk0;
+          i0 = pi0;
+        }
+        if ((asc1 == lower) == pl1) {
+          k1 = pk1;
+          i1 = pi1;
+        }
+      }
     }
-    const double vc = v > 0x1p20 ? 0x1p20 : v;
-    g.Q[r] = static_cast<unsigned long long>(ldexp(vc, F));
   }
+}
+
+// Number of entries of the sorted run [run, run + len) below (k, id); len a power of two.
+__device__ __forceinline__ int smem_rank(const unsigned long long* sk, const int32_t* si, int run, int len,
+                                         unsigned long long k, int32_t id) {
+  int pos = 0;
+  for (int step = len; step >= 1; step >>= 1)
+    if (pos + step <= len && key_less(sk[run + pos + step - 1], si[run + pos + step - 1], k, id)) pos += step;
+  return pos;
+}
+
+__global__ void __launch_bounds__(kTileThreads) tile_sort_kernel(int model, const double* __restrict__ x,
+                                                                 const double* __restrict__ y, int64_t n,
+                                                                 unsigned long long* __restrict__ kout,
+                                                                 int32_t* __restrict__ vout, Top2* __restrict__ tsuf,
+                                                                 Ctrl* ctrl, unsigned* clear, int64_t clear_words) {
+  __shared__ unsigned long long sk[kSortTile];
+  __shared__ int32_t si[kSortTile];
+  __shared__ Top2 warp_sums[kTileThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + t; w < clear_words;
+       w += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    clear[w] = 0u;  // single-pass scan states for the bound prep that follows
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+  bool bad = false;
+  unsigned long long k[2];
+  int32_t id[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t u = base + 64 * warp + 32 * h + lane;
+    k[h] = ~0ull;  // padding: distinct ids above every node id sort after all nodes, zero-valued ones included
+    id[h] = INT32_MAX - (64 * warp + 32 * h + lane);
+    if (u < n) {
+      const double xu = x[u];
+      bad |= !(xu >= 0.0 && xu <= 1e150);
+      double v = xu;
+      if (model == MH_UECM) {
+        const double yu = y[u];
+        bad |= !(yu >= 0.0 && yu < 1.0);
+        v = xu * yu;
+      }
+      v = (v > 0.0) ? v : 0.0;  // -0.0 sorts as +0.0; a bad input is reported through the status
+      k[h] = ~static_cast<unsigned long long>(__double_as_longlong(v));
+      id[h] = static_cast<int32_t>(u);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctrl->status, kStDomain);
+  warp_bitonic64(k[0], id[0], k[1], id[1]);
+  int pos[2] = {64 * warp + lane, 64 * warp + 32 + lane};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    sk[pos[h]] = k[h];
+    si[pos[h]] = id[h];
+  }
+  __syncthreads();
+  for (int len = 64; len < kSortTile; len <<= 1) {
+    int np[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int run = pos[h] & ~(len - 1), partner = run ^ len;
+      np[h] = (run & ~(2 * len - 1)) + (pos[h] - run) + smem_rank(sk, si, partner, len, k[h], id[h]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      pos[h] = np[h];
+      sk[pos[h]] = k[h];
+      si[pos[h]] = id[h];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (base + pos[h] < n) {
+      kout[base + pos[h]] = k[h];
+      vout[base + pos[h]] = id[h];
+    }
+  }
+  if (model != MH_UECM) return;
+  // suffix top-2 of y in sorted order: thread t holds positions 2047 - 2t and
+  // 2046 - 2t, so an inclusive scan in thread order runs from the tile's end
+  double* sy = reinterpret_cast<double*>(sk);
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) sy[pos[h]] = (base + pos[h] < n) ? y[id[h]] : 0.0;
+  __syncthreads();
+  const int p_hi = kSortTile - 1 - 2 * t, p_lo = p_hi - 1;
+  const Top2 one_hi{sy[p_hi], 0.0}, one_lo{sy[p_lo], 0.0};
+  Top2Op op;
+  Top2 v = op(one_hi, one_lo);
+  block_inclusive_scan<Top2, Top2Op>(v, warp_sums);  // suffix from p_lo on
+  Top2 prev = shfl_up(v, 1);
+  __shared__ Top2 last_of_warp[kTileThreads / 32];
+  if (lane == 31) last_of_warp[warp] = v;
+  __syncthreads();
+  if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Top2Op::identity();
+  if (base + p_hi < n) tsuf[base + p_hi] = op(prev, one_hi);
+  if (base + p_lo < n) tsuf[base + p_lo] = v;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, const unsigned long long* __restrict__ keys,
+                                                                     const int32_t* __restrict__ ids,
+                                                                     const Top2* __restrict__ tsuf, int tiles,
+                                                                     Ctrl* ctrl) {
+  __shared__ unsigned long long sk[kMergeMaxTiles * kMergeSamples];
+  __shared__ int32_t si[kMergeMaxTiles * kMergeSamples];
+  __shared__ int32_t s_top;
+  const int64_t n = g.n;
+  for (int q = threadIdx.x; q < tiles * kMergeSamples; q += blockDim.x) {
+    const int64_t e = static_cast<int64_t>(q / kMergeSamples) * kSortTile +
+                      static_cast<int64_t>(q % kMergeSamples) * kMergeStride;
+    sk[q] = e < n ? keys[e] : ~0ull;
+    si[q] = e < n ? ids[e] : INT32_MAX;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the largest value heads one of the tiles
+    int best = 0;
+    for (int q = 1; q < tiles; ++q)
+      if (key_less(sk[q * kMergeSamples], si[q * kMergeSamples], sk[best * kMergeSamples], si[best * kMergeSamples]))
+        best = q;
+    s_top = si[best * kMergeSamples];
+  }
+  if (blockIdx.x == 0) gather_tables(g);
+  __syncthreads();
+  const bool uecm = g.model == MH_UECM;
+  const int F = top_scale(g, s_top);
+  const int64_t e = blockIdx.x * static_cast<int64_t>(kMergeThreads / kMergeGroup) + threadIdx.x / kMergeGroup;
+  const int gl = threadIdx.x % kMergeGroup;
+  const bool live = e < n;
+  const unsigned long long k = live ? keys[e] : 0ull;
+  const int32_t id = live ? ids[e] : 0;
+  const int own = static_cast<int>(e / kSortTile);
+  long long below = 0;     // entries of this thread's tiles below (k, id)
+  Top2 above{0.0, 0.0};    // two largest y of those tiles' entries above (k, id)
+  Top2Op op;
+  for (int q = gl; live && q < tiles; q += kMergeGroup) {
+    if (q == own) continue;
+    const int64_t tb = static_cast<int64_t>(q) * kSortTile;
+    const int len = static_cast<int>((n - tb) < kSortTile ? (n - tb) : kSortTile);
+    const int ns = (len + kMergeStride - 1) / kMergeStride;
+    const unsigned long long* qk = sk + q * kMergeSamples;
+    const int32_t* qi = si + q * kMergeSamples;
+    int s = 0;  // samples below (k, id)
+#pragma unroll
+    for (int half = kMergeSamples; half >= 1; half >>= 1)
+      if (s + half <= ns && key_less(qk[s + half - 1], qi[s + half - 1], k, id)) s += half;
+    int c = 0;  // entries of tile q below (k, id)
+    if (s > 0) {
+      c = (s - 1) * kMergeStride + 1;
+#pragma unroll
+      for (int half = kMergeStride / 2; half >= 1; half >>= 1) {
+        const int at = c + half - 1;
+        if (at < len && key_less(keys[tb + at], ids[tb + at], k, id)) c += half;
+      }
+    }
+    below += c;
+    if (uecm && c < len) above = op(above, tsuf[tb + c]);
+  }
+#pragma unroll
+  for (int d = kMergeGroup / 2; d; d >>= 1) {
+    below += __shfl_xor_sync(0xffffffffu, below, d);
+    above = op(above, Top2{__shfl_xor_sync(0xffffffffu, above.a, d), __shfl_xor_sync(0xffffffffu, above.b, d)});
+  }
+  if (!live || gl != 0) return;
+  const int64_t r = e - static_cast<int64_t>(own) * kSortTile + below;
+  if (r >= n) {
+    atomicOr(&ctrl->status, kStInternal);
+    return;
+  }
+  gather_rank(g, r, id, F);
+  if (uecm) g.top[r] = op(tsuf[e], above);  // two largest y among ranks >= r
 }
 
 }  // namespace
@@ -413,6 +654,21 @@ cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cud
     v1 = vt;
   }
   return cudaSuccess;  // eight passes: the result is back in keys0 / vals0
+}
+
+cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
+  const int tiles = static_cast<int>((g.n + kSortTile - 1) / kSortTile);
+  auto* k1 = reinterpret_cast<unsigned long long*>(ws + L.keys1);
+  auto* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
+  // the scan counters and flags are adjacent at the end of the zeroed region
+  auto* clear = reinterpret_cast<unsigned*>(ws + L.scan_counters);
+  const int64_t clear_words = static_cast<int64_t>((L.zero_end - L.scan_counters) / 4);
+  auto* tsuf = reinterpret_cast<Top2*>(ws + L.tsuf);
+  tile_sort_kernel<<<tiles, kTileThreads, 0, s>>>(g.model, g.x, g.y, g.n, k1, v1, tsuf, ctrl, clear, clear_words);
+  merge_gather_kernel<<<grid_for(g.n, kMergeThreads / kMergeGroup), kMergeThreads, 0, s>>>(g, k1, v1, tsuf, tiles,
+                                                                                            ctrl);
+  note_launches(2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s) {

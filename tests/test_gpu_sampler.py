@@ -208,7 +208,7 @@ def test_call_info_counts_launches():
     s.run()
     info = nat.mh_last_call_info()
     assert info.walk_launches == 1 and info.sample_chunks == 1
-    assert 10 <= info.kernel_launches <= 30
+    assert 5 <= info.kernel_launches <= 30
     assert info.walk_ms > 0 and info.total_ms >= info.walk_ms
 
 
