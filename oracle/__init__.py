@@ -13,6 +13,8 @@ Everything here is plain and slow on purpose:
   FP64 with correctly rounded summation (``math.fsum``).
 * ``graph_probabilities`` enumerates every simple graph of a tiny network
   and multiplies the independent pair probabilities (Eq. 1 / Eq. 3).
+* ``symmetric_csr`` lists every sampled edge in both endpoint rows, in the
+  sample's edge order.
 * ``bip_*`` are the same for bipartite and directed networks (Sec. 2.6): the
   rows are the + set, the candidates the - set; a directed network uses the
   out-parameters as the + set and the in-parameters as the - set, without
@@ -309,6 +311,38 @@ def graph_codes(src, dst, counts, n):
         codes[s] = code
         pos += int(c)
     return codes
+
+
+def symmetric_csr(src, dst, w, counts, n):
+    """Every edge of every sample in both endpoint rows.
+
+    Sample s's rows follow the samples before it; each edge, taken in the
+    sample's output order, appends v to row u and u to row v (weights
+    alongside).  Returns (offsets int64[S (n + 1)] as global positions,
+    indices int32[2 M], weights int32[2 M] or None)."""
+    S = len(counts)
+    offsets = np.zeros(S * (n + 1), dtype=np.int64)
+    indices, weights = [], []
+    pos = 0
+    for s in range(S):
+        rows = [[] for _ in range(n)]
+        for e in range(pos, pos + int(counts[s])):
+            u, v = int(src[e]), int(dst[e])
+            we = None if w is None else int(w[e])
+            rows[u].append((v, we))
+            rows[v].append((u, we))
+        base = len(indices)
+        for u in range(n):
+            offsets[s * (n + 1) + u] = base
+            for v, we in rows[u]:
+                indices.append(v)
+                weights.append(we)
+            base = len(indices)
+        offsets[s * (n + 1) + n] = base
+        pos += int(counts[s])
+    idx = np.array(indices, dtype=np.int32)
+    wts = None if w is None else np.array(weights, dtype=np.int32)
+    return offsets, idx, wts
 
 
 # --------------------------------------------------------------------------
