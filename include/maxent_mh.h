@@ -67,6 +67,11 @@ typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
                              /* segment head (p_ii for a row's first segment,      */
                              /* Sec. 2.4 step (ii)); default: q = p at the head    */
 #define MH_DIRECTED 0x40u    /* mh_sample_bipartite: a directed network (Sec. 2.6) */
+#define MH_CSR_SYMMETRIC 0x80u /* with MH_OUT_CSR, mh_sample_ubcm / _weighted only:  */
+                               /* every edge in both endpoint rows, each row's      */
+                               /* neighbours in node order (descending key, ties by */
+                               /* ascending id); csr_indices and csr_weights then   */
+                               /* hold 2 x capacity_edges entries                   */
 #define MH_FP64_ONLY 0x100u  /* decide every draw with the plain FP64 path         */
 #define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
                              /* caller's stream (see mh_last_call_info)            */
@@ -134,7 +139,15 @@ int mh_workspace_size(int model, int64_t n, const mh_params* params, int64_t cap
  *                     the edges whose higher-ranked endpoint is u; offsets are
  *                     global positions in csr_indices.
  *   csr_indices       int32[capacity_edges] (MH_OUT_CSR)
- *   capacity_edges    length of each edge output array
+ *                     With MH_CSR_SYMMETRIC every edge is listed in both
+ *                     endpoint rows (row u: all neighbours of u in node
+ *                     order), offsets are global positions in a
+ *                     csr_indices of int32[2 * capacity_edges], and sample
+ *                     s starts at twice the edges of the samples before it.
+ *                     This is a layout of the same sample: the edges, their
+ *                     weights and the counts are unchanged.
+ *   capacity_edges    length of each edge output array (< 2^31 with
+ *                     MH_CSR_SYMMETRIC)
  *   h_edges_per_sample host int64[num_samples]: edges of each sample
  *   h_stats           host uint64[4] (MH_STAT_*), or NULL
  *

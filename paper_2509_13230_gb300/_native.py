@@ -28,6 +28,7 @@ MH_OUT_CSR = 0x02
 MH_BOUND_PAPER = 0x10
 MH_INIT_PREV = 0x20
 MH_DIRECTED = 0x40
+MH_CSR_SYMMETRIC = 0x80
 MH_FP64_ONLY = 0x100
 MH_TIMING = 0x200
 

@@ -85,7 +85,8 @@ struct PinnedBuffer {
 thread_local PinnedBuffer g_pinned;
 
 constexpr uint32_t kKnownFlags =
-    MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_DIRECTED | MH_FP64_ONLY | MH_TIMING;
+    MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_DIRECTED | MH_CSR_SYMMETRIC | MH_FP64_ONLY |
+    MH_TIMING;
 
 }  // namespace
 
@@ -134,6 +135,11 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   if (rows + 1 > scan_len) scan_len = rows + 1;
   if (L.items_max + 1 > scan_len) scan_len = L.items_max + 1;
   if (spc * (rows + 1) > scan_len) scan_len = spc * (rows + 1);
+  const bool sym = (p.flags & MH_CSR_SYMMETRIC) != 0 && !bip;
+  if (sym) {
+    L.sym_tiles = (capacity + kSortTile - 1) / kSortTile > 0 ? (capacity + kSortTile - 1) / kSortTile : 1;
+    if (256 * L.sym_tiles > scan_len) scan_len = 256 * L.sym_tiles;
+  }
   const size_t n1 = static_cast<size_t>(n) + 1, r1 = static_cast<size_t>(rows) + 1, nm = static_cast<size_t>(nmax);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -187,6 +193,17 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
     L.Q_r = take(8 * r1);
     L.top_r = take(sizeof(Top2) * r1);
     L.excl = take(4 * r);
+  }
+  if (sym) {
+    const size_t c = static_cast<size_t>(capacity > 0 ? capacity : 1);
+    L.sym_k0 = take(8 * c);
+    L.sym_k1 = take(8 * c);
+    L.sym_v0 = take(4 * c);
+    L.sym_v1 = take(4 * c);
+    L.sym_src = take(4 * c);
+    L.sym_w = take(4 * c);
+    L.sym_rev = take(8 * static_cast<size_t>(spc) * r1);
+    L.sym_hist = take(4 * 256 * static_cast<size_t>(L.sym_tiles));
   }
   // states of the single-pass scans and of the one-sweep sort, cleared by one
   // memset per sort (the kernels leave them cleared)
@@ -323,6 +340,10 @@ static int check_params_impl(int model, int64_t rows, int64_t n, bool bip, const
     set_error("MH_DIRECTED applies to mh_sample_bipartite only");
     return MH_ERR_ARG;
   }
+  if ((p->flags & MH_CSR_SYMMETRIC) && (bip || !(p->flags & MH_OUT_CSR))) {
+    set_error("MH_CSR_SYMMETRIC needs MH_OUT_CSR and one node set (mh_sample_ubcm / mh_sample_weighted)");
+    return MH_ERR_ARG;
+  }
   if (bip && (p->flags & (MH_BOUND_PAPER | MH_INIT_PREV))) {
     set_error("MH_BOUND_PAPER and MH_INIT_PREV do not apply to bipartite networks");
     return MH_ERR_ARG;
@@ -447,6 +468,17 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
   c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
   c.walk_ctas_per_sm = static_cast<int>(p->walk_ctas_per_sm);
+  if (L.sym_rev) {
+    c.sym.keys[0] = reinterpret_cast<unsigned long long*>(ws + L.sym_k0);
+    c.sym.keys[1] = reinterpret_cast<unsigned long long*>(ws + L.sym_k1);
+    c.sym.vals[0] = reinterpret_cast<int32_t*>(ws + L.sym_v0);
+    c.sym.vals[1] = reinterpret_cast<int32_t*>(ws + L.sym_v1);
+    c.sym.src = reinterpret_cast<int32_t*>(ws + L.sym_src);
+    c.sym.w = reinterpret_cast<int32_t*>(ws + L.sym_w);
+    c.sym.rev = reinterpret_cast<long long*>(ws + L.sym_rev);
+    c.sym.hist = reinterpret_cast<unsigned*>(ws + L.sym_hist);
+    c.sym.tiles = L.sym_tiles;
+  }
   for (int64_t first = 0; first < static_cast<int64_t>(p->num_samples); first += L.spc) {
     const int64_t left = static_cast<int64_t>(p->num_samples) - first;
     c.chunk_first = first;
@@ -548,8 +580,8 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     set_error("x%s, workspace and h_edges_per_sample must be non-NULL", model == MH_UECM ? ", y" : "");
     return MH_ERR_ARG;
   }
-  if (o.capacity < 0) {
-    set_error("capacity_edges must be >= 0");
+  if (o.capacity < 0 || ((p->flags & MH_CSR_SYMMETRIC) && o.capacity > 0x7FFFFFFFll)) {
+    set_error("capacity_edges must be >= 0 (and < 2^31 with MH_CSR_SYMMETRIC)");
     return MH_ERR_ARG;
   }
   if ((p->flags & MH_OUT_COO) && o.capacity > 0 && (!o.src || !o.dst)) {

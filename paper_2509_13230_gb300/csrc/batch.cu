@@ -842,6 +842,10 @@ int check_batch(const mh_network_desc* nets, int32_t n_nets, const mh_params* p)
     set_error("params->network_id must be 0 for a batch (each network has its own)");
     return MH_ERR_ARG;
   }
+  if (p->flags & MH_CSR_SYMMETRIC) {
+    set_error("MH_CSR_SYMMETRIC applies to mh_sample_ubcm and mh_sample_weighted only");
+    return MH_ERR_ARG;
+  }
   int64_t nodes = 0, segs = 0;
   for (int t = 0; t < n_nets; ++t) {
     const mh_network_desc& d = nets[t];
@@ -1092,6 +1096,10 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     return MH_ERR_ARG;
   }
   const uint32_t fl = params->flags;
+  if (fl & MH_CSR_SYMMETRIC) {
+    set_error("MH_CSR_SYMMETRIC applies to mh_sample_ubcm and mh_sample_weighted only");
+    return MH_ERR_ARG;
+  }
   if ((fl & MH_OUT_COO) && capacity_edges > 0 && (!src || !dst)) {
     set_error("MH_OUT_COO needs src and dst");
     return MH_ERR_ARG;

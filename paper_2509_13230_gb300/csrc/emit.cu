@@ -17,12 +17,20 @@
 
 namespace mh {
 
+#define MH_CUDA_RET(expr)                     \
+  do {                                        \
+    const cudaError_t e_ = (expr);            \
+    if (e_ != cudaSuccess) return e_;         \
+  } while (0)
+
 namespace {
 
 // csr_off[(chunk_first + s)(rows+1) + u] = edges of row u in sample s (0 for
 // u = rows); an in-place exclusive scan then turns counts into offsets.
+// With `rev` (symmetric layout) the count adds the edges arriving at u.
 __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, const Ctrl* ctrl,
-                                 int64_t chunk_first, int64_t chunk_samples, long long* csr_off) {
+                                 int64_t chunk_first, int64_t chunk_samples, long long* csr_off,
+                                 const long long* __restrict__ rev) {
   // A segment table that outgrew max_segments was truncated: rowoff still
   // holds the full prefix, which would index past item_off.  The call fails
   // with MH_ERR_WORKSPACE, so nothing is counted.
@@ -37,16 +45,26 @@ __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, 
     if (u < g.rows) {
       const int64_t i = g.rank_r[u];
       c = item_off[s * S + g.rowoff[i + 1]] - item_off[s * S + g.rowoff[i]];
+      if (rev) c += rev[s * n1 + i];
     }
     csr_off[chunk_first * n1 + t] = c;
   }
 }
+
+// Emit modes.  kEmitPlain writes COO and the one-row CSR.  The symmetric
+// layout takes two passes: kEmitSymPairs writes COO, the (sample, rank of
+// the lower endpoint) key and position of every edge for the key sort, the
+// edge's source and weight by position, and counts the edges arriving at
+// each rank; kEmitSymForward writes every edge into its higher-ranked
+// endpoint's row, after the row's arriving edges.
+enum EmitMode { kEmitPlain = 0, kEmitSymPairs = 1, kEmitSymForward = 2 };
 
 struct EmitParams {
   Net g;
   ChunkArgs c;
   Outputs o;
   Ctrl* ctrl;
+  int mode;
 };
 
 // Each block owns kEmitItems consecutive work items and writes their output
@@ -64,17 +82,31 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   const long long items = S * P.c.chunk_samples;
-  if (blockIdx.x == 0) {
+  const bool unwritten = ctrl->num_segments > g.max_segments ||  // truncated table: the call fails
+                         ctrl->stage_used > static_cast<unsigned long long>(P.c.staging_cap);
+  if (blockIdx.x == 0 && P.mode != kEmitSymForward) {
     // per-sample edge counts of this chunk; the next chunk continues after it
     for (int64_t s = threadIdx.x; s < P.c.chunk_samples; s += blockDim.x)
       P.c.sample_counts[P.c.chunk_first + s] = P.c.item_off[(s + 1) * S] - P.c.item_off[s * S];
-    if (threadIdx.x == 0) ctrl->out_base = ctrl->out_end;
+    if (threadIdx.x == 0) {
+      ctrl->out_base = ctrl->out_end;
+      if (P.mode == kEmitSymPairs) {
+        // the chunk's edges that have a place in the output (none when the
+        // walk's output was not kept), and where its CSR entries start
+        const long long first = P.c.item_off[0];
+        long long len = P.c.item_off[items] - first;
+        const long long room = P.o.capacity - first;
+        if (len > room) len = room;
+        ctrl->sym_len = (unwritten || len < 0) ? 0 : len;
+        ctrl->sym_base = 2 * first;
+      }
+    }
   }
   const long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems;
-  if (it0 >= items || ctrl->num_segments > g.max_segments) return;  // truncated table: the call fails
+  if (it0 >= items) return;
   // Staging that did not fit was never written: emit nothing (the call
   // reports MH_ERR_CAPACITY with exact counts).
-  if (ctrl->stage_used > static_cast<unsigned long long>(P.c.staging_cap)) return;
+  if (unwritten) return;
   const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
   __shared__ long long off[kEmitItems + 1];
   for (long long t = threadIdx.x; t <= it1 - it0; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
@@ -108,6 +140,21 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
       continue;
     }
     const int32_t u = g.perm_r[i], v = g.perm[j];
+    if (P.mode == kEmitSymForward) {
+      // after the row's arriving edges, then the row's own in (segment, candidate) order
+      if (pos >= P.o.capacity) continue;
+      const long long q = pos - P.c.item_off[0];  // position within the chunk
+      const long long s_all = P.c.chunk_first + s_local;
+      const long long row_first = s_local * S + g.rowoff[i];
+      const long long* rv = P.c.sym.rev + s_local * n1;
+      const long long at = P.o.csr_off[s_all * n1 + u] + (rv[i + 1] - rv[i]) +
+                           (P.c.item_off[item] - P.c.item_off[row_first]) + e;
+      if (at >= 0 && at < 2 * P.o.capacity) {
+        P.o.csr_idx[at] = v;
+        if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
+      }
+      continue;
+    }
     int32_t wt = 1;
     if (g.model == MH_UECM) {
       const float2 li = g.lny_r[i], lj = g.lny[j];
@@ -121,7 +168,14 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
         P.o.dst[pos] = v;
         if (P.o.w) P.o.w[pos] = wt;
       }
-      if (P.o.csr_idx) {
+      if (P.mode == kEmitSymPairs) {
+        const long long q = pos - P.c.item_off[0];  // position within the chunk
+        P.c.sym.keys[0][q] = (static_cast<unsigned long long>(s_local) << 32) | static_cast<uint32_t>(j);
+        P.c.sym.vals[0][q] = static_cast<int32_t>(q);
+        P.c.sym.src[q] = u;
+        P.c.sym.w[q] = wt;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.c.sym.rev[s_local * n1 + j]), 1ull);
+      } else if (P.o.csr_idx) {
         const long long s_all = P.c.chunk_first + s_local;
         const long long row_first = s_local * S + g.rowoff[i];
         const long long at = P.o.csr_off[s_all * n1 + u] + (P.c.item_off[item] - P.c.item_off[row_first]) + e;
@@ -136,6 +190,35 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   (void)fallbacks;
 }
 
+// Symmetric layout, second half: the sorted keys list every edge by
+// (sample, rank of its lower-ranked endpoint j), ties in output order, i.e.
+// by the rank of the other endpoint.  Entry t goes to row perm[j] at
+// position t - (first entry of its key), which the scan of the arriving
+// counts gives.
+__global__ void __launch_bounds__(256) sym_reverse_kernel(Net g, SymArgs sym, const unsigned long long* keys,
+                                                          const int32_t* vals, const Ctrl* ctrl, int64_t chunk_first,
+                                                          int64_t chunk_samples, Outputs o, Ctrl* status) {
+  const long long len = ctrl->sym_len;
+  const int64_t n1 = g.n + 1;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < len;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long key = keys[t];
+    const long long s_local = static_cast<long long>(key >> 32);
+    const int64_t j = static_cast<int64_t>(key & 0xFFFFFFFFull);
+    const long long q = vals[t];
+    if (s_local >= chunk_samples || j >= g.n || q < 0 || q >= len) {  // cannot happen: never index with it
+      atomicOr(&status->status, kStInternal);
+      continue;
+    }
+    const long long first = sym.rev[s_local * n1 + j];
+    const long long at = o.csr_off[(chunk_first + s_local) * n1 + g.perm[j]] + (t - first);
+    if (at >= 0 && at < 2 * o.capacity) {
+      o.csr_idx[at] = sym.src[q];
+      if (o.csr_w) o.csr_w[at] = sym.w[q];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl* ctrl, cudaStream_t s) {
@@ -146,18 +229,52 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
                                                   ScanLen{c.items_max, &ctrl->num_segments, c.chunk_samples}, true,
                                                   &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;
-  if (o.csr_off) {
-    const int64_t len = c.chunk_samples * (g.rows + 1);
-    csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
-        g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off);
+  const int64_t len = c.chunk_samples * (g.rows + 1);
+  const unsigned emit_blocks = grid_for(c.items_max, kEmitItems);
+  long long* region = o.csr_off ? o.csr_off + c.chunk_first * (g.rows + 1) : nullptr;
+  if (c.sym.rev && o.csr_off) {
+    // symmetric layout: keys and arriving counts, the key sort, offsets from
+    // both counts, then each edge into both of its rows
+    MH_CUDA_RET(cudaMemsetAsync(c.sym.rev, 0, 8 * static_cast<size_t>(len), s));
+    EmitParams P1{g, c, o, ctrl, kEmitSymPairs};
+    emit_kernel<<<emit_blocks, 256, 0, s>>>(P1);
     note_launches(1);
-    long long* region = o.csr_off + c.chunk_first * (g.rows + 1);
+    csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
+        g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off, c.sym.rev);
+    note_launches(1);
+    e = scan_any<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->sym_base,
+                                                    nullptr, false, st, s);
+    if (e != cudaSuccess) return e;
+    e = scan_any<long long, SumOp<long long>>(c.sym.rev, c.sym.rev, ScanLen{len, nullptr, 1}, true, nullptr,
+                                                    nullptr, false, st, s);
+    if (e != cudaSuccess) return e;
+    // digits of the rank (bytes 0..) and of the sample within the chunk (bytes 4..)
+    int shifts[8], passes = 0;
+    for (int b = 0; b < 4 && (b == 0 || ((g.n - 1) >> (8 * b)) != 0); ++b) shifts[passes++] = 8 * b;
+    for (int b = 0; b < 4 && ((c.chunk_samples - 1) >> (8 * b)) != 0; ++b) shifts[passes++] = 32 + 8 * b;
+    SymArgs sym = c.sym;
+    int buf = 0;
+    e = launch_pair_sort(sym.keys, sym.vals, o.capacity, &ctrl->sym_len, shifts, passes, sym.hist, &st, ctrl, &buf,
+                         s);
+    if (e != cudaSuccess) return e;
+    EmitParams P2{g, c, o, ctrl, kEmitSymForward};
+    emit_kernel<<<emit_blocks, 256, 0, s>>>(P2);
+    note_launches(1);
+    sym_reverse_kernel<<<grid_for(o.capacity, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
+        g, sym, sym.keys[buf], sym.vals[buf], ctrl, c.chunk_first, c.chunk_samples, o, ctrl);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  if (o.csr_off) {
+    csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
+        g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off, nullptr);
+    note_launches(1);
     e = scan_any<long long, SumOp<long long>>(region, region, ScanLen{len, nullptr, 1}, true, &ctrl->out_base,
                                                     nullptr, false, st, s);
     if (e != cudaSuccess) return e;
   }
-  EmitParams P{g, c, o, ctrl};
-  emit_kernel<<<grid_for(c.items_max, kEmitItems), 256, 0, s>>>(P);
+  EmitParams P{g, c, o, ctrl, kEmitPlain};
+  emit_kernel<<<emit_blocks, 256, 0, s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

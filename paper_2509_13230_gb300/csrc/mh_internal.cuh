@@ -44,6 +44,8 @@ struct Ctrl {
   unsigned long long ticket2;   // batched waves: work-queue ticket of the UECM walk
   long long wave_items;         // batched waves: work items of the wave
   long long model_items[2];     // batched waves: work items of the UBCM / UECM queues
+  long long sym_len;            // symmetric CSR: edges of the chunk that fit the capacity
+  long long sym_base;           // symmetric CSR: first index entry of the chunk (2 x its first edge)
 };
 
 // ---- tuning constants --------------------------------------------------------
@@ -78,6 +80,12 @@ struct Layout {
          item_off = 0, sample_counts = 0, staging = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
          lntab = 0, seg_c = 0, seg_cf = 0, ghist = 0, sort_state = 0, sort_counters = 0, scan_flags = 0,
          scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, tsuf = 0, total = 0;
+  // symmetric CSR scratch (MH_CSR_SYMMETRIC): (sample, rank) keys and
+  // positions of the chunk's edges, their sources and weights in output
+  // order, per-(sample, rank) counts of edges arriving at a node, and the
+  // histograms of the key sort
+  size_t sym_k0 = 0, sym_k1 = 0, sym_v0 = 0, sym_v1 = 0, sym_src = 0, sym_w = 0, sym_rev = 0, sym_hist = 0;
+  int64_t sym_tiles = 0;
   int64_t scan_tiles = 0;
   int64_t staging_entries = 0;
 };
@@ -197,8 +205,25 @@ cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, 
 // Sets of at most kMergeMaxTiles tiles: validation, tile sorts, then merge by
 // rank and gather (two launches); also clears the single-pass scan states.
 cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+// Stable LSD sort of `len` (key, value) pairs on the 8-bit digits at the
+// given shifts, `*dev_len` of them (at most host_len) present; the result
+// is in buffer 0 or 1 as returned through *out_buf.  `st` is the scan state.
+cudaError_t launch_pair_sort(unsigned long long* keys[2], int32_t* vals[2], int64_t host_len,
+                             const long long* dev_len, const int* shifts, int passes, unsigned* hist,
+                             const void* scan_state, Ctrl* ctrl, int* out_buf, cudaStream_t s);
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_exclusions(const Net& g, cudaStream_t s);  // directed: excl[i] = rank of row i's own node
+
+// Device scratch of the symmetric CSR layout (all NULL when it is off).
+struct SymArgs {
+  unsigned long long* keys[2];  // (sample in chunk << 32) | rank of the lower-ranked endpoint
+  int32_t* vals[2];             // the edge's position within the chunk
+  int32_t* src;                 // by position: the higher-ranked endpoint's id
+  int32_t* w;                   // by position: the weight (1 for UBCM)
+  long long* rev;               // [chunk samples][n + 1]: edges arriving at each rank, then its exclusive scan
+  unsigned* hist;               // radix histograms, 256 x tiles
+  int64_t tiles;                // key-sort tiles for capacity_edges keys
+};
 
 struct ChunkArgs {
   int64_t chunk_first;  // index of the chunk's first sample within the call
@@ -214,6 +239,7 @@ struct ChunkArgs {
   int64_t staging_cap;
   int64_t items_max;
   int walk_ctas_per_sm;  // 0: as many walk blocks per SM as fit
+  SymArgs sym{};         // symmetric CSR scratch, when requested
 };
 struct Outputs {
   int32_t* src;

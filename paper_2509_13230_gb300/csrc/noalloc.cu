@@ -52,8 +52,9 @@ extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_param
     set_error("x and h_edges_per_sample must be non-NULL and capacity_edges >= 0");
     return MH_ERR_ARG;
   }
-  if (params->num_samples > kNoAllocMaxSamples || (params->flags & MH_TIMING)) {
-    set_error("the fixed-scratch sampler takes at most %u samples per call and no MH_TIMING", kNoAllocMaxSamples);
+  if (params->num_samples > kNoAllocMaxSamples || (params->flags & (MH_TIMING | MH_CSR_SYMMETRIC))) {
+    set_error("the fixed-scratch sampler takes at most %u samples per call, no MH_TIMING and no MH_CSR_SYMMETRIC",
+              kNoAllocMaxSamples);
     return MH_ERR_ARG;
   }
   if ((params->flags & MH_OUT_COO) && capacity_edges > 0 && (!src || !dst)) {

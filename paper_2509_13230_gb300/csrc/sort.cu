@@ -73,11 +73,21 @@ __device__ __forceinline__ bool digit_constant(const Ctrl* ctrl, int shift) {
   return (((ctrl->key_or ^ ctrl->key_and) >> shift) & 0xFFull) == 0ull;
 }
 
-// hist[d * tiles + tile] = number of keys with digit d in the tile.
+// Length of a sort: n, or the device count *dev_len when given (at most n).
+__device__ __forceinline__ int64_t sort_len(int64_t n, const long long* dev_len) {
+  if (!dev_len) return n;
+  const long long v = *dev_len;
+  return v < 0 ? 0 : (v < n ? v : n);
+}
+
+// hist[d * tiles + tile] = number of keys with digit d in the tile.  With
+// ctrl, passes whose digit is constant over all keys are skipped (copy).
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys,
                                                                   int64_t n, int shift, unsigned* __restrict__ hist,
-                                                                  int64_t tiles, const Ctrl* ctrl) {
-  if (digit_constant(ctrl, shift)) return;
+                                                                  int64_t tiles, const Ctrl* ctrl,
+                                                                  const long long* dev_len) {
+  if (ctrl && digit_constant(ctrl, shift)) return;
+  n = sort_len(n, dev_len);
   __shared__ unsigned counts[256];
   counts[threadIdx.x] = 0;
   __syncthreads();
@@ -97,9 +107,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const unsigned
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
     int32_t* __restrict__ vout, int64_t n, int shift, const unsigned* __restrict__ hist, int64_t tiles,
-    const Ctrl* ctrl) {
+    const Ctrl* ctrl, const long long* dev_len) {
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
-  if (digit_constant(ctrl, shift)) {
+  n = sort_len(n, dev_len);
+  if (ctrl && digit_constant(ctrl, shift)) {
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
       const int64_t e = base + r * kSortThreads + threadIdx.x;
@@ -636,12 +647,13 @@ cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cud
       e = cudaGetLastError();
     } else {
       const int shift = pass * 8;
-      radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(k0, g.n, shift, hist, L.tiles, ctrl);
+      radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(k0, g.n, shift, hist, L.tiles, ctrl, nullptr);
       note_launches(1);
       e = scan_any<unsigned, SumOp<unsigned>>(hist, hist, ScanLen{256 * L.tiles, nullptr, 1}, true, nullptr, nullptr,
                                               false, sst, s);
       if (e != cudaSuccess) return e;
-      radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, shift, hist, L.tiles, ctrl);
+      radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(k0, v0, k1, v1, g.n, shift, hist, L.tiles, ctrl,
+                                                            nullptr);
       note_launches(1);
       e = cudaGetLastError();
     }
@@ -669,6 +681,31 @@ cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctr
                                                                                             ctrl);
   note_launches(2);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pair_sort(unsigned long long* keys[2], int32_t* vals[2], int64_t host_len,
+                             const long long* dev_len, const int* shifts, int passes, unsigned* hist,
+                             const void* scan_state, Ctrl* ctrl, int* out_buf, cudaStream_t s) {
+  (void)ctrl;
+  const ScanState& sst = *static_cast<const ScanState*>(scan_state);
+  const int64_t tiles = (host_len + kSortTile - 1) / kSortTile > 0 ? (host_len + kSortTile - 1) / kSortTile : 1;
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    radix_hist_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(keys[cur], host_len, shifts[p], hist,
+                                                                           tiles, nullptr, dev_len);
+    note_launches(1);
+    cudaError_t e = scan_any<unsigned, SumOp<unsigned>>(hist, hist, ScanLen{256 * tiles, nullptr, 1}, true, nullptr,
+                                                        nullptr, false, sst, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+        keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], host_len, shifts[p], hist, tiles, nullptr, dev_len);
+    note_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cur ^= 1;
+  }
+  *out_buf = cur;
+  return cudaSuccess;
 }
 
 cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, cudaStream_t s) {

@@ -61,7 +61,9 @@ class SampleResult:
 class Sampler:
     """Reusable buffers for repeated sampling calls on one network.
 
-    layout: "coo", "csr", "both" or "none" (counts only).
+    layout: "coo", "csr", "both" or "none" (counts only).  symmetric: with a
+    CSR layout, list every edge in both endpoint rows (each row's neighbours
+    in node order); the CSR index and weight arrays then hold 2 x capacity.
     bound: "suffix" (c = y_i max_{j >= head} y_j) or "paper" (two largest y
     among unprocessed nodes, Sec. 2.5).  init: "head" (q = p at the segment
     head) or "prev" (q = p at the rank before it; p_ii for a row's first
@@ -72,7 +74,7 @@ class Sampler:
                  seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
                  layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
                  capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0,
-                 extra_flags: int = 0):
+                 extra_flags: int = 0, symmetric: bool = False):
         self.model = int(model)
         self.x = _check_vec("x", x)
         self.n = int(self.x.shape[0])
@@ -85,6 +87,8 @@ class Sampler:
             flags |= nat.MH_INIT_PREV
         if fp64_only:
             flags |= nat.MH_FP64_ONLY
+        if symmetric:
+            flags |= nat.MH_CSR_SYMMETRIC
         self.flags = flags | int(extra_flags)
         self.num_samples = int(num_samples)
         self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
@@ -118,8 +122,9 @@ class Sampler:
         self.dst = torch.empty(cap, dtype=torch.int32, device=dev) if coo else None
         self.w = torch.empty(cap, dtype=torch.int32, device=dev) if coo and weighted else None
         self.csr_off = torch.empty(self.num_samples * (self.n + 1), dtype=torch.int64, device=dev) if csr else None
-        self.csr_idx = torch.empty(cap, dtype=torch.int32, device=dev) if csr else None
-        self.csr_w = torch.empty(cap, dtype=torch.int32, device=dev) if csr and weighted else None
+        per_edge = 2 if self.flags & nat.MH_CSR_SYMMETRIC else 1
+        self.csr_idx = torch.empty(per_edge * cap, dtype=torch.int32, device=dev) if csr else None
+        self.csr_w = torch.empty(per_edge * cap, dtype=torch.int32, device=dev) if csr and weighted else None
         self.h_counts = np.zeros(self.num_samples, dtype=np.int64)
         self.h_stats = np.zeros(4, dtype=np.uint64)
 
@@ -156,8 +161,10 @@ class Sampler:
     def result(self) -> SampleResult:
         tot = int(self.h_counts.sum())
         cut = (lambda t: None if t is None else t[:tot])
+        ctot = 2 * tot if self.flags & nat.MH_CSR_SYMMETRIC else tot
+        ccut = (lambda t: None if t is None else t[:ctot])
         return SampleResult(self.h_counts.copy(), self.h_stats.copy(), cut(self.src), cut(self.dst), cut(self.w),
-                            self.csr_off, cut(self.csr_idx), cut(self.csr_w))
+                            self.csr_off, ccut(self.csr_idx), ccut(self.csr_w))
 
 
 class BipartiteSampler(Sampler):

@@ -82,3 +82,21 @@ def test_bipartite_workspace_and_argument_checks(lib):
         nat.mh_workspace_size(nat.MH_UBCM, 10, nat.make_params(flags=nat.MH_DIRECTED), 10)
     # a directed network of equal sets is fine
     assert nat.mh_bipartite_workspace_size(nat.MH_UBCM, 10, 10, nat.make_params(flags=nat.MH_DIRECTED), 10) > 0
+
+
+def test_symmetric_csr_workspace_and_argument_checks(lib):
+    sym = nat.MH_OUT_CSR | nat.MH_CSR_SYMMETRIC
+    plain = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=nat.MH_OUT_CSR), 100_000)
+    with_sym = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=sym), 100_000)
+    assert with_sym - plain >= 100_000 * 32  # keys, positions, sources and weights of the edges
+    for bad in [nat.MH_CSR_SYMMETRIC, nat.MH_OUT_COO | nat.MH_CSR_SYMMETRIC]:  # needs MH_OUT_CSR
+        with pytest.raises(nat.MhError) as e:
+            nat.mh_workspace_size(nat.MH_UBCM, 10, nat.make_params(flags=bad), 10)
+        assert e.value.code == nat.MH_ERR_ARG
+    with pytest.raises(nat.MhError) as e:  # one node set only
+        nat.mh_bipartite_workspace_size(nat.MH_UBCM, 10, 12, nat.make_params(flags=sym), 10)
+    assert e.value.code == nat.MH_ERR_ARG
+    desc = nat.network_descs([(nat.MH_UBCM, 0, 10, ctypes.c_void_p(256), None)])  # never dereferenced
+    with pytest.raises(nat.MhError) as e:
+        nat.mh_batch_workspace_size(desc, 1, nat.make_params(flags=sym), 100, 100)
+    assert e.value.code == nat.MH_ERR_ARG
