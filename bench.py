@@ -502,6 +502,48 @@ def bipartite_leg(args, dev, flush):
 
 
 # ---------------------------------------------------------------------------
+# Output layouts of the headline workload: one-row CSR and the symmetric CSR
+# (every edge in both endpoint rows), same samples and segment length.
+# ---------------------------------------------------------------------------
+def layouts_leg(args, dev, flush, T):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.sampler import Sampler
+
+    net = workload()
+    x = torch.from_numpy(net.x).to(dev)
+    y = torch.from_numpy(net.y).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, sym in (("csr", False), ("csr_symmetric", True)):
+        s = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, seg_target=T, layout="csr", symmetric=sym)
+        s.run()
+        s.flags |= nat.MH_TIMING
+        for _ in range(args.warmup):
+            nat.check(s.call(), "mh_sample_weighted")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total_ms, edges, phase = 0.0, 0, np.zeros(3)
+        steps = max(args.steps, 5)
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            nat.check(s.call(), "mh_sample_weighted")
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            info = nat.mh_last_call_info()
+            phase += (info.prepare_ms, info.walk_ms, info.emit_ms)
+            edges += int(s.h_counts.sum())
+        per_edge = 16 if sym else 8  # index + weight per entry, one or two entries per edge
+        out[name] = {"value": edges / (total_ms / 1e3), "unit": "edges/s", "ms_per_step": total_ms / steps,
+                     "output": f"int64 offsets + int32 indices and weights, {per_edge} B/edge",
+                     "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit"), (phase / steps).tolist()))}
+        del s
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Replicas: rank r draws samples [r S, (r + 1) S) of the same network (the
 # counters are keyed by sample, so the union is the single-GPU ensemble);
 # the job's time is the slowest rank's and its edges are all ranks' edges.
@@ -645,11 +687,13 @@ def run_ours(args, rank, world, local_rank):
         # the other reading of the ensemble's fitness: z ~ N(-4, 1.2), 8 samples per network
         ensemble_lognormal = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8, capacity=1 << 30,
                                           seg_target=ensemble["seg_target"], loop_samples=1)
-    pairwise = fitted = bipartite = None
+    pairwise = fitted = bipartite = layouts = None
     if world == 1 and not args.no_ensemble:
         pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
         fitted = fit_leg(args, dev)
         bipartite = bipartite_leg(args, dev, flush)
+    if world == 1:
+        layouts = layouts_leg(args, dev, flush, T)
     if world > 1:
         dist.barrier()
 
@@ -697,6 +741,7 @@ def run_ours(args, rank, world, local_rank):
         "pairwise": pairwise,
         "fit_then_sample": fitted,
         "bipartite": bipartite,
+        "layouts": layouts,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -711,7 +756,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite"], default="all",
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--ensemble-seg-target", type=int, default=0,
@@ -739,6 +784,12 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"fit_then_sample": fit_leg(args, torch.device("cuda", local_rank))}), flush=True)
+    elif args.leg == "layouts":
+        import torch
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"layouts": layouts_leg(args, dev, flush, args.ensemble_seg_target or 8)}), flush=True)
     elif args.leg == "bipartite":
         import torch
         torch.cuda.set_device(local_rank)

@@ -205,6 +205,7 @@ cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, 
 // Sets of at most kMergeMaxTiles tiles: validation, tile sorts, then merge by
 // rank and gather (two launches); also clears the single-pass scan states.
 cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+cudaError_t sort_kernel_attributes(int dev);  // before any capture
 // Stable LSD sort of `len` (key, value) pairs on the 8-bit digits at the
 // given shifts, `*dev_len` of them (at most host_len) present; the result
 // is in buffer 0 or 1 as returned through *out_buf.  `st` is the scan state.

@@ -45,6 +45,7 @@ __device__ __forceinline__ unsigned long long weight_fixed(double w) {
 __device__ __forceinline__ int64_t unit_cut(const Net& g, int64_t i, double w) {
   const double* v = (g.model == MH_UBCM) ? g.xs : g.as;
   int64_t lo = row_start(g, i), hi = g.n;
+  if (lo < hi && w * v[lo] < 1.0) return lo;  // the common case: no candidate costs a whole unit
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo) / 2;
     if (w * v[mid] < 1.0)
@@ -59,15 +60,19 @@ struct RowCost {
   int64_t start, J;  // first candidate of the row, unit cut
   unsigned long long qw;
   int F;
-  __device__ __forceinline__ unsigned long long operator()(const unsigned long long* Q, int64_t b) const {
+  // cumulative cost up to candidate b, given Qb = Q[b] and QJ = Q[J]
+  __device__ __forceinline__ unsigned long long at(int64_t b, unsigned long long Qb, unsigned long long QJ) const {
     const int64_t units = (b < J ? b : J) - start;
     unsigned long long c = static_cast<unsigned long long>(units) << F;
     if (b > J) {
-      const unsigned long long dq = Q[b] - Q[J];
+      const unsigned long long dq = Qb - QJ;
       const unsigned long long lo = qw * dq, hi = __umul64hi(qw, dq);
       c += (hi << 24) | (lo >> 40);
     }
     return c;
+  }
+  __device__ __forceinline__ unsigned long long operator()(const unsigned long long* Q, int64_t b) const {
+    return at(b, b > J ? Q[b] : 0ull, b > J ? Q[J] : 0ull);
   }
 };
 
@@ -101,43 +106,108 @@ __global__ void __launch_bounds__(256) row_count_kernel(Net g) {
   }
 }
 
-// One thread per table row: finds its row by bisection of rowoff, then its
-// two cut points by bisection of the cumulative cost.
+// Last row whose first table row is <= s, within [lo, hi].
+__device__ __forceinline__ int64_t row_of(const Net& g, long long s, int64_t lo, int64_t hi) {
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (g.rowoff[mid] <= s)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// One thread per table row: finds its row (a block's table rows belong to a
+// few consecutive rows, found first by two bisections), then, for rows of
+// more than one segment, its cut points by bisection of the cumulative cost:
+// first over every stride-th entry of Q, kept in shared memory, then over
+// the stride between two of them.  A segment's start is the previous
+// segment's end, taken from the neighbouring lane when it walks the same row.
+constexpr int kFillSamples = 2048;
+
 __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
+  __shared__ int64_t s_lo, s_hi;
+  __shared__ unsigned long long sQ[kFillSamples + 1];
   const long long S = ctrl->num_segments;
   if (blockIdx.x == 0 && threadIdx.x == 0 && S > g.max_segments) atomicOr(&ctrl->status, kStSegments);
   const long long lim = S < g.max_segments ? S : g.max_segments;
   const int F = proxy_F(g);
-  for (long long s = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; s < lim;
-       s += static_cast<long long>(gridDim.x) * blockDim.x) {
-    int64_t lo = 0, hi = g.rows - 1;  // last row with rowoff[row] <= s
-    while (lo < hi) {
-      const int64_t mid = lo + (hi - lo + 1) / 2;
-      if (g.rowoff[mid] <= s)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const int64_t i = lo;
-    const long long k = s - g.rowoff[i];
-    const long long nseg = g.rowoff[i + 1] - g.rowoff[i];
-    const RowCost rc = make_row_cost(g, i, F);
-    const unsigned long long total = rc(g.Q, g.n);
-    const unsigned long long Tc = total / static_cast<unsigned long long>(nseg);
-    auto cut = [&](long long kk) -> int64_t {  // first b in [start+1, n] with cost(b) >= kk * Tc
-      const unsigned long long target = Tc * static_cast<unsigned long long>(kk);
-      int64_t a = rc.start + 1, b = g.n;
-      while (a < b) {
-        const int64_t mid = a + (b - a) / 2;
-        if (rc(g.Q, mid) >= target)
-          b = mid;
-        else
-          a = mid + 1;
+  const int64_t n = g.n;
+  const int64_t stride = n / kFillSamples + 1;  // samples m * stride <= n for m <= ms
+  const int64_t ms = n / stride;
+  for (int64_t m = threadIdx.x; m <= ms; m += blockDim.x) sQ[m] = g.Q[m * stride];
+  const int lane = threadIdx.x & 31;
+  for (long long s0 = blockIdx.x * static_cast<long long>(blockDim.x); s0 < lim;
+       s0 += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long s1 = (s0 + blockDim.x < lim ? s0 + blockDim.x : lim) - 1;
+    __syncthreads();
+    if (threadIdx.x == 0) s_lo = row_of(g, s0, 0, g.rows - 1);
+    if (threadIdx.x == 32) s_hi = row_of(g, s1, 0, g.rows - 1);
+    __syncthreads();
+    const long long s = s0 + threadIdx.x;
+    const bool live = s <= s1;
+    int64_t i = 0, a = 0, b = n;
+    long long k = 0, nseg = 1;
+    if (live) {
+      i = row_of(g, s, s_lo, s_hi);
+      k = s - g.rowoff[i];
+      nseg = g.rowoff[i + 1] - g.rowoff[i];
+      a = row_start(g, i);
+      if (k + 1 < nseg) {
+        const RowCost rc = make_row_cost(g, i, F);
+        const unsigned long long QJ = g.Q[rc.J];
+        const unsigned long long total = rc(g.Q, n);
+        const unsigned long long Tc = total / static_cast<unsigned long long>(nseg);
+        const unsigned long long target = Tc * static_cast<unsigned long long>(k + 1);
+        // first b in [start+1, n] with cost(b) >= target
+        int64_t lo = rc.start + 1, hi = n;
+        int64_t mlo = (lo + stride - 1) / stride, mhi = ms;  // sample indices inside [lo, n]
+        while (mlo < mhi) {
+          const int64_t mid = mlo + (mhi - mlo) / 2;
+          if (rc.at(mid * stride, sQ[mid], QJ) >= target)
+            mhi = mid;
+          else
+            mlo = mid + 1;
+        }
+        if (mlo <= ms && mlo * stride >= lo && rc.at(mlo * stride, sQ[mlo], QJ) >= target) {
+          hi = mlo * stride;
+          if ((mlo - 1) * stride + 1 > lo) lo = (mlo - 1) * stride + 1;
+        } else if (ms * stride + 1 > lo) {
+          lo = ms * stride + 1;
+        }
+        while (lo < hi) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          if (rc.at(mid, g.Q[mid], QJ) >= target)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        b = lo;
       }
-      return a;
-    };
-    const int64_t a = (k == 0) ? rc.start : cut(k);
-    const int64_t b = (k + 1 == nseg) ? g.n : cut(k + 1);
+    }
+    // the end of segment k - 1 of the same row is this segment's start
+    const int64_t prev_b = __shfl_up_sync(0xffffffffu, b, 1);
+    const int64_t prev_i = __shfl_up_sync(0xffffffffu, i, 1);
+    if (live && k > 0) {
+      if (lane > 0 && prev_i == i && s > s0) {
+        a = prev_b;
+      } else {
+        const RowCost rc = make_row_cost(g, i, F);
+        const unsigned long long total = rc(g.Q, n);
+        const unsigned long long target = total / static_cast<unsigned long long>(nseg) * static_cast<unsigned long long>(k);
+        int64_t lo = rc.start + 1, hi = n;
+        while (lo < hi) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          if (rc(g.Q, mid) >= target)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        a = lo;
+      }
+    }
+    if (!live) continue;
     g.seg[s] = make_int4(static_cast<int>(i), static_cast<int>(k), static_cast<int>(a), static_cast<int>(b));
     if (g.model == MH_UECM) {
       // exp(-beta_min) of this segment and the walk's FP32 / double-float forms

@@ -396,7 +396,6 @@ constexpr int kMergeThreads = 256;
 constexpr int kMergeGroup = 8;                             // threads per node in the merge
 constexpr int kMergeStride = 32;                           // tile entries per shared sample
 constexpr int kMergeSamples = kSortTile / kMergeStride;    // samples per tile
-constexpr int kTileThreads = kSortTile / 2;
 
 __device__ __forceinline__ bool key_less(unsigned long long ka, int32_t ia, unsigned long long kb, int32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
@@ -450,19 +449,20 @@ __device__ __forceinline__ int smem_rank(const unsigned long long* sk, const int
   return pos;
 }
 
-__global__ void __launch_bounds__(kTileThreads) tile_sort_kernel(int model, const double* __restrict__ x,
+template <int kTile>
+__global__ void __launch_bounds__(kTile / 2) tile_sort_kernel(int model, const double* __restrict__ x,
                                                                  const double* __restrict__ y, int64_t n,
                                                                  unsigned long long* __restrict__ kout,
                                                                  int32_t* __restrict__ vout, Top2* __restrict__ tsuf,
                                                                  Ctrl* ctrl, unsigned* clear, int64_t clear_words) {
-  __shared__ unsigned long long sk[kSortTile];
-  __shared__ int32_t si[kSortTile];
-  __shared__ Top2 warp_sums[kTileThreads / 32];
+  __shared__ unsigned long long sk[kTile];
+  __shared__ int32_t si[kTile];
+  __shared__ Top2 warp_sums[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + t; w < clear_words;
        w += static_cast<int64_t>(gridDim.x) * blockDim.x)
     clear[w] = 0u;  // single-pass scan states for the bound prep that follows
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   bool bad = false;
   unsigned long long k[2];
   int32_t id[2];
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_sort_kernel(int model, cons
     si[pos[h]] = id[h];
   }
   __syncthreads();
-  for (int len = 64; len < kSortTile; len <<= 1) {
+  for (int len = 64; len < kTile; len <<= 1) {
     int np[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -518,20 +518,21 @@ __global__ void __launch_bounds__(kTileThreads) tile_sort_kernel(int model, cons
     }
   }
   if (model != MH_UECM) return;
-  // suffix top-2 of y in sorted order: thread t holds positions 2047 - 2t and
-  // 2046 - 2t, so an inclusive scan in thread order runs from the tile's end
+  // suffix top-2 of y in sorted order: thread t holds positions kTile - 1 - 2t
+  // and kTile - 2 - 2t, so an inclusive scan in thread order runs from the
+  // tile's end
   double* sy = reinterpret_cast<double*>(sk);
   __syncthreads();
 #pragma unroll
   for (int h = 0; h < 2; ++h) sy[pos[h]] = (base + pos[h] < n) ? y[id[h]] : 0.0;
   __syncthreads();
-  const int p_hi = kSortTile - 1 - 2 * t, p_lo = p_hi - 1;
+  const int p_hi = kTile - 1 - 2 * t, p_lo = p_hi - 1;
   const Top2 one_hi{sy[p_hi], 0.0}, one_lo{sy[p_lo], 0.0};
   Top2Op op;
   Top2 v = op(one_hi, one_lo);
   block_inclusive_scan<Top2, Top2Op>(v, warp_sums);  // suffix from p_lo on
   Top2 prev = shfl_up(v, 1);
-  __shared__ Top2 last_of_warp[kTileThreads / 32];
+  __shared__ Top2 last_of_warp[32];
   if (lane == 31) last_of_warp[warp] = v;
   __syncthreads();
   if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Top2Op::identity();
@@ -543,23 +544,26 @@ __global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, cons
                                                                      const int32_t* __restrict__ ids,
                                                                      const Top2* __restrict__ tsuf, int tiles,
                                                                      Ctrl* ctrl) {
-  __shared__ unsigned long long sk[kMergeMaxTiles * kMergeSamples];
-  __shared__ int32_t si[kMergeMaxTiles * kMergeSamples];
+  // tile q's samples start at q * kSampleStride: the padding puts the eight
+  // tiles a warp searches at once in different banks
+  constexpr int kSampleStride = kMergeSamples + 1;
+  __shared__ unsigned long long sk[kMergeMaxTiles * kSampleStride];
+  __shared__ int32_t si[kMergeMaxTiles * kSampleStride];
   __shared__ int32_t s_top;
   const int64_t n = g.n;
   for (int q = threadIdx.x; q < tiles * kMergeSamples; q += blockDim.x) {
-    const int64_t e = static_cast<int64_t>(q / kMergeSamples) * kSortTile +
-                      static_cast<int64_t>(q % kMergeSamples) * kMergeStride;
-    sk[q] = e < n ? keys[e] : ~0ull;
-    si[q] = e < n ? ids[e] : INT32_MAX;
+    const int tq = q / kMergeSamples, sq = q % kMergeSamples;
+    const int64_t e = static_cast<int64_t>(tq) * kSortTile + static_cast<int64_t>(sq) * kMergeStride;
+    sk[tq * kSampleStride + sq] = e < n ? keys[e] : ~0ull;
+    si[tq * kSampleStride + sq] = e < n ? ids[e] : INT32_MAX;
   }
   __syncthreads();
   if (threadIdx.x == 0) {  // the largest value heads one of the tiles
     int best = 0;
     for (int q = 1; q < tiles; ++q)
-      if (key_less(sk[q * kMergeSamples], si[q * kMergeSamples], sk[best * kMergeSamples], si[best * kMergeSamples]))
+      if (key_less(sk[q * kSampleStride], si[q * kSampleStride], sk[best * kSampleStride], si[best * kSampleStride]))
         best = q;
-    s_top = si[best * kMergeSamples];
+    s_top = si[best * kSampleStride];
   }
   if (blockIdx.x == 0) gather_tables(g);
   __syncthreads();
@@ -579,8 +583,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, cons
     const int64_t tb = static_cast<int64_t>(q) * kSortTile;
     const int len = static_cast<int>((n - tb) < kSortTile ? (n - tb) : kSortTile);
     const int ns = (len + kMergeStride - 1) / kMergeStride;
-    const unsigned long long* qk = sk + q * kMergeSamples;
-    const int32_t* qi = si + q * kMergeSamples;
+    const unsigned long long* qk = sk + q * kSampleStride;
+    const int32_t* qi = si + q * kSampleStride;
     int s = 0;  // samples below (k, id)
 #pragma unroll
     for (int half = kMergeSamples; half >= 1; half >>= 1)
@@ -591,7 +595,10 @@ __global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, cons
 #pragma unroll
       for (int half = kMergeStride / 2; half >= 1; half >>= 1) {
         const int at = c + half - 1;
-        if (at < len && key_less(keys[tb + at], ids[tb + at], k, id)) c += half;
+        if (at < len) {
+          const unsigned long long ka = keys[tb + at];
+          if (ka < k || (ka == k && ids[tb + at] < id)) c += half;  // ids only on a tie
+        }
       }
     }
     below += c;
@@ -610,6 +617,101 @@ __global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, cons
   }
   gather_rank(g, r, id, F);
   if (uecm) g.top[r] = op(tsuf[e], above);  // two largest y among ranks >= r
+}
+
+// Sets of at most kMergeSmemMax nodes: tiles of kSmallTile keys, and every
+// merge block holds all sorted keys in shared memory, so a node's searches
+// in the other tiles (kMergeGroup threads per node, a binary search per
+// tile; ids are read only on equal keys) never leave the SM.  The node's
+// rank-order copies are then written by one thread per node.
+constexpr int kSmallTile = 512;
+constexpr int kMergeSmemMax = 24576;               // 8-byte keys in shared memory
+constexpr int kSmemThreads = 1024;
+constexpr int kSmemNodes = kSmemThreads / kMergeGroup;  // nodes per block
+
+// Tile q's keys start at q * kSmemTileStride in shared memory: the padding
+// puts the eight tiles a warp searches at once in different banks.
+constexpr int kSmemTileStride = kSmallTile + 2;
+
+__host__ __device__ inline size_t merge_smem_bytes(int64_t n) {
+  return 8 * static_cast<size_t>((n + kSmallTile - 1) / kSmallTile) * kSmemTileStride;
+}
+
+__global__ void __launch_bounds__(kSmemThreads) merge_smem_kernel(Net g, const unsigned long long* __restrict__ keys,
+                                                                  const int32_t* __restrict__ ids,
+                                                                  const Top2* __restrict__ tsuf, int tiles,
+                                                                  Ctrl* ctrl) {
+  extern __shared__ unsigned long long smk[];
+  __shared__ long long s_rank[kSmemNodes];
+  __shared__ Top2 s_above[kSmemNodes];
+  __shared__ int32_t s_top;
+  const int64_t n = g.n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    smk[(i / kSmallTile) * kSmemTileStride + i % kSmallTile] = keys[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the largest value heads one of the tiles
+    int best = 0;
+    for (int q = 1; q < tiles; ++q) {
+      const unsigned long long kq = smk[q * kSmemTileStride], kb = smk[best * kSmemTileStride];
+      if (kq < kb || (kq == kb && ids[q * kSmallTile] < ids[best * kSmallTile])) best = q;
+    }
+    s_top = ids[best * kSmallTile];
+  }
+  if (blockIdx.x == 0) gather_tables(g);
+  __syncthreads();
+  const bool uecm = g.model == MH_UECM;
+  const int F = top_scale(g, s_top);
+  const int local = threadIdx.x / kMergeGroup, gl = threadIdx.x % kMergeGroup;
+  Top2Op op;
+  // batches of kSmemNodes nodes, one block per SM holding the keys once
+  for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * kSmemNodes; e0 < n;
+       e0 += static_cast<int64_t>(gridDim.x) * kSmemNodes) {
+    const int64_t e = e0 + local;
+    const bool live = e < n;
+    const int own = static_cast<int>(e / kSmallTile);
+    const unsigned long long k = live ? smk[own * kSmemTileStride + e % kSmallTile] : 0ull;
+    const int32_t id = live ? ids[e] : 0;
+    long long below = 0;
+    Top2 above{0.0, 0.0};
+    for (int q = gl; live && q < tiles; q += kMergeGroup) {
+      if (q == own) continue;
+      const int tb = q * kSmallTile;
+      const unsigned long long* tk = smk + q * kSmemTileStride;
+      const int len = static_cast<int>((n - tb) < kSmallTile ? (n - tb) : kSmallTile);
+      int c = 0;  // entries of tile q below (k, id)
+#pragma unroll
+      for (int step = kSmallTile; step >= 1; step >>= 1) {
+        const int at = c + step - 1;
+        if (at < len) {
+          const unsigned long long ka = tk[at];
+          if (ka < k || (ka == k && ids[tb + at] < id)) c += step;  // ids only on a tie
+        }
+      }
+      below += c;
+      if (uecm && c < len) above = op(above, tsuf[tb + c]);
+    }
+#pragma unroll
+    for (int d = kMergeGroup / 2; d; d >>= 1) {
+      below += __shfl_xor_sync(0xffffffffu, below, d);
+      above = op(above, Top2{__shfl_xor_sync(0xffffffffu, above.a, d), __shfl_xor_sync(0xffffffffu, above.b, d)});
+    }
+    if (live && gl == 0) {
+      s_rank[local] = e - static_cast<int64_t>(own) * kSmallTile + below;
+      s_above[local] = above;
+    }
+    __syncthreads();
+    const int64_t e2 = e0 + threadIdx.x;
+    if (threadIdx.x < kSmemNodes && e2 < n) {
+      const long long r = s_rank[threadIdx.x];
+      if (r >= n) {
+        atomicOr(&ctrl->status, kStInternal);
+      } else {
+        gather_rank(g, r, ids[e2], F);
+        if (uecm) g.top[r] = op(tsuf[e2], s_above[threadIdx.x]);  // two largest y among ranks >= r
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -668,15 +770,38 @@ cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cud
   return cudaSuccess;  // eight passes: the result is back in keys0 / vals0
 }
 
+cudaError_t sort_kernel_attributes(int dev) {
+  static bool done[64] = {};
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (done[dev]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(merge_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(merge_smem_bytes(kMergeSmemMax)));
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
-  const int tiles = static_cast<int>((g.n + kSortTile - 1) / kSortTile);
   auto* k1 = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   auto* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
-  // the scan counters and flags are adjacent at the end of the zeroed region
   auto* clear = reinterpret_cast<unsigned*>(ws + L.scan_counters);
   const int64_t clear_words = static_cast<int64_t>((L.zero_end - L.scan_counters) / 4);
   auto* tsuf = reinterpret_cast<Top2*>(ws + L.tsuf);
-  tile_sort_kernel<<<tiles, kTileThreads, 0, s>>>(g.model, g.x, g.y, g.n, k1, v1, tsuf, ctrl, clear, clear_words);
+  if (g.n <= kMergeSmemMax) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = sort_kernel_attributes(dev);
+    if (e != cudaSuccess) return e;
+    const int tiles = static_cast<int>((g.n + kSmallTile - 1) / kSmallTile);
+    tile_sort_kernel<kSmallTile><<<tiles, kSmallTile / 2, 0, s>>>(g.model, g.x, g.y, g.n, k1, v1, tsuf, ctrl,
+                                                                   clear, clear_words);
+    merge_smem_kernel<<<grid_for(g.n, kSmemNodes, static_cast<unsigned>(sm_count())), kSmemThreads,
+                        merge_smem_bytes(g.n), s>>>(g, k1, v1, tsuf, tiles, ctrl);
+    note_launches(2);
+    return cudaGetLastError();
+  }
+  const int tiles = static_cast<int>((g.n + kSortTile - 1) / kSortTile);
+  tile_sort_kernel<kSortTile><<<tiles, kSortTile / 2, 0, s>>>(g.model, g.x, g.y, g.n, k1, v1, tsuf, ctrl, clear,
+                                                               clear_words);
   merge_gather_kernel<<<grid_for(g.n, kMergeThreads / kMergeGroup), kMergeThreads, 0, s>>>(g, k1, v1, tsuf, tiles,
                                                                                             ctrl);
   note_launches(2);

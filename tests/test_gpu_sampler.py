@@ -74,6 +74,22 @@ def test_segment_table_matches_oracle(model, T, flags):
         assert np.array_equal(got[key], ref[key]), key
 
 
+@pytest.mark.parametrize("n", [511, 512, 513, 24_576, 24_577, 40_000, 65_536, 65_537])
+@pytest.mark.parametrize("model", [UBCM, UECM])
+def test_sort_paths_match_oracle(model, n):
+    # node sets sorted with 512-key tiles and a shared-memory merge (up to
+    # 24,576 nodes), 2048-key tiles and a sampled merge (up to 65,536), or the
+    # radix passes; ties across tile boundaries and zero values in each
+    x, y = heavy_tailed(n, seed=n, uecm=model == UECM)
+    x *= min(1.0, 2000.0 / n)  # a mean degree of a few at every size
+    x[n // 3: n // 3 + 700] = x[1]
+    x[-50:] = 0.0
+    ref = oracle.partition(model, x, y, seg_target=16)
+    got = segment_table(model, dev(x), None if y is None else dev(y), seg_target=16)
+    for key in ("perm", "row", "k", "a", "b"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
 # --------------------------------------------------------------------------
 # Full-size workloads
 # --------------------------------------------------------------------------
