@@ -594,7 +594,9 @@ def run_ours(args, rank, world, local_rank):
     # segment length and walk block shape from the autotuner (probe: the same
     # 10-sample call, device time); every rank tunes the same workload alike
     T, ctas, tuned = 0, 0, None
-    if not args.no_tune:
+    if args.seg_target:
+        T = args.seg_target
+    elif not args.no_tune:
         from paper_2509_13230_gb300.autotune import tune_sampler
         tuned = tune_sampler(nat.MH_UECM, x, y, candidates_t=(8, 16, 32), candidates_ctas=(0,),
                              num_samples=SAMPLES_PER_STEP, reps=5)
@@ -759,6 +761,8 @@ def main():
     ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
+    ap.add_argument("--seg-target", type=int, default=0,
+                    help="headline call: use this seg_target instead of tuning (profiling runs)")
     ap.add_argument("--ensemble-seg-target", type=int, default=0,
                     help="ensemble leg: use this seg_target instead of tuning (profiling runs)")
     ap.add_argument("--ensemble-networks", type=int, default=128,

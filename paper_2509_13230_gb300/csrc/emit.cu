@@ -67,16 +67,31 @@ struct EmitParams {
   int mode;
 };
 
-// Each block owns kEmitItems consecutive work items and writes their output
-// range with consecutive threads on consecutive edges.
+// What every edge of a work item shares, set up once per item by one thread.
+struct ItemRec {
+  long long base;    // staging position of the item's first rank
+  long long at;      // CSR: index position of the item's first edge (one-row or symmetric forward)
+  int cnt;           // edges of the item
+  int i;             // row rank
+  int u;             // original id of row i's node
+  int k;             // segment index within the row
+  int s_local;       // sample within the chunk
+  int ex;            // directed: the excluded candidate rank, else -1
+  float2 lnyi;
+  double yi;
+};
+
+// Blocks take kEmitItems consecutive work items at a time (a grid-stride
+// loop over the chunk's items): one thread per item sets up its ItemRec,
+// then consecutive threads write consecutive edges of the items.
 __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   const Net& g = P.g;
   Ctrl* ctrl = P.ctrl;
   __shared__ LnEntry tab[kLnTable];
-  if (g.model == MH_UECM) {
-    ln_table_to_shared(tab, g.lntab);
-    __syncthreads();
-  }
+  __shared__ long long off[kEmitItems + 1];
+  __shared__ ItemRec info[kEmitItems];
+  const bool uecm = g.model == MH_UECM;
+  if (uecm && P.mode != kEmitSymForward) ln_table_to_shared(tab, g.lntab);
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
   unsigned long long fallbacks = 0;
   long long S = ctrl->num_segments;
@@ -84,6 +99,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   const long long items = S * P.c.chunk_samples;
   const bool unwritten = ctrl->num_segments > g.max_segments ||  // truncated table: the call fails
                          ctrl->stage_used > static_cast<unsigned long long>(P.c.staging_cap);
+  const long long chunk_first_edge = P.c.item_off[0];
   if (blockIdx.x == 0 && P.mode != kEmitSymForward) {
     // per-sample edge counts of this chunk; the next chunk continues after it
     for (int64_t s = threadIdx.x; s < P.c.chunk_samples; s += blockDim.x)
@@ -93,100 +109,123 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
       if (P.mode == kEmitSymPairs) {
         // the chunk's edges that have a place in the output (none when the
         // walk's output was not kept), and where its CSR entries start
-        const long long first = P.c.item_off[0];
-        long long len = P.c.item_off[items] - first;
-        const long long room = P.o.capacity - first;
+        long long len = P.c.item_off[items] - chunk_first_edge;
+        const long long room = P.o.capacity - chunk_first_edge;
         if (len > room) len = room;
         ctrl->sym_len = (unwritten || len < 0) ? 0 : len;
-        ctrl->sym_base = 2 * first;
+        ctrl->sym_base = 2 * chunk_first_edge;
       }
     }
   }
-  const long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems;
-  if (it0 >= items) return;
   // Staging that did not fit was never written: emit nothing (the call
   // reports MH_ERR_CAPACITY with exact counts).
   if (unwritten) return;
-  const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
-  __shared__ long long off[kEmitItems + 1];
-  for (long long t = threadIdx.x; t <= it1 - it0; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
-  __syncthreads();
-  const long long o0 = off[0], o1 = off[it1 - it0];
+  __syncthreads();  // the logarithm table
   const long long n1 = g.rows + 1;
-  bool overflow = false;
-  for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
-    int lo = 0, hi = static_cast<int>(it1 - it0) - 1;  // last local item with off <= pos
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (off[mid] <= pos)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const long long item = it0 + lo;
-    const long long e = pos - off[lo];
-    if (e >= P.c.item_cnt[item]) {  // offsets inconsistent with the counts: never read past a run
-      atomicOr(&ctrl->status, kStInternal);
-      continue;
-    }
-    const long long s_local = static_cast<unsigned>(item) / static_cast<unsigned>(S);  // items < 2^31
-    const long long seg = item - s_local * S;
-    const int4 sg = g.seg[seg];
-    const int32_t i = sg.x;
-    const int32_t j = P.c.staging[P.c.item_base[item] + e];
-    if (j < row_start(g, i) || j >= g.n || (g.excl && j == g.excl[i])) {
-      // cannot happen for a walked segment; never index with it
-      atomicOr(&ctrl->status, kStInternal);
-      continue;
-    }
-    const int32_t u = g.perm_r[i], v = g.perm[j];
-    if (P.mode == kEmitSymForward) {
-      // after the row's arriving edges, then the row's own in (segment, candidate) order
-      if (pos >= P.o.capacity) continue;
-      const long long q = pos - P.c.item_off[0];  // position within the chunk
-      const long long s_all = P.c.chunk_first + s_local;
-      const long long row_first = s_local * S + g.rowoff[i];
-      const long long* rv = P.c.sym.rev + s_local * n1;
-      const long long at = P.o.csr_off[s_all * n1 + u] + (rv[i + 1] - rv[i]) +
-                           (P.c.item_off[item] - P.c.item_off[row_first]) + e;
-      if (at >= 0 && at < 2 * P.o.capacity) {
-        P.o.csr_idx[at] = v;
-        if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
-      }
-      continue;
-    }
-    int32_t wt = 1;
-    if (g.model == MH_UECM) {
-      const float2 li = g.lny_r[i], lj = g.lny[j];
-      wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(sg.y), static_cast<uint32_t>(i),
-                       P.c.sample0 + static_cast<uint32_t>(s_local), P.c.key0, P.c.key1, g.ys_r[i], g.ys[j],
-                       df2{li.x, li.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
-    }
-    if (pos < P.o.capacity) {
-      if (P.o.src) {
-        P.o.src[pos] = u;
-        P.o.dst[pos] = v;
-        if (P.o.w) P.o.w[pos] = wt;
-      }
-      if (P.mode == kEmitSymPairs) {
-        const long long q = pos - P.c.item_off[0];  // position within the chunk
-        P.c.sym.keys[0][q] = (static_cast<unsigned long long>(s_local) << 32) | static_cast<uint32_t>(j);
-        P.c.sym.vals[0][q] = static_cast<int32_t>(q);
-        P.c.sym.src[q] = u;
-        P.c.sym.w[q] = wt;
-        atomicAdd(reinterpret_cast<unsigned long long*>(&P.c.sym.rev[s_local * n1 + j]), 1ull);
-      } else if (P.o.csr_idx) {
+  const bool one_row_csr = P.mode == kEmitPlain && P.o.csr_idx != nullptr;
+  bool overflow = false, bad = false;
+  for (long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems; it0 < items;
+       it0 += static_cast<long long>(gridDim.x) * kEmitItems) {
+    const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
+    const int nit = static_cast<int>(it1 - it0);
+    for (int t = threadIdx.x; t <= nit; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
+    if (threadIdx.x < nit) {
+      const long long item = it0 + threadIdx.x;
+      const int s_local = static_cast<int>(static_cast<unsigned>(item) / static_cast<unsigned>(S));  // items < 2^31
+      const long long seg = item - static_cast<long long>(s_local) * S;
+      const int4 sg = g.seg[seg];
+      ItemRec r;
+      r.base = P.c.item_base[item];
+      r.cnt = static_cast<int>(P.c.item_cnt[item]);
+      r.i = sg.x;
+      r.u = g.perm_r[sg.x];
+      r.k = sg.y;
+      r.s_local = s_local;
+      r.ex = g.excl ? g.excl[sg.x] : -1;
+      r.at = 0;
+      if (one_row_csr || P.mode == kEmitSymForward) {
         const long long s_all = P.c.chunk_first + s_local;
-        const long long row_first = s_local * S + g.rowoff[i];
-        const long long at = P.o.csr_off[s_all * n1 + u] + (P.c.item_off[item] - P.c.item_off[row_first]) + e;
-        if (at < P.o.capacity) {
+        const long long row_first = static_cast<long long>(s_local) * S + g.rowoff[sg.x];
+        r.at = P.o.csr_off[s_all * n1 + r.u] + (P.c.item_off[item] - P.c.item_off[row_first]);
+        if (P.mode == kEmitSymForward) {  // after the row's arriving edges
+          const long long* rv = P.c.sym.rev + static_cast<long long>(s_local) * n1;
+          r.at += rv[sg.x + 1] - rv[sg.x];
+        }
+      }
+      r.yi = 0.0;
+      r.lnyi = make_float2(0.f, 0.f);
+      if (uecm) {
+        r.yi = g.ys_r[sg.x];
+        r.lnyi = g.lny_r[sg.x];
+      }
+      info[threadIdx.x] = r;
+    }
+    __syncthreads();
+    const long long o0 = off[0], o1 = off[nit];
+    for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
+      int lo = 0, hi = nit - 1;  // last local item with off <= pos
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= pos)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const ItemRec& r = info[lo];
+      const int e = static_cast<int>(pos - off[lo]);
+      if (e >= r.cnt) {  // offsets inconsistent with the counts: never read past a run
+        bad = true;
+        continue;
+      }
+      const int32_t j = P.c.staging[r.base + e];
+      if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
+        bad = true;
+        continue;
+      }
+      const int32_t v = g.perm[j];
+      const long long q = pos - chunk_first_edge;  // position within the chunk
+      if (P.mode == kEmitSymForward) {
+        if (pos >= P.o.capacity) continue;
+        const long long at = r.at + e;
+        if (at >= 0 && at < 2 * P.o.capacity) {
           P.o.csr_idx[at] = v;
-          if (P.o.csr_w) P.o.csr_w[at] = wt;
+          if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
+        }
+        continue;
+      }
+      int32_t wt = 1;
+      if (uecm) {
+        const float2 lj = g.lny[j];
+        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
+                         P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, g.ys[j],
+                         df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
+      }
+      if (pos < P.o.capacity) {
+        if (P.o.src) {
+          P.o.src[pos] = r.u;
+          P.o.dst[pos] = v;
+          if (P.o.w) P.o.w[pos] = wt;
+        }
+        if (P.mode == kEmitSymPairs) {
+          P.c.sym.keys[0][q] = (static_cast<unsigned long long>(r.s_local) << 32) | static_cast<uint32_t>(j);
+          P.c.sym.vals[0][q] = static_cast<int32_t>(q);
+          P.c.sym.src[q] = r.u;
+          P.c.sym.w[q] = wt;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&P.c.sym.rev[static_cast<long long>(r.s_local) * n1 + j]),
+                    1ull);
+        } else if (one_row_csr) {
+          const long long at = r.at + e;
+          if (at < P.o.capacity) {
+            P.o.csr_idx[at] = v;
+            if (P.o.csr_w) P.o.csr_w[at] = wt;
+          }
         }
       }
     }
+    __syncthreads();
   }
   if (overflow) atomicOr(&ctrl->status, kStOverflow);
+  if (bad) atomicOr(&ctrl->status, kStInternal);
   (void)fallbacks;
 }
 
@@ -230,7 +269,7 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
                                                   &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;
   const int64_t len = c.chunk_samples * (g.rows + 1);
-  const unsigned emit_blocks = grid_for(c.items_max, kEmitItems);
+  const unsigned emit_blocks = grid_for(c.items_max, kEmitItems, static_cast<unsigned>(sm_count()) * 6u);
   long long* region = o.csr_off ? o.csr_off + c.chunk_first * (g.rows + 1) : nullptr;
   if (c.sym.rev && o.csr_off) {
     // symmetric layout: keys and arriving counts, the key sort, offsets from

@@ -144,8 +144,8 @@ def directed_uecm_n20k(n: int = 20_000, seed: int = 6):
 
 def bipartite_ubcm_pareto(n_plus: int = 200_000, n_minus: int = 20_000, seed: int = 7):
     """Bipartite unweighted network (Sec. 2.6), e.g. users x items: capped
-    Pareto fitness on both sides, scales chosen so that a + node has about 10
-    expected edges.  Returns (x_plus, x_minus)."""
+    Pareto fitness on both sides, scaled so that a + node has about 16
+    edges (3.3 M per sample).  Returns (x_plus, x_minus)."""
     rng = np.random.default_rng(seed)
     up = np.where((u := rng.uniform(0.0, 1.0, n_plus)) > 0.0, u, np.finfo(np.float64).tiny)
     um = np.where((u := rng.uniform(0.0, 1.0, n_minus)) > 0.0, u, np.finfo(np.float64).tiny)
