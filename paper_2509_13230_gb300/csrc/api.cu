@@ -153,6 +153,7 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.vals0 = take(4 * nm);
   L.vals1 = take(4 * nm);
   L.tsuf = take(sizeof(Top2) * nm);
+  L.tsuf2 = take(sizeof(Top2) * nm);
   L.hist = take(4 * 256 * static_cast<size_t>(L.tiles));
   L.perm = take(4 * static_cast<size_t>(n));
   L.rank = take(4 * static_cast<size_t>(n));
@@ -176,7 +177,6 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.adf = take(8 * static_cast<size_t>(n));
   L.ydf = take(8 * static_cast<size_t>(n));
   L.lny = take(8 * static_cast<size_t>(n));
-  L.lntab = take(16 * 512);
   L.seg_c = take(8 * static_cast<size_t>(L.max_segments));
   L.seg_cf = take(16 * static_cast<size_t>(L.max_segments));
   if (bip) {
@@ -251,7 +251,7 @@ static Net make_net(int model, const mh_params& p, const double* x, const double
   g.adf = (model == MH_UECM) ? reinterpret_cast<float2*>(ws + L.adf) : g.xdf;
   g.ydf = reinterpret_cast<float2*>(ws + L.ydf);
   g.lny = reinterpret_cast<float2*>(ws + L.lny);
-  g.lntab = reinterpret_cast<LnEntry*>(ws + L.lntab);
+  g.lntab = ln_table_ptr();
   g.max_segments = L.max_segments;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
   g.rows = L.rows;
@@ -605,6 +605,10 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   }
   char* ws = static_cast<char*>(workspace);
   Net g = make_net(model, *p, x, y, n, L, ws);
+  if (!g.lntab) {
+    set_error("the logarithm table could not be built on this device");
+    return MH_ERR_CUDA;
+  }
   if (bip) {
     g.x_r = xr;
     g.y_r = yr;
@@ -817,6 +821,10 @@ int mh_segment_table(int model, const double* x, const double* y, int64_t n, con
   char* ws = static_cast<char*>(workspace);
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
   const Net g = make_net(model, *params, x, y, n, L, ws);
+  if (!g.lntab) {
+    set_error("the logarithm table could not be built on this device");
+    return MH_ERR_CUDA;
+  }
   rc = prepare(g, L, ws, ctrl, s);
   if (rc != MH_OK) return rc;
   if (cap > 0) MH_CUDA(launch_export_table(g, ctrl, seg_row, seg_k, seg_a, seg_b, cap, s));

@@ -67,7 +67,7 @@ struct BatchLayout {
   // persistent part (the first `image` bytes are copied from the host)
   size_t header = 0, nets = 0, order = 0, image = 0, net_ctrl = 0, wave = 0, mb = 0, wave_ctrl = 0;
   size_t perm = 0, rank = 0, xs = 0, ys = 0, as = 0, xdf = 0, adf = 0, ydf = 0, lny = 0, top = 0, Q = 0,
-         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, lntab = 0, persistent_end = 0;
+         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, persistent_end = 0;
   // preparation scratch of one lane, relative to the lane's start
   Layout lane;
   size_t lane_bytes = 0, prep_end = 0;
@@ -127,7 +127,6 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
   B.seg = take(sizeof(int4) * SG);
   B.seg_c = take(8 * SG);
   B.seg_cf = take(16 * SG);
-  B.lntab = take(16 * 512);
   B.persistent_end = off;
 
   // one lane's sort and scan scratch, sized for the largest network
@@ -149,6 +148,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
     L.vals0 = ltake(4 * nm);
     L.vals1 = ltake(4 * nm);
     L.tsuf = ltake(sizeof(Top2) * nm);
+    L.tsuf2 = ltake(sizeof(Top2) * nm);
     L.hist = ltake(4 * 256 * tiles);
     L.zero_begin = lo;
     L.ghist = ltake(4 * 8 * 256);
@@ -222,6 +222,7 @@ Layout net_layout(const BatchLayout& B, const BatchNet& bn, int lane) {
   L.vals0 += lane_at;
   L.vals1 += lane_at;
   L.tsuf += lane_at;
+  L.tsuf2 += lane_at;
   L.hist += lane_at;
   L.zero_begin += lane_at;
   L.ghist += lane_at;
@@ -251,7 +252,6 @@ Layout net_layout(const BatchLayout& B, const BatchNet& bn, int lane) {
   L.seg = B.seg + sizeof(int4) * sb;
   L.seg_c = B.seg_c + 8 * sb;
   L.seg_cf = B.seg_cf + 16 * sb;
-  L.lntab = B.lntab;
   return L;
 }
 
@@ -298,7 +298,7 @@ Net make_batch_net(int model, const mh_params& p, const double* x, const double*
   g.adf = (model == MH_UECM) ? reinterpret_cast<float2*>(ws + L.adf) : g.xdf;
   g.ydf = reinterpret_cast<float2*>(ws + L.ydf);
   g.lny = reinterpret_cast<float2*>(ws + L.lny);
-  g.lntab = reinterpret_cast<LnEntry*>(ws + L.lntab);
+  g.lntab = ln_table_ptr();
   g.max_segments = L.max_segments;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
   return one_set_rows(g);
@@ -924,7 +924,7 @@ Net concatenated_net(const BatchLayout& B, const mh_params& p, char* ws) {
   g.adf = reinterpret_cast<float2*>(ws + B.adf);
   g.ydf = reinterpret_cast<float2*>(ws + B.ydf);
   g.lny = reinterpret_cast<float2*>(ws + B.lny);
-  g.lntab = reinterpret_cast<LnEntry*>(ws + B.lntab);
+  g.lntab = ln_table_ptr();
   g.max_segments = B.segs;
   g.seg_target = p.seg_target ? static_cast<int>(p.seg_target) : kDefaultSegTarget;
   return one_set_rows(g);
@@ -1009,6 +1009,10 @@ int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_par
       const int l = t % B.lanes;
       const Layout L = net_layout(B, bnets[t], l);
       const Net g = make_batch_net(h_nets[t].model, *params, h_nets[t].x, h_nets[t].y, h_nets[t].n, L, ws);
+      if (!g.lntab) {
+        set_error("the logarithm table could not be built on this device");
+        return MH_ERR_CUDA;
+      }
       Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + B.net_ctrl) + t;
       const int r = prepare_network(g, L, ws, ctrl, ds->lane[l]);
       if (r != MH_OK) return r;
@@ -1178,6 +1182,10 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
   V.csr_max = B.csr_max;
 
   const Net gall = concatenated_net(B, *params, ws);
+  if (!gall.lntab) {
+    set_error("the logarithm table could not be built on this device");
+    return MH_ERR_CUDA;
+  }
   Outputs out{src, dst, w, reinterpret_cast<long long*>(csr_offsets), csr_indices, csr_weights, capacity_edges};
   if (!(fl & MH_OUT_COO)) out.src = out.dst = out.w = nullptr;
   if (!(fl & MH_OUT_CSR)) out.csr_off = nullptr, out.csr_idx = nullptr, out.csr_w = nullptr;

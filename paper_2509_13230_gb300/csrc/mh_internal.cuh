@@ -78,8 +78,8 @@ struct Layout {
   size_t ctrl = 0, keys0 = 0, keys1 = 0, vals0 = 0, vals1 = 0, hist = 0, perm = 0, rank = 0, xs = 0, ys = 0,
          as = 0, top1 = 0, Q = 0, rowoff = 0, seg = 0, item_cnt = 0, item_base = 0,
          item_off = 0, sample_counts = 0, staging = 0, xdf = 0, adf = 0, ydf = 0, lny = 0,
-         lntab = 0, seg_c = 0, seg_cf = 0, ghist = 0, sort_state = 0, sort_counters = 0, scan_flags = 0,
-         scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, tsuf = 0, total = 0;
+         seg_c = 0, seg_cf = 0, ghist = 0, sort_state = 0, sort_counters = 0, scan_flags = 0,
+         scan_values = 0, scan_counters = 0, zero_begin = 0, zero_end = 0, tsuf = 0, tsuf2 = 0, total = 0;
   // symmetric CSR scratch (MH_CSR_SYMMETRIC): (sample, rank) keys and
   // positions of the chunk's edges, their sources and weights in output
   // order, per-(sample, rank) counts of edges arriving at a node, and the
@@ -121,7 +121,7 @@ struct Net {
   float2* adf;            // a_s = x_s y_s as double-float (UECM)
   float2* ydf;            // y_s as double-float (UECM)
   float2* lny;            // ln y_s as double-float (UECM weights)
-  LnEntry* lntab;         // logarithm table (kLnTable entries)
+  LnEntry* lntab;         // logarithm table (kLnTable entries, one per device)
   int64_t max_segments;
   int seg_target;
   // Rows.  One node set: the same nodes and arrays as the candidates, row i
@@ -206,6 +206,10 @@ cudaError_t launch_gather(const Net& g, const int32_t* sorted_vals, Ctrl* ctrl, 
 // rank and gather (two launches); also clears the single-pass scan states.
 cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
 cudaError_t sort_kernel_attributes(int dev);  // before any capture
+// Device copy of the logarithm table of the current device, built on first
+// use (a launch and a synchronisation: never while a stream is captured);
+// NULL if it could not be built.
+LnEntry* ln_table_ptr();
 // Stable LSD sort of `len` (key, value) pairs on the 8-bit digits at the
 // given shifts, `*dev_len` of them (at most host_len) present; the result
 // is in buffer 0 or 1 as returned through *out_buf.  `st` is the scan state.

@@ -95,6 +95,10 @@ extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_param
   }
   char* ws = static_cast<char*>(g_noalloc_ptr[dev]);
   const Net g = net_view(MH_UBCM, *params, x, nullptr, n, L, ws);
+  if (!g.lntab) {
+    set_error("the logarithm table could not be built on this device");
+    return MH_ERR_CUDA;
+  }
   const Outputs o{src, dst, nullptr, reinterpret_cast<long long*>(csr_offsets), csr_indices, nullptr,
                   capacity_edges};
   rc = enqueue_sample_direct(g, L, ws, params, o, g_noalloc_host, s);

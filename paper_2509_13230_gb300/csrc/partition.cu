@@ -91,20 +91,22 @@ __device__ __forceinline__ RowCost make_row_cost(const Net& g, int64_t i, int F)
   return rc;
 }
 
+// Segments of row i: max(1, floor(C(n) / 2^F) / T), 0 for a row without candidates.
+__device__ __forceinline__ long long row_segments(const Net& g, int64_t i, int F) {
+  if (row_start(g, i) >= g.n) return 0;
+  const RowCost rc = make_row_cost(g, i, F);
+  const unsigned long long total = rc(g.Q, g.n);
+  const unsigned long long ns = (total >> F) / static_cast<unsigned long long>(g.seg_target);
+  return ns < 1 ? 1 : static_cast<long long>(ns);
+}
+
 __global__ void __launch_bounds__(256) row_count_kernel(Net g) {
   const int F = proxy_F(g);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < g.rows;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    long long nseg = 0;
-    if (row_start(g, i) < g.n) {
-      const RowCost rc = make_row_cost(g, i, F);
-      const unsigned long long total = rc(g.Q, g.n);
-      unsigned long long ns = (total >> F) / static_cast<unsigned long long>(g.seg_target);
-      nseg = ns < 1 ? 1 : static_cast<long long>(ns);
-    }
-    g.rowoff[i] = nseg;
-  }
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    g.rowoff[i] = row_segments(g, i, F);
 }
+
 
 // Last row whose first table row is <= s, within [lo, hi].
 __device__ __forceinline__ int64_t row_of(const Net& g, long long s, int64_t lo, int64_t hi) {
@@ -118,12 +120,61 @@ __device__ __forceinline__ int64_t row_of(const Net& g, long long s, int64_t lo,
   return lo;
 }
 
+// Last row r in [lo, hi] with rowoff[r] <= s (rowoff[lo] <= s), by a whole
+// warp: 32 evenly spaced probes per round narrow the range 32-fold, so three
+// rounds of loads cover 20,000 rows.  Every lane returns the answer.
+__device__ __forceinline__ int64_t row_of_warp(const Net& g, long long s, int64_t lo, int64_t hi) {
+  const int lane = threadIdx.x & 31;
+  while (hi > lo) {
+    const int64_t step = (hi - lo) / 32 + 1;
+    const int64_t p = lo + lane * step;
+    const bool ok = p <= hi && g.rowoff[p] <= s;  // true for a prefix of the lanes (lane 0 always)
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    const int last = 31 - __clz(mask);
+    lo += last * step;
+    const int64_t top = lo + step - 1;
+    if (top < hi) hi = top;
+  }
+  return lo;
+}
+
+// First b in [lo, n] with cost(b) >= target, where cost(n) >= target: a
+// bisection over every stride-th entry of Q (sQ, in shared memory) and then
+// over the stride between two of them in global memory.
+__device__ __forceinline__ int64_t cut_search(const Net& g, const RowCost& rc, unsigned long long QJ,
+                                              unsigned long long target, int64_t lo,
+                                              const unsigned long long* sQ, int64_t stride, int64_t ms) {
+  const int64_t n = g.n;
+  int64_t hi = n;
+  int64_t mlo = (lo + stride - 1) / stride, mhi = ms;  // sample indices inside [lo, n]
+  while (mlo < mhi) {
+    const int64_t mid = mlo + (mhi - mlo) / 2;
+    if (rc.at(mid * stride, sQ[mid], QJ) >= target)
+      mhi = mid;
+    else
+      mlo = mid + 1;
+  }
+  if (mlo <= ms && mlo * stride >= lo && rc.at(mlo * stride, sQ[mlo], QJ) >= target) {
+    hi = mlo * stride;
+    if ((mlo - 1) * stride + 1 > lo) lo = (mlo - 1) * stride + 1;
+  } else if (ms * stride + 1 > lo) {
+    lo = ms * stride + 1;
+  }
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (rc.at(mid, g.Q[mid], QJ) >= target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
 // One thread per table row: finds its row (a block's table rows belong to a
-// few consecutive rows, found first by two bisections), then, for rows of
-// more than one segment, its cut points by bisection of the cumulative cost:
-// first over every stride-th entry of Q, kept in shared memory, then over
-// the stride between two of them.  A segment's start is the previous
-// segment's end, taken from the neighbouring lane when it walks the same row.
+// few consecutive rows, whose range two warps find first), then, for rows of
+// more than one segment, its cut points by cut_search.  A segment's start is
+// the previous segment's end, taken from the neighbouring lane when it walks
+// the same row.
 constexpr int kFillSamples = 2048;
 
 __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
@@ -136,76 +187,60 @@ __global__ void __launch_bounds__(256) seg_fill_kernel(Net g, Ctrl* ctrl) {
   const int64_t n = g.n;
   const int64_t stride = n / kFillSamples + 1;  // samples m * stride <= n for m <= ms
   const int64_t ms = n / stride;
-  for (int64_t m = threadIdx.x; m <= ms; m += blockDim.x) sQ[m] = g.Q[m * stride];
+  {
+    constexpr int kUnroll = kFillSamples / 256 + 1;  // every sample load in flight at once
+    unsigned long long v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t m = threadIdx.x + static_cast<int64_t>(u) * blockDim.x;
+      if (m <= ms) v[u] = g.Q[m * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t m = threadIdx.x + static_cast<int64_t>(u) * blockDim.x;
+      if (m <= ms) sQ[m] = v[u];
+    }
+  }
   const int lane = threadIdx.x & 31;
   for (long long s0 = blockIdx.x * static_cast<long long>(blockDim.x); s0 < lim;
        s0 += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long s1 = (s0 + blockDim.x < lim ? s0 + blockDim.x : lim) - 1;
     __syncthreads();
-    if (threadIdx.x == 0) s_lo = row_of(g, s0, 0, g.rows - 1);
-    if (threadIdx.x == 32) s_hi = row_of(g, s1, 0, g.rows - 1);
+    if (threadIdx.x < 32) {
+      const int64_t r = row_of_warp(g, s0, 0, g.rows - 1);
+      if (lane == 0) s_lo = r;
+    } else if (threadIdx.x < 64) {
+      const int64_t r = row_of_warp(g, s1, 0, g.rows - 1);
+      if (lane == 0) s_hi = r;
+    }
     __syncthreads();
     const long long s = s0 + threadIdx.x;
     const bool live = s <= s1;
     int64_t i = 0, a = 0, b = n;
     long long k = 0, nseg = 1;
+    RowCost rc{};
+    unsigned long long QJ = 0, Tc = 0;
     if (live) {
       i = row_of(g, s, s_lo, s_hi);
       k = s - g.rowoff[i];
       nseg = g.rowoff[i + 1] - g.rowoff[i];
       a = row_start(g, i);
-      if (k + 1 < nseg) {
-        const RowCost rc = make_row_cost(g, i, F);
-        const unsigned long long QJ = g.Q[rc.J];
-        const unsigned long long total = rc(g.Q, n);
-        const unsigned long long Tc = total / static_cast<unsigned long long>(nseg);
-        const unsigned long long target = Tc * static_cast<unsigned long long>(k + 1);
-        // first b in [start+1, n] with cost(b) >= target
-        int64_t lo = rc.start + 1, hi = n;
-        int64_t mlo = (lo + stride - 1) / stride, mhi = ms;  // sample indices inside [lo, n]
-        while (mlo < mhi) {
-          const int64_t mid = mlo + (mhi - mlo) / 2;
-          if (rc.at(mid * stride, sQ[mid], QJ) >= target)
-            mhi = mid;
-          else
-            mlo = mid + 1;
-        }
-        if (mlo <= ms && mlo * stride >= lo && rc.at(mlo * stride, sQ[mlo], QJ) >= target) {
-          hi = mlo * stride;
-          if ((mlo - 1) * stride + 1 > lo) lo = (mlo - 1) * stride + 1;
-        } else if (ms * stride + 1 > lo) {
-          lo = ms * stride + 1;
-        }
-        while (lo < hi) {
-          const int64_t mid = lo + (hi - lo) / 2;
-          if (rc.at(mid, g.Q[mid], QJ) >= target)
-            hi = mid;
-          else
-            lo = mid + 1;
-        }
-        b = lo;
+      if (nseg > 1) {
+        rc = make_row_cost(g, i, F);
+        QJ = g.Q[rc.J];
+        Tc = rc(g.Q, n) / static_cast<unsigned long long>(nseg);
+        if (k + 1 < nseg) b = cut_search(g, rc, QJ, Tc * static_cast<unsigned long long>(k + 1), rc.start + 1, sQ,
+                                         stride, ms);
       }
     }
     // the end of segment k - 1 of the same row is this segment's start
     const int64_t prev_b = __shfl_up_sync(0xffffffffu, b, 1);
     const int64_t prev_i = __shfl_up_sync(0xffffffffu, i, 1);
     if (live && k > 0) {
-      if (lane > 0 && prev_i == i && s > s0) {
+      if (lane > 0 && prev_i == i)
         a = prev_b;
-      } else {
-        const RowCost rc = make_row_cost(g, i, F);
-        const unsigned long long total = rc(g.Q, n);
-        const unsigned long long target = total / static_cast<unsigned long long>(nseg) * static_cast<unsigned long long>(k);
-        int64_t lo = rc.start + 1, hi = n;
-        while (lo < hi) {
-          const int64_t mid = lo + (hi - lo) / 2;
-          if (rc(g.Q, mid) >= target)
-            hi = mid;
-          else
-            lo = mid + 1;
-        }
-        a = lo;
-      }
+      else
+        a = cut_search(g, rc, QJ, Tc * static_cast<unsigned long long>(k), rc.start + 1, sQ, stride, ms);
     }
     if (!live) continue;
     g.seg[s] = make_int4(static_cast<int>(i), static_cast<int>(k), static_cast<int>(a), static_cast<int>(b));
@@ -252,6 +287,8 @@ cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws,
                                            st, s);
     if (e != cudaSuccess) return e;
   }
+  // one thread per row (a scan tile computing its 2048 rows itself is
+  // latency-bound), then the row offsets
   const unsigned blocks = grid_for(g.rows + 1, 256, static_cast<unsigned>(sm_count()) * 8u);
   row_count_kernel<<<blocks, 256, 0, s>>>(g);
   note_launches(1);

@@ -19,17 +19,28 @@ struct MaxOp {
   __device__ __forceinline__ double operator()(double a, double b) const { return a > b ? a : b; }
   __device__ __forceinline__ static double identity() { return 0.0; }
 };
+// Two largest of non-negative doubles.  Every y entering a Top2 is >= +0.0
+// (-0.0 is stored as +0.0), so the comparisons use the bit patterns, which
+// order like the values: integer compares instead of GB300's slow FP64 pipe.
 struct Top2Op {
+  __device__ __forceinline__ static bool gt(double a, double b) {
+    return static_cast<unsigned long long>(__double_as_longlong(a)) >
+           static_cast<unsigned long long>(__double_as_longlong(b));
+  }
   __device__ __forceinline__ Top2 operator()(Top2 u, Top2 v) const {
     Top2 r;
-    r.a = u.a > v.a ? u.a : v.a;
-    const double lo = u.a > v.a ? v.a : u.a;
-    const double sb = u.b > v.b ? u.b : v.b;
-    r.b = lo > sb ? lo : sb;
+    const bool ua = gt(u.a, v.a);
+    r.a = ua ? u.a : v.a;
+    const double lo = ua ? v.a : u.a;
+    const double sb = gt(u.b, v.b) ? u.b : v.b;
+    r.b = gt(lo, sb) ? lo : sb;
     return r;
   }
   __device__ __forceinline__ static Top2 identity() { return Top2{0.0, 0.0}; }
 };
+
+// y as it enters a Top2: -0.0 becomes +0.0 (the domain check admits y in [0, 1)).
+__device__ __forceinline__ double top2_entry(double y) { return y > 0.0 ? y : 0.0; }
 
 __device__ __forceinline__ unsigned shfl_up(unsigned v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ unsigned long long shfl_up(unsigned long long v, int d) {

@@ -353,15 +353,14 @@ __device__ __forceinline__ void gather_rank(const Net& g, int64_t r, int32_t u, 
     g.adf[r] = split2(v);
     g.ydf[r] = split2(yu);
     g.lny[r] = split2(log(yu));
-    g.top[r] = Top2{yu, 0.0};  // scanned in reverse into suffix top-2
+    g.top[r] = Top2{top2_entry(yu), 0.0};  // scanned in reverse into suffix top-2
   }
   const double vc = v > 0x1p20 ? 0x1p20 : v;
   g.Q[r] = static_cast<unsigned long long>(ldexp(vc, F));
 }
 
-// Block 0's share of a gather: the logarithm table and the sentinel top[n].
+// Block 0's share of a gather: the sentinel top[n].
 __device__ __forceinline__ void gather_tables(const Net& g) {
-  for (int k = threadIdx.x; k < kLnTable; k += blockDim.x) ln_table_entry(g.lntab, k);
   if (threadIdx.x == 0 && g.model == MH_UECM) g.top[g.n] = Top2{0.0, 0.0};
 }
 
@@ -524,7 +523,7 @@ __global__ void __launch_bounds__(kTile / 2) tile_sort_kernel(int model, const d
   double* sy = reinterpret_cast<double*>(sk);
   __syncthreads();
 #pragma unroll
-  for (int h = 0; h < 2; ++h) sy[pos[h]] = (base + pos[h] < n) ? y[id[h]] : 0.0;
+  for (int h = 0; h < 2; ++h) sy[pos[h]] = (base + pos[h] < n) ? top2_entry(y[id[h]]) : 0.0;
   __syncthreads();
   const int p_hi = kTile - 1 - 2 * t, p_lo = p_hi - 1;
   const Top2 one_hi{sy[p_hi], 0.0}, one_lo{sy[p_lo], 0.0};
@@ -619,43 +618,136 @@ __global__ void __launch_bounds__(kMergeThreads) merge_gather_kernel(Net g, cons
   if (uecm) g.top[r] = op(tsuf[e], above);  // two largest y among ranks >= r
 }
 
-// Sets of at most kMergeSmemMax nodes: tiles of kSmallTile keys, and every
-// merge block holds all sorted keys in shared memory, so a node's searches
-// in the other tiles (kMergeGroup threads per node, a binary search per
-// tile; ids are read only on equal keys) never leave the SM.  The node's
-// rank-order copies are then written by one thread per node.
+// Sets of at most kMergeSmemMax nodes: tiles of kSmallTile keys; groups of
+// kGroupTiles tiles merged into runs of kRun keys; then every merge block
+// holds all run-sorted keys in shared memory, so a node's searches in the
+// other runs (kMergeGroup threads per node, a binary search per run; ids are
+// read only on equal keys) never leave the SM.  The node's rank-order
+// copies are then written by one thread per node.
 constexpr int kSmallTile = 512;
-constexpr int kMergeSmemMax = 24576;               // 8-byte keys in shared memory
+constexpr int kGroupTiles = 4;
+constexpr int kRun = kSmallTile * kGroupTiles;      // 2048
+constexpr int kMergeSmemMax = 24576;                // 8-byte keys in shared memory
 constexpr int kSmemThreads = 1024;
 constexpr int kSmemNodes = kSmemThreads / kMergeGroup;  // nodes per block
 
-// Tile q's keys start at q * kSmemTileStride in shared memory: the padding
-// puts the eight tiles a warp searches at once in different banks.
-constexpr int kSmemTileStride = kSmallTile + 2;
+// Merges the kGroupTiles sorted tiles of a group into one run: block b
+// places the entries of tile b at their positions in the run (own position
+// plus a binary search in each other tile of the group), and combines the
+// tiles' suffix top-2 at those positions into the run's.
+__global__ void __launch_bounds__(kSmallTile / 2) group_merge_kernel(
+    int64_t n, const unsigned long long* __restrict__ kin, const int32_t* __restrict__ vin,
+    const Top2* __restrict__ sin, unsigned long long* __restrict__ kout, int32_t* __restrict__ vout,
+    Top2* __restrict__ sout, int uecm) {
+  __shared__ unsigned long long sk[kRun];
+  __shared__ int32_t si[kRun];
+  const int tile = blockIdx.x;
+  const int64_t gbase = static_cast<int64_t>(tile / kGroupTiles) * kRun;
+  const int own = tile % kGroupTiles;
+  const int64_t glen64 = n - gbase < kRun ? n - gbase : kRun;
+  const int glen = static_cast<int>(glen64);
+  {
+    constexpr int kPer = kRun / (kSmallTile / 2);  // entries per thread, all loads in flight together
+    unsigned long long kv[kPer];
+    int32_t iv[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int t = threadIdx.x + u * (kSmallTile / 2);
+      if (t < glen) {
+        kv[u] = kin[gbase + t];
+        iv[u] = vin[gbase + t];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int t = threadIdx.x + u * (kSmallTile / 2);
+      if (t < glen) {
+        sk[t] = kv[u];
+        si[t] = iv[u];
+      }
+    }
+  }
+  __syncthreads();
+  Top2Op op;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int l = threadIdx.x + h * (kSmallTile / 2);
+    const int p = own * kSmallTile + l;  // position within the group
+    if (p >= glen) continue;
+    const unsigned long long k = sk[p];
+    const int32_t id = si[p];
+    int r = l;
+    Top2 suf = uecm ? sin[gbase + p] : Top2{0.0, 0.0};
+    for (int q = 0; q < kGroupTiles; ++q) {
+      if (q == own) continue;
+      const int tb = q * kSmallTile;
+      const int len = glen - tb < kSmallTile ? glen - tb : kSmallTile;
+      if (len <= 0) continue;
+      int c = 0;
+#pragma unroll
+      for (int step = kSmallTile; step >= 1; step >>= 1) {
+        const int at = c + step - 1;
+        if (at < len && key_less(sk[tb + at], si[tb + at], k, id)) c += step;
+      }
+      r += c;
+      if (uecm && c < len) suf = op(suf, sin[gbase + tb + c]);
+    }
+    kout[gbase + r] = k;
+    vout[gbase + r] = id;
+    if (uecm) sout[gbase + r] = suf;
+  }
+}
+
+// Run q's keys start at q * kRunStride in shared memory: the padding puts
+// the eight runs a warp searches at once in different banks.
+constexpr int kRunStride = kRun + 2;
 
 __host__ __device__ inline size_t merge_smem_bytes(int64_t n) {
-  return 8 * static_cast<size_t>((n + kSmallTile - 1) / kSmallTile) * kSmemTileStride;
+  return 8 * static_cast<size_t>((n + kRun - 1) / kRun) * kRunStride;
 }
 
 __global__ void __launch_bounds__(kSmemThreads) merge_smem_kernel(Net g, const unsigned long long* __restrict__ keys,
                                                                   const int32_t* __restrict__ ids,
-                                                                  const Top2* __restrict__ tsuf, int tiles,
+                                                                  const Top2* __restrict__ tsuf, int runs,
                                                                   Ctrl* ctrl) {
   extern __shared__ unsigned long long smk[];
   __shared__ long long s_rank[kSmemNodes];
   __shared__ Top2 s_above[kSmemNodes];
   __shared__ int32_t s_top;
   const int64_t n = g.n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-    smk[(i / kSmallTile) * kSmemTileStride + i % kSmallTile] = keys[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {  // the largest value heads one of the tiles
-    int best = 0;
-    for (int q = 1; q < tiles; ++q) {
-      const unsigned long long kq = smk[q * kSmemTileStride], kb = smk[best * kSmemTileStride];
-      if (kq < kb || (kq == kb && ids[q * kSmallTile] < ids[best * kSmallTile])) best = q;
+  {
+    // pairs of keys by 16-byte loads (the key array is 256-byte aligned), eight in flight per thread
+    constexpr int kUnroll = 8;
+    const int64_t pairs = n / 2;
+    const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+    for (int64_t p0 = threadIdx.x; p0 < pairs; p0 += static_cast<int64_t>(kUnroll) * blockDim.x) {
+      ulonglong2 v[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t p = p0 + static_cast<int64_t>(u) * blockDim.x;
+        if (p < pairs) v[u] = k2[p];
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t p = p0 + static_cast<int64_t>(u) * blockDim.x;
+        if (p < pairs) {
+          const int64_t e = 2 * p;  // e and e + 1 share a run (kRun is even)
+          unsigned long long* d = smk + (e / kRun) * kRunStride + e % kRun;
+          d[0] = v[u].x;
+          d[1] = v[u].y;
+        }
+      }
     }
-    s_top = ids[best * kSmallTile];
+    if ((n & 1) && threadIdx.x == 0) smk[((n - 1) / kRun) * kRunStride + (n - 1) % kRun] = keys[n - 1];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the largest value heads one of the runs
+    int best = 0;
+    for (int q = 1; q < runs; ++q) {
+      const unsigned long long kq = smk[q * kRunStride], kb = smk[best * kRunStride];
+      if (kq < kb || (kq == kb && ids[q * kRun] < ids[best * kRun])) best = q;
+    }
+    s_top = ids[best * kRun];
   }
   if (blockIdx.x == 0) gather_tables(g);
   __syncthreads();
@@ -668,19 +760,19 @@ __global__ void __launch_bounds__(kSmemThreads) merge_smem_kernel(Net g, const u
        e0 += static_cast<int64_t>(gridDim.x) * kSmemNodes) {
     const int64_t e = e0 + local;
     const bool live = e < n;
-    const int own = static_cast<int>(e / kSmallTile);
-    const unsigned long long k = live ? smk[own * kSmemTileStride + e % kSmallTile] : 0ull;
+    const int own = static_cast<int>(e / kRun);
+    const unsigned long long k = live ? smk[own * kRunStride + e % kRun] : 0ull;
     const int32_t id = live ? ids[e] : 0;
     long long below = 0;
     Top2 above{0.0, 0.0};
-    for (int q = gl; live && q < tiles; q += kMergeGroup) {
+    for (int q = gl; live && q < runs; q += kMergeGroup) {
       if (q == own) continue;
-      const int tb = q * kSmallTile;
-      const unsigned long long* tk = smk + q * kSmemTileStride;
-      const int len = static_cast<int>((n - tb) < kSmallTile ? (n - tb) : kSmallTile);
-      int c = 0;  // entries of tile q below (k, id)
+      const int64_t tb = static_cast<int64_t>(q) * kRun;
+      const unsigned long long* tk = smk + q * kRunStride;
+      const int len = static_cast<int>((n - tb) < kRun ? (n - tb) : kRun);
+      int c = 0;  // entries of run q below (k, id)
 #pragma unroll
-      for (int step = kSmallTile; step >= 1; step >>= 1) {
+      for (int step = kRun; step >= 1; step >>= 1) {
         const int at = c + step - 1;
         if (at < len) {
           const unsigned long long ka = tk[at];
@@ -696,7 +788,7 @@ __global__ void __launch_bounds__(kSmemThreads) merge_smem_kernel(Net g, const u
       above = op(above, Top2{__shfl_xor_sync(0xffffffffu, above.a, d), __shfl_xor_sync(0xffffffffu, above.b, d)});
     }
     if (live && gl == 0) {
-      s_rank[local] = e - static_cast<int64_t>(own) * kSmallTile + below;
+      s_rank[local] = e - static_cast<int64_t>(own) * kRun + below;
       s_above[local] = above;
     }
     __syncthreads();
@@ -714,7 +806,36 @@ __global__ void __launch_bounds__(kSmemThreads) merge_smem_kernel(Net g, const u
   }
 }
 
+// The logarithm table of the walk's and the emit's double-float logarithm
+// (Tang's method).  It depends on nothing but its index, so it is built once
+// per device (FP64 divisions and logarithms, slow at GB300's FP64 rate) and
+// every call reads it.
+__device__ LnEntry g_ln_table[kLnTable];
+
+__global__ void ln_table_kernel(LnEntry* tab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < kLnTable) ln_table_entry(tab, k);
+}
+
 }  // namespace
+
+LnEntry* ln_table_ptr() {
+  static LnEntry* ptr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ln_table) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    ln_table_kernel<<<(kLnTable + 255) / 256, 256, 0, st>>>(static_cast<LnEntry*>(p));
+    const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    cudaStreamDestroy(st);
+    if (!ok) return nullptr;
+    ptr[dev] = static_cast<LnEntry*>(p);
+  }
+  return ptr[dev];
+}
 
 cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, unsigned* ghist, Ctrl* ctrl,
                                  cudaStream_t s) {
@@ -792,11 +913,16 @@ cudaError_t launch_sort_merge(const Net& g, const Layout& L, char* ws, Ctrl* ctr
     if (e == cudaSuccess) e = sort_kernel_attributes(dev);
     if (e != cudaSuccess) return e;
     const int tiles = static_cast<int>((g.n + kSmallTile - 1) / kSmallTile);
+    const int runs = static_cast<int>((g.n + kRun - 1) / kRun);
+    auto* k0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
+    auto* v0 = reinterpret_cast<int32_t*>(ws + L.vals0);
+    auto* tsuf2 = reinterpret_cast<Top2*>(ws + L.tsuf2);
     tile_sort_kernel<kSmallTile><<<tiles, kSmallTile / 2, 0, s>>>(g.model, g.x, g.y, g.n, k1, v1, tsuf, ctrl,
                                                                    clear, clear_words);
+    group_merge_kernel<<<tiles, kSmallTile / 2, 0, s>>>(g.n, k1, v1, tsuf, k0, v0, tsuf2, g.model == MH_UECM);
     merge_smem_kernel<<<grid_for(g.n, kSmemNodes, static_cast<unsigned>(sm_count())), kSmemThreads,
-                        merge_smem_bytes(g.n), s>>>(g, k1, v1, tsuf, tiles, ctrl);
-    note_launches(2);
+                        merge_smem_bytes(g.n), s>>>(g, k0, v0, tsuf2, runs, ctrl);
+    note_launches(3);
     return cudaGetLastError();
   }
   const int tiles = static_cast<int>((g.n + kSortTile - 1) / kSortTile);

@@ -478,6 +478,7 @@ cudaError_t prepare_kernel_attributes(int model) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if ((e = sort_kernel_attributes(dev)) != cudaSuccess) return e;
+  if (!ln_table_ptr()) return cudaErrorLaunchFailure;  // built here, before any capture
   if (model == MH_UECM) {
     if ((e = walk_attributes<true, 0>(dev)) != cudaSuccess) return e;
     if ((e = walk_attributes<true, 1>(dev)) != cudaSuccess) return e;
