@@ -502,6 +502,92 @@ def bipartite_leg(args, dev, flush):
 
 
 # ---------------------------------------------------------------------------
+# The other single-network configurations: unweighted N = 1,000 x 100
+# samples (COO) and unweighted Pareto N = 10^6, one sample (CSR); the
+# oracle's serial walk and its brute-force sampler timed beside them.
+# ---------------------------------------------------------------------------
+def configs_leg(args, dev, flush):
+    import torch
+
+    import oracle
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.autotune import pick
+    from paper_2509_13230_gb300.sampler import Sampler
+
+    hbm_gbs, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+    cases = [("ubcm_n1k_x100", workloads.ubcm_n1k(), 100, "coo", 8, 0),
+             ("ubcm_pareto_n1m_x1", workloads.ubcm_pareto_n1m(), 1, "csr", 4, 8)]
+    for name, net, samples, layout, bytes_per_edge, bytes_per_node in cases:
+        x = torch.from_numpy(net.x).to(dev)
+        table = []
+        for T in (8, 16, 32):
+            s = Sampler(nat.MH_UBCM, x, None, num_samples=samples, seg_target=T, layout=layout)
+            s.run()
+            s.flags |= nat.MH_TIMING
+            ms, edges = 0.0, 0
+            for _ in range(4):
+                nat.check(s.call(), "mh_sample_ubcm")
+                ms += nat.mh_last_call_info().total_ms
+                edges += int(s.h_counts.sum())
+            table.append({"T": T, "ctas": 0, "ms": ms / 4, "edges": edges // 4, "edges_per_ms": edges / ms})
+            del s
+        T, _ = pick(table)
+        s = Sampler(nat.MH_UBCM, x, None, num_samples=samples, seg_target=T, layout=layout)
+        s.run()
+        s.flags |= nat.MH_TIMING
+        for _ in range(args.warmup):
+            nat.check(s.call(), "mh_sample_ubcm")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total_ms, edges, phase = 0.0, 0, np.zeros(3)
+        steps = max(args.steps, 5)
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            nat.check(s.call(), "mh_sample_ubcm")
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            info = nat.mh_last_call_info()
+            phase += (info.prepare_ms, info.walk_ms, info.emit_ms)
+            edges += int(s.h_counts.sum())
+        walk_ms = phase[1]
+        out_bytes = bytes_per_edge * edges + bytes_per_node * (net.n + 1) * samples * steps
+        achieved = out_bytes / (walk_ms / 1e3) / 1e9
+        # oracle: a bounded share of the samples, and one brute-force sample
+        k = min(samples, 10)
+        t0 = time.perf_counter()
+        _, _, _, c, _ = oracle.mh_sample(oracle.UBCM, net.x, num_samples=k, seg_target=T)
+        mh_s = time.perf_counter() - t0
+        bf = None
+        if net.n <= 20_000:
+            t0 = time.perf_counter()
+            _, _, _, evals = oracle.bf_sample(oracle.UBCM, net.x)
+            bf_s = time.perf_counter() - t0
+            bf = {"pairs_per_s": evals / bf_s, "seconds_per_sample": bf_s,
+                  "mh_over_bf_speedup_cpu": bf_s / (mh_s / k)}
+        else:
+            pairs = net.n * (net.n - 1) / 2
+            bf = {"pairs": pairs, "note": "not run: one brute-force sample evaluates every pair"}
+        out[name] = {"value": edges / (total_ms / 1e3), "unit": "edges/s", "ms_per_step": total_ms / steps,
+                     "samples_per_step": samples, "edges_per_step": edges // steps, "seg_target": T,
+                     "output": f"{layout} ({bytes_per_edge} B/edge" + (f" + {bytes_per_node} B/node)" if
+                                                                      bytes_per_node else ")"),
+                     "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit"), (phase / steps).tolist())),
+                     "autotune": table,
+                     "roofline": {"bound": "hbm", "kernel": "walk_kernel", "achieved": achieved, "peak": hbm_gbs,
+                                  "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+                                  "peak_kind": peak_kind, "walk_ms_per_step": walk_ms / steps},
+                     "cpu_baseline": {"value": int(c.sum()) / mh_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"{k} samples of the same network, serial FP64 walk, {mh_s:.2f} s"},
+                     "cpu_brute_force": bf}
+        del s
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Output layouts of the headline workload: one-row CSR and the symmetric CSR
 # (every edge in both endpoint rows), same samples and segment length.
 # ---------------------------------------------------------------------------
@@ -694,8 +780,11 @@ def run_ours(args, rank, world, local_rank):
         pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
         fitted = fit_leg(args, dev)
         bipartite = bipartite_leg(args, dev, flush)
+    configs = None
     if world == 1:
         layouts = layouts_leg(args, dev, flush, T)
+        if not args.no_ensemble:
+            configs = configs_leg(args, dev, flush)
     if world > 1:
         dist.barrier()
 
@@ -710,8 +799,8 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if os.path.exists(WALK_PROFILE):
         prof = json.load(open(WALK_PROFILE))
-        if prof.get("sources_sha") == sources_hash() and prof.get("seg_target", 32) == (T or 32):
-            traffic = prof.get("dram_bytes_per_launch")
+        if prof.get("sources_sha") == sources_hash():
+            traffic = prof.get("dram_bytes_per_launch_by_seg_target", {}).get(str(T or 32))
     # CPU oracle on a bounded sample of the same workload (rank 0, N = 1 only)
     cpu = None
     if world == 1:
@@ -744,6 +833,7 @@ def run_ours(args, rank, world, local_rank):
         "fit_then_sample": fitted,
         "bipartite": bipartite,
         "layouts": layouts,
+        "configs": configs,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -758,7 +848,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts"], default="all",
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs"], default="all",
                     help="ensemble: run only the batched ensemble leg and print its object")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--seg-target", type=int, default=0,
@@ -788,6 +878,12 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"fit_then_sample": fit_leg(args, torch.device("cuda", local_rank))}), flush=True)
+    elif args.leg == "configs":
+        import torch
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"configs": configs_leg(args, dev, flush)}), flush=True)
     elif args.leg == "layouts":
         import torch
         torch.cuda.set_device(local_rank)
