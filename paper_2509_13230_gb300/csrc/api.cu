@@ -211,7 +211,7 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.zero_begin = off;
   L.ghist = take(4 * 8 * 256);
   L.sort_counters = take(16);
-  L.sort_state = take(8 * 256 * static_cast<size_t>(L.tiles > 0 ? L.tiles : 1));
+  L.sort_state = take(2 * 8 * 256 * static_cast<size_t>(L.tiles > 0 ? L.tiles : 1));
   L.scan_counters = take(16);
   L.scan_flags = take(4 * static_cast<size_t>(L.scan_tiles));
   L.zero_end = off;

@@ -153,7 +153,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
     L.zero_begin = lo;
     L.ghist = ltake(4 * 8 * 256);
     L.sort_counters = ltake(16);
-    L.sort_state = ltake(8 * 256 * tiles);
+    L.sort_state = ltake(2 * 8 * 256 * tiles);
     L.scan_counters = ltake(16);
     L.scan_flags = ltake(4 * static_cast<size_t>(L.scan_tiles));
     L.zero_end = lo;

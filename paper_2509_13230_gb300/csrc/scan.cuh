@@ -388,7 +388,7 @@ cudaError_t device_scan_1p(const T* in, T* out, ScanLen L, bool exclusive, const
 // Single pass for short inputs (launch count dominates), three kernels for
 // long ones (when every tile starts at once, look-backs would walk back over
 // many tiles).  `st.values` doubles as the three-kernel form's partials.
-constexpr int64_t kOnePassMaxTiles = 32;
+constexpr int64_t kOnePassMaxTiles = 1024;
 
 template <typename T, typename Op, bool kReverse = false>
 cudaError_t scan_any(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total, bool write_total_at_len,

@@ -172,9 +172,12 @@ __device__ __forceinline__ float2 split2(double v) {
 
 constexpr int kSortLookBack = 8;  // predecessor tiles read per look-back step
 
+// Two sets of look-back state, used by passes of alternate parity: a pass
+// clears, tile by tile, the set the next pass uses (the previous pass, its
+// last user, has finished), so no block clears the whole state alone.
 struct SortState {
-  unsigned long long* words;  // per (tile, digit): count << 2 | flag (1 aggregate, 2 inclusive)
-  unsigned* counters;         // [0] tile ticket, [1] finished blocks
+  unsigned long long* words[2];  // per (tile, digit): count << 2 | flag (1 aggregate, 2 inclusive)
+  unsigned* counters[2];         // [0] tile ticket
 };
 
 // One LSD pass (one-sweep): a tile claimed by ticket ranks its keys stably
@@ -187,17 +190,18 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
     int32_t* __restrict__ vout, int64_t n, int pass, const unsigned* __restrict__ ghist, SortState st, Ctrl* ctrl) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ unsigned s_tile;
-  __shared__ bool s_last;
   __shared__ unsigned wcount[kWarps][256];
   __shared__ unsigned run[256];
   __shared__ unsigned long long dbase[256];  // global start of each digit + earlier tiles
   const int shift = 8 * pass;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int64_t tiles = (n + kSortTile - 1) / kSortTile;
-  if (t == 0) s_tile = atomicAdd(&st.counters[0], 1u);
+  unsigned long long* const words = st.words[pass & 1];
+  if (t == 0) s_tile = atomicAdd(&st.counters[pass & 1][0], 1u);
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t base = tile * kSortTile;
+  st.words[(pass + 1) & 1][tile * 256 + t] = 0ull;  // this tile's share of the next pass's state
+  if (tile == 0 && t == 0) st.counters[(pass + 1) & 1][0] = 0u;
   if (digit_constant(ctrl, shift)) {
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
     // decoupled look-back per digit: counts of digit t in earlier tiles
     {
       const unsigned long long cnt = run[t];
-      unsigned long long* my = &st.words[tile * 256 + t];
+      unsigned long long* my = &words[tile * 256 + t];
       unsigned long long prefix = 0;
       if (tile == 0) {
         atomicExch(my, (cnt << 2) | 2ull);
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
           unsigned long long w[kSortLookBack];
 #pragma unroll
           for (int q = 0; q < kSortLookBack; ++q)
-            w[q] = (p - q >= 0) ? *reinterpret_cast<const volatile unsigned long long*>(&st.words[(p - q) * 256 + t])
+            w[q] = (p - q >= 0) ? *reinterpret_cast<const volatile unsigned long long*>(&words[(p - q) * 256 + t])
                                 : 2ull;
 #pragma unroll
           for (int q = 0; q < kSortLookBack; ++q) {
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
                 break;
               }
               __nanosleep(32);
-              w[q] = *reinterpret_cast<const volatile unsigned long long*>(&st.words[(p - q) * 256 + t]);
+              w[q] = *reinterpret_cast<const volatile unsigned long long*>(&words[(p - q) * 256 + t]);
             }
             prefix += w[q] >> 2;
             if ((w[q] & 3ull) == 2ull) done = true;
@@ -317,19 +321,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
           atomicOr(&ctrl->status, kStInternal);
         }
       }
-    }
-  }
-  __syncthreads();
-  if (t == 0) {
-    __threadfence();
-    s_last = atomicAdd(&st.counters[1], 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    for (int64_t w = t; w < tiles * 256; w += blockDim.x) st.words[w] = 0ull;
-    if (t == 0) {
-      st.counters[0] = 0u;
-      st.counters[1] = 0u;
     }
   }
 }
@@ -848,7 +839,7 @@ cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t
 // Small inputs: eight one-sweep passes (one launch each).  Large inputs:
 // per pass a tile histogram, a scan of the (digit, tile) counts and a stable
 // scatter, which keeps every launch bandwidth-bound.
-constexpr int64_t kOneSweepMaxTiles = 32;
+constexpr int64_t kOneSweepMaxTiles = 1024;
 
 cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
   auto* k0 = reinterpret_cast<unsigned long long*>(ws + L.keys0);
@@ -856,8 +847,10 @@ cudaError_t launch_sort(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cud
   auto* v0 = reinterpret_cast<int32_t*>(ws + L.vals0);
   auto* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
   const unsigned* ghist = reinterpret_cast<const unsigned*>(ws + L.ghist);
-  SortState st{reinterpret_cast<unsigned long long*>(ws + L.sort_state),
-               reinterpret_cast<unsigned*>(ws + L.sort_counters)};
+  auto* sw = reinterpret_cast<unsigned long long*>(ws + L.sort_state);
+  auto* sc = reinterpret_cast<unsigned*>(ws + L.sort_counters);
+  const int64_t set_words = 256 * (L.tiles > 0 ? L.tiles : 1);
+  SortState st{{sw, sw + set_words}, {sc, sc + 2}};
   const ScanState sst{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
                       reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
   auto* hist = reinterpret_cast<unsigned*>(ws + L.hist);
