@@ -143,6 +143,50 @@ def oracle_rate(net, seconds: float, first_sample: int = 0):
     return edges / t_total, s - first_sample, t_total
 
 
+def _oracle_worker(x, y, first_sample: int, stride: int, seconds: float):
+    """One process of the all-cores oracle baseline: samples first, first +
+    stride, ... for about `seconds`; returns (edges, samples, busy seconds)."""
+    import oracle
+    edges, t_total, s, k = 0, 0.0, first_sample, 0
+    while t_total < seconds:
+        t0 = time.perf_counter()
+        _, _, _, counts, _ = oracle.mh_sample(oracle.UECM, x, y, sample_begin=s, num_samples=1)
+        t_total += time.perf_counter() - t0
+        edges += int(counts.sum())
+        s += stride
+        k += 1
+    return edges, k, t_total
+
+
+def oracle_rate_all_cores(net, seconds: float):
+    """Edges/s of the serial oracle with one process per host core (spawned,
+    so no process inherits a CUDA context), each drawing whole samples."""
+    import concurrent.futures
+    import multiprocessing
+
+    import oracle
+    oracle.load()  # built once before the workers load it
+    cores = os.cpu_count() or 1
+    ctx = multiprocessing.get_context("spawn")
+    t0 = time.perf_counter()
+    with concurrent.futures.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+        futs = [ex.submit(_oracle_worker, net.x, net.y, c, cores, seconds) for c in range(cores)]
+        res = [f.result() for f in futs]
+    wall = time.perf_counter() - t0
+    edges = sum(r[0] for r in res)
+    # the workers run concurrently; the rate is over the longest worker's busy time
+    busy = max(r[2] for r in res)
+    return edges / busy, sum(r[1] for r in res), busy, wall, cores
+
+
+def oracle_bf_time(net):
+    """Seconds of one brute-force sample of the oracle (every pair a Bernoulli)."""
+    import oracle
+    t0 = time.perf_counter()
+    _, _, _, evals = oracle.bf_sample(oracle.UECM, net.x, net.y)
+    return time.perf_counter() - t0, evals
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -518,8 +562,10 @@ def configs_leg(args, dev, flush):
     hbm_gbs, peak_kind = peaks()
     stream = torch.cuda.current_stream()
     out = {}
+    n1m = workloads.ubcm_pareto_n1m()
     cases = [("ubcm_n1k_x100", workloads.ubcm_n1k(), 100, "coo", 8, 0),
-             ("ubcm_pareto_n1m_x1", workloads.ubcm_pareto_n1m(), 1, "csr", 4, 8)]
+             ("ubcm_pareto_n1m_x1", n1m, 1, "csr", 4, 8),
+             ("ubcm_pareto_n1m_x100_sustained", n1m, 100, "csr", 4, 8)]
     for name, net, samples, layout, bytes_per_edge, bytes_per_node in cases:
         x = torch.from_numpy(net.x).to(dev)
         table = []
@@ -557,7 +603,7 @@ def configs_leg(args, dev, flush):
         out_bytes = bytes_per_edge * edges + bytes_per_node * (net.n + 1) * samples * steps
         achieved = out_bytes / (walk_ms / 1e3) / 1e9
         # oracle: a bounded share of the samples, and one brute-force sample
-        k = min(samples, 10)
+        k = min(samples, 10) if net.n < 1_000_000 else 1
         t0 = time.perf_counter()
         _, _, _, c, _ = oracle.mh_sample(oracle.UBCM, net.x, num_samples=k, seg_target=T)
         mh_s = time.perf_counter() - t0
@@ -802,12 +848,22 @@ def run_ours(args, rank, world, local_rank):
         if prof.get("sources_sha") == sources_hash():
             traffic = prof.get("dram_bytes_per_launch_by_seg_target", {}).get(str(T or 32))
     # CPU oracle on a bounded sample of the same workload (rank 0, N = 1 only)
-    cpu = None
+    cpu = cpu_all = cpu_bf = None
     if world == 1:
         rate, nsamp, secs = oracle_rate(net, 10.0)
         cpu = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": f"{nsamp} whole samples of {WORKLOAD} (N = {net.n}), serial FP64 walk, "
                          f"{secs:.1f} s on one host core"}
+        if not args.no_ensemble:
+            rate_a, nsamp_a, busy_a, wall_a, cores_a = oracle_rate_all_cores(net, 8.0)
+            cpu_all = {"value": rate_a, "unit": "edges/s", "cores": cores_a, "kind": "oracle",
+                       "sample": f"{nsamp_a} whole samples of {WORKLOAD}, one spawned process per host core, "
+                                 f"{busy_a:.1f} s busy per process ({wall_a:.1f} s wall with start-up)"}
+            bf_s, evals = oracle_bf_time(net)
+            cpu_bf = {"seconds_per_sample": bf_s, "pairs": evals, "pairs_per_s": evals / bf_s,
+                      "edges_per_s": (edges / args.steps / SAMPLES_PER_STEP) / bf_s,
+                      "mh_over_bf_speedup_cpu": bf_s / (secs / nsamp), "kind": "oracle brute force",
+                      "cores": 1}
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -821,6 +877,8 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / hbm_gbs, "traffic": traffic, "kernel": "walk_kernel",
                      "peak_kind": peak_kind, "walk_ms_per_launch": walk_avg_ms},
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
+        "cpu_brute_force": cpu_bf,
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 16 * net.n,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,

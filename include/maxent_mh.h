@@ -74,7 +74,8 @@ typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
                                /* hold 2 x capacity_edges entries                   */
 #define MH_FP64_ONLY 0x100u  /* decide every draw with the plain FP64 path         */
 #define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
-                             /* caller's stream (see mh_last_call_info)            */
+                             /* caller's stream (see mh_last_call_info); calls of  */
+                             /* more than 1024 sample chunks are not timed         */
 
 /* stats slots (h_stats, 4 x uint64) */
 #define MH_STAT_PROPOSALS 0 /* candidate draws                                     */

@@ -23,8 +23,10 @@ thread_local int64_t g_launches = 0;
 
 // CUDA events of a timed call: start, after prepare, then (before walk,
 // after walk, after emit) per chunk.  Created on first use, per thread.
+constexpr int64_t kTimedChunks = 1024;  // MH_TIMING covers calls of at most this many sample chunks
+
 struct CallTimer {
-  static constexpr int kMax = 2 + 3 * 64;
+  static constexpr int kMax = 2 + 3 * kTimedChunks;
   cudaEvent_t ev[kMax] = {};
   bool ready = false;
   int used = 0;
@@ -613,7 +615,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     g.x_r = xr;
     g.y_r = yr;
   }
-  const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= 64;
+  const bool timed = (p->flags & MH_TIMING) != 0 && (p->num_samples + L.spc - 1) / L.spc <= kTimedChunks;
   const size_t counts_bytes = 8 * static_cast<size_t>(p->num_samples);
   if (g_pinned.bytes < sizeof(Ctrl) + counts_bytes) {
     g_graphs.clear();  // cached graphs copy into the old buffer
