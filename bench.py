@@ -221,7 +221,7 @@ def run_reference(args, rank):
 ENSEMBLE_SAMPLES = 64
 
 
-def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 << 28, seg_target=None,
+def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=None, seg_target=None,
                  loop_samples=None):
     import torch
 
@@ -238,6 +238,7 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 <<
     n = np.array([nw.n for nw in nets_np], dtype=np.int64)
     uecm = np.array([nw.model == nat.MH_UECM for nw in nets_np])
     samples = samples or args.ensemble_samples
+    capacity = capacity or args.ensemble_capacity
     tuned = None
     T, ctas = 0, 0
     if seg_target is not None:
@@ -246,10 +247,10 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=1 <<
         T = args.ensemble_seg_target
     elif not args.no_tune:
         from paper_2509_13230_gb300.autotune import tune_ensemble
-        tuned = tune_ensemble(nets, candidates_t=(16, 32, 64), candidates_ctas=(0, 2), num_samples=2, reps=2)
+        tuned = tune_ensemble(nets, candidates_t=(8, 16, 32), candidates_ctas=(0, 2), num_samples=2, reps=2)
         T, ctas = tuned.seg_target, tuned.walk_ctas_per_sm
     ens = Ensemble(nets, num_samples=samples, layout="csr", capacity=capacity, timing=True, seg_target=T,
-                   walk_ctas_per_sm=ctas)
+                   walk_ctas_per_sm=ctas, max_wave_items=args.ensemble_wave_items)
     stream = torch.cuda.current_stream()
     walk = {"ms": 0.0, "emit_ms": 0.0, "prepare_ms": 0.0}
 
@@ -916,6 +917,10 @@ def main():
     ap.add_argument("--ensemble-networks", type=int, default=128,
                     help="networks of the ensemble leg (evenly spaced subset of the 128)")
     ap.add_argument("--ensemble-samples", type=int, default=ENSEMBLE_SAMPLES, help="samples per network")
+    ap.add_argument("--ensemble-capacity", type=int, default=1 << 30,
+                    help="edges per wave (output buffers reused by every wave)")
+    ap.add_argument("--ensemble-wave-items", type=int, default=1 << 28,
+                    help="work items (sample, segment) per wave")
     ap.add_argument("--ensemble-loop-samples", type=int, default=4,
                     help="samples per network of the ensemble's per-sample loop (0 skips the loop)")
     args = ap.parse_args()
