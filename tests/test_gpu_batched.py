@@ -205,7 +205,7 @@ def test_ensemble_128_full_size_sampled_pairs():
         idx = [t for t in range(len(nets_np)) if nets_np[t].model == model]
         order = sorted(idx, key=lambda t: sizes[t])
         pick |= {(order[len(order) // 2], 31), (order[-1] if model == UBCM else order[len(order) * 3 // 4], 7)}
-    ens = Ensemble(to_device(nets), num_samples=64, layout="csr", capacity=1 << 28)
+    ens = Ensemble(to_device(nets), num_samples=64, layout="csr", capacity=1 << 30, max_wave_items=1 << 28)
     chk = Checker(nets, seed=0, sample_begin=0, layout="csr", only=pick)
     counts, stats = ens.sample(on_wave=chk)
     assert chk.pairs == len(pick)
