@@ -127,13 +127,15 @@ class Sampler:
         self.csr_w = torch.empty(per_edge * cap, dtype=torch.int32, device=dev) if csr and weighted else None
         self.h_counts = np.zeros(self.num_samples, dtype=np.int64)
         self.h_stats = np.zeros(4, dtype=np.uint64)
+        # host pointers passed on every call, converted once
+        self._h_counts_p = self.h_counts.ctypes.data_as(ctypes.c_void_p)
+        self._h_stats_p = self.h_stats.ctypes.data_as(ctypes.c_void_p)
 
     def call(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> int:
         """One C-ABI call with the current buffers; returns its code."""
         p = self.params(sample_begin)
         st = _stream_handle(stream)
-        counts = self.h_counts.ctypes.data_as(ctypes.c_void_p)
-        stats = self.h_stats.ctypes.data_as(ctypes.c_void_p)
+        counts, stats = self._h_counts_p, self._h_stats_p
         if self.model == nat.MH_UBCM:
             return nat.mh_sample_ubcm(_ptr(self.x), self.n, p, _ptr(self.workspace), self.ws_bytes, _ptr(self.src),
                                       _ptr(self.dst), _ptr(self.csr_off), _ptr(self.csr_idx), self.capacity, counts,
@@ -188,8 +190,7 @@ class BipartiteSampler(Sampler):
 
     def call(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> int:
         p = self.params(sample_begin)
-        counts = self.h_counts.ctypes.data_as(ctypes.c_void_p)
-        stats = self.h_stats.ctypes.data_as(ctypes.c_void_p)
+        counts, stats = self._h_counts_p, self._h_stats_p
         return nat.mh_sample_bipartite(self.model, _ptr(self.x), _ptr(self.y), self.n, _ptr(self.x_minus),
                                        _ptr(self.y_minus), self.n_minus, p, _ptr(self.workspace), self.ws_bytes,
                                        _ptr(self.src), _ptr(self.dst), _ptr(self.w), _ptr(self.csr_off),
