@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
       if (it.uecm) {
         const float2 lj = g.lny[gj];
         wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
-                         it.sample, P.key0, it.key1, it.yi, g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
+                         it.sample, P.key0, it.key1, it.yi, &g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
                          tab, fp64_only, overflow, fallbacks);
       }
       if (pos < P.o.capacity && P.o.src) {

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
       if (uecm) {
         const float2 lj = g.lny[j];
         wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
-                         P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, g.ys[j],
+                         P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
                          df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
       }
       if (pos < P.o.capacity) {

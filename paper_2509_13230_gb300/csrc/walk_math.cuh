@@ -368,8 +368,10 @@ static __device__ __noinline__ int32_t weight_fp64(unsigned long long N, double 
   return 1 + static_cast<int32_t>(floor(tw));
 }
 
+// yj points at y_j: it is read only on the canonical FP64 path (rare), so the
+// usual draw costs no load of it.
 __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t i, uint32_t sample, uint32_t key0,
-                                               uint32_t key1, double yi, double yj, df2 lnyi, df2 lnyj,
+                                               uint32_t key1, double yi, const double* yj, df2 lnyi, df2 lnyj,
                                                const LnEntry* tab, bool fp64_only, bool& overflow,
                                                unsigned long long& fallbacks) {
   const uint4 w = philox4x32_10(make_uint4(0x80000000u | (e >> 1), k, i, sample), key0, key1);
@@ -396,7 +398,7 @@ __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t 
     if (t.hi < 2.0e9f && floor_decided(t, 0x7FFFFFFF, fl)) return 1 + static_cast<int32_t>(fl);
   }
   fallbacks += 1;
-  return weight_fp64(N, yi * yj, overflow);
+  return weight_fp64(N, yi * *yj, overflow);
 }
 
 }  // namespace mh
