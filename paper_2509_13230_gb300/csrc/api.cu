@@ -1,10 +1,12 @@
 // C ABI entry points (include/maxent_mh.h).
 //
 // A sampling call runs, in stream order and without a host round trip until
-// the end:  validate + sort keys -> radix sort -> gather into rank order ->
-// bound prep + segment table -> per sample chunk: walk -> emit.  It then
-// copies the status word, the counters and the per-sample edge counts to a
-// pinned host buffer, synchronises the stream and maps the status to a code.
+// the end:  validate + sort keys and copy the parameters into rank order
+// (sort.cu) -> bound prep + segment table (partition.cu) -> per sample chunk:
+// walk (walk.cu) -> item scan + emit (emit.cu).  It then copies the status
+// word, the counters and the per-sample edge counts to a pinned host buffer,
+// synchronises the stream and maps the status to a code.  A call repeated
+// with the same arguments replays a captured CUDA graph.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>

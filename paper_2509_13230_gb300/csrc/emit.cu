@@ -10,7 +10,9 @@
 //   CSR  csr_idx[off[s(n+1) + perm[i]] + position within row i] = perm[j]
 // CSR rows are original node ids; row u holds the edges whose higher-ranked
 // endpoint is u (bipartite: whose + endpoint is u), and offsets are
-// positions in the concatenated index array.
+// positions in the concatenated index array.  The symmetric layout
+// (MH_CSR_SYMMETRIC) lists every edge in both endpoint rows: see
+// launch_emit for its passes.
 #include "mh_internal.cuh"
 #include "scan.cuh"
 #include "walk_math.cuh"

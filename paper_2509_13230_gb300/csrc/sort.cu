@@ -1,12 +1,23 @@
 // Node order (Sec. 2.4 step (i): ascending alpha; Algorithm 1: ascending
-// alpha + beta), i.e. descending x for UBCM and descending a = x*y for UECM.
+// alpha + beta), i.e. descending x for UBCM and descending a = x*y for UECM,
+// ties by ascending original id; then the rank-order copies the walk reads.
 //
-// LSD radix sort of the FP64 key bits, 8 bits per pass, stable, so equal
-// keys keep ascending original id.  Keys are non-negative doubles, whose bit
-// patterns order like the values; the sort key is the complement, which turns
-// descending values into ascending integers.  Passes whose digit is the same
-// for every key (found from the OR and AND of all keys) copy instead of
-// ranking, so the buffer parity never depends on the data.
+// Keys are non-negative doubles, whose bit patterns order like the values;
+// the sort key is the complement, which turns descending values into
+// ascending integers.  Three paths by set size, with the same result:
+//  * up to 24,576 nodes: 512-key tile sorts in shared memory, a merge of
+//    groups of four tiles into 2048-key runs, and a merge that ranks every
+//    node against the other runs with all keys in shared memory and writes
+//    the rank-order arrays and the suffix top-2 of y directly;
+//  * up to 65,536 nodes: 2048-key tile sorts and a merge that searches every
+//    32nd key in shared memory;
+//  * larger sets: LSD radix sort of the key bits, 8 bits per pass, stable
+//    (one-sweep passes up to 2 M keys, histogram + scan + scatter beyond),
+//    then a gather and, for UECM, a reverse scan for the suffix top-2.
+//    Passes whose digit is the same for every key (found from the OR and AND
+//    of all keys) copy instead of ranking, so the buffer parity never depends
+//    on the data.
+// The same radix kernels sort the symmetric CSR layout's (sample, rank) keys.
 #include "mh_internal.cuh"
 #include "scan.cuh"
 #include "walk_math.cuh"
