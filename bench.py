@@ -356,10 +356,14 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=None
 # 200,000, the size of the fitting workload), the O(N^2) sums of inference.
 # ---------------------------------------------------------------------------
 PAIR_N = 200_000
-# FP32 operations per ordered pair of the double-float evaluation, counted
-# from its operation sequence (two_sum 6, fast_two_sum 3, df_mul 7, df_add 20,
-# df_add_f 10, df_div 16 with each division as reciprocal + multiply).
-PAIR_OPS = {"fwd": 126, "bwd": 344}
+# FP32 operations per ordered pair of the UECM double-float evaluation,
+# counted from its operation sequence (two_sum 6, fast_two_sum 3, df_mul 7,
+# sloppy addition 11, 1 - r 7, df_div 16 with each division as reciprocal +
+# multiply, accumulation 8 per term plus a 6-operation renormalisation every
+# 8 terms).  Forward: a_i a_j, y_i y_j, 1 - r, D, two divisions, two sums.
+# Backward: r, 1 - r, A, D, D^2, Q, g_k and g_s sums, the x term (3 ops) and
+# the y term (6 ops), two sums.
+PAIR_OPS = {"fwd": 81, "bwd": 185}
 FP32_LANES_PER_SM = 128
 
 

@@ -3,23 +3,41 @@
 //
 //   <k_i> = sum_{j != i} p_ij,   <s_i> = sum_{j != i} m_ij,   m_ij = p_ij / (1 - r_ij)
 //
-// with E[w | w > 0] = 1 / (1 - r) from Eq. 4.  Each thread owns one row i and
-// walks all j in tiles staged through shared memory, recomputing every pair
-// term (nothing of size N^2 is stored).
+// with E[w | w > 0] = 1 / (1 - r) from Eq. 4.  Every pair term is recomputed
+// (nothing of size N^2 is stored).
+//
+// Work decomposition.  A persistent grid (SM count x resident blocks) walks
+// groups of 64 rows; in a block of 16 warps every lane owns two rows of the
+// group and warp w sums them over the w-th sixteenth of the columns, staged 32
+// at a time in the warp's own shared memory.  The 16 partial sums of a row
+// are added in warp order by one thread, so results do not depend on the
+// grid or the timing.  Groups of 64 rows keep the tail of the grid at about
+// 1/40 of the work for N = 2*10^5 (one row per thread in blocks of 256 left
+// a second wave 29% full).
 //
 // Arithmetic.  FP64 runs at 1/64 of the FP32 rate on this GPU, so each pair
 // term is evaluated in double-float arithmetic (pairs of FP32 values, about
-// 48 significant bits; walk_math.cuh), summed in double-float over a tile of
-// kPairThreads columns, and the tile sums are accumulated in FP64.  A term is
-// within a few 2^-45 of its exact value, a tile sum within 2^-38 of its
-// terms' total, and the FP64 accumulation over N / 256 tiles adds less than
-// N 2^-61, so the row sums are within about 1e-11 relative of exact sums.
+// 48 significant bits; walk_math.cuh).  Terms are summed with an error-free
+// two_sum of the high parts and a plain FP32 sum of the low parts and errors,
+// renormalised every 8 terms and added to an FP64 total every 32: a term is
+// within a few 2^-45 of its exact value, a 32-term partial within 2^-38 of
+// the sum of its absolute terms, so the row sums are within about 1e-11 of
+// the sum of |terms|.  Operands outside the double-float range (df_safe_*)
+// take FP64 terms added straight to the FP64 totals.  A batch of 32 columns
+// that is full, within range and away from the group's own rows takes a loop
+// without per-pair checks.
 //
-// Derivatives (A = a_i a_j, a = x y, r = y_i y_j, D = 1 - r + A, z = x_i x_j):
+// Derivatives (a = x y, A = a_i a_j, r = y_i y_j, D = 1 - r + A, Q = a_j / D^2,
+// z = x_i x_j), each written without dividing by x_i or y_i:
 //   UBCM  dp/dx_i = x_j / (1 + z)^2
-//   UECM  dp/dx_i = y_i a_j (1 - r) / D^2       dm/dx_i = y_i a_j / D^2
-//         dp/dy_i = x_i a_j / D^2               dm/dy_i = x_i a_j / (D^2 (1 - r)) + p y_j / (1 - r)^2
-// which equal p(1-p)/x_i, p/(y_i D), ... without dividing by x_i or y_i.
+//   UECM  dp/dx_i = y_i (1 - r) Q        dm/dx_i = y_i Q
+//         dp/dy_i = x_i Q                dm/dy_i = x_i Q (1 - r + r D) / (1 - r)^2
+// so that, with gk = g_k,i + g_k,j and gs = g_s,i + g_s,j,
+//   dL/dx_i = y_i sum_j Q (gk (1 - r) + gs)
+//   dL/dy_i = x_i sum_j Q (gk + gs (1 - r + r D) / (1 - r)^2)
+// and the row factors y_i, x_i multiply the finished sums.
+#include <algorithm>
+
 #include "mh_internal.cuh"
 #include "walk_math.cuh"
 
@@ -27,16 +45,61 @@ namespace mh {
 
 namespace {
 
-constexpr int kPairThreads = 256;
+constexpr int kPairWarps = 16;
+constexpr int kPairThreads = 32 * kPairWarps;
+constexpr int kLaneRows = 2;
+constexpr int kGroupRows = 32 * kLaneRows;
+constexpr int kBatch = 32;
+constexpr int kNormEvery = 8;
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ double df_to_double(df2 v) {
-  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
+// Operands the double-float path takes.  Every intermediate of the pair terms
+// then stays a normal FP32 number, low parts included:
+//   a (x for the UBCM, x y for the UECM): 0 or [2^-30, 2^30], so a product of
+//     two lies in [2^-60, 2^60], D^2 below 2^121 and Q above 2^-90;
+//   y: in [0, 1 - 2^-12], so 1 - y_i y_j >= 2^-11 and its double-float value
+//     (absolute error about 2^-48) is good to 2^-37 relative;
+//   gradients: |g| <= 2^40.
+__device__ __forceinline__ bool df_safe_a(double v) { return v == 0.0 || (v >= 0x1p-30 && v <= 0x1p30); }
+__device__ __forceinline__ bool df_safe_y(double v) { return v >= 0.0 && v <= 1.0 - 0x1p-12; }
+__device__ __forceinline__ bool df_safe_g(double g) { return fabs(g) <= 0x1p40; }
+
+// Sum of double-float terms: two_sum on the high parts, the low parts and the
+// rounding errors summed in FP32 until norm() folds them back.
+struct DfAcc {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(df2 t) {
+    const df2 s = two_sum(hi, t.hi);
+    hi = s.hi;
+    lo += s.lo + t.lo;
+  }
+  __device__ __forceinline__ void norm() {
+    const df2 s = two_sum(hi, lo);
+    hi = s.hi;
+    lo = s.lo;
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+// 1 - r for a double-float r in [0, 1 - 2^-11]: |1| >= r.hi, so fast_two_sum
+// returns 1 - r.hi exactly as a pair, and the low parts add without cancellation.
+__device__ __forceinline__ df2 one_minus(df2 r) {
+  const df2 s = fast_two_sum(1.0f, -r.hi);
+  return fast_two_sum(s.hi, s.lo - r.lo);
 }
 
-// Operands the double-float path represents without overflow or loss of
-// its low part; pairs with any other operand use the FP64 terms below.
-__device__ __forceinline__ bool df_safe(double v) { return v == 0.0 || (v >= 0x1p-60 && v <= 0x1p60); }
-__device__ __forceinline__ bool df_safe_grad(double g) { return fabs(g) < 0x1p100; }
+// Batches [begin, end) of kBatch columns that warp w of a block covers.
+struct BatchRange {
+  int64_t begin, end;
+};
+__device__ __forceinline__ BatchRange warp_batches(int64_t n, int w) {
+  const int64_t nb = (n + kBatch - 1) / kBatch;
+  const int64_t per = (nb + kPairWarps - 1) / kPairWarps;
+  const int64_t b0 = per * w < nb ? per * w : nb;
+  return {b0, b0 + per < nb ? b0 + per : nb};
+}
+
+// ---- forward -----------------------------------------------------------------------
 
 // FP64 terms of one pair (the same expressions, for out-of-range operands).
 __device__ __noinline__ void pair_fwd_fp64(int model, double xi, double yi, double xj, double yj, double& p,
@@ -53,211 +116,396 @@ __device__ __noinline__ void pair_fwd_fp64(int model, double xi, double yi, doub
   m = p / omr;
 }
 
-__device__ __noinline__ void pair_bwd_fp64(int model, double xi, double yi, double xj, double yj, double gkk,
-                                           double gss, double& dx, double& dy) {
+// Double-float terms; c = (a_j, y_j) as staged (x_j for the UBCM).
+template <int kModel>
+__device__ __forceinline__ void fwd_term(df2 ai, df2 yi, float4 c, df2& p, df2& m) {
+  const df2 prod = df_mul(ai, df2{c.x, c.y});
+  if (kModel == MH_UBCM) {
+    p = df_div(prod, df_add_f(prod, 1.0f));
+    return;
+  }
+  const df2 omr = one_minus(df_mul(yi, df2{c.z, c.w}));
+  p = df_div(prod, df_add_sloppy(omr, prod));  // both >= 0
+  m = df_div(p, omr);
+}
+
+template <int kModel>
+__global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const double* __restrict__ x,
+                                                                        const double* __restrict__ y, int64_t n,
+                                                                        double* __restrict__ k_out,
+                                                                        double* __restrict__ s_out) {
+  constexpr bool kW = kModel == MH_UECM;
+  __shared__ float4 stage[kPairWarps][kBatch];
+  __shared__ double part[2][kPairWarps][kGroupRows];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const BatchRange br = warp_batches(n, warp);
+  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t row0 = g * kGroupRows;
+    df2 ai[kLaneRows], yi[kLaneRows];
+    bool rok[kLaneRows];
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) {
+      const int64_t i = row0 + 32 * q + lane;
+      ai[q] = df2{0.0f, 0.0f};
+      yi[q] = df2{0.0f, 0.0f};
+      rok[q] = true;  // rows past n compute zero terms and are not stored
+      if (i < n) {
+        const double av = kW ? x[i] * y[i] : x[i];
+        ai[q] = df_from_double(av);
+        rok[q] = df_safe_a(av);
+        if (kW) {
+          yi[q] = df_from_double(y[i]);
+          rok[q] = rok[q] && df_safe_y(y[i]);
+        }
+      }
+    }
+    const bool rows_ok = __all_sync(kFull, rok[0] && rok[1]);
+    double k_tot[kLaneRows] = {0.0, 0.0}, s_tot[kLaneRows] = {0.0, 0.0};
+    for (int64_t b = br.begin; b < br.end; ++b) {
+      const int64_t c0 = b * kBatch;
+      const int64_t jl = c0 + lane;
+      bool ok = true;
+      if (jl < n) {
+        const double av = kW ? x[jl] * y[jl] : x[jl];
+        const df2 a = df_from_double(av);
+        float4 v = make_float4(a.hi, a.lo, 0.0f, 0.0f);
+        ok = df_safe_a(av);
+        if (kW) {
+          const df2 w = df_from_double(y[jl]);
+          v.z = w.hi;
+          v.w = w.lo;
+          ok = ok && df_safe_y(y[jl]);
+        }
+        stage[warp][lane] = v;
+      }
+      const unsigned okmask = __ballot_sync(kFull, ok);
+      __syncwarp();
+      const int m = n - c0 < kBatch ? static_cast<int>(n - c0) : kBatch;
+      const bool own_rows = c0 >= row0 && c0 < row0 + kGroupRows;
+      DfAcc ka[kLaneRows], sa[kLaneRows];
+      if (rows_ok && okmask == kFull && m == kBatch && !own_rows) {
+#pragma unroll 1
+        for (int t0 = 0; t0 < kBatch; t0 += kNormEvery) {
+#pragma unroll 2
+          for (int u = 0; u < kNormEvery; ++u) {
+            const float4 c = stage[warp][t0 + u];
+#pragma unroll
+            for (int q = 0; q < kLaneRows; ++q) {
+              df2 p, mm;
+              fwd_term<kModel>(ai[q], yi[q], c, p, mm);
+              ka[q].add(p);
+              if (kW) sa[q].add(mm);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kLaneRows; ++q) {
+            ka[q].norm();
+            if (kW) sa[q].norm();
+          }
+        }
+      } else {
+        for (int t = 0; t < m; ++t) {
+          const int64_t j = c0 + t;
+          const float4 c = stage[warp][t];
+          const bool jok = (okmask >> t) & 1u;
+#pragma unroll
+          for (int q = 0; q < kLaneRows; ++q) {
+            const int64_t i = row0 + 32 * q + lane;
+            if (i >= n || i == j) continue;
+            if (rok[q] && jok) {
+              df2 p, mm;
+              fwd_term<kModel>(ai[q], yi[q], c, p, mm);
+              ka[q].add(p);
+              if (kW) sa[q].add(mm);
+            } else {
+              double p, mm;
+              pair_fwd_fp64(kModel, x[i], kW ? y[i] : 0.0, x[j], kW ? y[j] : 0.0, p, mm);
+              k_tot[q] += p;
+              if (kW) s_tot[q] += mm;
+            }
+          }
+          if ((t % kNormEvery) == kNormEvery - 1) {
+#pragma unroll
+            for (int q = 0; q < kLaneRows; ++q) {
+              ka[q].norm();
+              if (kW) sa[q].norm();
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kLaneRows; ++q) {
+        k_tot[q] += ka[q].value();
+        if (kW) s_tot[q] += sa[q].value();
+      }
+      __syncwarp();  // the next batch overwrites stage[warp]
+    }
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) {
+      part[0][warp][32 * q + lane] = k_tot[q];
+      if (kW) part[1][warp][32 * q + lane] = s_tot[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kGroupRows) {
+      const int r = threadIdx.x;
+      double k = 0.0, s = 0.0;
+      for (int w = 0; w < kPairWarps; ++w) {
+        k += part[0][w][r];
+        if (kW) s += part[1][w][r];
+      }
+      const int64_t i = row0 + r;
+      if (i < n) {
+        k_out[i] = k;
+        if (kW) s_out[i] = s;
+      }
+    }
+    __syncthreads();  // part[] is rewritten by the next group
+  }
+}
+
+// ---- backward ----------------------------------------------------------------------
+
+// FP64 terms of one pair without the row factor (y_i for x, x_i for y).
+__device__ __noinline__ void pair_bwd_fp64(int model, double xi, double yi, double xj, double yj, double gk,
+                                           double gs, double& tx, double& ty) {
   if (model == MH_UBCM) {
     const double opz = 1.0 + xi * xj;
-    dx = gkk * (xj / (opz * opz));
-    dy = 0.0;
+    tx = gk * (xj / (opz * opz));
+    ty = 0.0;
     return;
   }
   const double aj = xj * yj;
-  const double A = (xi * yi) * aj;
-  const double omr = 1.0 - yi * yj;
-  const double D = omr + A;
-  const double D2 = D * D;
-  const double p = A / D;
-  dx = gkk * (yi * aj * omr / D2) + gss * (yi * aj / D2);
-  dy = gkk * (xi * aj / D2) + gss * (xi * aj / (D2 * omr) + p * yj / (omr * omr));
+  const double r = yi * yj;
+  const double omr = 1.0 - r;
+  const double D = omr + (xi * yi) * aj;
+  const double Q = aj / (D * D);
+  tx = Q * (gk * omr + gs);
+  ty = Q * (gk + gs * ((omr + r * D) / (omr * omr)));
 }
 
-// 1 - y_i y_j in double-float (exact product of the high parts by FMA).
-__device__ __forceinline__ df2 one_minus_prod(df2 yi, df2 yj) {
-  const df2 r = df_mul(yi, yj);
-  return df_add(df2{1.0f, 0.0f}, df2{-r.hi, -r.lo});
+// Double-float row state: UBCM v = x_i, UECM v = a_i (and y_i); gradients g_k,i, g_s,i.
+struct BwdRow {
+  df2 v, y, gk, gs;
+};
+
+// Double-float terms.  Staged columns: UBCM c0 = (x_j, g_k,j); UECM c0 = (a_j, y_j),
+// c1 = (g_k,j, g_s,j).  Mixed-sign sums use the sloppy addition: its error is a
+// few 2^-48 of the sum of the operands' magnitudes.
+template <int kModel>
+__device__ __forceinline__ void bwd_term(const BwdRow& R, float4 c0, float4 c1, df2& tx, df2& ty) {
+  if (kModel == MH_UBCM) {
+    const df2 xj{c0.x, c0.y};
+    const df2 opz = df_add_f(df_mul(R.v, xj), 1.0f);
+    const df2 gk = df_add_sloppy(R.gk, df2{c0.z, c0.w});
+    tx = df_mul(gk, df_div(xj, df_mul(opz, opz)));
+    return;
+  }
+  const df2 aj{c0.x, c0.y};
+  const df2 r = df_mul(R.y, df2{c0.z, c0.w});
+  const df2 omr = one_minus(r);
+  const df2 D = df_add_sloppy(omr, df_mul(R.v, aj));  // both >= 0
+  const df2 Q = df_div(aj, df_mul(D, D));
+  const df2 gk = df_add_sloppy(R.gk, df2{c1.x, c1.y});
+  const df2 gs = df_add_sloppy(R.gs, df2{c1.z, c1.w});
+  tx = df_mul(df_add_sloppy(df_mul(gk, omr), gs), Q);
+  const df2 fr = df_div(df_add_sloppy(omr, df_mul(r, D)), df_mul(omr, omr));  // (1 - r + r D) / (1 - r)^2
+  ty = df_mul(df_add_sloppy(gk, df_mul(gs, fr)), Q);
 }
 
 template <int kModel>
-__global__ void __launch_bounds__(kPairThreads) expected_fwd_kernel(const double* __restrict__ x,
-                                                                     const double* __restrict__ y, int64_t n,
-                                                                     double* __restrict__ k_out,
-                                                                     double* __restrict__ s_out) {
-  __shared__ float2 sa[kPairThreads];  // x_j (UBCM) or a_j (UECM), double-float
-  __shared__ float2 sy[kPairThreads];
-  __shared__ bool sok[kPairThreads];
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * kPairThreads + threadIdx.x;
-  const bool row = i < n;
-  df2 ai{0.0f, 0.0f}, yi{0.0f, 0.0f};
-  double xi64 = 0.0, yi64 = 0.0;
-  bool iok = true;
-  if (row) {
-    xi64 = x[i];
-    if (kModel == MH_UECM) yi64 = y[i];
-    const double av = (kModel == MH_UBCM) ? xi64 : xi64 * yi64;
-    ai = df_from_double(av);
-    iok = df_safe(av);
-    if (kModel == MH_UECM) yi = df_from_double(yi64);
-  }
-  double k_tot = 0.0, s_tot = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += kPairThreads) {
-    const int64_t jl = j0 + threadIdx.x;
-    if (jl < n) {
-      const double av = (kModel == MH_UBCM) ? x[jl] : x[jl] * y[jl];
-      const df2 v = df_from_double(av);
-      sa[threadIdx.x] = make_float2(v.hi, v.lo);
-      sok[threadIdx.x] = df_safe(av);
-      if (kModel == MH_UECM) {
-        const df2 w = df_from_double(y[jl]);
-        sy[threadIdx.x] = make_float2(w.hi, w.lo);
+__global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const double* __restrict__ x,
+                                                                        const double* __restrict__ y, int64_t n,
+                                                                        const double* __restrict__ gk,
+                                                                        const double* __restrict__ gs,
+                                                                        double* __restrict__ gx,
+                                                                        double* __restrict__ gy) {
+  constexpr bool kW = kModel == MH_UECM;
+  __shared__ float4 stage0[kPairWarps][kBatch];
+  __shared__ float4 stage1[kW ? kPairWarps : 1][kBatch];
+  __shared__ double part[2][kPairWarps][kGroupRows];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const BatchRange br = warp_batches(n, warp);
+  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t row0 = g * kGroupRows;
+    BwdRow R[kLaneRows];
+    bool rok[kLaneRows];
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) {
+      const int64_t i = row0 + 32 * q + lane;
+      const df2 zero{0.0f, 0.0f};
+      R[q] = BwdRow{zero, zero, zero, zero};
+      rok[q] = true;  // rows past n compute zero terms and are not stored
+      if (i < n) {
+        const double v = kW ? x[i] * y[i] : x[i];
+        R[q].v = df_from_double(v);
+        R[q].gk = df_from_double(gk[i]);
+        rok[q] = df_safe_a(v) && df_safe_g(gk[i]);
+        if (kW) {
+          R[q].y = df_from_double(y[i]);
+          R[q].gs = df_from_double(gs[i]);
+          rok[q] = rok[q] && df_safe_y(y[i]) && df_safe_g(gs[i]);
+        }
       }
     }
-    __syncthreads();
-    const int m = (n - j0) < kPairThreads ? static_cast<int>(n - j0) : kPairThreads;
-    df2 k_part{0.0f, 0.0f}, s_part{0.0f, 0.0f};
-    for (int t = 0; t < m; ++t) {
-      if (j0 + t == i) continue;
-      if (!(iok && sok[t])) {
-        double p, mm;
-        pair_fwd_fp64(kModel, xi64, yi64, x[j0 + t], kModel == MH_UECM ? y[j0 + t] : 0.0, p, mm);
-        k_part = df_add(k_part, df_from_double(p));
-        if (kModel == MH_UECM) s_part = df_add(s_part, df_from_double(mm));
-        continue;
+    const bool rows_ok = __all_sync(kFull, rok[0] && rok[1]);
+    double x_tot[kLaneRows] = {0.0, 0.0}, y_tot[kLaneRows] = {0.0, 0.0};
+    for (int64_t b = br.begin; b < br.end; ++b) {
+      const int64_t c0 = b * kBatch;
+      const int64_t jl = c0 + lane;
+      bool ok = true;
+      if (jl < n) {
+        const double v = kW ? x[jl] * y[jl] : x[jl];
+        const df2 a = df_from_double(v);
+        const df2 k = df_from_double(gk[jl]);
+        ok = df_safe_a(v) && df_safe_g(gk[jl]);
+        if (kW) {
+          const df2 w = df_from_double(y[jl]);
+          const df2 s = df_from_double(gs[jl]);
+          stage0[warp][lane] = make_float4(a.hi, a.lo, w.hi, w.lo);
+          stage1[warp][lane] = make_float4(k.hi, k.lo, s.hi, s.lo);
+          ok = ok && df_safe_y(y[jl]) && df_safe_g(gs[jl]);
+        } else {
+          stage0[warp][lane] = make_float4(a.hi, a.lo, k.hi, k.lo);
+        }
       }
-      const df2 prod = df_mul(ai, to_df(sa[t]));
-      if (kModel == MH_UBCM) {
-        k_part = df_add(k_part, df_div(prod, df_add_f(prod, 1.0f)));
+      const unsigned okmask = __ballot_sync(kFull, ok);
+      __syncwarp();
+      const int m = n - c0 < kBatch ? static_cast<int>(n - c0) : kBatch;
+      const bool own_rows = c0 >= row0 && c0 < row0 + kGroupRows;
+      DfAcc ax[kLaneRows], ay[kLaneRows];
+      if (rows_ok && okmask == kFull && m == kBatch && !own_rows) {
+#pragma unroll 1
+        for (int t0 = 0; t0 < kBatch; t0 += kNormEvery) {
+#pragma unroll 1
+          for (int u = 0; u < kNormEvery; ++u) {
+            const float4 s0 = stage0[warp][t0 + u];
+            const float4 s1 = kW ? stage1[warp][t0 + u] : s0;
+#pragma unroll
+            for (int q = 0; q < kLaneRows; ++q) {
+              df2 tx, ty;
+              bwd_term<kModel>(R[q], s0, s1, tx, ty);
+              ax[q].add(tx);
+              if (kW) ay[q].add(ty);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kLaneRows; ++q) {
+            ax[q].norm();
+            if (kW) ay[q].norm();
+          }
+        }
       } else {
-        const df2 omr = one_minus_prod(yi, to_df(sy[t]));
-        const df2 p = df_div(prod, df_add(omr, prod));
-        k_part = df_add(k_part, p);
-        s_part = df_add(s_part, df_div(p, omr));
+        for (int t = 0; t < m; ++t) {
+          const int64_t j = c0 + t;
+          const float4 s0 = stage0[warp][t];
+          const float4 s1 = kW ? stage1[warp][t] : s0;
+          const bool jok = (okmask >> t) & 1u;
+#pragma unroll
+          for (int q = 0; q < kLaneRows; ++q) {
+            const int64_t i = row0 + 32 * q + lane;
+            if (i >= n || i == j) continue;
+            if (rok[q] && jok) {
+              df2 tx, ty;
+              bwd_term<kModel>(R[q], s0, s1, tx, ty);
+              ax[q].add(tx);
+              if (kW) ay[q].add(ty);
+            } else {
+              double tx, ty;
+              pair_bwd_fp64(kModel, x[i], kW ? y[i] : 0.0, x[j], kW ? y[j] : 0.0, gk[i] + gk[j],
+                            kW ? gs[i] + gs[j] : 0.0, tx, ty);
+              x_tot[q] += tx;
+              if (kW) y_tot[q] += ty;
+            }
+          }
+          if ((t % kNormEvery) == kNormEvery - 1) {
+#pragma unroll
+            for (int q = 0; q < kLaneRows; ++q) {
+              ax[q].norm();
+              if (kW) ay[q].norm();
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kLaneRows; ++q) {
+        x_tot[q] += ax[q].value();
+        if (kW) y_tot[q] += ay[q].value();
+      }
+      __syncwarp();  // the next batch overwrites stage0/stage1[warp]
+    }
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) {
+      part[0][warp][32 * q + lane] = x_tot[q];
+      if (kW) part[1][warp][32 * q + lane] = y_tot[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kGroupRows) {
+      const int r = threadIdx.x;
+      double sx = 0.0, sy = 0.0;
+      for (int w = 0; w < kPairWarps; ++w) {
+        sx += part[0][w][r];
+        if (kW) sy += part[1][w][r];
+      }
+      const int64_t i = row0 + r;
+      if (i < n) {
+        gx[i] = kW ? y[i] * sx : sx;
+        if (kW) gy[i] = x[i] * sy;
       }
     }
-    k_tot += df_to_double(k_part);
-    if (kModel == MH_UECM) s_tot += df_to_double(s_part);
-    __syncthreads();
-  }
-  if (row) {
-    k_out[i] = k_tot;
-    if (kModel == MH_UECM) s_out[i] = s_tot;
+    __syncthreads();  // part[] is rewritten by the next group
   }
 }
 
-template <int kModel>
-__global__ void __launch_bounds__(kPairThreads) expected_bwd_kernel(const double* __restrict__ x,
-                                                                     const double* __restrict__ y, int64_t n,
-                                                                     const double* __restrict__ gk,
-                                                                     const double* __restrict__ gs,
-                                                                     double* __restrict__ gx,
-                                                                     double* __restrict__ gy) {
-  __shared__ float2 sx[kPairThreads];
-  __shared__ float2 sy[kPairThreads];
-  __shared__ float2 sgk[kPairThreads];
-  __shared__ float2 sgs[kPairThreads];
-  __shared__ bool sok[kPairThreads];
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * kPairThreads + threadIdx.x;
-  const bool row = i < n;
-  df2 xi{0.0f, 0.0f}, yi{0.0f, 0.0f}, gki{0.0f, 0.0f}, gsi{0.0f, 0.0f};
-  double xi64 = 0.0, yi64 = 0.0, gki64 = 0.0, gsi64 = 0.0;
-  bool iok = true;
-  if (row) {
-    xi64 = x[i];
-    gki64 = gk[i];
-    xi = df_from_double(xi64);
-    gki = df_from_double(gki64);
-    iok = df_safe(xi64) && df_safe_grad(gki64);
-    if (kModel == MH_UECM) {
-      yi64 = y[i];
-      gsi64 = gs[i];
-      yi = df_from_double(yi64);
-      gsi = df_from_double(gsi64);
-      iok = iok && df_safe(xi64 * yi64) && df_safe_grad(gsi64);
+// Persistent grid: resident blocks per SM (queried once per device and
+// kernel) times the SM count, at most one block per row group.
+template <typename Kernel>
+unsigned pair_grid(Kernel kernel, int* cache, int64_t n) {
+  int dev = 0;
+  int per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    if (cache[dev] == 0) {
+      int v = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kPairThreads, 0) != cudaSuccess || v < 1) v = 1;
+      cache[dev] = v;
     }
+    per_sm = cache[dev];
   }
-  const df2 ai = df_mul(xi, yi);
-  double gx_tot = 0.0, gy_tot = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += kPairThreads) {
-    const int64_t jl = j0 + threadIdx.x;
-    if (jl < n) {
-      df2 v = df_from_double(x[jl]);
-      sx[threadIdx.x] = make_float2(v.hi, v.lo);
-      sok[threadIdx.x] = df_safe(x[jl]) && df_safe_grad(gk[jl]) &&
-                         (kModel == MH_UBCM || (df_safe(x[jl] * y[jl]) && df_safe_grad(gs[jl])));
-      v = df_from_double(gk[jl]);
-      sgk[threadIdx.x] = make_float2(v.hi, v.lo);
-      if (kModel == MH_UECM) {
-        v = df_from_double(y[jl]);
-        sy[threadIdx.x] = make_float2(v.hi, v.lo);
-        v = df_from_double(gs[jl]);
-        sgs[threadIdx.x] = make_float2(v.hi, v.lo);
-      }
-    }
-    __syncthreads();
-    const int m = (n - j0) < kPairThreads ? static_cast<int>(n - j0) : kPairThreads;
-    df2 gx_part{0.0f, 0.0f}, gy_part{0.0f, 0.0f};
-    for (int t = 0; t < m; ++t) {
-      if (j0 + t == i) continue;
-      if (!(iok && sok[t])) {
-        double dx, dy;
-        const double yj64 = kModel == MH_UECM ? y[j0 + t] : 0.0;
-        const double gss64 = kModel == MH_UECM ? gsi64 + gs[j0 + t] : 0.0;
-        pair_bwd_fp64(kModel, xi64, yi64, x[j0 + t], yj64, gki64 + gk[j0 + t], gss64, dx, dy);
-        gx_part = df_add(gx_part, df_from_double(dx));
-        if (kModel == MH_UECM) gy_part = df_add(gy_part, df_from_double(dy));
-        continue;
-      }
-      const df2 gkk = df_add(gki, to_df(sgk[t]));
-      const df2 xj = to_df(sx[t]);
-      if (kModel == MH_UBCM) {
-        const df2 opz = df_add_f(df_mul(xi, xj), 1.0f);
-        gx_part = df_add(gx_part, df_mul(gkk, df_div(xj, df_mul(opz, opz))));
-      } else {
-        const df2 yj = to_df(sy[t]);
-        const df2 aj = df_mul(xj, yj);
-        const df2 A = df_mul(ai, aj);
-        const df2 omr = one_minus_prod(yi, yj);
-        const df2 D = df_add(omr, A);
-        const df2 D2 = df_mul(D, D);
-        const df2 p = df_div(A, D);
-        const df2 gss = df_add(gsi, to_df(sgs[t]));
-        const df2 yaj = df_div(df_mul(yi, aj), D2);  // y_i a_j / D^2 = dm/dx_i
-        const df2 xaj = df_div(df_mul(xi, aj), D2);  // x_i a_j / D^2 = dp/dy_i
-        // dp/dx_i = (1 - r) dm/dx_i;  dm/dy_i = dp/dy_i / (1 - r) + p y_j / (1 - r)^2
-        gx_part = df_add(gx_part, df_mul(df_add(df_mul(gkk, omr), gss), yaj));
-        const df2 dmdy = df_add(df_div(xaj, omr), df_div(df_mul(p, yj), df_mul(omr, omr)));
-        gy_part = df_add(gy_part, df_add(df_mul(gkk, xaj), df_mul(gss, dmdy)));
-      }
-    }
-    gx_tot += df_to_double(gx_part);
-    if (kModel == MH_UECM) gy_tot += df_to_double(gy_part);
-    __syncthreads();
-  }
-  if (row) {
-    gx[i] = gx_tot;
-    if (kModel == MH_UECM) gy[i] = gy_tot;
-  }
+  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * per_sm;
+  return static_cast<unsigned>(std::min(groups, cap));
 }
+
+int g_occ_fwd[2][64];
+int g_occ_bwd[2][64];
 
 }  // namespace
 
 cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k, double* s,
                                 cudaStream_t st) {
-  const unsigned blocks = grid_for(n, kPairThreads);
-  if (model == MH_UBCM)
+  if (model == MH_UBCM) {
+    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UBCM>, g_occ_fwd[0], n);
     expected_fwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, k, s);
-  else
+  } else {
+    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UECM>, g_occ_fwd[1], n);
     expected_fwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, k, s);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* gk,
                                 const double* gs, double* gx, double* gy, cudaStream_t st) {
-  const unsigned blocks = grid_for(n, kPairThreads);
-  if (model == MH_UBCM)
+  if (model == MH_UBCM) {
+    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UBCM>, g_occ_bwd[0], n);
     expected_bwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, gk, gs, gx, gy);
-  else
+  } else {
+    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UECM>, g_occ_bwd[1], n);
     expected_bwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, gk, gs, gx, gy);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
