@@ -367,12 +367,10 @@ PAIR_OPS = {"fwd": 81, "bwd": 185}
 FP32_LANES_PER_SM = 128
 
 
-def pairwise_leg(args, dev, sm_mhz):
+def pairwise_inputs(dev):
+    """Heavy-tailed x (log-normal), y ~ U(0.3, 0.9) and standard normal
+    gradients for the pairwise leg (seeded)."""
     import torch
-
-    from paper_2509_13230_gb300 import _native as nat
-    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
-
     rng = np.random.default_rng(11)
     x_np = np.exp(rng.normal(-5.5, 1.3, PAIR_N))
     y_np = rng.uniform(0.3, 0.9, PAIR_N)
@@ -380,6 +378,40 @@ def pairwise_leg(args, dev, sm_mhz):
     y = torch.from_numpy(y_np).to(dev)
     gk = torch.from_numpy(rng.normal(size=PAIR_N)).to(dev)
     gs = torch.from_numpy(rng.normal(size=PAIR_N)).to(dev)
+    return rng, x_np, y_np, x, y, gk, gs
+
+
+def kernels_once(dev):
+    """Each profiled kernel once, untimed, for ncu captures: the headline call
+    (10 samples of the weighted N = 20,000 workload) at segment lengths 8, 16
+    and 32 (three walk launches, in that order), then the UECM pairwise
+    forward and backward at N = 200,000 (one launch each)."""
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.sampler import Sampler, expected_bwd, expected_fwd
+
+    net = workload()
+    x = torch.from_numpy(net.x).to(dev)
+    y = torch.from_numpy(net.y).to(dev)
+    edges = {}
+    for T in (8, 16, 32):
+        res = Sampler(nat.MH_UECM, x, y, num_samples=SAMPLES_PER_STEP, seg_target=T).run()
+        edges[T] = res.total
+    _, _, _, px, py, gk, gs = pairwise_inputs(dev)
+    expected_fwd(nat.MH_UECM, px, py)
+    expected_bwd(nat.MH_UECM, px, py, gk, gs)
+    torch.cuda.synchronize()
+    return {"workload": WORKLOAD, "edges_by_seg_target": edges, "pairwise_n": PAIR_N}
+
+
+def pairwise_leg(args, dev, sm_mhz):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
+
+    rng, x_np, y_np, x, y, gk, gs = pairwise_inputs(dev)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
@@ -911,8 +943,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs"], default="all",
-                    help="ensemble: run only the batched ensemble leg and print its object")
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs", "kernels"],
+                    default="all",
+                    help="run only that leg and print its object; kernels: each profiled kernel once, "
+                         "untimed (walk at T = 8, 16, 32, then pairwise forward and backward), for ncu")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--seg-target", type=int, default=0,
                     help="headline call: use this seg_target instead of tuning (profiling runs)")
@@ -963,6 +997,10 @@ def main():
         dev = torch.device("cuda", local_rank)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps({"bipartite": bipartite_leg(args, dev, flush)}), flush=True)
+    elif args.leg == "kernels":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"kernels_once": kernels_once(torch.device("cuda", local_rank))}), flush=True)
     elif args.leg == "pairwise":
         import torch
         torch.cuda.set_device(local_rank)
