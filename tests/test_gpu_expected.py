@@ -42,6 +42,45 @@ def test_out_of_range_operands_take_the_fp64_terms(model):
 
 
 @pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_double_float_range_boundaries(model):
+    """Operands on both sides of the double-float range: a (x for the UBCM,
+    x y for the UECM) at 2^-30 and 2^30, y at 1 - 2^-12, gradients at 2^40.
+    Pairs outside it take the FP64 terms; every sum stays within 1e-10 of
+    the oracle's."""
+    rng = np.random.default_rng(21)
+    n = 600
+    x = np.exp(rng.normal(-1.0, 1.0, n))
+    y = rng.uniform(0.2, 0.9, n) if model == nat.MH_UECM else None
+    a_edges = np.array([2.0**-31, 2.0**-30, 2.0**-29, 2.0**29, 2.0**30, 2.0**31])
+    if y is not None:
+        y[:6] = 0.5
+        x[:6] = a_edges / 0.5  # a = x y exactly at and around the bounds
+        y[6:10] = [1 - 2.0**-11, 1 - 2.0**-12, 1 - 2.0**-13, 1 - 2.0**-20]
+    else:
+        x[:6] = a_edges
+    k, s = expected_fwd(model, dev(x), None if y is None else dev(y))
+    rk, rs = oracle.expected_fwd(model, x, y)
+    np.testing.assert_allclose(k.cpu().numpy(), rk, rtol=1e-10)
+    if y is not None:
+        np.testing.assert_allclose(s.cpu().numpy(), rs, rtol=1e-10)
+    gk = rng.normal(size=n)
+    gk[10:14] = [2.0**40, -(2.0**40), 2.0**41, -(2.0**41)]
+    gs = None
+    if y is not None:
+        gs = rng.normal(size=n)
+        gs[14:18] = [2.0**40, -(2.0**40), 2.0**41, -(2.0**41)]
+    # rows with a >= 2^20 are left out: there p is within 2^-20 of 1 for most
+    # pairs and the oracle's closed forms p (1 - p) / x_i lose digits in 1 - p
+    a = x * y if y is not None else x
+    keep = np.flatnonzero(a < 2.0**20)
+    gx, gy = expected_bwd(model, dev(x), None if y is None else dev(y), dev(gk), None if gs is None else dev(gs))
+    rgx, rgy = oracle.expected_bwd(model, x, y, gk, gs, rows=keep)
+    np.testing.assert_allclose(gx.cpu().numpy()[keep], rgx, rtol=1e-10, atol=1e-12 * np.abs(rgx).max())
+    if y is not None:
+        np.testing.assert_allclose(gy.cpu().numpy()[keep], rgy, rtol=1e-10, atol=1e-12 * np.abs(rgy).max())
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
 def test_autograd_function_gradcheck(model):
     # The forward is accurate to about 2^-45 relative (double-float terms), so
     # the finite-difference step is 1e-5: truncation and rounding noise both
