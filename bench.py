@@ -827,14 +827,25 @@ def run_ours(args, rank, world, local_rank):
         loop_ms += ev0.elapsed_time(ev1)
     loop_value = loop_edges / (loop_ms / 1e3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: x, y copied in from
+    # pinned host memory before every call, the edges copied back after it
     hx = torch.from_numpy(net.x).pin_memory()
     hy = torch.from_numpy(net.y).pin_memory()
+    e2e_flags = s.flags & ~nat.MH_TIMING
     cap = s.capacity
-    hsrc = torch.empty(cap, dtype=torch.int32).pin_memory()
-    hdst = torch.empty(cap, dtype=torch.int32).pin_memory()
-    hw = torch.empty(cap, dtype=torch.int32).pin_memory()
-    e2e_ms, e2e_edges, d2h = 0.0, 0, 0
+    d2h_step = None
+
+    def host_out():
+        return [torch.empty(cap, dtype=torch.int32).pin_memory() for _ in range(3)]
+
+    def copy_back(smp, hb, m):
+        for h, d in zip(hb, (smp.src, smp.dst, smp.w)):
+            h[:m].copy_(d[:m], non_blocking=True)
+
+    # serial: copy in, call, copy back, one step after another
+    s.flags = e2e_flags
+    hb = host_out()
+    ser_ms, ser_edges = 0.0, 0
     for it in range(args.warmup + args.steps):
         flush.zero_()
         ev0.record(stream)
@@ -842,16 +853,63 @@ def run_ours(args, rank, world, local_rank):
         y.copy_(hy, non_blocking=True)
         nat.check(s.call(), "mh_sample_weighted")
         m = int(s.h_counts.sum())
-        hsrc[:m].copy_(s.src[:m], non_blocking=True)
-        hdst[:m].copy_(s.dst[:m], non_blocking=True)
-        hw[:m].copy_(s.w[:m], non_blocking=True)
+        copy_back(s, hb, m)
         ev1.record(stream)
         ev1.synchronize()
         if it >= args.warmup:
-            e2e_ms += ev0.elapsed_time(ev1)
-            e2e_edges += m
-            d2h += 12 * m + 8 * SAMPLES_PER_STEP
-    e2e_value = e2e_edges / (e2e_ms / 1e3)
+            ser_ms += ev0.elapsed_time(ev1)
+            ser_edges += m
+            d2h_step = 12 * m + 8 * SAMPLES_PER_STEP
+    ser_value = ser_edges / (ser_ms / 1e3)
+
+    # pipelined: two samplers with their own inputs and outputs alternate; the
+    # results of step t go back on a second stream while step t + 1 runs.
+    # Step t's window opens after the L2 flush (no copy in flight: the flush
+    # waits for step t - 2's copy-back, the last one that could be) and closes
+    # when both its call and step t - 1's copy-back are done, so each timed
+    # window holds one copy-in, one call and one equal-sized copy-back.
+    xb, yb = torch.empty_like(x), torch.empty_like(y)
+    sb = Sampler(nat.MH_UECM, xb, yb, num_samples=SAMPLES_PER_STEP, sample_begin=first, seg_target=T,
+                 walk_ctas_per_sm=ctas, capacity=cap)
+    sb.flags = e2e_flags
+    pairs = [(s, x, y, hb), (sb, xb, yb, host_out())]
+    back = torch.cuda.Stream(device=dev)
+    n_it = args.warmup + args.steps
+    back_done = [None] * n_it
+    pipe_ms, pipe_edges, m_prev = 0.0, 0, 0
+    for it in range(n_it):
+        smp, xi, yi, _ = pairs[it & 1]
+        if it >= 2:
+            stream.wait_event(back_done[it - 2])
+        flush.zero_()
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        if it >= 1:
+            prev = pairs[(it - 1) & 1]
+            back.wait_event(start)
+            with torch.cuda.stream(back):
+                copy_back(prev[0], prev[3], m_prev)
+            back_done[it - 1] = torch.cuda.Event(enable_timing=True)
+            back_done[it - 1].record(back)
+        xi.copy_(hx, non_blocking=True)
+        yi.copy_(hy, non_blocking=True)
+        nat.check(smp.call(), "mh_sample_weighted")
+        m_prev = int(smp.h_counts.sum())
+        called = torch.cuda.Event(enable_timing=True)
+        called.record(stream)
+        called.synchronize()
+        if it >= 1:
+            back_done[it - 1].synchronize()
+        if it >= args.warmup:
+            win = start.elapsed_time(called)
+            if it >= 1:
+                win = max(win, start.elapsed_time(back_done[it - 1]))
+            pipe_ms += win
+            pipe_edges += m_prev
+    copy_back(*[pairs[(n_it - 1) & 1][q] for q in (0, 3)], m_prev)  # last results, untimed
+    torch.cuda.synchronize()
+    s.flags = e2e_flags | nat.MH_TIMING
+    e2e_value = pipe_edges / (pipe_ms / 1e3)
     ensemble = ensemble_lognormal = None
     if world == 1 and not args.no_ensemble:
         ensemble = ensemble_leg(args, dev, flush)
@@ -917,7 +975,12 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline_all_cores": cpu_all,
         "cpu_brute_force": cpu_bf,
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 16 * net.n,
-                "d2h_bytes_per_step": d2h // args.steps},
+                "d2h_bytes_per_step": d2h_step,
+                "copies": "x, y host-to-device before each call on its stream; the edges device-to-host on a "
+                          "second stream during the next call (two samplers, double-buffered); L2 flushed "
+                          "between steps with no copy in flight",
+                "serial": {"value": ser_value, "unit": "edges/s",
+                           "copies": "copy in, call, copy back, one step after another"}},
         "gpu_launches": launches,
         "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit", "call"),
                                        (float(v) for v in np.mean(np.array(phases), axis=0)))),
