@@ -862,25 +862,32 @@ def run_ours(args, rank, world, local_rank):
             d2h_step = 12 * m + 8 * SAMPLES_PER_STEP
     ser_value = ser_edges / (ser_ms / 1e3)
 
-    # pipelined: two samplers with their own inputs and outputs alternate; the
-    # results of step t go back on a second stream while step t + 1 runs.
-    # Step t's window opens after the L2 flush (no copy in flight: the flush
-    # waits for step t - 2's copy-back, the last one that could be) and closes
-    # when both its call and step t - 1's copy-back are done, so each timed
-    # window holds one copy-in, one call and one equal-sized copy-back.
+    # pipelined: two samplers with their own inputs and outputs alternate; while
+    # step t runs, the results of step t - 1 go back on one copy stream and
+    # the inputs of step t + 1 come in on another.  Step t's window opens after
+    # the L2 flush (no copy in flight: the flush waits for both copy streams)
+    # and closes when its call and both copies are done, so each timed window
+    # holds one copy-in, one call and one equal-sized copy-back.
     xb, yb = torch.empty_like(x), torch.empty_like(y)
     sb = Sampler(nat.MH_UECM, xb, yb, num_samples=SAMPLES_PER_STEP, sample_begin=first, seg_target=T,
                  walk_ctas_per_sm=ctas, capacity=cap)
     sb.flags = e2e_flags
     pairs = [(s, x, y, hb), (sb, xb, yb, host_out())]
     back = torch.cuda.Stream(device=dev)
+    ahead = torch.cuda.Stream(device=dev)
     n_it = args.warmup + args.steps
     back_done = [None] * n_it
+    in_ready = [None] * (n_it + 1)
     pipe_ms, pipe_edges, m_prev = 0.0, 0, 0
+    parts = {"call": 0.0, "copy_back": 0.0, "copy_in": 0.0}
+    x.copy_(hx, non_blocking=True)  # inputs of step 0
+    y.copy_(hy, non_blocking=True)
     for it in range(n_it):
-        smp, xi, yi, _ = pairs[it & 1]
+        smp = pairs[it & 1][0]
         if it >= 2:
             stream.wait_event(back_done[it - 2])
+        if in_ready[it] is not None:
+            stream.wait_event(in_ready[it])
         flush.zero_()
         start = torch.cuda.Event(enable_timing=True)
         start.record(stream)
@@ -891,25 +898,36 @@ def run_ours(args, rank, world, local_rank):
                 copy_back(prev[0], prev[3], m_prev)
             back_done[it - 1] = torch.cuda.Event(enable_timing=True)
             back_done[it - 1].record(back)
-        xi.copy_(hx, non_blocking=True)
-        yi.copy_(hy, non_blocking=True)
+        # the next step's sampler finished its last call (step t - 1) before this one began
+        nxt = pairs[(it + 1) & 1]
+        ahead.wait_event(start)
+        with torch.cuda.stream(ahead):
+            nxt[1].copy_(hx, non_blocking=True)
+            nxt[2].copy_(hy, non_blocking=True)
+        in_ready[it + 1] = torch.cuda.Event(enable_timing=True)
+        in_ready[it + 1].record(ahead)
         nat.check(smp.call(), "mh_sample_weighted")
         m_prev = int(smp.h_counts.sum())
         called = torch.cuda.Event(enable_timing=True)
         called.record(stream)
         called.synchronize()
+        in_ready[it + 1].synchronize()
         if it >= 1:
             back_done[it - 1].synchronize()
         if it >= args.warmup:
-            win = start.elapsed_time(called)
-            if it >= 1:
-                win = max(win, start.elapsed_time(back_done[it - 1]))
-            pipe_ms += win
+            t_call = start.elapsed_time(called)
+            t_in = start.elapsed_time(in_ready[it + 1])
+            t_back = start.elapsed_time(back_done[it - 1]) if it >= 1 else 0.0
+            pipe_ms += max(t_call, t_in, t_back)
             pipe_edges += m_prev
+            parts["call"] += t_call
+            parts["copy_back"] += t_back
+            parts["copy_in"] += t_in
     copy_back(*[pairs[(n_it - 1) & 1][q] for q in (0, 3)], m_prev)  # last results, untimed
     torch.cuda.synchronize()
     s.flags = e2e_flags | nat.MH_TIMING
     e2e_value = pipe_edges / (pipe_ms / 1e3)
+    e2e_parts = parts
     ensemble = ensemble_lognormal = None
     if world == 1 and not args.no_ensemble:
         ensemble = ensemble_leg(args, dev, flush)
@@ -976,9 +994,10 @@ def run_ours(args, rank, world, local_rank):
         "cpu_brute_force": cpu_bf,
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 16 * net.n,
                 "d2h_bytes_per_step": d2h_step,
-                "copies": "x, y host-to-device before each call on its stream; the edges device-to-host on a "
-                          "second stream during the next call (two samplers, double-buffered); L2 flushed "
-                          "between steps with no copy in flight",
+                "copies": "two samplers alternate (double-buffered inputs and outputs): during step t the "
+                          "edges of step t - 1 go device-to-host and x, y of step t + 1 host-to-device on two "
+                          "copy streams; L2 flushed between steps with no copy in flight",
+                "window_ms": {k: v / args.steps for k, v in e2e_parts.items()},
                 "serial": {"value": ser_value, "unit": "edges/s",
                            "copies": "copy in, call, copy back, one step after another"}},
         "gpu_launches": launches,
