@@ -598,6 +598,7 @@ def configs_leg(args, dev, flush):
 
     hbm_gbs, peak_kind = peaks()
     stream = torch.cuda.current_stream()
+    ubcm_bf_rate = None
     out = {}
     n1m = workloads.ubcm_pareto_n1m()
     cases = [("ubcm_n1k_x100", workloads.ubcm_n1k(), 100, "coo", 8, 0),
@@ -651,9 +652,16 @@ def configs_leg(args, dev, flush):
             bf_s = time.perf_counter() - t0
             bf = {"pairs_per_s": evals / bf_s, "seconds_per_sample": bf_s,
                   "mh_over_bf_speedup_cpu": bf_s / (mh_s / k)}
+            ubcm_bf_rate = evals / bf_s
         else:
+            # one brute-force sample evaluates every pair: extrapolated from the
+            # UBCM brute-force rate measured on the smaller network above
             pairs = net.n * (net.n - 1) / 2
-            bf = {"pairs": pairs, "note": "not run: one brute-force sample evaluates every pair"}
+            bf = {"pairs": pairs, "note": "not run: extrapolated at the brute-force pair rate of the UBCM "
+                                          "N = 1,000 network in this run"}
+            if ubcm_bf_rate:
+                bf["extrapolated_seconds_per_sample"] = pairs / ubcm_bf_rate
+                bf["mh_over_bf_speedup_cpu_extrapolated"] = (pairs / ubcm_bf_rate) / (mh_s / k)
         out[name] = {"value": edges / (total_ms / 1e3), "unit": "edges/s", "ms_per_step": total_ms / steps,
                      "samples_per_step": samples, "edges_per_step": edges // steps, "seg_target": T,
                      "output": f"{layout} ({bytes_per_edge} B/edge" + (f" + {bytes_per_node} B/node)" if
@@ -977,6 +985,13 @@ def run_ours(args, rank, world, local_rank):
                       "edges_per_s": (edges / args.steps / SAMPLES_PER_STEP) / bf_s,
                       "mh_over_bf_speedup_cpu": bf_s / (secs / nsamp), "kind": "oracle brute force",
                       "cores": 1}
+    if fitted is not None and cpu_bf is not None:
+        # config 5 brute force: N (N - 1) / 2 pairs per sample at the UECM pair
+        # rate measured on the headline network in this run
+        pairs5 = FIT_N * (FIT_N - 1) / 2
+        fitted["cpu_brute_force"] = {
+            "pairs": pairs5, "extrapolated_seconds_per_sample": pairs5 / cpu_bf["pairs_per_s"],
+            "note": "not run: extrapolated at the UECM brute-force pair rate of the N = 20,000 network"}
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
