@@ -353,6 +353,22 @@ int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, 
 int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* g_k,
                         const double* g_s, double* g_x, double* g_y, mh_stream_t stream);
 
+/*
+ * maxent_expected_fwd_rows / maxent_expected_bwd_rows — the same sums for the
+ * rows i in [row_begin, row_begin + row_count) only (every sum still runs over
+ * all j != i), so that ranks can share one call by rows with no reduction:
+ * x, y, g_k, g_s are FP64[n] as above (all rows' values are needed); k_out,
+ * s_out, g_x, g_y hold row_count values, entry r for row row_begin + r.  Each
+ * value equals, bit for bit, the one the whole call returns for that row.
+ * MH_ERR_ARG unless 0 <= row_begin, 0 <= row_count and row_begin + row_count
+ * <= n; row_count = 0 returns MH_OK without work.
+ */
+int maxent_expected_fwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                             int64_t row_count, double* k_out, double* s_out, mh_stream_t stream);
+int maxent_expected_bwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                             int64_t row_count, const double* g_k, const double* g_s, double* g_x, double* g_y,
+                             mh_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,8 @@ EXPORTED = (
     "mh_segment_table",
     "maxent_expected_fwd",
     "maxent_expected_bwd",
+    "maxent_expected_fwd_rows",
+    "maxent_expected_bwd_rows",
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
@@ -149,6 +151,10 @@ def load(path: str | None = None):
         lib.maxent_expected_fwd.restype = i32
         lib.maxent_expected_bwd.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_bwd.restype = i32
+        lib.maxent_expected_fwd_rows.argtypes = [i32, vp, vp, i64, i64, i64, vp, vp, vp]
+        lib.maxent_expected_fwd_rows.restype = i32
+        lib.maxent_expected_bwd_rows.argtypes = [i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+        lib.maxent_expected_bwd_rows.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
         lib.mh_bipartite_workspace_size.restype = i32
         lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
@@ -231,6 +237,14 @@ def maxent_expected_fwd(model, x, y, n, k_out, s_out, stream) -> int:
 
 def maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream) -> int:
     return load().maxent_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, stream)
+
+
+def maxent_expected_fwd_rows(model, x, y, n, row_begin, row_count, k_out, s_out, stream) -> int:
+    return load().maxent_expected_fwd_rows(model, x, y, n, row_begin, row_count, k_out, s_out, stream)
+
+
+def maxent_expected_bwd_rows(model, x, y, n, row_begin, row_count, g_k, g_s, g_x, g_y, stream) -> int:
+    return load().maxent_expected_bwd_rows(model, x, y, n, row_begin, row_count, g_k, g_s, g_x, g_y, stream)
 
 
 def mh_batch_workspace_size(h_nets, n_nets, params, max_wave_items, capacity_edges) -> int:

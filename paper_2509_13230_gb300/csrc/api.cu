@@ -848,26 +848,53 @@ int mh_segment_table(int model, const double* x, const double* y, int64_t n, con
   return MH_OK;
 }
 
-int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
-                        mh_stream_t stream) {
+int maxent_expected_fwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                             int64_t row_count, double* k_out, double* s_out, mh_stream_t stream) {
   if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !k_out ||
       (model == MH_UECM && (!y || !s_out))) {
     set_error("maxent_expected_fwd: bad model, n or pointer");
     return MH_ERR_ARG;
   }
-  MH_CUDA(launch_expected_fwd(model, x, y, n, k_out, s_out, reinterpret_cast<cudaStream_t>(stream)));
+  if (row_begin < 0 || row_count < 0 || row_begin > n || row_count > n - row_begin) {
+    set_error("maxent_expected_fwd_rows: rows [%lld, %lld + %lld) are not within [0, %lld)",
+              static_cast<long long>(row_begin), static_cast<long long>(row_begin),
+              static_cast<long long>(row_count), static_cast<long long>(n));
+    return MH_ERR_ARG;
+  }
+  if (row_count == 0) return MH_OK;
+  MH_CUDA(launch_expected_fwd(model, x, y, n, row_begin, row_count, k_out, s_out,
+                              reinterpret_cast<cudaStream_t>(stream)));
   return MH_OK;
 }
 
-int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* g_k,
-                        const double* g_s, double* g_x, double* g_y, mh_stream_t stream) {
+int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
+                        mh_stream_t stream) {
+  return maxent_expected_fwd_rows(model, x, y, n, 0, n, k_out, s_out, stream);
+}
+
+int maxent_expected_bwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                             int64_t row_count, const double* g_k, const double* g_s, double* g_x, double* g_y,
+                             mh_stream_t stream) {
   if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !g_k || !g_x ||
       (model == MH_UECM && (!y || !g_s || !g_y))) {
     set_error("maxent_expected_bwd: bad model, n or pointer");
     return MH_ERR_ARG;
   }
-  MH_CUDA(launch_expected_bwd(model, x, y, n, g_k, g_s, g_x, g_y, reinterpret_cast<cudaStream_t>(stream)));
+  if (row_begin < 0 || row_count < 0 || row_begin > n || row_count > n - row_begin) {
+    set_error("maxent_expected_bwd_rows: rows [%lld, %lld + %lld) are not within [0, %lld)",
+              static_cast<long long>(row_begin), static_cast<long long>(row_begin),
+              static_cast<long long>(row_count), static_cast<long long>(n));
+    return MH_ERR_ARG;
+  }
+  if (row_count == 0) return MH_OK;
+  MH_CUDA(launch_expected_bwd(model, x, y, n, row_begin, row_count, g_k, g_s, g_x, g_y,
+                              reinterpret_cast<cudaStream_t>(stream)));
   return MH_OK;
+}
+
+int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                        const double* g_s, double* g_x, double* g_y, mh_stream_t stream) {
+  return maxent_expected_bwd_rows(model, x, y, n, 0, n, g_k, g_s, g_x, g_y, stream);
 }
 
 }  // extern "C"

@@ -308,9 +308,12 @@ int enqueue_sample_direct(const Net& g, const Layout& L, char* ws, const mh_para
                           cudaStream_t s);
 int status_code(unsigned status, long long num_segments, int64_t max_segments);
 
-cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k, double* s,
+// Rows [row_begin, row_begin + rows) of the expected sums (outputs indexed from
+// row_begin); rows >= 1 and row_begin + rows <= n.
+cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                int64_t rows, double* k, double* s, cudaStream_t st);
+cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                int64_t rows, const double* gk, const double* gs, double* gx, double* gy,
                                 cudaStream_t st);
-cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* gk,
-                                const double* gs, double* gx, double* gy, cudaStream_t st);
 
 }  // namespace mh

@@ -7,13 +7,16 @@
 // (nothing of size N^2 is stored).
 //
 // Work decomposition.  A persistent grid (SM count x resident blocks) walks
-// groups of 64 rows; in a block of 16 warps every lane owns two rows of the
-// group and warp w sums them over the w-th sixteenth of the columns, staged 32
-// at a time in the warp's own shared memory.  The 16 partial sums of a row
-// are added in warp order by one thread, so results do not depend on the
-// grid or the timing.  Groups of 64 rows keep the tail of the grid at about
-// 1/40 of the work for N = 2*10^5 (one row per thread in blocks of 256 left
-// a second wave 29% full).
+// groups of 64 rows of the requested range [row_begin, row_begin + rows); in
+// a block of 16 warps every lane owns two rows of the group and warp w sums
+// them over the w-th sixteenth of the columns, staged 32 at a time in the
+// warp's own shared memory.  The 16 partial sums of a row are added in warp
+// order by one thread, so a row's result depends neither on the grid, the
+// timing nor the rows it shares a group with: a row range (one rank's share
+// of a sharded call) gives bit for bit the values of the whole call.  Groups
+// of 64 rows keep the tail of the grid at about 1/40 of the work for
+// N = 2*10^5 (one row per thread in blocks of 256 left a second wave 29%
+// full).
 //
 // Arithmetic.  FP64 runs at 1/64 of the FP32 rate on this GPU, so each pair
 // term is evaluated in double-float arithmetic (pairs of FP32 values, about
@@ -132,6 +135,7 @@ __device__ __forceinline__ void fwd_term(df2 ai, df2 yi, float4 c, df2& p, df2& 
 template <int kModel>
 __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const double* __restrict__ x,
                                                                         const double* __restrict__ y, int64_t n,
+                                                                        int64_t row_begin, int64_t rows,
                                                                         double* __restrict__ k_out,
                                                                         double* __restrict__ s_out) {
   constexpr bool kW = kModel == MH_UECM;
@@ -140,9 +144,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const BatchRange br = warp_batches(n, warp);
-  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  const int64_t row_end = row_begin + rows;  // <= n
+  const int64_t groups = (rows + kGroupRows - 1) / kGroupRows;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-    const int64_t row0 = g * kGroupRows;
+    const int64_t row0 = row_begin + g * kGroupRows;
     df2 ai[kLaneRows], yi[kLaneRows];
     bool rok[kLaneRows];
 #pragma unroll
@@ -150,8 +155,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
       const int64_t i = row0 + 32 * q + lane;
       ai[q] = df2{0.0f, 0.0f};
       yi[q] = df2{0.0f, 0.0f};
-      rok[q] = true;  // rows past n compute zero terms and are not stored
-      if (i < n) {
+      rok[q] = true;  // rows past the range compute zero terms and are not stored
+      if (i < row_end) {
         const double av = kW ? x[i] * y[i] : x[i];
         ai[q] = df_from_double(av);
         rok[q] = df_safe_a(av);
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
       const unsigned okmask = __ballot_sync(kFull, ok);
       __syncwarp();
       const int m = n - c0 < kBatch ? static_cast<int>(n - c0) : kBatch;
-      const bool own_rows = c0 >= row0 && c0 < row0 + kGroupRows;
+      const bool own_rows = c0 < row0 + kGroupRows && c0 + kBatch > row0;  // the batch meets the group's rows
       DfAcc ka[kLaneRows], sa[kLaneRows];
       if (rows_ok && okmask == kFull && m == kBatch && !own_rows) {
 #pragma unroll 1
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
 #pragma unroll
           for (int q = 0; q < kLaneRows; ++q) {
             const int64_t i = row0 + 32 * q + lane;
-            if (i >= n || i == j) continue;
+            if (i >= row_end || i == j) continue;
             if (rok[q] && jok) {
               df2 p, mm;
               fwd_term<kModel>(ai[q], yi[q], c, p, mm);
@@ -256,9 +261,9 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
         if (kW) s += part[1][w][r];
       }
       const int64_t i = row0 + r;
-      if (i < n) {
-        k_out[i] = k;
-        if (kW) s_out[i] = s;
+      if (i < row_end) {
+        k_out[i - row_begin] = k;
+        if (kW) s_out[i - row_begin] = s;
       }
     }
     __syncthreads();  // part[] is rewritten by the next group
@@ -317,6 +322,7 @@ __device__ __forceinline__ void bwd_term(const BwdRow& R, float4 c0, float4 c1, 
 template <int kModel>
 __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const double* __restrict__ x,
                                                                         const double* __restrict__ y, int64_t n,
+                                                                        int64_t row_begin, int64_t rows,
                                                                         const double* __restrict__ gk,
                                                                         const double* __restrict__ gs,
                                                                         double* __restrict__ gx,
@@ -328,9 +334,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const BatchRange br = warp_batches(n, warp);
-  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  const int64_t row_end = row_begin + rows;  // <= n
+  const int64_t groups = (rows + kGroupRows - 1) / kGroupRows;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-    const int64_t row0 = g * kGroupRows;
+    const int64_t row0 = row_begin + g * kGroupRows;
     BwdRow R[kLaneRows];
     bool rok[kLaneRows];
 #pragma unroll
@@ -338,8 +345,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
       const int64_t i = row0 + 32 * q + lane;
       const df2 zero{0.0f, 0.0f};
       R[q] = BwdRow{zero, zero, zero, zero};
-      rok[q] = true;  // rows past n compute zero terms and are not stored
-      if (i < n) {
+      rok[q] = true;  // rows past the range compute zero terms and are not stored
+      if (i < row_end) {
         const double v = kW ? x[i] * y[i] : x[i];
         R[q].v = df_from_double(v);
         R[q].gk = df_from_double(gk[i]);
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
       const unsigned okmask = __ballot_sync(kFull, ok);
       __syncwarp();
       const int m = n - c0 < kBatch ? static_cast<int>(n - c0) : kBatch;
-      const bool own_rows = c0 >= row0 && c0 < row0 + kGroupRows;
+      const bool own_rows = c0 < row0 + kGroupRows && c0 + kBatch > row0;  // the batch meets the group's rows
       DfAcc ax[kLaneRows], ay[kLaneRows];
       if (rows_ok && okmask == kFull && m == kBatch && !own_rows) {
 #pragma unroll 1
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
 #pragma unroll
           for (int q = 0; q < kLaneRows; ++q) {
             const int64_t i = row0 + 32 * q + lane;
-            if (i >= n || i == j) continue;
+            if (i >= row_end || i == j) continue;
             if (rok[q] && jok) {
               df2 tx, ty;
               bwd_term<kModel>(R[q], s0, s1, tx, ty);
@@ -451,9 +458,9 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
         if (kW) sy += part[1][w][r];
       }
       const int64_t i = row0 + r;
-      if (i < n) {
-        gx[i] = kW ? y[i] * sx : sx;
-        if (kW) gy[i] = x[i] * sy;
+      if (i < row_end) {
+        gx[i - row_begin] = kW ? y[i] * sx : sx;
+        if (kW) gy[i - row_begin] = x[i] * sy;
       }
     }
     __syncthreads();  // part[] is rewritten by the next group
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
 // Persistent grid: resident blocks per SM (queried once per device and
 // kernel) times the SM count, at most one block per row group.
 template <typename Kernel>
-unsigned pair_grid(Kernel kernel, int* cache, int64_t n) {
+unsigned pair_grid(Kernel kernel, int* cache, int64_t rows) {
   int dev = 0;
   int per_sm = 1;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
@@ -474,7 +481,7 @@ unsigned pair_grid(Kernel kernel, int* cache, int64_t n) {
     }
     per_sm = cache[dev];
   }
-  const int64_t groups = (n + kGroupRows - 1) / kGroupRows;
+  const int64_t groups = (rows + kGroupRows - 1) / kGroupRows;
   const int64_t cap = static_cast<int64_t>(sm_count()) * per_sm;
   return static_cast<unsigned>(std::min(groups, cap));
 }
@@ -484,27 +491,28 @@ int g_occ_bwd[2][64];
 
 }  // namespace
 
-cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, double* k, double* s,
-                                cudaStream_t st) {
+cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                int64_t rows, double* k, double* s, cudaStream_t st) {
   if (model == MH_UBCM) {
-    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UBCM>, g_occ_fwd[0], n);
-    expected_fwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, k, s);
+    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UBCM>, g_occ_fwd[0], rows);
+    expected_fwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s);
   } else {
-    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UECM>, g_occ_fwd[1], n);
-    expected_fwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, k, s);
+    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UECM>, g_occ_fwd[1], rows);
+    expected_fwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s);
   }
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, const double* gk,
-                                const double* gs, double* gx, double* gy, cudaStream_t st) {
+cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                int64_t rows, const double* gk, const double* gs, double* gx, double* gy,
+                                cudaStream_t st) {
   if (model == MH_UBCM) {
-    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UBCM>, g_occ_bwd[0], n);
-    expected_bwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, gk, gs, gx, gy);
+    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UBCM>, g_occ_bwd[0], rows);
+    expected_bwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, gk, gs, gx, gy);
   } else {
-    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UECM>, g_occ_bwd[1], n);
-    expected_bwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, gk, gs, gx, gy);
+    const unsigned blocks = pair_grid(expected_bwd_kernel<MH_UECM>, g_occ_bwd[1], rows);
+    expected_bwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, gk, gs, gx, gy);
   }
   note_launches(1);
   return cudaGetLastError();

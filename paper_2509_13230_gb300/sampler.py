@@ -244,28 +244,59 @@ def segment_table(model: int, x: torch.Tensor, y: torch.Tensor | None = None, *,
     raise RuntimeError("segment table did not fit")
 
 
-def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
-    """(<k>, <s>) as FP64 CUDA tensors (<s> is None for UBCM)."""
+def row_shard(n: int, rank: int, world: int) -> tuple[int, int]:
+    """(row_begin, row_count) of rank `rank` out of `world` for the pairwise
+    sums: contiguous blocks whose sizes differ by at most one, in rank order."""
+    if world < 1 or not 0 <= rank < world or n < 0:
+        raise ValueError("need 0 <= rank < world and n >= 0")
+    base, extra = divmod(n, world)
+    begin = rank * base + min(rank, extra)
+    return begin, base + (1 if rank < extra else 0)
+
+
+def _row_range(rows, n: int) -> tuple[int, int]:
+    if rows is None:
+        return 0, n
+    begin, count = (int(v) for v in rows)
+    return begin, count
+
+
+def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None):
+    """(<k>, <s>) as FP64 CUDA tensors (<s> is None for UBCM).  rows =
+    (row_begin, row_count) computes only those rows (outputs of row_count
+    entries), bit for bit the values of the whole call."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
-    k = torch.empty_like(x)
-    s = torch.empty_like(x) if model == nat.MH_UECM else None
-    nat.check(nat.maxent_expected_fwd(model, _ptr(x), _ptr(y), n, _ptr(k), _ptr(s), _stream_handle(stream)),
-              "maxent_expected_fwd")
+    begin, count = _row_range(rows, n)
+    k = torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
+    s = torch.empty_like(k) if model == nat.MH_UECM else None
+    if rows is None:
+        rc = nat.maxent_expected_fwd(model, _ptr(x), _ptr(y), n, _ptr(k), _ptr(s), _stream_handle(stream))
+    else:
+        rc = nat.maxent_expected_fwd_rows(model, _ptr(x), _ptr(y), n, begin, count, _ptr(k), _ptr(s),
+                                          _stream_handle(stream))
+    nat.check(rc, "maxent_expected_fwd")
     return k, s
 
 
 def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch.Tensor,
-                 g_s: torch.Tensor | None = None, stream=None):
-    """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors)."""
+                 g_s: torch.Tensor | None = None, stream=None, rows=None):
+    """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors); rows as in
+    expected_fwd."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
     g_k = _check_vec("g_k", g_k, n)
     g_s = _check_vec("g_s", g_s, n) if model == nat.MH_UECM else None
-    gx = torch.empty_like(x)
-    gy = torch.empty_like(x) if model == nat.MH_UECM else None
-    nat.check(nat.maxent_expected_bwd(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy),
-                                      _stream_handle(stream)), "maxent_expected_bwd")
+    begin, count = _row_range(rows, n)
+    gx = torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
+    gy = torch.empty_like(gx) if model == nat.MH_UECM else None
+    if rows is None:
+        rc = nat.maxent_expected_bwd(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy),
+                                     _stream_handle(stream))
+    else:
+        rc = nat.maxent_expected_bwd_rows(model, _ptr(x), _ptr(y), n, begin, count, _ptr(g_k), _ptr(g_s),
+                                          _ptr(gx), _ptr(gy), _stream_handle(stream))
+    nat.check(rc, "maxent_expected_bwd")
     return gx, gy

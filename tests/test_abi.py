@@ -100,3 +100,31 @@ def test_symmetric_csr_workspace_and_argument_checks(lib):
     with pytest.raises(nat.MhError) as e:
         nat.mh_batch_workspace_size(desc, 1, nat.make_params(flags=sym), 100, 100)
     assert e.value.code == nat.MH_ERR_ARG
+
+
+def test_row_range_argument_checks_without_a_gpu(lib):
+    # the checks run before anything touches the (never dereferenced) pointers
+    fake = ctypes.c_void_p(256)
+    for begin, count in ((-1, 2), (0, -1), (4, 2), (6, 0), (2, 4)):
+        assert nat.maxent_expected_fwd_rows(1, fake, fake, 5, begin, count, fake, fake, None) == nat.MH_ERR_ARG
+        assert nat.maxent_expected_bwd_rows(1, fake, fake, 5, begin, count, fake, fake, fake, fake,
+                                            None) == nat.MH_ERR_ARG
+    assert "rows" in nat.last_error_detail()
+    # an empty range is valid and launches nothing
+    assert nat.maxent_expected_fwd_rows(0, fake, None, 5, 5, 0, fake, None, None) == nat.MH_OK
+    assert nat.maxent_expected_bwd_rows(0, fake, None, 5, 0, 0, fake, None, fake, None, None) == nat.MH_OK
+    assert nat.maxent_expected_fwd_rows(1, None, fake, 5, 0, 1, fake, fake, None) == nat.MH_ERR_ARG
+
+
+def test_row_shard_covers_every_row_once():
+    from paper_2509_13230_gb300.sampler import row_shard
+    for n in (0, 1, 7, 64, 1537):
+        for world in (1, 2, 3, 8):
+            parts = [row_shard(n, r, world) for r in range(world)]
+            assert parts[0][0] == 0
+            for (b0, c0), (b1, _) in zip(parts, parts[1:]):
+                assert b0 + c0 == b1
+            assert sum(c for _, c in parts) == n
+            assert max(c for _, c in parts) - min(c for _, c in parts) <= 1
+    with pytest.raises(ValueError):
+        row_shard(5, 2, 2)

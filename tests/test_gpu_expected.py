@@ -81,6 +81,35 @@ def test_double_float_range_boundaries(model):
 
 
 @pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_row_ranges_equal_the_whole_call_bit_for_bit(model):
+    """Ragged row ranges (a rank's share of a call sharded by rows, cut
+    across 64-row groups and 32-column batches) give exactly the whole call's
+    values for their rows, also where operands take the FP64 terms."""
+    from paper_2509_13230_gb300.sampler import row_shard
+    rng = np.random.default_rng(22)
+    n = 1537
+    x = np.exp(rng.normal(-1.0, 1.5, n))
+    x[[5, 700]] = [1e30, 1e-30]
+    y = rng.uniform(0.1, 0.95, n) if model == nat.MH_UECM else None
+    gk = rng.normal(size=n)
+    gs = rng.normal(size=n) if y is not None else None
+    X, Y = dev(x), None if y is None else dev(y)
+    GK, GS = dev(gk), None if gs is None else dev(gs)
+    k, s = expected_fwd(model, X, Y)
+    gx, gy = expected_bwd(model, X, Y, GK, GS)
+    cuts = [0, 1, 64, 129, 700, 829, 1536, 1537]
+    ranges = list(zip(cuts, cuts[1:])) + [(b, b + c) for b, c in (row_shard(n, r, 3) for r in range(3))]
+    for a, b in ranges:
+        kr, sr = expected_fwd(model, X, Y, rows=(a, b - a))
+        gxr, gyr = expected_bwd(model, X, Y, GK, GS, rows=(a, b - a))
+        assert torch.equal(kr, k[a:b]) and torch.equal(gxr, gx[a:b]), (a, b)
+        if y is not None:
+            assert torch.equal(sr, s[a:b]) and torch.equal(gyr, gy[a:b]), (a, b)
+    kr, _ = expected_fwd(model, X, Y, rows=(n, 0))
+    assert kr.numel() == 0
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
 def test_autograd_function_gradcheck(model):
     # The forward is accurate to about 2^-45 relative (double-float terms), so
     # the finite-difference step is 1e-5: truncation and rounding noise both

@@ -76,3 +76,58 @@ def test_rank_samples_union_equals_one_call():
     assert np.array_equal(np.concatenate([p[0] for p in parts]), whole[0])
     assert np.array_equal(np.concatenate([p[1] for p in parts]), whole[1])
     assert np.array_equal(np.concatenate([p[3] for p in parts]), whole[3])
+
+
+def _pairwise_rank_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2509_13230_gb300.sampler import row_shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # every rank holds all of x and y and sums its own block of rows
+        rng = np.random.default_rng(31)
+        n = 301
+        x = np.exp(rng.normal(-2.0, 1.0, n))
+        y = rng.uniform(0.2, 0.9, n)
+        begin, count = row_shard(n, rank, world)
+        k, s = oracle.expected_fwd(oracle.UECM, x, y, rows=np.arange(begin, begin + count))
+        width = row_shard(n, 0, world)[1]  # the largest share
+        mine = torch.zeros(2, width, dtype=torch.float64)
+        mine[0, :count] = torch.from_numpy(k)
+        mine[1, :count] = torch.from_numpy(s)
+        parts = [torch.zeros_like(mine) for _ in range(world)]
+        dist.all_gather(parts, mine)
+        counts = [row_shard(n, r, world)[1] for r in range(world)]
+        out[rank] = (np.concatenate([p[0, :c].numpy() for p, c in zip(parts, counts)]),
+                     np.concatenate([p[1, :c].numpy() for p, c in zip(parts, counts)]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_the_pairwise_sums_by_rows():
+    """Rows of the expected-degree sums split over ranks (each rank sums all
+    columns of its rows, so nothing is reduced); the gathered shares are the
+    whole call's sums (oracle on CPU)."""
+    import oracle
+    world = 2
+    port = free_port()
+    ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    procs = [ctx.Process(target=_pairwise_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    rng = np.random.default_rng(31)
+    n = 301
+    x = np.exp(rng.normal(-2.0, 1.0, n))
+    y = rng.uniform(0.2, 0.9, n)
+    k, s = oracle.expected_fwd(oracle.UECM, x, y)
+    for r in range(world):
+        assert np.array_equal(out[r][0], k) and np.array_equal(out[r][1], s)
