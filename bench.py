@@ -424,15 +424,16 @@ def pairwise_leg(args, dev, sm_mhz):
             call()
         torch.cuda.synchronize()
         reps = 5
-        ev0.record(stream)
-        for _ in range(reps):
-            call()
-        ev1.record(stream)
-        ev1.synchronize()
+        with ClockSampler(dev.index or 0) as clk:
+            ev0.record(stream)
+            for _ in range(reps):
+                call()
+            ev1.record(stream)
+            ev1.synchronize()
         ms = ev0.elapsed_time(ev1) / reps
         pairs = PAIR_N * (PAIR_N - 1)
         out[kind] = {"ms": ms, "pairs_per_s": pairs / (ms / 1e3), "fp32_ops_per_pair": PAIR_OPS[kind],
-                     "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9}
+                     "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9, "clocks": clk.summary()}
     import torch.cuda as tc
     sms = tc.get_device_properties(dev).multi_processor_count
     mhz = sm_mhz or 2070.0
@@ -476,11 +477,28 @@ def fit_leg(args, dev):
     s_t = torch.from_numpy(s_np).to(dev)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    res = fit(k_t, s_t, tol=1e-8)
-    ev1.record(stream)
-    ev1.synchronize()
+    # count the pairwise calls the fit makes (wrappers installed here only)
+    from paper_2509_13230_gb300 import expected as expected_mod
+    calls = {"fwd": 0, "bwd": 0}
+    orig = expected_mod.expected_fwd, expected_mod.expected_bwd
+
+    def counted(kind, fn):
+        def wrapper(*a, **kw):
+            calls[kind] += 1
+            return fn(*a, **kw)
+        return wrapper
+
+    expected_mod.expected_fwd = counted("fwd", orig[0])
+    expected_mod.expected_bwd = counted("bwd", orig[1])
+    try:
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index or 0) as clk:
+            ev0.record(stream)
+            res = fit(k_t, s_t, tol=1e-8)
+            ev1.record(stream)
+            ev1.synchronize()
+    finally:
+        expected_mod.expected_fwd, expected_mod.expected_bwd = orig
     fit_ms = ev0.elapsed_time(ev1)
     # the oracle's compensated FP64 sums at the fitted parameters, on sampled rows
     rng = np.random.default_rng(12)
@@ -502,6 +520,7 @@ def fit_leg(args, dev):
     return {"workload": f"fit_uecm_n{FIT_N // 1000}k_then_x{FIT_SAMPLES}", "n": FIT_N,
             "fit_ms": fit_ms, "residual": res.residual, "residual_oracle_sampled_rows": oracle_resid,
             "adam_steps": res.adam_steps, "newton_steps": res.newton_steps,
+            "pairwise_calls": calls, "fit_clocks": clk.summary(),
             "sample_ms": sample_ms, "samples": FIT_SAMPLES, "edges": edges,
             "edges_per_s": edges / (sample_ms / 1e3), "mean_degree": 2.0 * edges / FIT_SAMPLES / FIT_N,
             "target_mean_degree": float(k_np.mean()),
