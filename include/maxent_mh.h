@@ -361,7 +361,9 @@ int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, 
  * s_out, g_x, g_y hold row_count values, entry r for row row_begin + r.  Each
  * value equals, bit for bit, the one the whole call returns for that row.
  * MH_ERR_ARG unless 0 <= row_begin, 0 <= row_count and row_begin + row_count
- * <= n; row_count = 0 returns MH_OK without work.
+ * <= n; row_count = 0 returns MH_OK without work (the pointers may then be
+ * NULL).  The whole-range calls above keep their order of checks: with
+ * n >= 1 a NULL required pointer is MH_ERR_ARG.
  */
 int maxent_expected_fwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
                              int64_t row_count, double* k_out, double* s_out, mh_stream_t stream);

@@ -848,20 +848,30 @@ int mh_segment_table(int model, const double* x, const double* y, int64_t n, con
   return MH_OK;
 }
 
-int maxent_expected_fwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
-                             int64_t row_count, double* k_out, double* s_out, mh_stream_t stream) {
-  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !k_out ||
-      (model == MH_UECM && (!y || !s_out))) {
-    set_error("maxent_expected_fwd: bad model, n or pointer");
+// Checks shared by the row-range entry points: model, n and the range, in
+// that order; an empty range needs no pointers.
+static int check_row_range(const char* fn, int model, int64_t n, int64_t row_begin, int64_t row_count) {
+  if ((model != MH_UBCM && model != MH_UECM) || n < 1) {
+    set_error("%s: bad model or n", fn);
     return MH_ERR_ARG;
   }
   if (row_begin < 0 || row_count < 0 || row_begin > n || row_count > n - row_begin) {
-    set_error("maxent_expected_fwd_rows: rows [%lld, %lld + %lld) are not within [0, %lld)",
-              static_cast<long long>(row_begin), static_cast<long long>(row_begin),
-              static_cast<long long>(row_count), static_cast<long long>(n));
+    set_error("%s: rows [%lld, %lld + %lld) are not within [0, %lld)", fn, static_cast<long long>(row_begin),
+              static_cast<long long>(row_begin), static_cast<long long>(row_count), static_cast<long long>(n));
     return MH_ERR_ARG;
   }
+  return MH_OK;
+}
+
+int maxent_expected_fwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                             int64_t row_count, double* k_out, double* s_out, mh_stream_t stream) {
+  const int rc = check_row_range("maxent_expected_fwd", model, n, row_begin, row_count);
+  if (rc != MH_OK) return rc;
   if (row_count == 0) return MH_OK;
+  if (!x || !k_out || (model == MH_UECM && (!y || !s_out))) {
+    set_error("maxent_expected_fwd: a required pointer is NULL");
+    return MH_ERR_ARG;
+  }
   MH_CUDA(launch_expected_fwd(model, x, y, n, row_begin, row_count, k_out, s_out,
                               reinterpret_cast<cudaStream_t>(stream)));
   return MH_OK;
@@ -875,18 +885,13 @@ int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, 
 int maxent_expected_bwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
                              int64_t row_count, const double* g_k, const double* g_s, double* g_x, double* g_y,
                              mh_stream_t stream) {
-  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || !x || !g_k || !g_x ||
-      (model == MH_UECM && (!y || !g_s || !g_y))) {
-    set_error("maxent_expected_bwd: bad model, n or pointer");
-    return MH_ERR_ARG;
-  }
-  if (row_begin < 0 || row_count < 0 || row_begin > n || row_count > n - row_begin) {
-    set_error("maxent_expected_bwd_rows: rows [%lld, %lld + %lld) are not within [0, %lld)",
-              static_cast<long long>(row_begin), static_cast<long long>(row_begin),
-              static_cast<long long>(row_count), static_cast<long long>(n));
-    return MH_ERR_ARG;
-  }
+  const int rc = check_row_range("maxent_expected_bwd", model, n, row_begin, row_count);
+  if (rc != MH_OK) return rc;
   if (row_count == 0) return MH_OK;
+  if (!x || !g_k || !g_x || (model == MH_UECM && (!y || !g_s || !g_y))) {
+    set_error("maxent_expected_bwd: a required pointer is NULL");
+    return MH_ERR_ARG;
+  }
   MH_CUDA(launch_expected_bwd(model, x, y, n, row_begin, row_count, g_k, g_s, g_x, g_y,
                               reinterpret_cast<cudaStream_t>(stream)));
   return MH_OK;
