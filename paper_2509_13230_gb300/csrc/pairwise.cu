@@ -166,8 +166,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
         }
       }
     }
-    const bool rows_ok = __all_sync(kFull, rok[0] && rok[1]);
-    double k_tot[kLaneRows] = {0.0, 0.0}, s_tot[kLaneRows] = {0.0, 0.0};
+    bool lane_ok = true;
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) lane_ok = lane_ok && rok[q];
+    const bool rows_ok = __all_sync(kFull, lane_ok);
+    double k_tot[kLaneRows] = {}, s_tot[kLaneRows] = {};
     for (int64_t b = br.begin; b < br.end; ++b) {
       const int64_t c0 = b * kBatch;
       const int64_t jl = c0 + lane;
@@ -358,8 +361,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_bwd_kernel(const dou
         }
       }
     }
-    const bool rows_ok = __all_sync(kFull, rok[0] && rok[1]);
-    double x_tot[kLaneRows] = {0.0, 0.0}, y_tot[kLaneRows] = {0.0, 0.0};
+    bool lane_ok = true;
+#pragma unroll
+    for (int q = 0; q < kLaneRows; ++q) lane_ok = lane_ok && rok[q];
+    const bool rows_ok = __all_sync(kFull, lane_ok);
+    double x_tot[kLaneRows] = {}, y_tot[kLaneRows] = {};
     for (int64_t b = br.begin; b < br.end; ++b) {
       const int64_t c0 = b * kBatch;
       const int64_t jl = c0 + lane;
