@@ -8,9 +8,10 @@ Everything here is plain and slow on purpose:
 
 * ``mh_sample`` / ``bf_sample`` / ``partition`` / ``philox`` call the serial C
   file ``mh_oracle.c`` (FP64, no FMA contraction, C library ``log``/``log1p``).
-* ``expected_fwd`` / ``expected_bwd`` evaluate the O(N^2) sums of the
-  maximum-likelihood conditions (Sec. 2.2, Sec. 2.5, Sec. 4) pair by pair in
-  FP64 with correctly rounded summation (``math.fsum``).
+* ``expected_fwd`` / ``expected_bwd`` / ``expected_jacobian_diag``
+  evaluate the O(N^2) sums of the maximum-likelihood conditions (Sec. 2.2,
+  Sec. 2.5, Sec. 4), their gradient and the diagonal of their Jacobian pair
+  by pair in FP64 with correctly rounded summation (``math.fsum``).
 * ``graph_probabilities`` enumerates every simple graph of a tiny network
   and multiplies the independent pair probabilities (Eq. 1 / Eq. 3).
 * ``symmetric_csr`` lists every sampled edge in both endpoint rows, in the
@@ -264,6 +265,36 @@ def expected_bwd(model, x, y, g_k, g_s=None, rows=None):
         gx[t] = math.fsum((gk * dp_dx).tolist() + (gs * dm_dx).tolist())
         gy[t] = math.fsum((gk * dp_dy).tolist() + (gs * dm_dy).tolist())
     return gx, gy
+
+
+def expected_jacobian_diag(model, x, y=None, rows=None):
+    """Diagonal of the Jacobian of the expected degrees (and strengths) of the
+    maximum-likelihood conditions (Sec. 2.2, Sec. 2.5): for each row i the
+    partial derivatives of <k_i> (and <s_i>) with respect to the node's own
+    x_i (and y_i), every other parameter held fixed.  With D = 1 - r + A,
+      d<k_i>/dx_i = sum_j p (1 - p) / x_i
+      d<k_i>/dy_i = sum_j p / (y_i D)
+      d<s_i>/dx_i = sum_j p (1 - p) / (x_i (1 - r))
+      d<s_i>/dy_i = sum_j p / (y_i D (1 - r)) + p r / (y_i (1 - r)^2)
+    Returns (dk_dx,) for the UBCM and (dk_dx, dk_dy, ds_dx, ds_dy) for the
+    UECM; x_i (and y_i) must be positive."""
+    x = _f64(x)
+    y = _f64(y) if model == UECM else None
+    idx = np.arange(len(x)) if rows is None else np.asarray(rows)
+    out = [np.zeros(len(idx)) for _ in range(1 if model == UBCM else 4)]
+    for t, i in enumerate(idx):
+        i = int(i)
+        j, p, m, r = _pair_terms(model, x, y, i)
+        dp_dx = p * (1.0 - p) / x[i]
+        out[0][t] = math.fsum(dp_dx.tolist())
+        if model == UBCM:
+            continue
+        a = x * y
+        D = (1.0 - r) + a[i] * a[j]
+        out[1][t] = math.fsum((p / (y[i] * D)).tolist())
+        out[2][t] = math.fsum((dp_dx / (1.0 - r)).tolist())
+        out[3][t] = math.fsum((p / (y[i] * D * (1.0 - r)) + p * r / (y[i] * (1.0 - r) ** 2)).tolist())
+    return tuple(out)
 
 
 # --------------------------------------------------------------------------

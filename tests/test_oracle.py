@@ -290,3 +290,45 @@ def test_pareto_scale_grid_matches_calibration():
     net = workloads.pareto_ubcm(n, workloads.pareto_scale(n), seed=3)
     _, _, _, counts, _ = oracle.mh_sample(oracle.UBCM, net.x, seed=0, num_samples=1, seg_target=1 << 30)
     assert abs(2.0 * counts[0] / n - 20.0) < 1.5
+
+
+@pytest.mark.parametrize("model", [oracle.UBCM, oracle.UECM])
+def test_jacobian_diagonal_matches_central_differences(model):
+    """Each entry against a central difference of the expected sums with only
+    node i's own parameter moved (Sec. 2.2, Sec. 2.5)."""
+    rng = np.random.default_rng(19)
+    n = 24
+    x = np.exp(rng.normal(-0.5, 1.0, n))
+    y = rng.uniform(0.2, 0.9, n) if model == oracle.UECM else None
+    diag = oracle.expected_jacobian_diag(model, x, y)
+    for i in range(n):
+        h = 1e-6 * x[i]
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        (kp, sp), (km, sm) = (oracle.expected_fwd(model, xx, y, rows=[i]) for xx in (xp, xm))
+        fd = [(kp[0] - km[0]) / (2 * h)] + ([(sp[0] - sm[0]) / (2 * h)] if y is not None else [])
+        got = [diag[0][i]] + ([diag[2][i]] if y is not None else [])
+        for f, g in zip(fd, got):
+            assert abs(f - g) <= 1e-6 * max(1.0, abs(f)), (i, f, g)
+        if y is None:
+            continue
+        h = 1e-6 * y[i]
+        yp, ym = y.copy(), y.copy()
+        yp[i] += h
+        ym[i] -= h
+        (kp, sp), (km, sm) = (oracle.expected_fwd(model, x, yy, rows=[i]) for yy in (yp, ym))
+        for f, g in (((kp[0] - km[0]) / (2 * h), diag[1][i]), ((sp[0] - sm[0]) / (2 * h), diag[3][i])):
+            assert abs(f - g) <= 1e-6 * max(1.0, abs(f)), (i, f, g)
+
+
+def test_jacobian_diagonal_rows_and_ubcm_closed_form():
+    # the UBCM entry is sum_j x_j / (1 + x_i x_j)^2; rows= picks the same values
+    rng = np.random.default_rng(20)
+    x = np.exp(rng.normal(-1.0, 1.0, 40))
+    (d,) = oracle.expected_jacobian_diag(oracle.UBCM, x)
+    i = 7
+    j = np.arange(40) != i
+    assert d[i] == pytest.approx(np.sum(x[j] / (1.0 + x[i] * x[j]) ** 2), rel=1e-13)
+    (dr,) = oracle.expected_jacobian_diag(oracle.UBCM, x, rows=[3, 7])
+    assert dr[1] == d[7] and dr[0] == d[3]
