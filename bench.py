@@ -479,8 +479,8 @@ def fit_leg(args, dev):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # count the pairwise calls the fit makes (wrappers installed here only)
     from paper_2509_13230_gb300 import expected as expected_mod
-    calls = {"fwd": 0, "bwd": 0}
-    orig = expected_mod.expected_fwd, expected_mod.expected_bwd
+    calls = {"fwd": 0, "bwd": 0, "jacobian_diag": 0}
+    orig = expected_mod.expected_fwd, expected_mod.expected_bwd, expected_mod.expected_jacobian_diag
 
     def counted(kind, fn):
         def wrapper(*a, **kw):
@@ -490,6 +490,7 @@ def fit_leg(args, dev):
 
     expected_mod.expected_fwd = counted("fwd", orig[0])
     expected_mod.expected_bwd = counted("bwd", orig[1])
+    expected_mod.expected_jacobian_diag = counted("jacobian_diag", orig[2])
     try:
         torch.cuda.synchronize()
         with ClockSampler(dev.index or 0) as clk:
@@ -498,7 +499,7 @@ def fit_leg(args, dev):
             ev1.record(stream)
             ev1.synchronize()
     finally:
-        expected_mod.expected_fwd, expected_mod.expected_bwd = orig
+        expected_mod.expected_fwd, expected_mod.expected_bwd, expected_mod.expected_jacobian_diag = orig
     fit_ms = ev0.elapsed_time(ev1)
     # the oracle's compensated FP64 sums at the fitted parameters, on sampled rows
     rng = np.random.default_rng(12)

@@ -354,6 +354,22 @@ int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, 
                         const double* g_s, double* g_x, double* g_y, mh_stream_t stream);
 
 /*
+ * maxent_expected_jacobian_diag — the diagonal of the Jacobian of the
+ * expected sums: for every node i the derivatives of its own <k_i> (and
+ * <s_i>) with respect to its own x_i (and y_i), the other parameters fixed
+ * (the per-node blocks a Newton step's preconditioner inverts; Sec. 2.2,
+ * Sec. 2.5):
+ *   dk_dx[i] = sum_{j != i} dp_ij/dx_i      dk_dy[i] = sum_{j != i} dp_ij/dy_i
+ *   ds_dx[i] = sum_{j != i} dm_ij/dx_i      ds_dy[i] = sum_{j != i} dm_ij/dy_i
+ * x, y (y NULL for UBCM) and the outputs are FP64[n]; the UBCM returns dk_dx
+ * only (dk_dy, ds_dx, ds_dy NULL).  One pass over the pairs, where two
+ * maxent_expected_bwd calls with unit upstream gradients would give the same
+ * values (each pair term then counted from both of its ends).
+ */
+int maxent_expected_jacobian_diag(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                  double* dk_dy, double* ds_dx, double* ds_dy, mh_stream_t stream);
+
+/*
  * maxent_expected_fwd_rows / maxent_expected_bwd_rows — the same sums for the
  * rows i in [row_begin, row_begin + row_count) only (every sum still runs over
  * all j != i), so that ranks can share one call by rows with no reduction:

@@ -10,13 +10,13 @@ from ._native import (MH_BOUND_PAPER, MH_CSR_SYMMETRIC, MH_DIRECTED, MH_FP64_ONL
                       MH_OUT_CSR, MH_UBCM, MH_UECM, MhError)
 from .expected import ExpectedDegrees, FitResult, expected_degrees, fit
 from .ensemble import Ensemble
-from .sampler import (BipartiteSampler, SampleResult, Sampler, expected_bwd, expected_fwd, row_shard,
-                      sample_bipartite, sample_ubcm, sample_weighted, segment_table)
+from .sampler import (BipartiteSampler, SampleResult, Sampler, expected_bwd, expected_fwd, expected_jacobian_diag,
+                      row_shard, sample_bipartite, sample_ubcm, sample_weighted, segment_table)
 
 __all__ = [
     "MH_UBCM", "MH_UECM", "MH_OUT_COO", "MH_OUT_CSR", "MH_BOUND_PAPER", "MH_INIT_PREV", "MH_DIRECTED",
     "MH_CSR_SYMMETRIC", "MH_FP64_ONLY",
     "MhError", "Sampler", "BipartiteSampler", "SampleResult", "sample_ubcm", "sample_weighted", "sample_bipartite",
-    "segment_table", "expected_fwd", "expected_bwd", "row_shard", "Ensemble",
+    "segment_table", "expected_fwd", "expected_bwd", "expected_jacobian_diag", "row_shard", "Ensemble",
     "ExpectedDegrees", "expected_degrees", "fit", "FitResult",
 ]

@@ -51,6 +51,7 @@ EXPORTED = (
     "maxent_expected_bwd",
     "maxent_expected_fwd_rows",
     "maxent_expected_bwd_rows",
+    "maxent_expected_jacobian_diag",
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
@@ -155,6 +156,8 @@ def load(path: str | None = None):
         lib.maxent_expected_fwd_rows.restype = i32
         lib.maxent_expected_bwd_rows.argtypes = [i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_bwd_rows.restype = i32
+        lib.maxent_expected_jacobian_diag.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
+        lib.maxent_expected_jacobian_diag.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
         lib.mh_bipartite_workspace_size.restype = i32
         lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
@@ -280,3 +283,7 @@ def mh_sample_bipartite(model, x_plus, y_plus, n_plus, x_minus, y_minus, n_minus
     return load().mh_sample_bipartite(model, x_plus, y_plus, n_plus, x_minus, y_minus, n_minus, ctypes.byref(params),
                                       workspace, workspace_bytes, src, dst, w, csr_offsets, csr_indices, csr_weights,
                                       capacity_edges, h_edges_per_sample, h_stats, stream)
+
+
+def maxent_expected_jacobian_diag(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, stream) -> int:
+    return load().maxent_expected_jacobian_diag(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, stream)

@@ -102,45 +102,91 @@ __device__ __forceinline__ BatchRange warp_batches(int64_t n, int w) {
   return {b0, b0 + per < nb ? b0 + per : nb};
 }
 
-// ---- forward -----------------------------------------------------------------------
+// ---- expected sums and the diagonal of their Jacobian ---------------------------------
+
+// What a row-sum kernel adds up over j: the expected sums (p, and m for the
+// UECM) or the diagonal of their Jacobian: UBCM x_j / (1 + z)^2 = dp/dx_i;
+// UECM (1 - r) Q, Q and Q (1 - r + r D) / (1 - r)^2, which the row factors
+// y_i and x_i turn into d<k_i>/dx_i, d<k_i>/dy_i (x_i Q), d<s_i>/dx_i (y_i Q)
+// and d<s_i>/dy_i.
+enum RowSumKind { kExpectedSums = 0, kJacobianDiag = 1 };
+
+template <int kModel, int kKind>
+struct RowSums {
+  static constexpr int kCount = kModel == MH_UBCM ? 1 : (kKind == kExpectedSums ? 2 : 3);
+};
 
 // FP64 terms of one pair (the same expressions, for out-of-range operands).
-__device__ __noinline__ void pair_fwd_fp64(int model, double xi, double yi, double xj, double yj, double& p,
-                                           double& m) {
-  if (model == MH_UBCM) {
+template <int kModel, int kKind>
+__device__ __noinline__ void row_terms_fp64(double xi, double yi, double xj, double yj, double* t) {
+  if constexpr (kModel == MH_UBCM) {
     const double z = xi * xj;
-    p = z / (1.0 + z);
-    m = 0.0;
-    return;
+    if constexpr (kKind == kExpectedSums) {
+      t[0] = z / (1.0 + z);
+    } else {
+      const double opz = 1.0 + z;
+      t[0] = xj / (opz * opz);
+    }
+  } else {
+    const double aj = xj * yj;
+    const double r = yi * yj;
+    const double omr = 1.0 - r;
+    const double A = (xi * yi) * aj;
+    if constexpr (kKind == kExpectedSums) {
+      t[0] = A / (omr + A);
+      t[1] = t[0] / omr;
+    } else {
+      const double D = omr + A;
+      const double Q = aj / (D * D);
+      t[0] = omr * Q;
+      t[1] = Q;
+      t[2] = Q * ((omr + r * D) / (omr * omr));
+    }
   }
-  const double A = (xi * yi) * (xj * yj);
-  const double omr = 1.0 - yi * yj;
-  p = A / (omr + A);
-  m = p / omr;
 }
 
 // Double-float terms; c = (a_j, y_j) as staged (x_j for the UBCM).
-template <int kModel>
-__device__ __forceinline__ void fwd_term(df2 ai, df2 yi, float4 c, df2& p, df2& m) {
-  const df2 prod = df_mul(ai, df2{c.x, c.y});
-  if (kModel == MH_UBCM) {
-    p = df_div(prod, df_add_f(prod, 1.0f));
-    return;
+template <int kModel, int kKind>
+__device__ __forceinline__ void row_terms(df2 ai, df2 yi, float4 c, df2* t) {
+  const df2 aj{c.x, c.y};
+  const df2 prod = df_mul(ai, aj);
+  if constexpr (kModel == MH_UBCM) {
+    const df2 opz = df_add_f(prod, 1.0f);
+    if constexpr (kKind == kExpectedSums) {
+      t[0] = df_div(prod, opz);
+    } else {
+      t[0] = df_div(aj, df_mul(opz, opz));
+    }
+  } else {
+    const df2 r = df_mul(yi, df2{c.z, c.w});
+    const df2 omr = one_minus(r);
+    const df2 D = df_add_sloppy(omr, prod);  // both >= 0
+    if constexpr (kKind == kExpectedSums) {
+      t[0] = df_div(prod, D);
+      t[1] = df_div(t[0], omr);
+    } else {
+      const df2 Q = df_div(aj, df_mul(D, D));
+      t[0] = df_mul(omr, Q);
+      t[1] = Q;
+      t[2] = df_mul(Q, df_div(df_add_sloppy(omr, df_mul(r, D)), df_mul(omr, omr)));  // (1 - r + r D) / (1 - r)^2
+    }
   }
-  const df2 omr = one_minus(df_mul(yi, df2{c.z, c.w}));
-  p = df_div(prod, df_add_sloppy(omr, prod));  // both >= 0
-  m = df_div(p, omr);
 }
 
-template <int kModel>
-__global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const double* __restrict__ x,
-                                                                        const double* __restrict__ y, int64_t n,
-                                                                        int64_t row_begin, int64_t rows,
-                                                                        double* __restrict__ k_out,
-                                                                        double* __restrict__ s_out) {
+// out0..out3: <k>, <s> (expected sums); d<k>/dx, d<k>/dy, d<s>/dx, d<s>/dy
+// (Jacobian diagonal; only d<k>/dx for the UBCM).  Entry r is row row_begin + r.
+template <int kModel, int kKind>
+__global__ void __launch_bounds__(kPairThreads, 1) row_sums_kernel(const double* __restrict__ x,
+                                                                    const double* __restrict__ y, int64_t n,
+                                                                    int64_t row_begin, int64_t rows,
+                                                                    double* __restrict__ out0,
+                                                                    double* __restrict__ out1,
+                                                                    double* __restrict__ out2,
+                                                                    double* __restrict__ out3) {
   constexpr bool kW = kModel == MH_UECM;
+  constexpr int kQ = RowSums<kModel, kKind>::kCount;
   __shared__ float4 stage[kPairWarps][kBatch];
-  __shared__ double part[2][kPairWarps][kGroupRows];
+  __shared__ double part[kQ][kPairWarps][kGroupRows];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const BatchRange br = warp_batches(n, warp);
@@ -170,7 +216,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
 #pragma unroll
     for (int q = 0; q < kLaneRows; ++q) lane_ok = lane_ok && rok[q];
     const bool rows_ok = __all_sync(kFull, lane_ok);
-    double k_tot[kLaneRows] = {}, s_tot[kLaneRows] = {};
+    double tot[kQ][kLaneRows] = {};
     for (int64_t b = br.begin; b < br.end; ++b) {
       const int64_t c0 = b * kBatch;
       const int64_t jl = c0 + lane;
@@ -192,7 +238,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
       __syncwarp();
       const int m = n - c0 < kBatch ? static_cast<int>(n - c0) : kBatch;
       const bool own_rows = c0 < row0 + kGroupRows && c0 + kBatch > row0;  // the batch meets the group's rows
-      DfAcc ka[kLaneRows], sa[kLaneRows];
+      DfAcc acc[kQ][kLaneRows];
       if (rows_ok && okmask == kFull && m == kBatch && !own_rows) {
 #pragma unroll 1
         for (int t0 = 0; t0 < kBatch; t0 += kNormEvery) {
@@ -201,17 +247,16 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
             const float4 c = stage[warp][t0 + u];
 #pragma unroll
             for (int q = 0; q < kLaneRows; ++q) {
-              df2 p, mm;
-              fwd_term<kModel>(ai[q], yi[q], c, p, mm);
-              ka[q].add(p);
-              if (kW) sa[q].add(mm);
+              df2 t[kQ];
+              row_terms<kModel, kKind>(ai[q], yi[q], c, t);
+#pragma unroll
+              for (int e = 0; e < kQ; ++e) acc[e][q].add(t[e]);
             }
           }
 #pragma unroll
-          for (int q = 0; q < kLaneRows; ++q) {
-            ka[q].norm();
-            if (kW) sa[q].norm();
-          }
+          for (int e = 0; e < kQ; ++e)
+#pragma unroll
+            for (int q = 0; q < kLaneRows; ++q) acc[e][q].norm();
         }
       } else {
         for (int t = 0; t < m; ++t) {
@@ -223,50 +268,59 @@ __global__ void __launch_bounds__(kPairThreads, 1) expected_fwd_kernel(const dou
             const int64_t i = row0 + 32 * q + lane;
             if (i >= row_end || i == j) continue;
             if (rok[q] && jok) {
-              df2 p, mm;
-              fwd_term<kModel>(ai[q], yi[q], c, p, mm);
-              ka[q].add(p);
-              if (kW) sa[q].add(mm);
+              df2 tt[kQ];
+              row_terms<kModel, kKind>(ai[q], yi[q], c, tt);
+#pragma unroll
+              for (int e = 0; e < kQ; ++e) acc[e][q].add(tt[e]);
             } else {
-              double p, mm;
-              pair_fwd_fp64(kModel, x[i], kW ? y[i] : 0.0, x[j], kW ? y[j] : 0.0, p, mm);
-              k_tot[q] += p;
-              if (kW) s_tot[q] += mm;
+              double tf[kQ];
+              row_terms_fp64<kModel, kKind>(x[i], kW ? y[i] : 0.0, x[j], kW ? y[j] : 0.0, tf);
+#pragma unroll
+              for (int e = 0; e < kQ; ++e) tot[e][q] += tf[e];
             }
           }
           if ((t % kNormEvery) == kNormEvery - 1) {
 #pragma unroll
-            for (int q = 0; q < kLaneRows; ++q) {
-              ka[q].norm();
-              if (kW) sa[q].norm();
-            }
+            for (int e = 0; e < kQ; ++e)
+#pragma unroll
+              for (int q = 0; q < kLaneRows; ++q) acc[e][q].norm();
           }
         }
       }
 #pragma unroll
-      for (int q = 0; q < kLaneRows; ++q) {
-        k_tot[q] += ka[q].value();
-        if (kW) s_tot[q] += sa[q].value();
-      }
+      for (int e = 0; e < kQ; ++e)
+#pragma unroll
+        for (int q = 0; q < kLaneRows; ++q) tot[e][q] += acc[e][q].value();
       __syncwarp();  // the next batch overwrites stage[warp]
     }
 #pragma unroll
-    for (int q = 0; q < kLaneRows; ++q) {
-      part[0][warp][32 * q + lane] = k_tot[q];
-      if (kW) part[1][warp][32 * q + lane] = s_tot[q];
-    }
+    for (int e = 0; e < kQ; ++e)
+#pragma unroll
+      for (int q = 0; q < kLaneRows; ++q) part[e][warp][32 * q + lane] = tot[e][q];
     __syncthreads();
     if (threadIdx.x < kGroupRows) {
       const int r = threadIdx.x;
-      double k = 0.0, s = 0.0;
-      for (int w = 0; w < kPairWarps; ++w) {
-        k += part[0][w][r];
-        if (kW) s += part[1][w][r];
-      }
+      double S[kQ];
+#pragma unroll
+      for (int e = 0; e < kQ; ++e) S[e] = 0.0;
+      for (int w = 0; w < kPairWarps; ++w)
+#pragma unroll
+        for (int e = 0; e < kQ; ++e) S[e] += part[e][w][r];
       const int64_t i = row0 + r;
       if (i < row_end) {
-        k_out[i - row_begin] = k;
-        if (kW) s_out[i - row_begin] = s;
+        const int64_t o = i - row_begin;
+        if constexpr (kKind == kExpectedSums) {
+          out0[o] = S[0];
+          if constexpr (kW) out1[o] = S[1];
+        } else if constexpr (!kW) {
+          out0[o] = S[0];
+        } else {
+          const double xi = x[i], yv = y[i];
+          out0[o] = yv * S[0];
+          out1[o] = xi * S[1];
+          out2[o] = yv * S[1];
+          out3[o] = xi * S[2];
+        }
       }
     }
     __syncthreads();  // part[] is rewritten by the next group
@@ -494,17 +548,36 @@ unsigned pair_grid(Kernel kernel, int* cache, int64_t rows) {
 
 int g_occ_fwd[2][64];
 int g_occ_bwd[2][64];
+int g_occ_diag[2][64];
 
 }  // namespace
 
 cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
                                 int64_t rows, double* k, double* s, cudaStream_t st) {
   if (model == MH_UBCM) {
-    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UBCM>, g_occ_fwd[0], rows);
-    expected_fwd_kernel<MH_UBCM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s);
+    auto kernel = row_sums_kernel<MH_UBCM, kExpectedSums>;
+    kernel<<<pair_grid(kernel, g_occ_fwd[0], rows), kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s, nullptr,
+                                                                          nullptr);
   } else {
-    const unsigned blocks = pair_grid(expected_fwd_kernel<MH_UECM>, g_occ_fwd[1], rows);
-    expected_fwd_kernel<MH_UECM><<<blocks, kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s);
+    auto kernel = row_sums_kernel<MH_UECM, kExpectedSums>;
+    kernel<<<pair_grid(kernel, g_occ_fwd[1], rows), kPairThreads, 0, st>>>(x, y, n, row_begin, rows, k, s, nullptr,
+                                                                          nullptr);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expected_jacobian_diag(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                          int64_t rows, double* dk_dx, double* dk_dy, double* ds_dx, double* ds_dy,
+                                          cudaStream_t st) {
+  if (model == MH_UBCM) {
+    auto kernel = row_sums_kernel<MH_UBCM, kJacobianDiag>;
+    kernel<<<pair_grid(kernel, g_occ_diag[0], rows), kPairThreads, 0, st>>>(x, y, n, row_begin, rows, dk_dx,
+                                                                           nullptr, nullptr, nullptr);
+  } else {
+    auto kernel = row_sums_kernel<MH_UECM, kJacobianDiag>;
+    kernel<<<pair_grid(kernel, g_occ_diag[1], rows), kPairThreads, 0, st>>>(x, y, n, row_begin, rows, dk_dx, dk_dy,
+                                                                           ds_dx, ds_dy);
   }
   note_launches(1);
   return cudaGetLastError();

@@ -26,7 +26,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _native as nat
-from .sampler import expected_bwd, expected_fwd
+from .sampler import expected_bwd, expected_fwd, expected_jacobian_diag
 
 
 class ExpectedDegrees(torch.autograd.Function):
@@ -80,17 +80,13 @@ def _residual(model, x, y, k_t, s_t):
 
 def _diagonal_blocks(model, x, y, n):
     """Per-node d<k_i>/dtheta_i (UBCM) or the 2x2 block of d(<k_i>, <s_i>) /
-    d(theta_i, phi_i) (UECM).  The backward kernel with all-ones dL/d<k>
-    returns 2 d<k_i>/dx_i (each pair term enters both endpoints' sums), so
-    half of it times x_i is the diagonal entry."""
-    ones = torch.ones(n, dtype=torch.float64, device=x.device)
+    d(theta_i, phi_i) (UECM), theta = log x and phi = log y: the Jacobian
+    diagonal kernel's derivatives in x and y times x_i and y_i."""
     if model == nat.MH_UBCM:
-        gx, _ = expected_bwd(model, x, None, ones)
-        return (0.5 * gx * x,)
-    zeros = torch.zeros_like(ones)
-    gx_k, gy_k = expected_bwd(model, x, y, ones, zeros)
-    gx_s, gy_s = expected_bwd(model, x, y, zeros, ones)
-    return 0.5 * gx_k * x, 0.5 * gy_k * y, 0.5 * gx_s * x, 0.5 * gy_s * y
+        (dk_dx,) = expected_jacobian_diag(model, x, None)
+        return (dk_dx * x,)
+    dk_dx, dk_dy, ds_dx, ds_dy = expected_jacobian_diag(model, x, y)
+    return dk_dx * x, dk_dy * y, ds_dx * x, ds_dy * y
 
 
 def _jvp(model, x, y, v):

@@ -300,3 +300,17 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
                                           _ptr(gx), _ptr(gy), _stream_handle(stream))
     nat.check(rc, "maxent_expected_bwd")
     return gx, gy
+
+
+def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """(d<k>/dx,) for the UBCM or (d<k>/dx, d<k>/dy, d<s>/dx, d<s>/dy) for the
+    UECM: each node's derivatives of its own expected degree (and strength)
+    with respect to its own parameters, FP64 CUDA tensors."""
+    x = _check_vec("x", x)
+    n = int(x.shape[0])
+    y = _check_vec("y", y, n) if model == nat.MH_UECM else None
+    outs = [torch.empty_like(x) for _ in range(1 if model == nat.MH_UBCM else 4)]
+    ptrs = [_ptr(t) for t in outs] + [None] * (4 - len(outs))
+    nat.check(nat.maxent_expected_jacobian_diag(model, _ptr(x), _ptr(y), n, *ptrs, _stream_handle(stream)),
+              "maxent_expected_jacobian_diag")
+    return tuple(outs)

@@ -128,3 +128,11 @@ def test_row_shard_covers_every_row_once():
             assert max(c for _, c in parts) - min(c for _, c in parts) <= 1
     with pytest.raises(ValueError):
         row_shard(5, 2, 2)
+
+
+def test_jacobian_diagonal_argument_checks_without_a_gpu(lib):
+    fake = ctypes.c_void_p(256)
+    assert nat.maxent_expected_jacobian_diag(1, fake, fake, 5, fake, None, fake, fake, None) == nat.MH_ERR_ARG
+    assert nat.maxent_expected_jacobian_diag(0, None, None, 5, fake, None, None, None, None) == nat.MH_ERR_ARG
+    assert nat.maxent_expected_jacobian_diag(0, fake, None, 0, fake, None, None, None, None) == nat.MH_ERR_ARG
+    assert nat.maxent_expected_jacobian_diag(2, fake, fake, 5, fake, fake, fake, fake, None) == nat.MH_ERR_ARG

@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2509_13230_gb300 import _native as nat
 from paper_2509_13230_gb300.expected import ExpectedDegrees, fit
-from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
+from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd, expected_jacobian_diag
 
 pytestmark = pytest.mark.gpu
 
@@ -107,6 +107,37 @@ def test_row_ranges_equal_the_whole_call_bit_for_bit(model):
             assert torch.equal(sr, s[a:b]) and torch.equal(gyr, gy[a:b]), (a, b)
     kr, _ = expected_fwd(model, X, Y, rows=(n, 0))
     assert kr.numel() == 0
+
+
+@pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
+def test_jacobian_diagonal_matches_oracle(model):
+    """Each node's derivatives of its own <k_i> (and <s_i>) with respect to
+    its own x_i (and y_i), against the oracle's closed forms (pinned by
+    central differences), with operands on both sides of the double-float
+    range; and equal to half the backward kernel with unit upstream
+    gradients."""
+    rng = np.random.default_rng(23)
+    n = 1537
+    x = np.exp(rng.normal(-1.0, 1.5, n))
+    x[[4, 900]] = [1e30, 2.0**-31]
+    y = rng.uniform(0.1, 0.95, n) if model == nat.MH_UECM else None
+    if y is not None:
+        y[[11, 12]] = [1 - 2.0**-13, 1 - 2.0**-11]
+    X, Y = dev(x), None if y is None else dev(y)
+    got = [t.cpu().numpy() for t in expected_jacobian_diag(model, X, Y)]
+    keep = np.flatnonzero(x < 2.0**20)  # the oracle's closed forms lose digits in 1 - p for p near 1
+    ref = oracle.expected_jacobian_diag(model, x, y, rows=keep)
+    for g, r in zip(got, ref):
+        np.testing.assert_allclose(g[keep], r, rtol=1e-10)
+    ones, zeros = torch.ones_like(X), torch.zeros_like(X)
+    if model == nat.MH_UBCM:
+        gx, _ = expected_bwd(model, X, None, ones)
+        np.testing.assert_allclose(got[0], 0.5 * gx.cpu().numpy(), rtol=1e-12)
+    else:
+        gxk, gyk = expected_bwd(model, X, Y, ones, zeros)
+        gxs, gys = expected_bwd(model, X, Y, zeros, ones)
+        for g, b in zip(got, (gxk, gyk, gxs, gys)):
+            np.testing.assert_allclose(g, 0.5 * b.cpu().numpy(), rtol=1e-12)
 
 
 @pytest.mark.parametrize("model", [nat.MH_UBCM, nat.MH_UECM])
