@@ -362,8 +362,9 @@ PAIR_N = 200_000
 # multiply, accumulation 8 per term plus a 6-operation renormalisation every
 # 8 terms).  Forward: a_i a_j, y_i y_j, 1 - r, D, two divisions, two sums.
 # Backward: r, 1 - r, A, D, D^2, Q, g_k and g_s sums, the x term (3 ops) and
-# the y term (6 ops), two sums.
-PAIR_OPS = {"fwd": 81, "bwd": 185}
+# the y term (6 ops), two sums.  Jacobian diagonal: A, r, 1 - r, D, D^2, Q,
+# (1 - r) Q, r D, 1 - r + r D, (1 - r)^2, a division and a product, three sums.
+PAIR_OPS = {"fwd": 81, "bwd": 185, "jacobian_diag": 136}
 FP32_LANES_PER_SM = 128
 
 
@@ -385,11 +386,11 @@ def kernels_once(dev):
     """Each profiled kernel once, untimed, for ncu captures: the headline call
     (10 samples of the weighted N = 20,000 workload) at segment lengths 8, 16
     and 32 (three walk launches, in that order), then the UECM pairwise
-    forward and backward at N = 200,000 (one launch each)."""
+    forward, backward and Jacobian diagonal at N = 200,000 (one launch each)."""
     import torch
 
     from paper_2509_13230_gb300 import _native as nat
-    from paper_2509_13230_gb300.sampler import Sampler, expected_bwd, expected_fwd
+    from paper_2509_13230_gb300.sampler import Sampler, expected_bwd, expected_fwd, expected_jacobian_diag
 
     net = workload()
     x = torch.from_numpy(net.x).to(dev)
@@ -401,6 +402,7 @@ def kernels_once(dev):
     _, _, _, px, py, gk, gs = pairwise_inputs(dev)
     expected_fwd(nat.MH_UECM, px, py)
     expected_bwd(nat.MH_UECM, px, py, gk, gs)
+    expected_jacobian_diag(nat.MH_UECM, px, py)
     torch.cuda.synchronize()
     return {"workload": WORKLOAD, "edges_by_seg_target": edges, "pairwise_n": PAIR_N}
 
@@ -409,16 +411,18 @@ def pairwise_leg(args, dev, sm_mhz):
     import torch
 
     from paper_2509_13230_gb300 import _native as nat
-    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd
+    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd, expected_jacobian_diag
 
     rng, x_np, y_np, x, y, gk, gs = pairwise_inputs(dev)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for kind in ("fwd", "bwd"):
+    for kind in ("fwd", "bwd", "jacobian_diag"):
         def call():
             if kind == "fwd":
                 return expected_fwd(nat.MH_UECM, x, y)
+            if kind == "jacobian_diag":
+                return expected_jacobian_diag(nat.MH_UECM, x, y)
             return expected_bwd(nat.MH_UECM, x, y, gk, gs)
         for _ in range(args.warmup):
             call()
@@ -1063,7 +1067,8 @@ def main():
     ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs", "kernels"],
                     default="all",
                     help="run only that leg and print its object; kernels: each profiled kernel once, "
-                         "untimed (walk at T = 8, 16, 32, then pairwise forward and backward), for ncu")
+                         "untimed (walk at T = 8, 16, 32, then pairwise forward, backward, Jacobian "
+                         "diagonal), for ncu")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: default T and block shape, no autotuner")
     ap.add_argument("--seg-target", type=int, default=0,
                     help="headline call: use this seg_target instead of tuning (profiling runs)")
