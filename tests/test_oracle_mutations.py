@@ -116,3 +116,106 @@ def test_planted_bipartite_mistake_is_caught(tmp_path, name, old, new, pin):
             f = ((src == u) & (dst == v)).sum() / S
             zmax = max(zmax, abs(f - p) / np.sqrt(p * (1 - p) / S))
         assert zmax > 6.0
+
+
+# Planted mistakes in the oracle's Jacobian diagonal (Python): each must be
+# rejected by the central-difference pin that the original passes.
+JAC_MUTATIONS = [
+    ("ds_dy_power_of_one_minus_r", "p * r / (y[i] * (1.0 - r) ** 2)", "p * r / (y[i] * (1.0 - r))"),
+    ("dk_dy_missing_y", "math.fsum((p / (y[i] * D)).tolist())", "math.fsum((p / D).tolist())"),
+    ("ds_dx_missing_one_minus_r", "math.fsum((dp_dx / (1.0 - r)).tolist())", "math.fsum(dp_dx.tolist())"),
+    ("dk_dx_missing_one_minus_p", "dp_dx = p * (1.0 - p) / x[i]", "dp_dx = p / x[i]"),
+]
+
+
+def _mutant(func, old, new):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(func))
+    assert src.count(old) == 1, old
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns[func.__name__]
+
+
+def _worst_jacobian_mismatch(jac, model):
+    rng = np.random.default_rng(19)
+    n = 12
+    x = np.exp(rng.normal(-0.5, 1.0, n))
+    y = rng.uniform(0.2, 0.9, n) if model == oracle.UECM else None
+    diag = jac(model, x, y)
+    worst = 0.0
+    for i in range(n):
+        for which, arr in (("x", x), ("y", y)):
+            if arr is None:
+                continue
+            h = 1e-6 * arr[i]
+            up, dn = arr.copy(), arr.copy()
+            up[i] += h
+            dn[i] -= h
+            args = ((up, y), (dn, y)) if which == "x" else ((x, up), (x, dn))
+            (kp, sp), (km, sm) = (oracle.expected_fwd(model, a, b, rows=[i]) for a, b in args)
+            fd = [(kp[0] - km[0]) / (2 * h)] + ([(sp[0] - sm[0]) / (2 * h)] if y is not None else [])
+            got = ([diag[0][i]] + ([diag[2][i]] if y is not None else [])) if which == "x" else \
+                [diag[1][i], diag[3][i]]
+            for f, g in zip(fd, got):
+                worst = max(worst, abs(f - g) / max(1.0, abs(f)))
+    return worst
+
+
+def test_jacobian_diagonal_pin_accepts_the_oracle():
+    for model in (oracle.UBCM, oracle.UECM):
+        assert _worst_jacobian_mismatch(oracle.expected_jacobian_diag, model) < 1e-6
+
+
+@pytest.mark.parametrize("name,old,new", JAC_MUTATIONS, ids=[m[0] for m in JAC_MUTATIONS])
+def test_planted_mistake_in_the_jacobian_diagonal_is_caught(name, old, new):
+    mutant = _mutant(oracle.expected_jacobian_diag, old, new)
+    assert _worst_jacobian_mismatch(mutant, oracle.UECM) > 1e-3
+
+
+# Planted mistakes in the oracle's gradient of the expected sums.
+BWD_MUTATIONS = [
+    ("upstream_k_of_j_dropped", "gk = g_k[i] + g_k[j]", "gk = g_k[i] + 0.0 * g_k[j]"),
+    ("upstream_s_of_j_dropped", "gs = g_s[i] + g_s[j]", "gs = g_s[i] + 0.0 * g_s[j]"),
+    ("dm_dx_missing_one_minus_r", "dm_dx = dp_dx / (1.0 - r)", "dm_dx = dp_dx"),
+    ("dp_dy_wrong_denominator", "dp_dy = p / (y[i] * D)", "dp_dy = p / (y[i] * y[i])"),
+]
+
+
+def _worst_gradient_mismatch(bwd, model):
+    rng = np.random.default_rng(8)
+    n = 12
+    x = np.exp(rng.normal(-0.5, 1.0, n))
+    y = rng.uniform(0.2, 0.9, n) if model == oracle.UECM else None
+    gk = rng.normal(size=n)
+    gs = rng.normal(size=n) if y is not None else None
+
+    def loss(xx, yy):
+        k, s = oracle.expected_fwd(model, xx, yy)
+        return float(np.dot(gk, k) + (np.dot(gs, s) if s is not None else 0.0))
+
+    gx, gy = bwd(model, x, y, gk, gs)
+    worst = 0.0
+    for i in range(n):
+        for arr, g in ((x, gx), (y, gy)):
+            if arr is None:
+                continue
+            h = 1e-6 * arr[i]
+            up, dn = arr.copy(), arr.copy()
+            up[i] += h
+            dn[i] -= h
+            fd = ((loss(up, y) - loss(dn, y)) if arr is x else (loss(x, up) - loss(x, dn))) / (2 * h)
+            worst = max(worst, abs(fd - g[i]) / max(1.0, abs(fd)))
+    return worst
+
+
+def test_gradient_pin_accepts_the_oracle():
+    for model in (oracle.UBCM, oracle.UECM):
+        assert _worst_gradient_mismatch(oracle.expected_bwd, model) < 1e-6
+
+
+@pytest.mark.parametrize("name,old,new", BWD_MUTATIONS, ids=[m[0] for m in BWD_MUTATIONS])
+def test_planted_mistake_in_the_gradient_is_caught(name, old, new):
+    mutant = _mutant(oracle.expected_bwd, old, new)
+    assert _worst_gradient_mismatch(mutant, oracle.UECM) > 1e-3
