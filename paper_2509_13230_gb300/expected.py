@@ -139,14 +139,17 @@ def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int):
 
 
 def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None, y0=None, tol: float = 1e-8,
-        adam_steps: int = 10, lr: float = 0.05, newton_steps: int = 100, cg_iters: int = 12,
+        adam_steps: int = 0, lr: float = 0.05, newton_steps: int = 100, cg_iters: int = 12,
         cg_rtol: float = 0.05, max_step: float = 2.0, verbose: bool = False) -> FitResult:
     """Fit x (UBCM) or x, y (UECM) so that the expected degrees (and strengths)
     equal the targets.  Targets are float64 CUDA tensors with k_i > 0 (and
     s_i > k_i, since every weight is at least 1).
 
-    Adam stage: adam_steps steps on the mean squared relative residual (a
-    warm start; the Newton stage converges from the sparse-limit start too).
+    Adam stage (optional, none by default): adam_steps steps on the mean
+    squared relative residual as a warm start.  From the sparse-limit start the
+    Newton stage alone reached 1e-8 on the N = 2*10^5 degree and strength
+    targets in the same 11 steps as after 10 Adam steps, without their 10
+    forward and 10 backward passes.
     Newton stage: each step solves J d = -(<k> - k, <s> - s) by up to
     cg_iters preconditioned conjugate-gradient iterations (relative residual
     cg_rtol), scales d to at most max_step per log-parameter, and backtracks
