@@ -21,7 +21,8 @@
  * Streams.  All device work is ordered on the given stream (NULL = the
  * legacy default stream).  The sampling calls read back the edge counts and
  * a status word at the end, so they return only after their device work is
- * done; maxent_expected_fwd / _bwd return without synchronising.
+ * done; the maxent_expected_* calls (sums, gradient, row ranges, Jacobian
+ * diagonal) return without synchronising.
  *
  * Errors.  Every call returns MH_OK (0) or a negative MH_ERR_* code; no C++
  * exception crosses the ABI.  mh_error_string() names a code and
@@ -370,9 +371,10 @@ int maxent_expected_jacobian_diag(int model, const double* x, const double* y, i
                                   double* dk_dy, double* ds_dx, double* ds_dy, mh_stream_t stream);
 
 /*
- * maxent_expected_fwd_rows / maxent_expected_bwd_rows — the same sums for the
- * rows i in [row_begin, row_begin + row_count) only (every sum still runs over
- * all j != i), so that ranks can share one call by rows with no reduction:
+ * maxent_expected_fwd_rows / maxent_expected_bwd_rows — the sums of
+ * maxent_expected_fwd / _bwd (Sec. 2.2, Sec. 2.5, Sec. 4) for the rows i in
+ * [row_begin, row_begin + row_count) only (every sum still runs over all
+ * j != i), so that ranks can share one call by rows with no reduction:
  * x, y, g_k, g_s are FP64[n] as above (all rows' values are needed); k_out,
  * s_out, g_x, g_y hold row_count values, entry r for row row_begin + r.  Each
  * value equals, bit for bit, the one the whole call returns for that row.
