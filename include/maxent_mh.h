@@ -77,12 +77,31 @@ typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
 #define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
                              /* caller's stream (see mh_last_call_info); calls of  */
                              /* more than 1024 sample chunks are not timed         */
+#define MH_TEST_WAIT_TIMEOUT 0x400u /* test hook for the bounded device waits: in    */
+                             /* every single-pass scan of the call, tile 1 first    */
+                             /* waits on a device flag that nothing sets; the wait  */
+                             /* gives up after 4096 polls (well under a            */
+                             /* millisecond) exactly as a real look-back wait that  */
+                             /* ran out would, and the scan then finishes normally. */
+                             /* The call returns MH_ERR_DEVICE_TIMEOUT; the device  */
+                             /* stays usable and the next call is unaffected.       */
+                             /* Needs at least 2 scan tiles (2,049 values) to fire. */
 
-/* stats slots (h_stats, 4 x uint64) */
+/* stats slots (h_stats, MH_NUM_STATS x uint64) */
 #define MH_STAT_PROPOSALS 0 /* candidate draws                                     */
 #define MH_STAT_EDGES 1     /* accepted edges                                      */
 #define MH_STAT_SEGMENTS 2  /* segments walked (samples x table rows)              */
-#define MH_STAT_FALLBACKS 3 /* draws the fast filter left to the FP64 path         */
+#define MH_STAT_FALLBACKS 3 /* skip draws the fast levels left to the FP64 path    */
+#define MH_STAT_BOUNDARY 4  /* boundary draws: a skip draw whose FP64 t =           */
+                            /* log(U)/log1p(-q) lies within 8 ulp of an integer m  */
+                            /* with 1 <= m <= b - pos - 1 (the integers that decide */
+                            /* the candidate), or a weight draw whose FP64         */
+                            /* log(U_w)/log(r) >= 0.5 lies within 8 ulp of an      */
+                            /* integer.  Only these draws may decide differently   */
+                            /* from a host FP64 evaluation (the device and host    */
+                            /* log/log1p may differ by an ulp); every other draw   */
+                            /* is decided as in FP64 (Sec. 2.3 skip, Eq. 4)        */
+#define MH_NUM_STATS 5
 
 typedef struct mh_params {
     uint64_t seed;         /* Philox key: (seed lo32, seed hi32 + network_id)       */
@@ -151,7 +170,7 @@ int mh_workspace_size(int model, int64_t n, const mh_params* params, int64_t cap
  *   capacity_edges    length of each edge output array (< 2^31 with
  *                     MH_CSR_SYMMETRIC)
  *   h_edges_per_sample host int64[num_samples]: edges of each sample
- *   h_stats           host uint64[4] (MH_STAT_*), or NULL
+ *   h_stats           host uint64[MH_NUM_STATS] (MH_STAT_*), or NULL
  *
  * On MH_ERR_CAPACITY the exact counts are in h_edges_per_sample and nothing
  * past capacity_edges was written; re-calling with more room reproduces the
@@ -284,7 +303,7 @@ int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_par
  *                    entries
  *   csr_indices, csr_weights  int32[capacity_edges]
  *   h_edges_per_pair host int64[pair_count]: edges of each pair
- *   h_stats          host uint64[4] (MH_STAT_*) of the wave, or NULL
+ *   h_stats          host uint64[MH_NUM_STATS] (MH_STAT_*) of the wave, or NULL
  * pair_count must be >= 1 and at most 2^20.  MH_ERR_WORKSPACE when the
  * wave has more than max_wave_items work items or the workspace is too
  * small; MH_ERR_CAPACITY as for the single-network calls (exact counts are
@@ -310,11 +329,17 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
  * Arguments as mh_sample_ubcm (no workspace).  Limits: the call's
  * mh_workspace_size must fit in the 64 MiB (about n <= 50,000 with a few
  * million edges; otherwise MH_ERR_WORKSPACE, use mh_sample_ubcm),
- * num_samples <= 1024, no MH_TIMING.  The first call on a device looks up
- * the scratch's device address; make it before any stream capture, and do
- * not call it inside a capture.  Calls share the scratch: the library
- * serialises them with a process-wide lock and each returns after its
- * device work, so calls through this function never overlap on a GPU.
+ * num_samples <= 1024 (otherwise MH_ERR_ARG), no MH_TIMING, no
+ * MH_CSR_SYMMETRIC.  The first call on a device looks up the scratch's
+ * device address and, unless another call already did, builds the library's
+ * logarithm table on the caller's stream; make it before any stream capture.
+ * Called inside a capture it returns MH_ERR_ARG and enqueues nothing.  Calls
+ * share the scratch: the library serialises them with a process-wide lock
+ * and each returns after its device work (also on an error return), so
+ * calls through this function never overlap on a GPU; any other kernel
+ * that wrote the scratch would race with them.  Each call clears what it
+ * reads before it writes it, so calls of any size may follow one another.
+ * mh_last_call_info describes the call (launches, sample chunks).
  * Output is bit-identical to mh_sample_ubcm with the same arguments.
  */
 int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_params* params, int32_t* src, int32_t* dst,

@@ -78,6 +78,10 @@ def _declare(lib):
     lib.orc_bip_sample.restype = i64
     lib.orc_bip_bf_sample.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, u64, u32, vp, vp, vp, i64, vp]
     lib.orc_bip_bf_sample.restype = i64
+    lib.orc_boundary_log.argtypes = [vp, i64]
+    lib.orc_boundary_log.restype = None
+    lib.orc_boundary_log_len.argtypes = []
+    lib.orc_boundary_log_len.restype = i64
     return lib
 
 
@@ -149,8 +153,10 @@ def mh_sample(model, x, y=None, *, seed=0, network_id=0, sample_begin=0, num_sam
               flags=0, lib=None):
     """Serial Miller-Hagberg samples.  Returns (src, dst, w or None, counts, stats).
 
-    stats = [proposals drawn, edges, segments walked, draws within 8 ulp of an
-    integer boundary of the skip or weight].
+    stats = [proposals drawn, edges, segments walked, boundary draws]: a
+    boundary draw is a skip draw whose t lies within 8 ulp of an integer m in
+    [1, b - pos - 1], or a weight draw whose t >= 0.5 lies within 8 ulp of an
+    integer (``boundary_draws`` lists them).
     """
     lib = lib or load()
     x = _f64(x)
@@ -171,6 +177,25 @@ def mh_sample(model, x, y=None, *, seed=0, network_id=0, sample_begin=0, num_sam
         if total <= cap:
             return (src[:total], dst[:total], None if w is None else w[:total], counts[:num_samples], stats)
         cap = int(total)
+
+
+def boundary_draws(sample_fn, *args, max_entries=1 << 16, **kw):
+    """Runs ``sample_fn(*args, **kw)`` (``mh_sample`` or ``bip_sample``) with
+    the oracle's boundary-draw log on.  Returns (its result, log) where log is
+    an int64 array of rows (sample, row rank i, segment k, kind, index):
+    kind 0 is the skip draw ``index`` of that segment, kind 1 the weight draw
+    of its edge ``index``."""
+    lib = kw.get("lib") or load()
+    buf = np.zeros(5 * max_entries, np.uint32)
+    lib.orc_boundary_log(_ptr(buf), max_entries)
+    try:
+        res = sample_fn(*args, **kw)
+        m = int(lib.orc_boundary_log_len())
+    finally:
+        lib.orc_boundary_log(None, 0)
+    if m > max_entries:
+        raise RuntimeError(f"{m} boundary draws, more than the log's {max_entries} entries")
+    return res, buf[:5 * m].reshape(m, 5).astype(np.int64)
 
 
 def bf_sample(model, x, y=None, *, seed=0, sample=0, lib=None):

@@ -95,13 +95,44 @@ static double unit_open1(uint32_t hi, uint32_t lo)
 
 /* A draw lands on an integer boundary when it is within 8 ulp of one.  The
  * CUDA and C library logarithms may differ there by an ulp or two, so these
- * draws are counted (they are the only ones allowed to decide differently). */
+ * draws are counted (they are the only ones allowed to decide differently).
+ * A skip draw counts only when the integer is one that decides the
+ * candidate, m in [1, b - pos - 1]: beyond that every t ends the segment. */
 static int near_integer(double t)
 {
     if (!(t >= 0.5) || !isfinite(t)) return 0;
     double m = nearbyint(t);
     double ulp = nextafter(t, INFINITY) - t;
     return fabs(t - m) <= 8.0 * ulp;
+}
+
+/* Optional log of the boundary draws, for tests that trace a difference
+ * between two samplers to the segment it came from.  Entry: sample, row
+ * rank i, segment k, kind (0 skip draw, 1 weight draw), draw or edge index. */
+static uint32_t* boundary_log = NULL;
+static int64_t boundary_log_cap = 0, boundary_log_len = 0;
+
+void orc_boundary_log(uint32_t* buf, int64_t cap_entries)
+{
+    boundary_log = buf;
+    boundary_log_cap = buf ? cap_entries : 0;
+    boundary_log_len = 0;
+}
+
+int64_t orc_boundary_log_len(void) { return boundary_log_len; }
+
+static void boundary_hit(uint64_t* stats, uint32_t sample, int64_t i, int32_t k, uint32_t kind, uint32_t index)
+{
+    stats[ORC_ST_BOUNDARY] += 1;
+    if (boundary_log_len < boundary_log_cap) {
+        uint32_t* e = boundary_log + 5 * boundary_log_len;
+        e[0] = sample;
+        e[1] = (uint32_t)i;
+        e[2] = (uint32_t)k;
+        e[3] = kind;
+        e[4] = index;
+    }
+    boundary_log_len += 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -449,7 +480,7 @@ static void walk_segment(const net_t* g, const uint32_t key[2], uint32_t sample,
         double V = unit_open1(rnd[3], rnd[2]);
         double R = (double)(b - pos - 1);
         double t = (q >= 1.0) ? 0.0 : log(U) / log1p(-q);
-        if (near_integer(t)) out->stats[ORC_ST_BOUNDARY] += 1;
+        if (near_integer(t) && nearbyint(t) <= R) boundary_hit(out->stats, sample, i, k, 0, d - 1);
         if (t >= R) break;
         int64_t j = pos + 1 + (int64_t)floor(t);
         double p = prob(g, i, j);
@@ -463,7 +494,7 @@ static void walk_segment(const net_t* g, const uint32_t key[2], uint32_t sample,
                 double r = g->ys[i] * g->ys[j];
                 if (r > 0.0) {
                     double tw = log(Uw) / log(r);
-                    if (near_integer(tw)) out->stats[ORC_ST_BOUNDARY] += 1;
+                    if (near_integer(tw)) boundary_hit(out->stats, sample, i, k, 1, e);
                     if (tw >= 2147483646.0) {
                         wt = 2147483647;
                         out->weight_overflow = 1;
@@ -766,7 +797,7 @@ static void bip_walk_segment(const bip_t* B, const uint32_t key[2], uint32_t sam
         double V = unit_open1(rnd[3], rnd[2]);
         double R = (double)(vb - pos - 1);
         double t = (q >= 1.0) ? 0.0 : log(U) / log1p(-q);
-        if (near_integer(t)) out->stats[ORC_ST_BOUNDARY] += 1;
+        if (near_integer(t) && nearbyint(t) <= R) boundary_hit(out->stats, sample, i, k, 0, d - 1);
         if (t >= R) break;
         int64_t jv = pos + 1 + (int64_t)floor(t);
         int64_t j = bip_actual(jv, ex);
@@ -781,7 +812,7 @@ static void bip_walk_segment(const bip_t* B, const uint32_t key[2], uint32_t sam
                 double r = B->R.ys[i] * B->C.ys[j];
                 if (r > 0.0) {
                     double tw = log(Uw) / log(r);
-                    if (near_integer(tw)) out->stats[ORC_ST_BOUNDARY] += 1;
+                    if (near_integer(tw)) boundary_hit(out->stats, sample, i, k, 1, e);
                     if (tw >= 2147483646.0) {
                         wt = 2147483647;
                         out->weight_overflow = 1;

@@ -31,11 +31,14 @@ MH_DIRECTED = 0x40
 MH_CSR_SYMMETRIC = 0x80
 MH_FP64_ONLY = 0x100
 MH_TIMING = 0x200
+MH_TEST_WAIT_TIMEOUT = 0x400
 
 MH_STAT_PROPOSALS = 0
 MH_STAT_EDGES = 1
 MH_STAT_SEGMENTS = 2
 MH_STAT_FALLBACKS = 3
+MH_STAT_BOUNDARY = 4
+MH_NUM_STATS = 5
 
 # Every symbol include/maxent_mh.h declares.
 EXPORTED = (

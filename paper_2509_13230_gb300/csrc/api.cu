@@ -98,7 +98,7 @@ thread_local PinnedBuffer g_pinned;
 
 constexpr uint32_t kKnownFlags =
     MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_DIRECTED | MH_CSR_SYMMETRIC | MH_FP64_ONLY |
-    MH_TIMING;
+    MH_TIMING | MH_TEST_WAIT_TIMEOUT;
 
 }  // namespace
 
@@ -475,7 +475,8 @@ static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_para
   c.staging = reinterpret_cast<int32_t*>(ws + L.staging);
   c.sample_counts = reinterpret_cast<long long*>(ws + L.sample_counts);
   const ScanState scan_state{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
-                             reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
+                             reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles,
+                             (p->flags & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
   c.scan_state = const_cast<ScanState*>(&scan_state);
   c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
@@ -716,7 +717,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   memcpy(&hc, hbuf, sizeof(Ctrl));
   memcpy(h_counts, hbuf + sizeof(Ctrl), counts_bytes);
   if (h_stats)
-    for (int t = 0; t < 4; ++t) h_stats[t] = hc.stats[t];
+    for (int t = 0; t < MH_NUM_STATS; ++t) h_stats[t] = hc.stats[t];
   rc = status_to_code(hc.status, hc.num_segments, L.max_segments);
   if (rc != MH_OK) return rc;
   int64_t total = 0;

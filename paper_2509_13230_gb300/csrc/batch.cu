@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(BatchView V) {
     wc->stage_used = 0;
     wc->out_base = 0;
     wc->out_end = 0;
-    for (int k = 0; k < 4; ++k) wc->stats[k] = 0;
+    for (int k = 0; k < MH_NUM_STATS; ++k) wc->stats[k] = 0;
     const bool run = status == 0;
     wc->wave_items = run ? items_total : 0;
     wc->model_items[0] = run ? model_total[0] : 0;
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
   if (wc->stage_used > static_cast<unsigned long long>(P.staging_cap)) return;  // staging overflowed
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
   const bool csr = P.o.csr_idx != nullptr;
-  unsigned long long fallbacks = 0;
+  unsigned long long fallbacks = 0, boundary = 0;  // weight draws left to FP64; boundary draws
   bool overflow = false, bad = false;
   for (long long it0 = static_cast<long long>(blockIdx.x) * kBatchEmitItems; it0 < items;
        it0 += static_cast<long long>(gridDim.x) * kBatchEmitItems) {
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
         const float2 lj = g.lny[gj];
         wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
                          it.sample, P.key0, it.key1, it.yi, &g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
-                         tab, fp64_only, overflow, fallbacks);
+                         tab, fp64_only, overflow, fallbacks, boundary);
       }
       if (pos < P.o.capacity && P.o.src) {
         P.o.src[pos] = it.u;
@@ -648,6 +648,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
   }
   if (overflow) atomicOr(&wc->status, kStOverflow);
   if (bad) atomicOr(&wc->status, kStInternal);
+  if (boundary) atomicAdd(&wc->stats[MH_STAT_BOUNDARY], boundary);
   (void)fallbacks;
 }
 
@@ -1203,7 +1204,8 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
   c.items_max = items_max;
   c.walk_ctas_per_sm = static_cast<int>(params->walk_ctas_per_sm);
   const ScanState scan_state{reinterpret_cast<unsigned*>(ws + B.scan_flags), ws + B.scan_values,
-                             reinterpret_cast<unsigned*>(ws + B.scan_counters), wc, B.scan_tiles};
+                             reinterpret_cast<unsigned*>(ws + B.scan_counters), wc, B.scan_tiles,
+                             (fl & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
   long long* pair_counts = reinterpret_cast<long long*>(ws + B.pair_counts);
   const bool timed = (fl & MH_TIMING) != 0;
 
@@ -1316,7 +1318,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
   memcpy(&hc, hback, sizeof(Ctrl));
   memcpy(h_edges_per_pair, hback + sizeof(Ctrl), 8 * static_cast<size_t>(pair_count));
   if (h_stats)
-    for (int k = 0; k < 4; ++k) h_stats[k] = hc.stats[k];
+    for (int k = 0; k < MH_NUM_STATS; ++k) h_stats[k] = hc.stats[k];
   if (hc.status & kStNotPrepared) {
     set_error("the workspace does not hold mh_batch_prepare's result for these networks and params");
     return MH_ERR_ARG;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   const bool uecm = g.model == MH_UECM;
   if (uecm && P.mode != kEmitSymForward) ln_table_to_shared(tab, g.lntab);
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
-  unsigned long long fallbacks = 0;
+  unsigned long long fallbacks = 0, boundary = 0;  // weight draws left to FP64; boundary draws
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   const long long items = S * P.c.chunk_samples;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
         const float2 lj = g.lny[j];
         wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
                          P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
-                         df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks);
+                         df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks, boundary);
       }
       if (pos < P.o.capacity) {
         if (P.o.src) {
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   }
   if (overflow) atomicOr(&ctrl->status, kStOverflow);
   if (bad) atomicOr(&ctrl->status, kStInternal);
+  if (boundary) atomicAdd(&ctrl->stats[MH_STAT_BOUNDARY], boundary);
   (void)fallbacks;
 }
 

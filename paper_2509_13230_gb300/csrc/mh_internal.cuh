@@ -40,7 +40,7 @@ struct Ctrl {
   unsigned long long overflow_count;  // items re-walked by the overflow kernel
   long long out_base;           // edges emitted by earlier sample chunks
   long long out_end;            // edges emitted including the current chunk
-  unsigned long long stats[4];  // MH_STAT_* counters
+  unsigned long long stats[MH_NUM_STATS];  // MH_STAT_* counters
   unsigned long long ticket2;   // batched waves: work-queue ticket of the UECM walk
   long long wave_items;         // batched waves: work items of the wave
   long long model_items[2];     // batched waves: work items of the UBCM / UECM queues
@@ -209,7 +209,7 @@ cudaError_t sort_kernel_attributes(int dev);  // before any capture
 // Device copy of the logarithm table of the current device, built on first
 // use (a launch and a synchronisation: never while a stream is captured);
 // NULL if it could not be built.
-LnEntry* ln_table_ptr();
+LnEntry* ln_table_ptr(cudaStream_t s = nullptr);  // per-device table, built on first use
 // Stable LSD sort of `len` (key, value) pairs on the 8-bit digits at the
 // given shifts, `*dev_len` of them (at most host_len) present; the result
 // is in buffer 0 or 1 as returned through *out_buf.  `st` is the scan state.

@@ -11,7 +11,9 @@
 // Scratch.  A file-scope __device__ array of kNoAllocScratchBytes (64 MiB),
 // which every GPU that loads the library holds until the process exits.  The
 // first call on a device looks up its device address (cudaGetSymbolAddress)
-// with that device current; make that first call before any stream capture.
+// with that device current and, if no other call has yet, builds the
+// library's logarithm table with one kernel on the caller's stream; make that
+// first call before any stream capture (a call inside a capture is refused).
 // Calls share the array: a process-wide lock serialises them and each call
 // returns only after its device work is done, so calls through this entry
 // point never overlap on a GPU; any other writer of the array would race.
@@ -39,6 +41,11 @@ alignas(64) char g_noalloc_host[sizeof(Ctrl) + 8 * kNoAllocMaxSamples];
 }  // namespace
 }  // namespace mh
 
+namespace mh {
+int64_t take_launch_count();
+void record_call_info(const mh_call_info& info);
+}  // namespace mh
+
 using namespace mh;
 
 extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_params* params, int32_t* src,
@@ -46,6 +53,7 @@ extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_param
                                       int64_t capacity_edges, int64_t* h_edges_per_sample, uint64_t* h_stats,
                                       mh_stream_t stream) {
   std::lock_guard<std::mutex> guard(g_noalloc_lock);
+  record_call_info(mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0});  // this call's info, filled below
   int rc = check_sample_params(MH_UBCM, n, params);
   if (rc != MH_OK) return rc;
   if (!x || !h_edges_per_sample || capacity_edges < 0) {
@@ -94,15 +102,28 @@ extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_param
     g_noalloc_ptr[dev] = ptr;
   }
   char* ws = static_cast<char*>(g_noalloc_ptr[dev]);
-  const Net g = net_view(MH_UBCM, *params, x, nullptr, n, L, ws);
-  if (!g.lntab) {
+  // the device's logarithm table, built on the caller's stream the first time
+  // (no stream of the library's own is created here)
+  if (!ln_table_ptr(s)) {
     set_error("the logarithm table could not be built on this device");
     return MH_ERR_CUDA;
   }
+  const Net g = net_view(MH_UBCM, *params, x, nullptr, n, L, ws);
   const Outputs o{src, dst, nullptr, reinterpret_cast<long long*>(csr_offsets), csr_indices, nullptr,
                   capacity_edges};
+  take_launch_count();
   rc = enqueue_sample_direct(g, L, ws, params, o, g_noalloc_host, s);
-  if (rc != MH_OK) return rc;
+  if (rc != MH_OK) {
+    // kernels already queued may still write the shared scratch: let them
+    // finish before the lock is released, so calls never overlap
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  mh_call_info info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
+  info.kernel_launches = take_launch_count();
+  info.sample_chunks = (params->num_samples + L.spc - 1) / L.spc;
+  info.walk_launches = info.sample_chunks;
+  record_call_info(info);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_error("cudaStreamSynchronize failed: %s", cudaGetErrorString(e));
@@ -113,7 +134,7 @@ extern "C" int mh_sample_ubcm_noalloc(const double* x, int64_t n, const mh_param
   const size_t counts_bytes = 8 * static_cast<size_t>(params->num_samples);
   memcpy(h_edges_per_sample, g_noalloc_host + sizeof(Ctrl), counts_bytes);
   if (h_stats)
-    for (int t = 0; t < 4; ++t) h_stats[t] = hc.stats[t];
+    for (int t = 0; t < MH_NUM_STATS; ++t) h_stats[t] = hc.stats[t];
   rc = status_code(hc.status, hc.num_segments, L.max_segments);
   if (rc != MH_OK) return rc;
   int64_t total = 0;

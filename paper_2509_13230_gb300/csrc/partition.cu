@@ -274,7 +274,8 @@ __global__ void export_table_kernel(const int4* __restrict__ seg, const Ctrl* ct
 
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
   const ScanState st{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
-                     reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles};
+                     reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles,
+                     (g.flags & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
   cudaError_t e;
   // Q = exclusive prefix of the fixed-point costs, Q[n] = total.
   e = scan_any<unsigned long long, SumOp<unsigned long long>>(g.Q, g.Q, ScanLen{g.n, nullptr, 1}, true,

@@ -212,16 +212,38 @@ cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T*
 // finish clears the tile states and tickets for the next scan.
 constexpr unsigned kSpinLimit = 1u << 22;
 
+__device__ __forceinline__ unsigned poll_flag(const unsigned* f) {
+  return *reinterpret_cast<const volatile unsigned*>(f);
+}
+
 struct ScanState {
   unsigned* flags;     // per tile: 0 empty, 1 aggregate published, 2 inclusive prefix published
   void* values;        // 2 x tiles values of the scanned type: aggregates, then inclusive prefixes
   unsigned* counters;  // [0] tile ticket, [1] finished blocks
   Ctrl* ctrl;          // status word for timeouts
   int64_t max_tiles;   // capacity of `values` (per half)
+  unsigned test_stuck_polls = 0;  // MH_TEST_WAIT_TIMEOUT: tile 1 first waits this long on a flag never set
 };
 
-__device__ __forceinline__ unsigned poll_flag(const unsigned* f) {
-  return *reinterpret_cast<const volatile unsigned*>(f);
+// Polls for the MH_TEST_WAIT_TIMEOUT hook; the hook's wait gives up after these.
+constexpr unsigned kTestStuckPolls = 4096u;
+
+// A device word that nothing ever writes: the MH_TEST_WAIT_TIMEOUT hook
+// waits on it, so that wait can only end by running out of polls.
+static __device__ unsigned g_never_set = 0u;
+
+// The hook's wait: the same bounded poll as the look-back's, on a flag that
+// is never set, so it always gives up and records kStTimeout.  The scan then
+// goes on with its real look-back, so its output stays correct.
+__device__ __forceinline__ void test_stuck_wait(Ctrl* ctrl, unsigned polls) {
+  for (unsigned it = 0;; ++it) {
+    if (poll_flag(&g_never_set) != 0u) return;
+    if (it >= polls) {
+      atomicOr(&ctrl->status, kStTimeout);
+      return;
+    }
+    __nanosleep(32);
+  }
 }
 
 // Loads through L2 (a value another block published after a fence).
@@ -325,6 +347,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in,
           __threadfence();
           atomicExch(&st.flags[tile], 1u);
         }
+        if (st.test_stuck_polls && tile == 1 && threadIdx.x == 0) test_stuck_wait(st.ctrl, st.test_stuck_polls);
         __syncwarp();
         prefix = warp_look_back<T, Op>(tile, st.flags, agg_v, inc_v, st.ctrl);
       }

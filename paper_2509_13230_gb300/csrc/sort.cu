@@ -18,6 +18,9 @@
 //    of all keys) copy instead of ranking, so the buffer parity never depends
 //    on the data.
 // The same radix kernels sort the symmetric CSR layout's (sample, rank) keys.
+#include <atomic>
+#include <mutex>
+
 #include "mh_internal.cuh"
 #include "scan.cuh"
 #include "walk_math.cuh"
@@ -821,22 +824,30 @@ __global__ void ln_table_kernel(LnEntry* tab) {
 
 }  // namespace
 
-LnEntry* ln_table_ptr() {
-  static LnEntry* ptr[64] = {};
+// The table is built once per device, under a lock (calls on several host
+// threads may race to build it), by one kernel on `s` (or on a stream of its
+// own when s is null), waited for before the pointer is published.
+LnEntry* ln_table_ptr(cudaStream_t s) {
+  static std::atomic<LnEntry*> ptr[64];
+  static std::mutex build_lock;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!ptr[dev]) {
-    void* p = nullptr;
-    cudaStream_t st = nullptr;
-    if (cudaGetSymbolAddress(&p, g_ln_table) != cudaSuccess) return nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    ln_table_kernel<<<(kLnTable + 255) / 256, 256, 0, st>>>(static_cast<LnEntry*>(p));
-    const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
-    cudaStreamDestroy(st);
-    if (!ok) return nullptr;
-    ptr[dev] = static_cast<LnEntry*>(p);
-  }
-  return ptr[dev];
+  LnEntry* p = ptr[dev].load(std::memory_order_acquire);
+  if (p) return p;
+  std::lock_guard<std::mutex> guard(build_lock);
+  p = ptr[dev].load(std::memory_order_acquire);
+  if (p) return p;
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_ln_table) != cudaSuccess) return nullptr;
+  cudaStream_t st = s;
+  if (!st && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  ln_table_kernel<<<(kLnTable + 255) / 256, 256, 0, st>>>(static_cast<LnEntry*>(sym));
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  if (!s) cudaStreamDestroy(st);
+  if (!ok) return nullptr;
+  p = static_cast<LnEntry*>(sym);
+  ptr[dev].store(p, std::memory_order_release);
+  return p;
 }
 
 cudaError_t launch_validate_keys(const Net& g, unsigned long long* keys, int32_t* vals, unsigned* ghist, Ctrl* ctrl,

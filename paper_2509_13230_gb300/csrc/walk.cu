@@ -128,7 +128,7 @@ struct SegWalker {
   template <bool kUecm, bool kExcl = false>
   __device__ __forceinline__ bool advance(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
                                           bool init_prev, const LnEntry* tab, unsigned long long& fallbacks,
-                                          bool& accepted, int32_t& j) {
+                                          unsigned long long& boundary, bool& accepted, int32_t& j) {
     accepted = false;
     const bool head = fresh;
     if (kExcl && head && a >= b) return false;  // the segment held only the excluded candidate
@@ -165,7 +165,7 @@ struct SegWalker {
           qc = q64(g, kUecm);
           have_qc = true;
         }
-        skip = skip_fp64(top53(r.y, r.x) + 1ull, qc, room);
+        skip = skip_fp64(top53(r.y, r.x) + 1ull, qc, room, boundary);
       }
       if (skip >= static_cast<unsigned>(room)) return false;
       jv = pos + 1 + static_cast<int32_t>(skip);
@@ -199,11 +199,11 @@ struct SegWalker {
     qj = j;
     if (!kUecm) {
       zq = prod;
-      fast = prod.hi > 0x1p-100f && prod.hi < 0x1p40f;
+      fast = prod.hi > 0x1p-100f && prod.hi < kFastZq;
       q_f = __fdividef(prod.hi, 1.0f + prod.hi);
     } else {
       zq = df_mul(prod, inv1mc);
-      fast = zq.hi > 0x1p-100f && zq.hi < 0x1p40f && omc_f >= 0x1p-20f;
+      fast = zq.hi > 0x1p-100f && zq.hi < kFastZq && omc_f >= 0x1p-20f;
       q_f = __fdividef(prod.hi, omc_f + prod.hi);
     }
     lam_f = fast ? log1p_f(zq, tab) : 1.0f;
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   unsigned long long next = 0, end = 0;     // warp-uniform work cursor
   unsigned long long wbase = 0, wleft = 0;  // warp-uniform staging chunk
   bool work_left = total > 0;
-  unsigned long long n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0;
+  unsigned long long n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0, n_boundary = 0;
 
   while (true) {
     if (work_left) {
@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
     if (active) {
       bool acc;
       int32_t j;
-      if (wk.advance<kUecm, kExcl>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback, acc,
-                                   j)) {
+      if (wk.advance<kUecm, kExcl>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback,
+                                   n_boundary, acc, j)) {
         if (acc) {
           if (!rewalk) {
             if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
@@ -439,12 +439,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
     n_edges += __shfl_xor_sync(0xffffffffu, n_edges, dd);
     n_segs += __shfl_xor_sync(0xffffffffu, n_segs, dd);
     n_fallback += __shfl_xor_sync(0xffffffffu, n_fallback, dd);
+    n_boundary += __shfl_xor_sync(0xffffffffu, n_boundary, dd);
   }
   if (lane == 0) {
     atomicAdd(&ctrl->stats[MH_STAT_PROPOSALS], n_draws);
     atomicAdd(&ctrl->stats[MH_STAT_EDGES], n_edges);
     atomicAdd(&ctrl->stats[MH_STAT_SEGMENTS], n_segs);
     atomicAdd(&ctrl->stats[MH_STAT_FALLBACKS], n_fallback);
+    if (n_boundary) atomicAdd(&ctrl->stats[MH_STAT_BOUNDARY], n_boundary);
   }
 }
 

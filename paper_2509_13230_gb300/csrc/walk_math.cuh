@@ -28,11 +28,27 @@
 // path above, so decisions equal the canonical ones except where the device
 // and host FP64 logarithms themselves round differently (draws within a few
 // ulp of an integer boundary).
+//
+// Fast range.  lambda above is the exact -ln(1 - q) of the exact q, while
+// the canonical t divides by log1p(-fl(q)): q = z / (1 + z) carries two
+// roundings, fl(q) = q (1 + eps) with |eps| <= 2^-52, and 1 - fl(q) =
+// (1 - q)(1 - z eps).  The canonical lambda is therefore off by a relative
+// z 2^-52 / ln(1 + z) (z = x_i x_j, or A / fl(1 - c) for the UECM bound),
+// which grows without limit in z: 2^-36 at z = 2^21.  The fast levels take
+// only q with z < kFastZq = 2^16, where that term is at most 2^-39.5, below a
+// ninth of the double-float margin (and far below the FP32 one); larger z go
+// to the canonical FP64 path.  The acceptance quotient p/q and the weight's
+// ln r carry no such term (p/q is a ratio of two values near 1 with relative
+// errors of a few 2^-53; fl(y_i y_j) moves ln r by at most 2^-53 against
+// |ln r| >= 2^-12 on the fast path).
 #pragma once
 
 #include "mh_internal.cuh"
 
 namespace mh {
+
+// Largest z (x_i x_j, or A / (1 - c)) whose q the fast levels decide.
+constexpr float kFastZq = 0x1p16f;
 
 // ---- canonical FP64 values ----------------------------------------------------
 __device__ __forceinline__ double prob_ubcm(double xi, double xj) {
@@ -333,11 +349,26 @@ __device__ __forceinline__ int floor_decided_f(float t, int room, unsigned& fl) 
   return 1;
 }
 
-// Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.
-static __device__ __noinline__ unsigned skip_fp64(unsigned long long N, double q, int room) {
+// A boundary draw: t >= 0.5 lies within 8 ulp of an integer.  The device
+// and host FP64 log / log1p may round differently only for such draws, so
+// they are counted (MH_STAT_BOUNDARY); the same rule as the oracle's.
+__device__ __forceinline__ bool near_integer(double t) {
+  if (!(t >= 0.5) || !isfinite(t)) return false;
+  // ulp of a positive normal t: 2^(exponent - 52), the step to the next double up
+  const double ulp = __longlong_as_double(__double_as_longlong(t) & 0x7FF0000000000000ll) * 0x1p-52;
+  return fabs(t - rint(t)) <= 8.0 * ulp;
+}
+
+// Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.  A draw
+// near an integer m in [1, room] (one that decides the candidate) is counted
+// in `boundary`.  Every such draw reaches this function: the fast levels
+// decide only draws whose t lies farther than their margins from an integer.
+static __device__ __noinline__ unsigned skip_fp64(unsigned long long N, double q, int room,
+                                                  unsigned long long& boundary) {
   if (q >= 1.0) return 0;
   const double U = static_cast<double>(N) * 0x1p-53;
   const double t = log(U) / log1p(-q);
+  if (near_integer(t) && rint(t) <= static_cast<double>(room)) boundary += 1;
   if (t >= static_cast<double>(room)) return static_cast<unsigned>(room);
   return static_cast<unsigned>(floor(t));
 }
@@ -358,9 +389,11 @@ __device__ __forceinline__ int accept_decided(unsigned long long mV, float p_f, 
 // from Philox {2^31 | e/2, k, i, s}, words (1,0) for even e and (3,2) for odd
 // e.  lny_i + lny_j approximates ln r in double-float (per-node ln y); the
 // FP64 path computes log(U_w) / log(fl(y_i y_j)).
-static __device__ __noinline__ int32_t weight_fp64(unsigned long long N, double r, bool& overflow) {
+static __device__ __noinline__ int32_t weight_fp64(unsigned long long N, double r, bool& overflow,
+                                                   unsigned long long& boundary) {
   if (!(r > 0.0)) return 1;
   const double tw = log(static_cast<double>(N) * 0x1p-53) / log(r);
+  if (near_integer(tw)) boundary += 1;
   if (tw >= 2147483646.0) {
     overflow = true;
     return 2147483647;
@@ -373,7 +406,7 @@ static __device__ __noinline__ int32_t weight_fp64(unsigned long long N, double 
 __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t i, uint32_t sample, uint32_t key0,
                                                uint32_t key1, double yi, const double* yj, df2 lnyi, df2 lnyj,
                                                const LnEntry* tab, bool fp64_only, bool& overflow,
-                                               unsigned long long& fallbacks) {
+                                               unsigned long long& fallbacks, unsigned long long& boundary) {
   const uint4 w = philox4x32_10(make_uint4(0x80000000u | (e >> 1), k, i, sample), key0, key1);
   const unsigned long long N = (e & 1u) ? top53(w.w, w.z) + 1ull : top53(w.y, w.x) + 1ull;
   const df2 nlr = df_add(lnyi, lnyj);  // ln r (negative)
@@ -398,7 +431,7 @@ __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t 
     if (t.hi < 2.0e9f && floor_decided(t, 0x7FFFFFFF, fl)) return 1 + static_cast<int32_t>(fl);
   }
   fallbacks += 1;
-  return weight_fp64(N, yi * *yj, overflow);
+  return weight_fp64(N, yi * *yj, overflow, boundary);
 }
 
 }  // namespace mh

@@ -73,7 +73,7 @@ class WaveResult:
     pair_begin: int
     pair_count: int
     counts: np.ndarray                        # int64[pair_count]
-    stats: np.ndarray                         # uint64[4]
+    stats: np.ndarray                         # uint64[5] (MH_STAT_*)
     networks: np.ndarray                      # int64[pair_count]: network of each pair
     samples: np.ndarray                       # int64[pair_count]: sample index of each pair (0-based)
     src: torch.Tensor | None = None
@@ -224,7 +224,7 @@ class Ensemble:
         """Draws pairs [first, first + count); returns (return code, result)."""
         self._ensure_csr_offsets(self._csr_len(first, count))
         counts = np.zeros(count, dtype=np.int64)
-        stats = np.zeros(4, dtype=np.uint64)
+        stats = np.zeros(nat.MH_NUM_STATS, dtype=np.uint64)
         rc = nat.mh_sample_batched(self.descs, len(self.entries), self.params, self.max_wave_items, _ptr(self.ws),
                                    self.ws.numel(), first, count, _ptr(self.src), _ptr(self.dst), _ptr(self.w),
                                    _ptr(self.csr_off), _ptr(self.csr_idx), _ptr(self.csr_w), self.capacity,
@@ -259,7 +259,7 @@ class Ensemble:
             self.prepare(stream)
         end = len(self.entries) * self.num_samples if pair_end is None else pair_end
         counts = np.zeros(end - pair_begin, dtype=np.int64)
-        stats = np.zeros(4, dtype=np.uint64)
+        stats = np.zeros(nat.MH_NUM_STATS, dtype=np.uint64)
         todo = self.plan(pair_begin, end)
         self.waves_run = 0
         while todo:

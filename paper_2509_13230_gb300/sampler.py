@@ -39,7 +39,7 @@ def _check_vec(name: str, t: torch.Tensor, n: int | None = None) -> torch.Tensor
 class SampleResult:
     """Edges of a sampling call; tensors are views trimmed to the edge total."""
     counts: np.ndarray          # int64[num_samples]
-    stats: np.ndarray           # uint64[4]: proposals, edges, segments, fallbacks
+    stats: np.ndarray           # uint64[5]: proposals, edges, segments, fallbacks, boundary draws
     src: torch.Tensor | None = None
     dst: torch.Tensor | None = None
     w: torch.Tensor | None = None
@@ -126,7 +126,7 @@ class Sampler:
         self.csr_idx = torch.empty(per_edge * cap, dtype=torch.int32, device=dev) if csr else None
         self.csr_w = torch.empty(per_edge * cap, dtype=torch.int32, device=dev) if csr and weighted else None
         self.h_counts = np.zeros(self.num_samples, dtype=np.int64)
-        self.h_stats = np.zeros(4, dtype=np.uint64)
+        self.h_stats = np.zeros(nat.MH_NUM_STATS, dtype=np.uint64)
         # host pointers passed on every call, converted once
         self._h_counts_p = self.h_counts.ctypes.data_as(ctypes.c_void_p)
         self._h_stats_p = self.h_stats.ctypes.data_as(ctypes.c_void_p)

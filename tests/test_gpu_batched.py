@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from parity import assert_traced, check_sample, oracle_sample, same_sample
 from paper_2509_13230_gb300 import _native as nat
 from paper_2509_13230_gb300 import workloads
 from paper_2509_13230_gb300.ensemble import Ensemble
@@ -70,17 +71,18 @@ class Checker:
             if self.only is not None and (t, s) not in self.only:
                 continue
             m, x, y, nid = self.nets[t]
-            src, dst, w, counts, stats = oracle.mh_sample(m, x, y, seed=self.seed, network_id=nid,
-                                                          sample_begin=self.sample_begin + s, num_samples=1,
-                                                          seg_target=self.seg_target, flags=self.flags)
+            ref, stats, log = oracle_sample(m, x, y, seed=self.seed, network_id=nid,
+                                            sample_begin=self.sample_begin + s, num_samples=1,
+                                            seg_target=self.seg_target, flags=self.flags)
+            src, dst, w, counts = ref
             self.pairs += 1
             if self.layout in ("coo", "both"):
                 gs, gd, gw = (None if a is None else a.cpu().numpy() for a in res.coo(k))
-                same = np.array_equal(gs, src) and np.array_equal(gd, dst)
-                if same and m == UECM:
-                    same = np.array_equal(gw, w)
-                if not same:
-                    assert stats[3] > 0, f"network {t} sample {s}: edges differ and the oracle saw no boundary draw"
+                got = (gs, gd, gw if m == UECM else None, np.array([len(gs)], np.int64))
+                if not same_sample(got, ref):
+                    # only segments holding an oracle boundary draw may differ
+                    assert_traced(m, x, y, got, ref, log, seg_target=self.seg_target, flags=self.flags,
+                                  sample_begin=self.sample_begin + s)
                     self.boundary += 1
                     continue
                 if m == UBCM and gw is not None:
@@ -228,9 +230,8 @@ def test_autotuner_choice_is_a_candidate_and_samples_exactly():
         assert torch.equal(a.src, b.src) and torch.equal(a.dst, b.dst)
     chosen = Sampler(m, dev(x), num_samples=1, seg_target=res.seg_target,
                      walk_ctas_per_sm=res.walk_ctas_per_sm).run()
-    src, dst, _, counts, stats = oracle.mh_sample(m, x, None, num_samples=1, seg_target=res.seg_target)
-    assert (np.array_equal(chosen.src.cpu().numpy(), src) and np.array_equal(chosen.dst.cpu().numpy(), dst)) \
-        or stats[3] > 0
+    check_sample((chosen.src.cpu().numpy(), chosen.dst.cpu().numpy(), None, chosen.counts), m, x, None,
+                 num_samples=1, seg_target=res.seg_target)
     ens_res = tune_ensemble(to_device(nets), candidates_t=(16, 32), candidates_ctas=(0, 2), num_samples=2, reps=1)
     assert ens_res.seg_target in (16, 32) and len(ens_res.table) == 4
 

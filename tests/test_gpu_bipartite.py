@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import oracle
+from parity import check_bip_sample
 from paper_2509_13230_gb300 import _native as nat
 from paper_2509_13230_gb300.sampler import BipartiteSampler
 
@@ -38,19 +39,20 @@ def check(model, xp, yp, xm, ym, *, directed=False, num_samples=3, seg_target=32
                          seed=seed, network_id=network_id, sample_begin=sample_begin, seg_target=seg_target,
                          layout=layout, **kw)
     res = s.run()
-    src, dst, w, counts, stats = oracle.bip_sample(model, xp, yp, xm, ym, directed=directed, seed=seed,
-                                                   network_id=network_id, sample_begin=sample_begin,
-                                                   num_samples=num_samples, seg_target=seg_target)
+    kw_o = dict(directed=directed, seed=seed, network_id=network_id, sample_begin=sample_begin,
+                num_samples=num_samples, seg_target=seg_target)
     if layout in ("coo", "both"):
-        same = (np.array_equal(res.counts, counts) and np.array_equal(res.src.cpu().numpy(), src)
-                and np.array_equal(res.dst.cpu().numpy(), dst)
-                and (w is None or np.array_equal(res.w.cpu().numpy(), w)))
-        if not same:
-            assert stats[3] > 0, "edge lists differ and the oracle saw no boundary draw"
+        got = (res.src.cpu().numpy(), res.dst.cpu().numpy(), None if res.w is None else res.w.cpu().numpy(),
+               res.counts)
+        same, (src, dst, w, counts), stats = check_bip_sample(got, model, xp, yp, xm, ym, **kw_o)
+        if not same:  # every differing segment holds an oracle boundary draw
             return res, stats
         assert int(res.stats[nat.MH_STAT_PROPOSALS]) == int(stats[0])
         assert int(res.stats[nat.MH_STAT_EDGES]) == int(stats[1])
         assert int(res.stats[nat.MH_STAT_SEGMENTS]) == int(stats[2])
+        assert int(res.stats[nat.MH_STAT_BOUNDARY]) == int(stats[3])
+    else:
+        src, dst, w, counts, stats = oracle.bip_sample(model, xp, yp, xm, ym, **kw_o)
     if layout in ("csr", "both"):
         n_plus = len(xp)
         pos = 0

@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+from parity import assert_traced, oracle_sample, same_sample
 from paper_2509_13230_gb300 import _native as nat
 from paper_2509_13230_gb300.sampler import Sampler
 
@@ -37,15 +38,21 @@ def check(model, x, y, *, num_samples=3, seg_target=32, layout="both", **kw):
     s = Sampler(model, dev(x), dev(y), num_samples=num_samples, seg_target=seg_target, layout=layout, symmetric=True,
                 **kw)
     res = s.run()
-    src, dst, w, counts, stats = oracle.mh_sample(model, x, y, num_samples=num_samples, seg_target=seg_target,
-                                                  sample_begin=kw.get("sample_begin", 0), seed=kw.get("seed", 0))
-    if not np.array_equal(res.counts, counts):
-        assert stats[3] > 0, "counts differ and the oracle saw no boundary draw"
-        return res
+    begin = kw.get("sample_begin", 0)
+    ref, stats, log = oracle_sample(model, x, y, num_samples=num_samples, seg_target=seg_target,
+                                    sample_begin=begin, seed=kw.get("seed", 0))
+    src, dst, w, counts = ref
     off, idx, wts = oracle.symmetric_csr(src, dst, w, counts, n)
     got_off = res.csr_offsets.cpu().numpy()
-    if not (np.array_equal(got_off, off) and np.array_equal(res.csr_indices.cpu().numpy(), idx)):
-        assert stats[3] > 0, "symmetric CSR differs and the oracle saw no boundary draw"
+    if not (np.array_equal(res.counts, counts) and np.array_equal(got_off, off)
+            and np.array_equal(res.csr_indices.cpu().numpy(), idx)):
+        # a difference must come from segments holding oracle boundary draws,
+        # traced on the same call's COO output (a CSR-only call has none)
+        assert layout == "both", "symmetric CSR differs from the oracle's"
+        got = (res.src.cpu().numpy(), res.dst.cpu().numpy(), None if res.w is None else res.w.cpu().numpy(),
+               res.counts)
+        assert not same_sample(got, ref), "the COO output equals the oracle's but the symmetric CSR does not"
+        assert_traced(model, x, y, got, ref, log, seg_target=seg_target, flags=0, sample_begin=begin)
         return res
     if model == UECM:
         assert np.array_equal(res.csr_weights.cpu().numpy(), wts)
