@@ -1,22 +1,25 @@
-"""Benchmark: sampled edges/s of the Miller-Hagberg UECM sampler on one GB300.
+"""Benchmark: sampled edges/s of batched Miller-Hagberg ensembles on one GB300.
 
-One step = one mh_sample_weighted call over the weighted degree+strength
-workload (N = 20,000, x = exp(z), z ~ N(-4.0, 1.2), y ~ U(0.3, 0.9), FP64),
-drawing 10 samples as int32 COO edges plus int32 geometric weights: node
-sort, bound preparation, row-segment table, proposal walk, edge emission.
-Inputs are resident in HBM; the L2 is flushed (a 512 MiB write) before every
-timed step.  Under torchrun each rank draws its own 10 samples (weak
-scaling, no collective on the data path).
+One step = the 128-network ensemble (N log-uniform in [10^3, 10^6], 64 UBCM
+and 64 UECM networks, capped Pareto fitness with mean expected degree about
+20, y ~ U(0.3, 0.9)), 64 samples of every network as CSR (int64 offsets,
+int32 indices and weights): mh_batch_prepare (node sorts, bound preparation,
+row-segment tables of all networks) and every (network, sample) pair in
+mh_sample_batched waves.  Inputs resident in HBM; the L2 is flushed (a
+512 MiB write) before every timed step.  Beside it: the same samples drawn by
+one call per (network, sample) (the per-sample launch loop), end to end with
+the inputs copied from pinned host memory, the walk's roofline, the oracle on
+a bounded sample.  Under torchrun rank r draws samples [64 r, 64 r + 64) of
+every network (weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle
-(the serial FP64 walk, one sample per step) on the host cores instead.
-
-At N = 1 the line also carries "ensemble": the 128-network batched ensemble
-(N log-uniform in [10^3, 10^6], half UBCM and half UECM, 64 samples each,
-CSR output) drawn by mh_batch_prepare + mh_sample_batched waves, beside a
-loop of one single-network call per (network, sample) on the same networks.
+Prints one JSON line on rank 0.  At N = 1 the line also carries the other
+workloads as sub-objects (the weighted N = 20,000 call, the lognormal
+ensemble, the pairwise sums, fit-then-sample, bipartite and directed
+networks, the other configurations, output layouts).  `--impl reference`
+times the CPU oracle (the serial FP64 walk, one sample of one ensemble
+network per step) on the host cores instead.
 """
 from __future__ import annotations
 
@@ -48,6 +51,17 @@ FALLBACK_HBM_GBS = 6800.0
 def workload():
     from paper_2509_13230_gb300 import workloads
     return workloads.uecm_n20k()
+
+
+def walk_traffic(T: int):
+    """DRAM bytes per walk launch of the 10-sample weighted call at segment
+    length T, from the ncu capture in profiles/ while the walk sources are
+    unchanged since it (else None)."""
+    if os.path.exists(WALK_PROFILE):
+        prof = json.load(open(WALK_PROFILE))
+        if prof.get("sources_sha") == sources_hash():
+            return prof.get("dram_bytes_per_launch_by_seg_target", {}).get(str(T))
+    return None
 
 
 def sources_hash() -> str:
@@ -188,30 +202,47 @@ def oracle_bf_time(net):
 
 
 def run_reference(args, rank):
+    """The oracle (serial FP64 walk, one host core) on a bounded sample of the
+    headline's ensemble: step k draws one sample of one network, cycling
+    through the ensemble's networks of at most REF_MAX_N nodes in size order."""
     if rank != 0:
         return
     import oracle
+
+    from paper_2509_13230_gb300 import workloads
     oracle.load()
-    net = workload()
+    nets = [(t, nw) for t, nw in enumerate(workloads.ensemble_128()) if nw.n <= REF_MAX_N]
+    nets.sort(key=lambda e: e[1].n)
+    T = args.ensemble_seg_target or 16
+
+    def step(k):
+        t, nw = nets[k % len(nets)]
+        t0 = time.perf_counter()
+        _, _, _, counts, _ = oracle.mh_sample(nw.model, nw.x, nw.y, network_id=t, sample_begin=k // len(nets),
+                                              num_samples=1, seg_target=T)
+        return time.perf_counter() - t0, int(counts.sum())
+
     for w in range(args.warmup):
-        oracle.mh_sample(oracle.UECM, net.x, net.y, sample_begin=w, num_samples=1)
+        step(w)
     edges, t = 0, 0.0
     for k in range(args.steps):
-        t0 = time.perf_counter()
-        _, _, _, counts, _ = oracle.mh_sample(oracle.UECM, net.x, net.y, sample_begin=k % SAMPLES_PER_STEP,
-                                              num_samples=1)
-        t += time.perf_counter() - t0
-        edges += int(counts.sum())
+        dt, e = step(k)
+        t += dt
+        edges += e
     value = edges / t
-    sample = (f"one of the {SAMPLES_PER_STEP} samples of {WORKLOAD} per step (N = {net.n}), serial FP64 oracle, "
-              f"single thread")
+    sample = (f"one sample of one network per step, cycling through the {len(nets)} networks of the 128-network "
+              f"ensemble with at most {REF_MAX_N} nodes in size order; serial FP64 oracle, one host core")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": net.n, "samples_per_step": 1, "output": "coo int32 + w int32"},
+            "config": {"workload": ENSEMBLE_WORKLOAD, "networks": len(nets), "samples_per_step": 1,
+                       "seg_target": T, "output": "coo int32 (+ int32 weights for the UECM networks)"},
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+REF_MAX_N = 200_000
 
 
 # ---------------------------------------------------------------------------
@@ -771,21 +802,18 @@ def reduce_over_ranks(total_ms: float, edges: float, world: int, device):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
-def run_ours(args, rank, world, local_rank):
+def single_call_leg(args, dev, flush, local_rank=0):
+    """The weighted N = 20,000 workload, 10 samples per mh_sample_weighted call:
+    device-timed rate, walk roofline, end to end with host buffers, the
+    per-sample launch loop and the oracle baselines (one process, N = 1)."""
     import torch
-    import torch.distributed as dist
 
     from paper_2509_13230_gb300 import _native as nat
     from paper_2509_13230_gb300.sampler import Sampler
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
+    rank, world = 0, 1
 
     def barrier():
-        if world > 1:
-            dist.barrier()
         torch.cuda.synchronize()
 
     net = workload()
@@ -806,7 +834,6 @@ def run_ours(args, rank, world, local_rank):
                 walk_ctas_per_sm=ctas)
     s.run()                                     # sizes the output buffers
     s.flags |= nat.MH_TIMING
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def timed_region():
@@ -815,6 +842,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         total_ms, walk_ms, edges, launches = 0.0, [], 0, 0
         phases.clear()
+        counters[:] = [0, 0]
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
             for _ in range(args.steps):
@@ -829,16 +857,19 @@ def run_ours(args, rank, world, local_rank):
                 phases.append((info.prepare_ms, info.walk_ms, info.emit_ms, info.total_ms))
                 launches += info.kernel_launches
                 edges += int(s.h_counts.sum())
+                counters[0] += int(s.h_stats[nat.MH_STAT_PROPOSALS])
+                counters[1] += int(s.h_stats[nat.MH_STAT_BOUNDARY])
         barrier()
         return total_ms, walk_ms, edges, launches, clk.summary()
 
     phases = []
+    counters = [0, 0]
     total_ms, walk_ms, edges, launches, clocks = timed_region()
     if rejected(clocks):
         total_ms, walk_ms, edges, launches, clocks = timed_region()
         clocks["remeasured"] = True
-    max_ms, all_edges = reduce_over_ranks(total_ms, edges, world, dev)
-    value = all_edges / (max_ms / 1e3)
+    max_ms, value = total_ms, edges / (total_ms / 1e3)
+    proposals, boundary = counters
 
     # per-sample launch loop: the same samples drawn by one call each
     s1 = Sampler(nat.MH_UECM, x, y, num_samples=1, sample_begin=first, seg_target=T, walk_ctas_per_sm=ctas)
@@ -960,71 +991,31 @@ def run_ours(args, rank, world, local_rank):
     s.flags = e2e_flags | nat.MH_TIMING
     e2e_value = pipe_edges / (pipe_ms / 1e3)
     e2e_parts = parts
-    ensemble = ensemble_lognormal = None
-    if world == 1 and not args.no_ensemble:
-        ensemble = ensemble_leg(args, dev, flush)
-        # the other reading of the ensemble's fitness: z ~ N(-4, 1.2), 8 samples per network
-        ensemble_lognormal = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8, capacity=1 << 30,
-                                          seg_target=ensemble["seg_target"], loop_samples=1)
-    pairwise = fitted = bipartite = layouts = None
-    if world == 1 and not args.no_ensemble:
-        pairwise = pairwise_leg(args, dev, clocks.get("sm_mhz"))
-        fitted = fit_leg(args, dev)
-        bipartite = bipartite_leg(args, dev, flush)
-    configs = None
-    if world == 1:
-        layouts = layouts_leg(args, dev, flush, T)
-        if not args.no_ensemble:
-            configs = configs_leg(args, dev, flush)
-    if world > 1:
-        dist.barrier()
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
     hbm_gbs, peak_kind = peaks()
     walk_avg_ms = float(np.mean(walk_ms))
     edges_per_step = edges / args.steps
     achieved = BYTES_PER_EDGE * edges_per_step / (walk_avg_ms / 1e3) / 1e9
-    traffic = None
-    if os.path.exists(WALK_PROFILE):
-        prof = json.load(open(WALK_PROFILE))
-        if prof.get("sources_sha") == sources_hash():
-            traffic = prof.get("dram_bytes_per_launch_by_seg_target", {}).get(str(T or 32))
-    # CPU oracle on a bounded sample of the same workload (rank 0, N = 1 only)
-    cpu = cpu_all = cpu_bf = None
-    if world == 1:
-        rate, nsamp, secs = oracle_rate(net, 10.0)
-        cpu = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nsamp} whole samples of {WORKLOAD} (N = {net.n}), serial FP64 walk, "
-                         f"{secs:.1f} s on one host core"}
-        if not args.no_ensemble:
-            rate_a, nsamp_a, busy_a, wall_a, cores_a = oracle_rate_all_cores(net, 8.0)
-            cpu_all = {"value": rate_a, "unit": "edges/s", "cores": cores_a, "kind": "oracle",
-                       "sample": f"{nsamp_a} whole samples of {WORKLOAD}, one spawned process per host core, "
-                                 f"{busy_a:.1f} s busy per process ({wall_a:.1f} s wall with start-up)"}
-            bf_s, evals = oracle_bf_time(net)
-            cpu_bf = {"seconds_per_sample": bf_s, "pairs": evals, "pairs_per_s": evals / bf_s,
-                      "edges_per_s": (edges / args.steps / SAMPLES_PER_STEP) / bf_s,
-                      "mh_over_bf_speedup_cpu": bf_s / (secs / nsamp), "kind": "oracle brute force",
-                      "cores": 1}
-    if fitted is not None and cpu_bf is not None:
-        # config 5 brute force: N (N - 1) / 2 pairs per sample at the UECM pair
-        # rate measured on the headline network in this run
-        pairs5 = FIT_N * (FIT_N - 1) / 2
-        fitted["cpu_brute_force"] = {
-            "pairs": pairs5, "extrapolated_seconds_per_sample": pairs5 / cpu_bf["pairs_per_s"],
-            "note": "not run: extrapolated at the UECM brute-force pair rate of the N = 20,000 network"}
-    line = {
-        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": net.n, "samples_per_step": SAMPLES_PER_STEP * world,
-                   "seg_target": T or 32, "walk_ctas_per_sm": ctas,
-                   "autotune": None if tuned is None else tuned.table,
-                   "output": "coo int32 + w int32 (12 B/edge)", "l2": "flushed (512 MiB write) before every step",
-                   "parallelism": f"replicas x{world}"},
+    traffic = walk_traffic(T or 32)
+    # CPU oracle on a bounded sample of the same workload
+    rate, nsamp, secs = oracle_rate(net, 10.0)
+    cpu = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+           "sample": f"{nsamp} whole samples of {WORKLOAD} (N = {net.n}), serial FP64 walk, "
+                     f"{secs:.1f} s on one host core"}
+    cpu_all = cpu_bf = None
+    if not args.no_ensemble:
+        rate_a, nsamp_a, busy_a, wall_a, cores_a = oracle_rate_all_cores(net, 8.0)
+        cpu_all = {"value": rate_a, "unit": "edges/s", "cores": cores_a, "kind": "oracle",
+                   "sample": f"{nsamp_a} whole samples of {WORKLOAD}, one spawned process per host core, "
+                             f"{busy_a:.1f} s busy per process ({wall_a:.1f} s wall with start-up)"}
+        bf_s, evals = oracle_bf_time(net)
+        cpu_bf = {"seconds_per_sample": bf_s, "pairs": evals, "pairs_per_s": evals / bf_s,
+                  "edges_per_s": (edges / args.steps / SAMPLES_PER_STEP) / bf_s,
+                  "mh_over_bf_speedup_cpu": bf_s / (secs / nsamp), "kind": "oracle brute force", "cores": 1}
+    return {
+        "workload": WORKLOAD, "value": value, "unit": "edges/s", "ms_per_step": max_ms / args.steps,
+        "n": net.n, "samples_per_step": SAMPLES_PER_STEP, "seg_target": T or 32, "walk_ctas_per_sm": ctas,
+        "autotune": None if tuned is None else tuned.table,
+        "output": "coo int32 + w int32 (12 B/edge)", "l2": "flushed (512 MiB write) before every step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
                      "frac": achieved / hbm_gbs, "traffic": traffic, "kernel": "walk_kernel",
                      "peak_kind": peak_kind, "walk_ms_per_launch": walk_avg_ms},
@@ -1043,14 +1034,340 @@ def run_ours(args, rank, world, local_rank):
         "phases_ms_per_step": dict(zip(("prepare", "walk", "scan_emit", "call"),
                                        (float(v) for v in np.mean(np.array(phases), axis=0)))),
         "per_sample_loop": {"value": loop_value, "unit": "edges/s", "batched_over_loop": value / loop_value},
-        "ensemble": ensemble,
-        "ensemble_lognormal": ensemble_lognormal,
-        "pairwise": pairwise,
-        "fit_then_sample": fitted,
-        "bipartite": bipartite,
-        "layouts": layouts,
-        "configs": configs,
+        "boundary_draws": boundary, "proposals": proposals,
         "clocks": clocks,
+    }
+
+
+# ---------------------------------------------------------------------------
+# Headline: the batched ensemble of 128 networks (N log-uniform in
+# [10^3, 10^6], half UBCM and half UECM, capped Pareto fitness with mean
+# expected degree about 20), 64 samples each, CSR output, drawn by
+# mh_batch_prepare + mh_sample_batched waves; beside it the same samples
+# drawn by one mh_sample_* call per (network, sample).  Rank r draws samples
+# [64 r, 64 (r + 1)) of every network (weak scaling, no data-path collective).
+# ---------------------------------------------------------------------------
+ENSEMBLE_WORKLOAD = "ensemble_128_x64"
+ENSEMBLE_PROFILE = os.path.join(ROOT, "profiles", "walk_kernel_batched_ensemble.json")
+LOOP_REPEATS = 3
+
+
+def ensemble_profile():
+    """Per-proposal figures of the batched walks from the ncu capture in
+    profiles/ (thread instructions, DRAM bytes), while the walk sources are
+    unchanged since it; else None."""
+    if os.path.exists(ENSEMBLE_PROFILE):
+        prof = json.load(open(ENSEMBLE_PROFILE))
+        if prof.get("sources_sha") == sources_hash():
+            return prof
+    return None
+
+
+def ensemble_networks(args, dev):
+    """The 128 networks (or an evenly spaced subset) with x and y of all
+    networks in two concatenated device arrays (one copy each end to end)."""
+    import torch
+
+    from paper_2509_13230_gb300 import workloads
+
+    nets_np = workloads.ensemble_128()
+    keep = max(1, min(args.ensemble_networks, len(nets_np)))
+    sel = np.linspace(0, len(nets_np) - 1, keep).round().astype(int)
+    nets_np = [(int(t), nets_np[t]) for t in sel]
+    x_host = np.concatenate([nw.x for _, nw in nets_np])
+    y_host = np.concatenate([nw.y for _, nw in nets_np if nw.y is not None] or [np.zeros(0)])
+    x_all = torch.from_numpy(x_host).to(dev)
+    y_all = torch.from_numpy(y_host).to(dev)
+    nets, ox, oy = [], 0, 0
+    for t, nw in nets_np:
+        xv = x_all[ox:ox + nw.n]
+        ox += nw.n
+        yv = None
+        if nw.y is not None:
+            yv = y_all[oy:oy + nw.n]
+            oy += nw.n
+        nets.append((nw.model, xv, yv, t))
+    return nets_np, nets, x_host, y_host, x_all, y_all
+
+
+def oracle_ensemble_rate(nets_np, T, seconds):
+    """The oracle on whole samples of the smallest networks, about `seconds` of one core."""
+    import oracle
+    oracle.load()
+    n = np.array([nw.n for _, nw in nets_np])
+    edges, secs, pairs = 0, 0.0, 0
+    for k in np.argsort(n, kind="stable"):
+        if secs > seconds:
+            break
+        t, nw = nets_np[k]
+        t0 = time.perf_counter()
+        _, _, _, c, _ = oracle.mh_sample(nw.model, nw.x, nw.y, network_id=t, num_samples=1, seg_target=T)
+        secs += time.perf_counter() - t0
+        edges += int(c.sum())
+        pairs += 1
+    return edges / secs, pairs, secs
+
+
+def ensemble_headline(args, dev, flush, rank, world, barrier):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300.ensemble import Ensemble
+    from paper_2509_13230_gb300.sampler import Sampler
+
+    nets_np, nets, x_host, y_host, x_all, y_all = ensemble_networks(args, dev)
+    n = np.array([nw.n for _, nw in nets_np], dtype=np.int64)
+    uecm = np.array([nw.model == nat.MH_UECM for _, nw in nets_np])
+    samples = args.ensemble_samples
+    first = rank * samples
+    T, ctas, tuned = 0, 0, None
+    if args.ensemble_seg_target:
+        T = args.ensemble_seg_target
+    elif not args.no_tune:
+        from paper_2509_13230_gb300.autotune import tune_ensemble
+        tuned = tune_ensemble(nets, candidates_t=(8, 16, 32), candidates_ctas=(0, 2), num_samples=2, reps=2)
+        T, ctas = tuned.seg_target, tuned.walk_ctas_per_sm
+    ens = Ensemble(nets, num_samples=samples, sample_begin=first, layout="csr", capacity=args.ensemble_capacity,
+                   timing=True, seg_target=T, walk_ctas_per_sm=ctas, max_wave_items=args.ensemble_wave_items)
+    stream = torch.cuda.current_stream()
+    acc = {}
+
+    def on_wave(res):
+        info = nat.mh_last_call_info()
+        acc["walk"] += info.walk_ms
+        acc["emit"] += info.emit_ms
+        acc["launches"] += info.kernel_launches
+        acc["waves"] += 1
+
+    def one_step():
+        ens.prepare()  # sort + bound prep + segment tables of every network are part of a step
+        info = nat.mh_last_call_info()
+        acc["prepare"] += info.prepare_ms
+        acc["launches"] += info.kernel_launches
+        counts, stats = ens.sample(on_wave=on_wave)
+        return counts, stats
+
+    def reset():
+        acc.update(walk=0.0, emit=0.0, prepare=0.0, launches=0, waves=0)
+
+    def out_bytes(counts):
+        per_net = counts.reshape(len(nets), samples).sum(axis=1)
+        return int((4 * per_net + 4 * per_net * uecm + 8 * (n + 1) * samples).sum())
+
+    def timed(steps, e2e=False):
+        reset()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot_ms, edges, nbytes, props, bnd, fb = 0.0, 0, 0, 0, 0, 0
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            if e2e:  # this step's inputs from pinned host memory
+                x_all.copy_(hx, non_blocking=True)
+                y_all.copy_(hy, non_blocking=True)
+            counts, stats = one_step()  # per-pair counts come back to the host in every wave
+            ev1.record(stream)
+            ev1.synchronize()
+            tot_ms += ev0.elapsed_time(ev1)
+            edges += int(counts.sum())
+            nbytes += out_bytes(counts)
+            props += int(stats[nat.MH_STAT_PROPOSALS])
+            bnd += int(stats[nat.MH_STAT_BOUNDARY])
+            fb += int(stats[nat.MH_STAT_FALLBACKS])
+        return dict(ms=tot_ms, edges=edges, bytes=nbytes, proposals=props, boundary=bnd, fallbacks=fb,
+                    **{k: v for k, v in acc.items()})
+
+    reset()
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    with ClockSampler(dev.index or 0) as clk:
+        r = timed(args.steps)
+    barrier()
+    clocks = clk.summary()
+    if rejected(clocks):
+        with ClockSampler(dev.index or 0) as clk:
+            r = timed(args.steps)
+        barrier()
+        clocks = clk.summary()
+        clocks["remeasured"] = True
+    max_ms, all_edges = reduce_over_ranks(r["ms"], r["edges"], world, dev)
+    value = all_edges / (max_ms / 1e3)
+
+    # end to end: the same steps with x and y of all networks copied in from
+    # pinned host memory first (one copy each), counts read back per wave
+    hx = torch.from_numpy(x_host).pin_memory()
+    hy = torch.from_numpy(y_host).pin_memory()
+    e2e_steps = max(3, min(args.steps, 8))
+    re = timed(e2e_steps, e2e=True)
+    barrier()
+    e_max_ms, e_edges = reduce_over_ranks(re["ms"], re["edges"], world, dev)
+    e2e_value = e_edges / (e_max_ms / 1e3)
+
+    # per-sample launch loop: one mh_sample_* call per (network, sample),
+    # the first loop_samples samples of each network, repeated
+    loop = None
+    loop_samples = args.ensemble_loop_samples
+    if loop_samples > 0:
+        samplers = []
+        for (m, x, y, nid) in nets:
+            s1 = Sampler(m, x, y, num_samples=1, network_id=nid, sample_begin=first, layout="csr", seg_target=T,
+                         walk_ctas_per_sm=ctas)
+            s1.run()
+            samplers.append(s1)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = []
+        for _ in range(LOOP_REPEATS):
+            flush.zero_()
+            l_edges = 0
+            ev0.record(stream)
+            for s1 in samplers:
+                for k in range(loop_samples):
+                    nat.check(s1.call(sample_begin=first + k), "mh_sample")
+                    l_edges += int(s1.h_counts.sum())
+            ev1.record(stream)
+            ev1.synchronize()
+            reps.append(l_edges / (ev0.elapsed_time(ev1) / 1e3))
+        del samplers
+        ratios = sorted(value / world / v for v in reps)
+        loop = {"value": statistics.median(reps), "unit": "edges/s", "repeats": reps,
+                "calls_per_repeat": len(nets) * loop_samples, "samples_per_network": loop_samples,
+                "batched_over_loop": statistics.median(ratios), "batched_over_loop_min": ratios[0],
+                "batched_over_loop_median": statistics.median(ratios),
+                "note": "batched: the headline's per-GPU rate; loop: one call per (network, sample), "
+                        "each call preparing its network and reading its counts back"}
+    del ens
+    torch.cuda.empty_cache()
+
+    hbm_gbs, peak_kind = peaks()
+    steps = args.steps
+    walk_s = r["walk"] / steps / 1e3
+    prof = ensemble_profile()
+    achieved = r["bytes"] / steps / walk_s / 1e9 if walk_s > 0 else None
+    issue = None
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sms * 128 * sm_mhz * 1e6
+    if prof is not None and walk_s > 0:
+        ipp = prof["thread_inst_per_proposal"]
+        issue_ach = ipp * r["proposals"] / steps / walk_s
+        issue = {"bound": "issue", "achieved": issue_ach / 1e12, "peak": issue_peak / 1e12,
+                 "unit": "T thread-instructions/s", "frac": issue_ach / issue_peak,
+                 "thread_inst_per_proposal": ipp,
+                 "basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock of the timed region); "
+                          "instructions per proposal from the ncu capture in profiles/"}
+    else:
+        issue = {"bound": "issue", "achieved": None, "peak": issue_peak / 1e12, "unit": "T thread-instructions/s",
+                 "frac": None, "note": "no ncu capture of the current walk sources"}
+    traffic = None if prof is None else prof["dram_bytes_per_proposal"] * r["proposals"] / steps
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, pairs, secs = oracle_ensemble_rate(nets_np, T or 32, 10.0)
+        cpu = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"one sample of each of the {pairs} smallest networks of the ensemble, serial FP64 "
+                         f"walk, {secs:.1f} s on one host core"}
+    return {
+        "value": value, "max_ms": max_ms, "edges_per_step": r["edges"] / steps,
+        "config": {"workload": ENSEMBLE_WORKLOAD, "networks": len(nets), "nodes": int(n.sum()),
+                   "samples_per_network": samples, "samples_per_step": samples * len(nets) * world,
+                   "fitness": "x = min(c(N) u^(-1/1.1), 50), u ~ U(0, 1), mean expected degree about 20; "
+                              "y ~ U(0.3, 0.9) for the 64 UECM networks",
+                   "seg_target": T or 32, "walk_ctas_per_sm": ctas, "autotune": None if tuned is None else tuned.table,
+                   "output": "CSR: int64 offsets, int32 indices (+ int32 weights for the UECM half)",
+                   "waves_per_step": r["waves"] / steps, "wave_edges": args.ensemble_capacity,
+                   "wave_items": args.ensemble_wave_items,
+                   "l2": "inputs and outputs far larger than L2; a 512 MiB write flushes it before every step",
+                   "parallelism": f"replicas x{world} (rank r draws samples [64 r, 64 r + 64) of every network)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": achieved / hbm_gbs if achieved else None, "traffic": traffic,
+                     "kernel": "walk_kernel (batched; the UBCM and UECM launches of a wave run concurrently)",
+                     "peak_kind": peak_kind, "walk_ms_per_step": r["walk"] / steps,
+                     "basis": "CSR output bytes of the step (4 B index, 4 B UECM weight, 8 B per offset) / walk "
+                              "time of the step (CUDA events around each wave's two concurrent walk launches); "
+                              "traffic: DRAM bytes per step scaled from the capture's bytes per proposal",
+                     "issue": issue},
+        "phases_ms_per_step": {"prepare": r["prepare"] / steps, "walk": r["walk"] / steps,
+                               "scan_emit": r["emit"] / steps},
+        "gpu_launches": r["launches"],
+        "proposals_per_step": r["proposals"] / steps,
+        "boundary_draws": {"count": r["boundary"], "draws": r["proposals"],
+                           "rate": r["boundary"] / max(1, r["proposals"]),
+                           "bound": 1e-8, "ok": r["boundary"] / max(1, r["proposals"]) < 1e-8},
+        "fp64_fallbacks": r["fallbacks"],
+        "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": int(x_host.nbytes + y_host.nbytes),
+                "d2h_bytes_per_step": 8 * len(nets) * samples,
+                "copies": "every step copies x and y of all networks from pinned host memory (one copy each) "
+                          "before the batched prepare and waves; the per-pair edge counts come back to the host "
+                          "with every wave; the sampled graphs stay in the device's reused wave buffers",
+                "steps": e2e_steps, "ms_per_step": re["ms"] / e2e_steps},
+        "per_sample_loop": loop,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    head = ensemble_headline(args, dev, flush, rank, world, barrier)
+    subs = {}
+    if world == 1 and not args.headline_only:
+        subs["uecm_n20k_x10"] = single_call_leg(args, dev, flush)
+        if not args.no_ensemble:
+            subs["ensemble_lognormal"] = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8,
+                                                      capacity=1 << 30, seg_target=head["config"]["seg_target"],
+                                                      loop_samples=1)
+            subs["pairwise"] = pairwise_leg(args, dev, head["clocks"].get("sm_mhz"))
+            subs["fit_then_sample"] = fit_leg(args, dev)
+            subs["bipartite"] = bipartite_leg(args, dev, flush)
+            subs["configs"] = configs_leg(args, dev, flush)
+        subs["layouts"] = layouts_leg(args, dev, flush, subs["uecm_n20k_x10"]["seg_target"])
+        fitted, cpu_bf = subs.get("fit_then_sample"), subs["uecm_n20k_x10"].get("cpu_brute_force")
+        if fitted is not None and cpu_bf is not None:
+            # config 5 brute force: N (N - 1) / 2 pairs per sample at the UECM pair
+            # rate measured on the weighted N = 20,000 network in this run
+            pairs5 = FIT_N * (FIT_N - 1) / 2
+            fitted["cpu_brute_force"] = {
+                "pairs": pairs5, "extrapolated_seconds_per_sample": pairs5 / cpu_bf["pairs_per_s"],
+                "note": "not run: extrapolated at the UECM brute-force pair rate of the N = 20,000 network"}
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    loop = head["per_sample_loop"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["max_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": head["config"],
+        "roofline": head["roofline"],
+        "cpu_baseline": head["cpu_baseline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "per_sample_loop": loop,
+        "batched_over_loop": None if loop is None else loop["batched_over_loop_median"],
+        "batched_over_loop_min": None if loop is None else loop["batched_over_loop_min"],
+        "edges_per_step": head["edges_per_step"],
+        "phases_ms_per_step": head["phases_ms_per_step"],
+        "proposals_per_step": head["proposals_per_step"],
+        "boundary_draws": head["boundary_draws"],
+        "fp64_fallbacks": head["fp64_fallbacks"],
+        **subs,
+        "clocks": head["clocks"],
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -1063,7 +1380,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-network batched ensemble leg")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the long sub-legs (lognormal ensemble, pairwise, fit, bipartite, configs)")
+    ap.add_argument("--headline-only", action="store_true", help="only the batched-ensemble headline")
     ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs", "kernels"],
                     default="all",
                     help="run only that leg and print its object; kernels: each profiled kernel once, "

@@ -196,6 +196,32 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
                        int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
 
 /*
+ * mh_sample_range — the share of mh_sample_ubcm / mh_sample_weighted that
+ * lies in rows [seg_begin, seg_end) of the segment table (the table
+ * mh_segment_table exports for the same arguments).  The walk of a segment
+ * depends only on the segment, the sample and the key (Sec. 2.3: each
+ * segment head restarts the proposal bound; the Philox counter names the
+ * segment), so ranges that tile [0, S) and are concatenated in range order
+ * give exactly the whole call's edges, for every sample.  This is how one
+ * large sample is split across GPUs: each rank draws a contiguous range and
+ * an exclusive scan of the ranks' edge counts places its edges.
+ *   model             MH_UBCM (y ignored) or MH_UECM
+ *   seg_begin/_end    0 <= seg_begin <= seg_end; rows past the table's end
+ *                     are empty
+ *   src, dst, w       COO int32[capacity_edges] (w: MH_UECM); sample s's
+ *                     edges of the range follow those of sample s - 1
+ *   other arguments   as mh_sample_weighted; params->flags must not ask for
+ *                     MH_OUT_CSR or MH_CSR_SYMMETRIC (MH_ERR_ARG)
+ *   h_edges_per_sample, h_stats: of the range only
+ * Workspace: mh_workspace_size of the whole call.  Errors as
+ * mh_sample_weighted (a truncated table: MH_ERR_WORKSPACE).
+ */
+int mh_sample_range(int model, const double* x, const double* y, int64_t n, const mh_params* params,
+                    int64_t seg_begin, int64_t seg_end, void* workspace, size_t workspace_bytes, int32_t* src,
+                    int32_t* dst, int32_t* w, int64_t capacity_edges, int64_t* h_edges_per_sample,
+                    uint64_t* h_stats, mh_stream_t stream);
+
+/*
  * Bipartite and directed networks (Sec. 2.6).  The + set's nodes are the
  * rows, each walked over every node of the - set; each set is sorted by its
  * own key (descending x, or a = x y for MH_UECM), so

@@ -69,6 +69,9 @@ def _declare(lib):
     lib.orc_partition.restype = i64
     lib.orc_mh_sample.argtypes = [i32, vp, vp, i64, u64, u32, u32, u32, i64, u32, vp, vp, vp, i64, vp, vp]
     lib.orc_mh_sample.restype = i64
+    lib.orc_mh_sample_segments.argtypes = [i32, vp, vp, i64, u64, u32, u32, u32, i64, u32, i64, i64, vp, vp, vp,
+                                           i64, vp, vp]
+    lib.orc_mh_sample_segments.restype = i64
     lib.orc_bf_sample.argtypes = [i32, vp, vp, i64, u64, u32, vp, vp, vp, i64, vp]
     lib.orc_bf_sample.restype = i64
     lib.orc_bip_partition.argtypes = [i32, vp, vp, i64, vp, vp, i64, i64, vp, vp, vp, vp, i64, vp, vp]
@@ -172,6 +175,32 @@ def mh_sample(model, x, y=None, *, seed=0, network_id=0, sample_begin=0, num_sam
         total = lib.orc_mh_sample(model, _ptr(x), _ptr(y), n, int(seed), int(network_id), int(sample_begin),
                                   int(num_samples), int(seg_target), int(flags), _ptr(src), _ptr(dst), _ptr(w),
                                   cap, _ptr(counts), _ptr(stats))
+        if total < 0:
+            raise OverflowError("a sampled weight exceeds INT32_MAX")
+        if total <= cap:
+            return (src[:total], dst[:total], None if w is None else w[:total], counts[:num_samples], stats)
+        cap = int(total)
+
+
+def mh_sample_segments(model, x, y=None, *, seg_begin, seg_end, seed=0, network_id=0, sample_begin=0,
+                       num_samples=1, seg_target=32, flags=0, lib=None):
+    """mh_sample restricted to rows [seg_begin, seg_end) of the segment table
+    (``partition``'s canonical order), each sample's edges in that range."""
+    lib = lib or load()
+    x = _f64(x)
+    y = _f64(y) if model == UECM else None
+    n = len(x)
+    cap = 1024
+    while True:
+        src = np.zeros(cap, np.int32)
+        dst = np.zeros(cap, np.int32)
+        w = np.zeros(cap, np.int32) if model == UECM else None
+        counts = np.zeros(max(num_samples, 1), np.int64)
+        stats = np.zeros(4, np.uint64)
+        total = lib.orc_mh_sample_segments(model, _ptr(x), _ptr(y), n, int(seed), int(network_id),
+                                           int(sample_begin), int(num_samples), int(seg_target), int(flags),
+                                           int(seg_begin), int(seg_end), _ptr(src), _ptr(dst), _ptr(w), cap,
+                                           _ptr(counts), _ptr(stats))
         if total < 0:
             raise OverflowError("a sampled weight exceeds INT32_MAX")
         if total <= cap:

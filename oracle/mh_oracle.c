@@ -21,6 +21,7 @@
  *   orc_sort_desc       node order of Sec. 2.4 step (i) / Algorithm 1 sort
  *   orc_partition       row-segment table (restart of the proposal bound)
  *   orc_mh_sample       serial Miller-Hagberg walk, Sec. 2.3-2.5, Algorithm 1
+ *   orc_mh_sample_segments  the same over a range of segment-table rows
  *   orc_bf_sample       brute-force Bernoulli sampler, Sec. 2.2 / Sec. 3
  *   orc_bip_partition   row-segment table of a bipartite network, Sec. 2.6
  *   orc_bip_sample      serial walk of bipartite and directed networks, Sec. 2.6
@@ -541,6 +542,44 @@ int64_t orc_mh_sample(int model, const double* x, const double* y, int64_t n, ui
             int64_t ns = row_segments(&g, &P, i, T, ta, tb, n);
             for (int64_t kk = 0; kk < ns; ++kk)
                 walk_segment(&g, key, sample_begin + s, i, (int32_t)kk, ta[kk], tb[kk], &out);
+        }
+        if (counts) counts[s] = out.count - before;
+    }
+    free(ta);
+    free(tb);
+    free(P.Q);
+    net_free(&g);
+    return out.weight_overflow ? -1 : out.count;
+}
+
+/* The same samples restricted to rows [seg_begin, seg_end) of the segment
+ * table (canonical (row, k) order): the share of one sample that a rank draws
+ * when the table is split into contiguous ranges.  The walk of a segment
+ * depends only on the segment and the sample, so the ranges' edge lists,
+ * concatenated in range order, are the whole sample's.  counts[s] receives
+ * the edges of sample s within the range. */
+int64_t orc_mh_sample_segments(int model, const double* x, const double* y, int64_t n, uint64_t seed,
+                               uint32_t network_id, uint32_t sample_begin, uint32_t num_samples, int64_t T,
+                               uint32_t flags, int64_t seg_begin, int64_t seg_end, int32_t* src, int32_t* dst,
+                               int32_t* w, int64_t cap, int64_t* counts, uint64_t* stats)
+{
+    net_t g;
+    proxy_t P;
+    net_build(&g, model, x, y, n, flags);
+    proxy_build(&P, &g);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) + network_id};
+    uint64_t local_stats[4] = {0, 0, 0, 0};
+    sink_t out = {src, dst, w, cap, 0, stats ? stats : local_stats, 0};
+    int64_t* ta = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (uint32_t s = 0; s < num_samples; ++s) {
+        int64_t before = out.count;
+        int64_t row_of_table = 0; /* index of the table row of (i, kk) */
+        for (int64_t i = 0; i + 1 < n && row_of_table < seg_end; ++i) {
+            int64_t ns = row_segments(&g, &P, i, T, ta, tb, n);
+            for (int64_t kk = 0; kk < ns; ++kk, ++row_of_table)
+                if (row_of_table >= seg_begin && row_of_table < seg_end)
+                    walk_segment(&g, key, sample_begin + s, i, (int32_t)kk, ta[kk], tb[kk], &out);
         }
         if (counts) counts[s] = out.count - before;
     }

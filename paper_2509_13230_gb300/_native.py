@@ -48,6 +48,7 @@ EXPORTED = (
     "mh_workspace_size",
     "mh_sample_ubcm",
     "mh_sample_weighted",
+    "mh_sample_range",
     "mh_sample_ubcm_noalloc",
     "mh_segment_table",
     "maxent_expected_fwd",
@@ -147,6 +148,8 @@ def load(path: str | None = None):
         lib.mh_sample_ubcm.restype = i32
         lib.mh_sample_weighted.argtypes = [vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
         lib.mh_sample_weighted.restype = i32
+        lib.mh_sample_range.argtypes = [i32, vp, vp, i64, P, i64, i64, vp, sz, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_range.restype = i32
         lib.mh_sample_ubcm_noalloc.argtypes = [vp, i64, P, vp, vp, vp, vp, i64, vp, vp, vp]
         lib.mh_sample_ubcm_noalloc.restype = i32
         lib.mh_segment_table.argtypes = [i32, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp]
@@ -223,6 +226,12 @@ def mh_sample_weighted(x, y, n, params, workspace, workspace_bytes, src, dst, w,
     return load().mh_sample_weighted(x, y, n, ctypes.byref(params), workspace, workspace_bytes, src, dst, w,
                                      csr_offsets, csr_indices, csr_weights, capacity_edges, h_edges_per_sample,
                                      h_stats, stream)
+
+
+def mh_sample_range(model, x, y, n, params, seg_begin, seg_end, workspace, workspace_bytes, src, dst, w,
+                    capacity_edges, h_edges_per_sample, h_stats, stream) -> int:
+    return load().mh_sample_range(model, x, y, n, ctypes.byref(params), seg_begin, seg_end, workspace,
+                                  workspace_bytes, src, dst, w, capacity_edges, h_edges_per_sample, h_stats, stream)
 
 
 def mh_sample_ubcm_noalloc(x, n, params, src, dst, csr_offsets, csr_indices, capacity_edges, h_edges_per_sample,

@@ -450,15 +450,42 @@ static int status_to_code(unsigned status, long long num_segments, int64_t max_s
   return MH_OK;
 }
 
+// A range [begin, end) of segment-table rows that a call walks (end < 0: all).
+struct SegRange {
+  int64_t begin = 0, end = -1;
+  bool all() const { return end < 0; }
+};
+
+// Narrows the walked table to rows [a, b) of the one the partition wrote:
+// the walk and the emit then see a table of b - a rows starting at row a
+// (their table pointers are offset by a on the host).  A truncated table
+// (more rows than max_segments) is left as it is, so the call fails as usual.
+__global__ void seg_range_kernel(Ctrl* ctrl, long long a, long long b, long long max_segments) {
+  const long long S = ctrl->num_segments;
+  if (S > max_segments) return;
+  const long long lo = a < S ? a : S, hi = b < S ? b : S;
+  ctrl->num_segments = hi > lo ? hi - lo : 0;
+}
+
 // Everything a sampling call enqueues: prepare, then walk + emit per sample
 // chunk, then the read-back of the control block and the per-sample counts
 // into the pinned buffer `hbuf`.
-static int enqueue_sample(const Net& g, const Layout& L, char* ws, const mh_params* p, const Outputs& o,
-                          bool timed, char* hbuf, cudaStream_t s) {
+static int enqueue_sample(const Net& g_full, const Layout& L, char* ws, const mh_params* p, const Outputs& o,
+                          bool timed, char* hbuf, cudaStream_t s, SegRange range = SegRange{}) {
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
   MH_CUDA(g_timer.start(timed, s));
-  int rc = prepare(g, L, ws, ctrl, s);
+  int rc = prepare(g_full, L, ws, ctrl, s);
   if (rc != MH_OK) return rc;
+  Net g = g_full;
+  if (!range.all()) {
+    const int64_t a = range.begin < L.max_segments ? range.begin : L.max_segments;
+    seg_range_kernel<<<1, 1, 0, s>>>(ctrl, a, range.end, L.max_segments);
+    note_launches(1);
+    MH_CUDA(cudaGetLastError());
+    g.seg += a;
+    if (g.seg_c) g.seg_c += a;
+    if (g.seg_cf) g.seg_cf += a;
+  }
   MH_CUDA(g_timer.mark(s));
 
   Outputs out = o;
@@ -520,6 +547,7 @@ struct CallKey {
   const void *x, *y, *xr, *yr, *ws, *src, *dst, *w, *csr_off, *csr_idx, *csr_w, *hbuf;
   size_t ws_bytes;
   mh_params params;
+  int64_t seg_begin, seg_end;
 };
 struct CachedGraph {
   CallKey key;
@@ -584,7 +612,8 @@ thread_local GraphCache g_graphs;
 // whose rows are (xr, yr, rows) and candidates (x, y, n).
 static int run_sample(int model, const double* x, const double* y, int64_t n, const mh_params* p, void* workspace,
                       size_t workspace_bytes, const Outputs& o, int64_t* h_counts, uint64_t* h_stats,
-                      cudaStream_t s, const double* xr = nullptr, const double* yr = nullptr, int64_t rows = 0) {
+                      cudaStream_t s, const double* xr = nullptr, const double* yr = nullptr, int64_t rows = 0,
+                      SegRange range = SegRange{}) {
   const bool bip = xr != nullptr;
   if (!bip) rows = n;
   int rc = check_params_impl(model, rows, n, bip, p);
@@ -659,6 +688,8 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
   key.hbuf = hbuf;
   key.ws_bytes = workspace_bytes;
   key.params = *p;
+  key.seg_begin = range.begin;
+  key.seg_end = range.end;
 
   g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};
   CachedGraph* cg = g_graphs.find(key);
@@ -668,7 +699,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     g_launches = 0;
     cudaGraph_t graph = nullptr;
     MH_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, cs);
+    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, cs, range);
     const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (rc != MH_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -698,7 +729,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
     g_info.sample_chunks = cg->chunks;
   } else {
     g_launches = 0;
-    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, s);
+    rc = enqueue_sample(g, L, ws, p, o, timed, hbuf, s, range);
     if (rc != MH_OK) return rc;
     g_info.kernel_launches = g_launches;
     g_info.sample_chunks = (p->num_samples + L.spc - 1) / L.spc;
@@ -787,6 +818,28 @@ int mh_sample_weighted(const double* x, const double* y, int64_t n, const mh_par
   Outputs o{src, dst, w, reinterpret_cast<long long*>(csr_offsets), csr_indices, csr_weights, capacity_edges};
   return run_sample(MH_UECM, x, y, n, params, workspace, workspace_bytes, o, h_edges_per_sample, h_stats,
                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mh_sample_range(int model, const double* x, const double* y, int64_t n, const mh_params* params,
+                    int64_t seg_begin, int64_t seg_end, void* workspace, size_t workspace_bytes, int32_t* src,
+                    int32_t* dst, int32_t* w, int64_t capacity_edges, int64_t* h_edges_per_sample,
+                    uint64_t* h_stats, mh_stream_t stream) {
+  if (model != MH_UBCM && model != MH_UECM) {
+    set_error("model must be MH_UBCM or MH_UECM");
+    return MH_ERR_ARG;
+  }
+  if (!params || seg_begin < 0 || seg_end < seg_begin) {
+    set_error("need params and 0 <= seg_begin <= seg_end");
+    return MH_ERR_ARG;
+  }
+  if (params->flags & (MH_OUT_CSR | MH_CSR_SYMMETRIC)) {
+    set_error("a segment range is drawn as COO only (no MH_OUT_CSR, no MH_CSR_SYMMETRIC)");
+    return MH_ERR_ARG;
+  }
+  Outputs o{src, dst, model == MH_UECM ? w : nullptr, nullptr, nullptr, nullptr, capacity_edges};
+  return run_sample(model, x, model == MH_UECM ? y : nullptr, n, params, workspace, workspace_bytes, o,
+                    h_edges_per_sample, h_stats, reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, 0,
+                    SegRange{seg_begin, seg_end});
 }
 
 int mh_bipartite_workspace_size(int model, int64_t n_plus, int64_t n_minus, const mh_params* params,

@@ -74,7 +74,7 @@ class Sampler:
                  seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
                  layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
                  capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0,
-                 extra_flags: int = 0, symmetric: bool = False):
+                 extra_flags: int = 0, symmetric: bool = False, seg_range: tuple[int, int] | None = None):
         self.model = int(model)
         self.x = _check_vec("x", x)
         self.n = int(self.x.shape[0])
@@ -95,6 +95,11 @@ class Sampler:
         self.seg_target = int(seg_target)
         self.max_segments = int(max_segments)
         self.walk_ctas_per_sm = int(walk_ctas_per_sm)
+        # seg_range = (seg_begin, seg_end): draw only those rows of the segment
+        # table (mh_sample_range; COO layout only)
+        self.seg_range = None if seg_range is None else (int(seg_range[0]), int(seg_range[1]))
+        if self.seg_range is not None and layout != "coo":
+            raise ValueError("a segment range is drawn as COO only")
         self.device = self.x.device
         if capacity is None:
             capacity = max(1024, 16 * self.n * self.num_samples)
@@ -136,6 +141,10 @@ class Sampler:
         p = self.params(sample_begin)
         st = _stream_handle(stream)
         counts, stats = self._h_counts_p, self._h_stats_p
+        if self.seg_range is not None:
+            return nat.mh_sample_range(self.model, _ptr(self.x), _ptr(self.y), self.n, p, self.seg_range[0],
+                                       self.seg_range[1], _ptr(self.workspace), self.ws_bytes, _ptr(self.src),
+                                       _ptr(self.dst), _ptr(self.w), self.capacity, counts, stats, st)
         if self.model == nat.MH_UBCM:
             return nat.mh_sample_ubcm(_ptr(self.x), self.n, p, _ptr(self.workspace), self.ws_bytes, _ptr(self.src),
                                       _ptr(self.dst), _ptr(self.csr_off), _ptr(self.csr_idx), self.capacity, counts,
