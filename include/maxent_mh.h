@@ -422,6 +422,19 @@ int maxent_expected_jacobian_diag(int model, const double* x, const double* y, i
                                   double* dk_dy, double* ds_dx, double* ds_dy, mh_stream_t stream);
 
 /*
+ * maxent_expected_jacobian_diag_rows — the same for rows
+ * [row_begin, row_begin + row_count) over all columns: outputs hold
+ * row_count entries, entry r being row row_begin + r, bit for bit the value
+ * of the whole call (a row's sum does not depend on the rows launched with
+ * it).  With the _rows forms of the sums and gradient it lets ranks of a
+ * distributed fit each evaluate their own block of rows.  Errors as
+ * maxent_expected_fwd_rows.
+ */
+int maxent_expected_jacobian_diag_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                       int64_t row_count, double* dk_dx, double* dk_dy, double* ds_dx, double* ds_dy,
+                                       mh_stream_t stream);
+
+/*
  * maxent_expected_fwd_rows / maxent_expected_bwd_rows — the sums of
  * maxent_expected_fwd / _bwd (Sec. 2.2, Sec. 2.5, Sec. 4) for the rows i in
  * [row_begin, row_begin + row_count) only (every sum still runs over all

@@ -56,6 +56,7 @@ EXPORTED = (
     "maxent_expected_fwd_rows",
     "maxent_expected_bwd_rows",
     "maxent_expected_jacobian_diag",
+    "maxent_expected_jacobian_diag_rows",
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
@@ -164,6 +165,8 @@ def load(path: str | None = None):
         lib.maxent_expected_bwd_rows.restype = i32
         lib.maxent_expected_jacobian_diag.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_jacobian_diag.restype = i32
+        lib.maxent_expected_jacobian_diag_rows.argtypes = [i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+        lib.maxent_expected_jacobian_diag_rows.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
         lib.mh_bipartite_workspace_size.restype = i32
         lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
@@ -299,3 +302,9 @@ def mh_sample_bipartite(model, x_plus, y_plus, n_plus, x_minus, y_minus, n_minus
 
 def maxent_expected_jacobian_diag(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, stream) -> int:
     return load().maxent_expected_jacobian_diag(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, stream)
+
+
+def maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_dx, dk_dy, ds_dx, ds_dy,
+                                       stream) -> int:
+    return load().maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_dx, dk_dy, ds_dx,
+                                                     ds_dy, stream)

@@ -944,17 +944,24 @@ int maxent_expected_fwd(int model, const double* x, const double* y, int64_t n, 
   return maxent_expected_fwd_rows(model, x, y, n, 0, n, k_out, s_out, stream);
 }
 
-int maxent_expected_jacobian_diag(int model, const double* x, const double* y, int64_t n, double* dk_dx,
-                                  double* dk_dy, double* ds_dx, double* ds_dy, mh_stream_t stream) {
-  const int rc = check_row_range("maxent_expected_jacobian_diag", model, n, 0, n);
+int maxent_expected_jacobian_diag_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
+                                       int64_t row_count, double* dk_dx, double* dk_dy, double* ds_dx, double* ds_dy,
+                                       mh_stream_t stream) {
+  const int rc = check_row_range("maxent_expected_jacobian_diag", model, n, row_begin, row_count);
   if (rc != MH_OK) return rc;
+  if (row_count == 0) return MH_OK;
   if (!x || !dk_dx || (model == MH_UECM && (!y || !dk_dy || !ds_dx || !ds_dy))) {
     set_error("maxent_expected_jacobian_diag: a required pointer is NULL");
     return MH_ERR_ARG;
   }
-  MH_CUDA(mh::launch_expected_jacobian_diag(model, x, y, n, 0, n, dk_dx, dk_dy, ds_dx, ds_dy,
+  MH_CUDA(mh::launch_expected_jacobian_diag(model, x, y, n, row_begin, row_count, dk_dx, dk_dy, ds_dx, ds_dy,
                                             reinterpret_cast<cudaStream_t>(stream)));
   return MH_OK;
+}
+
+int maxent_expected_jacobian_diag(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                  double* dk_dy, double* ds_dx, double* ds_dy, mh_stream_t stream) {
+  return maxent_expected_jacobian_diag_rows(model, x, y, n, 0, n, dk_dx, dk_dy, ds_dx, ds_dy, stream);
 }
 
 int maxent_expected_bwd_rows(int model, const double* x, const double* y, int64_t n, int64_t row_begin,

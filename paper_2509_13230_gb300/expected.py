@@ -69,8 +69,22 @@ class FitResult:
     history: list
 
 
-def _residual(model, x, y, k_t, s_t):
-    k, s = expected_fwd(model, x, y)
+class _LocalSums:
+    """The sums of a fit on this process's GPU (the module's functions, looked
+    up at call time)."""
+
+    def fwd(self, model, x, y=None):
+        return expected_fwd(model, x, y)
+
+    def bwd(self, model, x, y, g_k, g_s=None):
+        return expected_bwd(model, x, y, g_k, g_s)
+
+    def diag(self, model, x, y=None):
+        return expected_jacobian_diag(model, x, y)
+
+
+def _residual(model, x, y, k_t, s_t, ops):
+    k, s = ops.fwd(model, x, y)
     rk = (k - k_t) / k_t
     rs = None if s is None else (s - s_t) / s_t
     worst = float(rk.abs().max()) if rs is None else max(float(rk.abs().max()), float(rs.abs().max()))
@@ -78,23 +92,24 @@ def _residual(model, x, y, k_t, s_t):
     return k, s, rk, rs, worst, merit
 
 
-def _diagonal_blocks(model, x, y, n):
+def _diagonal_blocks(model, x, y, n, ops):
     """Per-node d<k_i>/dtheta_i (UBCM) or the 2x2 block of d(<k_i>, <s_i>) /
     d(theta_i, phi_i) (UECM), theta = log x and phi = log y: the Jacobian
     diagonal kernel's derivatives in x and y times x_i and y_i."""
     if model == nat.MH_UBCM:
-        (dk_dx,) = expected_jacobian_diag(model, x, None)
+        (dk_dx,) = ops.diag(model, x, None)
         return (dk_dx * x,)
-    dk_dx, dk_dy, ds_dx, ds_dy = expected_jacobian_diag(model, x, y)
+    dk_dx, dk_dy, ds_dx, ds_dy = ops.diag(model, x, y)
     return dk_dx * x, dk_dy * y, ds_dx * x, ds_dy * y
 
 
-def _jvp(model, x, y, v):
+def _jvp(model, x, y, v, ops=None):
     """J v in log-parameters (J symmetric: the vector-Jacobian product)."""
+    ops = ops or _LocalSums()
     if model == nat.MH_UBCM:
-        gx, _ = expected_bwd(model, x, None, v[0].contiguous())
+        gx, _ = ops.bwd(model, x, None, v[0].contiguous())
         return (gx * x,)
-    gx, gy = expected_bwd(model, x, y, v[0].contiguous(), v[1].contiguous())
+    gx, gy = ops.bwd(model, x, y, v[0].contiguous(), v[1].contiguous())
     return gx * x, gy * y
 
 
@@ -111,11 +126,12 @@ def _dot(u, v):
     return float(sum((a * b).sum() for a, b in zip(u, v)))
 
 
-def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int):
+def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int, ops=None):
     """Preconditioned conjugate gradients on J d = b, started from the
     block-diagonal solution."""
+    ops = ops or _LocalSums()
     d = _precond(blocks, b)
-    Jd = _jvp(model, x, y, d)
+    Jd = _jvp(model, x, y, d, ops)
     r = tuple(bi - ji for bi, ji in zip(b, Jd))
     bnorm = math.sqrt(_dot(b, b))
     z = _precond(blocks, r)
@@ -124,7 +140,7 @@ def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int):
     for _ in range(maxiter):
         if math.sqrt(_dot(r, r)) <= rtol * bnorm:
             break
-        Ap = _jvp(model, x, y, p)
+        Ap = _jvp(model, x, y, p, ops)
         pAp = _dot(p, Ap)
         if not pAp > 0.0:
             break
@@ -140,7 +156,7 @@ def _newton_direction(model, x, y, blocks, b, *, rtol: float, maxiter: int):
 
 def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None, y0=None, tol: float = 1e-8,
         adam_steps: int = 0, lr: float = 0.05, newton_steps: int = 100, cg_iters: int = 12,
-        cg_rtol: float = 0.05, max_step: float = 2.0, verbose: bool = False) -> FitResult:
+        cg_rtol: float = 0.05, max_step: float = 2.0, verbose: bool = False, sums=None) -> FitResult:
     """Fit x (UBCM) or x, y (UECM) so that the expected degrees (and strengths)
     equal the targets.  Targets are float64 CUDA tensors with k_i > 0 (and
     s_i > k_i, since every weight is at least 1).
@@ -153,7 +169,12 @@ def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None
     Newton stage: each step solves J d = -(<k> - k, <s> - s) by up to
     cg_iters preconditioned conjugate-gradient iterations (relative residual
     cg_rtol), scales d to at most max_step per log-parameter, and backtracks
-    on the sum of squared relative residuals."""
+    on the sum of squared relative residuals.
+    sums: where the Newton stage's sums, gradients and Jacobian diagonal come
+    from (default: this GPU); ``distributed.ShardedSums(group)`` splits them
+    by rows over the ranks of a torch.distributed group, every rank then
+    taking the same steps (the Adam stage stays on each rank's GPU)."""
+    ops = sums if sums is not None else _LocalSums()
     model = nat.MH_UECM if s_target is not None else nat.MH_UBCM
     k_t = k_target.to(torch.float64).contiguous()
     s_t = None if s_target is None else s_target.to(torch.float64).contiguous()
@@ -196,15 +217,15 @@ def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None
     phi = None if phi is None else torch.clamp(phi.detach(), max=-1e-9)
     x = torch.exp(theta)
     y = None if phi is None else torch.exp(phi)
-    k, s, rk, rs, worst, merit = _residual(model, x, y, k_t, s_t)
+    k, s, rk, rs, worst, merit = _residual(model, x, y, k_t, s_t, ops)
     it = 0
     for it in range(1, newton_steps + 1):
         if worst <= tol:
             it -= 1
             break
-        blocks = _diagonal_blocks(model, x, y, n)
+        blocks = _diagonal_blocks(model, x, y, n, ops)
         b = (k_t - k,) if model == nat.MH_UBCM else (k_t - k, s_t - s)
-        d = _newton_direction(model, x, y, blocks, b, rtol=cg_rtol, maxiter=cg_iters)
+        d = _newton_direction(model, x, y, blocks, b, rtol=cg_rtol, maxiter=cg_iters, ops=ops)
         biggest = max(float(di.abs().max()) for di in d)
         if biggest > max_step:
             d = tuple(di * (max_step / biggest) for di in d)
@@ -215,7 +236,7 @@ def fit(k_target: torch.Tensor, s_target: torch.Tensor | None = None, *, x0=None
             ph_new = None if phi is None else torch.clamp(phi + t * d[1], max=-1e-9)
             x_new = torch.exp(th_new)
             y_new = None if ph_new is None else torch.exp(ph_new)
-            k_new, s_new, rk_new, rs_new, worst_new, merit_new = _residual(model, x_new, y_new, k_t, s_t)
+            k_new, s_new, rk_new, rs_new, worst_new, merit_new = _residual(model, x_new, y_new, k_t, s_t, ops)
             if merit_new < (1.0 - 1e-4 * t) * merit:
                 accepted = True
                 break

@@ -311,15 +311,22 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
     return gx, gy
 
 
-def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None):
     """(d<k>/dx,) for the UBCM or (d<k>/dx, d<k>/dy, d<s>/dx, d<s>/dy) for the
     UECM: each node's derivatives of its own expected degree (and strength)
-    with respect to its own parameters, FP64 CUDA tensors."""
+    with respect to its own parameters, FP64 CUDA tensors; rows as in
+    expected_fwd."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
-    outs = [torch.empty_like(x) for _ in range(1 if model == nat.MH_UBCM else 4)]
+    begin, count = _row_range(rows, n)
+    outs = [torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
+            for _ in range(1 if model == nat.MH_UBCM else 4)]
     ptrs = [_ptr(t) for t in outs] + [None] * (4 - len(outs))
-    nat.check(nat.maxent_expected_jacobian_diag(model, _ptr(x), _ptr(y), n, *ptrs, _stream_handle(stream)),
-              "maxent_expected_jacobian_diag")
+    if rows is None:
+        rc = nat.maxent_expected_jacobian_diag(model, _ptr(x), _ptr(y), n, *ptrs, _stream_handle(stream))
+    else:
+        rc = nat.maxent_expected_jacobian_diag_rows(model, _ptr(x), _ptr(y), n, begin, count, *ptrs,
+                                                    _stream_handle(stream))
+    nat.check(rc, "maxent_expected_jacobian_diag")
     return tuple(outs)

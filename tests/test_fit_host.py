@@ -73,8 +73,9 @@ def test_newton_direction_solves_the_linear_system(oracle_kernels):
     x = torch.from_numpy(np.exp(rng.normal(-1.0, 0.7, n)))
     y = torch.from_numpy(rng.uniform(0.3, 0.8, n))
     b = (torch.from_numpy(rng.normal(size=n)), torch.from_numpy(rng.normal(size=n)))
-    blocks = E._diagonal_blocks(nat.MH_UECM, x, y, n)
-    d = E._newton_direction(nat.MH_UECM, x, y, blocks, b, rtol=1e-12, maxiter=200)
-    jd = E._jvp(nat.MH_UECM, x, y, d)
+    ops = E._LocalSums()
+    blocks = E._diagonal_blocks(nat.MH_UECM, x, y, n, ops)
+    d = E._newton_direction(nat.MH_UECM, x, y, blocks, b, rtol=1e-12, maxiter=200, ops=ops)
+    jd = E._jvp(nat.MH_UECM, x, y, d, ops)
     for lhs, rhs in zip(jd, b):
         np.testing.assert_allclose(lhs.numpy(), rhs.numpy(), rtol=1e-8, atol=1e-9)
