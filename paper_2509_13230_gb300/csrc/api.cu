@@ -615,6 +615,7 @@ static int run_sample(int model, const double* x, const double* y, int64_t n, co
                       cudaStream_t s, const double* xr = nullptr, const double* yr = nullptr, int64_t rows = 0,
                       SegRange range = SegRange{}) {
   const bool bip = xr != nullptr;
+  g_info = mh_call_info{0, 0, 0, 0.0, 0.0, 0.0, 0.0};  // describes this call, also when it is rejected
   if (!bip) rows = n;
   int rc = check_params_impl(model, rows, n, bip, p);
   if (rc != MH_OK) return rc;

@@ -602,45 +602,76 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
     }
     __syncthreads();
     const long long o0 = off[0], o1 = off[nit];
-    for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
-      int lo = 0, hi = nit - 1;  // last local item with off <= pos
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= pos)
-          lo = mid;
-        else
-          hi = mid - 1;
+    // kEmitUnroll edges per thread and pass (positions tid + u * blockDim),
+    // their loads issued together: the staged ranks, then the node ids and
+    // ln y of the candidates, then the weights and stores
+    int lo_prev = 0;
+    for (long long pos0 = o0 + threadIdx.x; pos0 < o1; pos0 += kEmitUnroll * static_cast<long long>(blockDim.x)) {
+      int itx[kEmitUnroll], ee[kEmitUnroll], gjs[kEmitUnroll];
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
+        itx[u] = -1;
+        if (pos >= o1) continue;
+        int lo = lo_prev, hi = nit - 1;  // last local item with off <= pos (positions only grow)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (off[mid] <= pos)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        lo_prev = lo;
+        const int e = static_cast<int>(pos - off[lo]);
+        if (e >= info[lo].cnt) {  // offsets inconsistent with the counts: never read past a run
+          bad = true;
+          continue;
+        }
+        itx[u] = lo;
+        ee[u] = e;
       }
-      const EmitItem& it = info[lo];
-      const int e = static_cast<int>(pos - off[lo]);
-      if (e >= it.cnt) {
-        bad = true;
-        continue;
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u)
+        gjs[u] = itx[u] >= 0 ? P.staging[info[itx[u]].base + ee[u]] : 0;
+      int32_t vv[kEmitUnroll];
+      float2 lj[kEmitUnroll];
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        vv[u] = 0;
+        lj[u] = make_float2(0.f, 0.f);
+        if (itx[u] < 0) continue;
+        const EmitItem& it = info[itx[u]];
+        const int j = gjs[u] - it.nb;
+        if (j <= it.i || j >= it.n) {  // cannot happen for a walked segment; never index with it
+          bad = true;
+          itx[u] = -1;
+          continue;
+        }
+        vv[u] = g.perm[gjs[u]];
+        if (it.uecm) lj[u] = g.lny[gjs[u]];
       }
-      const int gj = P.staging[it.base + e];
-      const int j = gj - it.nb;
-      if (j <= it.i || j >= it.n) {  // cannot happen for a walked segment; never index with it
-        bad = true;
-        continue;
-      }
-      const int32_t v = g.perm[gj];
-      int32_t wt = 1;
-      if (it.uecm) {
-        const float2 lj = g.lny[gj];
-        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
-                         it.sample, P.key0, it.key1, it.yi, &g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
-                         tab, fp64_only, overflow, fallbacks, boundary);
-      }
-      if (pos < P.o.capacity && P.o.src) {
-        P.o.src[pos] = it.u;
-        P.o.dst[pos] = v;
-        if (P.o.w) P.o.w[pos] = wt;
-      }
-      if (csr) {
-        const long long at = it.row_at + e;
-        if (at < P.o.capacity) {
-          P.o.csr_idx[at] = v;
-          if (P.o.csr_w) P.o.csr_w[at] = wt;
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        if (itx[u] < 0) continue;
+        const EmitItem& it = info[itx[u]];
+        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
+        const int e = ee[u];
+        int32_t wt = 1;
+        if (it.uecm)
+          wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
+                           it.sample, P.key0, it.key1, it.yi, &g.ys[gjs[u]], df2{it.lnyi.x, it.lnyi.y},
+                           df2{lj[u].x, lj[u].y}, tab, fp64_only, overflow, fallbacks, boundary);
+        if (pos < P.o.capacity && P.o.src) {
+          P.o.src[pos] = it.u;
+          P.o.dst[pos] = vv[u];
+          if (P.o.w) P.o.w[pos] = wt;
+        }
+        if (csr) {
+          const long long at = it.row_at + e;
+          if (at < P.o.capacity) {
+            P.o.csr_idx[at] = vv[u];
+            if (P.o.csr_w) P.o.csr_w[at] = wt;
+          }
         }
       }
     }

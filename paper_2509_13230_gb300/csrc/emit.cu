@@ -164,62 +164,96 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     }
     __syncthreads();
     const long long o0 = off[0], o1 = off[nit];
-    for (long long pos = o0 + threadIdx.x; pos < o1; pos += blockDim.x) {
-      int lo = 0, hi = nit - 1;  // last local item with off <= pos
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= pos)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const ItemRec& r = info[lo];
-      const int e = static_cast<int>(pos - off[lo]);
-      if (e >= r.cnt) {  // offsets inconsistent with the counts: never read past a run
-        bad = true;
-        continue;
-      }
-      const int32_t j = P.c.staging[r.base + e];
-      if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
-        bad = true;
-        continue;
-      }
-      const int32_t v = g.perm[j];
-      const long long q = pos - chunk_first_edge;  // position within the chunk
-      if (P.mode == kEmitSymForward) {
-        if (pos >= P.o.capacity) continue;
-        const long long at = r.at + e;
-        if (at >= 0 && at < 2 * P.o.capacity) {
-          P.o.csr_idx[at] = v;
-          if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
+    // kEmitUnroll edges per thread and pass (positions tid + u * blockDim),
+    // their loads issued together: the staged ranks, then the candidates'
+    // node ids and ln y, then the weights and stores
+    int lo_prev = 0;
+    for (long long pos0 = o0 + threadIdx.x; pos0 < o1; pos0 += kEmitUnroll * static_cast<long long>(blockDim.x)) {
+      int itx[kEmitUnroll], ee[kEmitUnroll], js[kEmitUnroll];
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
+        itx[u] = -1;
+        if (pos >= o1) continue;
+        int lo = lo_prev, hi = nit - 1;  // last local item with off <= pos (positions only grow)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (off[mid] <= pos)
+            lo = mid;
+          else
+            hi = mid - 1;
         }
-        continue;
-      }
-      int32_t wt = 1;
-      if (uecm) {
-        const float2 lj = g.lny[j];
-        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
-                         P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
-                         df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks, boundary);
-      }
-      if (pos < P.o.capacity) {
-        if (P.o.src) {
-          P.o.src[pos] = r.u;
-          P.o.dst[pos] = v;
-          if (P.o.w) P.o.w[pos] = wt;
+        lo_prev = lo;
+        const int e = static_cast<int>(pos - off[lo]);
+        if (e >= info[lo].cnt) {  // offsets inconsistent with the counts: never read past a run
+          bad = true;
+          continue;
         }
-        if (P.mode == kEmitSymPairs) {
-          P.c.sym.keys[0][q] = (static_cast<unsigned long long>(r.s_local) << 32) | static_cast<uint32_t>(j);
-          P.c.sym.vals[0][q] = static_cast<int32_t>(q);
-          P.c.sym.src[q] = r.u;
-          P.c.sym.w[q] = wt;
-          atomicAdd(reinterpret_cast<unsigned long long*>(&P.c.sym.rev[static_cast<long long>(r.s_local) * n1 + j]),
-                    1ull);
-        } else if (one_row_csr) {
+        itx[u] = lo;
+        ee[u] = e;
+      }
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) js[u] = itx[u] >= 0 ? P.c.staging[info[itx[u]].base + ee[u]] : 0;
+      int32_t vv[kEmitUnroll];
+      float2 lj[kEmitUnroll];
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        vv[u] = 0;
+        lj[u] = make_float2(0.f, 0.f);
+        if (itx[u] < 0) continue;
+        const ItemRec& r = info[itx[u]];
+        const int32_t j = js[u];
+        if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
+          bad = true;
+          itx[u] = -1;
+          continue;
+        }
+        vv[u] = g.perm[j];
+        if (uecm && P.mode != kEmitSymForward) lj[u] = g.lny[j];
+      }
+#pragma unroll
+      for (int u = 0; u < kEmitUnroll; ++u) {
+        if (itx[u] < 0) continue;
+        const ItemRec& r = info[itx[u]];
+        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
+        const int e = ee[u];
+        const int32_t j = js[u];
+        const int32_t v = vv[u];
+        const long long q = pos - chunk_first_edge;  // position within the chunk
+        if (P.mode == kEmitSymForward) {
+          if (pos >= P.o.capacity) continue;
           const long long at = r.at + e;
-          if (at < P.o.capacity) {
+          if (at >= 0 && at < 2 * P.o.capacity) {
             P.o.csr_idx[at] = v;
-            if (P.o.csr_w) P.o.csr_w[at] = wt;
+            if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
+          }
+          continue;
+        }
+        int32_t wt = 1;
+        if (uecm)
+          wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
+                           P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
+                           df2{r.lnyi.x, r.lnyi.y}, df2{lj[u].x, lj[u].y}, tab, fp64_only, overflow, fallbacks,
+                           boundary);
+        if (pos < P.o.capacity) {
+          if (P.o.src) {
+            P.o.src[pos] = r.u;
+            P.o.dst[pos] = v;
+            if (P.o.w) P.o.w[pos] = wt;
+          }
+          if (P.mode == kEmitSymPairs) {
+            P.c.sym.keys[0][q] = (static_cast<unsigned long long>(r.s_local) << 32) | static_cast<uint32_t>(j);
+            P.c.sym.vals[0][q] = static_cast<int32_t>(q);
+            P.c.sym.src[q] = r.u;
+            P.c.sym.w[q] = wt;
+            atomicAdd(
+                reinterpret_cast<unsigned long long*>(&P.c.sym.rev[static_cast<long long>(r.s_local) * n1 + j]), 1ull);
+          } else if (one_row_csr) {
+            const long long at = r.at + e;
+            if (at < P.o.capacity) {
+              P.o.csr_idx[at] = v;
+              if (P.o.csr_w) P.o.csr_w[at] = wt;
+            }
           }
         }
       }

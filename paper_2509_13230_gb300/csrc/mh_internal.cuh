@@ -61,6 +61,8 @@ constexpr int kScanTile = kScanThreads * kScanIPT;
 constexpr int kWalkWarps = 8;                    // warps per walk block
 constexpr int kSlot = 48;                        // edges a lane buffers in shared memory
 constexpr int kSlotStride = kSlot + 1;           // padded to spread banks
+constexpr int kFlushMin = 8;                     // walk: finished runs a warp gathers before it flushes them
+constexpr int kEmitUnroll = 4;                   // emit: edges a thread handles per pass
 constexpr int kMaxWalkWarps = 8192;              // cap on resident walk warps (staging slack)
 constexpr int kStageChunk = 1024;                // staging entries a warp reserves at a time
 constexpr int kEmitItems = 128;                  // work items per emit block
@@ -158,6 +160,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     const unsigned long long p1 = static_cast<unsigned long long>(0xCD9E8D57u) * c.z;
     c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
                    static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+  }
+  return c;
+}
+
+// Round keys of Philox4x32-10 (k_r = k + r W, mod 2^32, r = 0..9), set once
+// per launch so that a round reads its key as a kernel parameter.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys r;
+  for (int i = 0; i < 10; ++i) {
+    r.k0[i] = k0 + static_cast<uint32_t>(i) * 0x9E3779B9u;
+    r.k1[i] = k1 + static_cast<uint32_t>(i) * 0xBB67AE85u;
+  }
+  return r;
+}
+// philox4x32_10 with the round keys of word 0 precomputed, and of word 1
+// too (kK1 = true) or from a per-lane key k1 (batched networks).
+template <bool kK1>
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxKeys& rk, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (!kK1 && round) k1 += 0xBB67AE85u;
+    const uint32_t kr1 = kK1 ? rk.k1[round] : k1;
+    const unsigned long long p0 = static_cast<unsigned long long>(0xD2511F53u) * c.x;
+    const unsigned long long p1 = static_cast<unsigned long long>(0xCD9E8D57u) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ rk.k0[round], static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ kr1, static_cast<uint32_t>(p0));
   }
   return c;
 }

@@ -36,7 +36,8 @@ struct WalkParams {
   Net g;
   ChunkArgs c;
   Ctrl* ctrl;
-  BatchQueue q;  // batched waves only
+  BatchQueue q;    // batched waves only
+  PhiloxKeys rk;   // round keys of (key0, key1); batched waves use rk.k0 and each network's key1
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -125,8 +126,8 @@ struct SegWalker {
 
   // One iteration.  Returns false when the segment has ended; sets
   // `accepted` / `j` when a candidate was evaluated (never on a head step).
-  template <bool kUecm, bool kExcl = false>
-  __device__ __forceinline__ bool advance(const Net& g, uint32_t key0, uint32_t key1, bool fp64_only,
+  template <bool kUecm, bool kExcl = false, bool kLaneKey = false>
+  __device__ __forceinline__ bool advance(const Net& g, const PhiloxKeys& rk, uint32_t key1, bool fp64_only,
                                           bool init_prev, const LnEntry* tab, unsigned long long& fallbacks,
                                           unsigned long long& boundary, bool& accepted, int32_t& j) {
     accepted = false;
@@ -145,7 +146,8 @@ struct SegWalker {
     const bool e1 = e_ok;
     if (!head) d += 1;
     // Philox words and -ln U of the next draw (draw 0 on a head step)
-    rnd = philox4x32_10(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), key0, key1);
+    rnd = philox4x32_10_rk<!kLaneKey>(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), rk,
+                                      key1);
     Ef = neg_ln_u53_f(top53(rnd.y, rnd.x) + 1ull, tab, e_ok);
     int32_t jv;  // position of the candidate (virtual when kExcl)
     if (head) {
@@ -178,12 +180,12 @@ struct SegWalker {
       int verdict = -1;
       if (!kUecm) {
         if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f)
-          verdict = accept_decided(mV, __fdividef(prod.hi, 1.0f + prod.hi), q_f);
+          verdict = accept_decided(r.w, __fdividef(prod.hi, 1.0f + prod.hi), q_f);
       } else {
         const df2 yj = to_df(g.ydf[j]);
         const float omr = fmaf(-yi_df.hi, yj.hi, 1.0f) - fmaf(yi_df.hi, yj.lo, yi_df.lo * yj.hi);
         if (fast_q && prod.hi > 0x1p-100f && prod.hi < 0x1p40f && omr > 0x1p-20f)
-          verdict = accept_decided(mV, __fdividef(prod.hi, omr + prod.hi), q_f);
+          verdict = accept_decided(r.w, __fdividef(prod.hi, omr + prod.hi), q_f);
       }
       if (verdict < 0) {
         if (fast_q) fallbacks += 1;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
   const bool init_prev = (g.flags & MH_INIT_PREV) != 0;
   const unsigned long long cap = static_cast<unsigned long long>(P.c.staging_cap);
-  const uint32_t key0 = P.c.key0, key1 = P.c.key1;
+  const uint32_t key1 = P.c.key1;
 
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
@@ -297,87 +299,19 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   bool work_left = total > 0;
   unsigned long long n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0, n_boundary = 0;
 
+  // A lane whose segment ended keeps its run in its slot (pending) until
+  // the warp flushes: when kFlushMin runs are pending, or when no lane is
+  // walking.  Flushed lanes are then refilled together, so the warp-wide
+  // placement, copy and refill steps run once per several finished segments.
+  bool pending = false;
   while (true) {
-    if (work_left) {
-      unsigned idle = __ballot_sync(0xffffffffu, !active);
-      while (idle && work_left) {
-        if (next >= end) {
-          unsigned long long t0 = 0;
-          if (lane == 0) t0 = atomicAdd(ticket, chunk);
-          t0 = __shfl_sync(0xffffffffu, t0, 0);
-          if (t0 >= total) {
-            work_left = false;
-            break;
-          }
-          if (kBatch) qcur = queue_entry(P.q, t0);  // the same on every lane
-          next = t0;
-          end = t0 + chunk < total ? t0 + chunk : total;
-        }
-        const unsigned long long avail = end - next;
-        const unsigned rank = __popc(idle & lt);
-        if (!active && rank < avail) {
-          if (kBatch) {
-            qpos = static_cast<unsigned>(next + rank);
-            item = begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1);
-          } else {
-            item = static_cast<long long>(next + rank);
-            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
-          }
-          active = true;
-          rewalk = false;
-          cnt = 0;
-          n_segs += 1;
-        }
-        const unsigned take = __popc(idle);
-        next += take < avail ? take : avail;
-        idle = __ballot_sync(0xffffffffu, !active);
-      }
-    }
-    if (__ballot_sync(0xffffffffu, active) == 0u) break;
-
-    bool ended = false;
-    if (active) {
-      bool acc;
-      int32_t j;
-      if (wk.advance<kUecm, kExcl>(g, key0, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab, n_fallback,
-                                   n_boundary, acc, j)) {
-        if (acc) {
-          if (!rewalk) {
-            if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
-          } else if (rbase + cnt < cap) {
-            P.c.staging[rbase + cnt] = j;
-          }
-          cnt += 1;
-        }
-      } else if (rewalk) {
-        active = false;  // second pass done; count and base were recorded
-      } else {
-        n_draws += wk.d;
-        n_edges += cnt;
-        if (cnt <= static_cast<unsigned>(kSlot)) {
-          ended = true;
-        } else {
-          // too many edges for the slot: reserve exactly cnt entries and walk again
-          rbase = atomicAdd(&ctrl->stage_used, static_cast<unsigned long long>(cnt));
-          if (rbase + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
-          P.c.item_cnt[item] = cnt;
-          P.c.item_base[item] = static_cast<long long>(rbase);
-          if (kBatch)
-            begin_queued<kUecm>(g, P.q, qpos, queue_entry(P.q, qpos), wk, lane_key1);
-          else
-            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
-          rewalk = true;
-          cnt = 0;
-        }
-      }
-    }
-
-    const unsigned ended_mask = __ballot_sync(0xffffffffu, ended);
-    if (ended_mask) {
-      // Place the ended lanes' runs in the warp's staging chunk, in lane
+    const unsigned act_mask = __ballot_sync(0xffffffffu, active);
+    const unsigned pend_mask = __ballot_sync(0xffffffffu, pending);
+    if (pend_mask && (__popc(pend_mask) >= kFlushMin || act_mask == 0u)) {
+      // Place the pending lanes' runs in the warp's staging chunk, in lane
       // order; lanes that do not fit go to a fresh chunk (a run never spans
       // two chunks, so each segment stays contiguous).
-      const unsigned need = ended ? cnt : 0u;  // an ended run holds at most kSlot ranks
+      const unsigned need = pending ? cnt : 0u;  // a pending run holds at most kSlot ranks
       unsigned incl = need;
 #pragma unroll
       for (int dd = 1; dd < 32; dd <<= 1) {
@@ -387,7 +321,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
       const unsigned excl = incl - need;
       const unsigned warp_need = __shfl_sync(0xffffffffu, incl, 31);
       const bool fits = incl <= wleft;
-      const unsigned spill_mask = __ballot_sync(0xffffffffu, ended && !fits);
+      const unsigned spill_mask = __ballot_sync(0xffffffffu, pending && !fits);
       unsigned long long my_base = wbase + excl;
       if (spill_mask) {
         const int first = __ffs(spill_mask) - 1;  // lanes from `first` on move to the new chunk
@@ -404,13 +338,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
         wbase += warp_need;
         wleft -= warp_need;
       }
-      if (ended) {
+      if (pending) {
         P.c.item_cnt[item] = cnt;
         P.c.item_base[item] = static_cast<long long>(my_base);
         if (my_base + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
       }
       __syncwarp();
-      // Copy all ended runs in one pass: element idx of the concatenated
+      // Copy all pending runs in one pass: element idx of the concatenated
       // runs belongs to the last lane whose exclusive prefix is <= idx.
       const int32_t* wslots = slots + warp * 32 * kSlotStride;
       for (unsigned r0 = 0; r0 < warp_need; r0 += 32) {
@@ -429,7 +363,82 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
         }
       }
       __syncwarp();
-      if (ended) active = false;
+      pending = false;
+    }
+    if (work_left) {
+      unsigned idle = __ballot_sync(0xffffffffu, !active && !pending);
+      if (idle && (__popc(idle) >= kFlushMin || act_mask == 0u)) {
+        while (idle && work_left) {
+          if (next >= end) {
+            unsigned long long t0 = 0;
+            if (lane == 0) t0 = atomicAdd(ticket, chunk);
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            if (t0 >= total) {
+              work_left = false;
+              break;
+            }
+            if (kBatch) qcur = queue_entry(P.q, t0);  // the same on every lane
+            next = t0;
+            end = t0 + chunk < total ? t0 + chunk : total;
+          }
+          const unsigned long long avail = end - next;
+          const unsigned rank = __popc(idle & lt);
+          if (!active && !pending && rank < avail) {
+            if (kBatch) {
+              qpos = static_cast<unsigned>(next + rank);
+              item = begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1);
+            } else {
+              item = static_cast<long long>(next + rank);
+              wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
+            }
+            active = true;
+            rewalk = false;
+            cnt = 0;
+            n_segs += 1;
+          }
+          const unsigned take = __popc(idle);
+          next += take < avail ? take : avail;
+          idle = __ballot_sync(0xffffffffu, !active && !pending);
+        }
+      }
+    }
+    if (__ballot_sync(0xffffffffu, active || pending) == 0u) break;
+
+    if (active) {
+      bool acc;
+      int32_t j;
+      if (wk.advance<kUecm, kExcl, kBatch>(g, P.rk, kBatch ? lane_key1 : key1, fp64_only, init_prev, tab,
+                                           n_fallback, n_boundary, acc, j)) {
+        if (acc) {
+          if (!rewalk) {
+            if (cnt < static_cast<unsigned>(kSlot)) my_slot[cnt] = j;
+          } else if (rbase + cnt < cap) {
+            P.c.staging[rbase + cnt] = j;
+          }
+          cnt += 1;
+        }
+      } else if (rewalk) {
+        active = false;  // second pass done; count and base were recorded
+      } else {
+        n_draws += wk.d;
+        n_edges += cnt;
+        if (cnt <= static_cast<unsigned>(kSlot)) {
+          active = false;
+          pending = true;  // the run waits in the slot for the next flush
+        } else {
+          // too many edges for the slot: reserve exactly cnt entries and walk again
+          rbase = atomicAdd(&ctrl->stage_used, static_cast<unsigned long long>(cnt));
+          if (rbase + cnt > cap) atomicOr(&ctrl->status, kStCapacity);
+          P.c.item_cnt[item] = cnt;
+          P.c.item_base[item] = static_cast<long long>(rbase);
+          if (kBatch)
+            begin_queued<kUecm>(g, P.q, qpos, queue_entry(P.q, qpos), wk, lane_key1);
+          else
+            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
+          rewalk = true;
+          cnt = 0;
+        }
+      }
     }
   }
 
@@ -500,7 +509,7 @@ static unsigned walk_blocks(int dev, bool uecm, int mode, int ctas_per_sm) {
 }
 
 cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream_t s) {
-  WalkParams P{g, c, ctrl, BatchQueue{}};
+  WalkParams P{g, c, ctrl, BatchQueue{}, philox_round_keys(c.key0, c.key1)};
   const bool uecm = g.model == MH_UECM;
   const int mode = g.excl ? 2 : 0;
   cudaError_t e = prepare_kernel_attributes(g.model);
@@ -519,7 +528,7 @@ cudaError_t launch_walk(const Net& g, const ChunkArgs& c, Ctrl* ctrl, cudaStream
 // g holds the concatenated arrays of all networks.
 cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQueue& q, Ctrl* ctrl, int model,
                                 cudaStream_t s) {
-  WalkParams P{g, c, ctrl, q};
+  WalkParams P{g, c, ctrl, q, philox_round_keys(c.key0, c.key1)};
   const bool uecm = model == MH_UECM;
   cudaError_t e = prepare_kernel_attributes(model);
   if (e != cudaSuccess) return e;

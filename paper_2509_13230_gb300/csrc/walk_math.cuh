@@ -374,10 +374,12 @@ static __device__ __noinline__ unsigned skip_fp64(unsigned long long N, double q
 }
 
 // Acceptance filter: 1 = accept, 0 = reject, -1 = undecided (use FP64).
-// p_f / q_f approximates p/q to a relative error well below 2^-18.
-__device__ __forceinline__ int accept_decided(unsigned long long mV, float p_f, float q_f) {
+// p_f / q_f approximates p/q to a relative error well below 2^-18.  vw is
+// the high word of the draw's words (3,2): V = top53(vw, lo) 2^-53 lies in
+// [vlo, vlo + 2^-24) with vlo = (vw >> 8) 2^-24 (a 32-bit convert, exact).
+__device__ __forceinline__ int accept_decided(uint32_t vw, float p_f, float q_f) {
   const float R = __fdividef(p_f, q_f);
-  const float vlo = static_cast<float>(mV >> 29) * 0x1p-24f;          // V in [vlo, vlo + 2^-24)
+  const float vlo = __uint2float_rn(vw >> 8) * 0x1p-24f;
   const float vhi = vlo + 0x1p-24f;
   if (vhi <= R * (1.0f - 0x1p-18f)) return 1;
   if (vlo >= R * (1.0f + 0x1p-18f)) return 0;
