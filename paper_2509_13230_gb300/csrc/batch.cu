@@ -472,7 +472,12 @@ __global__ void batch_pair_counts_kernel(BatchView V, const long long* __restric
 }
 
 // CSR counts of every (pair, node) of the wave, in place of the offsets.
-__global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ rank,
+// Per-(pair, node) edge counts of the CSR rows (row u holds the edges whose
+// higher-ranked endpoint is u), written where the offsets go: entry o of a
+// pair's n + 1 is visited in rank order i, its count read from the item
+// offsets of row i's segments (coalesced) and stored at u = perm[i] (one
+// scattered write); the last entry of each pair is 0 for the scan's total.
+__global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ perm,
                                        const long long* __restrict__ rowoff, const long long* __restrict__ item_off,
                                        long long* __restrict__ csr_off) {
   const long long total = V.wc->num_segments;
@@ -485,14 +490,14 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
     const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
     const unsigned rel = static_cast<unsigned>(o - w.csr_base);
     const long long s = rel / n1;
-    const long long u = rel - static_cast<unsigned>(s) * n1;
-    long long c = 0;
-    if (u < bn.n) {
-      const long long i = rank[bn.node_base + u];
+    const long long i = rel - static_cast<unsigned>(s) * n1;
+    long long c = 0, u = bn.n;
+    if (i < bn.n) {
       const long long b0 = w.item_begin + s * w.S;
       c = item_off[b0 + rowoff[bn.node1_base + i + 1]] - item_off[b0 + rowoff[bn.node1_base + i]];
+      u = perm[bn.node_base + i];
     }
-    csr_off[o] = c;
+    csr_off[w.csr_base + s * n1 + u] = c;
   }
 }
 
@@ -556,7 +561,11 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
     if (threadIdx.x == 32)
       net_hi = last_at_or_below(V.n_nets, it1 - 1, [&](int q) { return V.wave[q].item_begin; });
     __syncthreads();
-    if (threadIdx.x < nit) {
+    // Most items of sparse rows are empty: their edge count decides whether
+    // the rest of the record (network, segment, row id, CSR position) is read.
+    const int my_cnt = threadIdx.x < nit ? static_cast<int>(P.item_cnt[it0 + threadIdx.x]) : 0;
+    if (threadIdx.x < nit && my_cnt == 0) info[threadIdx.x].cnt = 0;  // never selected by the edge loop
+    if (threadIdx.x < nit && my_cnt > 0) {
       const long long item = it0 + threadIdx.x;
       int t = net_lo, hi = net_hi;
       while (t < hi) {
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
       const long long gi = bn.node_base + sg.x;
       EmitItem it;
       it.base = P.item_base[item];
-      it.cnt = static_cast<int>(P.item_cnt[item]);
+      it.cnt = my_cnt;
       it.i = sg.x;
       it.u = g.perm[gi];
       it.k = sg.y;
@@ -1280,7 +1289,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     MHB_CUDA(cudaGetLastError());
     if (out.csr_off) {
       batch_csr_count_kernel<<<grid_for(B.csr_max, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
-          V, gall.rank, gall.rowoff, c.item_off, out.csr_off);
+          V, gall.perm, gall.rowoff, c.item_off, out.csr_off);
       note_launches(1);
       MHB_CUDA(cudaGetLastError());
       e = scan_any<long long, SumOp<long long>>(out.csr_off, out.csr_off, ScanLen{B.csr_max, &wc->num_segments, 1},

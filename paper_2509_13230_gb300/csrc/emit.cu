@@ -42,14 +42,17 @@ __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, 
   const int64_t total = chunk_samples * n1;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t s = t / n1, u = t - s * n1;
+    // visited in rank order i (coalesced reads of the row and item offsets),
+    // stored at the row's id u = perm[i]; the last entry of a sample is 0
+    const int64_t s = t / n1, i = t - s * n1;
     long long c = 0;
-    if (u < g.rows) {
-      const int64_t i = g.rank_r[u];
+    int64_t u = g.rows;
+    if (i < g.rows) {
       c = item_off[s * S + g.rowoff[i + 1]] - item_off[s * S + g.rowoff[i]];
       if (rev) c += rev[s * n1 + i];
+      u = g.perm_r[i];
     }
-    csr_off[chunk_first * n1 + t] = c;
+    csr_off[chunk_first * n1 + s * n1 + u] = c;
   }
 }
 
@@ -131,14 +134,17 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
     const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
     const int nit = static_cast<int>(it1 - it0);
     for (int t = threadIdx.x; t <= nit; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
-    if (threadIdx.x < nit) {
+    // empty items (most items of sparse rows) skip the rest of their record
+    const int my_cnt = threadIdx.x < nit ? static_cast<int>(P.c.item_cnt[it0 + threadIdx.x]) : 0;
+    if (threadIdx.x < nit && my_cnt == 0) info[threadIdx.x].cnt = 0;  // never selected by the edge loop
+    if (threadIdx.x < nit && my_cnt > 0) {
       const long long item = it0 + threadIdx.x;
       const int s_local = static_cast<int>(static_cast<unsigned>(item) / static_cast<unsigned>(S));  // items < 2^31
       const long long seg = item - static_cast<long long>(s_local) * S;
       const int4 sg = g.seg[seg];
       ItemRec r;
       r.base = P.c.item_base[item];
-      r.cnt = static_cast<int>(P.c.item_cnt[item]);
+      r.cnt = my_cnt;
       r.i = sg.x;
       r.u = g.perm_r[sg.x];
       r.k = sg.y;

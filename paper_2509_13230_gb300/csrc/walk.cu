@@ -422,7 +422,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
       } else {
         n_draws += wk.d;
         n_edges += cnt;
-        if (cnt <= static_cast<unsigned>(kSlot)) {
+        if (cnt == 0) {
+          active = false;  // nothing to place: the lane is free at once
+          P.c.item_cnt[item] = 0;
+          P.c.item_base[item] = 0;
+        } else if (cnt <= static_cast<unsigned>(kSlot)) {
           active = false;
           pending = true;  // the run waits in the slot for the next flush
         } else {
