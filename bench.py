@@ -300,13 +300,14 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=None
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(1, min(args.steps, 3))
-    total_ms, edges, out_bytes, waves = 0.0, 0, 0, 0
+    total_ms, edges, out_bytes, waves, proposals = 0.0, 0, 0, 0, 0
     for k in walk:
         walk[k] = 0.0
     for _ in range(steps):
         flush.zero_()
         ev0.record(stream)
-        counts, _ = one_pass()
+        counts, st = one_pass()
+        proposals += int(st[nat.MH_STAT_PROPOSALS])
         ev1.record(stream)
         ev1.synchronize()
         total_ms += ev0.elapsed_time(ev1)
@@ -355,7 +356,7 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=None
         "workload": f"ensemble_{len(nets)}_x{samples}" + ("" if fitness == "pareto" else f"_{fitness}"),
         "fitness": fitness, "networks": len(nets), "nodes": int(n.sum()),
         "samples_per_network": samples, "value": value, "unit": "edges/s", "ms_per_step": total_ms / steps,
-        "edges_per_step": edges // steps, "waves_per_step": waves / steps,
+        "edges_per_step": edges // steps, "proposals_per_step": proposals // steps, "waves_per_step": waves / steps,
         "output": "CSR int64 offsets + int32 indices (+ int32 weights for the UECM half)",
         "write_gbs_of_step": out_bytes / steps / (total_ms / steps / 1e3) / 1e9,
         "walk_ms_per_step": walk_ms,
