@@ -735,6 +735,56 @@ def configs_leg(args, dev, flush):
 
 
 # ---------------------------------------------------------------------------
+# Brute force against the walk on the GPU (the comparison of the paper's
+# Fig. 3A, Sec. 3.1, on synthetic Pareto fitness with mean degree about 20):
+# one sample per call, device time of each, N from 10^3 to 10^6.
+# ---------------------------------------------------------------------------
+BF_SIZES = (1_000, 10_000, 100_000, 1_000_000)
+
+
+def bf_leg(args, dev):
+    import torch
+
+    from paper_2509_13230_gb300 import _native as nat
+    from paper_2509_13230_gb300 import workloads
+    from paper_2509_13230_gb300.sampler import BruteForceSampler, Sampler
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for n in BF_SIZES:
+        rng = np.random.default_rng(1000 + n)
+        x_np = np.minimum(workloads.pareto_scale(n) * rng.uniform(0.0, 1.0, n) ** (-1.0 / 1.1), 50.0)
+        x = torch.from_numpy(x_np).to(dev)
+
+        def timed(call, reps):
+            call()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                call()
+            ev1.record(stream)
+            ev1.synchronize()
+            return ev0.elapsed_time(ev1) / reps
+
+        mh = Sampler(nat.MH_UBCM, x, None, num_samples=1, seg_target=16)
+        mh.run()
+        mh_ms = timed(lambda: nat.check(mh.call(), "mh_sample_ubcm"), 10)
+        bf = BruteForceSampler(nat.MH_UBCM, x, None, num_samples=1)
+        bf.run()
+        bf_ms = timed(lambda: nat.check(bf.call(), "mh_sample_bf"), 3 if n <= 100_000 else 1)
+        pairs = n * (n - 1) / 2
+        rows.append({"n": n, "edges_mh": int(mh.h_counts.sum()), "edges_bf": int(bf.h_counts.sum()),
+                     "mh_ms": mh_ms, "bf_ms": bf_ms, "bf_pairs_per_s": pairs / (bf_ms / 1e3),
+                     "bf_over_mh_time": bf_ms / mh_ms})
+        del mh, bf
+    return {"workload": "ubcm_pareto_bf_vs_mh", "model": "UBCM", "fitness": "x = min(c(N) u^(-1/1.1), 50)",
+            "note": "one sample per call, whole call (prepare + walk + emit for the walk; both passes of the "
+                    "brute force), CUDA events; the paper reports 10-100x on CPU (Sec. 3.1, Fig. 3A)",
+            "sizes": rows}
+
+
+# ---------------------------------------------------------------------------
 # Output layouts of the headline workload: one-row CSR and the symmetric CSR
 # (every edge in both endpoint rows), same samples and segment length.
 # ---------------------------------------------------------------------------
@@ -1334,6 +1384,7 @@ def run_ours(args, rank, world, local_rank):
             subs["fit_then_sample"] = fit_leg(args, dev)
             subs["bipartite"] = bipartite_leg(args, dev, flush)
             subs["configs"] = configs_leg(args, dev, flush)
+            subs["brute_force"] = bf_leg(args, dev)
         subs["layouts"] = layouts_leg(args, dev, flush, subs["uecm_n20k_x10"]["seg_target"])
         fitted, cpu_bf = subs.get("fit_then_sample"), subs["uecm_n20k_x10"].get("cpu_brute_force")
         if fitted is not None and cpu_bf is not None:
@@ -1384,7 +1435,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the long sub-legs (lognormal ensemble, pairwise, fit, bipartite, configs)")
     ap.add_argument("--headline-only", action="store_true", help="only the batched-ensemble headline")
-    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs", "kernels"],
+    ap.add_argument("--leg", choices=["all", "ensemble", "pairwise", "fit", "bipartite", "layouts", "configs", "kernels",
+                                      "bf"],
                     default="all",
                     help="run only that leg and print its object; kernels: each profiled kernel once, "
                          "untimed (walk at T = 8, 16, 32, then pairwise forward, backward, Jacobian "
@@ -1443,6 +1495,10 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"kernels_once": kernels_once(torch.device("cuda", local_rank))}), flush=True)
+    elif args.leg == "bf":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"brute_force": bf_leg(args, torch.device("cuda", local_rank))}), flush=True)
     elif args.leg == "pairwise":
         import torch
         torch.cuda.set_device(local_rank)

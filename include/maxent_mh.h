@@ -77,6 +77,14 @@ typedef struct CUstream_st* mh_stream_t; /* the same handle as cudaStream_t */
 #define MH_TIMING 0x200u     /* time the call's phases with CUDA events on the     */
                              /* caller's stream (see mh_last_call_info); calls of  */
                              /* more than 1024 sample chunks are not timed         */
+#define MH_CHUNG_LU 0x800u   /* mh_sample_ubcm, mh_sample_bf (MH_UBCM), the        */
+                             /* fixed-scratch call: the Chung-Lu law              */
+                             /* p_ij = min(1, x_i x_j) instead of Eq. 1 (Sec. 2.1: */
+                             /* the expected multiplicity k_i k_j / 2M read as a  */
+                             /* probability), sampled by the same walk (the       */
+                             /* Miller-Hagberg original, Sec. 2.3) with every     */
+                             /* draw decided by the FP64 expressions; for         */
+                             /* comparisons with the UBCM                          */
 #define MH_TEST_WAIT_TIMEOUT 0x400u /* test hook for the bounded device waits: in    */
                              /* every single-pass scan of the call, tile 1 first    */
                              /* waits on a device flag that nothing sets; the wait  */
@@ -340,6 +348,36 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
                       int64_t pair_count, int32_t* src, int32_t* dst, int32_t* w, int64_t* csr_offsets,
                       int32_t* csr_indices, int32_t* csr_weights, int64_t capacity_edges,
                       int64_t* h_edges_per_pair, uint64_t* h_stats, mh_stream_t stream);
+
+/*
+ * mh_bf_workspace_size / mh_sample_bf — the brute-force sampler (Sec. 2.2;
+ * the comparison baseline of Sec. 3): every pair u < v of original ids is an
+ * independent Bernoulli(p_uv) (Eq. 1, or Eq. 3 for MH_UECM), and a UECM edge
+ * draws its weight w ~ Geometric(1 - r_uv) on {1, 2, ...} (Eq. 4).  N (N - 1)
+ * / 2 pair evaluations per sample, against the walk's O(N + M).
+ *   Random words of pair (u, v) in sample s: Philox4x32-10 of the counter
+ *   {u, v, 0xB0F0B0F0, s}, key (seed lo32, seed hi32 + network_id); words
+ *   (1,0) give V on [0, 1), kept when V < p_uv (FP64); words (3,2) give
+ *   U_w on (0, 1], w = 1 + floor(log(U_w) / log(r)) (w = 1 when r = 0).
+ *   Samples [sample_begin, sample_begin + num_samples) one after another,
+ *   each sample's edges by (u, v).  Agrees with the walk in distribution,
+ *   not in bits.
+ *   model, x, y, n, params   as mh_sample_weighted (num_samples, seed,
+ *                           network_id, sample_begin and MH_FP64_ONLY are
+ *                           read; segment length and output flags are not)
+ *   src, dst, w            COO int32[capacity_edges] (w: MH_UECM)
+ *   h_edges_per_sample     host int64[num_samples]
+ *   h_stats                host uint64[MH_NUM_STATS] or NULL: pair
+ *                          evaluations (MH_STAT_PROPOSALS), edges, FP64
+ *                          decisions, weight boundary draws
+ * Workspace: mh_bf_workspace_size (about 12 B per node plus 8 B per 2^16
+ * pairs).  MH_ERR_CAPACITY keeps the exact counts; re-calling with more room
+ * draws the same samples.  Other errors as mh_sample_weighted.
+ */
+int mh_bf_workspace_size(int model, int64_t n, const mh_params* params, size_t* h_bytes);
+int mh_sample_bf(int model, const double* x, const double* y, int64_t n, const mh_params* params, void* workspace,
+                 size_t workspace_bytes, int32_t* src, int32_t* dst, int32_t* w, int64_t capacity_edges,
+                 int64_t* h_edges_per_sample, uint64_t* h_stats, mh_stream_t stream);
 
 /*
  * mh_sample_ubcm_noalloc — mh_sample_ubcm without a caller-supplied

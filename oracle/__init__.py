@@ -36,6 +36,7 @@ import numpy as np
 
 UBCM = 0
 UECM = 1
+CL = 2  # Chung-Lu: p_ij = min(1, x_i x_j) (Sec. 2.1; the Miller-Hagberg original, Sec. 2.3)
 BOUND_PAPER = 0x1
 INIT_PREV = 0x2
 
@@ -371,6 +372,8 @@ def graph_probabilities(model, alpha, beta=None):
         if model == UBCM:
             e = math.exp(-alpha[u] - alpha[v])
             probs.append(e / (1.0 + e))
+        elif model == CL:  # expected multiplicity k_u k_v / 2M taken as a probability, capped at 1
+            probs.append(min(1.0, math.exp(-alpha[u] - alpha[v])))
         else:
             num = math.exp(-alpha[u] - alpha[v] - beta[u] - beta[v])
             probs.append(num / (1.0 - math.exp(-beta[u] - beta[v]) + num))

@@ -34,6 +34,7 @@
 
 #define ORC_UBCM 0
 #define ORC_UECM 1
+#define ORC_CL 2 /* Chung-Lu: p_ij = min(1, x_i x_j), Sec. 2.1 and the MH algorithm of Sec. 2.3 */
 
 /* flags */
 #define ORC_BOUND_PAPER 0x1u /* c = product of the two largest y among ranks >= i */
@@ -211,7 +212,7 @@ static void net_build(net_t* g, int model, const double* x, const double* y, int
     g->top2 = (double*)malloc(sizeof(double) * (cnt + 1));
 
     double* key = (double*)malloc(sizeof(double) * cnt);
-    for (int64_t u = 0; u < n; ++u) key[u] = (model == ORC_UBCM) ? x[u] : x[u] * y[u];
+    for (int64_t u = 0; u < n; ++u) key[u] = (model != ORC_UECM) ? x[u] : x[u] * y[u];
     orc_sort_desc(key, n, g->perm);
     free(key);
 
@@ -244,6 +245,10 @@ static double prob(const net_t* g, int64_t i, int64_t j)
     if (g->model == ORC_UBCM) {
         double z = g->xs[i] * g->xs[j];
         return z / (1.0 + z);
+    }
+    if (g->model == ORC_CL) {
+        double z = g->xs[i] * g->xs[j];
+        return z >= 1.0 ? 1.0 : z;
     }
     double A = g->as[i] * g->as[j];
     double r = g->ys[i] * g->ys[j];
@@ -293,7 +298,7 @@ static int bitlen_u64(uint64_t v)
 static void proxy_build(proxy_t* P, const net_t* g)
 {
     int64_t n = g->n;
-    const double* v = (g->model == ORC_UBCM) ? g->xs : g->as;
+    const double* v = (g->model != ORC_UECM) ? g->xs : g->as;
     double vmax = (n > 0) ? v[0] : 0.0;
     if (vmax > 0x1p20) vmax = 0x1p20;
     uint64_t bits;
@@ -314,7 +319,7 @@ static void proxy_build(proxy_t* P, const net_t* g)
 /* Per-row weight w_i: the cost of candidate j is min(1, w_i v_j). */
 static double row_weight(const net_t* g, int64_t i)
 {
-    if (g->model == ORC_UBCM) return g->xs[i];
+    if (g->model != ORC_UECM) return g->xs[i];
     double c;
     if (g->flags & ORC_BOUND_PAPER)
         c = g->top1[i] * g->top2[i];
@@ -326,7 +331,7 @@ static double row_weight(const net_t* g, int64_t i)
 /* First j in [i+1, n) with w v_j < 1, else n (products are non-increasing). */
 static int64_t unit_cut(const net_t* g, int64_t i, double w)
 {
-    const double* v = (g->model == ORC_UBCM) ? g->xs : g->as;
+    const double* v = (g->model != ORC_UECM) ? g->xs : g->as;
     int64_t lo = i + 1, hi = g->n;
     while (lo < hi) {
         int64_t mid = lo + (hi - lo) / 2;
@@ -610,6 +615,9 @@ int64_t orc_bf_sample(int model, const double* x, const double* y, int64_t n, ui
             if (model == ORC_UBCM) {
                 double z = x[u] * x[v];
                 p = z / (1.0 + z);
+            } else if (model == ORC_CL) {
+                double z = x[u] * x[v];
+                p = z >= 1.0 ? 1.0 : z;
             } else {
                 double A = (x[u] * y[u]) * (x[v] * y[v]);
                 r = y[u] * y[v];

@@ -32,6 +32,7 @@ MH_CSR_SYMMETRIC = 0x80
 MH_FP64_ONLY = 0x100
 MH_TIMING = 0x200
 MH_TEST_WAIT_TIMEOUT = 0x400
+MH_CHUNG_LU = 0x800
 
 MH_STAT_PROPOSALS = 0
 MH_STAT_EDGES = 1
@@ -49,6 +50,8 @@ EXPORTED = (
     "mh_sample_ubcm",
     "mh_sample_weighted",
     "mh_sample_range",
+    "mh_bf_workspace_size",
+    "mh_sample_bf",
     "mh_sample_ubcm_noalloc",
     "mh_segment_table",
     "maxent_expected_fwd",
@@ -151,6 +154,10 @@ def load(path: str | None = None):
         lib.mh_sample_weighted.restype = i32
         lib.mh_sample_range.argtypes = [i32, vp, vp, i64, P, i64, i64, vp, sz, vp, vp, vp, i64, vp, vp, vp]
         lib.mh_sample_range.restype = i32
+        lib.mh_bf_workspace_size.argtypes = [i32, i64, P, vp]
+        lib.mh_bf_workspace_size.restype = i32
+        lib.mh_sample_bf.argtypes = [i32, vp, vp, i64, P, vp, sz, vp, vp, vp, i64, vp, vp, vp]
+        lib.mh_sample_bf.restype = i32
         lib.mh_sample_ubcm_noalloc.argtypes = [vp, i64, P, vp, vp, vp, vp, i64, vp, vp, vp]
         lib.mh_sample_ubcm_noalloc.restype = i32
         lib.mh_segment_table.argtypes = [i32, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp]
@@ -235,6 +242,18 @@ def mh_sample_range(model, x, y, n, params, seg_begin, seg_end, workspace, works
                     capacity_edges, h_edges_per_sample, h_stats, stream) -> int:
     return load().mh_sample_range(model, x, y, n, ctypes.byref(params), seg_begin, seg_end, workspace,
                                   workspace_bytes, src, dst, w, capacity_edges, h_edges_per_sample, h_stats, stream)
+
+
+def mh_bf_workspace_size(model, n, params) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().mh_bf_workspace_size(model, n, ctypes.byref(params), ctypes.byref(out)), "mh_bf_workspace_size")
+    return out.value
+
+
+def mh_sample_bf(model, x, y, n, params, workspace, workspace_bytes, src, dst, w, capacity_edges,
+                 h_edges_per_sample, h_stats, stream) -> int:
+    return load().mh_sample_bf(model, x, y, n, ctypes.byref(params), workspace, workspace_bytes, src, dst, w,
+                               capacity_edges, h_edges_per_sample, h_stats, stream)
 
 
 def mh_sample_ubcm_noalloc(x, n, params, src, dst, csr_offsets, csr_indices, capacity_edges, h_edges_per_sample,

@@ -98,7 +98,7 @@ thread_local PinnedBuffer g_pinned;
 
 constexpr uint32_t kKnownFlags =
     MH_OUT_COO | MH_OUT_CSR | MH_BOUND_PAPER | MH_INIT_PREV | MH_DIRECTED | MH_CSR_SYMMETRIC | MH_FP64_ONLY |
-    MH_TIMING | MH_TEST_WAIT_TIMEOUT;
+    MH_TIMING | MH_TEST_WAIT_TIMEOUT | MH_CHUNG_LU;
 
 }  // namespace
 
@@ -354,6 +354,10 @@ static int check_params_impl(int model, int64_t rows, int64_t n, bool bip, const
   }
   if ((p->flags & MH_CSR_SYMMETRIC) && (bip || !(p->flags & MH_OUT_CSR))) {
     set_error("MH_CSR_SYMMETRIC needs MH_OUT_CSR and one node set (mh_sample_ubcm / mh_sample_weighted)");
+    return MH_ERR_ARG;
+  }
+  if ((p->flags & MH_CHUNG_LU) && (model != MH_UBCM || bip)) {
+    set_error("MH_CHUNG_LU applies to one-set MH_UBCM calls only");
     return MH_ERR_ARG;
   }
   if (bip && (p->flags & (MH_BOUND_PAPER | MH_INIT_PREV))) {

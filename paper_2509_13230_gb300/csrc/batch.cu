@@ -883,8 +883,8 @@ int check_batch(const mh_network_desc* nets, int32_t n_nets, const mh_params* p)
     set_error("params->network_id must be 0 for a batch (each network has its own)");
     return MH_ERR_ARG;
   }
-  if (p->flags & MH_CSR_SYMMETRIC) {
-    set_error("MH_CSR_SYMMETRIC applies to mh_sample_ubcm and mh_sample_weighted only");
+  if (p->flags & (MH_CSR_SYMMETRIC | MH_CHUNG_LU)) {
+    set_error("MH_CSR_SYMMETRIC and MH_CHUNG_LU apply to single-network calls only");
     return MH_ERR_ARG;
   }
   int64_t nodes = 0, segs = 0;

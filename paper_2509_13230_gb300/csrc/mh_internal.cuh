@@ -333,6 +333,8 @@ cudaError_t launch_export_table(const Net& g, const Ctrl* ctrl, int32_t* row, in
 
 // Existing sampling steps, reachable from the fixed-scratch entry point.
 int check_sample_params(int model, int64_t n, const mh_params* p);
+int64_t take_launch_count();                          // kernels launched since the last call (and resets)
+void record_call_info(const mh_call_info& info);      // what mh_last_call_info returns
 Net net_view(int model, const mh_params& p, const double* x, const double* y, int64_t n, const Layout& L,
              char* ws);
 int enqueue_sample_direct(const Net& g, const Layout& L, char* ws, const mh_params* p, const Outputs& o, char* hbuf,

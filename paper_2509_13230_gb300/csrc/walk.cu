@@ -76,7 +76,8 @@ struct SegWalker {
 
   // Canonical FP64 values are read back on the (rare) FP64 paths.
   __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
-    return uecm ? prob_hat(g.as_r[gi], g.as[qj], g.seg_c[seg]) : prob_ubcm(g.xs_r[gi], g.xs[qj]);
+    if (uecm) return prob_hat(g.as_r[gi], g.as[qj], g.seg_c[seg]);
+    return (g.flags & MH_CHUNG_LU) ? prob_cl(g.xs_r[gi], g.xs[qj]) : prob_ubcm(g.xs_r[gi], g.xs[qj]);
   }
 
   // Loads row segment `seg` of sample `smp`; its head is set up by the next
@@ -190,8 +191,9 @@ struct SegWalker {
       if (verdict < 0) {
         if (fast_q) fallbacks += 1;
         if (!have_qc) qc = q64(g, kUecm);
-        const double p =
-            kUecm ? prob_uecm(g.as_r[gi], g.as[j], g.ys_r[gi] * g.ys[j]) : prob_ubcm(g.xs_r[gi], g.xs[j]);
+        const double p = kUecm                     ? prob_uecm(g.as_r[gi], g.as[j], g.ys_r[gi] * g.ys[j])
+                         : (g.flags & MH_CHUNG_LU) ? prob_cl(g.xs_r[gi], g.xs[j])
+                                                   : prob_ubcm(g.xs_r[gi], g.xs[j]);
         verdict = (static_cast<double>(mV) * 0x1p-53 < p / qc) ? 1 : 0;
       }
       accepted = verdict != 0;
@@ -265,7 +267,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   int32_t* my_slot = slots + (warp * 32 + lane) * kSlotStride;
-  const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
+  // the Chung-Lu law (MH_CHUNG_LU) has no fast levels: every draw is FP64
+  const bool fp64_only = (g.flags & (MH_FP64_ONLY | MH_CHUNG_LU)) != 0;
   const bool init_prev = (g.flags & MH_INIT_PREV) != 0;
   const unsigned long long cap = static_cast<unsigned long long>(P.c.staging_cap);
   const uint32_t key1 = P.c.key1;

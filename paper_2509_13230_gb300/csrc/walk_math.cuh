@@ -55,6 +55,11 @@ __device__ __forceinline__ double prob_ubcm(double xi, double xj) {
   const double z = xi * xj;
   return z / (1.0 + z);
 }
+// Chung-Lu (MH_CHUNG_LU): the expected multiplicity read as a probability.
+__device__ __forceinline__ double prob_cl(double xi, double xj) {
+  const double z = xi * xj;
+  return z >= 1.0 ? 1.0 : z;
+}
 __device__ __forceinline__ double prob_uecm(double ai, double aj, double r) {
   const double A = ai * aj;
   return A / ((1.0 - r) + A);

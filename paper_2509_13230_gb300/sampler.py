@@ -74,7 +74,8 @@ class Sampler:
                  seed: int = 0, network_id: int = 0, sample_begin: int = 0, seg_target: int = 0,
                  layout: str = "coo", bound: str = "suffix", init: str = "head", fp64_only: bool = False,
                  capacity: int | None = None, max_segments: int = 0, walk_ctas_per_sm: int = 0,
-                 extra_flags: int = 0, symmetric: bool = False, seg_range: tuple[int, int] | None = None):
+                 extra_flags: int = 0, symmetric: bool = False, seg_range: tuple[int, int] | None = None,
+                 chung_lu: bool = False):
         self.model = int(model)
         self.x = _check_vec("x", x)
         self.n = int(self.x.shape[0])
@@ -89,6 +90,8 @@ class Sampler:
             flags |= nat.MH_FP64_ONLY
         if symmetric:
             flags |= nat.MH_CSR_SYMMETRIC
+        if chung_lu:  # p = min(1, x_i x_j) (MH_UBCM only)
+            flags |= nat.MH_CHUNG_LU
         self.flags = flags | int(extra_flags)
         self.num_samples = int(num_samples)
         self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
@@ -221,6 +224,60 @@ def sample_ubcm(x: torch.Tensor, **kw) -> SampleResult:
 def sample_weighted(x: torch.Tensor, y: torch.Tensor, **kw) -> SampleResult:
     """UECM samples with integer weights (Sec. 2.5, Algorithm 1)."""
     return Sampler(nat.MH_UECM, x, y, **kw).run()
+
+
+class BruteForceSampler:
+    """Reusable buffers for the brute-force sampler (mh_sample_bf): every pair
+    an independent Bernoulli draw (Sec. 2.2), COO output by (u, v); the
+    comparison baseline of the walk (Sec. 3)."""
+
+    def __init__(self, model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, num_samples: int = 1,
+                 seed: int = 0, network_id: int = 0, sample_begin: int = 0, fp64_only: bool = False,
+                 capacity: int | None = None, chung_lu: bool = False):
+        self.model = int(model)
+        self.x = _check_vec("x", x)
+        self.n = int(self.x.shape[0])
+        self.y = _check_vec("y", y, self.n) if self.model == nat.MH_UECM else None
+        self.num_samples = int(num_samples)
+        self.seed, self.network_id, self.sample_begin = int(seed), int(network_id), int(sample_begin)
+        self.flags = (nat.MH_OUT_COO | (nat.MH_FP64_ONLY if fp64_only else 0)
+                      | (nat.MH_CHUNG_LU if chung_lu else 0))
+        p = self.params()
+        self.ws_bytes = nat.mh_bf_workspace_size(self.model, self.n, p)
+        self.workspace = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.x.device)
+        self.h_counts = np.zeros(self.num_samples, dtype=np.int64)
+        self.h_stats = np.zeros(nat.MH_NUM_STATS, dtype=np.uint64)
+        self._alloc(capacity if capacity is not None else max(1024, 16 * self.n * self.num_samples))
+
+    def params(self, sample_begin: int | None = None) -> nat.MhParams:
+        return nat.make_params(seed=self.seed, network_id=self.network_id,
+                               sample_begin=self.sample_begin if sample_begin is None else sample_begin,
+                               num_samples=self.num_samples, flags=self.flags)
+
+    def _alloc(self, capacity: int):
+        self.capacity = int(capacity)
+        dev = self.x.device
+        self.src = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.dst = torch.empty_like(self.src)
+        self.w = torch.empty_like(self.src) if self.model == nat.MH_UECM else None
+
+    def call(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> int:
+        return nat.mh_sample_bf(self.model, _ptr(self.x), _ptr(self.y), self.n, self.params(sample_begin),
+                                _ptr(self.workspace), self.ws_bytes, _ptr(self.src), _ptr(self.dst), _ptr(self.w),
+                                self.capacity, self.h_counts.ctypes.data_as(ctypes.c_void_p),
+                                self.h_stats.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream))
+
+    def run(self, sample_begin: int | None = None, stream: torch.cuda.Stream | None = None) -> SampleResult:
+        for _ in range(4):
+            rc = self.call(sample_begin, stream)
+            if rc == nat.MH_ERR_CAPACITY:
+                self._alloc(int(self.h_counts.sum() * 1.05) + 1024)
+                continue
+            nat.check(rc, "mh_sample_bf")
+            tot = int(self.h_counts.sum())
+            return SampleResult(self.h_counts.copy(), self.h_stats.copy(), self.src[:tot], self.dst[:tot],
+                                None if self.w is None else self.w[:tot])
+        raise RuntimeError("sampling did not converge on buffer sizes")
 
 
 def segment_table(model: int, x: torch.Tensor, y: torch.Tensor | None = None, *, seg_target: int = 0,
