@@ -472,12 +472,7 @@ __global__ void batch_pair_counts_kernel(BatchView V, const long long* __restric
 }
 
 // CSR counts of every (pair, node) of the wave, in place of the offsets.
-// Per-(pair, node) edge counts of the CSR rows (row u holds the edges whose
-// higher-ranked endpoint is u), written where the offsets go: entry o of a
-// pair's n + 1 is visited in rank order i, its count read from the item
-// offsets of row i's segments (coalesced) and stored at u = perm[i] (one
-// scattered write); the last entry of each pair is 0 for the scan's total.
-__global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ perm,
+__global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ rank,
                                        const long long* __restrict__ rowoff, const long long* __restrict__ item_off,
                                        long long* __restrict__ csr_off) {
   const long long total = V.wc->num_segments;
@@ -490,14 +485,14 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
     const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
     const unsigned rel = static_cast<unsigned>(o - w.csr_base);
     const long long s = rel / n1;
-    const long long i = rel - static_cast<unsigned>(s) * n1;
-    long long c = 0, u = bn.n;
-    if (i < bn.n) {
+    const long long u = rel - static_cast<unsigned>(s) * n1;
+    long long c = 0;
+    if (u < bn.n) {
+      const long long i = rank[bn.node_base + u];
       const long long b0 = w.item_begin + s * w.S;
       c = item_off[b0 + rowoff[bn.node1_base + i + 1]] - item_off[b0 + rowoff[bn.node1_base + i]];
-      u = perm[bn.node_base + i];
     }
-    csr_off[w.csr_base + s * n1 + u] = c;
+    csr_off[o] = c;
   }
 }
 
@@ -1289,7 +1284,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     MHB_CUDA(cudaGetLastError());
     if (out.csr_off) {
       batch_csr_count_kernel<<<grid_for(B.csr_max, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
-          V, gall.perm, gall.rowoff, c.item_off, out.csr_off);
+          V, gall.rank, gall.rowoff, c.item_off, out.csr_off);
       note_launches(1);
       MHB_CUDA(cudaGetLastError());
       e = scan_any<long long, SumOp<long long>>(out.csr_off, out.csr_off, ScanLen{B.csr_max, &wc->num_segments, 1},

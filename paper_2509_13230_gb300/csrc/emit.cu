@@ -42,17 +42,14 @@ __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, 
   const int64_t total = chunk_samples * n1;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    // visited in rank order i (coalesced reads of the row and item offsets),
-    // stored at the row's id u = perm[i]; the last entry of a sample is 0
-    const int64_t s = t / n1, i = t - s * n1;
+    const int64_t s = t / n1, u = t - s * n1;
     long long c = 0;
-    int64_t u = g.rows;
-    if (i < g.rows) {
+    if (u < g.rows) {
+      const int64_t i = g.rank_r[u];
       c = item_off[s * S + g.rowoff[i + 1]] - item_off[s * S + g.rowoff[i]];
       if (rev) c += rev[s * n1 + i];
-      u = g.perm_r[i];
     }
-    csr_off[chunk_first * n1 + s * n1 + u] = c;
+    csr_off[chunk_first * n1 + t] = c;
   }
 }
 
