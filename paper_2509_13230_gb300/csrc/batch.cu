@@ -525,51 +525,50 @@ struct EmitItem {
   float2 lnyi;
   double yi;
 };
-constexpr int kBatchEmitItems = 256;
+// Warps take groups of kEmitGroup consecutive work items: lane l sets up
+// item l's EmitItem in the warp's shared slice, then the group's edges are
+// written 32 at a time, lane l taking edge (pass * 32 + l) of the group.
+// Its item is the last lane whose first-edge offset (relative to the group)
+// is at most that index: a five-step search over the offsets held by the
+// lanes.  Empty items share their offset with the next item, so the search
+// never selects them.  No block-wide barrier: warps move on independently.
+constexpr int kBatchEmitWarps = 8;
 
-// Blocks take kBatchEmitItems consecutive work items at a time: one thread
-// per item sets up its EmitItem, then consecutive threads write consecutive
-// edges of the items.
-__global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
+__global__ void __launch_bounds__(kBatchEmitWarps * 32) batch_emit_kernel(BatchEmitParams P) {
   const BatchView& V = P.V;
   const Net& g = P.g;
   Ctrl* wc = V.wc;
   __shared__ LnEntry tab[kLnTable];
-  __shared__ long long off[kBatchEmitItems + 1];
-  __shared__ EmitItem info[kBatchEmitItems];
-  __shared__ int net_lo, net_hi;
+  __shared__ EmitItem info_all[kBatchEmitWarps][kEmitGroup];
   if (P.any_uecm) ln_table_to_shared(tab, g.lntab);
   __syncthreads();
   const long long items = wc->wave_items;
   if (wc->stage_used > static_cast<unsigned long long>(P.staging_cap)) return;  // staging overflowed
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
   const bool csr = P.o.csr_idx != nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  EmitItem* info = info_all[warp];
   unsigned long long fallbacks = 0, boundary = 0;  // weight draws left to FP64; boundary draws
   bool overflow = false, bad = false;
-  for (long long it0 = static_cast<long long>(blockIdx.x) * kBatchEmitItems; it0 < items;
-       it0 += static_cast<long long>(gridDim.x) * kBatchEmitItems) {
-    const long long it1 = it0 + kBatchEmitItems < items ? it0 + kBatchEmitItems : items;
-    const int nit = static_cast<int>(it1 - it0);
-    for (int t = threadIdx.x; t <= nit; t += blockDim.x) off[t] = P.item_off[it0 + t];
-    // networks of the first and last item bound every item's network
-    if (threadIdx.x == 0) net_lo = last_at_or_below(V.n_nets, it0, [&](int q) { return V.wave[q].item_begin; });
-    if (threadIdx.x == 32)
-      net_hi = last_at_or_below(V.n_nets, it1 - 1, [&](int q) { return V.wave[q].item_begin; });
-    __syncthreads();
-    // Most items of sparse rows are empty: their edge count decides whether
-    // the rest of the record (network, segment, row id, CSR position) is read.
-    const int my_cnt = threadIdx.x < nit ? static_cast<int>(P.item_cnt[it0 + threadIdx.x]) : 0;
-    if (threadIdx.x < nit && my_cnt == 0) info[threadIdx.x].cnt = 0;  // never selected by the edge loop
-    if (threadIdx.x < nit && my_cnt > 0) {
-      const long long item = it0 + threadIdx.x;
-      int t = net_lo, hi = net_hi;
-      while (t < hi) {
-        const int mid = (t + hi + 1) >> 1;
-        if (V.wave[mid].item_begin <= item)
-          t = mid;
-        else
-          hi = mid - 1;
-      }
+  const long long stride = static_cast<long long>(gridDim.x) * kBatchEmitWarps * kEmitGroup;
+  for (long long g0 = (static_cast<long long>(blockIdx.x) * kBatchEmitWarps + warp) * kEmitGroup; g0 < items;
+       g0 += stride) {
+    const long long item = g0 + lane;
+    const bool in = item < items;
+    // the group's edges are [item_off[g0], item_off[g0 + 32]) (item_off holds items + 1 entries)
+    const long long off_l = P.item_off[in ? item : items];
+    const long long first = __shfl_sync(0xffffffffu, off_l, 0);
+    const long long last = lane == 31 ? P.item_off[in ? item + 1 : items] : 0;
+    const long long total = __shfl_sync(0xffffffffu, last, 31) - first;
+    if (total == 0) continue;  // a group of empty items (common in sparse rows)
+    if (total >= (1ll << 31)) {  // cannot happen: a group's edges fit the staging, well below 2^31
+      bad = true;
+      continue;
+    }
+    const unsigned rel = static_cast<unsigned>(off_l - first);
+    const int my_cnt = in ? static_cast<int>(P.item_cnt[item]) : 0;
+    if (my_cnt > 0) {
+      const int t = last_at_or_below(V.n_nets, item, [&](int q) { return V.wave[q].item_begin; });
       const WaveNet& w = V.wave[t];
       const BatchNet& bn = V.nets[t];
       // a wave holds fewer than 2^31 items and a network fewer than 2^31 rows
@@ -594,7 +593,7 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
       if (csr) {
         const long long row_first = w.item_begin + static_cast<long long>(s_local) * S + g.rowoff[bn.node1_base + sg.x];
         it.row_at = P.o.csr_off[w.csr_base + static_cast<long long>(s_local) * (bn.n + 1) + it.u] +
-                    (P.item_off[item] - P.item_off[row_first]);
+                    (off_l - P.item_off[row_first]);
       }
       it.yi = 0.0;
       it.lnyi = make_float2(0.f, 0.f);
@@ -602,84 +601,55 @@ __global__ void __launch_bounds__(256) batch_emit_kernel(BatchEmitParams P) {
         it.yi = g.ys[gi];
         it.lnyi = g.lny[gi];
       }
-      info[threadIdx.x] = it;
+      info[lane] = it;
     }
-    __syncthreads();
-    const long long o0 = off[0], o1 = off[nit];
-    // kEmitUnroll edges per thread and pass (positions tid + u * blockDim),
-    // their loads issued together: the staged ranks, then the node ids and
-    // ln y of the candidates, then the weights and stores
-    int lo_prev = 0;
-    for (long long pos0 = o0 + threadIdx.x; pos0 < o1; pos0 += kEmitUnroll * static_cast<long long>(blockDim.x)) {
-      int itx[kEmitUnroll], ee[kEmitUnroll], gjs[kEmitUnroll];
+    __syncwarp();
+    const unsigned tot = static_cast<unsigned>(total);
+    for (unsigned p0 = 0; p0 < tot; p0 += 32) {
+      const unsigned idx = p0 + lane;
+      int l = 0;
 #pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
-        itx[u] = -1;
-        if (pos >= o1) continue;
-        int lo = lo_prev, hi = nit - 1;  // last local item with off <= pos (positions only grow)
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (off[mid] <= pos)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        lo_prev = lo;
-        const int e = static_cast<int>(pos - off[lo]);
-        if (e >= info[lo].cnt) {  // offsets inconsistent with the counts: never read past a run
-          bad = true;
-          continue;
-        }
-        itx[u] = lo;
-        ee[u] = e;
+      for (int step = 16; step; step >>= 1) {
+        const unsigned v = __shfl_sync(0xffffffffu, rel, l + step);
+        if (v <= idx) l += step;
       }
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u)
-        gjs[u] = itx[u] >= 0 ? P.staging[info[itx[u]].base + ee[u]] : 0;
-      int32_t vv[kEmitUnroll];
-      float2 lj[kEmitUnroll];
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        vv[u] = 0;
-        lj[u] = make_float2(0.f, 0.f);
-        if (itx[u] < 0) continue;
-        const EmitItem& it = info[itx[u]];
-        const int j = gjs[u] - it.nb;
-        if (j <= it.i || j >= it.n) {  // cannot happen for a walked segment; never index with it
-          bad = true;
-          itx[u] = -1;
-          continue;
-        }
-        vv[u] = g.perm[gjs[u]];
-        if (it.uecm) lj[u] = g.lny[gjs[u]];
+      const unsigned rel_l = __shfl_sync(0xffffffffu, rel, l);
+      if (idx >= tot) continue;
+      const EmitItem& it = info[l];
+      const int e = static_cast<int>(idx - rel_l);
+      if (e >= it.cnt) {  // offsets inconsistent with the counts: never read past a run
+        bad = true;
+        continue;
       }
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        if (itx[u] < 0) continue;
-        const EmitItem& it = info[itx[u]];
-        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
-        const int e = ee[u];
-        int32_t wt = 1;
-        if (it.uecm)
-          wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
-                           it.sample, P.key0, it.key1, it.yi, &g.ys[gjs[u]], df2{it.lnyi.x, it.lnyi.y},
-                           df2{lj[u].x, lj[u].y}, tab, fp64_only, overflow, fallbacks, boundary);
-        if (pos < P.o.capacity && P.o.src) {
-          P.o.src[pos] = it.u;
-          P.o.dst[pos] = vv[u];
-          if (P.o.w) P.o.w[pos] = wt;
-        }
-        if (csr) {
-          const long long at = it.row_at + e;
-          if (at < P.o.capacity) {
-            P.o.csr_idx[at] = vv[u];
-            if (P.o.csr_w) P.o.csr_w[at] = wt;
-          }
+      const int32_t gj = P.staging[it.base + e];
+      const int j = gj - it.nb;
+      if (j <= it.i || j >= it.n) {  // cannot happen for a walked segment; never index with it
+        bad = true;
+        continue;
+      }
+      const int32_t v = g.perm[gj];
+      int32_t wt = 1;
+      if (it.uecm) {
+        const float2 lj = g.lny[gj];
+        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(it.k), static_cast<uint32_t>(it.i),
+                         it.sample, P.key0, it.key1, it.yi, &g.ys[gj], df2{it.lnyi.x, it.lnyi.y}, df2{lj.x, lj.y},
+                         tab, fp64_only, overflow, fallbacks, boundary);
+      }
+      const long long pos = first + idx;
+      if (pos < P.o.capacity && P.o.src) {
+        P.o.src[pos] = it.u;
+        P.o.dst[pos] = v;
+        if (P.o.w) P.o.w[pos] = wt;
+      }
+      if (csr) {
+        const long long at = it.row_at + e;
+        if (at < P.o.capacity) {
+          P.o.csr_idx[at] = v;
+          if (P.o.csr_w) P.o.csr_w[at] = wt;
         }
       }
     }
-    __syncthreads();
+    __syncwarp();  // the slice is rewritten by the next group
   }
   if (overflow) atomicOr(&wc->status, kStOverflow);
   if (bad) atomicOr(&wc->status, kStInternal);
@@ -1293,7 +1263,8 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     }
     BatchEmitParams P{V, gall, c.item_cnt, c.item_base, c.item_off, c.staging, c.staging_cap, out, c.key0,
                       B.n_model[1] > 0};
-    batch_emit_kernel<<<grid_for(items_max, kBatchEmitItems, static_cast<unsigned>(sm_count()) * 6u), 256, 0, q>>>(P);
+    batch_emit_kernel<<<grid_for(items_max, kBatchEmitWarps * kEmitGroup, static_cast<unsigned>(sm_count()) * 5u),
+                        kBatchEmitWarps * 32, 0, q>>>(P);
     note_launches(1);
     MHB_CUDA(cudaGetLastError());
     MHB_CUDA(cudaMemcpyAsync(hback, wc, sizeof(Ctrl), cudaMemcpyDeviceToHost, q));

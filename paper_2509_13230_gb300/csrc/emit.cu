@@ -83,15 +83,19 @@ struct ItemRec {
   double yi;
 };
 
-// Blocks take kEmitItems consecutive work items at a time (a grid-stride
-// loop over the chunk's items): one thread per item sets up its ItemRec,
-// then consecutive threads write consecutive edges of the items.
-__global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
+// Warps take groups of kEmitGroup consecutive work items of the chunk (a
+// grid-stride loop): lane l sets up item l's ItemRec in the warp's shared
+// slice, then the group's edges are written 32 at a time, lane l taking
+// edge (pass * 32 + l) of the group.  Its item is the last lane whose
+// first-edge offset (relative to the group) is at most that index, found by
+// a five-step search over the offsets the lanes hold; empty items share
+// their offset with the next item and are never selected.  Warps move on
+// independently (no block-wide barrier after the logarithm table).
+__global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(EmitParams P) {
   const Net& g = P.g;
   Ctrl* ctrl = P.ctrl;
   __shared__ LnEntry tab[kLnTable];
-  __shared__ long long off[kEmitItems + 1];
-  __shared__ ItemRec info[kEmitItems];
+  __shared__ ItemRec info_all[kEmitWarps][kEmitGroup];
   const bool uecm = g.model == MH_UECM;
   if (uecm && P.mode != kEmitSymForward) ln_table_to_shared(tab, g.lntab);
   const bool fp64_only = (g.flags & MH_FP64_ONLY) != 0;
@@ -125,17 +129,27 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
   __syncthreads();  // the logarithm table
   const long long n1 = g.rows + 1;
   const bool one_row_csr = P.mode == kEmitPlain && P.o.csr_idx != nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ItemRec* info = info_all[warp];
   bool overflow = false, bad = false;
-  for (long long it0 = static_cast<long long>(blockIdx.x) * kEmitItems; it0 < items;
-       it0 += static_cast<long long>(gridDim.x) * kEmitItems) {
-    const long long it1 = it0 + kEmitItems < items ? it0 + kEmitItems : items;
-    const int nit = static_cast<int>(it1 - it0);
-    for (int t = threadIdx.x; t <= nit; t += blockDim.x) off[t] = P.c.item_off[it0 + t];
-    // empty items (most items of sparse rows) skip the rest of their record
-    const int my_cnt = threadIdx.x < nit ? static_cast<int>(P.c.item_cnt[it0 + threadIdx.x]) : 0;
-    if (threadIdx.x < nit && my_cnt == 0) info[threadIdx.x].cnt = 0;  // never selected by the edge loop
-    if (threadIdx.x < nit && my_cnt > 0) {
-      const long long item = it0 + threadIdx.x;
+  const long long stride = static_cast<long long>(gridDim.x) * kEmitWarps * kEmitGroup;
+  for (long long g0 = (static_cast<long long>(blockIdx.x) * kEmitWarps + warp) * kEmitGroup; g0 < items;
+       g0 += stride) {
+    const long long item = g0 + lane;
+    const bool in = item < items;
+    // the group's edges are [item_off[g0], item_off[g0 + 32]) (item_off holds items + 1 entries)
+    const long long off_l = P.c.item_off[in ? item : items];
+    const long long first = __shfl_sync(0xffffffffu, off_l, 0);
+    const long long last = lane == 31 ? P.c.item_off[in ? item + 1 : items] : 0;
+    const long long total = __shfl_sync(0xffffffffu, last, 31) - first;
+    if (total == 0) continue;  // a group of empty items (common in sparse rows)
+    if (total >= (1ll << 31)) {  // cannot happen: a group's edges fit the staging, well below 2^31
+      bad = true;
+      continue;
+    }
+    const unsigned rel = static_cast<unsigned>(off_l - first);
+    const int my_cnt = in ? static_cast<int>(P.c.item_cnt[item]) : 0;
+    if (my_cnt > 0) {
       const int s_local = static_cast<int>(static_cast<unsigned>(item) / static_cast<unsigned>(S));  // items < 2^31
       const long long seg = item - static_cast<long long>(s_local) * S;
       const int4 sg = g.seg[seg];
@@ -151,7 +165,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
       if (one_row_csr || P.mode == kEmitSymForward) {
         const long long s_all = P.c.chunk_first + s_local;
         const long long row_first = static_cast<long long>(s_local) * S + g.rowoff[sg.x];
-        r.at = P.o.csr_off[s_all * n1 + r.u] + (P.c.item_off[item] - P.c.item_off[row_first]);
+        r.at = P.o.csr_off[s_all * n1 + r.u] + (off_l - P.c.item_off[row_first]);
         if (P.mode == kEmitSymForward) {  // after the row's arriving edges
           const long long* rv = P.c.sym.rev + static_cast<long long>(s_local) * n1;
           r.at += rv[sg.x + 1] - rv[sg.x];
@@ -163,105 +177,73 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams P) {
         r.yi = g.ys_r[sg.x];
         r.lnyi = g.lny_r[sg.x];
       }
-      info[threadIdx.x] = r;
+      info[lane] = r;
     }
-    __syncthreads();
-    const long long o0 = off[0], o1 = off[nit];
-    // kEmitUnroll edges per thread and pass (positions tid + u * blockDim),
-    // their loads issued together: the staged ranks, then the candidates'
-    // node ids and ln y, then the weights and stores
-    int lo_prev = 0;
-    for (long long pos0 = o0 + threadIdx.x; pos0 < o1; pos0 += kEmitUnroll * static_cast<long long>(blockDim.x)) {
-      int itx[kEmitUnroll], ee[kEmitUnroll], js[kEmitUnroll];
+    __syncwarp();
+    const unsigned tot = static_cast<unsigned>(total);
+    for (unsigned p0 = 0; p0 < tot; p0 += 32) {
+      const unsigned idx = p0 + lane;
+      int l = 0;
 #pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
-        itx[u] = -1;
-        if (pos >= o1) continue;
-        int lo = lo_prev, hi = nit - 1;  // last local item with off <= pos (positions only grow)
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (off[mid] <= pos)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        lo_prev = lo;
-        const int e = static_cast<int>(pos - off[lo]);
-        if (e >= info[lo].cnt) {  // offsets inconsistent with the counts: never read past a run
-          bad = true;
-          continue;
-        }
-        itx[u] = lo;
-        ee[u] = e;
+      for (int step = 16; step; step >>= 1) {
+        const unsigned v = __shfl_sync(0xffffffffu, rel, l + step);
+        if (v <= idx) l += step;
       }
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) js[u] = itx[u] >= 0 ? P.c.staging[info[itx[u]].base + ee[u]] : 0;
-      int32_t vv[kEmitUnroll];
-      float2 lj[kEmitUnroll];
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        vv[u] = 0;
-        lj[u] = make_float2(0.f, 0.f);
-        if (itx[u] < 0) continue;
-        const ItemRec& r = info[itx[u]];
-        const int32_t j = js[u];
-        if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
-          bad = true;
-          itx[u] = -1;
-          continue;
-        }
-        vv[u] = g.perm[j];
-        if (uecm && P.mode != kEmitSymForward) lj[u] = g.lny[j];
+      const unsigned rel_l = __shfl_sync(0xffffffffu, rel, l);
+      if (idx >= tot) continue;
+      const ItemRec& r = info[l];
+      const int e = static_cast<int>(idx - rel_l);
+      if (e >= r.cnt) {  // offsets inconsistent with the counts: never read past a run
+        bad = true;
+        continue;
       }
-#pragma unroll
-      for (int u = 0; u < kEmitUnroll; ++u) {
-        if (itx[u] < 0) continue;
-        const ItemRec& r = info[itx[u]];
-        const long long pos = pos0 + static_cast<long long>(u) * blockDim.x;
-        const int e = ee[u];
-        const int32_t j = js[u];
-        const int32_t v = vv[u];
-        const long long q = pos - chunk_first_edge;  // position within the chunk
-        if (P.mode == kEmitSymForward) {
-          if (pos >= P.o.capacity) continue;
+      const int32_t j = P.c.staging[r.base + e];
+      if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
+        bad = true;
+        continue;
+      }
+      const int32_t v = g.perm[j];
+      const long long pos = first + idx;
+      const long long q = pos - chunk_first_edge;  // position within the chunk
+      if (P.mode == kEmitSymForward) {
+        if (pos >= P.o.capacity) continue;
+        const long long at = r.at + e;
+        if (at >= 0 && at < 2 * P.o.capacity) {
+          P.o.csr_idx[at] = v;
+          if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
+        }
+        continue;
+      }
+      int32_t wt = 1;
+      if (uecm) {
+        const float2 lj = g.lny[j];
+        wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
+                         P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
+                         df2{r.lnyi.x, r.lnyi.y}, df2{lj.x, lj.y}, tab, fp64_only, overflow, fallbacks, boundary);
+      }
+      if (pos < P.o.capacity) {
+        if (P.o.src) {
+          P.o.src[pos] = r.u;
+          P.o.dst[pos] = v;
+          if (P.o.w) P.o.w[pos] = wt;
+        }
+        if (P.mode == kEmitSymPairs) {
+          P.c.sym.keys[0][q] = (static_cast<unsigned long long>(r.s_local) << 32) | static_cast<uint32_t>(j);
+          P.c.sym.vals[0][q] = static_cast<int32_t>(q);
+          P.c.sym.src[q] = r.u;
+          P.c.sym.w[q] = wt;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&P.c.sym.rev[static_cast<long long>(r.s_local) * n1 + j]),
+                    1ull);
+        } else if (one_row_csr) {
           const long long at = r.at + e;
-          if (at >= 0 && at < 2 * P.o.capacity) {
+          if (at < P.o.capacity) {
             P.o.csr_idx[at] = v;
-            if (P.o.csr_w) P.o.csr_w[at] = P.c.sym.w[q];
-          }
-          continue;
-        }
-        int32_t wt = 1;
-        if (uecm)
-          wt = draw_weight(static_cast<uint32_t>(e), static_cast<uint32_t>(r.k), static_cast<uint32_t>(r.i),
-                           P.c.sample0 + static_cast<uint32_t>(r.s_local), P.c.key0, P.c.key1, r.yi, &g.ys[j],
-                           df2{r.lnyi.x, r.lnyi.y}, df2{lj[u].x, lj[u].y}, tab, fp64_only, overflow, fallbacks,
-                           boundary);
-        if (pos < P.o.capacity) {
-          if (P.o.src) {
-            P.o.src[pos] = r.u;
-            P.o.dst[pos] = v;
-            if (P.o.w) P.o.w[pos] = wt;
-          }
-          if (P.mode == kEmitSymPairs) {
-            P.c.sym.keys[0][q] = (static_cast<unsigned long long>(r.s_local) << 32) | static_cast<uint32_t>(j);
-            P.c.sym.vals[0][q] = static_cast<int32_t>(q);
-            P.c.sym.src[q] = r.u;
-            P.c.sym.w[q] = wt;
-            atomicAdd(
-                reinterpret_cast<unsigned long long*>(&P.c.sym.rev[static_cast<long long>(r.s_local) * n1 + j]), 1ull);
-          } else if (one_row_csr) {
-            const long long at = r.at + e;
-            if (at < P.o.capacity) {
-              P.o.csr_idx[at] = v;
-              if (P.o.csr_w) P.o.csr_w[at] = wt;
-            }
+            if (P.o.csr_w) P.o.csr_w[at] = wt;
           }
         }
       }
     }
-    __syncthreads();
+    __syncwarp();  // the slice is rewritten by the next group
   }
   if (overflow) atomicOr(&ctrl->status, kStOverflow);
   if (bad) atomicOr(&ctrl->status, kStInternal);
@@ -309,14 +291,14 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
                                                   &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;
   const int64_t len = c.chunk_samples * (g.rows + 1);
-  const unsigned emit_blocks = grid_for(c.items_max, kEmitItems, static_cast<unsigned>(sm_count()) * 6u);
+  const unsigned emit_blocks = grid_for(c.items_max, kEmitWarps * kEmitGroup, static_cast<unsigned>(sm_count()) * 5u);
   long long* region = o.csr_off ? o.csr_off + c.chunk_first * (g.rows + 1) : nullptr;
   if (c.sym.rev && o.csr_off) {
     // symmetric layout: keys and arriving counts, the key sort, offsets from
     // both counts, then each edge into both of its rows
     MH_CUDA_RET(cudaMemsetAsync(c.sym.rev, 0, 8 * static_cast<size_t>(len), s));
     EmitParams P1{g, c, o, ctrl, kEmitSymPairs};
-    emit_kernel<<<emit_blocks, 256, 0, s>>>(P1);
+    emit_kernel<<<emit_blocks, kEmitWarps * 32, 0, s>>>(P1);
     note_launches(1);
     csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
         g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off, c.sym.rev);
@@ -337,7 +319,7 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
                          s);
     if (e != cudaSuccess) return e;
     EmitParams P2{g, c, o, ctrl, kEmitSymForward};
-    emit_kernel<<<emit_blocks, 256, 0, s>>>(P2);
+    emit_kernel<<<emit_blocks, kEmitWarps * 32, 0, s>>>(P2);
     note_launches(1);
     sym_reverse_kernel<<<grid_for(o.capacity, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
         g, sym, sym.keys[buf], sym.vals[buf], ctrl, c.chunk_first, c.chunk_samples, o, ctrl);
@@ -353,7 +335,7 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
     if (e != cudaSuccess) return e;
   }
   EmitParams P{g, c, o, ctrl, kEmitPlain};
-  emit_kernel<<<emit_blocks, 256, 0, s>>>(P);
+  emit_kernel<<<emit_blocks, kEmitWarps * 32, 0, s>>>(P);
   note_launches(1);
   return cudaGetLastError();
 }

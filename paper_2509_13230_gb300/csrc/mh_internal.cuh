@@ -62,10 +62,10 @@ constexpr int kWalkWarps = 8;                    // warps per walk block
 constexpr int kSlot = 48;                        // edges a lane buffers in shared memory
 constexpr int kSlotStride = kSlot + 1;           // padded to spread banks
 constexpr int kFlushMin = 8;                     // walk: finished runs a warp gathers before it flushes them
-constexpr int kEmitUnroll = 1;                   // emit: edges a thread handles per pass (2 and 4 measured slower)
 constexpr int kMaxWalkWarps = 8192;              // cap on resident walk warps (staging slack)
 constexpr int kStageChunk = 1024;                // staging entries a warp reserves at a time
-constexpr int kEmitItems = 128;                  // work items per emit block
+constexpr int kEmitWarps = 8;                   // emit: warps per block
+constexpr int kEmitGroup = 32;                  // emit: work items a warp takes at a time (one per lane)
 constexpr long long kItemChunk = 1ll << 22;      // work items per sample chunk
 constexpr int kDefaultSegTarget = 32;
 
