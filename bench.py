@@ -397,6 +397,9 @@ PAIR_N = 200_000
 # the y term (6 ops), two sums.  Jacobian diagonal: A, r, 1 - r, D, D^2, Q,
 # (1 - r) Q, r D, 1 - r + r D, (1 - r)^2, a division and a product, three sums.
 PAIR_OPS = {"fwd": 81, "bwd": 185, "jacobian_diag": 136}
+# the symmetric forms, per unordered pair: the shared terms once, both rows' and
+# both columns' accumulations (8 per term and 6 per 8-term renormalisation)
+PAIR_SYM_OPS = {"fwd": 99, "bwd": 231, "jacobian_diag": 205}
 FP32_LANES_PER_SM = 128
 
 
@@ -443,19 +446,23 @@ def pairwise_leg(args, dev, sm_mhz):
     import torch
 
     from paper_2509_13230_gb300 import _native as nat
-    from paper_2509_13230_gb300.sampler import expected_bwd, expected_fwd, expected_jacobian_diag
+    from paper_2509_13230_gb300.sampler import SymWorkspace, expected_bwd, expected_fwd, expected_jacobian_diag
 
     rng, x_np, y_np, x, y, gk, gs = pairwise_inputs(dev)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for kind in ("fwd", "bwd", "jacobian_diag"):
+    ws = SymWorkspace()
+    for kind in ("fwd", "bwd", "jacobian_diag", "fwd_sym", "bwd_sym", "jacobian_diag_sym"):
+        sym = ws if kind.endswith("_sym") else None
+        base = kind[:-4] if sym is not None else kind
+
         def call():
-            if kind == "fwd":
-                return expected_fwd(nat.MH_UECM, x, y)
-            if kind == "jacobian_diag":
-                return expected_jacobian_diag(nat.MH_UECM, x, y)
-            return expected_bwd(nat.MH_UECM, x, y, gk, gs)
+            if base == "fwd":
+                return expected_fwd(nat.MH_UECM, x, y, sym=sym)
+            if base == "jacobian_diag":
+                return expected_jacobian_diag(nat.MH_UECM, x, y, sym=sym)
+            return expected_bwd(nat.MH_UECM, x, y, gk, gs, sym=sym)
         for _ in range(args.warmup):
             call()
         torch.cuda.synchronize()
@@ -468,8 +475,15 @@ def pairwise_leg(args, dev, sm_mhz):
             ev1.synchronize()
         ms = ev0.elapsed_time(ev1) / reps
         pairs = PAIR_N * (PAIR_N - 1)
-        out[kind] = {"ms": ms, "pairs_per_s": pairs / (ms / 1e3), "fp32_ops_per_pair": PAIR_OPS[kind],
-                     "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9, "clocks": clk.summary()}
+        if sym is None:
+            out[kind] = {"ms": ms, "pairs_per_s": pairs / (ms / 1e3), "fp32_ops_per_pair": PAIR_OPS[kind],
+                         "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9, "clocks": clk.summary()}
+        else:
+            # one evaluation per unordered pair serves both rows
+            out[kind] = {"ms": ms, "unordered_pairs_per_s": pairs / 2 / (ms / 1e3),
+                         "fp32_ops_per_unordered_pair": PAIR_SYM_OPS[base],
+                         "achieved_gops": PAIR_SYM_OPS[base] * pairs / 2 / (ms / 1e3) / 1e9,
+                         "speedup_over_row_form": out[base]["ms"] / ms, "clocks": clk.summary()}
     import torch.cuda as tc
     sms = tc.get_device_properties(dev).multi_processor_count
     mhz = sm_mhz or 2070.0

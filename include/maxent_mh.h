@@ -491,6 +491,41 @@ int maxent_expected_bwd_rows(int model, const double* x, const double* y, int64_
                              int64_t row_count, const double* g_k, const double* g_s, double* g_x, double* g_y,
                              mh_stream_t stream);
 
+/*
+ * maxent_expected_fwd_sym / maxent_expected_jacobian_diag_sym /
+ * maxent_expected_bwd_sym — the whole-range sums of maxent_expected_fwd,
+ * maxent_expected_jacobian_diag and maxent_expected_bwd (same arguments,
+ * same outputs, Sec. 2.2, Sec. 2.5, Sec. 4), with every unordered pair
+ * {i, j} evaluated once for both of its rows: p_ij = p_ji, and each
+ * derivative term is a factor symmetric in i and j times a_j (row i) or a_i
+ * (row j), a = x (UBCM) or x y (UECM).  Half the pair terms of the row forms.
+ *
+ * Results are deterministic (fixed order of additions, independent of the
+ * grid and timing) and within the error bound of the row forms (about 1e-11
+ * of the sum of the terms' magnitudes), but not bit for bit equal to them:
+ * the additions run in another order.  The _rows forms above stay the ones
+ * whose rows equal the whole call bit for bit.
+ *
+ * workspace: device memory of at least maxent_expected_sym_workspace_size()
+ * bytes, 256-byte aligned, owned by the caller, not kept after the call's
+ * work; it holds the double-float copies of the operands and one partial
+ * sum per (quantity, band of columns, node): 8 q ceil(n / L) n bytes with
+ * L = max(2048, n / 128 rounded up to a multiple of 512) and q = 1 (UBCM),
+ * 3 (UECM).  Calls on one stream may share it; concurrent calls may not.
+ * Errors: MH_ERR_ARG (model, n < 1 or n > 2^31, a NULL required pointer,
+ * misaligned workspace), MH_ERR_WORKSPACE (NULL or too small), MH_ERR_CUDA.
+ * The calls return without synchronising.
+ */
+int maxent_expected_sym_workspace_size(int model, int64_t n, size_t* h_bytes);
+int maxent_expected_fwd_sym(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
+                            void* workspace, size_t workspace_bytes, mh_stream_t stream);
+int maxent_expected_jacobian_diag_sym(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                      double* dk_dy, double* ds_dx, double* ds_dy, void* workspace,
+                                      size_t workspace_bytes, mh_stream_t stream);
+int maxent_expected_bwd_sym(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                            const double* g_s, double* g_x, double* g_y, void* workspace, size_t workspace_bytes,
+                            mh_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

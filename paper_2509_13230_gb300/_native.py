@@ -60,6 +60,10 @@ EXPORTED = (
     "maxent_expected_bwd_rows",
     "maxent_expected_jacobian_diag",
     "maxent_expected_jacobian_diag_rows",
+    "maxent_expected_sym_workspace_size",
+    "maxent_expected_fwd_sym",
+    "maxent_expected_jacobian_diag_sym",
+    "maxent_expected_bwd_sym",
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
@@ -174,6 +178,14 @@ def load(path: str | None = None):
         lib.maxent_expected_jacobian_diag.restype = i32
         lib.maxent_expected_jacobian_diag_rows.argtypes = [i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
         lib.maxent_expected_jacobian_diag_rows.restype = i32
+        lib.maxent_expected_sym_workspace_size.argtypes = [i32, i64, ctypes.POINTER(sz)]
+        lib.maxent_expected_sym_workspace_size.restype = i32
+        lib.maxent_expected_fwd_sym.argtypes = [i32, vp, vp, i64, vp, vp, vp, sz, vp]
+        lib.maxent_expected_fwd_sym.restype = i32
+        lib.maxent_expected_jacobian_diag_sym.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
+        lib.maxent_expected_jacobian_diag_sym.restype = i32
+        lib.maxent_expected_bwd_sym.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
+        lib.maxent_expected_bwd_sym.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
         lib.mh_bipartite_workspace_size.restype = i32
         lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
@@ -327,3 +339,21 @@ def maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_
                                        stream) -> int:
     return load().maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_dx, dk_dy, ds_dx,
                                                      ds_dy, stream)
+
+
+def maxent_expected_sym_workspace_size(model, n) -> tuple[int, int]:
+    out = ctypes.c_size_t(0)
+    rc = load().maxent_expected_sym_workspace_size(model, n, ctypes.byref(out))
+    return rc, int(out.value)
+
+
+def maxent_expected_fwd_sym(model, x, y, n, k_out, s_out, ws, ws_bytes, stream) -> int:
+    return load().maxent_expected_fwd_sym(model, x, y, n, k_out, s_out, ws, ws_bytes, stream)
+
+
+def maxent_expected_jacobian_diag_sym(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, ws, ws_bytes, stream) -> int:
+    return load().maxent_expected_jacobian_diag_sym(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, ws, ws_bytes, stream)
+
+
+def maxent_expected_bwd_sym(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream) -> int:
+    return load().maxent_expected_bwd_sym(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream)

@@ -20,9 +20,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmaxent_mh.so")
 ROOT = os.path.dirname(PKG)
 
-SOURCES = ["api.cu", "sort.cu", "partition.cu", "walk.cu", "emit.cu", "pairwise.cu", "noalloc.cu", "batch.cu",
-           "bf.cu"]
-HEADERS = ["mh_internal.cuh", "scan.cuh", "walk_math.cuh"]
+SOURCES = ["api.cu", "sort.cu", "partition.cu", "walk.cu", "emit.cu", "pairwise.cu", "pairsym.cu", "noalloc.cu",
+           "batch.cu", "bf.cu"]
+HEADERS = ["mh_internal.cuh", "scan.cuh", "walk_math.cuh", "pair_math.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", os.path.join(ROOT, "include")]

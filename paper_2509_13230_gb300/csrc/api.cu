@@ -989,6 +989,70 @@ int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, 
   return maxent_expected_bwd_rows(model, x, y, n, 0, n, g_k, g_s, g_x, g_y, stream);
 }
 
+int maxent_expected_sym_workspace_size(int model, int64_t n, size_t* h_bytes) {
+  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || n > (1ll << 31) || !h_bytes) {
+    set_error("maxent_expected_sym_workspace_size: bad model, n or NULL h_bytes");
+    return MH_ERR_ARG;
+  }
+  *h_bytes = mh::expected_sym_workspace_bytes(model, n);
+  return MH_OK;
+}
+
+// Shared checks of the symmetric forms: model, n, workspace, then pointers.
+static int check_sym(const char* fn, int model, int64_t n, const void* workspace, size_t workspace_bytes,
+                     bool ptrs_ok) {
+  if ((model != MH_UBCM && model != MH_UECM) || n < 1 || n > (1ll << 31)) {
+    set_error("%s: bad model or n", fn);
+    return MH_ERR_ARG;
+  }
+  const size_t need = mh::expected_sym_workspace_bytes(model, n);
+  if (!workspace || workspace_bytes < need) {
+    set_error("%s: the workspace needs %zu bytes, got %zu", fn, need, workspace ? workspace_bytes : 0);
+    return MH_ERR_WORKSPACE;
+  }
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) {
+    set_error("%s: the workspace must be 256-byte aligned", fn);
+    return MH_ERR_ARG;
+  }
+  if (!ptrs_ok) {
+    set_error("%s: a required pointer is NULL", fn);
+    return MH_ERR_ARG;
+  }
+  return MH_OK;
+}
+
+int maxent_expected_fwd_sym(int model, const double* x, const double* y, int64_t n, double* k_out, double* s_out,
+                            void* workspace, size_t workspace_bytes, mh_stream_t stream) {
+  const int rc = check_sym("maxent_expected_fwd_sym", model, n, workspace, workspace_bytes,
+                           x && k_out && (model == MH_UBCM || (y && s_out)));
+  if (rc != MH_OK) return rc;
+  MH_CUDA(mh::launch_expected_sym(0, model, x, y, nullptr, nullptr, n, workspace, k_out, s_out, nullptr, nullptr,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
+int maxent_expected_jacobian_diag_sym(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                      double* dk_dy, double* ds_dx, double* ds_dy, void* workspace,
+                                      size_t workspace_bytes, mh_stream_t stream) {
+  const int rc = check_sym("maxent_expected_jacobian_diag_sym", model, n, workspace, workspace_bytes,
+                           x && dk_dx && (model == MH_UBCM || (y && dk_dy && ds_dx && ds_dy)));
+  if (rc != MH_OK) return rc;
+  MH_CUDA(mh::launch_expected_sym(1, model, x, y, nullptr, nullptr, n, workspace, dk_dx, dk_dy, ds_dx, ds_dy,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
+int maxent_expected_bwd_sym(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                            const double* g_s, double* g_x, double* g_y, void* workspace, size_t workspace_bytes,
+                            mh_stream_t stream) {
+  const int rc = check_sym("maxent_expected_bwd_sym", model, n, workspace, workspace_bytes,
+                           x && g_k && g_x && (model == MH_UBCM || (y && g_s && g_y)));
+  if (rc != MH_OK) return rc;
+  MH_CUDA(mh::launch_expected_sym(2, model, x, y, g_k, g_s, n, workspace, g_x, g_y, nullptr, nullptr,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
 }  // extern "C"
 
 // ---- forwarders for the fixed-scratch entry point (noalloc.cu) -------------------

@@ -348,5 +348,11 @@ cudaError_t launch_expected_fwd(int model, const double* x, const double* y, int
 cudaError_t launch_expected_bwd(int model, const double* x, const double* y, int64_t n, int64_t row_begin,
                                 int64_t rows, const double* gk, const double* gs, double* gx, double* gy,
                                 cudaStream_t st);
+// Symmetric pair sums (pairsym.cu): kind 0 the expected sums, 1 the Jacobian
+// diagonal, 2 the gradient; outputs as the row kernels' whole-range calls.
+size_t expected_sym_workspace_bytes(int model, int64_t n);
+cudaError_t launch_expected_sym(int kind, int model, const double* x, const double* y, const double* gk,
+                                const double* gs, int64_t n, void* workspace, double* o0, double* o1, double* o2,
+                                double* o3, cudaStream_t st);
 
 }  // namespace mh

@@ -26,7 +26,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _native as nat
-from .sampler import expected_bwd, expected_fwd, expected_jacobian_diag
+from .sampler import SymWorkspace, expected_bwd, expected_fwd, expected_jacobian_diag
 
 
 class ExpectedDegrees(torch.autograd.Function):
@@ -71,16 +71,20 @@ class FitResult:
 
 class _LocalSums:
     """The sums of a fit on this process's GPU (the module's functions, looked
-    up at call time)."""
+    up at call time): each unordered pair evaluated once for both of its rows
+    (the symmetric forms), with one scratch buffer for the fit."""
+
+    def __init__(self):
+        self.ws = SymWorkspace()
 
     def fwd(self, model, x, y=None):
-        return expected_fwd(model, x, y)
+        return expected_fwd(model, x, y, sym=self.ws)
 
     def bwd(self, model, x, y, g_k, g_s=None):
-        return expected_bwd(model, x, y, g_k, g_s)
+        return expected_bwd(model, x, y, g_k, g_s, sym=self.ws)
 
     def diag(self, model, x, y=None):
-        return expected_jacobian_diag(model, x, y)
+        return expected_jacobian_diag(model, x, y, sym=self.ws)
 
 
 def _residual(model, x, y, k_t, s_t, ops):

@@ -327,17 +327,47 @@ def _row_range(rows, n: int) -> tuple[int, int]:
     return begin, count
 
 
-def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None):
+class SymWorkspace:
+    """Device scratch of the symmetric pair sums (maxent_expected_*_sym):
+    one buffer, grown to the largest (model, n) asked for on its device."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, model: int, n: int, device) -> tuple[torch.Tensor, int]:
+        rc, need = nat.maxent_expected_sym_workspace_size(model, n)
+        nat.check(rc, "maxent_expected_sym_workspace_size")
+        if self.buf is None or self.buf.numel() < need or self.buf.device != torch.device(device):
+            self.buf = None
+            self.buf = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+        return self.buf, need
+
+
+def _sym_args(sym, model, n, device, rows):
+    if rows is not None:
+        raise ValueError("the symmetric pair sums cover all rows; rows needs the row form")
+    ws, need = sym.get(model, n, device)
+    return _ptr(ws), need
+
+
+def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None,
+                 sym: SymWorkspace | None = None):
     """(<k>, <s>) as FP64 CUDA tensors (<s> is None for UBCM).  rows =
     (row_begin, row_count) computes only those rows (outputs of row_count
-    entries), bit for bit the values of the whole call."""
+    entries), bit for bit the values of the whole call.  sym = a
+    SymWorkspace evaluates each unordered pair once for both rows (all rows;
+    within rounding of the row form, not bit for bit)."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
     begin, count = _row_range(rows, n)
     k = torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
     s = torch.empty_like(k) if model == nat.MH_UECM else None
-    if rows is None:
+    if sym is not None:
+        ws, need = _sym_args(sym, model, n, x.device, rows)
+        rc = nat.maxent_expected_fwd_sym(model, _ptr(x), _ptr(y), n, _ptr(k), _ptr(s), ws, need,
+                                         _stream_handle(stream))
+    elif rows is None:
         rc = nat.maxent_expected_fwd(model, _ptr(x), _ptr(y), n, _ptr(k), _ptr(s), _stream_handle(stream))
     else:
         rc = nat.maxent_expected_fwd_rows(model, _ptr(x), _ptr(y), n, begin, count, _ptr(k), _ptr(s),
@@ -347,9 +377,9 @@ def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, str
 
 
 def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch.Tensor,
-                 g_s: torch.Tensor | None = None, stream=None, rows=None):
-    """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors); rows as in
-    expected_fwd."""
+                 g_s: torch.Tensor | None = None, stream=None, rows=None, sym: SymWorkspace | None = None):
+    """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors); rows and
+    sym as in expected_fwd."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
@@ -358,7 +388,11 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
     begin, count = _row_range(rows, n)
     gx = torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
     gy = torch.empty_like(gx) if model == nat.MH_UECM else None
-    if rows is None:
+    if sym is not None:
+        ws, need = _sym_args(sym, model, n, x.device, rows)
+        rc = nat.maxent_expected_bwd_sym(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy), ws,
+                                         need, _stream_handle(stream))
+    elif rows is None:
         rc = nat.maxent_expected_bwd(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy),
                                      _stream_handle(stream))
     else:
@@ -368,10 +402,11 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
     return gx, gy
 
 
-def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None):
+def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None,
+                           sym: SymWorkspace | None = None):
     """(d<k>/dx,) for the UBCM or (d<k>/dx, d<k>/dy, d<s>/dx, d<s>/dy) for the
     UECM: each node's derivatives of its own expected degree (and strength)
-    with respect to its own parameters, FP64 CUDA tensors; rows as in
+    with respect to its own parameters, FP64 CUDA tensors; rows and sym as in
     expected_fwd."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
@@ -380,7 +415,11 @@ def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None =
     outs = [torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
             for _ in range(1 if model == nat.MH_UBCM else 4)]
     ptrs = [_ptr(t) for t in outs] + [None] * (4 - len(outs))
-    if rows is None:
+    if sym is not None:
+        ws, need = _sym_args(sym, model, n, x.device, rows)
+        rc = nat.maxent_expected_jacobian_diag_sym(model, _ptr(x), _ptr(y), n, *ptrs, ws, need,
+                                                   _stream_handle(stream))
+    elif rows is None:
         rc = nat.maxent_expected_jacobian_diag(model, _ptr(x), _ptr(y), n, *ptrs, _stream_handle(stream))
     else:
         rc = nat.maxent_expected_jacobian_diag_rows(model, _ptr(x), _ptr(y), n, begin, count, *ptrs,

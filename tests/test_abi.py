@@ -136,3 +136,24 @@ def test_jacobian_diagonal_argument_checks_without_a_gpu(lib):
     assert nat.maxent_expected_jacobian_diag(0, None, None, 5, fake, None, None, None, None) == nat.MH_ERR_ARG
     assert nat.maxent_expected_jacobian_diag(0, fake, None, 0, fake, None, None, None, None) == nat.MH_ERR_ARG
     assert nat.maxent_expected_jacobian_diag(2, fake, fake, 5, fake, fake, fake, fake, None) == nat.MH_ERR_ARG
+
+
+def test_sym_workspace_size(lib):
+    """The symmetric pair sums' scratch: double-float copies of the operands
+    (16 B per node, twice for the UECM), a bit per node, and one FP64 partial
+    per (quantity, band of L columns, node), L = max(2048, n / 128 rounded
+    up to a multiple of 512), 1 quantity for the UBCM and 3 for the UECM."""
+    def align(v):
+        return (v + 255) // 256 * 256
+
+    for model, q in ((nat.MH_UBCM, 1), (nat.MH_UECM, 3)):
+        for n in (1, 31, 2048, 2049, 200_000, 1_000_000):
+            L = max(2048, -(-(-(-n // 128)) // 512) * 512)
+            nb = -(-n // L)
+            assert nb <= 128
+            want = align(16 * n) + (align(16 * n) if model == nat.MH_UECM else 0) + align(4 * (-(-n // 32)))
+            want += align(8 * q * nb * n)
+            rc, got = nat.maxent_expected_sym_workspace_size(model, n)
+            assert rc == nat.MH_OK and got == want, (model, n, got, want)
+    assert nat.maxent_expected_sym_workspace_size(nat.MH_UBCM, 0)[0] == nat.MH_ERR_ARG
+    assert nat.maxent_expected_sym_workspace_size(5, 10)[0] == nat.MH_ERR_ARG

@@ -20,17 +20,17 @@ def _np(t):
 def oracle_kernels(monkeypatch):
     calls = {"fwd": 0, "bwd": 0, "diag": 0}
 
-    def fwd(model, x, y=None, stream=None, rows=None):
+    def fwd(model, x, y=None, stream=None, rows=None, sym=None):
         calls["fwd"] += 1
         k, s = oracle.expected_fwd(model, _np(x), _np(y))
         return torch.from_numpy(k), None if s is None else torch.from_numpy(s)
 
-    def bwd(model, x, y, g_k, g_s=None, stream=None, rows=None):
+    def bwd(model, x, y, g_k, g_s=None, stream=None, rows=None, sym=None):
         calls["bwd"] += 1
         gx, gy = oracle.expected_bwd(model, _np(x), _np(y), _np(g_k), _np(g_s))
         return torch.from_numpy(gx), None if gy is None else torch.from_numpy(gy)
 
-    def diag(model, x, y=None, stream=None):
+    def diag(model, x, y=None, stream=None, rows=None, sym=None):
         calls["diag"] += 1
         return tuple(torch.from_numpy(a) for a in oracle.expected_jacobian_diag(model, _np(x), _np(y)))
 
