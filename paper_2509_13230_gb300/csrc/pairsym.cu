@@ -17,17 +17,19 @@
 // Work decomposition.  The nodes are cut into bands of L (a multiple of 512);
 // a unit is a pair of bands I <= J (a persistent grid takes units in turn).
 // A block of 16 warps sweeps the unit's columns in sub-bands of 512, warp w
-// owning 32 of them; for each tile of 32 rows, lane l of warp w holds row
-// r0 + l and column c0 + l, and in step t pairs its row with column
-// (l + t) mod 32 of its warp's columns: the row term goes to the lane's own
-// row sum, the column term to the column's owner, lane (l + t) mod 32, by
-// one shuffle.  A tile on the diagonal of a diagonal unit takes steps 1..16
-// (step 16 on lanes 0..15 only), so each unordered pair comes once.
+// owning 32 of them; for each tile of 64 rows, lane l of warp w holds rows
+// r0 + l and r0 + 32 + l and column c0 + l, and in step t pairs both rows
+// with column (l + t) mod 32 of its warp's columns: the row terms go to the
+// lane's own row sums, the column terms to the column's owner, lane
+// (l + t) mod 32, by shuffles.  A 32-row half on the diagonal of a diagonal
+// unit takes steps 1..16 (step 16 on lanes 0..15 only), so each unordered
+// pair comes once.
 //
 // Determinism.  Sums go to a partial array P[q][B][i] = sum over the j of
-// band B of row i's terms (kQ quantities, nb bands): a warp's 32 terms of a
-// row or a column in double-float (DfAcc), the 16 warps' row partials added
-// in warp order, tiles and sub-bands in loop order; a row's entry for its own
+// band B of row i's terms (kQ quantities, nb bands): a row's 32 terms of a
+// tile and a column's terms of a whole sub-band in double-float (DfAcc,
+// folded every 8 terms), the 16 warps' row partials added in warp order,
+// tiles and sub-bands in loop order; a row's entry for its own
 // band (diagonal unit) gets the row and column parts in that fixed order.
 // A second kernel adds P over B in order.  The result therefore depends on
 // neither the grid nor the timing, but the order of additions differs from
@@ -47,6 +49,7 @@ namespace {
 constexpr int kSymWarps = 16;
 constexpr int kSymThreads = 32 * kSymWarps;
 constexpr int kSubBand = 32 * kSymWarps;  // columns of one sweep
+constexpr int kSymRows = 64;              // rows of a tile: two per lane
 constexpr unsigned kAll = 0xffffffffu;
 
 enum SymKind { kSymFwd = 0, kSymDiag = 1, kSymBwd = 2 };
@@ -226,6 +229,8 @@ __device__ __forceinline__ bool node_unsafe(const unsigned* unsafe, int64_t i, i
 }
 
 // P[(q nb + B) n + i]: row i's sum of quantity q over the columns of band B.
+// Row tiles are 64 rows: lane l holds rows r0 + l and r0 + 32 + l (two
+// independent pair terms per step), each against the same column.
 template <int kModel, int kKind>
 __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, const double* __restrict__ x,
                                                                    const double* __restrict__ y,
@@ -236,11 +241,13 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
   constexpr bool kTwo = SymCount<kModel, kKind>::kTwo;
   __shared__ float4 cst0[kSymWarps][32];
   __shared__ float4 cst1[kTwo ? kSymWarps : 1][32];
-  __shared__ double rpart[2][kQ][kSymWarps][32];
+  // a tile's row partials: double-float (hi, lo) bits, or FP64 bits where the
+  // warp's tile took the FP64 terms (rslow), whose sums may lie below FP32's range
+  __shared__ unsigned long long rpart[kQ][kSymWarps][kSymRows];
+  __shared__ int rslow[kSymWarps];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t units = nb * (nb + 1) / 2;
-  int buf = 0;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     int64_t I, J;
     unit_bands(u, nb, I, J);
@@ -258,71 +265,143 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
       if constexpr (kTwo) cst1[warp][lane] = node_or_zero(N.d1, j, n);
       const unsigned cbad = __ballot_sync(kAll, node_unsafe(N.unsafe, j, n));
       __syncwarp();
+      // column sums: double-float over the whole sub-band (FP64 tiles add to ctot)
+      DfAcc cacc[kQ];
       double ctot[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) ctot[q] = 0.0;
-      const int64_t ct = (s >> 5) + warp;  // the warp's column tile within the band
-      const int64_t tiles = dg ? (s + kSubBand) >> 5 : L >> 5;
-      for (int64_t rt = 0; rt < tiles && rb + 32 * rt < n; ++rt) {
-        const int64_t i = rb + 32 * rt + lane;
-        const float4 rd0 = node_or_zero(N.d0, i, n);
-        const float4 rd1 = kTwo ? node_or_zero(N.d1, i, n) : rd0;
-        const unsigned rbad = __ballot_sync(kAll, node_unsafe(N.unsafe, i, n));
-        const bool skip = dg && rt > ct;   // the transposed tile holds these pairs
-        const bool dtile = dg && rt == ct;  // rows and columns are the same 32 nodes
-        double rsum[kQ];
+      const int64_t ct = (s >> 5) + warp;  // the warp's column tile (of 32) within the band
+      const int64_t tiles = dg ? (s + kSubBand + kSymRows - 1) / kSymRows : L / kSymRows;
+      for (int64_t rt = 0; rt < tiles && rb + kSymRows * rt < n; ++rt) {
+        const int64_t r0 = rb + kSymRows * rt;
+        float4 rd0[2], rd1[2];
+        unsigned rbad = 0u;
+        int mode[2];  // 0 skip (the transposed tile holds these pairs), 1 same 32 nodes, 2 all pairs
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) rsum[q] = 0.0;
-        if (!skip) {
-          const int t0 = dtile ? 1 : 0, t1 = dtile ? 17 : 32;
-          if ((rbad | cbad) == 0u) {
-            DfAcc ra[kQ], ca[kQ];
-#pragma unroll 2
-            for (int t = t0; t < t1; ++t) {
+        for (int h = 0; h < 2; ++h) {
+          const int64_t i = r0 + 32 * h + lane;
+          rd0[h] = node_or_zero(N.d0, i, n);
+          rd1[h] = kTwo ? node_or_zero(N.d1, i, n) : rd0[h];
+          rbad |= __ballot_sync(kAll, node_unsafe(N.unsafe, i, n));
+          const int64_t rh = 2 * rt + h;  // row sub-tile (of 32) within the band
+          mode[h] = !dg || rh < ct ? 2 : (rh == ct ? 1 : 0);
+        }
+        df2 rsum[2][kQ];  // the tile's row sums, double-float
+        double rs[2][kQ];  // or FP64 (slow)
+        bool slow = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            rsum[h][q] = df2{0.0f, 0.0f};
+            rs[h][q] = 0.0;
+          }
+        const bool any_full = mode[0] == 2 || mode[1] == 2;
+        if (mode[0] | mode[1]) {
+          const int t0 = any_full ? 0 : 1, t1 = any_full ? 32 : 17;
+          if ((rbad | cbad) == 0u && mode[0] == 2 && mode[1] == 2) {
+            // every pair of the tile, no per-step checks (all tiles of off-diagonal units)
+            DfAcc ra[2][kQ];
+#pragma unroll 4
+            for (int t = 0; t < 32; ++t) {
               const int c = (lane + t) & 31;
               const float4 c0 = cst0[warp][c];
               const float4 c1 = kTwo ? cst1[warp][c] : c0;
-              df2 tr[kQ], tc[kQ];
-              sym_terms<kModel, kKind>(rd0, rd1, c0, c1, tr, tc);
-              const bool dup = dtile && t == 16 && lane >= 16;  // lane - 16 has this pair
-              const int from = (lane - t) & 31;                  // the row paired with my column
+              const int from = (lane - t) & 31;
 #pragma unroll
-              for (int q = 0; q < kQ; ++q) {
-                if (!dup) ra[q].add(tr[q]);
-                const float hi = __shfl_sync(kAll, dup ? 0.0f : tc[q].hi, from);
-                const float lo = __shfl_sync(kAll, dup ? 0.0f : tc[q].lo, from);
-                ca[q].add(df2{hi, lo});
-              }
-              if ((t & 7) == 7) {
+              for (int h = 0; h < 2; ++h) {
+                df2 tr[kQ], tc[kQ];
+                sym_terms<kModel, kKind>(rd0[h], rd1[h], c0, c1, tr, tc);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                  ra[q].norm();
-                  ca[q].norm();
+                  ra[h][q].add(tr[q]);
+                  cacc[q].add(df2{__shfl_sync(kAll, tc[q].hi, from), __shfl_sync(kAll, tc[q].lo, from)});
+                }
+              }
+              if ((t & 3) == 3) {  // ca takes two terms a step, ra[h] one: at most 8 terms between folds
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                  cacc[q].norm();
+                  if ((t & 7) == 7) {
+                    ra[0][q].norm();
+                    ra[1][q].norm();
+                  }
                 }
               }
             }
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-              rsum[q] = ra[q].value();
-              ctot[q] += ca[q].value();
+              cacc[q].norm();
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                ra[h][q].norm();
+                rsum[h][q] = df2{ra[h][q].hi, ra[h][q].lo};
+              }
+            }
+          } else if ((rbad | cbad) == 0u) {
+            DfAcc ra[2][kQ];
+#pragma unroll 2
+            for (int t = t0; t < t1; ++t) {
+              const int c = (lane + t) & 31;
+              const float4 c0 = cst0[warp][c];
+              const float4 c1 = kTwo ? cst1[warp][c] : c0;
+              const int from = (lane - t) & 31;  // the lane whose rows meet my column in this step
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                df2 tr[kQ], tc[kQ];
+                sym_terms<kModel, kKind>(rd0[h], rd1[h], c0, c1, tr, tc);
+                // a diagonal sub-tile takes steps 1..16, step 16 on lanes 0..15 only
+                const bool use = mode[h] == 2 || (mode[h] == 1 && t >= 1 && (t < 16 || (t == 16 && lane < 16)));
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                  if (use) ra[h][q].add(tr[q]);
+                  const float hi = __shfl_sync(kAll, use ? tc[q].hi : 0.0f, from);
+                  const float lo = __shfl_sync(kAll, use ? tc[q].lo : 0.0f, from);
+                  cacc[q].add(df2{hi, lo});
+                }
+              }
+              if ((t & 3) == 3) {  // ca takes two terms a step, ra[h] one: at most 8 terms between folds
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                  cacc[q].norm();
+                  if ((t & 7) == 7) {
+                    ra[0][q].norm();
+                    ra[1][q].norm();
+                  }
+                }
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+              cacc[q].norm();
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                ra[h][q].norm();
+                rsum[h][q] = df2{ra[h][q].hi, ra[h][q].lo};
+              }
             }
           } else {
+            slow = true;
             double cs[kQ];
 #pragma unroll
             for (int q = 0; q < kQ; ++q) cs[q] = 0.0;
             for (int t = t0; t < t1; ++t) {
               const int c = (lane + t) & 31;
               const int64_t jj = cw + c;
-              double tr[kQ], tc[kQ];
-#pragma unroll
-              for (int q = 0; q < kQ; ++q) tr[q] = tc[q] = 0.0;
-              const bool dup = dtile && t == 16 && lane >= 16;
-              if (!dup && i < n && jj < n) sym_terms_fp64<kModel, kKind>(x, y, gk, gs, i, jj, tr, tc);
               const int from = (lane - t) & 31;
 #pragma unroll
-              for (int q = 0; q < kQ; ++q) {
-                rsum[q] += tr[q];
-                cs[q] += __shfl_sync(kAll, tc[q], from);
+              for (int h = 0; h < 2; ++h) {
+                const int64_t i = r0 + 32 * h + lane;
+                double tr[kQ], tc[kQ];
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) tr[q] = tc[q] = 0.0;
+                const bool use = mode[h] == 2 || (mode[h] == 1 && t >= 1 && (t < 16 || (t == 16 && lane < 16)));
+                if (use && i < n && jj < n) sym_terms_fp64<kModel, kKind>(x, y, gk, gs, i, jj, tr, tc);
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                  rs[h][q] += tr[q];
+                  cs[q] += __shfl_sync(kAll, tc[q], from);
+                }
               }
             }
 #pragma unroll
@@ -330,24 +409,44 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
           }
         }
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) rpart[buf][q][warp][lane] = rsum[q];
+        for (int q = 0; q < kQ; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            rpart[q][warp][32 * h + lane] =
+                slow ? static_cast<unsigned long long>(__double_as_longlong(rs[h][q]))
+                     : (static_cast<unsigned long long>(__float_as_uint(rsum[h][q].lo)) << 32) |
+                           __float_as_uint(rsum[h][q].hi);
+        if (lane == 0) rslow[warp] = slow;
         __syncthreads();
         if (warp < kQ) {  // warp q adds quantity q of the 16 warps, in warp order
-          double v = 0.0;
-          for (int w = 0; w < kSymWarps; ++w) v += rpart[buf][warp][w][lane];
-          if (i < n) P[(warp * nb + J) * n + i] += v;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            DfAcc v;
+            double sv = 0.0;
+#pragma unroll
+            for (int w = 0; w < kSymWarps; ++w) {
+              const unsigned long long e = rpart[warp][w][32 * h + lane];
+              if (rslow[w])
+                sv += __longlong_as_double(static_cast<long long>(e));
+              else
+                v.add(df2{__uint_as_float(static_cast<unsigned>(e)), __uint_as_float(static_cast<unsigned>(e >> 32))});
+              if ((w & 7) == 7) v.norm();
+            }
+            const int64_t i = r0 + 32 * h + lane;
+            if (i < n) P[(warp * nb + J) * n + i] += v.value() + sv;
+          }
         }
-        buf ^= 1;
+        __syncthreads();  // rpart is rewritten by the next tile
       }
-      __syncthreads();  // the row entries of the last tile may be these columns (diagonal unit)
-      if (j < n) {
+      if (j < n) {  // after the last tile's row entries (the barrier above), which may be these columns
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           double* e = &P[(q * nb + I) * n + j];
+          const double v = ctot[q] + cacc[q].value();
           if (dg)
-            *e += ctot[q];  // after the row part of its own tile, before later sub-bands
+            *e += v;  // after the row part of its own tile, before later sub-bands
           else
-            *e = ctot[q];
+            *e = v;
         }
       }
     }
