@@ -67,7 +67,8 @@ struct BatchLayout {
   // persistent part (the first `image` bytes are copied from the host)
   size_t header = 0, nets = 0, order = 0, image = 0, net_ctrl = 0, wave = 0, mb = 0, wave_ctrl = 0;
   size_t perm = 0, rank = 0, xs = 0, ys = 0, as = 0, xdf = 0, adf = 0, ydf = 0, lny = 0, top = 0, Q = 0,
-         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, persistent_end = 0;
+         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, rowoff_node = 0, seg_slot = 0, slot_seg = 0,
+         persistent_end = 0;
   // preparation scratch of one lane, relative to the lane's start
   Layout lane;
   size_t lane_bytes = 0, prep_end = 0;
@@ -127,6 +128,9 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
   B.seg = take(sizeof(int4) * SG);
   B.seg_c = take(8 * SG);
   B.seg_cf = take(16 * SG);
+  B.rowoff_node = take(8 * N1);
+  B.seg_slot = take(4 * SG);
+  B.slot_seg = take(4 * SG);
   B.persistent_end = off;
 
   // one lane's sort and scan scratch, sized for the largest network
@@ -496,6 +500,65 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
   }
 }
 
+// Node-id order of a network's work items, for CSR waves: rowoff_node[u] =
+// the first slot of node u's row (an exclusive scan over node ids of each
+// row's segment count; rowoff_node[n] = S), seg_slot[sg] = the slot of
+// segment-table row sg, slot_seg its inverse.  A CSR wave numbers its items
+// (sample, node id, segment), so the item scan gives every edge's CSR
+// position at once: the index array lists rows by node id.
+__global__ void node_seg_count_kernel(Net g, const Ctrl* ctrl, long long* __restrict__ rowoff_node) {
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;  // a truncated table fails the batch; stay in bounds
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u <= g.n;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    long long c = 0;
+    if (u < g.n) {
+      const int64_t r = g.rank[u];
+      long long lo = g.rowoff[r], hi = g.rowoff[r + 1];
+      lo = lo < S ? lo : S;
+      hi = hi < S ? hi : S;
+      c = hi - lo;
+    }
+    rowoff_node[u] = c;
+  }
+}
+
+__global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__ rowoff_node,
+                                int32_t* __restrict__ seg_slot, int32_t* __restrict__ slot_seg) {
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;
+  for (int64_t sg = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; sg < S;
+       sg += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int4 e = g.seg[sg];
+    const long long slot = rowoff_node[g.perm[e.x]] + e.y;
+    if (slot < 0 || slot >= S) {  // cannot happen for a consistent table; never index with it
+      atomicOr(&ctrl->status, kStInternal);
+      continue;
+    }
+    seg_slot[sg] = static_cast<int32_t>(slot);
+    slot_seg[slot] = static_cast<int32_t>(sg);
+  }
+}
+
+// CSR offsets of a node-order wave: entry (pair, u) is the item offset of
+// node u's first slot (u = n: the pair's end).
+__global__ void batch_csr_off_kernel(BatchView V, const long long* __restrict__ rowoff_node,
+                                     const long long* __restrict__ item_off, long long* __restrict__ csr_off) {
+  const long long total = V.wc->num_segments;
+  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < total;
+       o += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int t = last_at_or_below(V.n_nets, o, [&](int k) { return V.wave[k].csr_base; });
+    const WaveNet& w = V.wave[t];
+    const BatchNet& bn = V.nets[t];
+    // a wave holds fewer than 2^31 CSR offsets
+    const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
+    const unsigned rel = static_cast<unsigned>(o - w.csr_base);
+    const long long s = rel / n1;
+    const long long u = rel - static_cast<unsigned>(s) * n1;
+    csr_off[o] = item_off[w.item_begin + s * w.S + rowoff_node[bn.node1_base + u]];
+  }
+}
+
 struct BatchEmitParams {
   BatchView V;
   Net g;  // concatenated arrays
@@ -507,6 +570,7 @@ struct BatchEmitParams {
   Outputs o;
   uint32_t key0;
   bool any_uecm;
+  const int32_t* slot_seg;  // node-order CSR wave: the segment of each slot (NULL: rank order)
 };
 
 // What every edge of a work item shares, set up once per item.
@@ -575,7 +639,8 @@ __global__ void __launch_bounds__(kBatchEmitWarps * 32) batch_emit_kernel(BatchE
       const unsigned local = static_cast<unsigned>(item - w.item_begin);
       const unsigned S = static_cast<unsigned>(w.S);
       const unsigned s_local = local / S;
-      const unsigned seg_local = local - s_local * S;
+      const unsigned slot = local - s_local * S;
+      const unsigned seg_local = P.slot_seg ? static_cast<unsigned>(P.slot_seg[bn.seg_base + slot]) : slot;
       const int4 sg = g.seg[bn.seg_base + seg_local];
       const long long gi = bn.node_base + sg.x;
       EmitItem it;
@@ -590,7 +655,9 @@ __global__ void __launch_bounds__(kBatchEmitWarps * 32) batch_emit_kernel(BatchE
       it.n = bn.n;
       it.uecm = bn.model == MH_UECM;
       it.row_at = 0;
-      if (csr) {
+      if (csr && P.slot_seg) {
+        it.row_at = off_l;  // node-order wave: the item offset is the CSR position
+      } else if (csr) {
         const long long row_first = w.item_begin + static_cast<long long>(s_local) * S + g.rowoff[bn.node1_base + sg.x];
         it.row_at = P.o.csr_off[w.csr_base + static_cast<long long>(s_local) * (bn.n + 1) + it.u] +
                     (off_l - P.item_off[row_first]);
@@ -1022,6 +1089,25 @@ int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_par
       Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + B.net_ctrl) + t;
       const int r = prepare_network(g, L, ws, ctrl, ds->lane[l]);
       if (r != MH_OK) return r;
+      // node-id order of the network's work items (CSR waves)
+      {
+        const BatchNet& bn = bnets[t];
+        long long* rn = reinterpret_cast<long long*>(ws + B.rowoff_node) + bn.node1_base;
+        int32_t* ss = reinterpret_cast<int32_t*>(ws + B.seg_slot) + bn.seg_base;
+        int32_t* sl = reinterpret_cast<int32_t*>(ws + B.slot_seg) + bn.seg_base;
+        const unsigned sms = static_cast<unsigned>(sm_count());
+        node_seg_count_kernel<<<grid_for(bn.n + 1, 256, sms * 4u), 256, 0, ds->lane[l]>>>(g, ctrl, rn);
+        note_launches(1);
+        MHB_CUDA(cudaGetLastError());
+        const ScanState st{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
+                           reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles,
+                           (params->flags & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
+        MHB_CUDA((scan_any<long long, SumOp<long long>>(rn, rn, ScanLen{bn.n + 1, nullptr, 1}, true, nullptr,
+                                                         nullptr, false, st, ds->lane[l])));
+        seg_slot_kernel<<<grid_for(bn.max_segments, 256, sms * 4u), 256, 0, ds->lane[l]>>>(g, ctrl, rn, ss, sl);
+        note_launches(1);
+        MHB_CUDA(cudaGetLastError());
+      }
     }
     for (int l = 0; l < B.lanes; ++l) {
       MHB_CUDA(cudaEventRecord(ds->join[l], ds->lane[l]));
@@ -1213,6 +1299,9 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
                              (fl & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
   long long* pair_counts = reinterpret_cast<long long*>(ws + B.pair_counts);
   const bool timed = (fl & MH_TIMING) != 0;
+  // CSR-only waves number their work items by node id (the COO order stays
+  // the canonical rank order)
+  const bool node_order = out.csr_off != nullptr && out.src == nullptr;
 
   auto enqueue = [&](cudaStream_t q) -> int {
     MHB_CUDA(cudaMemcpyAsync(V.wave, hshare, share_bytes, cudaMemcpyHostToDevice, q));
@@ -1238,6 +1327,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
       bq.n_order = B.n_model[m];
       bq.ticket = m ? &wc->ticket2 : &wc->ticket;
       bq.total = &wc->model_items[m];
+      bq.seg_slot = node_order ? reinterpret_cast<const int32_t*>(ws + B.seg_slot) : nullptr;
       MHB_CUDA(launch_walk_batched(model_view(gall, m), c, bq, wc, m, (m == 1 && both) ? ds->aux : q));
     }
     if (both) {
@@ -1252,7 +1342,12 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
                                                                               pair_count);
     note_launches(1);
     MHB_CUDA(cudaGetLastError());
-    if (out.csr_off) {
+    if (out.csr_off && node_order) {
+      batch_csr_off_kernel<<<grid_for(B.csr_max, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
+          V, reinterpret_cast<const long long*>(ws + B.rowoff_node), c.item_off, out.csr_off);
+      note_launches(1);
+      MHB_CUDA(cudaGetLastError());
+    } else if (out.csr_off) {
       batch_csr_count_kernel<<<grid_for(B.csr_max, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
           V, gall.rank, gall.rowoff, c.item_off, out.csr_off);
       note_launches(1);
@@ -1262,7 +1357,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
       MHB_CUDA(e);
     }
     BatchEmitParams P{V, gall, c.item_cnt, c.item_base, c.item_off, c.staging, c.staging_cap, out, c.key0,
-                      B.n_model[1] > 0};
+                      B.n_model[1] > 0, node_order ? reinterpret_cast<const int32_t*>(ws + B.slot_seg) : nullptr};
     batch_emit_kernel<<<grid_for(items_max, kBatchEmitWarps * kEmitGroup, static_cast<unsigned>(sm_count()) * 5u),
                         kBatchEmitWarps * 32, 0, q>>>(P);
     note_launches(1);

@@ -323,6 +323,10 @@ struct BatchQueue {
   int n_order;
   unsigned long long* ticket;
   const long long* total;  // queue length
+  // CSR waves: the slot of each segment-table row among its network's rows
+  // in node-id order (work items numbered (sample, node id, segment)); NULL
+  // numbers them (sample, rank, segment)
+  const int32_t* seg_slot;
 };
 cudaError_t launch_walk_batched(const Net& g, const ChunkArgs& c, const BatchQueue& q, Ctrl* ctrl, int model,
                                 cudaStream_t s);

@@ -248,6 +248,8 @@ __device__ __forceinline__ long long begin_queued(const Net& g, const BatchQueue
   key1 = w.key1;
   wk.begin_seg(g, static_cast<unsigned>(bn.seg_base) + seg, w.sample_lo + s_local, static_cast<int>(bn.node_base),
                kUecm);
+  if (q.seg_slot)  // CSR wave: the item's slot among its sample's rows in node-id order
+    return w.item_begin + static_cast<long long>(s_local) * S + q.seg_slot[bn.seg_base + seg];
   return w.item_begin + local;
 }
 
