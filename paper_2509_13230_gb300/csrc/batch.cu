@@ -67,7 +67,7 @@ struct BatchLayout {
   // persistent part (the first `image` bytes are copied from the host)
   size_t header = 0, nets = 0, order = 0, image = 0, net_ctrl = 0, wave = 0, mb = 0, wave_ctrl = 0;
   size_t perm = 0, rank = 0, xs = 0, ys = 0, as = 0, xdf = 0, adf = 0, ydf = 0, lny = 0, top = 0, Q = 0,
-         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, rowoff_node = 0, seg_slot = 0, slot_seg = 0,
+         rowoff = 0, seg = 0, seg_c = 0, seg_cf = 0, rowoff_node = 0, seg_slot = 0, slot_ik = 0,
          persistent_end = 0;
   // preparation scratch of one lane, relative to the lane's start
   Layout lane;
@@ -130,7 +130,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
   B.seg_cf = take(16 * SG);
   B.rowoff_node = take(8 * N1);
   B.seg_slot = take(4 * SG);
-  B.slot_seg = take(4 * SG);
+  B.slot_ik = take(8 * SG);
   B.persistent_end = off;
 
   // one lane's sort and scan scratch, sized for the largest network
@@ -503,7 +503,8 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
 // Node-id order of a network's work items, for CSR waves: rowoff_node[u] =
 // the first slot of node u's row (an exclusive scan over node ids of each
 // row's segment count; rowoff_node[n] = S), seg_slot[sg] = the slot of
-// segment-table row sg, slot_seg its inverse.  A CSR wave numbers its items
+// segment-table row sg, and slot_ik[slot] = (row rank, segment index) of the
+// row at that slot, which the emit reads in slot order.  A CSR wave numbers its items
 // (sample, node id, segment), so the item scan gives every edge's CSR
 // position at once: the index array lists rows by node id.
 __global__ void node_seg_count_kernel(Net g, const Ctrl* ctrl, long long* __restrict__ rowoff_node) {
@@ -524,7 +525,7 @@ __global__ void node_seg_count_kernel(Net g, const Ctrl* ctrl, long long* __rest
 }
 
 __global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__ rowoff_node,
-                                int32_t* __restrict__ seg_slot, int32_t* __restrict__ slot_seg) {
+                                int32_t* __restrict__ seg_slot, int2* __restrict__ slot_ik) {
   long long S = ctrl->num_segments;
   if (S > g.max_segments) S = g.max_segments;
   for (int64_t sg = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; sg < S;
@@ -536,7 +537,7 @@ __global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__
       continue;
     }
     seg_slot[sg] = static_cast<int32_t>(slot);
-    slot_seg[slot] = static_cast<int32_t>(sg);
+    slot_ik[slot] = make_int2(e.x, e.y);
   }
 }
 
@@ -570,7 +571,7 @@ struct BatchEmitParams {
   Outputs o;
   uint32_t key0;
   bool any_uecm;
-  const int32_t* slot_seg;  // node-order CSR wave: the segment of each slot (NULL: rank order)
+  const int2* slot_ik;  // node-order CSR wave: (row rank, segment index) of each slot (NULL: rank order)
 };
 
 // What every edge of a work item shares, set up once per item.
@@ -640,25 +641,30 @@ __global__ void __launch_bounds__(kBatchEmitWarps * 32) batch_emit_kernel(BatchE
       const unsigned S = static_cast<unsigned>(w.S);
       const unsigned s_local = local / S;
       const unsigned slot = local - s_local * S;
-      const unsigned seg_local = P.slot_seg ? static_cast<unsigned>(P.slot_seg[bn.seg_base + slot]) : slot;
-      const int4 sg = g.seg[bn.seg_base + seg_local];
-      const long long gi = bn.node_base + sg.x;
+      int2 ik;
+      if (P.slot_ik) {
+        ik = P.slot_ik[bn.seg_base + slot];  // read in slot order
+      } else {
+        const int4 sg = g.seg[bn.seg_base + slot];
+        ik = make_int2(sg.x, sg.y);
+      }
+      const long long gi = bn.node_base + ik.x;
       EmitItem it;
       it.base = P.item_base[item];
       it.cnt = my_cnt;
-      it.i = sg.x;
-      it.u = g.perm[gi];
-      it.k = sg.y;
+      it.i = ik.x;
+      it.u = P.o.src ? g.perm[gi] : 0;  // the row's id, for COO only
+      it.k = ik.y;
       it.sample = w.sample_lo + s_local;
       it.key1 = w.key1;
       it.nb = static_cast<int>(bn.node_base);
       it.n = bn.n;
       it.uecm = bn.model == MH_UECM;
       it.row_at = 0;
-      if (csr && P.slot_seg) {
+      if (csr && P.slot_ik) {
         it.row_at = off_l;  // node-order wave: the item offset is the CSR position
       } else if (csr) {
-        const long long row_first = w.item_begin + static_cast<long long>(s_local) * S + g.rowoff[bn.node1_base + sg.x];
+        const long long row_first = w.item_begin + static_cast<long long>(s_local) * S + g.rowoff[bn.node1_base + ik.x];
         it.row_at = P.o.csr_off[w.csr_base + static_cast<long long>(s_local) * (bn.n + 1) + it.u] +
                     (off_l - P.item_off[row_first]);
       }
@@ -1094,7 +1100,7 @@ int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_par
         const BatchNet& bn = bnets[t];
         long long* rn = reinterpret_cast<long long*>(ws + B.rowoff_node) + bn.node1_base;
         int32_t* ss = reinterpret_cast<int32_t*>(ws + B.seg_slot) + bn.seg_base;
-        int32_t* sl = reinterpret_cast<int32_t*>(ws + B.slot_seg) + bn.seg_base;
+        int2* sl = reinterpret_cast<int2*>(ws + B.slot_ik) + bn.seg_base;
         const unsigned sms = static_cast<unsigned>(sm_count());
         node_seg_count_kernel<<<grid_for(bn.n + 1, 256, sms * 4u), 256, 0, ds->lane[l]>>>(g, ctrl, rn);
         note_launches(1);
@@ -1357,7 +1363,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
       MHB_CUDA(e);
     }
     BatchEmitParams P{V, gall, c.item_cnt, c.item_base, c.item_off, c.staging, c.staging_cap, out, c.key0,
-                      B.n_model[1] > 0, node_order ? reinterpret_cast<const int32_t*>(ws + B.slot_seg) : nullptr};
+                      B.n_model[1] > 0, node_order ? reinterpret_cast<const int2*>(ws + B.slot_ik) : nullptr};
     batch_emit_kernel<<<grid_for(items_max, kBatchEmitWarps * kEmitGroup, static_cast<unsigned>(sm_count()) * 5u),
                         kBatchEmitWarps * 32, 0, q>>>(P);
     note_launches(1);
