@@ -542,21 +542,34 @@ __global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__
 }
 
 // CSR offsets of a node-order wave: entry (pair, u) is the item offset of
-// node u's first slot (u = n: the pair's end).
-__global__ void batch_csr_off_kernel(BatchView V, const long long* __restrict__ rowoff_node,
-                                     const long long* __restrict__ item_off, long long* __restrict__ csr_off) {
+// node u's first slot (u = n: the pair's end).  Blocks take chunks of
+// consecutive entries; the network of the chunk's first entry is searched
+// once and the threads scan forward from it.
+constexpr int kCsrOffChunk = 4096;
+
+__global__ void __launch_bounds__(256) batch_csr_off_kernel(BatchView V, const long long* __restrict__ rowoff_node,
+                                                            const long long* __restrict__ item_off,
+                                                            long long* __restrict__ csr_off) {
+  __shared__ int t_first;
   const long long total = V.wc->num_segments;
-  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < total;
-       o += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int t = last_at_or_below(V.n_nets, o, [&](int k) { return V.wave[k].csr_base; });
-    const WaveNet& w = V.wave[t];
-    const BatchNet& bn = V.nets[t];
-    // a wave holds fewer than 2^31 CSR offsets
-    const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
-    const unsigned rel = static_cast<unsigned>(o - w.csr_base);
-    const long long s = rel / n1;
-    const long long u = rel - static_cast<unsigned>(s) * n1;
-    csr_off[o] = item_off[w.item_begin + s * w.S + rowoff_node[bn.node1_base + u]];
+  for (long long c0 = static_cast<long long>(blockIdx.x) * kCsrOffChunk; c0 < total;
+       c0 += static_cast<long long>(gridDim.x) * kCsrOffChunk) {
+    if (threadIdx.x == 0) t_first = last_at_or_below(V.n_nets, c0, [&](int k) { return V.wave[k].csr_base; });
+    __syncthreads();
+    int t = t_first;
+    for (int k = threadIdx.x; k < kCsrOffChunk && c0 + k < total; k += blockDim.x) {
+      const long long o = c0 + k;
+      while (t + 1 < V.n_nets && V.wave[t + 1].csr_base <= o) ++t;
+      const WaveNet& w = V.wave[t];
+      const BatchNet& bn = V.nets[t];
+      // a wave holds fewer than 2^31 CSR offsets
+      const unsigned n1 = static_cast<unsigned>(bn.n) + 1u;
+      const unsigned rel = static_cast<unsigned>(o - w.csr_base);
+      const long long s = rel / n1;
+      const long long u = rel - static_cast<unsigned>(s) * n1;
+      csr_off[o] = item_off[w.item_begin + s * w.S + rowoff_node[bn.node1_base + u]];
+    }
+    __syncthreads();  // t_first is rewritten for the next chunk
   }
 }
 
@@ -1365,7 +1378,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
     note_launches(1);
     MHB_CUDA(cudaGetLastError());
     if (out.csr_off && node_order) {
-      batch_csr_off_kernel<<<grid_for(B.csr_max, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
+      batch_csr_off_kernel<<<grid_for(B.csr_max, kCsrOffChunk, static_cast<unsigned>(sm_count()) * 8u), 256, 0, q>>>(
           V, reinterpret_cast<const long long*>(ws + B.rowoff_node), c.item_off, out.csr_off);
       note_launches(1);
       MHB_CUDA(cudaGetLastError());

@@ -98,6 +98,9 @@ __device__ __forceinline__ T block_inclusive_scan(T& v, T* warp_sums) {
   return agg;
 }
 
+// Tile aggregates.  The operators are exact and commutative, so a thread
+// takes elements k * kScanThreads + tid of the tile (k = 0 .. kScanIPT - 1):
+// every load of the warp is one contiguous run.
 template <typename T, typename Op, bool kReverse>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T* __restrict__ in, ScanLen L,
                                                                     T* __restrict__ partial) {
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T* __re
   T acc = Op::identity();
 #pragma unroll
   for (int k = 0; k < kScanIPT; ++k) {
-    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+    const int64_t e = base + static_cast<int64_t>(k) * kScanThreads + threadIdx.x;
     if (e < len) acc = op(acc, in[scan_index<kReverse>(e, len)]);
   }
   const T agg = block_inclusive_scan<T, Op>(acc, warp_sums);
@@ -147,23 +150,38 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(T* __restrict__ par
   }
 }
 
+// Scan of each tile with its carry-in.  The tile moves between global and
+// shared memory in rounds of kScanThreads contiguous elements (coalesced),
+// and each thread scans kScanIPT consecutive elements from shared memory
+// (element i stored at i + i / 32, which spreads a thread's consecutive
+// elements over the banks).
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
 template <typename T, typename Op, bool kReverse>
 __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T* out, ScanLen L,
                                                                    const T* __restrict__ partial, bool exclusive,
                                                                    bool write_total_at_len) {
-  // `in` and `out` may alias: each thread reads only the elements it writes.
+  // `in` and `out` may alias: a block reads all of its tile before it writes.
   __shared__ T warp_sums[kScanThreads / 32];
+  __shared__ T last_of_warp[kScanThreads / 32];
+  __shared__ T tile[kScanTile + kScanTile / 32];
   const int64_t len = L.get();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
   if (len == 0 && blockIdx.x == 0 && threadIdx.x == 0 && write_total_at_len) out[0] = partial[0];
   if (base >= len) return;
   Op op;
+#pragma unroll
+  for (int k = 0; k < kScanIPT; ++k) {
+    const int i = k * kScanThreads + threadIdx.x;
+    const int64_t e = base + i;
+    tile[scan_pad(i)] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+  }
+  __syncthreads();
   T vals[kScanIPT];
   T acc = Op::identity();
 #pragma unroll
   for (int k = 0; k < kScanIPT; ++k) {
-    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
-    vals[k] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+    vals[k] = tile[scan_pad(threadIdx.x * kScanIPT + k)];
     acc = op(acc, vals[k]);
   }
   T inc = acc;
@@ -171,18 +189,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T
   // exclusive prefix of this thread = carry-in (+) inclusive of the previous thread
   T prev = shfl_up(inc, 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ T last_of_warp[kScanThreads / 32];
   if (lane == 31) last_of_warp[warp] = inc;
   __syncthreads();
   if (lane == 0) prev = warp > 0 ? last_of_warp[warp - 1] : Op::identity();
   T run = op(partial[blockIdx.x], prev);
 #pragma unroll
   for (int k = 0; k < kScanIPT; ++k) {
-    const int64_t e = base + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
+    const int i = threadIdx.x * kScanIPT + k;
     const T next = op(run, vals[k]);
-    if (e < len) out[scan_index<kReverse>(e, len)] = exclusive ? run : next;
-    if (write_total_at_len && e == len - 1) out[len] = next;
+    tile[scan_pad(i)] = exclusive ? run : next;
+    if (write_total_at_len && base + i == len - 1) out[len] = next;
     run = next;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanIPT; ++k) {
+    const int i = k * kScanThreads + threadIdx.x;
+    const int64_t e = base + i;
+    if (e < len) out[scan_index<kReverse>(e, len)] = tile[scan_pad(i)];
   }
 }
 
