@@ -1463,9 +1463,9 @@ def main():
     ap.add_argument("--ensemble-networks", type=int, default=128,
                     help="networks of the ensemble leg (evenly spaced subset of the 128)")
     ap.add_argument("--ensemble-samples", type=int, default=ENSEMBLE_SAMPLES, help="samples per network")
-    ap.add_argument("--ensemble-capacity", type=int, default=1 << 30,
+    ap.add_argument("--ensemble-capacity", type=int, default=1 << 31,
                     help="edges per wave (output buffers reused by every wave)")
-    ap.add_argument("--ensemble-wave-items", type=int, default=1 << 28,
+    ap.add_argument("--ensemble-wave-items", type=int, default=1 << 29,
                     help="work items (sample, segment) per wave")
     ap.add_argument("--ensemble-loop-samples", type=int, default=4,
                     help="samples per network of the ensemble's per-sample loop (0 skips the loop)")

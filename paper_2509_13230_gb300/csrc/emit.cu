@@ -181,23 +181,39 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(EmitParams P) {
     }
     __syncwarp();
     const unsigned tot = static_cast<unsigned>(total);
-    for (unsigned p0 = 0; p0 < tot; p0 += 32) {
-      const unsigned idx = p0 + lane;
-      int l = 0;
+    // Lane state of a pass: its item, edge and staged rank, the rank loaded
+    // one pass ahead so that the load overlaps the current pass's work.
+    auto locate = [&](unsigned idx, int& l, int& e) -> bool {
+      l = 0;
 #pragma unroll
       for (int step = 16; step; step >>= 1) {
         const unsigned v = __shfl_sync(0xffffffffu, rel, l + step);
         if (v <= idx) l += step;
       }
       const unsigned rel_l = __shfl_sync(0xffffffffu, rel, l);
-      if (idx >= tot) continue;
-      const ItemRec& r = info[l];
-      const int e = static_cast<int>(idx - rel_l);
-      if (e >= r.cnt) {  // offsets inconsistent with the counts: never read past a run
+      if (idx >= tot) return false;
+      e = static_cast<int>(idx - rel_l);
+      if (e >= info[l].cnt) {  // offsets inconsistent with the counts: never read past a run
         bad = true;
-        continue;
+        return false;
       }
-      const int32_t j = P.c.staging[r.base + e];
+      return true;
+    };
+    int l_n = 0, e_n = 0;
+    int32_t j_n = 0;
+    bool ok_n = locate(lane, l_n, e_n);
+    if (ok_n) j_n = P.c.staging[info[l_n].base + e_n];
+    for (unsigned p0 = 0; p0 < tot; p0 += 32) {
+      const unsigned idx = p0 + lane;
+      const int l = l_n, e = e_n;
+      const int32_t j = j_n;
+      const bool ok = ok_n;
+      if (p0 + 32 < tot) {  // warp-uniform
+        ok_n = locate(idx + 32, l_n, e_n);
+        if (ok_n) j_n = P.c.staging[info[l_n].base + e_n];
+      }
+      if (!ok) continue;
+      const ItemRec& r = info[l];
       if (j < row_start(g, r.i) || j >= g.n || j == r.ex) {  // cannot happen for a walked segment
         bad = true;
         continue;
