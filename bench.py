@@ -1392,7 +1392,7 @@ def run_ours(args, rank, world, local_rank):
         subs["uecm_n20k_x10"] = single_call_leg(args, dev, flush)
         if not args.no_ensemble:
             subs["ensemble_lognormal"] = ensemble_leg(args, dev, flush, fitness="lognormal", samples=8,
-                                                      capacity=1 << 30, seg_target=head["config"]["seg_target"],
+                                                      capacity=1 << 31, seg_target=head["config"]["seg_target"],
                                                       loop_samples=1)
             subs["pairwise"] = pairwise_leg(args, dev, head["clocks"].get("sm_mhz"))
             subs["fit_then_sample"] = fit_leg(args, dev)
