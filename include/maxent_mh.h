@@ -292,10 +292,10 @@ typedef struct mh_network_desc {
 } mh_network_desc;
 
 /*
- * Workspace bytes for a batch: the prepared networks (about 100 bytes per
- * node plus 40 bytes per segment-table row) and the larger of the sort
- * scratch and a wave's buffers (24 bytes per work item, staging for
- * capacity_edges edges).
+ * Workspace bytes for a batch: the prepared networks (about 112 bytes per
+ * node plus 52 bytes per segment-table row, the node-order slot maps of CSR
+ * waves included) and the larger of the sort scratch and a wave's buffers
+ * (20 bytes per work item, staging for capacity_edges edges).
  *   h_nets           host array of n_nets descriptors (1 <= n_nets <= 65536,
  *                    sum of n < 2^31 - 2^20)
  *   params           seed, sample_begin, num_samples (per network),

@@ -176,7 +176,7 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.Q = take(8 * n1);
   L.rowoff = take(8 * r1);
   L.seg = take(sizeof(int4) * static_cast<size_t>(L.max_segments));
-  L.item_cnt = take(8 * static_cast<size_t>(L.items_max));
+  L.item_cnt = take(4 * static_cast<size_t>(L.items_max));
   L.item_base = take(8 * static_cast<size_t>(L.items_max));
   L.item_off = take(8 * (static_cast<size_t>(L.items_max) + 1));
   L.sample_counts = take(8 * static_cast<size_t>(p.num_samples));
@@ -500,7 +500,7 @@ static int enqueue_sample(const Net& g_full, const Layout& L, char* ws, const mh
   ChunkArgs c;
   c.key0 = static_cast<uint32_t>(p->seed);
   c.key1 = static_cast<uint32_t>(p->seed >> 32) + p->network_id;
-  c.item_cnt = reinterpret_cast<long long*>(ws + L.item_cnt);
+  c.item_cnt = reinterpret_cast<int32_t*>(ws + L.item_cnt);
   c.item_base = reinterpret_cast<long long*>(ws + L.item_base);
   c.item_off = reinterpret_cast<long long*>(ws + L.item_off);
   c.staging = reinterpret_cast<int32_t*>(ws + L.staging);

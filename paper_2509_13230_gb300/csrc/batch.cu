@@ -178,7 +178,7 @@ BatchLayout make_batch_layout(const mh_network_desc* nets, int n_nets, const mh_
   int64_t scan_len = items_max + 1 > B.csr_max ? items_max + 1 : B.csr_max;
   B.scan_tiles = scan_len / kScanTile + 2;
   off = B.persistent_end;
-  B.item_cnt = take(8 * static_cast<size_t>(items_max));
+  B.item_cnt = take(4 * static_cast<size_t>(items_max));
   B.item_base = take(8 * static_cast<size_t>(items_max));
   B.item_off = take(8 * (static_cast<size_t>(items_max) + 1));
   B.pair_counts = take(8 * static_cast<size_t>(B.pairs_max));
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256) batch_csr_off_kernel(BatchView V, const l
 struct BatchEmitParams {
   BatchView V;
   Net g;  // concatenated arrays
-  const long long* item_cnt;
+  const int32_t* item_cnt;
   const long long* item_base;
   const long long* item_off;
   const int32_t* staging;
@@ -1322,7 +1322,7 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
   memset(&c, 0, sizeof(c));
   c.key0 = static_cast<uint32_t>(params->seed);
   c.key1 = static_cast<uint32_t>(params->seed >> 32);
-  c.item_cnt = reinterpret_cast<long long*>(ws + B.item_cnt);
+  c.item_cnt = reinterpret_cast<int32_t*>(ws + B.item_cnt);
   c.item_base = reinterpret_cast<long long*>(ws + B.item_base);
   c.item_off = reinterpret_cast<long long*>(ws + B.item_off);
   c.staging = reinterpret_cast<int32_t*>(ws + B.staging);
@@ -1370,7 +1370,8 @@ int mh_sample_batched(const mh_network_desc* h_nets, int32_t n_nets, const mh_pa
       MHB_CUDA(cudaStreamWaitEvent(q, ds->join[0], 0));
     }
     if (timed) MHB_CUDA(mark(ds->timer[2], q));
-    cudaError_t e = scan_any<long long, SumOp<long long>>(c.item_cnt, c.item_off, ScanLen{items_max, &wc->wave_items, 1},
+    cudaError_t e = scan_any<long long, SumOp<long long>, false, int32_t>(c.item_cnt, c.item_off,
+                                                                         ScanLen{items_max, &wc->wave_items, 1},
                                                         true, nullptr, &wc->out_end, true, scan_state, q);
     MHB_CUDA(e);
     batch_pair_counts_kernel<<<grid_for(pair_count, 256, 1024), 256, 0, q>>>(V, c.item_off, pair_counts,

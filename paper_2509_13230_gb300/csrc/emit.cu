@@ -302,7 +302,7 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
   const ScanState& st = *static_cast<const ScanState*>(c.scan_state);
   cudaError_t e;
   // item offsets (continuing from the edges of earlier chunks)
-  e = scan_any<long long, SumOp<long long>>(c.item_cnt, c.item_off,
+  e = scan_any<long long, SumOp<long long>, false, int32_t>(c.item_cnt, c.item_off,
                                                   ScanLen{c.items_max, &ctrl->num_segments, c.chunk_samples}, true,
                                                   &ctrl->out_base, &ctrl->out_end, true, st, s);
   if (e != cudaSuccess) return e;

@@ -266,7 +266,7 @@ struct ChunkArgs {
   int64_t chunk_samples;
   uint32_t sample0;     // global sample id of the chunk's first sample
   uint32_t key0, key1;
-  long long* item_cnt;
+  int32_t* item_cnt;     // edges of each work item (< 2^31: a run fits int32 staging positions)
   long long* item_base;
   long long* item_off;
   int32_t* staging;

@@ -101,8 +101,8 @@ __device__ __forceinline__ T block_inclusive_scan(T& v, T* warp_sums) {
 // Tile aggregates.  The operators are exact and commutative, so a thread
 // takes elements k * kScanThreads + tid of the tile (k = 0 .. kScanIPT - 1):
 // every load of the warp is one contiguous run.
-template <typename T, typename Op, bool kReverse>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T* __restrict__ in, ScanLen L,
+template <typename T, typename Op, bool kReverse, typename TIn = T>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const TIn* __restrict__ in, ScanLen L,
                                                                     T* __restrict__ partial) {
   __shared__ T warp_sums[kScanThreads / 32];
   const int64_t len = L.get();
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T* __re
 #pragma unroll
   for (int k = 0; k < kScanIPT; ++k) {
     const int64_t e = base + static_cast<int64_t>(k) * kScanThreads + threadIdx.x;
-    if (e < len) acc = op(acc, in[scan_index<kReverse>(e, len)]);
+    if (e < len) acc = op(acc, static_cast<T>(in[scan_index<kReverse>(e, len)]));
   }
   const T agg = block_inclusive_scan<T, Op>(acc, warp_sums);
   if (threadIdx.x == 0) partial[blockIdx.x] = agg;
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(T* __restrict__ par
 // elements over the banks).
 __device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
 
-template <typename T, typename Op, bool kReverse>
-__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T* out, ScanLen L,
+template <typename T, typename Op, bool kReverse, typename TIn = T>
+__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const TIn* in, T* out, ScanLen L,
                                                                    const T* __restrict__ partial, bool exclusive,
                                                                    bool write_total_at_len) {
   // `in` and `out` may alias: a block reads all of its tile before it writes.
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T
   for (int k = 0; k < kScanIPT; ++k) {
     const int i = k * kScanThreads + threadIdx.x;
     const int64_t e = base + i;
-    tile[scan_pad(i)] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+    tile[scan_pad(i)] = e < len ? static_cast<T>(in[scan_index<kReverse>(e, len)]) : Op::identity();
   }
   __syncthreads();
   T vals[kScanIPT];
@@ -213,13 +213,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const T* in, T
 // Multi-kernel form (reduce, scan of partials, scan with carry-in) for long
 // inputs, where a single-pass look-back would walk back over many tiles.
 // scan_tmp must hold ceil(host_len / kScanTile) + 2 elements of T.
-template <typename T, typename Op, bool kReverse = false>
-cudaError_t device_scan(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
+template <typename T, typename Op, bool kReverse = false, typename TIn = T>
+cudaError_t device_scan(const TIn* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
                         bool write_total_at_len, T* scan_tmp, cudaStream_t s) {
   const unsigned tiles = grid_for(L.host_len, kScanTile);
-  scan_reduce_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, L, scan_tmp);
+  scan_reduce_kernel<T, Op, kReverse, TIn><<<tiles, kScanThreads, 0, s>>>(in, L, scan_tmp);
   scan_partials_kernel<T, Op><<<1, 1024, 0, s>>>(scan_tmp, L, base, total);
-  scan_final_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, out, L, scan_tmp, exclusive,
+  scan_final_kernel<T, Op, kReverse, TIn><<<tiles, kScanThreads, 0, s>>>(in, out, L, scan_tmp, exclusive,
                                                                       write_total_at_len);
   note_launches(3);
   return cudaGetLastError();
@@ -329,8 +329,8 @@ __device__ __forceinline__ T warp_look_back(int64_t tile, const unsigned* flags,
   }
 }
 
-template <typename T, typename Op, bool kReverse>
-__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in, T* out, ScanLen L, bool exclusive,
+template <typename T, typename Op, bool kReverse, typename TIn = T>
+__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const TIn* in, T* out, ScanLen L, bool exclusive,
                                                                      const T* base, T* total,
                                                                      bool write_total_at_len, ScanState st) {
   __shared__ T warp_sums[kScanThreads / 32];
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in,
 #pragma unroll
     for (int k = 0; k < kScanIPT; ++k) {
       const int64_t e = b0 + static_cast<int64_t>(threadIdx.x) * kScanIPT + k;
-      vals[k] = e < len ? in[scan_index<kReverse>(e, len)] : Op::identity();
+      vals[k] = e < len ? static_cast<T>(in[scan_index<kReverse>(e, len)]) : Op::identity();
       acc = op(acc, vals[k]);
     }
     T inc = acc;
@@ -422,11 +422,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T* in,
 
 // One launch; `st` must hold ceil(host_len / kScanTile) flags and values and
 // start cleared (it is left cleared).
-template <typename T, typename Op, bool kReverse = false>
-cudaError_t device_scan_1p(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
+template <typename T, typename Op, bool kReverse = false, typename TIn = T>
+cudaError_t device_scan_1p(const TIn* in, T* out, ScanLen L, bool exclusive, const T* base, T* total,
                            bool write_total_at_len, const ScanState& st, cudaStream_t s) {
   const unsigned tiles = grid_for(L.host_len, kScanTile);
-  scan_onepass_kernel<T, Op, kReverse><<<tiles, kScanThreads, 0, s>>>(in, out, L, exclusive, base, total,
+  scan_onepass_kernel<T, Op, kReverse, TIn><<<tiles, kScanThreads, 0, s>>>(in, out, L, exclusive, base, total,
                                                                        write_total_at_len, st);
   note_launches(1);
   return cudaGetLastError();
@@ -437,12 +437,14 @@ cudaError_t device_scan_1p(const T* in, T* out, ScanLen L, bool exclusive, const
 // many tiles).  `st.values` doubles as the three-kernel form's partials.
 constexpr int64_t kOnePassMaxTiles = 1024;
 
-template <typename T, typename Op, bool kReverse = false>
-cudaError_t scan_any(const T* in, T* out, ScanLen L, bool exclusive, const T* base, T* total, bool write_total_at_len,
+// TIn: the input's element type when it differs from the sum's (int32 counts
+// scanned into int64 offsets); such a scan cannot run in place.
+template <typename T, typename Op, bool kReverse = false, typename TIn = T>
+cudaError_t scan_any(const TIn* in, T* out, ScanLen L, bool exclusive, const T* base, T* total, bool write_total_at_len,
                      const ScanState& st, cudaStream_t s) {
   if ((L.host_len + kScanTile - 1) / kScanTile <= kOnePassMaxTiles)
-    return device_scan_1p<T, Op, kReverse>(in, out, L, exclusive, base, total, write_total_at_len, st, s);
-  return device_scan<T, Op, kReverse>(in, out, L, exclusive, base, total, write_total_at_len,
+    return device_scan_1p<T, Op, kReverse, TIn>(in, out, L, exclusive, base, total, write_total_at_len, st, s);
+  return device_scan<T, Op, kReverse, TIn>(in, out, L, exclusive, base, total, write_total_at_len,
                                       static_cast<T*>(st.values), s);
 }
 

@@ -88,7 +88,7 @@ def test_batch_workspace_grows_with_nodes_items_and_capacity(lib):
     c = nat.mh_batch_workspace_size(d1, 2, p, 1 << 22, 1 << 20)
     d = nat.mh_batch_workspace_size(d1, 2, p, 1 << 20, 1 << 24)
     assert b - a >= 20000 * 100           # prepared arrays of the extra network
-    assert c - a >= 24 * ((1 << 22) - (1 << 20))   # three int64 arrays per work item
+    assert c - a >= 20 * ((1 << 22) - (1 << 20))   # int32 count, int64 staging base and offset per work item
     assert d - a >= 4 * ((1 << 24) - (1 << 20))    # int32 staging per edge of capacity
 
 
