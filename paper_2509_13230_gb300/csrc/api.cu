@@ -191,6 +191,13 @@ static Layout make_layout_impl(int model, int64_t rows, int64_t n, bool bip, con
   L.lny = take(8 * static_cast<size_t>(n));
   L.seg_c = take(8 * static_cast<size_t>(L.max_segments));
   L.seg_cf = take(16 * static_cast<size_t>(L.max_segments));
+  // CSR-only output of a one-set network numbers its work items by node id
+  // (the item scan then gives every edge its CSR position)
+  if ((p.flags & MH_OUT_CSR) && !(p.flags & MH_OUT_COO) && !sym && !bip) {
+    L.rowoff_node = take(8 * r1);
+    L.seg_slot = take(4 * static_cast<size_t>(L.max_segments));
+    L.slot_ik = take(8 * static_cast<size_t>(L.max_segments));
+  }
   if (bip) {
     const size_t r = static_cast<size_t>(rows);
     L.perm_r = take(4 * r);
@@ -512,6 +519,15 @@ static int enqueue_sample(const Net& g_full, const Layout& L, char* ws, const mh
   c.staging_cap = L.staging_entries;
   c.items_max = L.items_max;
   c.walk_ctas_per_sm = static_cast<int>(p->walk_ctas_per_sm);
+  if (L.rowoff_node && range.all()) {
+    long long* rn = reinterpret_cast<long long*>(ws + L.rowoff_node);
+    int32_t* ss = reinterpret_cast<int32_t*>(ws + L.seg_slot);
+    int2* ik = reinterpret_cast<int2*>(ws + L.slot_ik);
+    MH_CUDA(launch_node_order(g, ctrl, rn, ss, ik, scan_state, s));
+    c.seg_slot = ss;
+    c.slot_ik = ik;
+    c.rowoff_node = rn;
+  }
   if (L.sym_rev) {
     c.sym.keys[0] = reinterpret_cast<unsigned long long*>(ws + L.sym_k0);
     c.sym.keys[1] = reinterpret_cast<unsigned long long*>(ws + L.sym_k1);

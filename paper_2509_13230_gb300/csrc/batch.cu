@@ -500,47 +500,6 @@ __global__ void batch_csr_count_kernel(BatchView V, const int32_t* __restrict__ 
   }
 }
 
-// Node-id order of a network's work items, for CSR waves: rowoff_node[u] =
-// the first slot of node u's row (an exclusive scan over node ids of each
-// row's segment count; rowoff_node[n] = S), seg_slot[sg] = the slot of
-// segment-table row sg, and slot_ik[slot] = (row rank, segment index) of the
-// row at that slot, which the emit reads in slot order.  A CSR wave numbers its items
-// (sample, node id, segment), so the item scan gives every edge's CSR
-// position at once: the index array lists rows by node id.
-__global__ void node_seg_count_kernel(Net g, const Ctrl* ctrl, long long* __restrict__ rowoff_node) {
-  long long S = ctrl->num_segments;
-  if (S > g.max_segments) S = g.max_segments;  // a truncated table fails the batch; stay in bounds
-  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u <= g.n;
-       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    long long c = 0;
-    if (u < g.n) {
-      const int64_t r = g.rank[u];
-      long long lo = g.rowoff[r], hi = g.rowoff[r + 1];
-      lo = lo < S ? lo : S;
-      hi = hi < S ? hi : S;
-      c = hi - lo;
-    }
-    rowoff_node[u] = c;
-  }
-}
-
-__global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__ rowoff_node,
-                                int32_t* __restrict__ seg_slot, int2* __restrict__ slot_ik) {
-  long long S = ctrl->num_segments;
-  if (S > g.max_segments) S = g.max_segments;
-  for (int64_t sg = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; sg < S;
-       sg += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int4 e = g.seg[sg];
-    const long long slot = rowoff_node[g.perm[e.x]] + e.y;
-    if (slot < 0 || slot >= S) {  // cannot happen for a consistent table; never index with it
-      atomicOr(&ctrl->status, kStInternal);
-      continue;
-    }
-    seg_slot[sg] = static_cast<int32_t>(slot);
-    slot_ik[slot] = make_int2(e.x, e.y);
-  }
-}
-
 // CSR offsets of a node-order wave: entry (pair, u) is the item offset of
 // node u's first slot (u = n: the pair's end).  Blocks take chunks of
 // consecutive entries; the network of the chunk's first entry is searched
@@ -1130,18 +1089,10 @@ int mh_batch_prepare(const mh_network_desc* h_nets, int32_t n_nets, const mh_par
         long long* rn = reinterpret_cast<long long*>(ws + B.rowoff_node) + bn.node1_base;
         int32_t* ss = reinterpret_cast<int32_t*>(ws + B.seg_slot) + bn.seg_base;
         int2* sl = reinterpret_cast<int2*>(ws + B.slot_ik) + bn.seg_base;
-        const unsigned sms = static_cast<unsigned>(sm_count());
-        node_seg_count_kernel<<<grid_for(bn.n + 1, 256, sms * 4u), 256, 0, ds->lane[l]>>>(g, ctrl, rn);
-        note_launches(1);
-        MHB_CUDA(cudaGetLastError());
         const ScanState st{reinterpret_cast<unsigned*>(ws + L.scan_flags), ws + L.scan_values,
                            reinterpret_cast<unsigned*>(ws + L.scan_counters), ctrl, L.scan_tiles,
                            (params->flags & MH_TEST_WAIT_TIMEOUT) ? kTestStuckPolls : 0u};
-        MHB_CUDA((scan_any<long long, SumOp<long long>>(rn, rn, ScanLen{bn.n + 1, nullptr, 1}, true, nullptr,
-                                                         nullptr, false, st, ds->lane[l])));
-        seg_slot_kernel<<<grid_for(bn.max_segments, 256, sms * 4u), 256, 0, ds->lane[l]>>>(g, ctrl, rn, ss, sl);
-        note_launches(1);
-        MHB_CUDA(cudaGetLastError());
+        MHB_CUDA(launch_node_order(g, ctrl, rn, ss, sl, st, ds->lane[l]));
       }
     }
     for (int l = 0; l < B.lanes; ++l) {

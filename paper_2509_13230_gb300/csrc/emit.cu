@@ -53,6 +53,23 @@ __global__ void csr_count_kernel(Net g, const long long* __restrict__ item_off, 
   }
 }
 
+// CSR offsets of a node-order chunk: entry (sample, u) is the item offset of
+// node u's first slot (u = rows: the sample's end), positions that already
+// continue from earlier chunks.
+__global__ void csr_off_node_kernel(Net g, const long long* __restrict__ item_off,
+                                    const long long* __restrict__ rowoff_node, const Ctrl* ctrl, int64_t chunk_first,
+                                    int64_t chunk_samples, long long* __restrict__ csr_off) {
+  if (ctrl->num_segments > g.max_segments) return;  // a truncated table fails the call
+  const long long S = ctrl->num_segments;
+  const int64_t n1 = g.rows + 1;
+  const int64_t total = chunk_samples * n1;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t s = t / n1, u = t - s * n1;
+    csr_off[chunk_first * n1 + t] = item_off[s * S + rowoff_node[u]];
+  }
+}
+
 // Emit modes.  kEmitPlain writes COO and the one-row CSR.  The symmetric
 // layout takes two passes: kEmitSymPairs writes COO, the (sample, rank of
 // the lower endpoint) key and position of every edge for the key sort, the
@@ -151,31 +168,39 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(EmitParams P) {
     const int my_cnt = in ? static_cast<int>(P.c.item_cnt[item]) : 0;
     if (my_cnt > 0) {
       const int s_local = static_cast<int>(static_cast<unsigned>(item) / static_cast<unsigned>(S));  // items < 2^31
-      const long long seg = item - static_cast<long long>(s_local) * S;
-      const int4 sg = g.seg[seg];
+      const long long seg = item - static_cast<long long>(s_local) * S;  // the slot, in node order
+      int2 ik;
+      if (P.c.slot_ik) {
+        ik = P.c.slot_ik[seg];  // read in slot order
+      } else {
+        const int4 sg = g.seg[seg];
+        ik = make_int2(sg.x, sg.y);
+      }
       ItemRec r;
       r.base = P.c.item_base[item];
       r.cnt = my_cnt;
-      r.i = sg.x;
-      r.u = g.perm_r[sg.x];
-      r.k = sg.y;
+      r.i = ik.x;
+      r.u = P.c.slot_ik ? 0 : g.perm_r[ik.x];  // the row's id, for COO and rank-order CSR only
+      r.k = ik.y;
       r.s_local = s_local;
-      r.ex = g.excl ? g.excl[sg.x] : -1;
+      r.ex = g.excl ? g.excl[ik.x] : -1;
       r.at = 0;
-      if (one_row_csr || P.mode == kEmitSymForward) {
+      if (one_row_csr && P.c.slot_ik) {
+        r.at = off_l;  // node order: the item offset is the CSR position
+      } else if (one_row_csr || P.mode == kEmitSymForward) {
         const long long s_all = P.c.chunk_first + s_local;
-        const long long row_first = static_cast<long long>(s_local) * S + g.rowoff[sg.x];
+        const long long row_first = static_cast<long long>(s_local) * S + g.rowoff[ik.x];
         r.at = P.o.csr_off[s_all * n1 + r.u] + (off_l - P.c.item_off[row_first]);
         if (P.mode == kEmitSymForward) {  // after the row's arriving edges
           const long long* rv = P.c.sym.rev + static_cast<long long>(s_local) * n1;
-          r.at += rv[sg.x + 1] - rv[sg.x];
+          r.at += rv[ik.x + 1] - rv[ik.x];
         }
       }
       r.yi = 0.0;
       r.lnyi = make_float2(0.f, 0.f);
       if (uecm) {
-        r.yi = g.ys_r[sg.x];
-        r.lnyi = g.lny_r[sg.x];
+        r.yi = g.ys_r[ik.x];
+        r.lnyi = g.lny_r[ik.x];
       }
       info[lane] = r;
     }
@@ -342,7 +367,12 @@ cudaError_t launch_emit(const Net& g, const ChunkArgs& c, const Outputs& o, Ctrl
     note_launches(1);
     return cudaGetLastError();
   }
-  if (o.csr_off) {
+  if (o.csr_off && c.rowoff_node) {
+    csr_off_node_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
+        g, c.item_off, c.rowoff_node, ctrl, c.chunk_first, c.chunk_samples, o.csr_off);
+    note_launches(1);
+    MH_CUDA_RET(cudaGetLastError());
+  } else if (o.csr_off) {
     csr_count_kernel<<<grid_for(len, 256, static_cast<unsigned>(sm_count()) * 8u), 256, 0, s>>>(
         g, c.item_off, ctrl, c.chunk_first, c.chunk_samples, o.csr_off, nullptr);
     note_launches(1);

@@ -87,6 +87,9 @@ struct Layout {
   // order, per-(sample, rank) counts of edges arriving at a node, and the
   // histograms of the key sort
   size_t sym_k0 = 0, sym_k1 = 0, sym_v0 = 0, sym_v1 = 0, sym_src = 0, sym_w = 0, sym_rev = 0, sym_hist = 0;
+  // CSR-only output of a one-set network: work items numbered (sample, node
+  // id, segment) through these maps (0 when not allocated)
+  size_t rowoff_node = 0, seg_slot = 0, slot_ik = 0;
   int64_t sym_tiles = 0;
   int64_t scan_tiles = 0;
   int64_t staging_entries = 0;
@@ -248,6 +251,12 @@ cudaError_t launch_pair_sort(unsigned long long* keys[2], int32_t* vals[2], int6
                              const long long* dev_len, const int* shifts, int passes, unsigned* hist,
                              const void* scan_state, Ctrl* ctrl, int* out_buf, cudaStream_t s);
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s);
+struct ScanState;
+// Node-id order of a one-set network's work items (CSR-only output): the
+// exclusive scan over node ids of each row's segment count (rows + 1
+// entries), each table row's slot and each slot's (row rank, segment index).
+cudaError_t launch_node_order(const Net& g, Ctrl* ctrl, long long* rowoff_node, int32_t* seg_slot, int2* slot_ik,
+                              const ScanState& st, cudaStream_t s);
 cudaError_t launch_exclusions(const Net& g, cudaStream_t s);  // directed: excl[i] = rank of row i's own node
 
 // Device scratch of the symmetric CSR layout (all NULL when it is off).
@@ -274,6 +283,12 @@ struct ChunkArgs {
   void* scan_state;  // ScanState of the single-pass scans
   int64_t staging_cap;
   int64_t items_max;
+  // node-order CSR: each table row's slot, each slot's (row rank, segment
+  // index), and the exclusive scan over node ids of each row's segment count
+  // (all NULL: items in (sample, rank, segment) order)
+  const int32_t* seg_slot = nullptr;
+  const int2* slot_ik = nullptr;
+  const long long* rowoff_node = nullptr;
   int walk_ctas_per_sm;  // 0: as many walk blocks per SM as fit
   SymArgs sym{};         // symmetric CSR scratch, when requested
 };

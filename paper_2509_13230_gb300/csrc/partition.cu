@@ -270,6 +270,47 @@ __global__ void export_table_kernel(const int4* __restrict__ seg, const Ctrl* ct
   }
 }
 
+// Node-id order of a network's work items, for CSR waves: rowoff_node[u] =
+// the first slot of node u's row (an exclusive scan over node ids of each
+// row's segment count; rowoff_node[n] = S), seg_slot[sg] = the slot of
+// segment-table row sg, and slot_ik[slot] = (row rank, segment index) of the
+// row at that slot, which the emit reads in slot order.  A CSR wave numbers its items
+// (sample, node id, segment), so the item scan gives every edge's CSR
+// position at once: the index array lists rows by node id.
+__global__ void node_seg_count_kernel(Net g, const Ctrl* ctrl, long long* __restrict__ rowoff_node) {
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;  // a truncated table fails the batch; stay in bounds
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u <= g.rows;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    long long c = 0;
+    if (u < g.rows) {
+      const int64_t r = g.rank[u];
+      long long lo = g.rowoff[r], hi = g.rowoff[r + 1];
+      lo = lo < S ? lo : S;
+      hi = hi < S ? hi : S;
+      c = hi - lo;
+    }
+    rowoff_node[u] = c;
+  }
+}
+
+__global__ void seg_slot_kernel(Net g, Ctrl* ctrl, const long long* __restrict__ rowoff_node,
+                                int32_t* __restrict__ seg_slot, int2* __restrict__ slot_ik) {
+  long long S = ctrl->num_segments;
+  if (S > g.max_segments) S = g.max_segments;
+  for (int64_t sg = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; sg < S;
+       sg += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int4 e = g.seg[sg];
+    const long long slot = rowoff_node[g.perm[e.x]] + e.y;
+    if (slot < 0 || slot >= S) {  // cannot happen for a consistent table; never index with it
+      atomicOr(&ctrl->status, kStInternal);
+      continue;
+    }
+    seg_slot[sg] = static_cast<int32_t>(slot);
+    slot_ik[slot] = make_int2(e.x, e.y);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_bounds_and_partition(const Net& g, const Layout& L, char* ws, Ctrl* ctrl, cudaStream_t s) {
@@ -324,6 +365,21 @@ cudaError_t launch_export_table(const Net& g, const Ctrl* ctrl, int32_t* row, in
                                 int64_t cap, cudaStream_t s) {
   const unsigned blocks = grid_for(g.max_segments, 256, static_cast<unsigned>(sm_count()) * 8u);
   export_table_kernel<<<blocks, 256, 0, s>>>(g.seg, ctrl, g.max_segments, row, k, a, b, cap);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_order(const Net& g, Ctrl* ctrl, long long* rowoff_node, int32_t* seg_slot, int2* slot_ik,
+                              const ScanState& st, cudaStream_t s) {
+  const unsigned sms = static_cast<unsigned>(sm_count());
+  node_seg_count_kernel<<<grid_for(g.rows + 1, 256, sms * 4u), 256, 0, s>>>(g, ctrl, rowoff_node);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = scan_any<long long, SumOp<long long>>(rowoff_node, rowoff_node, ScanLen{g.rows + 1, nullptr, 1}, true, nullptr,
+                                            nullptr, false, st, s);
+  if (e != cudaSuccess) return e;
+  seg_slot_kernel<<<grid_for(g.max_segments, 256, sms * 4u), 256, 0, s>>>(g, ctrl, rowoff_node, seg_slot, slot_ik);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -395,6 +395,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
             } else {
               item = static_cast<long long>(next + rank);
               wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
+              // node-order CSR: the record goes to the segment's slot among its sample's rows
+              if (P.c.seg_slot)
+                item = static_cast<long long>(wk.sample - P.c.sample0) * S + P.c.seg_slot[wk.seg];
             }
             active = true;
             rewalk = false;
@@ -442,8 +445,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
           P.c.item_base[item] = static_cast<long long>(rbase);
           if (kBatch)
             begin_queued<kUecm>(g, P.q, qpos, queue_entry(P.q, qpos), wk, lane_key1);
-          else
-            wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
+          else  // the item's queue position: (sample in the chunk, segment)
+            wk.begin<kExcl>(g, static_cast<long long>(wk.sample - P.c.sample0) * S + wk.seg, S, P.c.sample0,
+                            kUecm);
           rewalk = true;
           cnt = 0;
         }

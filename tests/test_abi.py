@@ -86,9 +86,13 @@ def test_bipartite_workspace_and_argument_checks(lib):
 
 def test_symmetric_csr_workspace_and_argument_checks(lib):
     sym = nat.MH_OUT_CSR | nat.MH_CSR_SYMMETRIC
-    plain = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=nat.MH_OUT_CSR), 100_000)
+    # (CSR with COO: no node-order slot maps, which a CSR-only layout adds)
+    plain = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=nat.MH_OUT_CSR | nat.MH_OUT_COO),
+                                  100_000)
     with_sym = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=sym), 100_000)
     assert with_sym - plain >= 100_000 * 32  # keys, positions, sources and weights of the edges
+    csr_only = nat.mh_workspace_size(nat.MH_UECM, 1000, nat.make_params(flags=nat.MH_OUT_CSR), 100_000)
+    assert csr_only - plain >= 8 * 1001  # node-order slot maps of a CSR-only call
     for bad in [nat.MH_CSR_SYMMETRIC, nat.MH_OUT_COO | nat.MH_CSR_SYMMETRIC]:  # needs MH_OUT_CSR
         with pytest.raises(nat.MhError) as e:
             nat.mh_workspace_size(nat.MH_UBCM, 10, nat.make_params(flags=bad), 10)
