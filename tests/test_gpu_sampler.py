@@ -304,3 +304,24 @@ def test_bounded_wait_gives_up_and_next_call_is_exact(model):
     s.flags &= ~nat.MH_TEST_WAIT_TIMEOUT
     res = s.run()
     assert_matches_oracle(res, model, x, y, num_samples=2, seg_target=16)
+
+
+@pytest.mark.parametrize("model", [UBCM, UECM])
+def test_csr_only_calls_equal_the_csr_of_both_layouts(model):
+    """A CSR-only call numbers its work items by node id (node-order slot
+    maps) while a call that also writes COO keeps the rank order: the CSR
+    arrays must agree bit for bit, over several sample chunks."""
+    rng = np.random.default_rng(91)
+    n = 300_000
+    x = np.minimum(workloads.pareto_scale(n) * rng.uniform(0.0, 1.0, n) ** (-1.0 / 1.1), 50.0)
+    y = rng.uniform(0.3, 0.9, n) if model == UECM else None
+    samples = 30  # more items than one chunk holds: several chunks
+    csr, s1 = gpu_run(model, x, y, num_samples=samples, layout="csr", seed=5, sample_begin=2)
+    both, s2 = gpu_run(model, x, y, num_samples=samples, layout="both", seed=5, sample_begin=2)
+    assert np.array_equal(csr.counts, both.counts)
+    assert torch.equal(csr.csr_offsets, both.csr_offsets)
+    assert torch.equal(csr.csr_indices, both.csr_indices)
+    if model == UECM:
+        assert torch.equal(csr.csr_weights, both.csr_weights)
+    for k in range(nat.MH_NUM_STATS):
+        assert int(csr.stats[k]) == int(both.stats[k])
