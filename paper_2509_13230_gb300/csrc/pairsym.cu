@@ -243,8 +243,11 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
   __shared__ float4 cst1[kTwo ? kSymWarps : 1][32];
   // a tile's row partials: double-float (hi, lo) bits, or FP64 bits where the
   // warp's tile took the FP64 terms (rslow), whose sums may lie below FP32's range
-  __shared__ unsigned long long rpart[kQ][kSymWarps][kSymRows];
-  __shared__ int rslow[kSymWarps];
+  // two buffers where they fit the static shared memory: one barrier a tile
+  constexpr int kBufs = (kQ <= 2 && !kTwo) ? 2 : 1;
+  __shared__ unsigned long long rpart[kBufs][kQ][kSymWarps][kSymRows];
+  __shared__ int rslow[kBufs][kSymWarps];
+  int buf = 0;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t units = nb * (nb + 1) / 2;
@@ -412,11 +415,11 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
         for (int q = 0; q < kQ; ++q)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            rpart[q][warp][32 * h + lane] =
+            rpart[buf][q][warp][32 * h + lane] =
                 slow ? static_cast<unsigned long long>(__double_as_longlong(rs[h][q]))
                      : (static_cast<unsigned long long>(__float_as_uint(rsum[h][q].lo)) << 32) |
                            __float_as_uint(rsum[h][q].hi);
-        if (lane == 0) rslow[warp] = slow;
+        if (lane == 0) rslow[buf][warp] = slow;
         __syncthreads();
         if (warp < kQ) {  // warp q adds quantity q of the 16 warps, in warp order
 #pragma unroll
@@ -425,8 +428,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
             double sv = 0.0;
 #pragma unroll
             for (int w = 0; w < kSymWarps; ++w) {
-              const unsigned long long e = rpart[warp][w][32 * h + lane];
-              if (rslow[w])
+              const unsigned long long e = rpart[buf][warp][w][32 * h + lane];
+              if (rslow[buf][w])
                 sv += __longlong_as_double(static_cast<long long>(e));
               else
                 v.add(df2{__uint_as_float(static_cast<unsigned>(e)), __uint_as_float(static_cast<unsigned>(e >> 32))});
@@ -436,9 +439,11 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
             if (i < n) P[(warp * nb + J) * n + i] += v.value() + sv;
           }
         }
-        __syncthreads();  // rpart is rewritten by the next tile
+        if (kBufs == 1) __syncthreads();  // rpart is rewritten by the next tile
+        buf ^= kBufs - 1;
       }
-      if (j < n) {  // after the last tile's row entries (the barrier above), which may be these columns
+      __syncthreads();  // the last tile's row entries may be these columns (diagonal unit)
+      if (j < n) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           double* e = &P[(q * nb + I) * n + j];
