@@ -143,7 +143,7 @@ struct SegWalker {
       if (!(qc > 0.0)) return false;
     }
     const uint4 r = rnd;
-    const float t1 = __fdividef(Ef, lam_f);
+    const float t1 = quot_f(Ef, lam_f);
     const bool e1 = e_ok;
     if (!head) d += 1;
     // Philox words and -ln U of the next draw (draw 0 on a head step)

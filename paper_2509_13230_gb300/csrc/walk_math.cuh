@@ -278,8 +278,9 @@ __device__ __forceinline__ int floor_decided(df2 t, int room, unsigned& fl) {
 
 // ---- FP32 first level ------------------------------------------------------------
 // The same table, used in FP32: ln f = ln c_k + log1p(r) with r rounded once
-// and a cubic in r.  These estimates have a relative error of a few 2^-24;
-// a decision is taken from them only when it is 2^-18 t away from a boundary.
+// and a cubic in r.  These estimates have a relative error of at most 6u
+// (u = 2^-24); a skip is decided from them only when t lies 28u t + 2^-22 away
+// from an integer (floor_decided_f), a weight 2^-18 tw + 2^-22 away.
 
 // float(v) for v < 2^23, exact, without a convert instruction.
 __device__ __forceinline__ float small_u2f(unsigned v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
@@ -316,7 +317,12 @@ __device__ __forceinline__ float neg_ln_u53_f(unsigned long long N, const LnEntr
   const unsigned top = nh << lz;                // leading one at bit 31: f = top 2^-31 in [1, 2)
   const int k = static_cast<int>((top >> 22) & 511u);
   const bool half = top >= 0xC0000000u;         // f >= 1.5: use f / 2 and one more power of two
-  const float d = small_u2f(top & 0x3FFFFFu) * (half ? 0x1p-32f : 0x1p-31f);  // f - c_k, exact
+  // f - c_k: the 22 bits of top below the table index (exact) plus the 21
+  // bits of N below nh, worth lo 2^(lz - 52) in f = N 2^(lz - 52), added with
+  // one rounding (dropping them would cost up to 2^(lz - 31) in U)
+  const float d_top = small_u2f(top & 0x3FFFFFu) * (half ? 0x1p-32f : 0x1p-31f);
+  const float lo_scale = __uint_as_float(static_cast<unsigned>(127 + lz - 52 - (half ? 1 : 0)) << 23);
+  const float d = fmaf(small_u2f(static_cast<unsigned>(N & 0x1FFFFFull)), lo_scale, d_top);
   const LnEntry e = tab[k];
   const float lnf = e.ln_hi + log1p_poly_f(d * e.inv_hi);
   const float m = static_cast<float>(1 + lz - static_cast<int>(half));  // U = 2^-m f
@@ -338,7 +344,23 @@ __device__ __forceinline__ float log1p_f(df2 v, const LnEntry* tab) {
   return fmaf(fe, kLn2Lo, fmaf(fe, kLn2Hi, ln_mid_f(f, tab))) + corr;
 }
 
+// a / b to within about one rounding: the quotient of a reciprocal estimate,
+// corrected once by Newton-Raphson with an FMA residual (Markstein, "IA-64
+// and Elementary Functions", 2000): |result - a/b| <= 2^-24 |a/b| (1 + 2^-20).
+__device__ __forceinline__ float quot_f(float a, float b) {
+  const float rc = __fdividef(1.0f, b);
+  const float q0 = a * rc;
+  const float e = fmaf(-q0, b, a);
+  return fmaf(e, rc, q0);
+}
+
 // floor(t) from the FP32 estimate t ~ E / lambda: 1 and `fl` when decided.
+// Error of the estimate (u = 2^-24): neg_ln_u53_f is within 6u of E (table
+// entry and sum roundings against E >= 0.29 for U <= 3/4, and the rounded
+// offset r = (f - c) / c, |r| < 2^-9, against E >= 2^-9 above), log1p_f
+// within 6u of lambda (the same terms against lambda >= 2^-9; the series
+// below 2^-9 within 3.1u), quot_f within 1.01u: 13.1u in all.  The margin,
+// 28u t + 2^-22, is more than twice that.
 __device__ __forceinline__ int floor_decided_f(float t, int room, unsigned& fl) {
   const float froom = static_cast<float>(room);
   if (t > fmaf(froom, 0x1p-16f, froom) + 1.0f) {  // past the end of the segment
@@ -346,7 +368,7 @@ __device__ __forceinline__ int floor_decided_f(float t, int room, unsigned& fl) 
     return 1;
   }
   if (!(t < 0x1p23f)) return 0;
-  const float margin = fmaf(t, 0x1p-18f, 0x1p-22f);
+  const float margin = fmaf(t, 0x1.cp-20f, 0x1p-22f);
   const float fh = floorf(t);
   const float fr = t - fh;  // exact
   if (!(fr > margin) || !(1.0f - fr > margin)) return 0;

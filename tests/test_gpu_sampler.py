@@ -325,3 +325,21 @@ def test_csr_only_calls_equal_the_csr_of_both_layouts(model):
         assert torch.equal(csr.csr_weights, both.csr_weights)
     for k in range(nat.MH_NUM_STATS):
         assert int(csr.stats[k]) == int(both.stats[k])
+
+
+@pytest.mark.parametrize("model", [UBCM, UECM])
+def test_fast_levels_equal_fp64_only_on_long_skips(model):
+    """The sparse rows of a large capped-Pareto network make skips of 10^3 to
+    10^5 candidates, where the FP32 level's error bound matters most: the
+    default levels and the canonical FP64 path must draw the same samples."""
+    n = 1_000_000
+    rng = np.random.default_rng(97)
+    x = np.minimum(workloads.pareto_scale(n) * rng.uniform(0.0, 1.0, n) ** (-1.0 / 1.1), 50.0)
+    y = rng.uniform(0.3, 0.9, n) if model == UECM else None
+    fast, _ = gpu_run(model, x, y, num_samples=4, seed=41, layout="coo")
+    slow, _ = gpu_run(model, x, y, num_samples=4, seed=41, layout="coo", fp64_only=True)
+    assert np.array_equal(fast.counts, slow.counts)
+    assert torch.equal(fast.src, slow.src) and torch.equal(fast.dst, slow.dst)
+    if model == UECM:
+        assert torch.equal(fast.w, slow.w)
+    assert int(fast.stats[nat.MH_STAT_PROPOSALS]) == int(slow.stats[nat.MH_STAT_PROPOSALS])
