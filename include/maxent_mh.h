@@ -424,6 +424,27 @@ int mh_segment_table(int model, const double* x, const double* y, int64_t n, con
                      int64_t* seg_b, int32_t* perm, int64_t cap, int64_t* h_num_segments, mh_stream_t stream);
 
 /*
+ * mh_debug_first_level — the walk's first decision level on given inputs,
+ * for tests of its error bound.  The walk's skip is L = 1 + floor(t) with
+ * t = E / lambda, E = -ln U, lambda = -ln(1 - q) (Sec. 2.3, Fig. 2); the
+ * first level evaluates E and lambda as pairs (hi, lo) of FP32 numbers and
+ * decides floor(t) only when t lies farther than t 2^-28 + 2^-22 from every
+ * integer.  For i < n:
+ *   E_out[2i], E_out[2i+1]      the pair for E = -ln(N[i] 2^-53), N[i] in [1, 2^53]
+ *   lam_out[2i], lam_out[2i+1]  the pair for lambda = log1p(z[i]), z[i] in [2^-100, 2^16)
+ *                               (z[i] is first rounded to a double-float, as the walk holds it)
+ *   fl_out[i]                   floor(t) capped at room[i] (0 <= room[i] < 2^31), or -1 when
+ *                               the level leaves the draw to the next one
+ * All arrays are device memory owned by the caller (N uint64[n], z FP64[n],
+ * room int32[n], E_out and lam_out FP32[2n], fl_out int32[n]); outside the
+ * stated ranges the outputs are unspecified.  MH_ERR_ARG for n < 0 or a NULL
+ * pointer with n > 0.  Asynchronous on `stream`; builds the library's
+ * logarithm table on first use.
+ */
+int mh_debug_first_level(const uint64_t* N, const double* z, const int32_t* room, int64_t n, float* E_out,
+                         float* lam_out, int32_t* fl_out, mh_stream_t stream);
+
+/*
  * maxent_expected_fwd — expected degrees and strengths, the O(N^2) sums
  * behind maximum-likelihood inference (Sec. 2.2, Sec. 2.5, Sec. 4):
  *   k_out[i] = sum_{j != i} p_ij

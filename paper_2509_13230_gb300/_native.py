@@ -69,6 +69,7 @@ EXPORTED = (
     "mh_sample_batched",
     "mh_bipartite_workspace_size",
     "mh_sample_bipartite",
+    "mh_debug_first_level",
 )
 
 
@@ -186,6 +187,8 @@ def load(path: str | None = None):
         lib.maxent_expected_jacobian_diag_sym.restype = i32
         lib.maxent_expected_bwd_sym.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
         lib.maxent_expected_bwd_sym.restype = i32
+        lib.mh_debug_first_level.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+        lib.mh_debug_first_level.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
         lib.mh_bipartite_workspace_size.restype = i32
         lib.mh_sample_bipartite.argtypes = [i32, vp, vp, i64, vp, vp, i64, P, vp, sz, vp, vp, vp, vp, vp, vp, i64,
@@ -339,6 +342,10 @@ def maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_
                                        stream) -> int:
     return load().maxent_expected_jacobian_diag_rows(model, x, y, n, row_begin, row_count, dk_dx, dk_dy, ds_dx,
                                                      ds_dy, stream)
+
+
+def mh_debug_first_level(N, z, room, n, E_out, lam_out, fl_out, stream) -> int:
+    return load().mh_debug_first_level(N, z, room, n, E_out, lam_out, fl_out, stream)
 
 
 def maxent_expected_sym_workspace_size(model, n) -> tuple[int, int]:

@@ -1005,6 +1005,18 @@ int maxent_expected_bwd(int model, const double* x, const double* y, int64_t n, 
   return maxent_expected_bwd_rows(model, x, y, n, 0, n, g_k, g_s, g_x, g_y, stream);
 }
 
+int mh_debug_first_level(const uint64_t* N, const double* z, const int32_t* room, int64_t n, float* E_out,
+                         float* lam_out, int32_t* fl_out, mh_stream_t stream) {
+  if (n < 0 || (n > 0 && (!N || !z || !room || !E_out || !lam_out || !fl_out))) {
+    set_error("mh_debug_first_level: n < 0 or a NULL pointer");
+    return MH_ERR_ARG;
+  }
+  if (n == 0) return MH_OK;
+  MH_CUDA(mh::launch_first_level_probe(reinterpret_cast<const unsigned long long*>(N), z, room, n, E_out, lam_out,
+                                       fl_out, reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
 int maxent_expected_sym_workspace_size(int model, int64_t n, size_t* h_bytes) {
   if ((model != MH_UBCM && model != MH_UECM) || n < 1 || n > (1ll << 31) || !h_bytes) {
     set_error("maxent_expected_sym_workspace_size: bad model, n or NULL h_bytes");

@@ -244,6 +244,8 @@ cudaError_t sort_kernel_attributes(int dev);  // before any capture
 // use (a launch and a synchronisation: never while a stream is captured);
 // NULL if it could not be built.
 LnEntry* ln_table_ptr(cudaStream_t s = nullptr);  // per-device table, built on first use
+cudaError_t launch_first_level_probe(const unsigned long long* N, const double* z, const int32_t* room, long long n,
+                                     float* E_out, float* lam_out, int32_t* fl_out, cudaStream_t s);
 // Stable LSD sort of `len` (key, value) pairs on the 8-bit digits at the
 // given shifts, `*dev_len` of them (at most host_len) present; the result
 // is in buffer 0 or 1 as returned through *out_buf.  `st` is the scan state.

@@ -10,8 +10,9 @@
 // Random words: Philox4x32-10 of counter {d, k, i, s} (draw d of segment k of
 // row i in sample s); U from words (1,0), V from words (3,2).
 //
-// Decision arithmetic (walk_math.cuh): each draw is decided in double-float
-// arithmetic with an error bound and falls back to the canonical FP64
+// Decision arithmetic (walk_math.cuh): each draw is decided from estimates
+// with an error bound (pairs of FP32 numbers first, then double-float
+// arithmetic) and falls back to the canonical FP64
 // expressions only when it lies within that bound of a decision boundary
 // (or outside the fast path's range).  The acceptance test compares V with
 // the FP64 quotient p/q whenever the FP32 estimate is inconclusive, so the
@@ -53,26 +54,27 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // converged.  The next draw is computed one iteration ahead: it does not
 // depend on this iteration's decisions, so the dependency chains overlap.
 //
-// Decisions go through three levels: FP32 estimates (walk_math.cuh) decide
-// almost every draw; draws within the FP32 margin of a boundary recompute t
-// in double-float from the kept product; draws within that margin, or with q
-// outside the fast range, use the canonical FP64 expressions.
+// Decisions go through three levels: first-level estimates of E, lambda and
+// t as pairs of FP32 numbers (walk_math.cuh, within 2^-30.4 t of the
+// canonical t) decide almost every draw; draws within that level's margin of
+// a boundary recompute t in double-float from the kept product; draws within
+// that margin, or with q outside the fast range, use the canonical FP64
+// expressions.
 struct SegWalker {
   int32_t i, k, a, b, pos, qj;  // qj: the rank whose p (or phat) is the current q
   uint32_t sample, d;           // d: index of the next draw
   bool fresh;                   // the head of the segment is still to be set up
   bool fast;                    // q lies inside the fast levels' range
-  bool e_ok;                    // Ef is valid
   int32_t gi;                   // slot of row i in the row arrays
   int32_t ex;                   // directed: the candidate row i skips (its own in-copy)
   uint32_t seg;                 // segment-table row (UECM: its bound constant c)
   df2 xi_df, yi_df, inv1mc;     // double-float x_i (a_i), y_i and 1 / (1 - c)
   float omc_f;                  // 1 - c in FP32
   df2 zq;                       // -ln(1 - q) = log1p(zq): zq = x_i x_j (UBCM) or A / (1 - c) (UECM)
-  float lam_f;                  // log1p(zq) in FP32
+  df2 lam;                      // log1p(zq), first level
   float q_f;                    // q in FP32
   uint4 rnd;                    // Philox words of draw d
-  float Ef;                     // -ln U of draw d in FP32
+  df2 E;                        // -ln U of draw d, first level
 
   // Canonical FP64 values are read back on the (rare) FP64 paths.
   __device__ __forceinline__ double q64(const Net& g, bool uecm) const {
@@ -143,13 +145,12 @@ struct SegWalker {
       if (!(qc > 0.0)) return false;
     }
     const uint4 r = rnd;
-    const float t1 = quot_f(Ef, lam_f);
-    const bool e1 = e_ok;
+    const df2 t1 = quot_df(E, lam);
     if (!head) d += 1;
     // Philox words and -ln U of the next draw (draw 0 on a head step)
     rnd = philox4x32_10_rk<!kLaneKey>(make_uint4(d, static_cast<uint32_t>(k), static_cast<uint32_t>(i), sample), rk,
                                       key1);
-    Ef = neg_ln_u53_f(top53(rnd.y, rnd.x) + 1ull, tab, e_ok);
+    E = neg_ln_u53_m(top53(rnd.y, rnd.x) + 1ull, tab);
     int32_t jv;  // position of the candidate (virtual when kExcl)
     if (head) {
       fresh = false;
@@ -157,10 +158,11 @@ struct SegWalker {
     } else {
       const int room = b - pos - 1;
       unsigned skip = 0;
-      bool decided = fast_q && e1 && floor_decided_f(t1, room, skip);
+      bool decided = fast_q && floor_decided_m(t1, room, skip);
       if (!decided && fast_q) {  // double-float level
-        const df2 t = df_div(neg_ln_u53(top53(r.y, r.x) + 1ull, tab), log1p_df(zq, tab));
-        decided = floor_decided(t, room, skip) != 0;
+        const int fl = skip_df(top53(r.y, r.x) + 1ull, zq, room, tab);
+        decided = fl >= 0;
+        if (decided) skip = static_cast<unsigned>(fl);
       }
       if (!decided) {  // canonical FP64
         if (fast_q) fallbacks += 1;
@@ -210,7 +212,7 @@ struct SegWalker {
       fast = zq.hi > 0x1p-100f && zq.hi < kFastZq && omc_f >= 0x1p-20f;
       q_f = __fdividef(prod.hi, omc_f + prod.hi);
     }
-    lam_f = fast ? log1p_f(zq, tab) : 1.0f;
+    lam = fast ? log1p_m(zq, tab) : df2{1.0f, 0.0f};
     return true;
   }
 };
@@ -472,7 +474,35 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   }
 }
 
+// The walk's first decision level on given inputs (mh_debug_first_level).
+__global__ void first_level_probe_kernel(const unsigned long long* N, const double* z, const int32_t* room,
+                                         long long n, const LnEntry* tab, float2* E_out, float2* lam_out,
+                                         int32_t* fl_out) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const df2 E = neg_ln_u53_m(N[i], tab);
+    const df2 lam = log1p_m(df_from_double(z[i]), tab);
+    unsigned fl = 0;
+    const int decided = floor_decided_m(quot_df(E, lam), room[i], fl);
+    E_out[i] = make_float2(E.hi, E.lo);
+    lam_out[i] = make_float2(lam.hi, lam.lo);
+    fl_out[i] = decided ? static_cast<int32_t>(fl) : -1;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_first_level_probe(const unsigned long long* N, const double* z, const int32_t* room, long long n,
+                                     float* E_out, float* lam_out, int32_t* fl_out, cudaStream_t s) {
+  const LnEntry* tab = ln_table_ptr(s);
+  if (!tab) return cudaErrorLaunchFailure;
+  const long long want = (n + 255) / 256;
+  const unsigned grid = static_cast<unsigned>(want < 1024 ? (want < 1 ? 1 : want) : 1024);
+  first_level_probe_kernel<<<grid, 256, 0, s>>>(N, z, room, n, tab, reinterpret_cast<float2*>(E_out),
+                                                reinterpret_cast<float2*>(lam_out), fl_out);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 size_t walk_smem_bytes() {
   return sizeof(LnEntry) * kLnTable + static_cast<size_t>(kWalkWarps) * 32 * kSlotStride * sizeof(int32_t);

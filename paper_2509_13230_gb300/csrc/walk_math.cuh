@@ -276,26 +276,17 @@ __device__ __forceinline__ int floor_decided(df2 t, int room, unsigned& fl) {
   return 1;
 }
 
-// ---- FP32 first level ------------------------------------------------------------
+// ---- FP32 level of the weight draw ------------------------------------------------
 // The same table, used in FP32: ln f = ln c_k + log1p(r) with r rounded once
-// and a cubic in r.  These estimates have a relative error of at most 6u
-// (u = 2^-24); a skip is decided from them only when t lies 28u t + 2^-22 away
-// from an integer (floor_decided_f), a weight 2^-18 tw + 2^-22 away.
+// and a cubic in r.  The estimate of E below has a relative error of at most
+// 6u (u = 2^-24); a weight is decided from it only when tw lies 2^-18 tw +
+// 2^-22 away from an integer.
 
 // float(v) for v < 2^23, exact, without a convert instruction.
 __device__ __forceinline__ float small_u2f(unsigned v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
 
 __device__ __forceinline__ float log1p_poly_f(float r) {  // r - r^2/2 + r^3/3, |r| < 2^-9
   return r * fmaf(r, fmaf(r, 0.333333343f, -0.5f), 1.0f);
-}
-
-// ln f for f in [0.75, 1.5).
-__device__ __forceinline__ float ln_mid_f(float f, const LnEntry* tab) {
-  const unsigned bits = __float_as_uint(f);
-  const int k = static_cast<int>((bits >> 14) & 511u);
-  const float c = __uint_as_float(bits & ~0x3FFFu);
-  const LnEntry e = tab[k];
-  return e.ln_hi + log1p_poly_f((f - c) * e.inv_hi);
 }
 
 // -ln U for U = N 2^-53.  Sets ok = false for U < 2^-8 (about 2^-8 of the
@@ -329,51 +320,144 @@ __device__ __forceinline__ float neg_ln_u53_f(unsigned long long N, const LnEntr
   return fmaf(m, kLn2Lo, fmaf(m, kLn2Hi, -lnf));
 }
 
-// log1p(v) for v.hi in [2^-100, 2^40).
-__device__ __forceinline__ float log1p_f(df2 v, const LnEntry* tab) {
-  if (v.hi < 0x1p-9f) return log1p_poly_f(v.hi) + v.lo;
-  const df2 D = two_sum(1.0f, v.hi);            // 1 + v.hi exactly
-  const float corr = __fdividef(D.lo + v.lo, D.hi);
+// ---- first level of the walk: FP32 pairs ---------------------------------------------
+// E = -ln U and lambda = log1p(z) as unevaluated pairs hi + lo of FP32
+// numbers, from the same table: the leading terms (m ln 2, ln c_k, r) are
+// added with error-free transformations and everything smaller (the low
+// words of ln 2, ln c_k, 1 / c_k and of the inputs, and the series beyond r)
+// is summed in FP32 into lo, and the pair is normalised (|lo| <= ulp(hi) /
+// 2; the pair quotient needs it: its low word divides by hi alone).  Error
+// bounds (u = 2^-24), from the term sizes:
+//   E, U > 1 - 2^-9 (w = 1 - U < 2^-9): the quartic w + w^2/2 + w^3/3 + w^4/4
+//     (truncation below 2^-38 w) with its square term rounded three times,
+//     3u w^2/2 <= 2^-32.4 w, the low word of w in the square (2^-33 w) and the
+//     last rounding (2^-34 w): 2^-31.5 relative;
+//   E, U <= 1 - 2^-9: absolute errors of about 2^-41 (the cubic's roundings,
+//     3u r^2/2 with |r| <= 2^-9.6; the low word of r in the square; the three
+//     roundings of lo) against E >= 2^-9: 2^-32;
+//   lambda, z < 2^-9: as the first case, 2^-31.5 (plus 2^-44 carried by the
+//     double-float z itself);
+//   lambda, z >= 2^-9: absolute about 2^-40.3 against lambda >= 2^-9: 2^-31.3.
+// The pair quotient adds below 2^-41 and the canonical FP64 t differs from
+// E / lambda by at most 2^-39.5 relative (the fast-range note above), so the
+// estimate of t lies within 2^-30.4 t (plus 2^-24 from rounding its
+// fraction) of the canonical t; floor_decided_m decides a skip only when t
+// lies 2^-28 t + 2^-22 away from every integer, over five times that.
+
+// ln 2 = kLn2A + kLn2B with kLn2A of 17 significant bits (m kLn2A exact for
+// integers m < 128) and kLn2B rounded to FP32 (error below 2^-44).
+constexpr float kLn2A = 0x1.62e4p-1f;
+constexpr float kLn2B = 0x1.7f7d1cp-20f;
+
+// log1p(r) - r = r^2 (-1/2 + r/3 - r^2/4) + lo, for |r| < 2^-9 (truncation
+// below |r|^5 / 5); `lo` is the low word of r.
+__device__ __forceinline__ float log1p_rest(float r, float lo) {
+  return fmaf(r * r, fmaf(r, fmaf(r, -0.25f, 0.333333343f), -0.5f), lo);
+}
+
+// E = -ln U for U = N 2^-53, N = 1 .. 2^53, as hi + lo.
+__device__ __forceinline__ df2 neg_ln_u53_m(unsigned long long N, const LnEntry* tab) {
+  const unsigned long long W = (1ull << 53) - N;
+  if (W < (1ull << 44)) {  // U > 1 - 2^-9: -ln(1 - w) = w + w^2/2 + w^3/3 + w^4/4
+    const df2 w = fast_two_sum(small_u2f(static_cast<unsigned>(W >> 21)) * 0x1p-32f,   // exact (23 bits)
+                               small_u2f(static_cast<unsigned>(W & 0x1FFFFFu)) * 0x1p-53f);  // exact (21 bits)
+    return fast_two_sum(w.hi, fmaf(w.hi * w.hi, fmaf(w.hi, fmaf(w.hi, 0.25f, 0.333333343f), 0.5f), w.lo));
+  }
+  // N = 2^(63 - lz64) f with f = top 2^-31 + low 2^-52 in [1, 2): top holds the
+  // leading 32 bits, low the 21 bits below them
+  unsigned nh = static_cast<unsigned>(N >> 21);
+  unsigned low = static_cast<unsigned>(N) & 0x1FFFFFu;
+  int lz = __clz(nh);
+  float lo_scale;
+  int m;  // U = 2^-m f before the halving below
+  if (lz <= 8) {
+    nh <<= lz;
+    lo_scale = __uint_as_float(static_cast<unsigned>(127 + lz - 52) << 23);
+    m = 1 + lz;
+  } else {  // U < 2^-8: normalise over the whole word (about 2^-8 of the draws)
+    lz = __clzll(static_cast<long long>(N));
+    const unsigned long long Nn = N << lz;
+    nh = static_cast<unsigned>(Nn >> 32);
+    low = static_cast<unsigned>(Nn) >> 11;  // the 21 low significant bits (bits 10..0 of Nn are zero)
+    lo_scale = 0x1p-52f;
+    m = lz - 10;
+  }
+  const bool half = nh >= 0xC0000000u;  // f >= 1.5: use f / 2 and one more power of two
+  const LnEntry e = tab[(nh >> 22) & 511u];
+  // f - c_k = d_hi + d_lo, both exact: the 22 bits of nh below the table index and the low bits
+  const float d_hi = small_u2f(nh & 0x3FFFFFu) * (half ? 0x1p-32f : 0x1p-31f);
+  const float d_lo = small_u2f(low) * (half ? 0.5f * lo_scale : lo_scale);
+  const float mf = static_cast<float>(m - static_cast<int>(half));  // U = 2^-m f, m >= 0
+  // r = (f - c_k) / c_k = r_hi + r_lo, |r| < 2^-9.6.  d_hi + d_lo is not
+  // normalised (d_lo reaches 2^-23), so r_lo can exceed an ulp of r_hi: the
+  // square term takes the rounded sum r_hi + r_lo (relative error 2^-24).
+  const float r_hi = d_hi * e.inv_hi;
+  const float r_lo = fmaf(d_lo, e.inv_hi, fmaf(d_hi, e.inv_lo, fmaf(d_hi, e.inv_hi, -r_hi)));
+  // E = m ln 2 - ln c_k - log1p(r).  m kLn2A >= |ln c_k| (m >= 1) or m = 0,
+  // and |m kLn2A - ln c_k| >= 2^-9 > |r_hi| (m = 0 only for f / 2 < 1 - 2^-9).
+  const df2 s = fast_two_sum(mf * kLn2A, -e.ln_hi);
+  const df2 v = fast_two_sum(s.hi, -r_hi);
+  return fast_two_sum(v.hi, v.lo + (s.lo + (fmaf(mf, kLn2B, -e.ln_lo) - log1p_rest(r_hi + r_lo, r_lo))));
+}
+
+// lambda = log1p(v) for a double-float v with v.hi in [2^-100, 2^40), as hi + lo.
+__device__ __forceinline__ df2 log1p_m(df2 v, const LnEntry* tab) {
+  if (v.hi < 0x1p-9f) return fast_two_sum(v.hi, log1p_rest(v.hi, v.lo));
+  const df2 D = two_sum(1.0f, v.hi);  // 1 + v.hi exactly
+  const float corr = __fdividef(D.lo + v.lo, D.hi);  // log1p(corr) = corr to 2^-47
   int ex = static_cast<int>((__float_as_uint(D.hi) >> 23) & 0xFF) - 127;
   float f = __uint_as_float((__float_as_uint(D.hi) & 0x007FFFFFu) | 0x3F800000u);
   if (f >= 1.5f) {
     f *= 0.5f;
     ex += 1;
   }
+  const unsigned bits = __float_as_uint(f);
+  const LnEntry e = tab[(bits >> 14) & 511u];
+  const float d = f - __uint_as_float(bits & ~0x3FFFu);  // f - c_k, exact
+  const float r_hi = d * e.inv_hi;
+  const float r_lo = fmaf(d, e.inv_lo, fmaf(d, e.inv_hi, -r_hi));
+  // lambda = ex ln 2 + ln c_k + log1p(r) + corr.  ex kLn2A >= |ln c_k| (ex >=
+  // 1) or ex = 0, where c_k >= 1 and ln c_k >= r_hi or ln c_k = 0.
   const float fe = static_cast<float>(ex);
-  return fmaf(fe, kLn2Lo, fmaf(fe, kLn2Hi, ln_mid_f(f, tab))) + corr;
+  const df2 s = fast_two_sum(fe * kLn2A, e.ln_hi);
+  const df2 w = fast_two_sum(s.hi, r_hi);
+  return fast_two_sum(w.hi, w.lo + (s.lo + (fmaf(fe, kLn2B, e.ln_lo) + (log1p_rest(r_hi, r_lo) + corr))));
 }
 
-// a / b to within about one rounding: the quotient of a reciprocal estimate,
-// corrected once by Newton-Raphson with an FMA residual (Markstein, "IA-64
-// and Elementary Functions", 2000): |result - a/b| <= 2^-24 |a/b| (1 + 2^-20).
-__device__ __forceinline__ float quot_f(float a, float b) {
-  const float rc = __fdividef(1.0f, b);
-  const float q0 = a * rc;
-  const float e = fmaf(-q0, b, a);
-  return fmaf(e, rc, q0);
+// a / b for normalised pairs (|lo| <= ulp(hi) / 2): a reciprocal
+// estimate corrected once by Newton-Raphson with an FMA residual (Markstein,
+// "IA-64 and Elementary Functions", 2000), then the low word from the
+// residual a - q b: relative error below 2^-41.
+__device__ __forceinline__ df2 quot_df(df2 a, df2 b) {
+  const float rc = __fdividef(1.0f, b.hi);
+  const float q0 = a.hi * rc;
+  const float q1 = fmaf(fmaf(-q0, b.hi, a.hi), rc, q0);
+  const float rho = fmaf(-q1, b.lo, fmaf(-q1, b.hi, a.hi) + a.lo);
+  return df2{q1, rho * rc};
 }
 
-// floor(t) from the FP32 estimate t ~ E / lambda: 1 and `fl` when decided.
-// Error of the estimate (u = 2^-24): neg_ln_u53_f is within 6u of E (table
-// entry and sum roundings against E >= 0.29 for U <= 3/4, and the rounded
-// offset r = (f - c) / c, |r| < 2^-9, against E >= 2^-9 above), log1p_f
-// within 6u of lambda (the same terms against lambda >= 2^-9; the series
-// below 2^-9 within 3.1u), quot_f within 1.01u: 13.1u in all.  The margin,
-// 28u t + 2^-22, is more than twice that.
-__device__ __forceinline__ int floor_decided_f(float t, int room, unsigned& fl) {
+// floor(t) of a first-level estimate t = hi + lo (t >= 0, hi < 2^32): 1 and
+// `fl` when t lies more than t 2^-28 + 2^-22 from every integer, 0 otherwise.
+__device__ __forceinline__ int floor_m(df2 t, unsigned& fl) {
+  const float margin = fmaf(t.hi, 0x1p-28f, 0x1p-22f);
+  const float fh = floorf(t.hi);
+  const float fr0 = (t.hi - fh) + t.lo;  // t.hi - fh exact
+  const float ff = floorf(fr0);          // -1, 0 or 1 below 2^23; lo's whole part above
+  const float fr = fr0 - ff;             // exact, or rounded up to 1 when fr0 is a tiny negative
+  if (!(fr > margin) || !(1.0f - fr > margin)) return 0;
+  fl = __float2uint_rz(fh) + static_cast<unsigned>(__float2int_rz(ff));
+  return 1;
+}
+
+// The skip's floor(t) against `room` (0 <= room < 2^31): fl >= room means
+// past the end of the segment.
+__device__ __forceinline__ int floor_decided_m(df2 t, int room, unsigned& fl) {
   const float froom = static_cast<float>(room);
-  if (t > fmaf(froom, 0x1p-16f, froom) + 1.0f) {  // past the end of the segment
+  if (t.hi > fmaf(froom, 0x1p-20f, froom) + 1.0f) {  // past the end of the segment
     fl = static_cast<unsigned>(room);
     return 1;
   }
-  if (!(t < 0x1p23f)) return 0;
-  const float margin = fmaf(t, 0x1.cp-20f, 0x1p-22f);
-  const float fh = floorf(t);
-  const float fr = t - fh;  // exact
-  if (!(fr > margin) || !(1.0f - fr > margin)) return 0;
-  fl = static_cast<unsigned>(fh);
-  return 1;
+  return floor_m(t, fl);
 }
 
 // A boundary draw: t >= 0.5 lies within 8 ulp of an integer.  The device
@@ -384,6 +468,17 @@ __device__ __forceinline__ bool near_integer(double t) {
   // ulp of a positive normal t: 2^(exponent - 52), the step to the next double up
   const double ulp = __longlong_as_double(__double_as_longlong(t) & 0x7FF0000000000000ll) * 0x1p-52;
   return fabs(t - rint(t)) <= 8.0 * ulp;
+}
+
+// Double-float level of the skip: floor(t) for U = N 2^-53 and lambda =
+// log1p(zq), capped at `room`, or -1 when t lies within that level's margin
+// of an integer.  Out of line: the walk reaches it only for draws within the
+// first level's margin (a few in 10^5 on long skips), and inlined it would
+// hold registers across the whole walk loop.
+static __device__ __noinline__ int skip_df(unsigned long long N, df2 zq, int room, const LnEntry* tab) {
+  const df2 t = df_div(neg_ln_u53(N, tab), log1p_df(zq, tab));
+  unsigned fl = 0;
+  return floor_decided(t, room, fl) ? static_cast<int>(fl) : -1;
 }
 
 // Canonical FP64 skip: floor(log(U) / log1p(-q)), capped at `room`.  A draw
