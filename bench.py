@@ -400,6 +400,10 @@ PAIR_OPS = {"fwd": 81, "bwd": 185, "jacobian_diag": 136}
 # the symmetric forms, per unordered pair: the shared terms once, both rows' and
 # both columns' accumulations (8 per term and 6 per 8-term renormalisation)
 PAIR_SYM_OPS = {"fwd": 99, "bwd": 231, "jacobian_diag": 205}
+# the FP32 forms (Newton directions): r, 1 - r, D, D^2, two reciprocals, the
+# factor (1 - r + r D) / (1 - r)^2 (3), then bwd: g sums (2), U and V (4), four
+# products; diag: two products, six; both: the row and column sums (4 or 6)
+PAIR_SYM_F32_OPS = {"bwd": 23, "jacobian_diag": 23}
 FP32_LANES_PER_SM = 128
 
 
@@ -453,16 +457,18 @@ def pairwise_leg(args, dev, sm_mhz):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
     ws = SymWorkspace()
-    for kind in ("fwd", "bwd", "jacobian_diag", "fwd_sym", "bwd_sym", "jacobian_diag_sym"):
-        sym = ws if kind.endswith("_sym") else None
-        base = kind[:-4] if sym is not None else kind
+    for kind in ("fwd", "bwd", "jacobian_diag", "fwd_sym", "bwd_sym", "jacobian_diag_sym", "bwd_sym_f32",
+                 "jacobian_diag_sym_f32"):
+        f32 = kind.endswith("_f32")
+        sym = ws if "_sym" in kind else None
+        base = kind.split("_sym")[0]
 
         def call():
             if base == "fwd":
                 return expected_fwd(nat.MH_UECM, x, y, sym=sym)
             if base == "jacobian_diag":
-                return expected_jacobian_diag(nat.MH_UECM, x, y, sym=sym)
-            return expected_bwd(nat.MH_UECM, x, y, gk, gs, sym=sym)
+                return expected_jacobian_diag(nat.MH_UECM, x, y, sym=sym, f32=f32)
+            return expected_bwd(nat.MH_UECM, x, y, gk, gs, sym=sym, f32=f32)
         for _ in range(args.warmup):
             call()
         torch.cuda.synchronize()
@@ -480,9 +486,10 @@ def pairwise_leg(args, dev, sm_mhz):
                          "achieved_gops": PAIR_OPS[kind] * pairs / (ms / 1e3) / 1e9, "clocks": clk.summary()}
         else:
             # one evaluation per unordered pair serves both rows
+            ops = (PAIR_SYM_F32_OPS if f32 else PAIR_SYM_OPS)[base]
             out[kind] = {"ms": ms, "unordered_pairs_per_s": pairs / 2 / (ms / 1e3),
-                         "fp32_ops_per_unordered_pair": PAIR_SYM_OPS[base],
-                         "achieved_gops": PAIR_SYM_OPS[base] * pairs / 2 / (ms / 1e3) / 1e9,
+                         "fp32_ops_per_unordered_pair": ops,
+                         "achieved_gops": ops * pairs / 2 / (ms / 1e3) / 1e9,
                          "speedup_over_row_form": out[base]["ms"] / ms, "clocks": clk.summary()}
     import torch.cuda as tc
     sms = tc.get_device_properties(dev).multi_processor_count

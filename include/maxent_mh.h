@@ -547,6 +547,24 @@ int maxent_expected_bwd_sym(int model, const double* x, const double* y, int64_t
                             const double* g_s, double* g_x, double* g_y, void* workspace, size_t workspace_bytes,
                             mh_stream_t stream);
 
+/*
+ * maxent_expected_jacobian_diag_sym_f32 / maxent_expected_bwd_sym_f32 — the
+ * sums of maxent_expected_jacobian_diag_sym and maxent_expected_bwd_sym
+ * (same arguments, workspace and outputs, FP64 outputs) with FP32 pair terms,
+ * summed in FP32 over tiles of 32 and 64 terms and in double-float across
+ * tiles: within about 1e-5 of the sum of the terms' magnitudes, for Newton
+ * directions (the derivatives of Sec. 2.2 and Sec. 2.5 that an inexact
+ * Newton step solves with; the residual it drives to zero keeps the
+ * double-float forms).  Operands outside the double-float range (see above)
+ * take FP64 terms as there.  Deterministic, as the other symmetric forms.
+ */
+int maxent_expected_jacobian_diag_sym_f32(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                          double* dk_dy, double* ds_dx, double* ds_dy, void* workspace,
+                                          size_t workspace_bytes, mh_stream_t stream);
+int maxent_expected_bwd_sym_f32(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                                const double* g_s, double* g_x, double* g_y, void* workspace, size_t workspace_bytes,
+                                mh_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,8 @@ EXPORTED = (
     "maxent_expected_fwd_sym",
     "maxent_expected_jacobian_diag_sym",
     "maxent_expected_bwd_sym",
+    "maxent_expected_jacobian_diag_sym_f32",
+    "maxent_expected_bwd_sym_f32",
     "mh_batch_workspace_size",
     "mh_batch_prepare",
     "mh_sample_batched",
@@ -187,6 +189,10 @@ def load(path: str | None = None):
         lib.maxent_expected_jacobian_diag_sym.restype = i32
         lib.maxent_expected_bwd_sym.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
         lib.maxent_expected_bwd_sym.restype = i32
+        lib.maxent_expected_jacobian_diag_sym_f32.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
+        lib.maxent_expected_jacobian_diag_sym_f32.restype = i32
+        lib.maxent_expected_bwd_sym_f32.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp, vp, sz, vp]
+        lib.maxent_expected_bwd_sym_f32.restype = i32
         lib.mh_debug_first_level.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
         lib.mh_debug_first_level.restype = i32
         lib.mh_bipartite_workspace_size.argtypes = [i32, i64, i64, P, i64, ctypes.POINTER(sz)]
@@ -364,3 +370,12 @@ def maxent_expected_jacobian_diag_sym(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy
 
 def maxent_expected_bwd_sym(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream) -> int:
     return load().maxent_expected_bwd_sym(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream)
+
+
+def maxent_expected_jacobian_diag_sym_f32(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, ws, ws_bytes, stream) -> int:
+    return load().maxent_expected_jacobian_diag_sym_f32(model, x, y, n, dk_dx, dk_dy, ds_dx, ds_dy, ws, ws_bytes,
+                                                        stream)
+
+
+def maxent_expected_bwd_sym_f32(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream) -> int:
+    return load().maxent_expected_bwd_sym_f32(model, x, y, n, g_k, g_s, g_x, g_y, ws, ws_bytes, stream)

@@ -1081,6 +1081,28 @@ int maxent_expected_bwd_sym(int model, const double* x, const double* y, int64_t
   return MH_OK;
 }
 
+int maxent_expected_jacobian_diag_sym_f32(int model, const double* x, const double* y, int64_t n, double* dk_dx,
+                                          double* dk_dy, double* ds_dx, double* ds_dy, void* workspace,
+                                          size_t workspace_bytes, mh_stream_t stream) {
+  const int rc = check_sym("maxent_expected_jacobian_diag_sym_f32", model, n, workspace, workspace_bytes,
+                           x && dk_dx && (model == MH_UBCM || (y && dk_dy && ds_dx && ds_dy)));
+  if (rc != MH_OK) return rc;
+  MH_CUDA(mh::launch_expected_sym(3, model, x, y, nullptr, nullptr, n, workspace, dk_dx, dk_dy, ds_dx, ds_dy,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
+int maxent_expected_bwd_sym_f32(int model, const double* x, const double* y, int64_t n, const double* g_k,
+                                const double* g_s, double* g_x, double* g_y, void* workspace, size_t workspace_bytes,
+                                mh_stream_t stream) {
+  const int rc = check_sym("maxent_expected_bwd_sym_f32", model, n, workspace, workspace_bytes,
+                           x && g_k && g_x && (model == MH_UBCM || (y && g_s && g_y)));
+  if (rc != MH_OK) return rc;
+  MH_CUDA(mh::launch_expected_sym(4, model, x, y, g_k, g_s, n, workspace, g_x, g_y, nullptr, nullptr,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+  return MH_OK;
+}
+
 }  // extern "C"
 
 // ---- forwarders for the fixed-scratch entry point (noalloc.cu) -------------------

@@ -52,17 +52,29 @@ constexpr int kSubBand = 32 * kSymWarps;  // columns of one sweep
 constexpr int kSymRows = 64;              // rows of a tile: two per lane
 constexpr unsigned kAll = 0xffffffffu;
 
-enum SymKind { kSymFwd = 0, kSymDiag = 1, kSymBwd = 2 };
+// kSymDiagF / kSymBwdF: the Jacobian diagonal and the gradient with FP32 pair
+// terms summed in FP32 over a tile (rows: 32 terms, columns: 64), the
+// tiles' partials then added as the other kinds add theirs.  Each term is
+// within a few units of 2^-24 and a tile's sum within about 2^-19 of its
+// terms' magnitudes: the relative accuracy of a Newton direction (the fit's
+// conjugate gradients stop at a relative residual of 5e-2), at a fraction
+// of the double-float terms' cost.
+enum SymKind { kSymFwd = 0, kSymDiag = 1, kSymBwd = 2, kSymDiagF = 3, kSymBwdF = 4 };
+
+__host__ __device__ constexpr int base_kind(int k) { return k == kSymDiagF ? kSymDiag : (k == kSymBwdF ? kSymBwd : k); }
+__host__ __device__ constexpr bool f32_kind(int k) { return k == kSymDiagF || k == kSymBwdF; }
 
 template <int kModel, int kKind>
 struct SymCount {
-  static constexpr int kQ = kModel == MH_UBCM ? 1 : (kKind == kSymDiag ? 3 : 2);
-  static constexpr bool kTwo = kModel == MH_UECM && kKind == kSymBwd;  // a second float4 per node
+  static constexpr int kB = base_kind(kKind);
+  static constexpr int kQ = kModel == MH_UBCM ? 1 : (kB == kSymDiag ? 3 : 2);
+  static constexpr bool kTwo = kModel == MH_UECM && kB == kSymBwd;  // a second float4 per node
 };
 
 // Per-node double-float operands, written once per call:
 //   d0  UBCM (x, g_k) / UECM (a, y)    d1  UECM gradient (g_k, g_s)
-// and a bit per node (word i / 32) set when an operand is outside the
+// (FP32 kinds: d0 UBCM (x, g_k, 0, 0) / UECM (a, y, 1 - y, g_k), d1 (g_s, 0,
+// 0, 0)) and a bit per node (word i / 32) set when an operand is outside the
 // double-float range.
 struct SymNodes {
   const float4* d0;
@@ -80,7 +92,26 @@ __global__ void sym_nodes_kernel(const double* __restrict__ x, const double* __r
        w0 += static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5)) {
     const int64_t i = w0 * 32 + (threadIdx.x & 31);
     bool bad = false;
-    if (i < n) {
+    if (f32_kind(kKind) && i < n) {
+      constexpr bool kG = base_kind(kKind) == kSymBwd;
+      const double a = kW ? x[i] * y[i] : x[i];
+      bad = !df_safe_a(a);
+      float4 v = make_float4(__double2float_rn(a), 0.0f, 0.0f, 0.0f);
+      if constexpr (kW) {
+        v.y = __double2float_rn(y[i]);
+        v.z = __double2float_rn(1.0 - y[i]);  // 1 - y_i y_j = (1 - y_i) + y_i (1 - y_j) without cancellation
+        bad = bad || !df_safe_y(y[i]);
+        if constexpr (kG) {
+          v.w = __double2float_rn(gk[i]);
+          d1[i] = make_float4(__double2float_rn(gs[i]), 0.0f, 0.0f, 0.0f);
+          bad = bad || !df_safe_g(gk[i]) || !df_safe_g(gs[i]);
+        }
+      } else if constexpr (kG) {
+        v.y = __double2float_rn(gk[i]);
+        bad = bad || !df_safe_g(gk[i]);
+      }
+      d0[i] = v;
+    } else if (i < n) {
       const double a = kW ? x[i] * y[i] : x[i];
       const df2 av = df_from_double(a);
       bad = !df_safe_a(a);
@@ -161,6 +192,47 @@ __device__ __forceinline__ void sym_terms(float4 r0, float4 r1, float4 c0, float
   }
 }
 
+// FP32 terms of one pair (kinds kSymDiagF, kSymBwdF), the same expressions as
+// sym_terms; with the operands in the double-float range every intermediate
+// is a normal FP32 number (D^2 <= 2^120, 1 - r >= 2^-11).
+template <int kModel, int kKind>
+__device__ __forceinline__ void sym_terms_f32(float4 r0, float4 r1, float4 c0, float4 c1, float* tr, float* tc) {
+  const float ai = r0.x, aj = c0.x;
+  if constexpr (kModel == MH_UBCM) {
+    const float opz = fmaf(ai, aj, 1.0f);
+    const float num = kKind == kSymBwdF ? r0.y + c0.y : 1.0f;
+    const float F = __fdividef(num, opz * opz);
+    tr[0] = aj * F;
+    tc[0] = ai * F;
+  } else {
+    const float r = r0.y * c0.y;
+    const float omr = fmaf(r0.y, c0.z, r0.z);  // (1 - y_i) + y_i (1 - y_j)
+    const float D = fmaf(ai, aj, omr);
+    const float H = __fdividef(1.0f, D * D);
+    const float rc = __fdividef(1.0f, omr);
+    const float fr = fmaf(r, D, omr) * rc * rc;  // (1 - r + r D) / (1 - r)^2
+    if constexpr (kKind == kSymDiagF) {
+      const float s0 = omr * H;
+      const float s2 = H * fr;
+      tr[0] = aj * s0;
+      tr[1] = aj * H;
+      tr[2] = aj * s2;
+      tc[0] = ai * s0;
+      tc[1] = ai * H;
+      tc[2] = ai * s2;
+    } else {
+      const float gk = r0.w + c0.w;
+      const float gsum = r1.x + c1.x;
+      const float U = fmaf(gk, omr, gsum) * H;
+      const float V = fmaf(gsum, fr, gk) * H;
+      tr[0] = aj * U;
+      tr[1] = aj * V;
+      tc[0] = ai * U;
+      tc[1] = ai * V;
+    }
+  }
+}
+
 // FP64 terms of one pair (tiles with an operand outside the double-float range).
 template <int kModel, int kKind>
 __device__ __noinline__ void sym_terms_fp64(const double* x, const double* y, const double* gk, const double* gs,
@@ -224,6 +296,12 @@ __device__ __forceinline__ void unit_bands(int64_t u, int64_t nb, int64_t& I, in
 __device__ __forceinline__ float4 node_or_zero(const float4* d, int64_t i, int64_t n) {
   return i < n ? d[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
+// Past the last node: a = 0 with y = 0 (1 - y = 1 for the FP32 kinds'
+// third word), so the pair terms are zero and finite.
+template <bool kF>
+__device__ __forceinline__ float4 node_or_pad(const float4* d, int64_t i, int64_t n) {
+  return i < n ? d[i] : make_float4(0.0f, 0.0f, kF ? 1.0f : 0.0f, 0.0f);
+}
 __device__ __forceinline__ bool node_unsafe(const unsigned* unsafe, int64_t i, int64_t n) {
   return i < n && ((unsafe[i >> 5] >> (i & 31)) & 1u);
 }
@@ -239,6 +317,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
                                                                    int64_t L, int64_t nb, double* __restrict__ P) {
   constexpr int kQ = SymCount<kModel, kKind>::kQ;
   constexpr bool kTwo = SymCount<kModel, kKind>::kTwo;
+  constexpr bool kF = f32_kind(kKind);
   __shared__ float4 cst0[kSymWarps][32];
   __shared__ float4 cst1[kTwo ? kSymWarps : 1][32];
   // a tile's row partials: double-float (hi, lo) bits, or FP64 bits where the
@@ -264,7 +343,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
     for (int64_t s = 0; s < L && cb + s < n; s += kSubBand) {
       const int64_t cw = cb + s + 32 * warp;  // the warp's first column
       const int64_t j = cw + lane;
-      cst0[warp][lane] = node_or_zero(N.d0, j, n);
+      cst0[warp][lane] = node_or_pad<kF>(N.d0, j, n);
       if constexpr (kTwo) cst1[warp][lane] = node_or_zero(N.d1, j, n);
       const unsigned cbad = __ballot_sync(kAll, node_unsafe(N.unsafe, j, n));
       __syncwarp();
@@ -283,7 +362,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int64_t i = r0 + 32 * h + lane;
-          rd0[h] = node_or_zero(N.d0, i, n);
+          rd0[h] = node_or_pad<kF>(N.d0, i, n);
           rd1[h] = kTwo ? node_or_zero(N.d1, i, n) : rd0[h];
           rbad |= __ballot_sync(kAll, node_unsafe(N.unsafe, i, n));
           const int64_t rh = 2 * rt + h;  // row sub-tile (of 32) within the band
@@ -302,7 +381,72 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
         const bool any_full = mode[0] == 2 || mode[1] == 2;
         if (mode[0] | mode[1]) {
           const int t0 = any_full ? 0 : 1, t1 = any_full ? 32 : 17;
-          if ((rbad | cbad) == 0u && mode[0] == 2 && mode[1] == 2) {
+          if (kF && (rbad | cbad) == 0u && mode[0] == 2 && mode[1] == 2) {
+            // FP32 kinds, every pair of the tile: FP32 sums over the tile
+            float ra[2][kQ], cf[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) ra[0][q] = ra[1][q] = cf[q] = 0.0f;
+#pragma unroll 4
+            for (int t = 0; t < 32; ++t) {
+              const int c = (lane + t) & 31;
+              const float4 c0 = cst0[warp][c];
+              const float4 c1 = kTwo ? cst1[warp][c] : c0;
+              const int from = (lane - t) & 31;
+              float tr0[kQ], tc0[kQ], tr1[kQ], tc1[kQ];
+              sym_terms_f32<kModel, kKind>(rd0[0], rd1[0], c0, c1, tr0, tc0);
+              sym_terms_f32<kModel, kKind>(rd0[1], rd1[1], c0, c1, tr1, tc1);
+#pragma unroll
+              for (int q = 0; q < kQ; ++q) {
+                ra[0][q] += tr0[q];
+                ra[1][q] += tr1[q];
+                cf[q] += __shfl_sync(kAll, tc0[q] + tc1[q], from);  // both rows meet the same column
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+              cacc[q].add(df2{cf[q], 0.0f});
+              cacc[q].norm();
+              rsum[0][q] = df2{ra[0][q], 0.0f};
+              rsum[1][q] = df2{ra[1][q], 0.0f};
+            }
+          } else if (kF && (rbad | cbad) == 0u) {
+            float ra[2][kQ], cf[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) ra[0][q] = ra[1][q] = cf[q] = 0.0f;
+#pragma unroll 2
+            for (int t = t0; t < t1; ++t) {
+              const int c = (lane + t) & 31;
+              const float4 c0 = cst0[warp][c];
+              const float4 c1 = kTwo ? cst1[warp][c] : c0;
+              const int from = (lane - t) & 31;
+              float cs[kQ];
+#pragma unroll
+              for (int q = 0; q < kQ; ++q) cs[q] = 0.0f;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                float tr[kQ], tc[kQ];
+                sym_terms_f32<kModel, kKind>(rd0[h], rd1[h], c0, c1, tr, tc);
+                // a diagonal sub-tile takes steps 1..16, step 16 on lanes 0..15 only
+                const bool use = mode[h] == 2 || (mode[h] == 1 && t >= 1 && (t < 16 || (t == 16 && lane < 16)));
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                  if (use) {
+                    ra[h][q] += tr[q];
+                    cs[q] += tc[q];
+                  }
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < kQ; ++q) cf[q] += __shfl_sync(kAll, cs[q], from);
+            }
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+              cacc[q].add(df2{cf[q], 0.0f});
+              cacc[q].norm();
+              rsum[0][q] = df2{ra[0][q], 0.0f};
+              rsum[1][q] = df2{ra[1][q], 0.0f};
+            }
+          } else if ((rbad | cbad) == 0u && mode[0] == 2 && mode[1] == 2) {
             // every pair of the tile, no per-step checks (all tiles of off-diagonal units)
             DfAcc ra[2][kQ];
 #pragma unroll 4
@@ -314,7 +458,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 df2 tr[kQ], tc[kQ];
-                sym_terms<kModel, kKind>(rd0[h], rd1[h], c0, c1, tr, tc);
+                sym_terms<kModel, base_kind(kKind)>(rd0[h], rd1[h], c0, c1, tr, tc);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                   ra[h][q].add(tr[q]);
@@ -352,7 +496,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 df2 tr[kQ], tc[kQ];
-                sym_terms<kModel, kKind>(rd0[h], rd1[h], c0, c1, tr, tc);
+                sym_terms<kModel, base_kind(kKind)>(rd0[h], rd1[h], c0, c1, tr, tc);
                 // a diagonal sub-tile takes steps 1..16, step 16 on lanes 0..15 only
                 const bool use = mode[h] == 2 || (mode[h] == 1 && t >= 1 && (t < 16 || (t == 16 && lane < 16)));
 #pragma unroll
@@ -399,7 +543,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) sym_pairs_kernel(SymNodes N, c
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) tr[q] = tc[q] = 0.0;
                 const bool use = mode[h] == 2 || (mode[h] == 1 && t >= 1 && (t < 16 || (t == 16 && lane < 16)));
-                if (use && i < n && jj < n) sym_terms_fp64<kModel, kKind>(x, y, gk, gs, i, jj, tr, tc);
+                if (use && i < n && jj < n) sym_terms_fp64<kModel, base_kind(kKind)>(x, y, gk, gs, i, jj, tr, tc);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                   rs[h][q] += tr[q];
@@ -466,6 +610,7 @@ __global__ void sym_reduce_kernel(const double* __restrict__ P, int64_t n, int64
                                   double* __restrict__ o0, double* __restrict__ o1, double* __restrict__ o2,
                                   double* __restrict__ o3) {
   constexpr int kQ = SymCount<kModel, kKind>::kQ;
+  constexpr int kB = base_kind(kKind);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double S[kQ];
@@ -477,10 +622,10 @@ __global__ void sym_reduce_kernel(const double* __restrict__ P, int64_t n, int64
     }
     if constexpr (kModel == MH_UBCM) {
       o0[i] = S[0];
-    } else if constexpr (kKind == kSymFwd) {
+    } else if constexpr (kB == kSymFwd) {
       o0[i] = S[0];
       o1[i] = S[1];
-    } else if constexpr (kKind == kSymDiag) {
+    } else if constexpr (kB == kSymDiag) {
       const double xi = x[i], yi = y[i];
       o0[i] = yi * S[0];
       o1[i] = xi * S[1];
@@ -525,7 +670,7 @@ SymLayout sym_layout(int model, int64_t n) {
   return S;
 }
 
-int g_occ_sym[2][3][64];
+int g_occ_sym[2][5][64];
 
 template <int kModel, int kKind>
 cudaError_t run_sym(const double* x, const double* y, const double* gk, const double* gs, int64_t n, char* ws,
@@ -570,10 +715,14 @@ cudaError_t launch_expected_sym(int kind, int model, const double* x, const doub
   if (model == MH_UBCM) {
     if (kind == kSymFwd) return run_sym<MH_UBCM, kSymFwd>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
     if (kind == kSymDiag) return run_sym<MH_UBCM, kSymDiag>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
+    if (kind == kSymDiagF) return run_sym<MH_UBCM, kSymDiagF>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
+    if (kind == kSymBwdF) return run_sym<MH_UBCM, kSymBwdF>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
     return run_sym<MH_UBCM, kSymBwd>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
   }
   if (kind == kSymFwd) return run_sym<MH_UECM, kSymFwd>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
   if (kind == kSymDiag) return run_sym<MH_UECM, kSymDiag>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
+  if (kind == kSymDiagF) return run_sym<MH_UECM, kSymDiagF>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
+  if (kind == kSymBwdF) return run_sym<MH_UECM, kSymBwdF>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
   return run_sym<MH_UECM, kSymBwd>(x, y, gk, gs, n, ws, o0, o1, o2, o3, st);
 }
 

@@ -72,19 +72,24 @@ class FitResult:
 class _LocalSums:
     """The sums of a fit on this process's GPU (the module's functions, looked
     up at call time): each unordered pair evaluated once for both of its rows
-    (the symmetric forms), with one scratch buffer for the fit."""
+    (the symmetric forms), with one scratch buffer for the fit.  The residual
+    (fwd) takes the double-float terms; the Newton direction's products (bwd)
+    and preconditioner (diag) take the FP32 terms unless f32_direction is
+    False: conjugate gradients stopped at a relative residual of 5e-2 need
+    nothing closer than their 1e-5."""
 
-    def __init__(self):
+    def __init__(self, f32_direction: bool = True):
         self.ws = SymWorkspace()
+        self.f32 = f32_direction
 
     def fwd(self, model, x, y=None):
         return expected_fwd(model, x, y, sym=self.ws)
 
     def bwd(self, model, x, y, g_k, g_s=None):
-        return expected_bwd(model, x, y, g_k, g_s, sym=self.ws)
+        return expected_bwd(model, x, y, g_k, g_s, sym=self.ws, f32=self.f32)
 
     def diag(self, model, x, y=None):
-        return expected_jacobian_diag(model, x, y, sym=self.ws)
+        return expected_jacobian_diag(model, x, y, sym=self.ws, f32=self.f32)
 
 
 def _residual(model, x, y, k_t, s_t, ops):

@@ -377,9 +377,11 @@ def expected_fwd(model: int, x: torch.Tensor, y: torch.Tensor | None = None, str
 
 
 def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch.Tensor,
-                 g_s: torch.Tensor | None = None, stream=None, rows=None, sym: SymWorkspace | None = None):
+                 g_s: torch.Tensor | None = None, stream=None, rows=None, sym: SymWorkspace | None = None,
+                 f32: bool = False):
     """(dL/dx, dL/dy) given dL/d<k>, dL/d<s> (FP64 CUDA tensors); rows and
-    sym as in expected_fwd."""
+    sym as in expected_fwd.  f32 (with sym): FP32 pair terms, within about
+    1e-5 of the sum of the terms' magnitudes (Newton directions)."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
@@ -388,10 +390,13 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
     begin, count = _row_range(rows, n)
     gx = torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
     gy = torch.empty_like(gx) if model == nat.MH_UECM else None
+    if f32 and sym is None:
+        raise ValueError("f32 needs the symmetric form (sym=SymWorkspace())")
     if sym is not None:
         ws, need = _sym_args(sym, model, n, x.device, rows)
-        rc = nat.maxent_expected_bwd_sym(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy), ws,
-                                         need, _stream_handle(stream))
+        fn = nat.maxent_expected_bwd_sym_f32 if f32 else nat.maxent_expected_bwd_sym
+        rc = fn(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy), ws, need,
+                _stream_handle(stream))
     elif rows is None:
         rc = nat.maxent_expected_bwd(model, _ptr(x), _ptr(y), n, _ptr(g_k), _ptr(g_s), _ptr(gx), _ptr(gy),
                                      _stream_handle(stream))
@@ -403,11 +408,11 @@ def expected_bwd(model: int, x: torch.Tensor, y: torch.Tensor | None, g_k: torch
 
 
 def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None, rows=None,
-                           sym: SymWorkspace | None = None):
+                           sym: SymWorkspace | None = None, f32: bool = False):
     """(d<k>/dx,) for the UBCM or (d<k>/dx, d<k>/dy, d<s>/dx, d<s>/dy) for the
     UECM: each node's derivatives of its own expected degree (and strength)
-    with respect to its own parameters, FP64 CUDA tensors; rows and sym as in
-    expected_fwd."""
+    with respect to its own parameters, FP64 CUDA tensors; rows, sym and f32
+    as in expected_fwd and expected_bwd."""
     x = _check_vec("x", x)
     n = int(x.shape[0])
     y = _check_vec("y", y, n) if model == nat.MH_UECM else None
@@ -415,10 +420,12 @@ def expected_jacobian_diag(model: int, x: torch.Tensor, y: torch.Tensor | None =
     outs = [torch.empty(max(count, 0), dtype=torch.float64, device=x.device)
             for _ in range(1 if model == nat.MH_UBCM else 4)]
     ptrs = [_ptr(t) for t in outs] + [None] * (4 - len(outs))
+    if f32 and sym is None:
+        raise ValueError("f32 needs the symmetric form (sym=SymWorkspace())")
     if sym is not None:
         ws, need = _sym_args(sym, model, n, x.device, rows)
-        rc = nat.maxent_expected_jacobian_diag_sym(model, _ptr(x), _ptr(y), n, *ptrs, ws, need,
-                                                   _stream_handle(stream))
+        fn = nat.maxent_expected_jacobian_diag_sym_f32 if f32 else nat.maxent_expected_jacobian_diag_sym
+        rc = fn(model, _ptr(x), _ptr(y), n, *ptrs, ws, need, _stream_handle(stream))
     elif rows is None:
         rc = nat.maxent_expected_jacobian_diag(model, _ptr(x), _ptr(y), n, *ptrs, _stream_handle(stream))
     else:

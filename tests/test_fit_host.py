@@ -25,12 +25,12 @@ def oracle_kernels(monkeypatch):
         k, s = oracle.expected_fwd(model, _np(x), _np(y))
         return torch.from_numpy(k), None if s is None else torch.from_numpy(s)
 
-    def bwd(model, x, y, g_k, g_s=None, stream=None, rows=None, sym=None):
+    def bwd(model, x, y, g_k, g_s=None, stream=None, rows=None, sym=None, f32=False):
         calls["bwd"] += 1
         gx, gy = oracle.expected_bwd(model, _np(x), _np(y), _np(g_k), _np(g_s))
         return torch.from_numpy(gx), None if gy is None else torch.from_numpy(gy)
 
-    def diag(model, x, y=None, stream=None, rows=None, sym=None):
+    def diag(model, x, y=None, stream=None, rows=None, sym=None, f32=False):
         calls["diag"] += 1
         return tuple(torch.from_numpy(a) for a in oracle.expected_jacobian_diag(model, _np(x), _np(y)))
 

@@ -187,14 +187,16 @@ def test_jacobian_vector_product_is_the_symmetric_vjp(model):
     # fit() uses J v = (backward kernel with upstream v) * (x, y) in
     # log-parameters; check it against central differences of the oracle's
     # sums along a random direction.
-    from paper_2509_13230_gb300.expected import _jvp
+    from paper_2509_13230_gb300.expected import _LocalSums, _jvp
     rng = np.random.default_rng(16)
     n = 300
     theta = rng.normal(-1.5, 1.0, n)
     phi = np.log(rng.uniform(0.2, 0.9, n)) if model == nat.MH_UECM else None
     v = [rng.normal(size=n)] + ([rng.normal(size=n)] if model == nat.MH_UECM else [])
     x, y = np.exp(theta), None if phi is None else np.exp(phi)
-    got = _jvp(model, dev(x), None if y is None else dev(y), tuple(dev(a) for a in v))
+    got = _jvp(model, dev(x), None if y is None else dev(y), tuple(dev(a) for a in v),
+               _LocalSums(f32_direction=False))
+    got32 = _jvp(model, dev(x), None if y is None else dev(y), tuple(dev(a) for a in v), _LocalSums())
     eps = 1e-6
 
     def sums(sign):
@@ -204,8 +206,10 @@ def test_jacobian_vector_product_is_the_symmetric_vjp(model):
 
     (kp, sp), (km, sm) = sums(1), sums(-1)
     fd = [(kp - km) / (2 * eps)] + ([(sp - sm) / (2 * eps)] if model == nat.MH_UECM else [])
-    for g, f in zip(got, fd):
+    for g, g32, f in zip(got, got32, fd):
         np.testing.assert_allclose(g.cpu().numpy(), f, rtol=1e-6, atol=1e-8 * np.abs(f).max())
+        # the fit's default: FP32 terms for the Newton direction
+        np.testing.assert_allclose(g32.cpu().numpy(), f, rtol=1e-4, atol=1e-5 * np.abs(f).max())
 
 
 def test_fit_then_sample_full_size():

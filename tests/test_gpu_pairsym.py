@@ -149,3 +149,40 @@ def test_sym_argument_errors():
     assert nat.maxent_expected_fwd_sym(UECM, _ptr(X), _ptr(Y), n, _ptr(k), _ptr(s), _ptr(ws), need,
                                        stream) == nat.MH_OK
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("model", [UBCM, UECM])
+@pytest.mark.parametrize("n", [1, 33, 2049, 6145])
+def test_f32_forms_within_their_bound(model, n):
+    """The FP32 forms (Newton directions) against the double-float forms:
+    within 2e-5 of the sum of the terms' magnitudes (FP32 terms of a few ulp,
+    FP32 sums over tiles of 32 and 64 terms), extremes taking FP64 tiles."""
+    x, y = params(model, n, 500 + n, extremes=True)
+    X, Y = dev(x), dev(y)
+    ws = SymWorkspace()
+    got = expected_jacobian_diag(model, X, Y, sym=ws, f32=True)
+    ref = expected_jacobian_diag(model, X, Y, sym=ws)
+    for g, r in zip(got, ref):
+        r = r.cpu().numpy()
+        close(g.cpu().numpy(), r, np.abs(r), tol=2e-5)  # positive terms
+    rng = np.random.default_rng(n + 1)
+    GK = dev(rng.normal(size=n))
+    GS = dev(rng.normal(size=n)) if model == UECM else None
+    gx, gy = expected_bwd(model, X, Y, GK, GS, sym=ws, f32=True)
+    rx, ry = expected_bwd(model, X, Y, GK, GS, sym=ws)
+    ax, ay = expected_bwd(model, X, Y, GK.abs(), None if GS is None else GS.abs(), sym=ws)
+    close(gx.cpu().numpy(), rx.cpu().numpy(), ax.cpu().numpy(), tol=2e-5)
+    if model == UECM:
+        close(gy.cpu().numpy(), ry.cpu().numpy(), ay.cpu().numpy(), tol=2e-5)
+    # deterministic, like the other symmetric forms
+    gx2, _ = expected_bwd(model, X, Y, GK, GS, sym=SymWorkspace(), f32=True)
+    assert torch.equal(gx, gx2)
+
+
+def test_f32_forms_need_the_symmetric_form():
+    x, y = params(UECM, 10, 1)
+    X, Y = dev(x), dev(y)
+    with pytest.raises(ValueError):
+        expected_jacobian_diag(UECM, X, Y, f32=True)
+    with pytest.raises(ValueError):
+        expected_bwd(UECM, X, Y, X, X, f32=True)
