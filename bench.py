@@ -397,13 +397,17 @@ PAIR_N = 200_000
 # the y term (6 ops), two sums.  Jacobian diagonal: A, r, 1 - r, D, D^2, Q,
 # (1 - r) Q, r D, 1 - r + r D, (1 - r)^2, a division and a product, three sums.
 PAIR_OPS = {"fwd": 81, "bwd": 185, "jacobian_diag": 136}
-# the symmetric forms, per unordered pair: the shared terms once, both rows' and
-# both columns' accumulations (8 per term and 6 per 8-term renormalisation)
-PAIR_SYM_OPS = {"fwd": 99, "bwd": 231, "jacobian_diag": 205}
-# the FP32 forms (Newton directions): r, 1 - r, D, D^2, two reciprocals, the
-# factor (1 - r + r D) / (1 - r)^2 (3), then bwd: g sums (2), U and V (4), four
-# products; diag: two products, six; both: the row and column sums (4 or 6)
-PAIR_SYM_F32_OPS = {"bwd": 23, "jacobian_diag": 23}
+# the symmetric forms, per unordered pair (products and quotients without the
+# renormalising fast_two_sum: 4 and 8 operations plus the reciprocal): the
+# shared terms once (forward 42, backward 141, Jacobian diagonal 97), both
+# rows' and both columns' accumulations (8 per term and 6 per 8-term
+# renormalisation: 35 for two quantities, 53 for three)
+PAIR_SYM_OPS = {"fwd": 77, "bwd": 176, "jacobian_diag": 150}
+# the FP32 forms (Newton directions): r, 1 - r, D, D^2, the factor
+# (1 - r + r D) / (1 - r)^2 (3, with two reciprocals), then bwd: g sums (2),
+# U and V (4), four products; diag: two products, six; both: the row sums and
+# the column sums (two rows' column terms added before the shuffle)
+PAIR_SYM_F32_OPS = {"bwd": 21, "jacobian_diag": 21}
 FP32_LANES_PER_SM = 128
 
 
