@@ -389,14 +389,14 @@ def ensemble_leg(args, dev, flush, fitness="pareto", samples=None, capacity=None
 # ---------------------------------------------------------------------------
 PAIR_N = 200_000
 # FP32 operations per ordered pair of the UECM double-float evaluation,
-# counted from its operation sequence (two_sum 6, fast_two_sum 3, df_mul 7,
-# sloppy addition 11, 1 - r 7, df_div 16 with each division as reciprocal +
-# multiply, accumulation 8 per term plus a 6-operation renormalisation every
-# 8 terms).  Forward: a_i a_j, y_i y_j, 1 - r, D, two divisions, two sums.
-# Backward: r, 1 - r, A, D, D^2, Q, g_k and g_s sums, the x term (3 ops) and
-# the y term (6 ops), two sums.  Jacobian diagonal: A, r, 1 - r, D, D^2, Q,
-# (1 - r) Q, r D, 1 - r + r D, (1 - r)^2, a division and a product, three sums.
-PAIR_OPS = {"fwd": 81, "bwd": 185, "jacobian_diag": 136}
+# counted from its operation sequence (two_sum 6, fast_two_sum 3, products 4
+# and quotients 8 plus a reciprocal, both left unnormalised, sloppy addition
+# 11, 1 - r 7, accumulation 8 per term plus a 6-operation renormalisation
+# every 8 terms).  Forward: a_i a_j, y_i y_j, 1 - r, D, two divisions, two
+# sums.  Backward: r, 1 - r, A, D, D^2, Q, g_k and g_s sums, the x term and
+# the y term, two sums.  Jacobian diagonal: A, r, 1 - r, D, D^2, Q, (1 - r) Q,
+# r D, 1 - r + r D, (1 - r)^2, a division and a product, three sums.
+PAIR_OPS = {"fwd": 59, "bwd": 142, "jacobian_diag": 99}
 # the symmetric forms, per unordered pair (products and quotients without the
 # renormalising fast_two_sum: 4 and 8 operations plus the reciprocal): the
 # shared terms once (forward 42, backward 141, Jacobian diagonal 97), both

@@ -1,6 +1,7 @@
 // Double-float helpers shared by the pairwise kernels (pairwise.cu,
 // pairsym.cu): the operand ranges the double-float terms accept, the
-// compensated accumulator and 1 - r.
+// compensated accumulator, 1 - r, and products and quotients whose results
+// stay unnormalised.
 #pragma once
 
 #include "walk_math.cuh"
@@ -40,6 +41,25 @@ struct DfAcc {
 __device__ __forceinline__ df2 one_minus(df2 r) {
   const df2 s = fast_two_sum(1.0f, -r.hi);
   return fast_two_sum(s.hi, s.lo - r.lo);
+}
+
+// Products and quotients of the pair terms without the final renormalising
+// fast_two_sum: every consumer in the pair kernels takes a pair whose low word is up to a
+// few units of 2^-24 of its high word (the quotient's residual subtracts the
+// high words exactly and the low words separately, the sloppy sums and the
+// accumulators add the words apart), so the value hi + lo keeps the same
+// accuracy at three fewer operations each.
+__device__ __forceinline__ df2 dfu_mul(df2 a, df2 b) {
+  const float p = a.hi * b.hi;
+  return df2{p, fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, fmaf(a.hi, b.hi, -p)))};
+}
+__device__ __forceinline__ df2 dfu_div(df2 a, df2 b) {
+  const float rc = __fdividef(1.0f, b.hi);
+  const float th = a.hi * rc;
+  const float p = b.hi * th;
+  const float e = fmaf(b.lo, th, fmaf(b.hi, th, -p));  // b th = p + e
+  // a.hi - p is exact: th is within a few ulp of a.hi / b.hi
+  return df2{th, ((a.hi - p) + (a.lo - e)) * rc};
 }
 
 }  // namespace mh

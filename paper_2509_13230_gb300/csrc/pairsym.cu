@@ -141,25 +141,6 @@ __global__ void sym_nodes_kernel(const double* __restrict__ x, const double* __r
   }
 }
 
-// Products and quotients of the pair terms without the final renormalising
-// fast_two_sum: every consumer below takes a pair whose low word is up to a
-// few units of 2^-24 of its high word (the quotient's residual subtracts the
-// high words exactly and the low words separately, the sloppy sums and the
-// accumulators add the words apart), so the value hi + lo keeps the same
-// accuracy at three fewer operations each.
-__device__ __forceinline__ df2 dfu_mul(df2 a, df2 b) {
-  const float p = a.hi * b.hi;
-  return df2{p, fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, fmaf(a.hi, b.hi, -p)))};
-}
-__device__ __forceinline__ df2 dfu_div(df2 a, df2 b) {
-  const float rc = __fdividef(1.0f, b.hi);
-  const float th = a.hi * rc;
-  const float p = b.hi * th;
-  const float e = fmaf(b.lo, th, fmaf(b.hi, th, -p));  // b th = p + e
-  // a.hi - p is exact: th is within a few ulp of a.hi / b.hi
-  return df2{th, ((a.hi - p) + (a.lo - e)) * rc};
-}
-
 // Double-float terms of one pair: tr for the row (factor a_j), tc for the
 // column (factor a_i).  r0/c0: d0 of the row and column node, r1/c1: d1.
 template <int kModel, int kKind>

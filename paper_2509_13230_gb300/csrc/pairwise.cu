@@ -115,26 +115,26 @@ __device__ __noinline__ void row_terms_fp64(double xi, double yi, double xj, dou
 template <int kModel, int kKind>
 __device__ __forceinline__ void row_terms(df2 ai, df2 yi, float4 c, df2* t) {
   const df2 aj{c.x, c.y};
-  const df2 prod = df_mul(ai, aj);
+  const df2 prod = dfu_mul(ai, aj);
   if constexpr (kModel == MH_UBCM) {
     const df2 opz = df_add_f(prod, 1.0f);
     if constexpr (kKind == kExpectedSums) {
-      t[0] = df_div(prod, opz);
+      t[0] = dfu_div(prod, opz);
     } else {
-      t[0] = df_div(aj, df_mul(opz, opz));
+      t[0] = dfu_div(aj, dfu_mul(opz, opz));
     }
   } else {
-    const df2 r = df_mul(yi, df2{c.z, c.w});
+    const df2 r = dfu_mul(yi, df2{c.z, c.w});
     const df2 omr = one_minus(r);
     const df2 D = df_add_sloppy(omr, prod);  // both >= 0
     if constexpr (kKind == kExpectedSums) {
-      t[0] = df_div(prod, D);
-      t[1] = df_div(t[0], omr);
+      t[0] = dfu_div(prod, D);
+      t[1] = dfu_div(t[0], omr);
     } else {
-      const df2 Q = df_div(aj, df_mul(D, D));
-      t[0] = df_mul(omr, Q);
+      const df2 Q = dfu_div(aj, dfu_mul(D, D));
+      t[0] = dfu_mul(omr, Q);
       t[1] = Q;
-      t[2] = df_mul(Q, df_div(df_add_sloppy(omr, df_mul(r, D)), df_mul(omr, omr)));  // (1 - r + r D) / (1 - r)^2
+      t[2] = dfu_mul(Q, dfu_div(df_add_sloppy(omr, dfu_mul(r, D)), dfu_mul(omr, omr)));  // (1 - r + r D) / (1 - r)^2
     }
   }
 }
@@ -325,21 +325,21 @@ template <int kModel>
 __device__ __forceinline__ void bwd_term(const BwdRow& R, float4 c0, float4 c1, df2& tx, df2& ty) {
   if (kModel == MH_UBCM) {
     const df2 xj{c0.x, c0.y};
-    const df2 opz = df_add_f(df_mul(R.v, xj), 1.0f);
+    const df2 opz = df_add_f(dfu_mul(R.v, xj), 1.0f);
     const df2 gk = df_add_sloppy(R.gk, df2{c0.z, c0.w});
-    tx = df_mul(gk, df_div(xj, df_mul(opz, opz)));
+    tx = dfu_mul(gk, dfu_div(xj, dfu_mul(opz, opz)));
     return;
   }
   const df2 aj{c0.x, c0.y};
-  const df2 r = df_mul(R.y, df2{c0.z, c0.w});
+  const df2 r = dfu_mul(R.y, df2{c0.z, c0.w});
   const df2 omr = one_minus(r);
-  const df2 D = df_add_sloppy(omr, df_mul(R.v, aj));  // both >= 0
-  const df2 Q = df_div(aj, df_mul(D, D));
+  const df2 D = df_add_sloppy(omr, dfu_mul(R.v, aj));  // both >= 0
+  const df2 Q = dfu_div(aj, dfu_mul(D, D));
   const df2 gk = df_add_sloppy(R.gk, df2{c1.x, c1.y});
   const df2 gs = df_add_sloppy(R.gs, df2{c1.z, c1.w});
-  tx = df_mul(df_add_sloppy(df_mul(gk, omr), gs), Q);
-  const df2 fr = df_div(df_add_sloppy(omr, df_mul(r, D)), df_mul(omr, omr));  // (1 - r + r D) / (1 - r)^2
-  ty = df_mul(df_add_sloppy(gk, df_mul(gs, fr)), Q);
+  tx = dfu_mul(df_add_sloppy(dfu_mul(gk, omr), gs), Q);
+  const df2 fr = dfu_div(df_add_sloppy(omr, dfu_mul(r, D)), dfu_mul(omr, omr));  // (1 - r + r D) / (1 - r)^2
+  ty = dfu_mul(df_add_sloppy(gk, dfu_mul(gs, fr)), Q);
 }
 
 template <int kModel>
