@@ -10,9 +10,8 @@
 //   weight (Eq. 4): w = 1 + floor(log(U_w) / log(r))
 // with a = x y and the FP64 library log / log1p.
 //
-// Fast path.  A draw is first decided in double-float arithmetic: values
-// are unevaluated sums hi + lo of two FP32 numbers (about 48 significant
-// bits), built from error-free transformations (Dekker 1971; Joldes, Muller,
+// Fast path.  Values are unevaluated sums hi + lo of two FP32 numbers,
+// built from error-free transformations (Dekker 1971; Joldes, Muller,
 // Popescu, "Tight and rigorous error bounds for basic building blocks of
 // double-word arithmetic", 2017).  Logarithms use Tang's table-driven method
 // ("Table-driven implementation of the logarithm function in IEEE
@@ -21,13 +20,17 @@
 // alternating series.  With these
 //   t = E / lambda,  E = -ln U,  lambda = -ln(1 - q) = log1p(z)  (UBCM)
 //                                              = log1p(A / (1 - c))  (UECM)
-// is known to a relative error far below 2^-36; the skip is decided when t
-// lies more than t 2^-36 + 2^-40 from every integer, the acceptance when
-// V lies more than p/q 2^-18 from p/q (estimated in FP32).  Anything else,
-// and any input outside the fast path's range, takes the canonical FP64
-// path above, so decisions equal the canonical ones except where the device
-// and host FP64 logarithms themselves round differently (draws within a few
-// ulp of an integer boundary).
+// is estimated twice: by the first level (FP32 pairs whose low words carry
+// only the leading error terms, within 2^-30.4 t of the canonical t; the skip
+// is decided when t lies more than t 2^-28 + 2^-22 from every integer) and,
+// for the few draws that level leaves, by full double-float arithmetic
+// (about 48 significant bits, relative error far below 2^-36; decided when t
+// lies more than t 2^-36 + 2^-40 from every integer).  The acceptance is
+// decided when V lies more than p/q 2^-18 from the FP32 estimate of p/q.
+// Anything else, and any input outside the fast path's range, takes the
+// canonical FP64 path above, so decisions equal the canonical ones except
+// where the device and host FP64 logarithms themselves round differently
+// (draws within a few ulp of an integer boundary).
 //
 // Fast range.  lambda above is the exact -ln(1 - q) of the exact q, while
 // the canonical t divides by log1p(-fl(q)): q = z / (1 + z) carries two
@@ -36,7 +39,7 @@
 // z 2^-52 / ln(1 + z) (z = x_i x_j, or A / fl(1 - c) for the UECM bound),
 // which grows without limit in z: 2^-36 at z = 2^21.  The fast levels take
 // only q with z < kFastZq = 2^16, where that term is at most 2^-39.5, below a
-// ninth of the double-float margin (and far below the FP32 one); larger z go
+// ninth of the double-float margin (and far below the first level's); larger z go
 // to the canonical FP64 path.  The acceptance quotient p/q and the weight's
 // ln r carry no such term (p/q is a ratio of two values near 1 with relative
 // errors of a few 2^-53; fl(y_i y_j) moves ln r by at most 2^-53 against
@@ -535,9 +538,9 @@ __device__ __forceinline__ int32_t draw_weight(uint32_t e, uint32_t k, uint32_t 
   const unsigned long long N = (e & 1u) ? top53(w.w, w.z) + 1ull : top53(w.y, w.x) + 1ull;
   const df2 nlr = df_add(lnyi, lnyj);  // ln r (negative)
   if (!fp64_only && nlr.hi < -0x1p-12f && nlr.hi > -0x1p+100f) {
-    // FP32 level: t = E / -ln r with E from the FP32 logarithm of U; the
-    // divisor is the double-float ln r rounded once, more accurate than the
-    // walk's FP32 log1p, so the walk's FP32 margin covers this quotient.
+    // FP32 level: t = E / -ln r with E from the FP32 logarithm of U (within
+    // 6u), the divisor the double-float ln r rounded once (0.5u) and a 2-ulp
+    // quotient: about 9u in all, far inside the margin 2^-18 t + 2^-22.
     bool ok;
     const float Ef = neg_ln_u53_f(N, tab, ok);
     if (ok) {
