@@ -131,7 +131,7 @@ struct SegWalker {
   // `accepted` / `j` when a candidate was evaluated (never on a head step).
   template <bool kUecm, bool kExcl = false, bool kLaneKey = false>
   __device__ __forceinline__ bool advance(const Net& g, const PhiloxKeys& rk, uint32_t key1, bool fp64_only,
-                                          bool init_prev, const LnEntry* tab, unsigned long long& fallbacks,
+                                          bool init_prev, const LnEntry* tab, unsigned& fallbacks,
                                           unsigned long long& boundary, bool& accepted, int32_t& j) {
     accepted = false;
     const bool head = fresh;
@@ -297,14 +297,27 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
   bool rewalk = false;           // second pass of an overflowing segment
   unsigned cnt = 0;              // edges of the current pass
   unsigned long long rbase = 0;  // staging base of a second pass
-  long long item = 0;
+  unsigned item = 0;  // a chunk or a wave holds fewer than 2^31 work items
   unsigned qpos = 0;        // batched: the lane's queue position (< 2^31)
   uint32_t lane_key1 = key1;
   int qcur = 0;             // batched: queue entry at or before the chunk's first position
   unsigned long long next = 0, end = 0;     // warp-uniform work cursor
-  unsigned long long wbase = 0, wleft = 0;  // warp-uniform staging chunk
+  unsigned long long wbase = 0;  // warp-uniform staging chunk: next free entry
+  unsigned wleft = 0;            // and entries left (at most kStageChunk)
   bool work_left = total > 0;
-  unsigned long long n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0, n_boundary = 0;
+  // Per-lane statistics in 32 bits (registers are the walk's occupancy limit),
+  // added to the call's 64-bit totals at the end and whenever n_draws passes
+  // 2^28: a segment adds fewer than 2^31 draws, at most two fallbacks per draw
+  // and pass, and at least one draw, so no counter wraps.
+  unsigned n_draws = 0, n_edges = 0, n_segs = 0, n_fallback = 0;
+  unsigned long long n_boundary = 0;
+  auto flush_stats = [&]() {
+    atomicAdd(&ctrl->stats[MH_STAT_PROPOSALS], static_cast<unsigned long long>(n_draws));
+    atomicAdd(&ctrl->stats[MH_STAT_EDGES], static_cast<unsigned long long>(n_edges));
+    atomicAdd(&ctrl->stats[MH_STAT_SEGMENTS], static_cast<unsigned long long>(n_segs));
+    atomicAdd(&ctrl->stats[MH_STAT_FALLBACKS], static_cast<unsigned long long>(n_fallback));
+    n_draws = n_edges = n_segs = n_fallback = 0;
+  };
 
   // A lane whose segment ended keeps its run in its slot (pending) until
   // the warp flushes: when kFlushMin runs are pending, or when no lane is
@@ -340,7 +353,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
         nb = __shfl_sync(0xffffffffu, nb, 0);
         if (lane >= first) my_base = nb + (excl - moved_excl);
         wbase = nb + rest;
-        wleft = want - rest;
+        wleft = static_cast<unsigned>(want - rest);
       } else {
         wbase += warp_need;
         wleft -= warp_need;
@@ -393,13 +406,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
           if (!active && !pending && rank < avail) {
             if (kBatch) {
               qpos = static_cast<unsigned>(next + rank);
-              item = begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1);
+              item = static_cast<unsigned>(begin_queued<kUecm>(g, P.q, next + rank, qcur, wk, lane_key1));
             } else {
-              item = static_cast<long long>(next + rank);
+              item = static_cast<unsigned>(next + rank);
               wk.begin<kExcl>(g, item, S, P.c.sample0, kUecm);
               // node-order CSR: the record goes to the segment's slot among its sample's rows
               if (P.c.seg_slot)
-                item = static_cast<long long>(wk.sample - P.c.sample0) * S + P.c.seg_slot[wk.seg];
+                item = (wk.sample - P.c.sample0) * static_cast<unsigned>(S) + static_cast<unsigned>(P.c.seg_slot[wk.seg]);
             }
             active = true;
             rewalk = false;
@@ -432,6 +445,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
       } else {
         n_draws += wk.d;
         n_edges += cnt;
+        if (n_draws >= (1u << 28)) flush_stats();
         if (cnt == 0) {
           active = false;  // nothing to place: the lane is free at once
           P.c.item_cnt[item] = 0;
@@ -457,19 +471,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 3) walk_kernel(WalkParams P) 
     }
   }
 
+  unsigned long long t_draws = n_draws, t_edges = n_edges, t_segs = n_segs, t_fallback = n_fallback;
 #pragma unroll
   for (int dd = 16; dd; dd >>= 1) {
-    n_draws += __shfl_xor_sync(0xffffffffu, n_draws, dd);
-    n_edges += __shfl_xor_sync(0xffffffffu, n_edges, dd);
-    n_segs += __shfl_xor_sync(0xffffffffu, n_segs, dd);
-    n_fallback += __shfl_xor_sync(0xffffffffu, n_fallback, dd);
+    t_draws += __shfl_xor_sync(0xffffffffu, t_draws, dd);
+    t_edges += __shfl_xor_sync(0xffffffffu, t_edges, dd);
+    t_segs += __shfl_xor_sync(0xffffffffu, t_segs, dd);
+    t_fallback += __shfl_xor_sync(0xffffffffu, t_fallback, dd);
     n_boundary += __shfl_xor_sync(0xffffffffu, n_boundary, dd);
   }
   if (lane == 0) {
-    atomicAdd(&ctrl->stats[MH_STAT_PROPOSALS], n_draws);
-    atomicAdd(&ctrl->stats[MH_STAT_EDGES], n_edges);
-    atomicAdd(&ctrl->stats[MH_STAT_SEGMENTS], n_segs);
-    atomicAdd(&ctrl->stats[MH_STAT_FALLBACKS], n_fallback);
+    atomicAdd(&ctrl->stats[MH_STAT_PROPOSALS], t_draws);
+    atomicAdd(&ctrl->stats[MH_STAT_EDGES], t_edges);
+    atomicAdd(&ctrl->stats[MH_STAT_SEGMENTS], t_segs);
+    atomicAdd(&ctrl->stats[MH_STAT_FALLBACKS], t_fallback);
     if (n_boundary) atomicAdd(&ctrl->stats[MH_STAT_BOUNDARY], n_boundary);
   }
 }
